@@ -1,0 +1,920 @@
+/*
+ * ezoracle.c -- plain, slow FP64 CPU oracle for the Epstein zeta method
+ * ("Epstein zeta method for many-body lattice sums", Buchheit & Busse).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py; never by the product path.  It
+ * shares no code with the CUDA library.  Every function follows the paper's
+ * definitions in their order, with no blocking or fusion:
+ *
+ *   Def. "Epstein zeta function"      Z_{Lambda,nu}(x,k) = sum'_z e^{-2 pi i z.k} |z-x|^{-nu}
+ *   (cited, not printed) incomplete-gamma splitting of Z.  Written out here from
+ *       the Mellin integral |z|^{-nu} = pi^{nu/2}/Gamma(nu/2) int t^{nu/2-1} e^{-pi t |z|^2} dt
+ *       split at t = 1/lam^2 with Poisson summation on the lower part:
+ *       Z = P_nu [ sum_{z != x} Phi_{nu/2}(pi|z-x|^2/lam^2) e^{-2 pi i y.z}
+ *                + lam^d/V sum_{g in Lambda*} Phi_{(d-nu)/2}(pi lam^2 |g+y|^2) e^{-2 pi i x.(g+y)}
+ *                - [x in Lambda] (2/nu) e^{-2 pi i x.y} ],   P_nu = pi^{nu/2}/(Gamma(nu/2) lam^nu),
+ *       Phi_a(t) = t^{-a} Gamma(a,t).
+ *   Sec. 3, singular split  Z = Z^reg + s_hat_nu / |det A| (power or log form).
+ *   Thm "Epstein representation" + Cor. "Duffy transformation": sectors (j, p),
+ *       k~ = u sigma^j(p v, 1), k = A^{-T} k~, weight 2 u^{d-1} w_u prod w_v.
+ *   Sec. 3, meromorphic continuation: eps-split, Taylor series of Z^reg of order
+ *       2 ell, closed-form Hadamard integrals of u^{mu-1} log(pi u^2 w^2)^m.
+ *   Prop. (ATM) recombination is done by the caller.
+ *
+ * Readings where the paper is silent (splitting parameter, cutoffs, fixed u rule,
+ * truncation of the near-part product) are listed in the design notes; the parity
+ * of this oracle with the paper is pinned by tests/test_oracle_*.py.
+ */
+#include "ezoracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.141592653589793238462643383279502884
+#define OR_EULER_GAMMA 0.577215664901532860606512090082402431
+
+/* ------------------------------------------------------------------------- */
+/* Small dense linear algebra for d <= 3                                       */
+/* ------------------------------------------------------------------------- */
+static double or_det(int d, const double* A) {
+  if (d == 1) return A[0];
+  if (d == 2) return A[0] * A[3] - A[1] * A[2];
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse via the adjugate */
+static int or_inverse(int d, const double* A, double* Ai) {
+  double det = or_det(d, A);
+  if (det == 0.0 || !isfinite(det)) return 1;
+  if (d == 1) {
+    Ai[0] = 1.0 / A[0];
+  } else if (d == 2) {
+    Ai[0] = A[3] / det;
+    Ai[1] = -A[1] / det;
+    Ai[2] = -A[2] / det;
+    Ai[3] = A[0] / det;
+  } else {
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  }
+  return 0;
+}
+
+static void or_transpose(int d, const double* A, double* At) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) At[i * d + j] = A[j * d + i];
+}
+
+static void or_matvec(int d, const double* M, const double* x, double* y) {
+  for (int i = 0; i < d; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += M[i * d + j] * x[j];
+    y[i] = s;
+  }
+}
+
+static double or_dot(int d, const double* a, const double* b) {
+  double s = 0.0;
+  for (int i = 0; i < d; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* compensated (Kahan-Babuska) accumulator */
+typedef struct {
+  double s, c;
+} or_acc;
+static void or_acc_add(or_acc* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x))
+    a->c += (a->s - t) + x;
+  else
+    a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double or_acc_get(const or_acc* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------- */
+/* Upper incomplete gamma: Phi_a(t) = t^{-a} Gamma(a,t) = int_1^inf s^{a-1} e^{-ts} ds */
+/* ------------------------------------------------------------------------- */
+
+/* E_1(t): power series (Abramowitz & Stegun 5.1.11) for t <= 1, continued
+ * fraction E_1(t) = e^{-t} / (t+1 - 1/(t+3 - 4/(t+5 - ...))) (A&S 5.1.22,
+ * evaluated by the modified Lentz method) for t > 1. */
+double or_expint_e1(double t) {
+  if (!(t > 0.0)) return t == 0.0 ? INFINITY : NAN;
+  if (t <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 200; ++k) {
+      term *= -t / k; /* (-t)^k / k! */
+      double add = term / k;
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -OR_EULER_GAMMA - log(t) - sum;
+  }
+  const double tiny = 1e-300;
+  double b = t + 1.0;
+  double c = 1.0 / tiny;
+  double dd = 1.0 / b;
+  double h = dd;
+  for (int i = 1; i < 10000; ++i) {
+    double an = -(double)i * (double)i;
+    b += 2.0;
+    dd = 1.0 / (an * dd + b);
+    c = b + an / c;
+    double del = c * dd;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-17) break;
+  }
+  return h * exp(-t);
+}
+
+/* Phi_a(t) = e^{-t} / (t+1-a - 1(1-a)/(t+3-a - 2(2-a)/(t+5-a - ...))): the even part of
+ * Legendre's continued fraction for Gamma(a,t) (DLMF 8.9.2), modified Lentz method. */
+static double or_phi_cf(double a, double t) {
+  const double tiny = 1e-300;
+  double b = t + 1.0 - a;
+  double c = 1.0 / tiny;
+  double dd = 1.0 / b;
+  double h = dd;
+  for (int i = 1; i < 100000; ++i) {
+    double an = -(double)i * ((double)i - a);
+    b += 2.0;
+    dd = an * dd + b;
+    if (fabs(dd) < tiny) dd = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    dd = 1.0 / dd;
+    double del = dd * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-17) break;
+  }
+  return exp(-t) * h;
+}
+
+double or_phi(double a, double t) {
+  double tw = 2.0 * a;
+  long twi = lround(tw);
+  if (fabs(tw - (double)twi) > 1e-12) return NAN; /* only a in Z/2 */
+  if (t < 0.0 || isnan(t)) return NAN;
+  if (t == 0.0) return a < 0.0 ? -1.0 / a : INFINITY;
+  /* negative orders at larger t: the downward recurrence below would lose digits */
+  if (a <= 0.0 && t > 1.0) return or_phi_cf(a, t);
+  double et = exp(-t);
+  if (twi % 2 == 0) {
+    long n = twi / 2;
+    if (n >= 1) {
+      /* Gamma(n,t) = (n-1)! e^{-t} sum_{k<n} t^k/k! */
+      double s = 0.0, term = 1.0;
+      for (long k = 0; k < n; ++k) {
+        s += term;
+        term *= t / (double)(k + 1);
+      }
+      return tgamma((double)n) * et * s * pow(t, -(double)n);
+    }
+    /* Phi_0 = E_1, then Phi_{c-1} = (t Phi_c - e^{-t}) / (c-1) */
+    double phi = or_expint_e1(t);
+    for (long c = 0; c > n; --c) phi = (t * phi - et) / (double)(c - 1);
+    return phi;
+  }
+  /* half-integers from Phi_{1/2}(t) = sqrt(pi/t) erfc(sqrt t) */
+  double phi = sqrt(OR_PI / t) * erfc(sqrt(t));
+  double cur = 0.5;
+  while (cur < a - 0.25) { /* Phi_{c+1} = (c Phi_c + e^{-t}) / t */
+    phi = (cur * phi + et) / t;
+    cur += 1.0;
+  }
+  while (cur > a + 0.25) { /* Phi_{c-1} = (t Phi_c - e^{-t}) / (c-1) */
+    phi = (t * phi - et) / (cur - 1.0);
+    cur -= 1.0;
+  }
+  return phi;
+}
+
+/* is a a non-positive integer (log case of the regularisation)? returns m >= 0 or -1 */
+static int or_log_order(double a) {
+  double r = round(a);
+  if (fabs(a - r) < 1e-12 && r <= 0.0) return (int)(-r);
+  return -1;
+}
+
+/* Coefficients r_n (n = 0..nmax) of the entire function Phi^reg_a(t) = sum_n r_n t^n,
+ * i.e. Phi_a(t) minus its singular part.  Non-log (a not in -N0):
+ *   Phi_a(t) = Gamma(a) t^{-a} - sum_n (-1)^n t^n / (n! (a+n)).
+ * Log case a = -m:
+ *   Phi_{-m}(t) = ((-1)^m/m!) (psi(m+1) - log t) t^m - sum_{n != m} (-1)^n t^n/(n!(n-m));
+ * the removed singular part is ((-1)^{m+1}/m!) t^m log(t/lam^2), matching s_hat of
+ * Sec. 3 which uses log(pi |k|^2) = log(t/lam^2). */
+static void or_phi_reg_series(double a, double lam, int nmax, double* r) {
+  int m = or_log_order(a);
+  double fact = 1.0;
+  for (int n = 0; n <= nmax; ++n) {
+    if (n > 0) fact *= (double)n;
+    double sgn = (n % 2 == 0) ? 1.0 : -1.0;
+    if (m >= 0 && n == m) {
+      double psi = -OR_EULER_GAMMA;
+      for (int k = 1; k <= m; ++k) psi += 1.0 / k;
+      r[n] = sgn / fact * (psi - 2.0 * log(lam));
+    } else {
+      r[n] = -sgn / (fact * (a + (double)n));
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lattice points                                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int n, cap;
+  int* idx;   /* integer coordinates, d per point */
+  double* p;  /* M * idx, d per point */
+} or_points;
+
+static void or_points_push(or_points* P, int d, const int* id, const double* x) {
+  if (P->n == P->cap) {
+    P->cap = P->cap ? 2 * P->cap : 256;
+    P->idx = (int*)realloc(P->idx, sizeof(int) * 3 * P->cap);
+    P->p = (double*)realloc(P->p, sizeof(double) * 3 * P->cap);
+  }
+  for (int i = 0; i < d; ++i) {
+    P->idx[P->n * 3 + i] = id[i];
+    P->p[P->n * 3 + i] = x[i];
+  }
+  P->n++;
+}
+static void or_points_free(or_points* P) {
+  free(P->idx);
+  free(P->p);
+  memset(P, 0, sizeof(*P));
+}
+
+/* All integer h with |M h - c| <= R; Minv = M^{-1} bounds the box. */
+static void or_enumerate(int d, const double* M, const double* Minv, const double* c, double R,
+                         or_points* out) {
+  double mc[3] = {0, 0, 0};
+  or_matvec(d, Minv, c, mc);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int i = 0; i < d; ++i) {
+    double rn = 0.0;
+    for (int j = 0; j < d; ++j) rn += Minv[i * d + j] * Minv[i * d + j];
+    double ext = R * sqrt(rn) + 1e-9;
+    lo[i] = (int)floor(mc[i] - ext);
+    hi[i] = (int)ceil(mc[i] + ext);
+  }
+  int id[3] = {0, 0, 0};
+  for (id[0] = lo[0]; id[0] <= hi[0]; ++id[0])
+    for (id[1] = (d > 1 ? lo[1] : 0); id[1] <= (d > 1 ? hi[1] : 0); ++id[1])
+      for (id[2] = (d > 2 ? lo[2] : 0); id[2] <= (d > 2 ? hi[2] : 0); ++id[2]) {
+        double fid[3] = {id[0], id[1], id[2]}, x[3];
+        or_matvec(d, M, fid, x);
+        double r2 = 0.0;
+        for (int i = 0; i < d; ++i) r2 += (x[i] - c[i]) * (x[i] - c[i]);
+        if (r2 <= R * R) or_points_push(out, d, id, x);
+      }
+}
+
+static double or_prefactor(double nu, double lam) {
+  /* P_nu = pi^{nu/2} / (Gamma(nu/2) lam^nu) */
+  return pow(OR_PI, 0.5 * nu) / (tgamma(0.5 * nu) * pow(lam, nu));
+}
+
+static int or_gamma_pole(double x) { return x <= 0.0 && fabs(x - round(x)) < 1e-12; }
+
+/* ------------------------------------------------------------------------- */
+/* Epstein zeta, general (x, y)                                                */
+/* ------------------------------------------------------------------------- */
+int or_epstein_zeta(int d, const double* A, double nu, const double* x, const double* y,
+                    double lam, double r_real, double r_recip, double* re, double* im) {
+  if (d < 1 || d > 3) return 1;
+  if (or_gamma_pole(0.5 * nu)) return 2;
+  double Ai[9], AiT[9], At[9];
+  if (or_inverse(d, A, Ai)) return 1;
+  or_transpose(d, Ai, AiT);
+  or_transpose(d, A, At);
+  double V = fabs(or_det(d, A));
+  double P = or_prefactor(nu, lam);
+  double a_real = 0.5 * nu, a_rec = 0.5 * (d - nu);
+
+  /* x in Lambda ? */
+  double mx[3];
+  or_matvec(d, Ai, x, mx);
+  int x_in = 1, mxr[3] = {0, 0, 0};
+  for (int i = 0; i < d; ++i) {
+    mxr[i] = (int)lround(mx[i]);
+    if (fabs(mx[i] - mxr[i]) > 1e-12) x_in = 0;
+  }
+
+  or_acc sre = {0, 0}, sim = {0, 0};
+  /* real space: z in Lambda, 0 < |z - x| <= r_real */
+  or_points pts = {0};
+  or_enumerate(d, A, Ai, x, r_real, &pts);
+  for (int e = 0; e < pts.n; ++e) {
+    const int* m = pts.idx + 3 * e;
+    const double* z = pts.p + 3 * e;
+    if (x_in) {
+      int same = 1;
+      for (int i = 0; i < d; ++i) same &= (m[i] == mxr[i]);
+      if (same) continue;
+    }
+    double r2 = 0.0;
+    for (int i = 0; i < d; ++i) r2 += (z[i] - x[i]) * (z[i] - x[i]);
+    double phi = or_phi(a_real, OR_PI * r2 / (lam * lam));
+    double arg = 2.0 * OR_PI * or_dot(d, y, z);
+    or_acc_add(&sre, phi * cos(arg));
+    or_acc_add(&sim, -phi * sin(arg));
+  }
+  or_points_free(&pts);
+
+  /* reciprocal space: g in Lambda*, |g + y| <= r_recip */
+  or_acc rre = {0, 0}, rim = {0, 0};
+  double my[3];
+  for (int i = 0; i < d; ++i) my[i] = -y[i];
+  or_enumerate(d, AiT, At, my, r_recip, &pts);
+  for (int e = 0; e < pts.n; ++e) {
+    const double* g = pts.p + 3 * e;
+    double q[3], q2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      q[i] = g[i] + y[i];
+      q2 += q[i] * q[i];
+    }
+    double phi;
+    if (q2 == 0.0) {
+      if (a_rec >= 0.0) {
+        or_points_free(&pts);
+        return 2;
+      }
+      phi = -1.0 / a_rec;
+    } else {
+      phi = or_phi(a_rec, OR_PI * lam * lam * q2);
+    }
+    double arg = 2.0 * OR_PI * or_dot(d, x, q);
+    or_acc_add(&rre, phi * cos(arg));
+    or_acc_add(&rim, -phi * sin(arg));
+  }
+  or_points_free(&pts);
+
+  double c = pow(lam, (double)d) / V;
+  double tre = or_acc_get(&sre) + c * or_acc_get(&rre);
+  double tim = or_acc_get(&sim) + c * or_acc_get(&rim);
+  if (x_in) {
+    double arg = 2.0 * OR_PI * or_dot(d, x, y);
+    tre -= (2.0 / nu) * cos(arg);
+    tim += (2.0 / nu) * sin(arg);
+  }
+  *re = P * tre;
+  *im = P * tim;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Singular part (Sec. 3)                                                      */
+/* ------------------------------------------------------------------------- */
+/* coefficient sigma_nu with s_hat_nu(k) = sigma_nu |k|^{nu-d} [log(pi k^2)]^{is_log} */
+static double or_sigma(int d, double nu, int* is_log) {
+  double mm = 0.5 * (nu - d);
+  int m = -1;
+  if (fabs(mm - round(mm)) < 1e-12 && round(mm) >= 0.0) m = (int)round(mm);
+  if (m >= 0) {
+    *is_log = 1;
+    double mf = tgamma((double)m + 1.0);
+    double sgn = (m % 2 == 0) ? -1.0 : 1.0; /* (-1)^{m+1} */
+    return pow(OR_PI, 2.0 * m + 0.5 * d) / tgamma(m + 0.5 * d) * sgn / mf;
+  }
+  *is_log = 0;
+  return pow(OR_PI, nu - 0.5 * d) * tgamma(0.5 * (d - nu)) / tgamma(0.5 * nu);
+}
+
+double or_s_hat(int d, double nu, const double* k) {
+  int lg;
+  double sig = or_sigma(d, nu, &lg);
+  double k2 = 0.0;
+  for (int i = 0; i < d; ++i) k2 += k[i] * k[i];
+  double v = sig * pow(k2, 0.5 * (nu - d));
+  if (lg) v *= log(OR_PI * k2);
+  return v;
+}
+
+int or_epstein_zeta_reg(int d, const double* A, double nu, const double* k, double lam,
+                        double r_real, double r_recip, double* out) {
+  double x0[3] = {0, 0, 0}, re, im;
+  int rc = or_epstein_zeta(d, A, nu, x0, k, lam, r_real, r_recip, &re, &im);
+  if (rc) return rc;
+  *out = re - or_s_hat(d, nu, k) / fabs(or_det(d, A));
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Legendre and Hadamard integrals                                       */
+/* ------------------------------------------------------------------------- */
+/* Newton iteration on theta for P_n(cos theta) = 0; x = sin^2(theta/2) in [0,1],
+ * w = 2 / ((1 - z^2) P_n'(z)^2) / 2. */
+void or_gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double th = OR_PI * (i + 0.75) / (n + 0.5);
+    double p0 = 1.0, p1 = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double z = cos(th);
+      p0 = 1.0;
+      p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double s = sin(th);
+      double dth = -(double)n * (p0 - z * p1) / s; /* d/dtheta P_n(cos theta) */
+      double step = p1 / dth;
+      th -= step;
+      if (fabs(step) < 1e-15) { /* converged; the final evaluation below refines once more */
+        z = cos(th);
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        th -= p1 / (-(double)n * (p0 - z * p1) / sin(th));
+        break;
+      }
+    }
+    double z = cos(th), s = sin(th);
+    p0 = 1.0;
+    p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double q = (double)n * (p0 - z * p1); /* = s^2 P_n'(z) */
+    double sh = sin(0.5 * th);
+    x[i] = sh * sh;
+    w[i] = s * s / (q * q); /* (2 / (s^2 P'^2)) / 2 */
+  }
+}
+
+/* I_m(mu) = finite part of int_0^eps u^{mu-1} L(u)^m du, L(u) = log(pi u^2 w2):
+ * I_0 = eps^mu / mu, and integrating by parts
+ * I_m = eps^mu L(eps)^m / mu - (2m/mu) I_{m-1}   (Sec. 3, closed forms for m <= 3). */
+double or_hadamard(double mu, int m, double eps, double w2) {
+  double L = log(OR_PI * eps * eps * w2);
+  double em = pow(eps, mu);
+  double I = em / mu;
+  double Lp = 1.0;
+  for (int j = 1; j <= m; ++j) {
+    Lp *= L;
+    I = em * Lp / mu - (2.0 * j / mu) * I;
+  }
+  return I;
+}
+
+/* ------------------------------------------------------------------------- */
+/* n-body lattice sums                                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  const or_problem* P;
+  int d, nsect, nu_tot;
+  double Ai[9], AiT[9], At[9], V, vol_fac;
+  double pref[OR_MAXNU];
+  or_points real;   /* 0 < |z| <= r_real */
+  double* g;        /* real.n x n_distinct : Phi_{nu/2}(pi |z|^2 / lam^2) */
+  or_points rec;    /* |g| <= r_recip + max_BZ |k| */
+  double* u_nodes;
+  double* u_w;
+  double* v_nodes;
+  double* v_w;
+} or_ctx;
+
+int or_n_sectors(const or_problem* P) { return P->d * (1 << (P->d - 1)); }
+
+static int or_n_panels(double eps) {
+  int np = 0;
+  double b = eps;
+  while (b < 0.5) {
+    b = fmin(2.0 * b, 0.5);
+    np++;
+  }
+  return np;
+}
+
+int or_n_u_total(const or_problem* P) {
+  return P->u_rule == 2 ? P->n_u * or_n_panels(P->eps) : P->n_u;
+}
+
+int or_u_rule(const or_problem* P, double* u, double* w) {
+  double* x = (double*)malloc(sizeof(double) * P->n_u);
+  double* wx = (double*)malloc(sizeof(double) * P->n_u);
+  or_gauss_legendre01(P->n_u, x, wx);
+  if (P->u_rule == 1) {
+    for (int i = 0; i < P->n_u; ++i) {
+      u[i] = 0.5 * x[i];
+      w[i] = 0.5 * wx[i];
+    }
+  } else {
+    double a = P->eps;
+    int o = 0;
+    while (a < 0.5) {
+      double b = fmin(2.0 * a, 0.5);
+      for (int i = 0; i < P->n_u; ++i) {
+        u[o] = a + (b - a) * x[i];
+        w[o] = (b - a) * wx[i];
+        o++;
+      }
+      a = b;
+    }
+  }
+  free(x);
+  free(wx);
+  return 0;
+}
+
+static void or_ctx_free(or_ctx* c) {
+  or_points_free(&c->real);
+  or_points_free(&c->rec);
+  free(c->g);
+  free(c->u_nodes);
+  free(c->u_w);
+  free(c->v_nodes);
+  free(c->v_w);
+}
+
+static int or_ctx_init(or_ctx* c, const or_problem* P) {
+  memset(c, 0, sizeof(*c));
+  c->P = P;
+  int d = P->d;
+  c->d = d;
+  if (d < 1 || d > 3 || P->n_distinct < 1 || P->n_distinct > OR_MAXNU || P->n_prod < 1 ||
+      P->n_prod > OR_MAXPROD || P->n_u < 1 || (d > 1 && P->n_v < 1))
+    return 1;
+  if (or_inverse(d, P->A, c->Ai)) return 1;
+  or_transpose(d, c->Ai, c->AiT);
+  or_transpose(d, P->A, c->At);
+  c->V = fabs(or_det(d, P->A));
+  c->vol_fac = pow(P->lam, (double)d) / c->V;
+  c->nsect = or_n_sectors(P);
+  for (int j = 0; j < P->n_distinct; ++j) {
+    if (or_gamma_pole(0.5 * P->nu[j])) return 2;
+    c->pref[j] = or_prefactor(P->nu[j], P->lam);
+  }
+  double zero[3] = {0, 0, 0};
+  or_points all = {0};
+  or_enumerate(d, P->A, c->Ai, zero, P->r_real, &all);
+  for (int e = 0; e < all.n; ++e) {
+    int nz = 0;
+    for (int i = 0; i < d; ++i) nz |= all.idx[3 * e + i] != 0;
+    if (nz) or_points_push(&c->real, d, all.idx + 3 * e, all.p + 3 * e);
+  }
+  or_points_free(&all);
+  c->g = (double*)malloc(sizeof(double) * (c->real.n + 1) * P->n_distinct);
+  for (int e = 0; e < c->real.n; ++e) {
+    double r2 = 0.0;
+    for (int i = 0; i < d; ++i) r2 += c->real.p[3 * e + i] * c->real.p[3 * e + i];
+    for (int j = 0; j < P->n_distinct; ++j)
+      c->g[e * P->n_distinct + j] = or_phi(0.5 * P->nu[j], OR_PI * r2 / (P->lam * P->lam));
+  }
+  /* reciprocal points: cover every k = A^{-T} k~ with k~ in [-1/2,1/2]^d */
+  double kmax = 0.0;
+  for (int corner = 0; corner < (1 << d); ++corner) {
+    double kt[3], k[3];
+    for (int i = 0; i < d; ++i) kt[i] = (corner >> i & 1) ? 0.5 : -0.5;
+    or_matvec(d, c->AiT, kt, k);
+    kmax = fmax(kmax, sqrt(or_dot(d, k, k)));
+  }
+  or_enumerate(d, c->AiT, c->At, zero, P->r_recip + kmax, &c->rec);
+  int nu_t = or_n_u_total(P);
+  c->u_nodes = (double*)malloc(sizeof(double) * nu_t);
+  c->u_w = (double*)malloc(sizeof(double) * nu_t);
+  or_u_rule(P, c->u_nodes, c->u_w);
+  int nv = d > 1 ? P->n_v : 1;
+  c->v_nodes = (double*)malloc(sizeof(double) * nv);
+  c->v_w = (double*)malloc(sizeof(double) * nv);
+  if (d > 1)
+    or_gauss_legendre01(nv, c->v_nodes, c->v_w);
+  else {
+    c->v_nodes[0] = 0.0;
+    c->v_w[0] = 1.0;
+  }
+  return 0;
+}
+
+/* Z_{nu_j}(k) at x = 0, k = A^{-T} k~, by the splitting (real part only: the sum is
+ * symmetric under z -> -z, so the imaginary part vanishes). */
+static double or_zeta_at(const or_ctx* c, int j, const double* k, const double* kt) {
+  const or_problem* P = c->P;
+  int d = c->d;
+  double nu = P->nu[j];
+  or_acc sr = {0, 0}, sk = {0, 0};
+  for (int e = 0; e < c->real.n; ++e) {
+    double mk = 0.0;
+    for (int i = 0; i < d; ++i) mk += c->real.idx[3 * e + i] * kt[i];
+    or_acc_add(&sr, c->g[e * P->n_distinct + j] * cos(2.0 * OR_PI * mk));
+  }
+  double a = 0.5 * (d - nu);
+  double R2 = P->r_recip * P->r_recip;
+  for (int e = 0; e < c->rec.n; ++e) {
+    double q2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double q = c->rec.p[3 * e + i] + k[i];
+      q2 += q * q;
+    }
+    if (q2 > R2) continue;
+    double phi;
+    if (q2 == 0.0) {
+      if (a >= 0.0) return NAN;
+      phi = -1.0 / a;
+    } else {
+      phi = or_phi(a, OR_PI * P->lam * P->lam * q2);
+    }
+    or_acc_add(&sk, phi);
+  }
+  return c->pref[j] * (or_acc_get(&sr) + c->vol_fac * or_acc_get(&sk) - 2.0 / nu);
+}
+
+/* direction of sector s at v: y = sigma^j (p v, 1), sigma^j(y)[i] = y[(i - j) mod d] */
+static void or_sector_dir(int d, int s, const double* v, double* ktdir) {
+  int half = 1 << (d - 1);
+  int j = s / half, pbits = s % half;
+  double y[3];
+  for (int i = 0; i < d - 1; ++i) y[i] = ((pbits >> i) & 1 ? -1.0 : 1.0) * v[i];
+  y[d - 1] = 1.0;
+  for (int i = 0; i < d; ++i) ktdir[i] = y[((i - j) % d + d) % d];
+}
+
+static void or_products(const or_problem* P, const double* Z, double* f) {
+  for (int p = 0; p < P->n_prod; ++p) {
+    double v = 1.0;
+    for (int j = 0; j < P->n_distinct; ++j)
+      for (int e = 0; e < P->expo[p][j]; ++e) v *= Z[j];
+    f[p] = v;
+  }
+}
+
+int or_nbody_node(const or_problem* P, int sector, double u, const double* v, double* f,
+                  double* kt_out) {
+  or_ctx c;
+  int rc = or_ctx_init(&c, P);
+  if (rc) {
+    or_ctx_free(&c);
+    return rc;
+  }
+  double dir[3], kt[3], k[3], Z[OR_MAXNU];
+  or_sector_dir(P->d, sector, v, dir);
+  for (int i = 0; i < P->d; ++i) kt[i] = u * dir[i];
+  or_matvec(P->d, c.AiT, kt, k);
+  for (int j = 0; j < P->n_distinct; ++j) Z[j] = or_zeta_at(&c, j, k, kt);
+  or_products(P, Z, f);
+  if (kt_out)
+    for (int i = 0; i < P->d; ++i) kt_out[i] = kt[i];
+  or_ctx_free(&c);
+  return 0;
+}
+
+/* iterate v multi-index (d-1 axes) */
+static int or_n_vnodes(const or_ctx* c) {
+  int n = 1;
+  for (int i = 0; i < c->d - 1; ++i) n *= c->P->n_v;
+  return n;
+}
+static double or_vnode(const or_ctx* c, int iv, double* v) {
+  double w = 1.0;
+  for (int i = 0; i < c->d - 1; ++i) {
+    int ii = iv % c->P->n_v;
+    iv /= c->P->n_v;
+    v[i] = c->v_nodes[ii];
+    w *= c->v_w[ii];
+  }
+  return w;
+}
+
+static void or_far_line(const or_ctx* c, int s, int iu, double* out) {
+  const or_problem* P = c->P;
+  int d = c->d;
+  double u = c->u_nodes[iu], wu = c->u_w[iu];
+  double wpow = 2.0 * wu * pow(u, (double)(d - 1));
+  or_acc acc[OR_MAXPROD];
+  memset(acc, 0, sizeof(acc));
+  int nv = or_n_vnodes(c);
+  for (int iv = 0; iv < nv; ++iv) {
+    double v[3] = {0, 0, 0};
+    double wv = or_vnode(c, iv, v);
+    double dir[3], kt[3], k[3], Z[OR_MAXNU], f[OR_MAXPROD];
+    or_sector_dir(d, s, v, dir);
+    for (int i = 0; i < d; ++i) kt[i] = u * dir[i];
+    or_matvec(d, c->AiT, kt, k);
+    for (int j = 0; j < P->n_distinct; ++j) Z[j] = or_zeta_at(c, j, k, kt);
+    or_products(P, Z, f);
+    for (int p = 0; p < P->n_prod; ++p) or_acc_add(&acc[p], wpow * wv * f[p]);
+  }
+  for (int p = 0; p < P->n_prod; ++p) out[p] = or_acc_get(&acc[p]);
+}
+
+/* truncated power series in u: c[0..D] */
+static void or_series_mul(const double* a, const double* b, double* out, int D) {
+  double tmp[2 * OR_MAXELL + 2];
+  for (int i = 0; i <= D; ++i) {
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) s += a[j] * b[i - j];
+    tmp[i] = s;
+  }
+  memcpy(out, tmp, sizeof(double) * (D + 1));
+}
+
+/* Taylor coefficients C_{k,nu_j}(w) = (w.grad)^{2k} Z^reg(0) / (2k)!, k = 0..ell, by
+ * Taylor-mode expansion in u of every term of Z^reg(u w):
+ *   real space   g(m) cos(2 pi u z.w)            -> (-1)^k (2 pi z.w)^{2k} / (2k)!
+ *   h != 0       Phi_a(t0 + delta(u)),  delta = c (2 u G.w + u^2 |w|^2),
+ *                Phi_a(t0 + delta) = sum_n (-1)^n Phi_{a+n}(t0) delta^n / n!
+ *                (from Phi_a' = -Phi_{a+1})
+ *   h = 0        Phi^reg_a(c |w|^2 u^2) from its entire series. */
+static void or_taylor(const or_ctx* c, int j, const double* w, double* C) {
+  const or_problem* P = c->P;
+  int d = c->d, ell = P->ell, D = 2 * ell;
+  double nu = P->nu[j];
+  double a = 0.5 * (d - nu);
+  double cc = OR_PI * P->lam * P->lam;
+  double w2 = or_dot(d, w, w);
+  or_acc real[OR_MAXELL + 1], rec[OR_MAXELL + 1];
+  memset(real, 0, sizeof(real));
+  memset(rec, 0, sizeof(rec));
+  for (int e = 0; e < c->real.n; ++e) {
+    double zw = or_dot(d, c->real.p + 3 * e, w);
+    double g = c->g[e * P->n_distinct + j];
+    double x = 2.0 * OR_PI * zw, xp = 1.0, fact = 1.0;
+    for (int k = 0; k <= ell; ++k) {
+      if (k > 0) {
+        xp *= x * x;
+        fact *= (2.0 * k - 1.0) * (2.0 * k);
+      }
+      or_acc_add(&real[k], ((k % 2) ? -1.0 : 1.0) * g * xp / fact);
+    }
+  }
+  double R2 = P->r_recip * P->r_recip;
+  for (int e = 0; e < c->rec.n; ++e) {
+    const double* G = c->rec.p + 3 * e;
+    double G2 = or_dot(d, G, G);
+    if (G2 == 0.0 || G2 > R2) continue;
+    double t0 = cc * G2;
+    double delta[2 * OR_MAXELL + 2] = {0};
+    delta[1] = 2.0 * cc * or_dot(d, G, w);
+    if (D >= 2) delta[2] = cc * w2;
+    double S[2 * OR_MAXELL + 2] = {0}, dp[2 * OR_MAXELL + 2] = {0};
+    dp[0] = 1.0; /* delta^0 */
+    double fact = 1.0;
+    for (int n = 0; n <= D; ++n) {
+      if (n > 0) {
+        or_series_mul(dp, delta, dp, D);
+        fact *= n;
+      }
+      double coef = ((n % 2) ? -1.0 : 1.0) * or_phi(a + n, t0) / fact;
+      for (int i = 0; i <= D; ++i) S[i] += coef * dp[i];
+    }
+    for (int k = 0; k <= ell; ++k) or_acc_add(&rec[k], S[2 * k]);
+  }
+  double r[OR_MAXELL + 1];
+  or_phi_reg_series(a, P->lam, ell, r);
+  double bp = 1.0;
+  for (int k = 0; k <= ell; ++k) {
+    or_acc_add(&rec[k], r[k] * bp);
+    bp *= cc * w2;
+  }
+  for (int k = 0; k <= ell; ++k) {
+    double v = or_acc_get(&real[k]) + c->vol_fac * or_acc_get(&rec[k]);
+    if (k == 0) v -= 2.0 / nu;
+    C[k] = c->pref[j] * v;
+  }
+}
+
+int or_reg_taylor(const or_problem* P, int j, const double* w, double* C) {
+  or_ctx c;
+  int rc = or_ctx_init(&c, P);
+  if (!rc) or_taylor(&c, j, w, C);
+  or_ctx_free(&c);
+  return rc;
+}
+
+/* Near part of one ray for product p: Hadamard integral over (0, eps) of
+ * u^{d-1} prod_i (R_i(u) + S_i(u)), R_i = sum_{k<=ell} C_{k,i} u^{2k}, S_i = s_hat_i(u w)/V,
+ * expanded over subsets T of singular factors:
+ *   sum_T [prod_{i in T} sigma_i |w|^{nu_i-d} / V] sum_{k<=ell} G_{T,k} I_{m_T}(mu_T + 2k),
+ * mu_T = d + sum_{i in T}(nu_i - d), m_T = #log factors in T, G_T = prod_{i not in T} R_i
+ * kept in full (each factor is truncated at order 2 ell, their product is not truncated
+ * again; this is the reading under which Table "taylor" of Sec. 4.1 is reproduced). */
+static double or_near_ray(const or_ctx* c, int p, const double* w, double Ctab[][OR_MAXELL + 1]) {
+  const or_problem* P = c->P;
+  int d = c->d, ell = P->ell;
+  int fac[64], nf = 0;
+  for (int j = 0; j < P->n_distinct; ++j)
+    for (int e = 0; e < P->expo[p][j]; ++e) fac[nf++] = j;
+  if (nf > 20) return NAN;
+  int K = ell * nf; /* full product of the order-2ell series */
+  double w2 = or_dot(d, w, w);
+  double wn = sqrt(w2);
+  or_acc acc = {0, 0};
+  for (long T = 0; T < (1L << nf); ++T) {
+    double coef = 1.0, mu = d;
+    int mlog = 0;
+    double G[8 * OR_MAXELL + 1] = {0};
+    G[0] = 1.0;
+    for (int f = 0; f < nf; ++f) {
+      int j = fac[f];
+      double nu = P->nu[j];
+      if (T >> f & 1) {
+        int lg;
+        double sig = or_sigma(d, nu, &lg);
+        coef *= sig * pow(wn, nu - d) / c->V;
+        mu += nu - d;
+        mlog += lg;
+      } else {
+        double tmp[8 * OR_MAXELL + 1];
+        for (int i = 0; i <= K; ++i) {
+          double s = 0.0;
+          for (int q = 0; q <= i; ++q) if (i - q <= ell) s += G[q] * Ctab[j][i - q];
+          tmp[i] = s;
+        }
+        memcpy(G, tmp, sizeof(tmp));
+      }
+    }
+    for (int k = 0; k <= K; ++k)
+      if (G[k] != 0.0) or_acc_add(&acc, coef * G[k] * or_hadamard(mu + 2.0 * k, mlog, P->eps, w2));
+  }
+  return or_acc_get(&acc);
+}
+
+static void or_near_line(const or_ctx* c, int s, double* out) {
+  const or_problem* P = c->P;
+  int d = c->d;
+  or_acc acc[OR_MAXPROD];
+  memset(acc, 0, sizeof(acc));
+  int nv = or_n_vnodes(c);
+  double Ctab[OR_MAXNU][OR_MAXELL + 1];
+  for (int iv = 0; iv < nv; ++iv) {
+    double v[3] = {0, 0, 0};
+    double wv = or_vnode(c, iv, v);
+    double dir[3], w[3];
+    or_sector_dir(d, s, v, dir);
+    or_matvec(d, c->AiT, dir, w);
+    for (int j = 0; j < P->n_distinct; ++j) or_taylor(c, j, w, Ctab[j]);
+    for (int p = 0; p < P->n_prod; ++p) or_acc_add(&acc[p], 2.0 * wv * or_near_ray(c, p, w, Ctab));
+  }
+  for (int p = 0; p < P->n_prod; ++p) out[p] = or_acc_get(&acc[p]);
+}
+
+int or_nbody_line(const or_problem* P, int sector, int iu, double* out) {
+  or_ctx c;
+  int rc = or_ctx_init(&c, P);
+  if (rc) {
+    or_ctx_free(&c);
+    return rc;
+  }
+  if (sector < 0 || sector >= c.nsect || iu >= or_n_u_total(P)) rc = 1;
+  else if (iu >= 0) or_far_line(&c, sector, iu, out);
+  else if (P->u_rule == 2) or_near_line(&c, sector, out);
+  else
+    for (int p = 0; p < P->n_prod; ++p) out[p] = 0.0;
+  or_ctx_free(&c);
+  return rc;
+}
+
+int or_nbody(const or_problem* P, int n_threads, double* out, double* far_lines, double* near_lines) {
+  or_ctx c;
+  int rc = or_ctx_init(&c, P);
+  if (rc) {
+    or_ctx_free(&c);
+    return rc;
+  }
+  int nu_t = or_n_u_total(P), ns = c.nsect, np = P->n_prod;
+  int nfar = ns * nu_t;
+  int nlines = nfar + (P->u_rule == 2 ? ns : 0);
+  double* lines = (double*)calloc((size_t)nlines * np, sizeof(double));
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+  for (int L = 0; L < nlines; ++L) {
+    if (L < nfar)
+      or_far_line(&c, L / nu_t, L % nu_t, lines + (size_t)L * np);
+    else
+      or_near_line(&c, L - nfar, lines + (size_t)L * np);
+  }
+  for (int p = 0; p < np; ++p) {
+    or_acc acc = {0, 0};
+    for (int L = 0; L < nlines; ++L) or_acc_add(&acc, lines[(size_t)L * np + p]);
+    out[p] = or_acc_get(&acc);
+  }
+  if (far_lines) memcpy(far_lines, lines, sizeof(double) * (size_t)nfar * np);
+  if (near_lines && P->u_rule == 2) memcpy(near_lines, lines + (size_t)nfar * np, sizeof(double) * ns * np);
+  free(lines);
+  or_ctx_free(&c);
+  return 0;
+}
