@@ -419,50 +419,54 @@ int or_epstein_zeta_reg(int d, const double* A, double nu, const double* k, doub
 /* ------------------------------------------------------------------------- */
 /* Gauss-Legendre and Hadamard integrals                                       */
 /* ------------------------------------------------------------------------- */
-/* Newton iteration on theta for P_n(cos theta) = 0; x = sin^2(theta/2) in [0,1],
- * w = 2 / ((1 - z^2) P_n'(z)^2) / 2. */
+/* P_n(z) and D_n = P_n(z) - P_{n-1}(z) at z = 1 - delta, from the Legendre recurrence
+ * rewritten for differences: D_{k+1} = (k D_k - (2k+1) delta P_k) / (k+1), P_{k+1} = P_k + D_{k+1}.
+ * It never forms z = 1 - delta, so nodes close to z = 1 keep their relative accuracy. */
+static void or_legendre_delta(int n, double delta, double* pn, double* dn) {
+  double p = 1.0 - delta, dd = -delta; /* P_1, D_1 */
+  if (n == 0) {
+    *pn = 1.0;
+    *dn = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    double nd = ((double)k * dd - (2.0 * k + 1.0) * delta * p) / (k + 1.0);
+    p += nd;
+    dd = nd;
+  }
+  *pn = p;
+  *dn = dd;
+}
+
+/* Gauss-Legendre nodes on [0,1], ascending: Newton's method on f(theta) = P_n(cos theta),
+ * f'(theta) = -n (P_{n-1} - z P_n) / sin(theta) = -n (delta P_n - D_n) / sin(theta), with
+ * delta = 1 - cos(theta) = 2 sin^2(theta/2).  Nodes x = sin^2(theta/2) = delta/2 and weights
+ * sin^2(theta) / (n (P_{n-1} - z P_n))^2 (the [-1,1] weight halved) for theta <= pi/2; the
+ * upper half by the symmetry x -> 1 - x. */
 void or_gauss_legendre01(int n, double* x, double* w) {
-  for (int i = 0; i < n; ++i) {
+  int half = (n + 1) / 2;
+  for (int i = 0; i < half; ++i) {
     double th = OR_PI * (i + 0.75) / (n + 0.5);
-    double p0 = 1.0, p1 = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double z = cos(th);
-      p0 = 1.0;
-      p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      double s = sin(th);
-      double dth = -(double)n * (p0 - z * p1) / s; /* d/dtheta P_n(cos theta) */
-      double step = p1 / dth;
+    if (2 * i + 1 == n) th = 0.5 * OR_PI; /* middle root of odd n: z = 0 */
+    double pn, dn;
+    for (int it = 0; it < 100 && 2 * i + 1 != n; ++it) {
+      double sh = sin(0.5 * th);
+      double delta = 2.0 * sh * sh;
+      or_legendre_delta(n, delta, &pn, &dn);
+      double fp = -(double)n * (delta * pn - dn) / sin(th);
+      double step = pn / fp;
       th -= step;
-      if (fabs(step) < 1e-15) { /* converged; the final evaluation below refines once more */
-        z = cos(th);
-        p0 = 1.0;
-        p1 = z;
-        for (int k = 2; k <= n; ++k) {
-          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-          p0 = p1;
-          p1 = p2;
-        }
-        th -= p1 / (-(double)n * (p0 - z * p1) / sin(th));
-        break;
-      }
+      if (fabs(step) < 1e-16 * th) break;
     }
-    double z = cos(th), s = sin(th);
-    p0 = 1.0;
-    p1 = z;
-    for (int k = 2; k <= n; ++k) {
-      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-      p0 = p1;
-      p1 = p2;
-    }
-    double q = (double)n * (p0 - z * p1); /* = s^2 P_n'(z) */
-    double sh = sin(0.5 * th);
+    double sh = sin(0.5 * th), ch = cos(0.5 * th);
+    double delta = 2.0 * sh * sh;
+    or_legendre_delta(n, delta, &pn, &dn);
+    double q = (double)n * (delta * pn - dn);
+    double s = sin(th);
     x[i] = sh * sh;
-    w[i] = s * s / (q * q); /* (2 / (s^2 P'^2)) / 2 */
+    w[i] = s * s / (q * q);
+    x[n - 1 - i] = ch * ch;
+    w[n - 1 - i] = w[i];
   }
 }
 

@@ -100,3 +100,28 @@ def test_hadamard_finite_part_for_negative_mu(oracle_mod, m):
     num = integrate.quad(f, delta, eps, epsabs=0, epsrel=1e-13, limit=500)[0]
     at_delta = oracle_mod.hadamard(mu, m, delta, w2)
     assert oracle_mod.hadamard(mu, m, eps, w2) == pytest.approx(num + at_delta, rel=1e-10)
+
+
+def test_gl_endpoint_nodes_relative_accuracy(oracle_mod):
+    # nodes next to the endpoints of a 4096-point rule (the config-1 u rule) must be
+    # accurate relative to their own size, not just to 1e-16 absolute
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    n = 4096
+    x, w = oracle_mod.gauss_legendre01(n)
+
+    def legendre(z):
+        p0, p1 = mp.mpf(1), z
+        for k in range(2, n + 1):
+            p0, p1 = p1, ((2 * k - 1) * z * p1 - (k - 1) * p0) / k
+        return p1, p0
+
+    for i in (0, 1, 5, n - 2, n - 1):
+        z = 1 - 2 * mp.mpf(x[i])
+        for _ in range(4):
+            pn, pm = legendre(z)
+            z -= pn / (n * (z * pn - pm) / (z * z - 1))
+        pn, pm = legendre(z)
+        dp = n * (z * pn - pm) / (z * z - 1)
+        assert x[i] == pytest.approx(float((1 - z) / 2), rel=4e-15)
+        assert w[i] == pytest.approx(float(1 / ((1 - z * z) * dp * dp)), rel=8e-15)
