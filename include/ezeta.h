@@ -1,0 +1,147 @@
+/*
+ * ezeta.h -- C ABI of the GB300 (sm_103a) Epstein zeta library.
+ *
+ * Implements the data-parallel path of "Epstein zeta method for many-body
+ * lattice sums" (Buchheit & Busse): the Epstein zeta function evaluated by its
+ * incomplete-gamma splitting, the n-body zeta function through the Epstein
+ * representation theorem with the Duffy transformation, the singular split of
+ * Sec. 3 with its eps-split/Taylor/Hadamard meromorphic continuation, and the
+ * ATM energy of the Proposition in Sec. 2.
+ *
+ * General rules for every entry point:
+ *  - Lattice matrices are row-major d x d (A[i*d+j] = component i of basis
+ *    vector j); the lattice is A Z^d and the reciprocal lattice A^{-T} Z^d
+ *    (Def. "Lattices").  1 <= d <= 3.
+ *  - Pointers marked "host or device" may point to host memory or to device
+ *    memory of the current CUDA device; the library detects which.  The caller
+ *    owns every input and output buffer.  Library handles own their own device
+ *    tables and scratch.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  When an output
+ *    is host memory the call synchronises that stream before returning; when all
+ *    outputs are device memory the call is asynchronous on `stream`.
+ *  - Return value: EZ_OK or one of the error codes below; ez_last_error()
+ *    returns a thread-local message for the last failure.  No C++ exception
+ *    crosses the ABI and no device code traps or asserts.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef EZETA_H
+#define EZETA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EZ_OK 0
+#define EZ_EINVAL 1        /* bad argument: d, singular A, n, node counts, NULL pointer */
+#define EZ_EDOMAIN 2       /* pole: Gamma(nu/2) pole (nu in -2N0), y in Lambda* with nu <= d,  \
+                              or a Hadamard exponent mu + 2k = 0 */
+#define EZ_EUNSUPPORTED 3  /* exponent not an integer (half-integer orders of Gamma(a,t) only) */
+#define EZ_ENOMEM 4        /* device allocation failed */
+#define EZ_ECUDA 5         /* CUDA runtime error */
+#define EZ_ETIMEOUT 6      /* a bounded device or host wait ran out */
+#define EZ_EBUSY 7         /* serving queue full */
+
+#define EZ_MAX_NU 8   /* distinct exponents per sum */
+#define EZ_MAX_PROD 4 /* products per sum (ATM uses 3) */
+
+typedef struct ez_lattice_s* ez_lattice;
+
+typedef enum {
+  EZ_FP64 = 0,  /* every operation in IEEE binary64 */
+  EZ_MIXED = 1  /* Gaussian-decaying tail terms in binary32 with compensated sums;
+                   leading terms, singular parts and reductions in binary64 */
+} ez_precision;
+
+/* Quadrature and truncation of one lattice sum.  Zero fields take the defaults. */
+typedef struct {
+  int n_u;        /* u_rule 1: Gauss-Legendre nodes on [0, 1/2];
+                     u_rule 2: nodes per graded panel [eps,2eps],[2eps,4eps],..,[.,1/2] */
+  int n_v;        /* Gauss-Legendre nodes per v axis, v in [0,1]^{d-1} (ignored for d=1) */
+  int u_rule;     /* 0: 2 if some nu_i < d or nu_i - d in 2N0, else 1 */
+  double eps;     /* split point of the near part (default 1e-2, Sec. 4.1) */
+  int ell;        /* Taylor order 2*ell of Z^reg in the near part (default 4, Sec. 4.1) */
+  double lambda;  /* splitting parameter of the incomplete-gamma form (default V^{1/d}) */
+  double r_real;  /* real-space cutoff |z| <= r_real (default 3.6 lambda) */
+  double r_recip; /* reciprocal cutoff |g + k| <= r_recip (default 3.6 / lambda) */
+  int prec;       /* ez_precision */
+  int dedupe;     /* 0: one Epstein zeta evaluation per factor; 1 (default 1 when
+                     negative is not given; see ez_quadrature_default) : one per distinct nu */
+} ez_quadrature;
+
+/* Fills *q with the defaults (n_u = 32, n_v = 32, u_rule 0, eps 1e-2, ell 4, lambda 0,
+ * cutoffs 0, EZ_FP64, dedupe 1). */
+void ez_quadrature_default(ez_quadrature* q);
+
+/* One lattice sum: product p = prod_j Z_{nu_j}(k)^{expo[p][j]} integrated over the
+ * Brillouin zone (Thm "Epstein representation"): value_p = V int_BZ product_p dk. */
+typedef struct {
+  int n_distinct;
+  double nu[EZ_MAX_NU];
+  int n_prod;
+  int expo[EZ_MAX_PROD][EZ_MAX_NU];
+} ez_sum_spec;
+
+/* --- lattices (Def. "Lattices") ------------------------------------------------ */
+/* Creates a lattice from A (host, d*d doubles).  EZ_EINVAL if d not in 1..3 or A
+ * is singular.  The handle owns device tables built for it. */
+int ez_lattice_create(int d, const double* A, ez_lattice* out);
+int ez_lattice_destroy(ez_lattice lat);
+
+/* --- Epstein zeta function (Def. "Epstein zeta function") -------------------- */
+/* Z_{Lambda,nu}(x, y_i) for i < m, by the incomplete-gamma splitting with
+ * parameter lambda = V^{1/d}: re[i] + i im[i] = sum'_{z} e^{-2 pi i z.y_i} |z - x|^{-nu},
+ * meromorphically continued in nu.  nu must be an integer (EZ_EUNSUPPORTED
+ * otherwise); nu in -2N0 is EZ_EDOMAIN.
+ *   x  : host, d doubles.
+ *   y  : host or device, m*d doubles (point i at y[i*d .. i*d+d-1]).
+ *   re, im : host or device, m doubles each (im may be NULL).
+ * y_i in Lambda* with nu <= d is a pole: re[i] = im[i] = NaN and the call returns
+ * EZ_EDOMAIN after finishing the other points.  m = 0 is a no-op. */
+int ez_epstein_zeta(ez_lattice lat, double nu, const double* x, const double* y, size_t m,
+                    double* re, double* im, int prec, void* stream);
+
+/* --- n-body zeta function (Def. "Many-body zeta function") ------------------- */
+/* zeta^(n)_Lambda(nu_1..nu_n) through the Epstein representation and the Duffy
+ * transformation (Cor. "Duffy transformation"), with the eps-split meromorphic
+ * continuation of Sec. 3 when u_rule is 2.
+ *   nu    : host, n integers stored as doubles (1 <= n <= 64).
+ *   value : host or device, 1 double. */
+int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q,
+                         double* value, void* stream);
+
+/* --- ATM cohesive energy (Prop. in Sec. 2) ------------------------------------ */
+/* E = zeta(3,3,3)/24 - 3 zeta(-1,5,5)/16 + 3 zeta(1,3,5)/8; the three zeta^(3) are
+ * computed in one pass over the nodes (distinct nu = -1, 1, 3, 5).
+ *   energy : host, 1 double; parts : host, 3 doubles (may be NULL). */
+int ez_atm_energy(ez_lattice lat, const ez_quadrature* q, double* energy, double* parts,
+                  void* stream);
+
+/* --- batched lattice sums ----------------------------------------------------- */
+/* n_req sums in one pass: sum r uses lats[r], specs[r], quads[r] and writes
+ * out[r*EZ_MAX_PROD + p] for p < specs[r].n_prod (host or device).
+ * lines (optional, host or device): per-line partial sums laid out per request as
+ *   [sector][u node][p] for the far field followed by [sector][p] for the near part,
+ * request r starting at offset ez_lines_offset(...) -- used for sampled checks.
+ * line_offsets (optional, host, n_req+1 ints) receives those offsets (in doubles). */
+int ez_lattice_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
+                    const ez_quadrature* quads, double* out, double* lines, long long* line_offsets,
+                    void* stream);
+
+/* Number of Duffy sectors (d 2^{d-1}) and far-field u nodes for (d, q). */
+int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q, int* n_sectors,
+              int* n_u_total, int* u_rule_used);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* ez_last_error(void);
+
+/* Number of kernels launched by this library on the calling thread since the
+ * last reset (reset = 1 clears it). */
+long long ez_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EZETA_H */

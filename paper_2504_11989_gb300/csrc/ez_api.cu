@@ -1,0 +1,1114 @@
+// Host side of the C ABI declared in include/ezeta.h: argument checks, lattice
+// handles, Gauss-Legendre rules, planning of tables and output segments, and the
+// launch sequence (setup kernels -> far/near kernels -> fixed-order reductions).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ez_kernels.h"
+
+using namespace ez;
+
+// ---------------------------------------------------------------------------
+// errors and launch accounting
+// ---------------------------------------------------------------------------
+static thread_local std::string t_err;
+static thread_local long long t_launches = 0;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+#define EZ_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(EZ_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                        \
+  } while (0)
+
+#define EZ_LAUNCHED()                                                                       \
+  do {                                                                                      \
+    ++t_launches;                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                    \
+    if (e_ != cudaSuccess) return fail(EZ_ECUDA, "launch: %s (line %d)", cudaGetErrorString(e_), __LINE__); \
+  } while (0)
+
+extern "C" const char* ez_last_error(void) { return t_err.c_str(); }
+extern "C" long long ez_launch_count(int reset) {
+  long long v = t_launches;
+  if (reset) t_launches = 0;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// lattices
+// ---------------------------------------------------------------------------
+struct ez_lattice_s {
+  int d;
+  double A[9], Ai[9], AiT[9], At[9], V;
+};
+
+static double det3(int d, const double* A) {
+  if (d == 1) return A[0];
+  if (d == 2) return A[0] * A[3] - A[1] * A[2];
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+// inverse by Gauss-Jordan elimination with partial pivoting
+static bool invert(int d, const double* A, double* X) {
+  double M[3][6];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < 2 * d; ++j) M[i][j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
+  for (int c = 0; c < d; ++c) {
+    int p = c;
+    for (int r = c + 1; r < d; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+    if (M[p][c] == 0.0 || !std::isfinite(M[p][c])) return false;
+    if (p != c)
+      for (int j = 0; j < 2 * d; ++j) std::swap(M[p][j], M[c][j]);
+    double inv = 1.0 / M[c][c];
+    for (int j = 0; j < 2 * d; ++j) M[c][j] *= inv;
+    for (int r = 0; r < d; ++r)
+      if (r != c) {
+        double f = M[r][c];
+        for (int j = 0; j < 2 * d; ++j) M[r][j] -= f * M[c][j];
+      }
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) X[i * d + j] = M[i][j + d];
+  return true;
+}
+
+extern "C" int ez_lattice_create(int d, const double* A, ez_lattice* out) {
+  if (!out || !A) return fail(EZ_EINVAL, "ez_lattice_create: NULL argument");
+  if (d < 1 || d > 3) return fail(EZ_EINVAL, "ez_lattice_create: d = %d not in 1..3", d);
+  for (int i = 0; i < d * d; ++i)
+    if (!std::isfinite(A[i])) return fail(EZ_EINVAL, "ez_lattice_create: non-finite A");
+  ez_lattice L = new ez_lattice_s();
+  L->d = d;
+  std::memset(L->A, 0, sizeof L->A);
+  std::memcpy(L->A, A, sizeof(double) * d * d);
+  L->V = std::fabs(det3(d, L->A));
+  if (!(L->V > 0.0) || !invert(d, L->A, L->Ai)) {
+    delete L;
+    return fail(EZ_EINVAL, "ez_lattice_create: singular lattice matrix");
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      L->AiT[i * d + j] = L->Ai[j * d + i];
+      L->At[i * d + j] = L->A[j * d + i];
+    }
+  *out = L;
+  return EZ_OK;
+}
+
+extern "C" int ez_lattice_destroy(ez_lattice L) {
+  delete L;
+  return EZ_OK;
+}
+
+extern "C" void ez_quadrature_default(ez_quadrature* q) {
+  if (!q) return;
+  std::memset(q, 0, sizeof *q);
+  q->n_u = 32;
+  q->n_v = 32;
+  q->eps = 1e-2;
+  q->ell = 4;
+  q->prec = EZ_FP64;
+  q->dedupe = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre on [0, 1].  Newton's method in theta on P_n(cos theta).  The
+// Legendre recurrence runs on (P_k, P_k - P_{k-1}) at z = 1 - delta with delta =
+// 2 sin^2(theta/2) computed directly, so the nodes next to the endpoints keep full
+// relative accuracy (the plain recurrence at z = cos(theta) loses ~ eps/theta^2).
+// Nodes with theta <= pi/2 are computed, the rest mirrored (x -> 1 - x).
+// ---------------------------------------------------------------------------
+static void legendre_near_one(int n, double delta, double* p_n, double* diff_n) {
+  // k = 1: P_1 = 1 - delta, P_1 - P_0 = -delta
+  double p = 1.0 - delta, df = -delta;
+  for (int k = 1; k < n; ++k) {
+    const double next = (k * df - (2 * k + 1) * delta * p) / (k + 1);
+    p += next;
+    df = next;
+  }
+  *p_n = n ? p : 1.0;
+  *diff_n = n ? df : 0.0;
+}
+
+static void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; 2 * i < n; ++i) {
+    const bool middle = 2 * i + 1 == n;
+    double th = middle ? 0.5 * kPi : kPi * (4.0 * i + 3.0) / (4.0 * n + 2.0);
+    double pn = 0.0, df = 0.0;
+    for (int it = 0; it < 60 && !middle; ++it) {
+      const double sh = std::sin(0.5 * th);
+      const double delta = 2.0 * sh * sh;
+      legendre_near_one(n, delta, &pn, &df);
+      const double slope = -n * (delta * pn - df) / std::sin(th);
+      const double step = pn / slope;
+      th -= step;
+      if (std::fabs(step) <= 1e-16 * th) break;
+    }
+    const double sh = std::sin(0.5 * th), ch = std::cos(0.5 * th);
+    const double delta = 2.0 * sh * sh;
+    legendre_near_one(n, delta, &pn, &df);
+    const double q = n * (delta * pn - df), s = std::sin(th);
+    x[i] = sh * sh;
+    w[i] = s * s / (q * q);
+    x[n - 1 - i] = ch * ch;
+    w[n - 1 - i] = w[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr double kTcut = 45.0;  // default cutoffs: exp(-45) ~ 3e-20
+
+struct Plan {
+  const ez_lattice_s* L;
+  ez_sum_spec spec;
+  int d, nsect, n_ui, n_v, u_rule, ell, prec;
+  double lam, r_real, r_recip, eps;
+  int M[3], box[3];
+  long long cells;
+  int rlo[3], rext[3];
+  long long rcap;
+  double R2enum;
+  std::vector<double> un, uw, vn, vw;
+  PhiInfo phi[EZ_MAX_NU];
+  double rser[EZ_MAX_NU][16];
+  bool near;
+  std::vector<int> alpha, alpha_off;
+  int nch;            // far segments per line (d = 3: v2 chunks)
+  int n_far_seg, n_far_items, near_per_sector, n_near_seg, n_lines_far, n_lines;
+  size_t smem;
+};
+
+double psi_int(int m) {  // digamma(m + 1)
+  double s = -0.57721566490153286060651209;
+  for (int k = 1; k <= m; ++k) s += 1.0 / k;
+  return s;
+}
+
+bool is_integer(double x) { return std::fabs(x - std::nearbyint(x)) < 1e-12; }
+
+void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
+  std::memset(&P, 0, sizeof P);
+  P.a = a;
+  P.two_a = (int)std::lrint(2.0 * a);
+  P.log_m = (is_integer(a) && a <= 0.0) ? (int)std::lrint(-a) : -1;
+  P.t_geo_end = kT0 * std::pow(kGeoR, kNGeo);
+  int n_unit = (int)std::ceil(std::max(0.0, t_hi_needed - P.t_geo_end)) + 1;
+  P.n_int = std::min(kNGeo + n_unit, kMaxInt);
+  P.t_hi = P.t_geo_end + (P.n_int - kNGeo);
+  double fact = 1.0;
+  if (P.log_m >= 0) {
+    const int m = P.log_m;
+    double mf = 1.0;
+    for (int k = 2; k <= m; ++k) mf *= k;
+    P.gam = ((m & 1) ? -1.0 : 1.0) / mf;
+    for (int n = 0; n < kNSer; ++n) {
+      if (n > 0) fact *= n;
+      double sg = (n & 1) ? -1.0 : 1.0;
+      P.ser[n] = n == m ? P.gam * psi_int(m) : -sg / (fact * (n - m));
+    }
+  } else {
+    P.gam = std::tgamma(a);
+    for (int n = 0; n < kNSer; ++n) {
+      if (n > 0) fact *= n;
+      double sg = (n & 1) ? -1.0 : 1.0;
+      P.ser[n] = -sg / (fact * (a + n));
+    }
+  }
+}
+
+// regularised h = 0 series (lambda piece of the log case included)
+void fill_rser(double* r, double a, double lam, int nmax) {
+  int m = (is_integer(a) && a <= 0.0) ? (int)std::lrint(-a) : -1;
+  double fact = 1.0;
+  for (int n = 0; n <= nmax; ++n) {
+    if (n > 0) fact *= n;
+    double sg = (n & 1) ? -1.0 : 1.0;
+    if (n == m)
+      r[n] = sg / fact * (psi_int(m) - 2.0 * std::log(lam));
+    else
+      r[n] = -sg / (fact * (a + n));
+  }
+}
+
+// combinations of singular factors: returns false if some mu + 2k == 0
+bool near_exponents_ok(const Plan& p, int prod, std::string* why) {
+  const ez_sum_spec& s = p.spec;
+  int e[EZ_MAX_NU], t[EZ_MAX_NU];
+  for (int j = 0; j < s.n_distinct; ++j) {
+    e[j] = s.expo[prod][j];
+    t[j] = 0;
+  }
+  while (true) {
+    int mu = p.d, deg = 0;
+    for (int j = 0; j < s.n_distinct; ++j) {
+      mu += t[j] * ((int)std::lrint(s.nu[j]) - p.d);
+      deg += (e[j] - t[j]) * p.ell;
+    }
+    deg = std::min(deg, kNearMaxDeg);
+    for (int k = 0; k <= deg; ++k)
+      if (mu + 2 * k == 0) {
+        char b[160];
+        snprintf(b, sizeof b, "Hadamard exponent mu + 2k = 0 (mu = %d, k = %d) in product %d", mu, k, prod);
+        *why = b;
+        return false;
+      }
+    int j = 0;
+    for (; j < s.n_distinct; ++j) {
+      if (t[j] < e[j]) {
+        t[j]++;
+        break;
+      }
+      t[j] = 0;
+    }
+    if (j == s.n_distinct) break;
+  }
+  return true;
+}
+
+int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadrature& qin, Plan& p) {
+  ez_quadrature q = qin;
+  p.L = L;
+  p.spec = spec;
+  p.d = L->d;
+  const int d = p.d;
+  if (spec.n_distinct < 1 || spec.n_distinct > EZ_MAX_NU) return fail(EZ_EINVAL, "n_distinct = %d", spec.n_distinct);
+  if (spec.n_prod < 1 || spec.n_prod > EZ_MAX_PROD) return fail(EZ_EINVAL, "n_prod = %d", spec.n_prod);
+  int maxfac = 0;
+  for (int pr = 0; pr < spec.n_prod; ++pr) {
+    int nf = 0;
+    for (int j = 0; j < spec.n_distinct; ++j) {
+      if (spec.expo[pr][j] < 0) return fail(EZ_EINVAL, "negative exponent count");
+      nf += spec.expo[pr][j];
+    }
+    if (nf > kMaxFactor) return fail(EZ_EINVAL, "product %d has %d > %d factors", pr, nf, kMaxFactor);
+    maxfac = std::max(maxfac, nf);
+  }
+  bool singular = false;
+  for (int j = 0; j < spec.n_distinct; ++j) {
+    double nu = spec.nu[j];
+    if (!std::isfinite(nu)) return fail(EZ_EINVAL, "non-finite exponent");
+    if (!is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
+    if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
+    int dn = (int)std::lrint(nu) - d;
+    if (dn < 0 || (dn % 2) == 0) singular = true;
+  }
+  if (q.n_u < 1 || q.n_u > 1 << 20) return fail(EZ_EINVAL, "n_u = %d", q.n_u);
+  if (d > 1 && (q.n_v < 1 || q.n_v > 256)) return fail(EZ_EINVAL, "n_v = %d (1..256)", q.n_v);
+  p.n_v = d > 1 ? q.n_v : 1;
+  p.u_rule = q.u_rule ? q.u_rule : (singular ? 2 : 1);
+  if (p.u_rule != 1 && p.u_rule != 2) return fail(EZ_EINVAL, "u_rule = %d", q.u_rule);
+  p.eps = q.eps > 0.0 ? q.eps : 1e-2;
+  if (!(p.eps < 0.5)) return fail(EZ_EINVAL, "eps = %g", p.eps);
+  p.ell = q.ell > 0 ? q.ell : 4;
+  if (p.ell > 8) return fail(EZ_EINVAL, "ell = %d > 8", p.ell);
+  p.prec = q.prec;
+  if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
+  if (p.prec == EZ_MIXED) return fail(EZ_EUNSUPPORTED, "mixed precision not built yet");
+  p.lam = q.lambda > 0.0 ? q.lambda : std::pow(L->V, 1.0 / d);
+  p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(kTcut / kPi);
+  p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(kTcut / kPi) / p.lam;
+  p.nsect = d * (1 << (d - 1));
+  p.near = p.u_rule == 2;
+
+  // real-space box
+  p.cells = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < d) {
+      double rn = 0.0;
+      for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+      p.M[i] = (int)std::ceil(p.r_real * std::sqrt(rn) + 1e-9);
+      if (p.M[i] > 16) return fail(EZ_EINVAL, "real-space box half-width %d > 16 (r_real too large)", p.M[i]);
+    } else {
+      p.M[i] = 0;
+    }
+    p.box[i] = 2 * p.M[i] + 1;
+    p.cells *= p.box[i];
+  }
+  // reciprocal enumeration: |A^{-T} h| <= r_recip + max_BZ |k|
+  double kmax = 0.0;
+  for (int c = 0; c < (1 << d); ++c) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double ki = 0.0;
+      for (int j = 0; j < d; ++j) ki += L->AiT[i * d + j] * (((c >> j) & 1) ? 0.5 : -0.5);
+      s += ki * ki;
+    }
+    kmax = std::max(kmax, std::sqrt(s));
+  }
+  double Renum = p.r_recip + kmax;
+  p.R2enum = Renum * Renum;
+  p.rcap = 1;
+  for (int i = 0; i < 3; ++i) {
+    int H = 0;
+    if (i < d) {
+      double cn = 0.0;
+      for (int j = 0; j < d; ++j) cn += L->A[j * d + i] * L->A[j * d + i];
+      H = (int)std::ceil(Renum * std::sqrt(cn) + 1e-9);
+    }
+    p.rlo[i] = -H;
+    p.rext[i] = 2 * H + 1;
+    p.rcap *= p.rext[i];
+  }
+  if (p.rcap > (1 << 22)) return fail(EZ_EINVAL, "reciprocal box too large (r_recip)");
+
+  // quadrature rules
+  std::vector<double> x, w;
+  gauss_legendre01(q.n_u, x, w);
+  if (p.u_rule == 1) {
+    p.un.resize(q.n_u);
+    p.uw.resize(q.n_u);
+    for (int i = 0; i < q.n_u; ++i) {
+      p.un[i] = 0.5 * x[i];
+      p.uw[i] = 0.5 * w[i];
+    }
+  } else {
+    double a = p.eps;
+    while (a < 0.5) {
+      double b = std::min(2.0 * a, 0.5);
+      for (int i = 0; i < q.n_u; ++i) {
+        p.un.push_back(a + (b - a) * x[i]);
+        p.uw.push_back((b - a) * w[i]);
+      }
+      a = b;
+    }
+  }
+  p.n_ui = (int)p.un.size();
+  if (d > 1) {
+    gauss_legendre01(p.n_v, p.vn, p.vw);
+  } else {
+    p.vn.assign(1, 0.0);
+    p.vw.assign(1, 1.0);
+  }
+
+  // Phi tables
+  const double c_lam = kPi * p.lam * p.lam;
+  for (int j = 0; j < spec.n_distinct; ++j) {
+    fill_phi_host(p.phi[j], 0.5 * (d - spec.nu[j]), c_lam * p.r_recip * p.r_recip);
+    fill_rser(p.rser[j], 0.5 * (d - spec.nu[j]), p.lam, 15);
+  }
+
+  // near part
+  if (p.near) {
+    p.alpha.clear();
+    p.alpha_off.clear();
+    for (int k = 0; k <= p.ell; ++k) {
+      p.alpha_off.push_back((int)(p.alpha.size() / 3));
+      int K2 = 2 * k;
+      for (int a0 = K2; a0 >= 0; --a0)
+        for (int a1 = (d > 1 ? K2 - a0 : 0); a1 >= 0; --a1) {
+          int a2 = K2 - a0 - a1;
+          if (d < 3 && a2 != 0) continue;
+          if (d < 2 && a1 != 0) continue;
+          p.alpha.push_back(a0);
+          p.alpha.push_back(a1);
+          p.alpha.push_back(a2);
+        }
+    }
+    p.alpha_off.push_back((int)(p.alpha.size() / 3));
+    for (int pr = 0; pr < spec.n_prod; ++pr) {
+      std::string why;
+      if (!near_exponents_ok(p, pr, &why)) return fail(EZ_EDOMAIN, "%s", why.c_str());
+    }
+  }
+
+  // segments
+  p.nch = d == 3 ? (p.n_v + kVChunk - 1) / kVChunk : 1;
+  if (d == 1) {
+    p.n_far_seg = p.n_ui;
+    p.n_far_items = (p.n_ui + 127) / 128;
+  } else {
+    p.n_far_seg = p.nsect * p.n_ui * p.nch;
+    p.n_far_items = p.n_far_seg;
+  }
+  int nrays = d == 1 ? 1 : (d == 2 ? p.n_v : p.n_v * p.n_v);
+  p.near_per_sector = p.near ? (nrays + 127) / 128 : 0;
+  p.n_near_seg = p.nsect * p.near_per_sector;
+  p.n_lines_far = p.nsect * p.n_ui;
+  p.n_lines = p.n_lines_far + (p.near ? p.nsect : 0);
+  p.smem = far_smem_bytes(d, spec.n_distinct, p.M, p.n_v);
+  return EZ_OK;
+}
+
+// sigma_nu of s_hat (Sec. 3)
+double sigma_of(int d, double nu, int* islog) {
+  int dn = (int)std::lrint(nu) - d;
+  if (dn >= 0 && dn % 2 == 0) {
+    int m = dn / 2;
+    *islog = 1;
+    double mf = std::tgamma(m + 1.0);
+    return std::pow(kPi, 2.0 * m + 0.5 * d) / std::tgamma(m + 0.5 * d) * ((m & 1) ? 1.0 : -1.0) / mf;
+  }
+  *islog = 0;
+  return std::pow(kPi, nu - 0.5 * d) * std::tgamma(0.5 * (d - nu)) / std::tgamma(0.5 * nu);
+}
+
+// ---------------------------------------------------------------------------
+// device arena (grow-only) and pinned staging
+// ---------------------------------------------------------------------------
+struct Arena {
+  std::mutex mu;
+  int dev = -1;
+  char* d = nullptr;
+  size_t dcap = 0;
+  char* h = nullptr;
+  size_t hcap = 0;
+};
+Arena g_arena;
+
+int arena_reserve(size_t dbytes, size_t hbytes) {
+  int dev = 0;
+  EZ_CUDA(cudaGetDevice(&dev));
+  if (g_arena.dev != dev) {
+    g_arena.d = nullptr;
+    g_arena.dcap = 0;
+    g_arena.dev = dev;
+  }
+  if (dbytes > g_arena.dcap) {
+    if (g_arena.d) cudaFree(g_arena.d);
+    g_arena.d = nullptr;
+    size_t want = std::max(dbytes, g_arena.dcap * 2);
+    if (cudaMalloc(&g_arena.d, want) != cudaSuccess) {
+      cudaGetLastError();
+      g_arena.dcap = 0;
+      return fail(EZ_ENOMEM, "device allocation of %zu bytes failed", want);
+    }
+    g_arena.dcap = want;
+  }
+  if (hbytes > g_arena.hcap) {
+    if (g_arena.h) cudaFreeHost(g_arena.h);
+    g_arena.h = nullptr;
+    size_t want = std::max(hbytes, g_arena.hcap * 2);
+    if (cudaMallocHost(&g_arena.h, want) != cudaSuccess) {
+      cudaGetLastError();
+      g_arena.hcap = 0;
+      return fail(EZ_ENOMEM, "pinned allocation of %zu bytes failed", want);
+    }
+    g_arena.hcap = want;
+  }
+  return EZ_OK;
+}
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes, size_t align = 256) {
+    off = (off + align - 1) / align * align;
+    size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool g_init = false;
+int init_constants() {
+  if (g_init) return EZ_OK;
+  // Chebyshev -> monomial matrix: T_j(x) = sum_i c[j][i] x^i
+  double c[kNC][kNC];
+  std::memset(c, 0, sizeof c);
+  c[0][0] = 1.0;
+  if (kNC > 1) c[1][1] = 1.0;
+  for (int j = 2; j < kNC; ++j)
+    for (int i = 0; i < kNC; ++i) c[j][i] = (i > 0 ? 2.0 * c[j - 1][i - 1] : 0.0) - c[j - 2][i];
+  EZ_CUDA(upload_cheb2mono(&c[0][0]));
+  EZ_CUDA(cudaFuncSetAttribute(far_kernel_d3, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  EZ_CUDA(cudaFuncSetAttribute(far_kernel_d2, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  g_init = true;
+  return EZ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batched lattice sums
+// ---------------------------------------------------------------------------
+static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs, const ez_quadrature* quads,
+                    double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
+  if (n_req < 1) return fail(EZ_EINVAL, "n_req = %d", n_req);
+  if (!lats || !specs || !quads || !out) return fail(EZ_EINVAL, "NULL argument");
+  int rc = init_constants();
+  if (rc) return rc;
+  std::vector<Plan> plans(n_req);
+  for (int r = 0; r < n_req; ++r) {
+    if (!lats[r]) return fail(EZ_EINVAL, "lattice %d is NULL", r);
+    rc = make_plan(lats[r], specs[r], quads[r], plans[r]);
+    if (rc) return rc;
+  }
+  // ---- order: requests grouped by d for the far launches
+  std::vector<int> order;
+  for (int d = 1; d <= 3; ++d)
+    for (int r = 0; r < n_req; ++r)
+      if (plans[r].d == d) order.push_back(r);
+
+  // ---- sizes
+  long long n_seg = 0, n_lines = 0;
+  size_t n_items_far = 0, n_items_near = 0;
+  std::vector<long long> seg_far0(n_req), seg_near0(n_req), line0(n_req);
+  for (int r : order) {
+    seg_far0[r] = n_seg;
+    n_seg += plans[r].n_far_seg;
+    n_items_far += plans[r].n_far_items;
+  }
+  for (int r : order) {
+    seg_near0[r] = n_seg;
+    n_seg += plans[r].n_near_seg;
+    n_items_near += plans[r].n_near_seg;
+  }
+  for (int r = 0; r < n_req; ++r) {
+    line0[r] = n_lines;
+    n_lines += plans[r].n_lines;
+  }
+  Layout dl, hl;
+  const size_t o_req = dl.take(sizeof(ReqDesc) * n_req), h_req = hl.take(sizeof(ReqDesc) * n_req);
+  const size_t o_items = dl.take(sizeof(Item) * (n_items_far + n_items_near)),
+               h_items = hl.take(sizeof(Item) * (n_items_far + n_items_near));
+  const size_t o_rj = dl.take(sizeof(RecipJob) * n_req), h_rj = hl.take(sizeof(RecipJob) * n_req);
+  const size_t o_gj = dl.take(sizeof(GboxJob) * n_req), h_gj = hl.take(sizeof(GboxJob) * n_req);
+  int n_phi = 0, n_tay = 0;
+  for (int r = 0; r < n_req; ++r) {
+    n_phi += plans[r].spec.n_distinct;
+    if (plans[r].near) n_tay += plans[r].spec.n_distinct;
+  }
+  const size_t o_pj = dl.take(sizeof(PhiJob) * n_phi), h_pj = hl.take(sizeof(PhiJob) * n_phi);
+  const size_t o_tj = dl.take(sizeof(TaylorJob) * std::max(n_tay, 1)), h_tj = hl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
+  const size_t o_lreq = dl.take(sizeof(int) * n_lines), h_lreq = hl.take(sizeof(int) * n_lines);
+  const size_t o_lseg0 = dl.take(sizeof(long long) * n_lines), h_lseg0 = hl.take(sizeof(long long) * n_lines);
+  const size_t o_lnseg = dl.take(sizeof(int) * n_lines), h_lnseg = hl.take(sizeof(int) * n_lines);
+  const size_t o_rl0 = dl.take(sizeof(long long) * n_req), h_rl0 = hl.take(sizeof(long long) * n_req);
+  const size_t o_rnl = dl.take(sizeof(int) * n_req), h_rnl = hl.take(sizeof(int) * n_req);
+  std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
+  std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
+  std::vector<size_t> o_rec(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
+  std::vector<std::vector<size_t>> o_tab(n_req);
+  for (int r = 0; r < n_req; ++r) {
+    Plan& p = plans[r];
+    o_un[r] = dl.take(sizeof(double) * p.n_ui);
+    h_un[r] = hl.take(sizeof(double) * p.n_ui);
+    o_uw[r] = dl.take(sizeof(double) * p.n_ui);
+    h_uw[r] = hl.take(sizeof(double) * p.n_ui);
+    o_vn[r] = dl.take(sizeof(double) * p.vn.size());
+    h_vn[r] = hl.take(sizeof(double) * p.vn.size());
+    o_vw[r] = dl.take(sizeof(double) * p.vw.size());
+    h_vw[r] = hl.take(sizeof(double) * p.vw.size());
+    o_al[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
+    h_al[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
+    o_alo[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
+    h_alo[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
+    o_rec[r] = dl.take(sizeof(G4) * p.rcap);
+    o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
+    for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
+    const size_t na = p.alpha.size() / 3;
+    o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
+    o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
+  }
+  const size_t o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
+  const size_t o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
+  const size_t o_out = dl.take(sizeof(double) * EZ_MAX_PROD * n_req);
+
+  std::lock_guard<std::mutex> lock(g_arena.mu);
+  rc = arena_reserve(dl.off, hl.off);
+  if (rc) return rc;
+  char* D = g_arena.d;
+  char* Hs = g_arena.h;
+  auto dptr = [&](size_t o) { return (void*)(D + o); };
+
+  // ---- fill host staging
+  ReqDesc* reqs = (ReqDesc*)(Hs + h_req);
+  Item* items = (Item*)(Hs + h_items);
+  RecipJob* rjobs = (RecipJob*)(Hs + h_rj);
+  GboxJob* gjobs = (GboxJob*)(Hs + h_gj);
+  PhiJob* pjobs = (PhiJob*)(Hs + h_pj);
+  TaylorJob* tjobs = (TaylorJob*)(Hs + h_tj);
+  int* lreq = (int*)(Hs + h_lreq);
+  long long* lseg0 = (long long*)(Hs + h_lseg0);
+  int* lnseg = (int*)(Hs + h_lnseg);
+  long long* rl0 = (long long*)(Hs + h_rl0);
+  int* rnl = (int*)(Hs + h_rnl);
+  int ipj = 0, itj = 0;
+  for (int r = 0; r < n_req; ++r) {
+    Plan& p = plans[r];
+    const ez_lattice_s* L = p.L;
+    ReqDesc& R = reqs[r];
+    std::memset(&R, 0, sizeof R);
+    R.d = p.d;
+    R.nsect = p.nsect;
+    R.n_ui = p.n_ui;
+    R.n_v = p.n_v;
+    R.u_rule = p.u_rule;
+    R.n_distinct = p.spec.n_distinct;
+    R.n_prod = p.spec.n_prod;
+    R.ell = p.ell;
+    R.prec = p.prec;
+    std::memcpy(R.expo, p.spec.expo, sizeof R.expo);
+    std::memcpy(R.A, L->A, sizeof R.A);
+    std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+    R.V = L->V;
+    R.lam = p.lam;
+    R.c_lam = kPi * p.lam * p.lam;
+    R.vol_fac = std::pow(p.lam, p.d) / L->V;
+    R.R2_recip = p.r_recip * p.r_recip;
+    R.eps = p.eps;
+    for (int j = 0; j < p.spec.n_distinct; ++j) {
+      double nu = p.spec.nu[j];
+      R.nu[j] = nu;
+      R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
+      R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
+      R.phi[j] = p.phi[j];
+      R.phi[j].tab = (const double*)dptr(o_tab[r][j]);
+      PhiJob& J = pjobs[ipj++];
+      J.a = p.phi[j].a;
+      J.t_geo_end = p.phi[j].t_geo_end;
+      J.n_int = p.phi[j].n_int;
+      J.out = (double*)dptr(o_tab[r][j]);
+      J.outf = nullptr;
+    }
+    for (int i = 0; i < 3; ++i) {
+      R.M[i] = p.M[i];
+      R.box[i] = p.box[i];
+    }
+    R.gbox = (const double*)dptr(o_gbox[r]);
+    R.rec = (const G4*)dptr(o_rec[r]);
+    R.n_rec = 0;
+    R.u_nodes = (const double*)dptr(o_un[r]);
+    R.u_w = (const double*)dptr(o_uw[r]);
+    R.v_nodes = (const double*)dptr(o_vn[r]);
+    R.v_w = (const double*)dptr(o_vw[r]);
+    std::memcpy(Hs + h_un[r], p.un.data(), sizeof(double) * p.n_ui);
+    std::memcpy(Hs + h_uw[r], p.uw.data(), sizeof(double) * p.n_ui);
+    std::memcpy(Hs + h_vn[r], p.vn.data(), sizeof(double) * p.vn.size());
+    std::memcpy(Hs + h_vw[r], p.vw.data(), sizeof(double) * p.vw.size());
+    R.n_alpha = (int)(p.alpha.size() / 3);
+    R.alpha = (const int*)dptr(o_al[r]);
+    R.alpha_off = (const int*)dptr(o_alo[r]);
+    R.taylor = (const double*)dptr(o_tay[r]);
+    if (!p.alpha.empty()) {
+      std::memcpy(Hs + h_al[r], p.alpha.data(), sizeof(int) * p.alpha.size());
+      std::memcpy(Hs + h_alo[r], p.alpha_off.data(), sizeof(int) * p.alpha_off.size());
+    }
+    RecipJob& RJ = rjobs[r];
+    RJ.req = r;
+    for (int i = 0; i < 3; ++i) {
+      RJ.lo[i] = p.rlo[i];
+      RJ.ext[i] = p.rext[i];
+    }
+    RJ.R2 = p.R2enum;
+    RJ.cap = (int)p.rcap;
+    RJ.out = (G4*)dptr(o_rec[r]);
+    GboxJob& GJ = gjobs[r];
+    std::memset(&GJ, 0, sizeof GJ);
+    GJ.req = r;
+    GJ.x_in_lattice = 1;
+    GJ.R2 = p.r_real * p.r_real;
+    GJ.out = (double*)dptr(o_gbox[r]);
+    if (p.near)
+      for (int j = 0; j < p.spec.n_distinct; ++j) {
+        TaylorJob& T = tjobs[itj++];
+        T.req = r;
+        T.nu_index = j;
+        T.phiG = (double*)dptr(o_phig[r]) + (size_t)j * p.rcap * (2 * p.ell + 1);
+        std::memcpy(T.rser, p.rser[j], sizeof T.rser);
+        T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
+      }
+  }
+  // items (far: grouped by d; near after)
+  size_t ii = 0;
+  size_t far_begin[4] = {0, 0, 0, 0}, far_end[4] = {0, 0, 0, 0};
+  for (int d = 1; d <= 3; ++d) {
+    far_begin[d] = ii;
+    for (int r : order) {
+      Plan& p = plans[r];
+      if (p.d != d) continue;
+      if (d == 1) {
+        for (int c = 0; c < p.n_far_items; ++c) items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
+      } else {
+        long long s0 = seg_far0[r];
+        for (int s = 0; s < p.nsect; ++s)
+          for (int iu = 0; iu < p.n_ui; ++iu)
+            for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, s0++};
+      }
+    }
+    far_end[d] = ii;
+  }
+  const size_t near_begin = ii;
+  for (int r : order) {
+    Plan& p = plans[r];
+    long long s0 = seg_near0[r];
+    for (int s = 0; s < p.nsect; ++s)
+      for (int c = 0; c < p.near_per_sector; ++c) items[ii++] = Item{r, s, 0, c, s0++};
+  }
+  const size_t near_end = ii;
+  // lines
+  for (int r = 0; r < n_req; ++r) {
+    Plan& p = plans[r];
+    long long L0 = line0[r];
+    rl0[r] = L0;
+    rnl[r] = p.n_lines;
+    for (int s = 0; s < p.nsect; ++s)
+      for (int iu = 0; iu < p.n_ui; ++iu) {
+        long long L = L0 + (long long)s * p.n_ui + iu;
+        lreq[L] = r;
+        lseg0[L] = seg_far0[r] + ((long long)s * p.n_ui + iu) * p.nch;
+        lnseg[L] = p.nch;
+      }
+    if (p.near)
+      for (int s = 0; s < p.nsect; ++s) {
+        long long L = L0 + p.n_lines_far + s;
+        lreq[L] = r;
+        lseg0[L] = seg_near0[r] + (long long)s * p.near_per_sector;
+        lnseg[L] = p.near_per_sector;
+      }
+  }
+  // ---- upload and launch
+  EZ_CUDA(cudaMemcpyAsync(D, Hs, hl.off, cudaMemcpyHostToDevice, stream));
+  ReqDesc* dreqs = (ReqDesc*)dptr(o_req);
+  enum_recip_kernel<<<n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(o_rj));
+  EZ_LAUNCHED();
+  long long max_cells = 0;
+  for (auto& p : plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
+  gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(o_gj), n_req);
+  EZ_LAUNCHED();
+  int max_int = 0;
+  for (auto& p : plans)
+    for (int j = 0; j < p.spec.n_distinct; ++j) max_int = std::max(max_int, p.phi[j].n_int);
+  phitab_kernel<<<dim3(max_int, n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(o_pj));
+  EZ_LAUNCHED();
+  if (n_tay) {
+    long long max_rec = 0;
+    int tot_alpha = 0;
+    for (auto& p : plans)
+      if (p.near) {
+        max_rec = std::max(max_rec, p.rcap);
+        tot_alpha += (int)(p.alpha.size() / 3) * p.spec.n_distinct;
+      }
+    phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(o_tj), n_tay);
+    EZ_LAUNCHED();
+    taylor_kernel<<<(tot_alpha + 63) / 64, 64, 0, stream>>>(dreqs, (const TaylorJob*)dptr(o_tj), n_tay);
+    EZ_LAUNCHED();
+  }
+  Item* ditems = (Item*)dptr(o_items);
+  double* dseg = (double*)dptr(o_seg);
+  if (far_end[1] > far_begin[1]) {
+    far_kernel_d1<<<(unsigned)(far_end[1] - far_begin[1]), 128, 0, stream>>>(dreqs, ditems + far_begin[1], dseg);
+    EZ_LAUNCHED();
+  }
+  if (far_end[2] > far_begin[2]) {
+    size_t sm = 0;
+    for (auto& p : plans)
+      if (p.d == 2) sm = std::max(sm, p.smem);
+    far_kernel_d2<<<(unsigned)(far_end[2] - far_begin[2]), 128, sm, stream>>>(dreqs, ditems + far_begin[2], dseg);
+    EZ_LAUNCHED();
+  }
+  if (far_end[3] > far_begin[3]) {
+    size_t sm = 0;
+    for (auto& p : plans)
+      if (p.d == 3) sm = std::max(sm, p.smem);
+    if (sm > 200 * 1024) return fail(EZ_EINVAL, "far kernel needs %zu bytes of shared memory", sm);
+    far_kernel_d3<<<(unsigned)(far_end[3] - far_begin[3]), 256, sm, stream>>>(dreqs, ditems + far_begin[3], dseg);
+    EZ_LAUNCHED();
+  }
+  if (near_end > near_begin) {
+    near_kernel<<<(unsigned)(near_end - near_begin), 128, 0, stream>>>(dreqs, ditems + near_begin, dseg);
+    EZ_LAUNCHED();
+  }
+  double* dlines = (double*)dptr(o_lines);
+  lines_kernel<<<(unsigned)((n_lines + 127) / 128), 128, 0, stream>>>(dreqs, (const int*)dptr(o_lreq),
+                                                                     (const long long*)dptr(o_lseg0),
+                                                                     (const int*)dptr(o_lnseg), (int)n_lines, dseg, dlines);
+  EZ_LAUNCHED();
+  double* dout = (double*)dptr(o_out);
+  total_kernel<<<(n_req * EZ_MAX_PROD + 127) / 128, 128, 0, stream>>>(dreqs, (const long long*)dptr(o_rl0),
+                                                                     (const int*)dptr(o_rnl), n_req, dlines, dout);
+  EZ_LAUNCHED();
+  EZ_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * EZ_MAX_PROD * n_req, cudaMemcpyDefault, stream));
+  if (lines_out)
+    EZ_CUDA(cudaMemcpyAsync(lines_out, dlines, sizeof(double) * EZ_MAX_PROD * n_lines, cudaMemcpyDefault, stream));
+  if (line_offsets)
+    for (int r = 0; r <= n_req; ++r) line_offsets[r] = r < n_req ? line0[r] : n_lines;
+  EZ_CUDA(cudaStreamSynchronize(stream));
+  return EZ_OK;
+}
+
+extern "C" int ez_lattice_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
+                               const ez_quadrature* quads, double* out, double* lines, long long* line_offsets,
+                               void* stream) {
+  return run_sums(n_req, lats, specs, quads, out, lines, line_offsets, (cudaStream_t)stream);
+}
+
+extern "C" int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q, int* n_sectors, int* n_u_total,
+                         int* u_rule_used) {
+  if (!spec || !q) return fail(EZ_EINVAL, "NULL argument");
+  ez_lattice_s L;
+  L.d = d;
+  if (d < 1 || d > 3) return fail(EZ_EINVAL, "d = %d", d);
+  double I[9] = {0};
+  for (int i = 0; i < d; ++i) I[i * d + i] = 1.0;
+  std::memcpy(L.A, I, sizeof I);
+  std::memcpy(L.Ai, I, sizeof I);
+  std::memcpy(L.AiT, I, sizeof I);
+  std::memcpy(L.At, I, sizeof I);
+  L.V = 1.0;
+  Plan p;
+  int rc = make_plan(&L, *spec, *q, p);
+  if (rc) return rc;
+  if (n_sectors) *n_sectors = p.nsect;
+  if (n_u_total) *n_u_total = p.n_ui;
+  if (u_rule_used) *u_rule_used = p.u_rule;
+  return EZ_OK;
+}
+
+extern "C" int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q, double* value,
+                                    void* stream) {
+  if (!lat || !nu || !q || !value) return fail(EZ_EINVAL, "NULL argument");
+  if (n < 1 || n > kMaxFactor) return fail(EZ_EINVAL, "n = %d not in 1..%d", n, kMaxFactor);
+  ez_sum_spec s;
+  std::memset(&s, 0, sizeof s);
+  s.n_prod = 1;
+  if (q->dedupe == 0) {
+    if (n > EZ_MAX_NU) return fail(EZ_EINVAL, "dedupe = 0 supports n <= %d", EZ_MAX_NU);
+    s.n_distinct = n;
+    for (int i = 0; i < n; ++i) {
+      s.nu[i] = nu[i];
+      s.expo[0][i] = 1;
+    }
+  } else {
+    for (int i = 0; i < n; ++i) {
+      int j = 0;
+      for (; j < s.n_distinct; ++j)
+        if (s.nu[j] == nu[i]) break;
+      if (j == s.n_distinct) {
+        if (s.n_distinct == EZ_MAX_NU) return fail(EZ_EINVAL, "more than %d distinct exponents", EZ_MAX_NU);
+        s.nu[s.n_distinct++] = nu[i];
+      }
+      s.expo[0][j]++;
+    }
+  }
+  double out[EZ_MAX_PROD];
+  int rc = run_sums(1, &lat, &s, q, out, nullptr, nullptr, (cudaStream_t)stream);
+  if (rc) return rc;
+  if (is_device_ptr(value))
+    EZ_CUDA(cudaMemcpyAsync(value, out, sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  else
+    *value = out[0];
+  return EZ_OK;
+}
+
+extern "C" int ez_atm_energy(ez_lattice lat, const ez_quadrature* q, double* energy, double* parts, void* stream) {
+  if (!lat || !q || !energy) return fail(EZ_EINVAL, "NULL argument");
+  ez_sum_spec s;
+  std::memset(&s, 0, sizeof s);
+  s.n_distinct = 4;
+  s.nu[0] = -1.0;
+  s.nu[1] = 1.0;
+  s.nu[2] = 3.0;
+  s.nu[3] = 5.0;
+  s.n_prod = 3;
+  s.expo[0][2] = 3;  // (3,3,3)
+  s.expo[1][0] = 1;  // (-1,5,5)
+  s.expo[1][3] = 2;
+  s.expo[2][1] = 1;  // (1,3,5)
+  s.expo[2][2] = 1;
+  s.expo[2][3] = 1;
+  double out[EZ_MAX_PROD];
+  int rc = run_sums(1, &lat, &s, q, out, nullptr, nullptr, (cudaStream_t)stream);
+  if (rc) return rc;
+  *energy = out[0] / 24.0 - 3.0 * out[1] / 16.0 + 3.0 * out[2] / 8.0;
+  if (parts)
+    for (int i = 0; i < 3; ++i) parts[i] = out[i];
+  return EZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Epstein zeta at many y
+// ---------------------------------------------------------------------------
+extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const double* y, size_t m, double* re,
+                               double* im, int prec, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!L || !x || (m && (!y || !re))) return fail(EZ_EINVAL, "NULL argument");
+  if (m == 0) return EZ_OK;
+  if (m > (size_t)1 << 31) return fail(EZ_EINVAL, "m too large");
+  if (prec != EZ_FP64 && prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", prec);
+  if (prec == EZ_MIXED) return fail(EZ_EUNSUPPORTED, "mixed precision not built yet");
+  if (!std::isfinite(nu) || !is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
+  if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
+  int rc = init_constants();
+  if (rc) return rc;
+  const int d = L->d;
+  ez_sum_spec s;
+  std::memset(&s, 0, sizeof s);
+  s.n_distinct = 1;
+  s.nu[0] = nu;
+  s.n_prod = 1;
+  s.expo[0][0] = 1;
+  ez_quadrature q;
+  ez_quadrature_default(&q);
+  q.n_u = 1;
+  q.n_v = 1;
+  q.u_rule = 1;
+  Plan p;
+  rc = make_plan(L, s, q, p);
+  if (rc) return rc;
+  // box around round(A^{-1} x)
+  double xt[3] = {0, 0, 0};
+  int mx[3] = {0, 0, 0};
+  bool x_in = true;
+  for (int i = 0; i < d; ++i) {
+    double v = 0.0;
+    for (int j = 0; j < d; ++j) v += L->Ai[i * d + j] * x[j];
+    xt[i] = v;
+    mx[i] = (int)std::lrint(v);
+    if (std::fabs(v - mx[i]) > 1e-12) x_in = false;
+  }
+  p.cells = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < d) {
+      double rn = 0.0;
+      for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+      p.M[i] = (int)std::ceil(p.r_real * std::sqrt(rn) + 0.5 + 1e-9);
+      if (p.M[i] > 24) return fail(EZ_EINVAL, "real-space box too large");
+    }
+    p.box[i] = 2 * p.M[i] + 1;
+    p.cells *= p.box[i];
+  }
+  const bool y_dev = is_device_ptr(y), re_dev = is_device_ptr(re), im_dev = im && is_device_ptr(im);
+  Layout dl, hl;
+  const size_t o_req = dl.take(sizeof(ReqDesc)), h_req = hl.take(sizeof(ReqDesc));
+  const size_t o_rj = dl.take(sizeof(RecipJob)), h_rj = hl.take(sizeof(RecipJob));
+  const size_t o_gj = dl.take(sizeof(GboxJob)), h_gj = hl.take(sizeof(GboxJob));
+  const size_t o_pj = dl.take(sizeof(PhiJob)), h_pj = hl.take(sizeof(PhiJob));
+  const size_t o_rec = dl.take(sizeof(G4) * p.rcap);
+  const size_t o_gbox = dl.take(sizeof(double) * p.cells);
+  const size_t o_tab = dl.take(sizeof(double) * kRec * p.phi[0].n_int);
+  const size_t o_st = dl.take(sizeof(int));
+  const size_t o_y = y_dev ? 0 : dl.take(sizeof(double) * m * d);
+  const size_t o_re = re_dev ? 0 : dl.take(sizeof(double) * m);
+  const size_t o_im = (!im || im_dev) ? 0 : dl.take(sizeof(double) * m);
+  std::lock_guard<std::mutex> lock(g_arena.mu);
+  rc = arena_reserve(dl.off, hl.off);
+  if (rc) return rc;
+  char* D = g_arena.d;
+  char* Hs = g_arena.h;
+  ReqDesc& R = *(ReqDesc*)(Hs + h_req);
+  std::memset(&R, 0, sizeof R);
+  R.d = d;
+  R.n_distinct = 1;
+  R.nu[0] = nu;
+  std::memcpy(R.A, L->A, sizeof R.A);
+  std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+  R.lam = p.lam;
+  for (int i = 0; i < 3; ++i) {
+    R.M[i] = p.M[i];
+    R.box[i] = p.box[i];
+  }
+  R.rec = (const G4*)(D + o_rec);
+  R.gbox = (const double*)(D + o_gbox);
+  RecipJob& RJ = *(RecipJob*)(Hs + h_rj);
+  RJ.req = 0;
+  for (int i = 0; i < 3; ++i) {
+    RJ.lo[i] = p.rlo[i];
+    RJ.ext[i] = p.rext[i];
+  }
+  RJ.R2 = p.R2enum;
+  RJ.cap = (int)p.rcap;
+  RJ.out = (G4*)(D + o_rec);
+  GboxJob& GJ = *(GboxJob*)(Hs + h_gj);
+  std::memset(&GJ, 0, sizeof GJ);
+  GJ.req = 0;
+  for (int i = 0; i < d; ++i) {
+    GJ.x[i] = x[i];
+    GJ.mx[i] = mx[i];
+  }
+  GJ.x_in_lattice = x_in ? 1 : 0;
+  GJ.R2 = p.r_real * p.r_real;
+  GJ.out = (double*)(D + o_gbox);
+  PhiJob& PJ = *(PhiJob*)(Hs + h_pj);
+  PJ.a = p.phi[0].a;
+  PJ.t_geo_end = p.phi[0].t_geo_end;
+  PJ.n_int = p.phi[0].n_int;
+  PJ.out = (double*)(D + o_tab);
+  PJ.outf = nullptr;
+  EZ_CUDA(cudaMemcpyAsync(D, Hs, hl.off, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemsetAsync(D + o_st, 0, sizeof(int), stream));
+  if (!y_dev) EZ_CUDA(cudaMemcpyAsync(D + o_y, y, sizeof(double) * m * d, cudaMemcpyHostToDevice, stream));
+  enum_recip_kernel<<<1, 512, 0, stream>>>((ReqDesc*)(D + o_req), (const RecipJob*)(D + o_rj));
+  EZ_LAUNCHED();
+  gbox_kernel<<<dim3((unsigned)((p.cells + 255) / 256), 1), 256, 0, stream>>>((const ReqDesc*)(D + o_req),
+                                                                              (const GboxJob*)(D + o_gj), 1);
+  EZ_LAUNCHED();
+  phitab_kernel<<<dim3(p.phi[0].n_int, 1), kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
+  EZ_LAUNCHED();
+  EpsteinArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.d = d;
+  A.m = (int)m;
+  A.nu = nu;
+  A.pref = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
+  A.vol_fac = std::pow(p.lam, d) / L->V;
+  A.c_lam = kPi * p.lam * p.lam;
+  A.lam = p.lam;
+  A.R2_recip = p.r_recip * p.r_recip;
+  A.two_over_nu = 2.0 / nu;
+  std::memcpy(A.A, L->A, sizeof A.A);
+  std::memcpy(A.AiT, L->AiT, sizeof A.AiT);
+  std::memcpy(A.At, L->At, sizeof A.At);
+  for (int i = 0; i < d; ++i) {
+    A.x[i] = x[i];
+    A.xt[i] = xt[i];
+    A.mx[i] = mx[i];
+  }
+  A.x_in_lattice = x_in ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    A.M[i] = p.M[i];
+    A.box[i] = p.box[i];
+  }
+  A.gbox = (const double*)(D + o_gbox);
+  A.rq = (const ReqDesc*)(D + o_req);
+  A.phi = p.phi[0];
+  A.phi.tab = (const double*)(D + o_tab);
+  A.y = y_dev ? y : (const double*)(D + o_y);
+  A.re = re_dev ? re : (double*)(D + o_re);
+  A.im = im ? (im_dev ? im : (double*)(D + o_im)) : nullptr;
+  A.status = (int*)(D + o_st);
+  epstein_kernel<<<(unsigned)((m + 127) / 128), 128, 0, stream>>>(A);
+  EZ_LAUNCHED();
+  if (!re_dev) EZ_CUDA(cudaMemcpyAsync(re, D + o_re, sizeof(double) * m, cudaMemcpyDeviceToHost, stream));
+  if (im && !im_dev) EZ_CUDA(cudaMemcpyAsync(im, D + o_im, sizeof(double) * m, cudaMemcpyDeviceToHost, stream));
+  int status = 0;
+  EZ_CUDA(cudaMemcpyAsync(&status, D + o_st, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EZ_CUDA(cudaStreamSynchronize(stream));
+  if (status) return fail(EZ_EDOMAIN, "some y lie in the reciprocal lattice with nu <= d (pole)");
+  return EZ_OK;
+}

@@ -1,0 +1,94 @@
+// Internal definitions of the GB300 Epstein zeta library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/ezeta.h"
+
+namespace ez {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------------------
+// Tables of Phi_a(t) = t^{-a} Gamma(a,t) for the reciprocal-space hot loop.
+// t in [kT0, t_hi]: piecewise polynomials of degree kNC-1 in x = (t - t_mid)/h on
+//   kNGeo geometric intervals [kT0 r^i, kT0 r^{i+1}] (r = kGeoR), then unit-width
+//   intervals up to t_hi.  Each record: t_mid, 1/h, b_0 .. b_{kNC-1} (monomials in x).
+// t < kT0: series of the entire part plus the singular term.
+// t > t_hi: asymptotic expansion e^{-t}/t (1 + (a-1)/t + (a-1)(a-2)/t^2 + ...).
+// ---------------------------------------------------------------------------
+constexpr int kNC = 16;
+constexpr int kRec = kNC + 2;
+constexpr int kNGeo = 5;
+constexpr double kT0 = 0.5;
+constexpr double kGeoR = 1.4;
+constexpr int kNSer = 22;
+constexpr int kMaxInt = 320;  // intervals per table (t_hi <= ~316)
+
+// reciprocal-space record: (G_0, G_1, G_2, |G|^2) with G = A^{-T} h
+struct alignas(32) G4 {
+  double x, y, z, w;
+};
+
+struct PhiInfo {
+  double a;           // order
+  int log_m;          // a = -log_m (log case) or -1
+  int two_a;          // 2a (integer)
+  double gam;         // Gamma(a) (non-log) or (-1)^m/m! (log)
+  double t_geo_end;   // kT0 * kGeoR^kNGeo
+  double t_hi;        // end of the tabulated range
+  int n_int;          // number of intervals
+  const double* tab;  // n_int * kRec doubles (device)
+  const float* tabf;  // float copy for the mixed form (device)
+  double ser[kNSer];  // entire part for t < kT0
+};
+
+// ---------------------------------------------------------------------------
+// One lattice sum as seen by the kernels (device resident).
+// ---------------------------------------------------------------------------
+constexpr int kMaxD = 3;
+constexpr int kMaxFactor = 64;
+constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
+constexpr int kVChunk = 16;      // v2 rows per block for d = 3
+
+struct ReqDesc {
+  int d, nsect, n_ui, n_v, u_rule, n_distinct, n_prod, ell, prec;
+  int expo[EZ_MAX_PROD][EZ_MAX_NU];
+  double A[9], AiT[9];
+  double V, lam, c_lam, vol_fac, R2_recip, eps;
+  double nu[EZ_MAX_NU], pref[EZ_MAX_NU];
+  double sig[EZ_MAX_NU];  // singular coefficient sigma_nu of s_hat
+  int islog[EZ_MAX_NU];
+  // real space: full box prod_i (2 M_i + 1), g = 0 outside the ball and at m = 0
+  int M[3], box[3];
+  const double* gbox;  // [n_distinct][box0][box1][box2]
+  const float* gboxf;
+  // reciprocal space: all h with |A^{-T} h| <= r_recip + max_BZ |k|
+  int n_rec;
+  const G4* rec;  // (G_0, G_1, G_2, |G|^2)
+  PhiInfo phi[EZ_MAX_NU];
+  // quadrature
+  const double* u_nodes;
+  const double* u_w;
+  const double* v_nodes;
+  const double* v_w;
+  // near part
+  int n_alpha;            // multi-indices with |alpha| even <= 2 ell
+  const int* alpha;       // [n_alpha][3]
+  const int* alpha_off;   // start of |alpha| = 2k blocks, k = 0..ell+1
+  const double* taylor;   // [n_distinct][n_alpha] : d^alpha Z^reg(0) / alpha!
+  // output slices
+  int far_item0, n_far_items, near_item0, n_near_items;
+  int line0;  // first line (far lines then near lines)
+};
+
+// Work item of a far-field or near-field launch.
+struct Item {
+  int req, sector, iu, chunk;
+  long long seg;  // first output segment of this item
+  __host__ __device__ long long chunk_seg() const { return seg; }
+};
+
+}  // namespace ez

@@ -1,0 +1,77 @@
+// Kernel entry points and setup job records of the Epstein zeta library.
+#pragma once
+
+#include "ez_internal.h"
+
+namespace ez {
+
+struct RecipJob {
+  int req;
+  int lo[3], ext[3];
+  double R2;
+  int cap;
+  G4* out;
+};
+
+struct GboxJob {
+  int req;
+  double x[3];  // centre (0 for the n-body path)
+  int mx[3];    // integer offset of the box centre (round(A^{-1} x))
+  int x_in_lattice;
+  double R2;
+  double* out;
+  float* outf;
+};
+
+struct PhiJob {
+  double a;
+  double t_geo_end;
+  int n_int;
+  double* out;
+  float* outf;
+};
+
+struct TaylorJob {
+  int req, nu_index;
+  double* phiG;   // [n_rec_cap][2 ell + 1]
+  double rser[16];  // entire series of the regularised h = 0 term (lambda piece included)
+  double* out;    // [n_alpha]
+};
+
+struct EpsteinArgs {
+  int d, m;
+  double nu, pref, vol_fac, c_lam, lam, R2_recip, two_over_nu;
+  double A[9], AiT[9], At[9];
+  double x[3], xt[3];  // x and A^{-1} x
+  int x_in_lattice;
+  int M[3], box[3], mx[3];
+  const double* gbox;
+  int n_rec_cap;
+  const ReqDesc* rq;  // for n_rec and the reciprocal list
+  PhiInfo phi;
+  const double* y;
+  double* re;
+  double* im;
+  int* status;
+};
+
+__global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs);
+__global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs);
+__global__ void phitab_kernel(const PhiJob* jobs);
+__global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
+__global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
+
+__global__ void far_kernel_d1(const ReqDesc* reqs, const Item* items, double* seg);
+__global__ void far_kernel_d2(const ReqDesc* reqs, const Item* items, double* seg);
+__global__ void far_kernel_d3(const ReqDesc* reqs, const Item* items, double* seg);
+__global__ void near_kernel(const ReqDesc* reqs, const Item* items, double* seg);
+__global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
+                             const int* line_nseg, int n_lines, const double* seg, double* lines);
+__global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines,
+                             int n_req, const double* lines, double* out);
+__global__ void epstein_kernel(EpsteinArgs args);
+
+size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v);
+cudaError_t upload_cheb2mono(const double* host_matrix);  // kNC x kNC
+
+}  // namespace ez

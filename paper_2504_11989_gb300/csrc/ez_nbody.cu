@@ -1,0 +1,508 @@
+// Far-field, near-field and reduction kernels of the n-body lattice sums
+// (Thm "Epstein representation", Cor. "Duffy transformation", Sec. 3).
+//
+// Far field: a block owns one Duffy line (sector s, u node) -- for d = 3 one
+// chunk of kVChunk v2 rows of it.  On a line k~ = u sigma^j(p1 v1, p2 v2, 1), so
+// the real-space sum of every node factorises over the axes:
+//   sum_m g(m) e^{2 pi i m.k~} = sum_{ma} Ea(ma, v1) B(ma, v2),
+//   B(ma, v2) = sum_{mb} Eb(mb, v2) H(ma, mb),  H(ma, mb) = sum_{mc} g(m) e^{2 pi i mc u},
+// H and B are built once per block in shared memory; g(-m) = g(m) folds ma < 0.
+// The reciprocal sum runs per node over the compacted list of A^{-T} h.
+#include <cstdio>
+
+#include "ez_kernels.h"
+#include "ez_phi.cuh"
+
+namespace ez {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+template <int NT>
+__device__ __forceinline__ void block_reduce_store(double (&v)[EZ_MAX_PROD], int np, double scale,
+                                                   double* out) {
+  __shared__ double red[NT / 32][EZ_MAX_PROD];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    double x = v[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[wid][p] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < EZ_MAX_PROD) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+    if (threadIdx.x < np) out[threadIdx.x] = scale * s;
+  }
+}
+
+__device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd) {
+  const int words = (int)(sizeof(PhiInfo) / sizeof(double));
+  const double* src = reinterpret_cast<const double*>(R->phi);
+  double* dst = reinterpret_cast<double*>(sphi);
+  for (int i = threadIdx.x; i < nd * words; i += blockDim.x) dst[i] = src[i];
+}
+
+// reciprocal sum at k (x = 0): acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over |G + k| <= R
+template <int D>
+__device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
+                                          double* acc) {
+  const int nrec = R->n_rec;
+  const double R2 = R->R2_recip, c = R->c_lam;
+  const G4* rec = R->rec;
+  for (int h = 0; h < nrec; ++h) {
+    const G4 G = ldg_g4(rec + h);
+    double qq;
+    if (D == 1) {
+      double q0 = G.x + k[0];
+      qq = q0 * q0;
+    } else if (D == 2) {
+      double q0 = G.x + k[0], q1 = G.y + k[1];
+      qq = fma(q0, q0, q1 * q1);
+    } else {
+      double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
+      qq = fma(q0, q0, fma(q1, q1, q2 * q2));
+    }
+    if (qq <= R2) {
+      const double t = c * qq;
+#pragma unroll
+      for (int j = 0; j < EZ_MAX_NU; ++j)
+        if (j < nd) acc[j] += phi_eval(sphi[j], t);
+    }
+  }
+}
+
+__device__ __forceinline__ void products(const ReqDesc* R, int nd, int np, const double* Z, double w,
+                                         double (&acc)[EZ_MAX_PROD]) {
+#pragma unroll
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    if (p >= np) break;
+    double f = 1.0;
+    for (int j = 0; j < nd; ++j) {
+      const int e = R->expo[p][j];
+      for (int q = 0; q < e; ++q) f *= Z[j];
+    }
+    acc[p] = fma(w, f, acc[p]);
+  }
+}
+
+size_t far_smem_bytes(int d, int nd, const int* M, int n_v) {
+  int Mx = 0;
+  for (int i = 0; i < d; ++i) Mx = M[i] > Mx ? M[i] : Mx;
+  size_t n = 0;
+  if (d == 3)
+    n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * kVChunk + (Mx + 1) + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
+        (size_t)nd * (Mx + 1) * kVChunk;
+  else if (d == 2)
+    n = (size_t)(Mx + 1) + (size_t)nd * (Mx + 1);
+  return n * sizeof(double2);
+}
+
+// ------------------------------------------------------------------------- d = 3
+__global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__ reqs,
+                                                       const Item* __restrict__ items, double* __restrict__ seg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  const Item it = items[blockIdx.x];
+  const ReqDesc* R = reqs + it.req;
+  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
+  load_phi(sphi, R, nd);
+
+  const int j = it.sector >> 2, pb = it.sector & 3;
+  const double p1 = (pb & 1) ? -1.0 : 1.0, p2 = (pb & 2) ? -1.0 : 1.0;
+  const int ax_a = j, ax_b = (j + 1) % 3, ax_c = (j + 2) % 3;
+  const double u = R->u_nodes[it.iu];
+  const double wblk = 2.0 * R->u_w[it.iu] * u * u;
+  const int Ma = R->M[ax_a], Mb = R->M[ax_b], Mc = R->M[ax_c];
+  const int v2_0 = it.chunk * kVChunk, nv2 = min(kVChunk, nv - v2_0);
+  const int st[3] = {R->box[1] * R->box[2], R->box[2], 1};
+  const int sta = st[ax_a], stb = st[ax_b], stc = st[ax_c];
+  const int gbase = R->M[0] * st[0] + R->M[1] * st[1] + R->M[2] * st[2];
+  const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
+
+  double2* Ea = reinterpret_cast<double2*>(smem_raw);
+  double2* Eb = Ea + (Ma + 1) * nv;
+  double2* Ec = Eb + (Mb + 1) * kVChunk;
+  double2* H = Ec + (Mc + 1);
+  double2* B = H + nd * (Ma + 1) * (2 * Mb + 1);
+
+  for (int v1 = threadIdx.x; v1 < nv; v1 += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (u * (p1 * R->v_nodes[v1])), &sn, &cs);
+    const double2 e1 = make_double2(cs, sn);
+    double2 e = make_double2(1.0, 0.0);
+    Ea[v1] = e;
+    for (int ma = 1; ma <= Ma; ++ma) {
+      e = cmul(e, e1);
+      Ea[ma * nv + v1] = e;
+    }
+  }
+  for (int v2l = threadIdx.x; v2l < nv2; v2l += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (u * (p2 * R->v_nodes[v2_0 + v2l])), &sn, &cs);
+    const double2 e1 = make_double2(cs, sn);
+    double2 e = make_double2(1.0, 0.0);
+    Eb[v2l] = e;
+    for (int mb = 1; mb <= Mb; ++mb) {
+      e = cmul(e, e1);
+      Eb[mb * kVChunk + v2l] = e;
+    }
+  }
+  if (threadIdx.x <= Mc) {
+    double sn, cs;
+    sincospi(2.0 * ((double)threadIdx.x * u), &sn, &cs);
+    Ec[threadIdx.x] = make_double2(cs, sn);
+  }
+  __syncthreads();
+
+  const int nH = (Ma + 1) * (2 * Mb + 1);
+  for (int e = threadIdx.x; e < nd * nH; e += blockDim.x) {
+    const int jn = e / nH, r = e - jn * nH;
+    const int ma = r / (2 * Mb + 1), mb = r - ma * (2 * Mb + 1) - Mb;
+    const double* g = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
+    double hr = g[0], hi = 0.0;
+    for (int mc = 1; mc <= Mc; ++mc) {
+      const double gp = g[mc * stc], gm = g[-mc * stc];
+      hr = fma(gp + gm, Ec[mc].x, hr);
+      hi = fma(gp - gm, Ec[mc].y, hi);
+    }
+    H[e] = make_double2(hr, hi);
+  }
+  __syncthreads();
+
+  const int nB = (Ma + 1) * nv2;
+  for (int e = threadIdx.x; e < nd * nB; e += blockDim.x) {
+    const int jn = e / nB, r = e - jn * nB;
+    const int ma = r / nv2, v2l = r - ma * nv2;
+    const double2* h = H + (jn * (Ma + 1) + ma) * (2 * Mb + 1) + Mb;
+    double br = h[0].x, bi = h[0].y;
+    for (int mb = 1; mb <= Mb; ++mb) {
+      const double2 E = Eb[mb * kVChunk + v2l];
+      const double2 hp = h[mb], hm = h[-mb];
+      br = fma(hp.x + hm.x, E.x, fma(hm.y - hp.y, E.y, br));
+      bi = fma(hp.y + hm.y, E.x, fma(hp.x - hm.x, E.y, bi));
+    }
+    B[(jn * (Ma + 1) + ma) * kVChunk + v2l] = make_double2(br, bi);
+  }
+  __syncthreads();
+
+  double kca[3], kcb[3], kcc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    kca[i] = R->AiT[i * 3 + ax_a];
+    kcb[i] = R->AiT[i * 3 + ax_b];
+    kcc[i] = R->AiT[i * 3 + ax_c];
+  }
+  double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  const int nn = nv * nv2;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+    const int v2l = n / nv, v1 = n - v2l * nv;
+    const double kta = u * (p1 * R->v_nodes[v1]);
+    const double ktb = u * (p2 * R->v_nodes[v2_0 + v2l]);
+    const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
+    double k[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) k[i] = fma(kca[i], kta, fma(kcb[i], ktb, kcc[i] * u));
+    double Z[EZ_MAX_NU], acc[EZ_MAX_NU];
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn) {
+      acc[jn] = 0.0;
+      if (jn < nd) {
+        const double2* b = B + jn * (Ma + 1) * kVChunk + v2l;
+        double sr = 0.0;
+        for (int ma = 1; ma <= Ma; ++ma) {
+          const double2 E = Ea[ma * nv + v1];
+          const double2 bb = b[ma * kVChunk];
+          sr = fma(E.x, bb.x, fma(-E.y, bb.y, sr));
+        }
+        Z[jn] = fma(2.0, sr, b[0].x);
+      }
+    }
+    recip_sum<3>(R, sphi, nd, k, acc);
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+    products(R, nd, np, Z, wv, wsum);
+  }
+  block_reduce_store<256>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
+}
+
+// ------------------------------------------------------------------------- d = 2
+__global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__ reqs,
+                                                       const Item* __restrict__ items, double* __restrict__ seg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  const Item it = items[blockIdx.x];
+  const ReqDesc* R = reqs + it.req;
+  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
+  load_phi(sphi, R, nd);
+  const int j = it.sector >> 1;
+  const double p1 = (it.sector & 1) ? -1.0 : 1.0;
+  const int ax_a = j, ax_c = 1 - j;
+  const double u = R->u_nodes[it.iu];
+  const double wblk = 2.0 * R->u_w[it.iu] * u;
+  const int Ma = R->M[ax_a], Mc = R->M[ax_c];
+  const int st[2] = {R->box[1], 1};
+  const int sta = st[ax_a], stc = st[ax_c];
+  const int gbase = R->M[0] * st[0] + R->M[1] * st[1];
+  const long long cells = (long long)R->box[0] * R->box[1];
+  double2* Ec = reinterpret_cast<double2*>(smem_raw);
+  double2* H = Ec + (Mc + 1);
+  if (threadIdx.x <= Mc) {
+    double sn, cs;
+    sincospi(2.0 * ((double)threadIdx.x * u), &sn, &cs);
+    Ec[threadIdx.x] = make_double2(cs, sn);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nd * (Ma + 1); e += blockDim.x) {
+    const int jn = e / (Ma + 1), ma = e - jn * (Ma + 1);
+    const double* g = R->gbox + (size_t)jn * cells + gbase + ma * sta;
+    double hr = g[0], hi = 0.0;
+    for (int mc = 1; mc <= Mc; ++mc) {
+      const double gp = g[mc * stc], gm = g[-mc * stc];
+      hr = fma(gp + gm, Ec[mc].x, hr);
+      hi = fma(gp - gm, Ec[mc].y, hi);
+    }
+    H[e] = make_double2(hr, hi);
+  }
+  __syncthreads();
+  const double kca0 = R->AiT[0 * 2 + ax_a], kca1 = R->AiT[1 * 2 + ax_a];
+  const double kcc0 = R->AiT[0 * 2 + ax_c], kcc1 = R->AiT[1 * 2 + ax_c];
+  double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const double kta = u * (p1 * R->v_nodes[v]);
+    const double wv = R->v_w[v];
+    double k[2] = {fma(kca0, kta, kcc0 * u), fma(kca1, kta, kcc1 * u)};
+    double sn, cs;
+    sincospi(2.0 * kta, &sn, &cs);
+    const double2 e1 = make_double2(cs, sn);
+    double sr[EZ_MAX_NU], Z[EZ_MAX_NU], acc[EZ_MAX_NU];
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
+    double2 e = make_double2(1.0, 0.0);
+    for (int ma = 1; ma <= Ma; ++ma) {
+      e = cmul(e, e1);
+#pragma unroll
+      for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+        if (jn < nd) {
+          const double2 hh = H[jn * (Ma + 1) + ma];
+          sr[jn] = fma(e.x, hh.x, fma(-e.y, hh.y, sr[jn]));
+        }
+    }
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
+    recip_sum<2>(R, sphi, nd, k, acc);
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+    products(R, nd, np, Z, wv, wsum);
+  }
+  block_reduce_store<128>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
+}
+
+// ------------------------------------------------------------------------- d = 1
+__global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__ reqs,
+                                                       const Item* __restrict__ items, double* __restrict__ seg) {
+  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  const Item it = items[blockIdx.x];
+  const ReqDesc* R = reqs + it.req;
+  const int nd = R->n_distinct, np = R->n_prod;
+  load_phi(sphi, R, nd);
+  __syncthreads();
+  const int iu = it.iu + threadIdx.x;
+  if (iu >= R->n_ui) return;
+  const double u = R->u_nodes[iu];
+  const double w = 2.0 * R->u_w[iu];
+  const int M = R->M[0];
+  double k[1] = {R->AiT[0] * u};
+  double sn, cs;
+  sincospi(2.0 * u, &sn, &cs);
+  const double2 e1 = make_double2(cs, sn);
+  double2 e = make_double2(1.0, 0.0);
+  double sr[EZ_MAX_NU], acc[EZ_MAX_NU], Z[EZ_MAX_NU];
+#pragma unroll
+  for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
+  for (int m = 1; m <= M; ++m) {
+    e = cmul(e, e1);
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], e.x, sr[jn]);
+  }
+  recip_sum<1>(R, sphi, nd, k, acc);
+#pragma unroll
+  for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+    if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+  double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  products(R, nd, np, Z, w, f);
+  double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;
+  for (int p = 0; p < np; ++p) o[p] = f[p];
+}
+
+
+// ------------------------------------------------------------------------- near part
+// One thread per ray (sector, v): C_{k,nu}(w) = sum_{|alpha| = 2k} D_nu[alpha] w^alpha, then
+// every product expanded over how many of each factor's singular parts s_hat/V enter,
+// integrated on (0, eps) in closed form (Hadamard finite part):
+//   I_m(mu) = eps^mu J_m,  J_0 = 1/mu,  J_m = L^m/mu - (2m/mu) J_{m-1},  L = log(pi eps^2 |w|^2).
+__device__ double ipow(double x, int e) {
+  double r = 1.0, b = x;
+  int k = e < 0 ? -e : e;
+  while (k) {
+    if (k & 1) r *= b;
+    b *= b;
+    k >>= 1;
+  }
+  return e < 0 ? 1.0 / r : r;
+}
+
+__device__ double near_product(const ReqDesc* R, int p, const double (*C)[9], double wn, double w2, double L) {
+  const int nd = R->n_distinct, d = R->d, ell = R->ell;
+  int e[EZ_MAX_NU], t[EZ_MAX_NU];
+  for (int j = 0; j < nd; ++j) {
+    e[j] = R->expo[p][j];
+    t[j] = 0;
+  }
+  double total = 0.0;
+  double G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
+  const double eps2 = R->eps * R->eps;
+  while (true) {
+    double mult = 1.0, coef = 1.0;
+    int mu = d, mlog = 0;
+    for (int j = 0; j < nd; ++j) {
+      if (t[j]) {
+        double bj = 1.0;
+        for (int i = 1; i <= t[j]; ++i) bj = bj * (e[j] - t[j] + i) / i;
+        mult *= bj;
+        const int dn = (int)lrint(R->nu[j]) - d;
+        coef *= ipow(R->sig[j] * ipow(wn, dn) / R->V, t[j]);
+        mu += t[j] * dn;
+        mlog += t[j] * R->islog[j];
+      }
+    }
+    int deg = 0;
+    G[0] = 1.0;
+    for (int j = 0; j < nd; ++j)
+      for (int r = 0; r < e[j] - t[j]; ++r) {
+        const int nd2 = min(deg + ell, kNearMaxDeg);
+        for (int i = 0; i <= nd2; ++i) {
+          double s = 0.0;
+          for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = fma(G[q], C[j][i - q], s);
+          T[i] = s;
+        }
+        deg = nd2;
+        for (int i = 0; i <= deg; ++i) G[i] = T[i];
+      }
+    double epm = ipow(R->eps, mu);
+    double sumk = 0.0;
+    for (int k = 0; k <= deg; ++k) {
+      const double muk = (double)(mu + 2 * k);
+      double J = 1.0 / muk, Lp = 1.0;
+      for (int i = 1; i <= mlog; ++i) {
+        Lp *= L;
+        J = Lp / muk - (2.0 * i / muk) * J;
+      }
+      sumk = fma(G[k], epm * J, sumk);
+      epm *= eps2;
+    }
+    total = fma(mult * coef, sumk, total);
+    int j = 0;
+    for (; j < nd; ++j) {
+      if (t[j] < e[j]) {
+        t[j]++;
+        break;
+      }
+      t[j] = 0;
+    }
+    if (j == nd) break;
+  }
+  return total;
+}
+
+__global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
+                                                   double* __restrict__ seg) {
+  const Item it = items[blockIdx.x];
+  const ReqDesc* R = reqs + it.req;
+  const int d = R->d, nv = R->n_v, ell = R->ell, nd = R->n_distinct, np = R->n_prod;
+  const int nrays = d == 1 ? 1 : (d == 2 ? nv : nv * nv);
+  const int r = it.chunk * blockDim.x + threadIdx.x;
+  double val[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  if (r < nrays) {
+    double v[2] = {0.0, 0.0}, wv = 1.0;
+    if (d >= 2) {
+      v[0] = R->v_nodes[r % nv];
+      wv *= R->v_w[r % nv];
+    }
+    if (d == 3) {
+      v[1] = R->v_nodes[r / nv];
+      wv *= R->v_w[r / nv];
+    }
+    const int half = 1 << (d - 1);
+    const int j = it.sector / half, pb = it.sector % half;
+    double y[3], dir[3], w[3];
+    for (int i = 0; i < d - 1; ++i) y[i] = (((pb >> i) & 1) ? -1.0 : 1.0) * v[i];
+    y[d - 1] = 1.0;
+    for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
+    double w2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double s = 0.0;
+      for (int q = 0; q < d; ++q) s = fma(R->AiT[i * d + q], dir[q], s);
+      w[i] = s;
+      w2 = fma(s, s, w2);
+    }
+    for (int i = d; i < 3; ++i) w[i] = 0.0;
+    double C[EZ_MAX_NU][9];
+    for (int jn = 0; jn < nd; ++jn)
+      for (int kk = 0; kk <= ell; ++kk) {
+        double s = 0.0;
+        for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
+          const int* al = R->alpha + 3 * ia;
+          double mono = 1.0;
+          for (int i = 0; i < 3; ++i)
+            for (int q = 0; q < al[i]; ++q) mono *= w[i];
+          s = fma(R->taylor[(size_t)jn * R->n_alpha + ia], mono, s);
+        }
+        C[jn][kk] = s;
+      }
+    const double L = log(kPi * R->eps * R->eps * w2);
+    const double wn = sqrt(w2);
+    for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * near_product(R, p, C, wn, w2, L);
+  }
+  block_reduce_store<128>(val, np, 1.0, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
+}
+
+// ------------------------------------------------------------------------- reductions
+__global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
+                             const int* line_nseg, int n_lines, const double* seg, double* lines) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= n_lines) return;
+  const int np = reqs[line_req[L]].n_prod;
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    double s = 0.0;
+    if (p < np)
+      for (int q = 0; q < line_nseg[L]; ++q) s += seg[(size_t)(line_seg0[L] + q) * EZ_MAX_PROD + p];
+    lines[(size_t)L * EZ_MAX_PROD + p] = s;
+  }
+}
+
+// compensated (Neumaier) sum of a request's lines in order
+__global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines, int n_req,
+                             const double* lines, double* out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = g / EZ_MAX_PROD, p = g % EZ_MAX_PROD;
+  if (r >= n_req) return;
+  double s = 0.0, c = 0.0;
+  if (p < reqs[r].n_prod)
+    for (int q = 0; q < req_nlines[r]; ++q) {
+      const double x = lines[(size_t)(req_line0[r] + q) * EZ_MAX_PROD + p];
+      const double t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+  out[(size_t)r * EZ_MAX_PROD + p] = s + c;
+}
+
+}  // namespace ez

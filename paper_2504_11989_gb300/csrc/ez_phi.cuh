@@ -1,0 +1,171 @@
+// Device library for Phi_a(t) = t^{-a} Gamma(a, t) = int_1^inf s^{a-1} e^{-t s} ds,
+// a in Z/2: the upper incomplete gamma function of the splitting of Z (orders
+// a = nu/2 in real space and a = (d - nu)/2 in reciprocal space).
+//
+// Two paths:
+//  * phi_accurate(a, t): used only while building tables.  Closed form for
+//    integer a >= 1; for a <= 0 and t > 1 the even part of Legendre's continued
+//    fraction for Gamma(a, t) (DLMF 8.9.2) by the modified Lentz method; for
+//    t <= 1 the E_1 power series (A&S 5.1.11) or sqrt(pi/t) erfc(sqrt t),
+//    then the recurrence t Phi_{a+1} = a Phi_a + e^{-t}.
+//  * phi_eval(PhiInfo, t): the hot path.  Piecewise polynomial on [kT0, t_hi],
+//    entire-part series plus singular term below kT0, asymptotic series above.
+#pragma once
+
+#include <math_constants.h>
+
+#include <cmath>
+
+#include "ez_internal.h"
+
+namespace ez {
+
+__host__ __device__ inline double e1_series(double t) {
+  // E_1(t) = -gamma - log t - sum_{k>=1} (-t)^k / (k k!)
+  double sum = 0.0, term = 1.0;
+  for (int k = 1; k < 60; ++k) {
+    term *= -t / k;
+    double add = term / k;
+    sum += add;
+    if (fabs(add) < 1e-19 * fabs(sum)) break;
+  }
+  return -0.57721566490153286060651209 - log(t) - sum;
+}
+
+__host__ __device__ inline double phi_cf(double a, double t) {
+  // Phi_a(t) = e^{-t} / (t + 1 - a - 1(1-a)/(t + 3 - a - 2(2-a)/(t + 5 - a - ...)))
+  const double tiny = 1e-300;
+  double b = t + 1.0 - a;
+  double c = 1.0 / tiny;
+  double dd = 1.0 / b;
+  double h = dd;
+  for (int i = 1; i < 20000; ++i) {
+    double an = -(double)i * ((double)i - a);
+    b += 2.0;
+    dd = fma(an, dd, b);
+    if (fabs(dd) < tiny) dd = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    dd = 1.0 / dd;
+    double del = dd * c;
+    h *= del;
+    if (fabs(del - 1.0) < 2e-17) break;
+  }
+  return exp(-t) * h;
+}
+
+__host__ __device__ inline double phi_accurate(double a, double t) {
+  int two_a = (int)lrint(2.0 * a);
+  if (!(t > 0.0)) return a < 0.0 ? -1.0 / a : (double)INFINITY;
+  bool integer = (two_a & 1) == 0;
+  if (integer && a >= 1.0) {
+    int n = two_a / 2;
+    double s = 0.0, term = 1.0, fact = 1.0;
+    for (int k = 0; k < n; ++k) {
+      s += term;
+      term *= t / (k + 1);
+    }
+    for (int k = 2; k < n; ++k) fact *= k;  // (n-1)!
+    double tp = 1.0;
+    for (int k = 0; k < n; ++k) tp *= t;
+    return fact * exp(-t) * s / tp;
+  }
+  if (a <= 0.0 && t > 1.0) return phi_cf(a, t);
+  double et = exp(-t);
+  if (integer) {  // a <= 0, t <= 1: from Phi_0 = E_1 downward
+    double p = e1_series(t);
+    for (int c = 0; c > two_a / 2; --c) p = (t * p - et) / (double)(c - 1);
+    return p;
+  }
+  double p = sqrt(kPi / t) * erfc(sqrt(t));  // Phi_{1/2}
+  double cur = 0.5;
+  while (cur < a - 0.25) {
+    p = (cur * p + et) / t;
+    cur += 1.0;
+  }
+  while (cur > a + 0.25) {
+    p = (t * p - et) / (cur - 1.0);
+    cur -= 1.0;
+  }
+  return p;
+}
+
+// t^{-two_a/2} for t > 0 using sqrt and integer powers only.
+__device__ __forceinline__ double pow_half(double t, int two_a) {
+  int e = -two_a;  // power of sqrt(t)
+  double base = (e & 1) ? sqrt(t) : 1.0;
+  int k = e >> 1;  // floor(e/2)
+  double r = base;
+  double tt = t;
+  if (k < 0) {
+    tt = 1.0 / t;
+    k = -k;
+  }
+  while (k) {
+    if (k & 1) r *= tt;
+    tt *= tt;
+    k >>= 1;
+  }
+  return r;
+}
+
+// Interval index of t in a table (t >= kT0), computed in binary32.
+__device__ __forceinline__ int phi_interval(float tf, float t_geo_end_f) {
+  int i;
+  if (tf < t_geo_end_f) {
+    // log_{1.4}(t / kT0) = log2(2 t) / log2(1.4)
+    i = (int)(__log2f(2.0f * tf) * 2.06008f);
+    i = max(0, min(i, kNGeo - 1));
+  } else {
+    i = kNGeo + (int)(tf - t_geo_end_f);
+  }
+  return i;
+}
+
+__device__ __forceinline__ double phi_table(const PhiInfo& P, double t) {
+  int i = phi_interval((float)t, (float)P.t_geo_end);
+  i = min(i, P.n_int - 1);
+  const double* r = P.tab + (size_t)i * kRec;
+  double x = (t - __ldg(r)) * __ldg(r + 1);
+  double p = __ldg(r + 2 + kNC - 1);
+#pragma unroll
+  for (int k = kNC - 2; k >= 0; --k) p = fma(p, x, __ldg(r + 2 + k));
+  return p;
+}
+
+static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
+  double s = P.ser[kNSer - 1];
+#pragma unroll 4
+  for (int k = kNSer - 2; k >= 0; --k) s = fma(s, t, P.ser[k]);
+  if (t == 0.0) return P.log_m >= 0 ? (P.log_m == 0 ? CUDART_INF : s) : (P.a < 0.0 ? s : CUDART_INF);
+  if (P.log_m >= 0) {
+    double tm = 1.0;
+    for (int k = 0; k < P.log_m; ++k) tm *= t;
+    return s - P.gam * tm * log(t);
+  }
+  return s + P.gam * pow_half(t, P.two_a);
+}
+
+static __device__ __noinline__ double phi_large(const PhiInfo& P, double t) {
+  double inv = 1.0 / t;
+  double s = 1.0, term = 1.0;
+  for (int k = 1; k <= 8; ++k) {
+    term *= (P.a - k) * inv;
+    s += term;
+  }
+  return exp(-t) * inv * s;
+}
+
+__device__ __forceinline__ double phi_eval(const PhiInfo& P, double t) {
+  if (t < kT0) return phi_small(P, t);
+  if (t > P.t_hi) return phi_large(P, t);
+  return phi_table(P, t);
+}
+
+__device__ __forceinline__ G4 ldg_g4(const G4* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return G4{a.x, a.y, b.x, b.y};
+}
+
+}  // namespace ez

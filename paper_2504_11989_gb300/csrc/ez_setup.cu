@@ -1,0 +1,279 @@
+// Setup kernels: lattice-point tables, incomplete-gamma tables and Taylor
+// tensors of Z^reg at the origin.  All of them run once per lattice sum.
+#include "ez_kernels.h"
+#include "ez_phi.cuh"
+
+namespace ez {
+
+// ---------------------------------------------------------------------------
+// Reciprocal lattice points h with |A^{-T} h| <= R (box lo..hi), compacted in
+// lexicographic order by one block (ordered prefix sums), written as
+// (G_0, G_1, G_2, |G|^2).  The count goes to req->n_rec.
+// ---------------------------------------------------------------------------
+__global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
+  const RecipJob J = jobs[blockIdx.x];
+  ReqDesc* R = reqs + J.req;
+  const int d = R->d;
+  const long long total = (long long)J.ext[0] * J.ext[1] * J.ext[2];
+  __shared__ int warp_sums[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long long start = 0; start < total; start += blockDim.x) {
+    long long idx = start + threadIdx.x;
+    int keep = 0;
+    double G[3] = {0, 0, 0}, G2 = 0.0;
+    if (idx < total) {
+      int h[3];
+      long long r = idx;
+      h[2] = (int)(r % J.ext[2]) + J.lo[2];
+      r /= J.ext[2];
+      h[1] = (int)(r % J.ext[1]) + J.lo[1];
+      r /= J.ext[1];
+      h[0] = (int)r + J.lo[0];
+      for (int i = 0; i < d; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s = fma(R->AiT[i * d + k], (double)h[k], s);
+        G[i] = s;
+        G2 = fma(s, s, G2);
+      }
+      keep = G2 <= J.R2;
+    }
+    unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    int before = __popc(ballot & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[wid] = __popc(ballot);
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < wid; ++w) off += warp_sums[w];
+    if (keep) {
+      int pos = base + off + before;
+      if (pos < J.cap) J.out[pos] = G4{G[0], G[1], G[2], G2};
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < nw; ++w) tot += warp_sums[w];
+      base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) R->n_rec = min(base, J.cap);
+}
+
+// ---------------------------------------------------------------------------
+// Real-space box: g_nu(m) = Phi_{nu/2}(pi |A m - x|^2 / lam^2) for 0 < |A m - x| <= R,
+// zero elsewhere.  One thread per (box cell, distinct nu).
+// ---------------------------------------------------------------------------
+__global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs) {
+  int jid = blockIdx.y;
+  if (jid >= n_jobs) return;
+  const GboxJob J = jobs[jid];
+  const ReqDesc* R = reqs + J.req;
+  const int d = R->d;
+  const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= cells * R->n_distinct) return;
+  int jn = (int)(idx / cells);
+  long long c = idx % cells;
+  int m[3];
+  m[2] = (int)(c % R->box[2]) - R->M[2];
+  c /= R->box[2];
+  m[1] = (int)(c % R->box[1]) - R->M[1];
+  c /= R->box[1];
+  m[0] = (int)c - R->M[0];
+  double r2 = 0.0;
+  bool center = true;
+  for (int i = 0; i < d; ++i) {
+    double s = -J.x[i];
+    for (int k = 0; k < d; ++k) s = fma(R->A[i * d + k], (double)(m[k] + J.mx[k]), s);
+    r2 = fma(s, s, r2);
+    center &= (m[i] + J.mx[i]) == J.mx[i];
+  }
+  double g = 0.0;
+  bool excluded = J.x_in_lattice ? center : false;
+  if (!excluded && r2 <= J.R2 && r2 > 0.0) g = phi_accurate(0.5 * R->nu[jn], kPi * r2 / (R->lam * R->lam));
+  J.out[idx] = g;
+  if (J.outf) J.outf[idx] = (float)g;
+}
+
+// ---------------------------------------------------------------------------
+// Phi_a tables: one block of kNC threads per (request, distinct nu, interval).
+// Chebyshev interpolation at the kNC Chebyshev points of the interval, then
+// conversion to monomials in x in [-1, 1] (matrix in constant memory).
+// ---------------------------------------------------------------------------
+__constant__ double c_cheb2mono[kNC * kNC];  // [j][i]: coefficient of x^i in T_j(x)
+
+cudaError_t upload_cheb2mono(const double* m) { return cudaMemcpyToSymbol(c_cheb2mono, m, sizeof(double) * kNC * kNC); }
+
+__global__ void phitab_kernel(const PhiJob* jobs) {
+  const PhiJob J = jobs[blockIdx.y];
+  const int iv = blockIdx.x;
+  if (iv >= J.n_int) return;
+  double lo, hi;
+  if (iv < kNGeo) {
+    lo = kT0 * pow(kGeoR, (double)iv);
+    hi = lo * kGeoR;
+  } else {
+    lo = J.t_geo_end + (iv - kNGeo);
+    hi = lo + 1.0;
+  }
+  const double tm = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+  __shared__ double f[kNC], cj[kNC];
+  const int k = threadIdx.x;
+  const double xk = cospi((k + 0.5) / kNC);
+  f[k] = phi_accurate(J.a, tm + h * xk);
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < kNC; ++q) s += f[q] * cospi((double)k * (q + 0.5) / kNC);
+  cj[k] = (k == 0 ? 1.0 : 2.0) * s / kNC;
+  __syncthreads();
+  double b = 0.0;
+  for (int j = k; j < kNC; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
+  double* r = J.out + (size_t)iv * kRec;
+  r[2 + k] = b;
+  if (J.outf) J.outf[(size_t)iv * kRec + 2 + k] = (float)b;
+  if (k == 0) {
+    r[0] = tm;
+    r[1] = 1.0 / h;
+    if (J.outf) {
+      J.outf[(size_t)iv * kRec] = (float)tm;
+      J.outf[(size_t)iv * kRec + 1] = (float)(1.0 / h);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Taylor tensors of Z^reg_nu at k = 0:  D[alpha] = d^alpha Z^reg(0) / alpha!, |alpha|
+// even <= 2 ell.  One thread per (request, distinct nu, alpha); serial sums in a
+// fixed order (deterministic).  Terms (P_nu, c = pi lam^2):
+//   real space   P_nu sum_m g(m) (-1)^K (2 pi)^{2K} z^alpha / alpha!,    2K = |alpha|
+//   h != 0       P_nu lam^d/V sum_n (-1)^n Phi_{a+n}(c|G|^2) c^n / n! [k^alpha](2 G.k + |k|^2)^n
+//   h = 0        P_nu lam^d/V r_K c^K K!/prod (alpha_i/2)!  (alpha all even)
+//   constant     -P_nu 2/nu at alpha = 0.
+// ---------------------------------------------------------------------------
+__device__ double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+__device__ double factd(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+__global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs) {
+  int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  // jobs are (request, nu) pairs; each owns n_alpha consecutive threads
+  int acc = 0, jid = -1;
+  for (int q = 0; q < n_jobs; ++q) {
+    int na = reqs[jobs[q].req].n_alpha;
+    if (gid < acc + na) {
+      jid = q;
+      break;
+    }
+    acc += na;
+  }
+  if (jid < 0) return;
+  const TaylorJob J = jobs[jid];
+  const ReqDesc* R = reqs + J.req;
+  const int ia = gid - acc;
+  const int d = R->d, jn = J.nu_index;
+  const int* al = R->alpha + 3 * ia;
+  int alpha[3] = {al[0], al[1], al[2]};
+  int K2 = alpha[0] + alpha[1] + alpha[2];
+  int K = K2 / 2;
+  double afact = factd(alpha[0]) * factd(alpha[1]) * factd(alpha[2]);
+  const double nu = R->nu[jn];
+  const double c = R->c_lam;
+  // real space
+  double sreal = 0.0;
+  const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
+  const double* g = R->gbox + (size_t)jn * cells;
+  for (long long idx = 0; idx < cells; ++idx) {
+    double gv = g[idx];
+    if (gv == 0.0) continue;
+    long long cc = idx;
+    int m[3];
+    m[2] = (int)(cc % R->box[2]) - R->M[2];
+    cc /= R->box[2];
+    m[1] = (int)(cc % R->box[1]) - R->M[1];
+    cc /= R->box[1];
+    m[0] = (int)cc - R->M[0];
+    double mono = 1.0;
+    for (int i = 0; i < d; ++i) {
+      double zi = 0.0;
+      for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
+      for (int e = 0; e < alpha[i]; ++e) mono *= zi;
+    }
+    sreal = fma(gv, mono, sreal);
+  }
+  double twopi_pow = 1.0;
+  for (int e = 0; e < K2; ++e) twopi_pow *= 2.0 * kPi;
+  sreal *= ((K & 1) ? -1.0 : 1.0) * twopi_pow / afact;
+  // reciprocal, h != 0
+  double srec = 0.0;
+  const double* phis = J.phiG;  // [n_rec][2 ell + 1]
+  const int stride = 2 * R->ell + 1;
+  for (int hi = 0; hi < R->n_rec; ++hi) {
+    const G4 G = R->rec[hi];
+    if (G.w == 0.0 || G.w > R->R2_recip) continue;
+    double Gv[3] = {G.x, G.y, G.z};
+    double term = 0.0;
+    for (int n = K; n <= K2; ++n) {
+      int jj = 2 * n - K2;  // number of linear factors
+      // coefficient of k^alpha in (2 G.k)^jj (|k|^2)^(n-jj)
+      double coef = 0.0;
+      int b[3];
+      for (b[0] = 0; b[0] <= alpha[0]; ++b[0])
+        for (b[1] = 0; b[1] <= alpha[1]; ++b[1]) {
+          b[2] = jj - b[0] - b[1];
+          if (b[2] < 0 || b[2] > alpha[2]) continue;
+          bool even = true;
+          for (int i = 0; i < 3; ++i) even &= ((alpha[i] - b[i]) & 1) == 0;
+          if (!even) continue;
+          double lin = factd(jj);
+          double quad = factd(n - jj);
+          for (int i = 0; i < 3; ++i) {
+            lin /= factd(b[i]);
+            for (int e = 0; e < b[i]; ++e) lin *= 2.0 * Gv[i];
+            quad /= factd((alpha[i] - b[i]) / 2);
+          }
+          coef += lin * quad;
+        }
+      if (coef == 0.0) continue;
+      double cn = 1.0;
+      for (int e = 0; e < n; ++e) cn *= c;
+      term += ((n & 1) ? -1.0 : 1.0) * phis[(size_t)hi * stride + n] * cn / factd(n) * binom(n, jj) * coef;
+    }
+    srec += term;
+  }
+  // h = 0: regularised entire series
+  bool all_even = ((alpha[0] | alpha[1] | alpha[2]) & 1) == 0;
+  if (all_even && K <= R->ell) {
+    double cK = 1.0;
+    for (int e = 0; e < K; ++e) cK *= c;
+    srec += J.rser[K] * cK * factd(K) / (factd(alpha[0] / 2) * factd(alpha[1] / 2) * factd(alpha[2] / 2));
+  }
+  double v = sreal + R->vol_fac * srec;
+  if (K2 == 0) v -= 2.0 / nu;
+  J.out[ia] = R->pref[jn] * v;
+}
+
+// Phi_{a+n}(c |G_h|^2), n = 0..2 ell, for every reciprocal point (setup of the tensors).
+__global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs) {
+  int jid = blockIdx.y;
+  if (jid >= n_jobs) return;
+  const TaylorJob J = jobs[jid];
+  const ReqDesc* R = reqs + J.req;
+  int hi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (hi >= R->n_rec) return;
+  const double a = 0.5 * (R->d - R->nu[J.nu_index]);
+  const double t = R->c_lam * R->rec[hi].w;
+  const int stride = 2 * R->ell + 1;
+  for (int n = 0; n < stride; ++n) J.phiG[(size_t)hi * stride + n] = t > 0.0 ? phi_accurate(a + n, t) : 0.0;
+}
+
+}  // namespace ez

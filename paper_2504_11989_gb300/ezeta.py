@@ -1,0 +1,239 @@
+"""ctypes binding of the C ABI in include/ezeta.h (argument marshalling only).
+
+Every numerical step runs in libezeta.so; this module converts Python/numpy/torch
+arguments to pointers and sizes.  Loading fails loudly when the library has not
+been built (call :func:`paper_2504_11989_gb300.build.build`).
+
+Pointers: numpy arrays are passed as host pointers, torch CUDA tensors as device
+pointers; the library detects which.  ``stream`` is a ``torch.cuda.Stream``, a raw
+``cudaStream_t`` integer, or None (legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB
+
+EZ_OK, EZ_EINVAL, EZ_EDOMAIN, EZ_EUNSUPPORTED, EZ_ENOMEM, EZ_ECUDA, EZ_ETIMEOUT, EZ_EBUSY = range(8)
+EZ_FP64, EZ_MIXED = 0, 1
+EZ_MAX_NU, EZ_MAX_PROD = 8, 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ezeta error {code}: {msg}")
+        self.code = code
+
+
+class ez_quadrature(ctypes.Structure):
+    _fields_ = [
+        ("n_u", ctypes.c_int),
+        ("n_v", ctypes.c_int),
+        ("u_rule", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("ell", ctypes.c_int),
+        ("lam", ctypes.c_double),
+        ("r_real", ctypes.c_double),
+        ("r_recip", ctypes.c_double),
+        ("prec", ctypes.c_int),
+        ("dedupe", ctypes.c_int),
+    ]
+
+
+class ez_sum_spec(ctypes.Structure):
+    _fields_ = [
+        ("n_distinct", ctypes.c_int),
+        ("nu", ctypes.c_double * EZ_MAX_NU),
+        ("n_prod", ctypes.c_int),
+        ("expo", (ctypes.c_int * EZ_MAX_NU) * EZ_MAX_PROD),
+    ]
+
+
+def lib():
+    """The loaded libezeta.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"libezeta.so not built at {LIB}; run paper_2504_11989_gb300.build.build()")
+            L = ctypes.CDLL(LIB)
+            vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+            L.ez_last_error.restype = ctypes.c_char_p
+            L.ez_launch_count.restype = ctypes.c_longlong
+            L.ez_launch_count.argtypes = [ctypes.c_int]
+            L.ez_lattice_create.argtypes = [ctypes.c_int, dp, ctypes.POINTER(vp)]
+            L.ez_lattice_destroy.argtypes = [vp]
+            L.ez_quadrature_default.argtypes = [ctypes.POINTER(ez_quadrature)]
+            L.ez_epstein_zeta.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, ctypes.c_int, vp]
+            L.ez_lattice_sum_nbody.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ez_quadrature), vp, vp]
+            L.ez_atm_energy.argtypes = [vp, ctypes.POINTER(ez_quadrature), dp, dp, vp]
+            L.ez_lattice_sums.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
+                                          ctypes.POINTER(ez_quadrature), vp, vp,
+                                          ctypes.POINTER(ctypes.c_longlong), vp]
+            L.ez_layout.argtypes = [ctypes.c_int, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != EZ_OK:
+        raise EzError(rc, lib().ez_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array or torch tensor (any device)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.float64:
+            raise ValueError("numpy arguments must be C-contiguous float64")
+        return ctypes.c_void_p(a.ctypes.data), a
+    # torch.Tensor
+    if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+        raise ValueError("tensor arguments must be contiguous float64")
+    return ctypes.c_void_p(a.data_ptr()), a
+
+
+def ez_launch_count(reset: bool = False) -> int:
+    return int(lib().ez_launch_count(1 if reset else 0))
+
+
+def quadrature(q=None, **kw) -> ez_quadrature:
+    """Build an ez_quadrature from a workloads.Quad (or keyword overrides)."""
+    Q = ez_quadrature()
+    lib().ez_quadrature_default(ctypes.byref(Q))
+    if q is not None:
+        Q.n_u, Q.n_v, Q.u_rule = q.n_u, q.n_v, q.u_rule
+        Q.eps, Q.ell, Q.lam, Q.r_real, Q.r_recip = q.eps, q.ell, q.lam, q.r_real, q.r_recip
+    for k, v in kw.items():
+        setattr(Q, k, v)
+    return Q
+
+
+def sum_spec(nu, expo) -> ez_sum_spec:
+    S = ez_sum_spec()
+    S.n_distinct = len(nu)
+    for j, v in enumerate(nu):
+        S.nu[j] = float(v)
+    S.n_prod = len(expo)
+    for p, row in enumerate(expo):
+        for j, e in enumerate(row):
+            S.expo[p][j] = int(e)
+    return S
+
+
+class Lattice:
+    """Owning wrapper of an ez_lattice handle (Def. "Lattices")."""
+
+    def __init__(self, A):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        self.d = A.shape[0]
+        self.A = A
+        h = ctypes.c_void_p()
+        _check(lib().ez_lattice_create(self.d, A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.ez_lattice_destroy(h)
+            self.handle = None
+
+
+def ez_epstein_zeta(lat: Lattice, nu: float, x, y, re=None, im=None, prec: int = EZ_FP64, stream=None):
+    """Z_{Lambda,nu}(x, y_i).  y: (m, d) numpy array or CUDA tensor.  Returns (re, im)
+    in the same kind of container as y (allocated if not given)."""
+    xv = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
+    if isinstance(y, np.ndarray):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        m = y.shape[0] if y.ndim > 1 else (y.size // lat.d)
+        if re is None:
+            re = np.zeros(m)
+        if im is None:
+            im = np.zeros(m)
+    else:
+        m = y.shape[0] if y.dim() > 1 else y.numel() // lat.d
+        if re is None:
+            re = y.new_zeros(m)
+        if im is None:
+            im = y.new_zeros(m)
+    yp, _ = _ptr(y)
+    rp, _ = _ptr(re)
+    ip, _ = _ptr(im)
+    _check(lib().ez_epstein_zeta(lat.handle, float(nu), xv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), yp,
+                                 int(m), rp, ip, int(prec), _stream_ptr(stream)))
+    return re, im
+
+
+def ez_lattice_sum_nbody(lat: Lattice, nu, q: ez_quadrature, out=None, stream=None) -> float:
+    nuv = np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    if out is None:
+        v = ctypes.c_double()
+        _check(lib().ez_lattice_sum_nbody(lat.handle, nuv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          int(nuv.size), ctypes.byref(q), ctypes.byref(v), _stream_ptr(stream)))
+        return v.value
+    op, _ = _ptr(out)
+    _check(lib().ez_lattice_sum_nbody(lat.handle, nuv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      int(nuv.size), ctypes.byref(q), op, _stream_ptr(stream)))
+    return out
+
+
+def ez_atm_energy(lat: Lattice, q: ez_quadrature, stream=None):
+    """(E, [zeta(3,3,3), zeta(-1,5,5), zeta(1,3,5)]) -- Prop. in Sec. 2."""
+    E = ctypes.c_double()
+    parts = (ctypes.c_double * 3)()
+    _check(lib().ez_atm_energy(lat.handle, ctypes.byref(q), ctypes.byref(E), parts, _stream_ptr(stream)))
+    return E.value, np.array(parts[:])
+
+
+def ez_lattice_sums(lats, specs, quads, out=None, lines: bool = False, stream=None):
+    """Batched sums.  Returns out[(n_req, EZ_MAX_PROD)] and, if lines, (lines array
+    [n_lines, EZ_MAX_PROD], offsets[n_req + 1])."""
+    n = len(lats)
+    harr = (ctypes.c_void_p * n)(*[l.handle for l in lats])
+    sarr = (ez_sum_spec * n)(*specs)
+    qarr = (ez_quadrature * n)(*quads)
+    if out is None:
+        out = np.zeros((n, EZ_MAX_PROD))
+    op, _ = _ptr(out)
+    offs = (ctypes.c_longlong * (n + 1))()
+    lp = None
+    lbuf = None
+    if lines:
+        # size from a first pass of the layout
+        total = 0
+        for l, s, q in zip(lats, specs, quads):
+            ns, nu_t, ur = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _check(lib().ez_layout(l.d, ctypes.byref(s), ctypes.byref(q), ctypes.byref(ns), ctypes.byref(nu_t),
+                                   ctypes.byref(ur)))
+            total += ns.value * nu_t.value + (ns.value if ur.value == 2 else 0)
+        lbuf = np.zeros((total, EZ_MAX_PROD))
+        lp = ctypes.c_void_p(lbuf.ctypes.data)
+    _check(lib().ez_lattice_sums(n, harr, sarr, qarr, op, lp, offs, _stream_ptr(stream)))
+    if lines:
+        return out, lbuf, np.array(offs[:])
+    return out
+
+
+def ez_layout(d: int, spec: ez_sum_spec, q: ez_quadrature):
+    ns, nu_t, ur = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().ez_layout(int(d), ctypes.byref(spec), ctypes.byref(q), ctypes.byref(ns), ctypes.byref(nu_t),
+                           ctypes.byref(ur)))
+    return ns.value, nu_t.value, ur.value

@@ -1,0 +1,91 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, exports every
+function declared in include/ezeta.h, and its host-side validation and layout
+logic behave as documented (no kernel is launched here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2504_11989_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ez():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2504_11989_gb300 import build, ezeta
+
+    build.build()
+    return ezeta
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ezeta.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*|long long)\s+(ez_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(ez):
+    names = declared_functions()
+    assert len(names) >= 10
+    L = ez.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_lattice_validation(ez):
+    with pytest.raises(ez.EzError) as e:
+        ez.Lattice([[1.0, 2.0], [0.5, 1.0]])
+    assert e.value.code == ez.EZ_EINVAL
+    h = ctypes.c_void_p()
+    A = (ctypes.c_double * 16)(*([1.0] * 16))
+    assert ez.lib().ez_lattice_create(4, A, ctypes.byref(h)) == ez.EZ_EINVAL
+    assert b"d = 4" in ez.lib().ez_last_error()
+    lat = ez.Lattice(W.lattice("fcc"))
+    assert lat.d == 3
+
+
+@pytest.mark.parametrize(
+    "d,nu,expo,quad,expect",
+    [
+        (1, [4.0], [[3]], W.config1(4096), (1, 4096, 1)),
+        (2, [3.0], [[3]], W.config2(256), (4, 128, 1)),
+        (3, [-1.0, 1.0, 3.0, 5.0], W.ATM_EXPO, W.config3(64, 8), (12, 48, 2)),
+        (3, [6.0], [[8]], W.config4(), (12, 32, 1)),
+        (2, [4.0], [[2]], W.Quad(n_u=7, n_v=5, u_rule=0), (4, 42, 2)),  # log case picks the eps-split
+    ],
+)
+def test_layout(ez, d, nu, expo, quad, expect):
+    assert ez.ez_layout(d, ez.sum_spec(nu, expo), ez.quadrature(quad)) == expect
+
+
+def test_layout_rejects_hadamard_pole_and_bad_exponents(ez):
+    q = ez.quadrature(W.Quad(n_u=8, n_v=1, u_rule=2))
+    with pytest.raises(ez.EzError) as e:  # d = 1, nu = (-1, 2): mu_T = 1 - 2 + 1 = 0
+        ez.ez_layout(1, ez.sum_spec([-1.0, 2.0], [[1, 1]]), q)
+    assert e.value.code == ez.EZ_EDOMAIN
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_layout(2, ez.sum_spec([2.5], [[2]]), q)
+    assert e.value.code == ez.EZ_EUNSUPPORTED
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_layout(2, ez.sum_spec([-4.0], [[2]]), q)
+    assert e.value.code == ez.EZ_EDOMAIN
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_layout(2, ez.sum_spec([3.0], [[2]]), ez.quadrature(W.Quad(n_u=8, n_v=300)))
+    assert e.value.code == ez.EZ_EINVAL
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import importlib
+
+    from paper_2504_11989_gb300 import ezeta
+
+    monkeypatch.setattr(ezeta, "_lib", None)
+    monkeypatch.setattr(ezeta, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        ezeta.lib()
+    importlib.reload(ezeta)
