@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput of the Epstein zeta method on GB300: lattice sums/s (and Epstein zeta
+evaluations/s) of the three-body zeta function zeta^(3)(3,3,3) on the square and
+hexagonal lattices (unit density times a seeded lattice constant in [0.9, 1.3]),
+256 x 256 Brillouin-zone grid mapped to 4 Duffy sectors x 128 u x 128 v nodes,
+cutoff radius 6 in real and reciprocal space, FP64.
+
+One step = one pass of the whole path (table setup, per-node Epstein zeta, product,
+quadrature reduction) over a batch of 128 sums (64 per lattice).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Epstein zeta evals/sec and lattice sums/sec at stated rel. error; p50/p99 latency"
+PER_LATTICE = 64
+LATTICES = ("square", "hexagonal")
+GRID = 256
+R_CUT = 6.0
+NU = 3.0
+N_BODY = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-lattice", type=int, default=PER_LATTICE, help="sums per lattice per step (profiling)")
+    return ap.parse_args()
+
+
+def workload(rank: int, per_lattice: int = PER_LATTICE):
+    """[(lattice name, lattice constant)] of the sums of one step."""
+    from paper_2504_11989_gb300 import workloads as W
+
+    items = []
+    for li, name in enumerate(LATTICES):
+        for s in W.lattice_constants(per_lattice, W.SEED_BASE + 1 + 100 * rank + li):
+            items.append((name, float(s)))
+    return items
+
+
+def quad_for(scale: float):
+    from paper_2504_11989_gb300 import workloads as W
+
+    # lattice constant s scales lambda = V^{1/d} = s and the cutoffs (6 spacings)
+    return W.Quad(n_u=GRID // 2, n_v=GRID // 2, u_rule=1, lam=scale, r_real=R_CUT * scale, r_recip=R_CUT / scale)
+
+
+# ----------------------------------------------------------------------------- counts
+def gl01(n):
+    import numpy as np
+
+    x, w = np.polynomial.legendre.leggauss(n)
+    return (x + 1) / 2, w / 2
+
+
+def algorithmic_flops_d2(A, q, nd=1, nfac=3):
+    """FP64 flops of the far-field kernel for one d = 2 sum, per the unit costs of the design:
+    in-range reciprocal term 3d + 33 nd; real space per node Ma (6 + 4 nd) + 2 nd; per-node
+    k, assembly, product and weight 2 d^2 + 4 nd + nfac + 2."""
+    import numpy as np
+
+    d = 2
+    AiT = np.linalg.inv(A).T
+    u, _ = gl01(q.n_u)
+    u = u * 0.5
+    v, _ = gl01(q.n_v)
+    ks = []
+    for s in range(4):
+        j, p = s >> 1, (-1.0 if s & 1 else 1.0)
+        for uu in u:
+            y = np.stack([p * v, np.ones_like(v)], axis=1)
+            kt = uu * y[:, [(0 - j) % 2, (1 - j) % 2]]
+            ks.append(kt @ AiT.T)
+    k = np.concatenate(ks)
+    kmax = max(np.linalg.norm(AiT @ np.array(c)) for c in ([.5, .5], [.5, -.5]))
+    Rn = q.r_recip + kmax
+    H = [int(math.ceil(Rn * np.linalg.norm(A[:, i]))) for i in range(2)]
+    hs = np.array([[a, b] for a in range(-H[0], H[0] + 1) for b in range(-H[1], H[1] + 1)], dtype=float)
+    G = hs @ AiT.T
+    G = G[np.sum(G * G, axis=1) <= Rn * Rn]
+    n_in = 0
+    for c0 in range(0, len(k), 8192):
+        kk = k[c0:c0 + 8192]
+        q2 = np.sum((kk[:, None, :] + G[None, :, :]) ** 2, axis=2)
+        n_in += int(np.count_nonzero(q2 <= q.r_recip ** 2))
+    Ainv = np.linalg.inv(A)
+    M = [int(math.ceil(q.r_real * np.linalg.norm(Ainv[i]) + 1e-9)) for i in range(2)]
+    Ma_mean = 0.5 * (M[0] + M[1])  # sectors alternate the v axis
+    nodes = len(k)
+    per_node = Ma_mean * (6 + 4 * nd) + 2 * nd + 2 * d * d + 4 * nd + nfac + 2
+    return n_in * (3 * d + 33 * nd) + nodes * per_node, nodes, n_in
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if not sm:
+            return None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sums(items, seconds: float, threads: int):
+    """Oracle on the first sums of the workload until `seconds` have elapsed."""
+    import oracle
+    from paper_2504_11989_gb300 import workloads as W
+
+    oracle.build()
+    vals, t0 = [], time.perf_counter()
+    for name, s in items:
+        prob = W.nbody_problem(name, NU, N_BODY, quad_for(s), scale=s)
+        vals.append(float(oracle.nbody(prob, threads=threads)[0]))
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return vals, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    items = workload(0)
+    per_step = max(1, int(args.cpu_seconds / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sums(items[:1], 0.0, threads)
+    times, n_done = [], 0
+    for k in range(args.steps):
+        sub = items[(k * per_step) % len(items):][:per_step]
+        vals, dt = oracle_sums(sub, 1e9, threads)
+        times.append(dt)
+        n_done += len(vals)
+    total = sum(times)
+    value = n_done / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lattice_sums/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic lattices (seeded lattice constants)",
+            "config": config_dict(),
+            "cpu_baseline": {"value": value, "unit": "lattice_sums/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} full sum(s) per step of the same workload"},
+            "e2e": {"value": value, "unit": "lattice_sums/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_dict(per_lattice: int = PER_LATTICE):
+    return {"workload": "zeta^(3)(3,3,3) on square+hexagonal lattices, 256^2 BZ grid (4x128x128 Duffy nodes), "
+                        f"cutoff radius 6, {per_lattice} lattice constants per lattice per step",
+            "global_batch": len(LATTICES) * per_lattice, "nodes_per_sum": 4 * (GRID // 2) ** 2,
+            "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps"}
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2504_11989_gb300 import build, ezeta
+    from paper_2504_11989_gb300 import workloads as W
+
+    build.build()
+    items = workload(rank, args.per_lattice)
+    lats = [ezeta.Lattice(W.lattice(n, scale=s)) for n, s in items]
+    spec = ezeta.sum_spec([NU], [[N_BODY]])
+    quads = [ezeta.quadrature(quad_for(s)) for _, s in items]
+    stream = torch.cuda.Stream()
+    batch = ezeta.Batch(lats, [spec] * len(items), quads, stream=stream)
+    out = torch.zeros(len(items) * ezeta.EZ_MAX_PROD, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        batch.run(out, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    batch.timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ezeta.ez_launch_count()
+    far_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            batch.run(out, stream)
+            ev[k][1].record(stream)
+            f, _ = batch.timing(True)
+            far_ms.append(f)
+    torch.cuda.synchronize()
+    launches = ezeta.ez_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    clocks = sampler.stop()
+    n_sums = len(items)
+    value = world * n_sums * args.steps / (total_ms / 1e3)
+    res = out.view(n_sums, ezeta.EZ_MAX_PROD)[:, 0].cpu().numpy()
+
+    # end to end through the C ABI with host buffers (planning, upload, kernels, download)
+    host_out = np.zeros((n_sums, ezeta.EZ_MAX_PROD))
+    e2e_steps = max(2, min(args.steps, 5))
+    ezeta.ez_lattice_sums(lats, [spec] * n_sums, quads, out=host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ezeta.ez_lattice_sums(lats, [spec] * n_sums, quads, out=host_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    assert np.array_equal(host_out[:, 0], res), "batch and one-shot paths disagree"
+    _, staging = batch.sizes()
+
+    # roofline of the far-field kernel (one launch per step)
+    flops = 0.0
+    nodes_total = 0
+    for name in LATTICES:
+        f, nodes, _ = algorithmic_flops_d2(W.lattice(name), quad_for(1.0))
+        flops += args.per_lattice * f
+        nodes_total += args.per_lattice * nodes
+    far_mean_ms = float(np.mean(far_ms))
+    achieved = flops / (far_mean_ms * 1e-3) / 1e12
+    peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
+    probe = ezeta.ez_diag_fp64_peak(stream)
+    line = {
+        "metric": METRIC, "value": value, "unit": "lattice_sums/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic lattices (seeded lattice constants)",
+        "config": config_dict(args.per_lattice),
+        "zeta_evals_per_s": {"per_factor": value * nodes_total / n_sums * N_BODY, "distinct_nu": value * nodes_total / n_sums},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "unit": f"per step of {n_sums} sums"},
+        "e2e": {"value": world * n_sums / e2e_s, "unit": "lattice_sums/s", "h2d_bytes_per_step": int(staging),
+                "d2h_bytes_per_step": int(n_sums * ezeta.EZ_MAX_PROD * 8)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "far_kernel_d2", "achieved": achieved, "peak": peak_nominal,
+                     "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": None,
+                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
+                                    f"DFMA probe measured {probe:.3f} TFLOP/s in this run",
+                     "far_ms_per_launch": far_mean_ms, "flops_per_launch": flops},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        vals, dt = oracle_sums(items, args.cpu_seconds, threads)
+        rel = [abs(res[i] - v) / abs(v) for i, v in enumerate(vals)]
+        line["cpu_baseline"] = {"value": len(vals) / dt, "unit": "lattice_sums/s", "cores": threads, "kind": "oracle",
+                                "sample": f"first {len(vals)} sums of the step's batch, full size"}
+        line["rel_err_vs_oracle"] = float(max(rel))
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

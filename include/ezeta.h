@@ -64,11 +64,11 @@ typedef struct {
   double eps;     /* split point of the near part (default 1e-2, Sec. 4.1) */
   int ell;        /* Taylor order 2*ell of Z^reg in the near part (default 4, Sec. 4.1) */
   double lambda;  /* splitting parameter of the incomplete-gamma form (default V^{1/d}) */
-  double r_real;  /* real-space cutoff |z| <= r_real (default 3.6 lambda) */
-  double r_recip; /* reciprocal cutoff |g + k| <= r_recip (default 3.6 / lambda) */
+  double r_real;  /* real-space cutoff |z| <= r_real (default sqrt(45/pi) lambda) */
+  double r_recip; /* reciprocal cutoff |g + k| <= r_recip (default sqrt(45/pi) / lambda) */
   int prec;       /* ez_precision */
-  int dedupe;     /* 0: one Epstein zeta evaluation per factor; 1 (default 1 when
-                     negative is not given; see ez_quadrature_default) : one per distinct nu */
+  int dedupe;     /* 1: one Epstein zeta evaluation per distinct nu and node (default);
+                     0: one evaluation per factor (n <= EZ_MAX_NU) */
 } ez_quadrature;
 
 /* Fills *q with the defaults (n_u = 32, n_v = 32, u_rule 0, eps 1e-2, ell 4, lambda 0,
@@ -122,17 +122,51 @@ int ez_atm_energy(ez_lattice lat, const ez_quadrature* q, double* energy, double
 /* --- batched lattice sums ----------------------------------------------------- */
 /* n_req sums in one pass: sum r uses lats[r], specs[r], quads[r] and writes
  * out[r*EZ_MAX_PROD + p] for p < specs[r].n_prod (host or device).
- * lines (optional, host or device): per-line partial sums laid out per request as
- *   [sector][u node][p] for the far field followed by [sector][p] for the near part,
- * request r starting at offset ez_lines_offset(...) -- used for sampled checks.
- * line_offsets (optional, host, n_req+1 ints) receives those offsets (in doubles). */
+ * lines (optional, host or device): per-line partial sums, EZ_MAX_PROD doubles per
+ * line; the lines of sum r are line_offsets[r] .. line_offsets[r+1]-1: first the
+ * far-field lines in the order (sector, u node), then, for the eps-split rule, one
+ * near-part line per sector.  The value of product p is the sum of its lines.
+ * line_offsets (optional, host, n_req+1 entries).  Synchronises `stream`. */
 int ez_lattice_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
                     const ez_quadrature* quads, double* out, double* lines, long long* line_offsets,
                     void* stream);
 
+/* A batch keeps the plans of n_req sums and the device memory of all their tables
+ * and partial sums resident.  ez_batch_create plans, allocates (cudaMalloc and
+ * pinned host staging, owned by the batch) and uploads the descriptors on
+ * `stream`.  ez_batch_run launches every kernel of the path (tables are rebuilt on
+ * each run) and writes out[r*EZ_MAX_PROD + p] (host or device; with host memory
+ * the call synchronises `stream`, with device memory it is asynchronous).
+ * ez_batch_lines copies the per-line partial sums of the last run (layout as in
+ * ez_lattice_sums); ez_batch_n_lines gives their count.  A batch may be run any
+ * number of times, on one stream at a time. */
+typedef struct ez_batch_s* ez_batch;
+int ez_batch_create(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
+                    const ez_quadrature* quads, void* stream, ez_batch* out);
+int ez_batch_run(ez_batch b, double* out, void* stream);
+long long ez_batch_n_lines(ez_batch b);
+int ez_batch_lines(ez_batch b, double* lines, long long* line_offsets, void* stream);
+int ez_batch_destroy(ez_batch b);
+
+/* Timing of batch runs with CUDA events recorded on the run's stream: after
+ * ez_batch_timing(b, 1, ...) every run records events around its setup kernels,
+ * its far-field kernels and its near-part/reduction kernels.  A later call
+ * (enable 0 or 1) returns, for the last run, the milliseconds of the far-field
+ * kernels (far_ms) and of the whole launch sequence (total_ms); it waits for
+ * that run's last event. */
+int ez_batch_timing(ez_batch b, int enable, float* far_ms, float* total_ms);
+
+/* Bytes of device memory owned by the batch and of its host staging (the bytes
+ * uploaded by ez_batch_create and by every ez_lattice_sums call of the same sums). */
+int ez_batch_sizes(ez_batch b, long long* device_bytes, long long* staging_bytes);
+
 /* Number of Duffy sectors (d 2^{d-1}) and far-field u nodes for (d, q). */
 int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q, int* n_sectors,
               int* n_u_total, int* u_rule_used);
+
+/* Diagnostic (no counterpart in the paper): sustained FP64 FMA throughput of the
+ * current device in TFLOP/s, from a DFMA loop on every SM timed with CUDA events. */
+int ez_diag_fp64_peak(double* tflops, void* stream);
 
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* ez_last_error(void);

@@ -554,30 +554,63 @@ int init_constants() {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// batched lattice sums
+// batched lattice sums: a batch holds the plans of its sums, the packed host
+// staging (descriptors, quadrature rules, launch lists) and the device memory of
+// every table and output segment.  Running a batch launches every kernel of the
+// path (tables are rebuilt on each run); nothing but the result leaves the device.
 // ---------------------------------------------------------------------------
-static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs, const ez_quadrature* quads,
-                    double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
+struct ez_batch_s {
+  int n_req = 0;
+  std::vector<Plan> plans;
+  bool owns = false;
+  char* d = nullptr;
+  char* h = nullptr;
+  size_t dbytes = 0, hbytes = 0;
+  size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
+         o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
+  int n_phi = 0, n_tay = 0;
+  size_t far_begin[4] = {0, 0, 0, 0}, far_end[4] = {0, 0, 0, 0}, near_begin = 0, near_end = 0;
+  long long n_lines = 0;
+  std::vector<long long> line0;
+  bool ran = false;
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, far begin, far end, end
+};
+
+namespace {
+
+int batch_plan(ez_batch_s& B, int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
+               const ez_quadrature* quads) {
   if (n_req < 1) return fail(EZ_EINVAL, "n_req = %d", n_req);
-  if (!lats || !specs || !quads || !out) return fail(EZ_EINVAL, "NULL argument");
+  if (!lats || !specs || !quads) return fail(EZ_EINVAL, "NULL argument");
   int rc = init_constants();
   if (rc) return rc;
-  std::vector<Plan> plans(n_req);
+  B.n_req = n_req;
+  B.plans.assign(n_req, Plan());
   for (int r = 0; r < n_req; ++r) {
     if (!lats[r]) return fail(EZ_EINVAL, "lattice %d is NULL", r);
-    rc = make_plan(lats[r], specs[r], quads[r], plans[r]);
+    rc = make_plan(lats[r], specs[r], quads[r], B.plans[r]);
     if (rc) return rc;
   }
-  // ---- order: requests grouped by d for the far launches
+  return EZ_OK;
+}
+
+// layout of buffers (fill = false) or packing of the staging with device addresses (fill = true)
+int batch_layout(ez_batch_s& B, bool fill) {
+  const int n_req = B.n_req;
+  std::vector<Plan>& plans = B.plans;
   std::vector<int> order;
   for (int d = 1; d <= 3; ++d)
     for (int r = 0; r < n_req; ++r)
       if (plans[r].d == d) order.push_back(r);
-
   // ---- sizes
-  long long n_seg = 0, n_lines = 0;
+  long long n_seg = 0;
+  long long& n_lines = B.n_lines;
+  n_lines = 0;
   size_t n_items_far = 0, n_items_near = 0;
-  std::vector<long long> seg_far0(n_req), seg_near0(n_req), line0(n_req);
+  std::vector<long long> seg_far0(n_req), seg_near0(n_req);
+  std::vector<long long>& line0 = B.line0;
+  line0.assign(n_req, 0);
   for (int r : order) {
     seg_far0[r] = n_seg;
     n_seg += plans[r].n_far_seg;
@@ -593,23 +626,35 @@ static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
     n_lines += plans[r].n_lines;
   }
   Layout dl, hl;
-  const size_t o_req = dl.take(sizeof(ReqDesc) * n_req), h_req = hl.take(sizeof(ReqDesc) * n_req);
-  const size_t o_items = dl.take(sizeof(Item) * (n_items_far + n_items_near)),
-               h_items = hl.take(sizeof(Item) * (n_items_far + n_items_near));
-  const size_t o_rj = dl.take(sizeof(RecipJob) * n_req), h_rj = hl.take(sizeof(RecipJob) * n_req);
-  const size_t o_gj = dl.take(sizeof(GboxJob) * n_req), h_gj = hl.take(sizeof(GboxJob) * n_req);
-  int n_phi = 0, n_tay = 0;
+  B.o_req = dl.take(sizeof(ReqDesc) * n_req);
+  const size_t h_req = hl.take(sizeof(ReqDesc) * n_req);
+  B.o_items = dl.take(sizeof(Item) * (n_items_far + n_items_near));
+  const size_t h_items = hl.take(sizeof(Item) * (n_items_far + n_items_near));
+  B.o_rj = dl.take(sizeof(RecipJob) * n_req);
+  const size_t h_rj = hl.take(sizeof(RecipJob) * n_req);
+  B.o_gj = dl.take(sizeof(GboxJob) * n_req);
+  const size_t h_gj = hl.take(sizeof(GboxJob) * n_req);
+  int& n_phi = B.n_phi;
+  int& n_tay = B.n_tay;
+  n_phi = n_tay = 0;
   for (int r = 0; r < n_req; ++r) {
     n_phi += plans[r].spec.n_distinct;
     if (plans[r].near) n_tay += plans[r].spec.n_distinct;
   }
-  const size_t o_pj = dl.take(sizeof(PhiJob) * n_phi), h_pj = hl.take(sizeof(PhiJob) * n_phi);
-  const size_t o_tj = dl.take(sizeof(TaylorJob) * std::max(n_tay, 1)), h_tj = hl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
-  const size_t o_lreq = dl.take(sizeof(int) * n_lines), h_lreq = hl.take(sizeof(int) * n_lines);
-  const size_t o_lseg0 = dl.take(sizeof(long long) * n_lines), h_lseg0 = hl.take(sizeof(long long) * n_lines);
-  const size_t o_lnseg = dl.take(sizeof(int) * n_lines), h_lnseg = hl.take(sizeof(int) * n_lines);
-  const size_t o_rl0 = dl.take(sizeof(long long) * n_req), h_rl0 = hl.take(sizeof(long long) * n_req);
-  const size_t o_rnl = dl.take(sizeof(int) * n_req), h_rnl = hl.take(sizeof(int) * n_req);
+  B.o_pj = dl.take(sizeof(PhiJob) * n_phi);
+  const size_t h_pj = hl.take(sizeof(PhiJob) * n_phi);
+  B.o_tj = dl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
+  const size_t h_tj = hl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
+  B.o_lreq = dl.take(sizeof(int) * n_lines);
+  const size_t h_lreq = hl.take(sizeof(int) * n_lines);
+  B.o_lseg0 = dl.take(sizeof(long long) * n_lines);
+  const size_t h_lseg0 = hl.take(sizeof(long long) * n_lines);
+  B.o_lnseg = dl.take(sizeof(int) * n_lines);
+  const size_t h_lnseg = hl.take(sizeof(int) * n_lines);
+  B.o_rl0 = dl.take(sizeof(long long) * n_req);
+  const size_t h_rl0 = hl.take(sizeof(long long) * n_req);
+  B.o_rnl = dl.take(sizeof(int) * n_req);
+  const size_t h_rnl = hl.take(sizeof(int) * n_req);
   std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_rec(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
@@ -635,17 +680,18 @@ static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
   }
-  const size_t o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
-  const size_t o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
-  const size_t o_out = dl.take(sizeof(double) * EZ_MAX_PROD * n_req);
+  B.o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
+  B.o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
+  B.o_out = dl.take(sizeof(double) * EZ_MAX_PROD * n_req);
 
-  std::lock_guard<std::mutex> lock(g_arena.mu);
-  rc = arena_reserve(dl.off, hl.off);
-  if (rc) return rc;
-  char* D = g_arena.d;
-  char* Hs = g_arena.h;
+  if (!fill) {
+    B.dbytes = dl.off;
+    B.hbytes = hl.off;
+    return EZ_OK;
+  }
+  char* D = B.d;
+  char* Hs = B.h;
   auto dptr = [&](size_t o) { return (void*)(D + o); };
-
   // ---- fill host staging
   ReqDesc* reqs = (ReqDesc*)(Hs + h_req);
   Item* items = (Item*)(Hs + h_items);
@@ -746,9 +792,8 @@ static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
   }
   // items (far: grouped by d; near after)
   size_t ii = 0;
-  size_t far_begin[4] = {0, 0, 0, 0}, far_end[4] = {0, 0, 0, 0};
   for (int d = 1; d <= 3; ++d) {
-    far_begin[d] = ii;
+    B.far_begin[d] = ii;
     for (int r : order) {
       Plan& p = plans[r];
       if (p.d != d) continue;
@@ -761,16 +806,16 @@ static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
             for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, s0++};
       }
     }
-    far_end[d] = ii;
+    B.far_end[d] = ii;
   }
-  const size_t near_begin = ii;
+  B.near_begin = ii;
   for (int r : order) {
     Plan& p = plans[r];
     long long s0 = seg_near0[r];
     for (int s = 0; s < p.nsect; ++s)
       for (int c = 0; c < p.near_per_sector; ++c) items[ii++] = Item{r, s, 0, c, s0++};
   }
-  const size_t near_end = ii;
+  B.near_end = ii;
   // lines
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -792,72 +837,197 @@ static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
         lnseg[L] = p.near_per_sector;
       }
   }
-  // ---- upload and launch
-  EZ_CUDA(cudaMemcpyAsync(D, Hs, hl.off, cudaMemcpyHostToDevice, stream));
-  ReqDesc* dreqs = (ReqDesc*)dptr(o_req);
-  enum_recip_kernel<<<n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(o_rj));
+  return EZ_OK;
+}
+
+int batch_launch(ez_batch_s& B, cudaStream_t stream) {
+  char* D = B.d;
+  auto dptr = [&](size_t o) { return (void*)(D + o); };
+  if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[0], stream));
+  ReqDesc* dreqs = (ReqDesc*)dptr(B.o_req);
+  enum_recip_kernel<<<B.n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(B.o_rj));
   EZ_LAUNCHED();
   long long max_cells = 0;
-  for (auto& p : plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
-  gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(o_gj), n_req);
+  for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
+  gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
   EZ_LAUNCHED();
   int max_int = 0;
-  for (auto& p : plans)
+  for (auto& p : B.plans)
     for (int j = 0; j < p.spec.n_distinct; ++j) max_int = std::max(max_int, p.phi[j].n_int);
-  phitab_kernel<<<dim3(max_int, n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(o_pj));
+  phitab_kernel<<<dim3(max_int, B.n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
   EZ_LAUNCHED();
-  if (n_tay) {
+  if (B.n_tay) {
     long long max_rec = 0;
     int tot_alpha = 0;
-    for (auto& p : plans)
+    for (auto& p : B.plans)
       if (p.near) {
         max_rec = std::max(max_rec, p.rcap);
         tot_alpha += (int)(p.alpha.size() / 3) * p.spec.n_distinct;
       }
-    phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(o_tj), n_tay);
+    phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
-    taylor_kernel<<<(tot_alpha + 63) / 64, 64, 0, stream>>>(dreqs, (const TaylorJob*)dptr(o_tj), n_tay);
-    EZ_LAUNCHED();
-  }
-  Item* ditems = (Item*)dptr(o_items);
-  double* dseg = (double*)dptr(o_seg);
-  if (far_end[1] > far_begin[1]) {
-    far_kernel_d1<<<(unsigned)(far_end[1] - far_begin[1]), 128, 0, stream>>>(dreqs, ditems + far_begin[1], dseg);
+    taylor_kernel<<<(tot_alpha + 63) / 64, 64, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
   }
-  if (far_end[2] > far_begin[2]) {
+  Item* ditems = (Item*)dptr(B.o_items);
+  double* dseg = (double*)dptr(B.o_seg);
+  if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[1], stream));
+  if (B.far_end[1] > B.far_begin[1]) {
+    far_kernel_d1<<<(unsigned)(B.far_end[1] - B.far_begin[1]), 128, 0, stream>>>(dreqs, ditems + B.far_begin[1], dseg);
+    EZ_LAUNCHED();
+  }
+  if (B.far_end[2] > B.far_begin[2]) {
     size_t sm = 0;
-    for (auto& p : plans)
+    for (auto& p : B.plans)
       if (p.d == 2) sm = std::max(sm, p.smem);
-    far_kernel_d2<<<(unsigned)(far_end[2] - far_begin[2]), 128, sm, stream>>>(dreqs, ditems + far_begin[2], dseg);
+    far_kernel_d2<<<(unsigned)(B.far_end[2] - B.far_begin[2]), 128, sm, stream>>>(dreqs, ditems + B.far_begin[2], dseg);
     EZ_LAUNCHED();
   }
-  if (far_end[3] > far_begin[3]) {
+  if (B.far_end[3] > B.far_begin[3]) {
     size_t sm = 0;
-    for (auto& p : plans)
+    for (auto& p : B.plans)
       if (p.d == 3) sm = std::max(sm, p.smem);
     if (sm > 200 * 1024) return fail(EZ_EINVAL, "far kernel needs %zu bytes of shared memory", sm);
-    far_kernel_d3<<<(unsigned)(far_end[3] - far_begin[3]), 256, sm, stream>>>(dreqs, ditems + far_begin[3], dseg);
+    far_kernel_d3<<<(unsigned)(B.far_end[3] - B.far_begin[3]), 256, sm, stream>>>(dreqs, ditems + B.far_begin[3], dseg);
     EZ_LAUNCHED();
   }
-  if (near_end > near_begin) {
-    near_kernel<<<(unsigned)(near_end - near_begin), 128, 0, stream>>>(dreqs, ditems + near_begin, dseg);
+  if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[2], stream));
+  if (B.near_end > B.near_begin) {
+    near_kernel<<<(unsigned)(B.near_end - B.near_begin), 128, 0, stream>>>(dreqs, ditems + B.near_begin, dseg);
     EZ_LAUNCHED();
   }
-  double* dlines = (double*)dptr(o_lines);
-  lines_kernel<<<(unsigned)((n_lines + 127) / 128), 128, 0, stream>>>(dreqs, (const int*)dptr(o_lreq),
-                                                                     (const long long*)dptr(o_lseg0),
-                                                                     (const int*)dptr(o_lnseg), (int)n_lines, dseg, dlines);
+  double* dlines = (double*)dptr(B.o_lines);
+  lines_kernel<<<(unsigned)((B.n_lines + 127) / 128), 128, 0, stream>>>(dreqs, (const int*)dptr(B.o_lreq),
+                                                                     (const long long*)dptr(B.o_lseg0),
+                                                                     (const int*)dptr(B.o_lnseg), (int)B.n_lines, dseg, dlines);
   EZ_LAUNCHED();
-  double* dout = (double*)dptr(o_out);
-  total_kernel<<<(n_req * EZ_MAX_PROD + 127) / 128, 128, 0, stream>>>(dreqs, (const long long*)dptr(o_rl0),
-                                                                     (const int*)dptr(o_rnl), n_req, dlines, dout);
+  double* dout = (double*)dptr(B.o_out);
+  total_kernel<<<(B.n_req * EZ_MAX_PROD + 127) / 128, 128, 0, stream>>>(dreqs, (const long long*)dptr(B.o_rl0),
+                                                                     (const int*)dptr(B.o_rnl), B.n_req, dlines, dout);
   EZ_LAUNCHED();
-  EZ_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * EZ_MAX_PROD * n_req, cudaMemcpyDefault, stream));
-  if (lines_out)
-    EZ_CUDA(cudaMemcpyAsync(lines_out, dlines, sizeof(double) * EZ_MAX_PROD * n_lines, cudaMemcpyDefault, stream));
+  if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[3], stream));
+  B.ran = true;
+  return EZ_OK;
+}
+
+}  // namespace
+
+extern "C" int ez_batch_create(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
+                               const ez_quadrature* quads, void* stream, ez_batch* out) {
+  if (!out) return fail(EZ_EINVAL, "NULL argument");
+  ez_batch B = new ez_batch_s();
+  int rc = batch_plan(*B, n_req, lats, specs, quads);
+  if (!rc) rc = batch_layout(*B, false);
+  if (!rc) {
+    if (cudaMalloc(&B->d, B->dbytes) != cudaSuccess) {
+      cudaGetLastError();
+      B->d = nullptr;
+      rc = fail(EZ_ENOMEM, "device allocation of %zu bytes failed", B->dbytes);
+    } else if (cudaMallocHost(&B->h, B->hbytes) != cudaSuccess) {
+      cudaGetLastError();
+      B->h = nullptr;
+      rc = fail(EZ_ENOMEM, "pinned allocation of %zu bytes failed", B->hbytes);
+    }
+    B->owns = true;
+  }
+  if (!rc) rc = batch_layout(*B, true);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(B->d, B->h, B->hbytes, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) rc = fail(EZ_ECUDA, "upload: %s", cudaGetErrorString(e));
+  }
+  if (rc) {
+    ez_batch_destroy(B);
+    return rc;
+  }
+  *out = B;
+  return EZ_OK;
+}
+
+extern "C" int ez_batch_run(ez_batch B, double* out, void* stream_) {
+  if (!B) return fail(EZ_EINVAL, "NULL batch");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  int rc = batch_launch(*B, stream);
+  if (rc) return rc;
+  if (out) {
+    EZ_CUDA(cudaMemcpyAsync(out, B->d + B->o_out, sizeof(double) * EZ_MAX_PROD * B->n_req, cudaMemcpyDefault, stream));
+    if (!is_device_ptr(out)) EZ_CUDA(cudaStreamSynchronize(stream));
+  }
+  return EZ_OK;
+}
+
+extern "C" long long ez_batch_n_lines(ez_batch B) { return B ? B->n_lines : -1; }
+
+extern "C" int ez_batch_lines(ez_batch B, double* lines, long long* line_offsets, void* stream_) {
+  if (!B || !B->ran) return fail(EZ_EINVAL, "batch has not run");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (lines) {
+    EZ_CUDA(cudaMemcpyAsync(lines, B->d + B->o_lines, sizeof(double) * EZ_MAX_PROD * B->n_lines, cudaMemcpyDefault, stream));
+    if (!is_device_ptr(lines)) EZ_CUDA(cudaStreamSynchronize(stream));
+  }
   if (line_offsets)
-    for (int r = 0; r <= n_req; ++r) line_offsets[r] = r < n_req ? line0[r] : n_lines;
+    for (int r = 0; r <= B->n_req; ++r) line_offsets[r] = r < B->n_req ? B->line0[r] : B->n_lines;
+  return EZ_OK;
+}
+
+extern "C" int ez_batch_timing(ez_batch B, int enable, float* far_ms, float* total_ms) {
+  if (!B) return fail(EZ_EINVAL, "NULL batch");
+  if ((far_ms || total_ms) && B->timing && B->ran) {
+    EZ_CUDA(cudaEventSynchronize(B->ev[3]));
+    if (far_ms) EZ_CUDA(cudaEventElapsedTime(far_ms, B->ev[1], B->ev[2]));
+    if (total_ms) EZ_CUDA(cudaEventElapsedTime(total_ms, B->ev[0], B->ev[3]));
+  } else {
+    if (far_ms) *far_ms = -1.f;
+    if (total_ms) *total_ms = -1.f;
+  }
+  if (enable && !B->ev[0])
+    for (int i = 0; i < 4; ++i) EZ_CUDA(cudaEventCreate(&B->ev[i]));
+  B->timing = enable != 0;
+  return EZ_OK;
+}
+
+extern "C" int ez_batch_sizes(ez_batch B, long long* device_bytes, long long* staging_bytes) {
+  if (!B) return fail(EZ_EINVAL, "NULL batch");
+  if (device_bytes) *device_bytes = (long long)B->dbytes;
+  if (staging_bytes) *staging_bytes = (long long)B->hbytes;
+  return EZ_OK;
+}
+
+extern "C" int ez_batch_destroy(ez_batch B) {
+  if (!B) return EZ_OK;
+  for (int i = 0; i < 4; ++i)
+    if (B->ev[i]) cudaEventDestroy(B->ev[i]);
+  if (B->owns) {
+    if (B->d) cudaFree(B->d);
+    if (B->h) cudaFreeHost(B->h);
+  }
+  delete B;
+  return EZ_OK;
+}
+
+// one-shot path: the batch lives in the shared arena for the duration of the call
+static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs, const ez_quadrature* quads,
+                    double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
+  if (!out) return fail(EZ_EINVAL, "NULL argument");
+  ez_batch_s B;
+  int rc = batch_plan(B, n_req, lats, specs, quads);
+  if (!rc) rc = batch_layout(B, false);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_arena.mu);
+  rc = arena_reserve(B.dbytes, B.hbytes);
+  if (rc) return rc;
+  B.d = g_arena.d;
+  B.h = g_arena.h;
+  B.owns = false;
+  rc = batch_layout(B, true);
+  if (rc) return rc;
+  EZ_CUDA(cudaMemcpyAsync(B.d, B.h, B.hbytes, cudaMemcpyHostToDevice, stream));
+  rc = batch_launch(B, stream);
+  if (rc) return rc;
+  EZ_CUDA(cudaMemcpyAsync(out, B.d + B.o_out, sizeof(double) * EZ_MAX_PROD * n_req, cudaMemcpyDefault, stream));
+  if (lines_out)
+    EZ_CUDA(cudaMemcpyAsync(lines_out, B.d + B.o_lines, sizeof(double) * EZ_MAX_PROD * B.n_lines, cudaMemcpyDefault, stream));
+  if (line_offsets)
+    for (int r = 0; r <= n_req; ++r) line_offsets[r] = r < n_req ? B.line0[r] : B.n_lines;
   EZ_CUDA(cudaStreamSynchronize(stream));
   return EZ_OK;
 }

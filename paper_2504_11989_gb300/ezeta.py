@@ -77,6 +77,17 @@ def lib():
             L.ez_lattice_sums.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
                                           ctypes.POINTER(ez_quadrature), vp, vp,
                                           ctypes.POINTER(ctypes.c_longlong), vp]
+            L.ez_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
+                                          ctypes.POINTER(ez_quadrature), vp, ctypes.POINTER(vp)]
+            L.ez_batch_run.argtypes = [vp, vp, vp]
+            L.ez_batch_n_lines.restype = ctypes.c_longlong
+            L.ez_batch_n_lines.argtypes = [vp]
+            L.ez_batch_lines.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_longlong), vp]
+            L.ez_batch_destroy.argtypes = [vp]
+            L.ez_batch_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]
+            L.ez_batch_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+            L.ez_diag_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
             L.ez_layout.argtypes = [ctypes.c_int, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
@@ -237,3 +248,58 @@ def ez_layout(d: int, spec: ez_sum_spec, q: ez_quadrature):
     _check(lib().ez_layout(int(d), ctypes.byref(spec), ctypes.byref(q), ctypes.byref(ns), ctypes.byref(nu_t),
                            ctypes.byref(ur)))
     return ns.value, nu_t.value, ur.value
+
+
+class Batch:
+    """ez_batch: resident plans and device tables of n sums (one upload); run() launches
+    every kernel of the path again and returns the values."""
+
+    def __init__(self, lats, specs, quads, stream=None):
+        n = len(lats)
+        self.n = n
+        self._lats = list(lats)  # keep the lattice handles alive
+        harr = (ctypes.c_void_p * n)(*[l.handle for l in lats])
+        sarr = (ez_sum_spec * n)(*specs)
+        qarr = (ez_quadrature * n)(*quads)
+        h = ctypes.c_void_p()
+        _check(lib().ez_batch_create(n, harr, sarr, qarr, _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, out=None, stream=None):
+        """out: None (host array returned), numpy array or CUDA tensor of n*EZ_MAX_PROD."""
+        if out is None:
+            out = np.zeros((self.n, EZ_MAX_PROD))
+        op, _ = _ptr(out)
+        _check(lib().ez_batch_run(self.handle, op, _stream_ptr(stream)))
+        return out
+
+    def timing(self, enable: bool = True):
+        """Enable event timing for following runs; returns (far_ms, total_ms) of the last timed run."""
+        f, t = ctypes.c_float(), ctypes.c_float()
+        _check(lib().ez_batch_timing(self.handle, 1 if enable else 0, ctypes.byref(f), ctypes.byref(t)))
+        return f.value, t.value
+
+    def sizes(self):
+        """(device bytes, host staging bytes) of the batch."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().ez_batch_sizes(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def lines(self, stream=None):
+        n_lines = int(lib().ez_batch_n_lines(self.handle))
+        buf = np.zeros((n_lines, EZ_MAX_PROD))
+        offs = (ctypes.c_longlong * (self.n + 1))()
+        _check(lib().ez_batch_lines(self.handle, ctypes.c_void_p(buf.ctypes.data), offs, _stream_ptr(stream)))
+        return buf, np.array(offs[:])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.ez_batch_destroy(h)
+            self.handle = None
+
+
+def ez_diag_fp64_peak(stream=None) -> float:
+    v = ctypes.c_double()
+    _check(lib().ez_diag_fp64_peak(ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
