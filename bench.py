@@ -31,6 +31,10 @@ GRID = 256
 R_CUT = 6.0
 NU = 3.0
 N_BODY = 3
+# DRAM bytes (read + write) of far_kernel_d2 per sum of this workload, from the ncu capture
+# summarised in profiles/far_kernel_d2_config2.md (4 sums: 250.6 KB); traffic scales with the
+# number of sums (per-sum tables).  Set to None whenever that kernel changes until re-captured.
+FAR_DRAM_BYTES_PER_SUM = 250.624e3 / 4
 
 
 def parse():
@@ -61,52 +65,6 @@ def quad_for(scale: float):
 
     # lattice constant s scales lambda = V^{1/d} = s and the cutoffs (6 spacings)
     return W.Quad(n_u=GRID // 2, n_v=GRID // 2, u_rule=1, lam=scale, r_real=R_CUT * scale, r_recip=R_CUT / scale)
-
-
-# ----------------------------------------------------------------------------- counts
-def gl01(n):
-    import numpy as np
-
-    x, w = np.polynomial.legendre.leggauss(n)
-    return (x + 1) / 2, w / 2
-
-
-def algorithmic_flops_d2(A, q, nd=1, nfac=3):
-    """FP64 flops of the far-field kernel for one d = 2 sum, per the unit costs of the design:
-    in-range reciprocal term 3d + 33 nd; real space per node Ma (6 + 4 nd) + 2 nd; per-node
-    k, assembly, product and weight 2 d^2 + 4 nd + nfac + 2."""
-    import numpy as np
-
-    d = 2
-    AiT = np.linalg.inv(A).T
-    u, _ = gl01(q.n_u)
-    u = u * 0.5
-    v, _ = gl01(q.n_v)
-    ks = []
-    for s in range(4):
-        j, p = s >> 1, (-1.0 if s & 1 else 1.0)
-        for uu in u:
-            y = np.stack([p * v, np.ones_like(v)], axis=1)
-            kt = uu * y[:, [(0 - j) % 2, (1 - j) % 2]]
-            ks.append(kt @ AiT.T)
-    k = np.concatenate(ks)
-    kmax = max(np.linalg.norm(AiT @ np.array(c)) for c in ([.5, .5], [.5, -.5]))
-    Rn = q.r_recip + kmax
-    H = [int(math.ceil(Rn * np.linalg.norm(A[:, i]))) for i in range(2)]
-    hs = np.array([[a, b] for a in range(-H[0], H[0] + 1) for b in range(-H[1], H[1] + 1)], dtype=float)
-    G = hs @ AiT.T
-    G = G[np.sum(G * G, axis=1) <= Rn * Rn]
-    n_in = 0
-    for c0 in range(0, len(k), 8192):
-        kk = k[c0:c0 + 8192]
-        q2 = np.sum((kk[:, None, :] + G[None, :, :]) ** 2, axis=2)
-        n_in += int(np.count_nonzero(q2 <= q.r_recip ** 2))
-    Ainv = np.linalg.inv(A)
-    M = [int(math.ceil(q.r_real * np.linalg.norm(Ainv[i]) + 1e-9)) for i in range(2)]
-    Ma_mean = 0.5 * (M[0] + M[1])  # sectors alternate the v axis
-    nodes = len(k)
-    per_node = Ma_mean * (6 + 4 * nd) + 2 * nd + 2 * d * d + 4 * nd + nfac + 2
-    return n_in * (3 * d + 33 * nd) + nodes * per_node, nodes, n_in
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -280,13 +238,10 @@ def main():
     assert np.array_equal(host_out[:, 0], res), "batch and one-shot paths disagree"
     _, staging = batch.sizes()
 
-    # roofline of the far-field kernel (one launch per step)
-    flops = 0.0
-    nodes_total = 0
-    for name in LATTICES:
-        f, nodes, _ = algorithmic_flops_d2(W.lattice(name), quad_for(1.0))
-        flops += args.per_lattice * f
-        nodes_total += args.per_lattice * nodes
+    # roofline of the far-field kernel (one launch per step): algorithmic FP64 flops counted
+    # by the library for the last run (same work every step)
+    flops, n_terms, n_coefs = batch.far_flops()
+    nodes_total = n_sums * 4 * (GRID // 2) ** 2
     far_mean_ms = float(np.mean(far_ms))
     achieved = flops / (far_mean_ms * 1e-3) / 1e12
     peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
@@ -303,10 +258,12 @@ def main():
                 "d2h_bytes_per_step": int(n_sums * ezeta.EZ_MAX_PROD * 8)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "far_kernel_d2", "achieved": achieved, "peak": peak_nominal,
-                     "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_nominal,
+                     "traffic": None if FAR_DRAM_BYTES_PER_SUM is None else FAR_DRAM_BYTES_PER_SUM * n_sums,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
                                     f"DFMA probe measured {probe:.3f} TFLOP/s in this run",
-                     "far_ms_per_launch": far_mean_ms, "flops_per_launch": flops},
+                     "far_ms_per_launch": far_mean_ms, "flops_per_launch": flops,
+                     "recip_terms_per_launch": n_terms, "mean_poly_len": n_coefs / max(1, n_terms)},
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

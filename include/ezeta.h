@@ -156,6 +156,14 @@ int ez_batch_destroy(ez_batch b);
  * that run's last event. */
 int ez_batch_timing(ez_batch b, int enable, float* far_ms, float* total_ms);
 
+/* Algorithmic FP64 flops of the far-field kernels of the last run: every in-range
+ * reciprocal term costs 3d - 1 flops for |g + k|^2 plus, per distinct exponent,
+ * 2n + 1 for its Phi polynomial of n coefficients (n counted on the device: the
+ * tables keep 4..16 coefficients per interval as accuracy needs), plus the fixed
+ * per-node and per-block costs of the real-space contraction and bookkeeping.
+ * terms / coefs (optional) receive the device counts.  Synchronous. */
+int ez_batch_far_flops(ez_batch b, double* flops, long long* terms, long long* coefs);
+
 /* Bytes of device memory owned by the batch and of its host staging (the bytes
  * uploaded by ez_batch_create and by every ez_lattice_sums call of the same sums). */
 int ez_batch_sizes(ez_batch b, long long* device_bytes, long long* staging_bytes);

@@ -221,6 +221,8 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   int n_unit = (int)std::ceil(std::max(0.0, t_hi_needed - P.t_geo_end)) + 1;
   P.n_int = std::min(kNGeo + n_unit, kMaxInt);
   P.t_hi = P.t_geo_end + (P.n_int - kNGeo);
+  P.t_geo_end_f = (float)P.t_geo_end;
+  P.t_hi_f = (float)P.t_hi;
   double fact = 1.0;
   if (P.log_m >= 0) {
     const int m = P.log_m;
@@ -566,6 +568,7 @@ struct ez_batch_s {
   char* d = nullptr;
   char* h = nullptr;
   size_t dbytes = 0, hbytes = 0;
+  size_t o_work = 0;
   size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
   int n_phi = 0, n_tay = 0;
@@ -657,7 +660,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_rnl = hl.take(sizeof(int) * n_req);
   std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
-  std::vector<size_t> o_rec(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
+  std::vector<size_t> o_rec(n_req), o_recf(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -673,7 +676,16 @@ int batch_layout(ez_batch_s& B, bool fill) {
     h_al[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
     o_alo[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
     h_alo[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
+  }
+  // everything above is uploaded as one prefix: device and staging offsets must agree
+  if (dl.off != hl.off || B.o_items != h_items || B.o_rnl != h_rnl ||
+      (n_req > 0 && (o_alo[n_req - 1] != h_alo[n_req - 1] || o_un[n_req - 1] != h_un[n_req - 1])))
+    return fail(EZ_EINVAL, "internal: staging layout mismatch");
+  // device-only tables and outputs
+  for (int r = 0; r < n_req; ++r) {
+    Plan& p = plans[r];
     o_rec[r] = dl.take(sizeof(G4) * p.rcap);
+    o_recf[r] = dl.take(sizeof(float4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
     const size_t na = p.alpha.size() / 3;
@@ -683,6 +695,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   B.o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
   B.o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
   B.o_out = dl.take(sizeof(double) * EZ_MAX_PROD * n_req);
+  B.o_work = dl.take(sizeof(unsigned long long) * 2 * n_req);
 
   if (!fill) {
     B.dbytes = dl.off;
@@ -734,9 +747,11 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
       R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
       R.phi[j] = p.phi[j];
+      R.phi[j].c_lam = R.c_lam;
       R.phi[j].tab = (const double*)dptr(o_tab[r][j]);
       PhiJob& J = pjobs[ipj++];
       J.a = p.phi[j].a;
+      J.c_lam = R.c_lam;
       J.t_geo_end = p.phi[j].t_geo_end;
       J.n_int = p.phi[j].n_int;
       J.out = (double*)dptr(o_tab[r][j]);
@@ -748,6 +763,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
     }
     R.gbox = (const double*)dptr(o_gbox[r]);
     R.rec = (const G4*)dptr(o_rec[r]);
+    R.recf = (const float4*)dptr(o_recf[r]);
+    R.R2f = (float)(p.r_recip * p.r_recip);
+    R.work = (unsigned long long*)dptr(B.o_work) + 2 * r;
+    R.c_lam_f = (float)R.c_lam;
     R.n_rec = 0;
     R.u_nodes = (const double*)dptr(o_un[r]);
     R.u_w = (const double*)dptr(o_uw[r]);
@@ -774,6 +793,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     RJ.R2 = p.R2enum;
     RJ.cap = (int)p.rcap;
     RJ.out = (G4*)dptr(o_rec[r]);
+    RJ.outf = (float4*)dptr(o_recf[r]);
     GboxJob& GJ = gjobs[r];
     std::memset(&GJ, 0, sizeof GJ);
     GJ.req = r;
@@ -844,6 +864,7 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   char* D = B.d;
   auto dptr = [&](size_t o) { return (void*)(D + o); };
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[0], stream));
+  EZ_CUDA(cudaMemsetAsync(dptr(B.o_work), 0, sizeof(unsigned long long) * 2 * B.n_req, stream));
   ReqDesc* dreqs = (ReqDesc*)dptr(B.o_req);
   enum_recip_kernel<<<B.n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(B.o_rj));
   EZ_LAUNCHED();
@@ -982,6 +1003,51 @@ extern "C" int ez_batch_timing(ez_batch B, int enable, float* far_ms, float* tot
   if (enable && !B->ev[0])
     for (int i = 0; i < 4; ++i) EZ_CUDA(cudaEventCreate(&B->ev[i]));
   B->timing = enable != 0;
+  return EZ_OK;
+}
+
+// FP64 flops of the far-field kernels of the last run: counted reciprocal terms
+// ((3d - 1) per in-range term, 2n + 1 per evaluated polynomial of n coefficients)
+// plus the per-node and per-block real-space and bookkeeping costs of the design.
+extern "C" int ez_batch_far_flops(ez_batch B, double* flops, long long* terms, long long* coefs) {
+  if (!B || !B->ran) return fail(EZ_EINVAL, "batch has not run");
+  std::vector<unsigned long long> w(2 * B->n_req);
+  EZ_CUDA(cudaMemcpy(w.data(), B->d + B->o_work, sizeof(unsigned long long) * w.size(), cudaMemcpyDeviceToHost));
+  double total = 0.0;
+  long long nt = 0, nc = 0;
+  for (int r = 0; r < B->n_req; ++r) {
+    const Plan& p = B->plans[r];
+    const int d = p.d, nd = p.spec.n_distinct;
+    int nfac = 0;
+    for (int pr = 0; pr < p.spec.n_prod; ++pr)
+      for (int j = 0; j < nd; ++j) nfac += p.spec.expo[pr][j];
+    const double t = (double)w[2 * r], c = (double)w[2 * r + 1];
+    nt += (long long)w[2 * r];
+    nc += (long long)w[2 * r + 1];
+    double per_term = (3.0 * d - 1.0) * t + 2.0 * c + 1.0 * t * nd;
+    double nodes = (double)p.nsect * p.n_ui * (d == 1 ? 1 : (d == 2 ? p.n_v : (double)p.n_v * p.n_v));
+    double per_node = 2.0 * d * d + 4.0 * nd + nfac + 2.0;  // k, assembly, products, weight
+    double blocks = 0.0, per_block = 0.0;
+    if (d == 1) {
+      per_node += p.M[0] * (6.0 + 2.0 * nd);
+    } else if (d == 2) {
+      const double Ma = 0.5 * (p.M[0] + p.M[1]), Mc = Ma;
+      per_node += Ma * (6.0 + 4.0 * nd) + 2.0 * nd;
+      blocks = (double)p.nsect * p.n_ui;
+      per_block = nd * (Ma + 1) * Mc * 4.0;
+    } else {
+      const double Mm = (p.M[0] + p.M[1] + p.M[2]) / 3.0;
+      per_node += Mm * 4.0 * nd + 2.0 * nd;
+      blocks = (double)p.nsect * p.n_ui * p.nch;
+      const double nv2 = std::min(kVChunk, p.n_v);
+      per_block = (Mm + 1) * p.n_v * 6.0 + (Mm + 1) * nv2 * 6.0 + nd * (Mm + 1) * (2 * Mm + 1) * Mm * 4.0 +
+                  nd * (Mm + 1) * nv2 * Mm * 8.0;
+    }
+    total += per_term + nodes * per_node + blocks * per_block;
+  }
+  if (flops) *flops = total;
+  if (terms) *terms = nt;
+  if (coefs) *coefs = nc;
   return EZ_OK;
 }
 
@@ -1180,6 +1246,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   const size_t o_gj = dl.take(sizeof(GboxJob)), h_gj = hl.take(sizeof(GboxJob));
   const size_t o_pj = dl.take(sizeof(PhiJob)), h_pj = hl.take(sizeof(PhiJob));
   const size_t o_rec = dl.take(sizeof(G4) * p.rcap);
+  const size_t o_recf = dl.take(sizeof(float4) * p.rcap);
   const size_t o_gbox = dl.take(sizeof(double) * p.cells);
   const size_t o_tab = dl.take(sizeof(double) * kRec * p.phi[0].n_int);
   const size_t o_st = dl.take(sizeof(int));
@@ -1214,6 +1281,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   RJ.R2 = p.R2enum;
   RJ.cap = (int)p.rcap;
   RJ.out = (G4*)(D + o_rec);
+  RJ.outf = (float4*)(D + o_recf);
   GboxJob& GJ = *(GboxJob*)(Hs + h_gj);
   std::memset(&GJ, 0, sizeof GJ);
   GJ.req = 0;
@@ -1226,6 +1294,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   GJ.out = (double*)(D + o_gbox);
   PhiJob& PJ = *(PhiJob*)(Hs + h_pj);
   PJ.a = p.phi[0].a;
+  PJ.c_lam = kPi * p.lam * p.lam;
   PJ.t_geo_end = p.phi[0].t_geo_end;
   PJ.n_int = p.phi[0].n_int;
   PJ.out = (double*)(D + o_tab);
@@ -1267,7 +1336,10 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   A.gbox = (const double*)(D + o_gbox);
   A.rq = (const ReqDesc*)(D + o_req);
   A.phi = p.phi[0];
+  A.phi.c_lam = A.c_lam;
   A.phi.tab = (const double*)(D + o_tab);
+  A.c_lam_f = (float)A.c_lam;
+  A.R2f = (float)A.R2_recip;
   A.y = y_dev ? y : (const double*)(D + o_y);
   A.re = re_dev ? re : (double*)(D + o_re);
   A.im = im ? (im_dev ? im : (double*)(D + o_im)) : nullptr;

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(128) epstein_kernel(EpsteinArgs P) {
       }
       phi = -1.0 / P.phi.a;
     } else {
-      phi = phi_eval(P.phi, P.c_lam * qq);
+      int nused;
+      phi = phi_eval_qq(P.phi, qq, P.c_lam_f * (float)qq, nused);
     }
     if (P.x_in_lattice && P.xt[0] == 0.0 && P.xt[1] == 0.0 && P.xt[2] == 0.0) {
       rre += phi;

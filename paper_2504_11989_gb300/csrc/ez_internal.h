@@ -13,14 +13,18 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 
 // ---------------------------------------------------------------------------
 // Tables of Phi_a(t) = t^{-a} Gamma(a,t) for the reciprocal-space hot loop.
-// t in [kT0, t_hi]: piecewise polynomials of degree kNC-1 in x = (t - t_mid)/h on
-//   kNGeo geometric intervals [kT0 r^i, kT0 r^{i+1}] (r = kGeoR), then unit-width
-//   intervals up to t_hi.  Each record: t_mid, 1/h, b_0 .. b_{kNC-1} (monomials in x).
+// t in [kT0, t_hi]: piecewise polynomials in x = (t - t_mid)/h on kNGeo geometric
+//   intervals [kT0 r^i, kT0 r^{i+1}] (r = kGeoR), then unit-width intervals up to
+//   t_hi.  Record of an interval (kRec doubles, 16-byte aligned): the number n of
+//   coefficients kept (4, 8, 12 or 16, an int in the first slot), s = c/h and
+//   o = -t_mid/h so that x = fma(|q|^2, s, o) with t = c |q|^2, one pad slot, then
+//   b_0 .. b_{kNC-1} (monomials in x; b_j = 0 for j >= n).  n is the shortest length whose Chebyshev
+//   tail is below max(2^-55 max|Phi|, 1e-19) on the interval.
 // t < kT0: series of the entire part plus the singular term.
 // t > t_hi: asymptotic expansion e^{-t}/t (1 + (a-1)/t + (a-1)(a-2)/t^2 + ...).
 // ---------------------------------------------------------------------------
 constexpr int kNC = 16;
-constexpr int kRec = kNC + 2;
+constexpr int kRec = kNC + 4;
 constexpr int kNGeo = 5;
 constexpr double kT0 = 0.5;
 constexpr double kGeoR = 1.4;
@@ -34,11 +38,13 @@ struct alignas(32) G4 {
 
 struct PhiInfo {
   double a;           // order
+  double c_lam;       // t = c_lam |q|^2
   int log_m;          // a = -log_m (log case) or -1
   int two_a;          // 2a (integer)
   double gam;         // Gamma(a) (non-log) or (-1)^m/m! (log)
   double t_geo_end;   // kT0 * kGeoR^kNGeo
   double t_hi;        // end of the tabulated range
+  float t_geo_end_f, t_hi_f;
   int n_int;          // number of intervals
   const double* tab;  // n_int * kRec doubles (device)
   const float* tabf;  // float copy for the mixed form (device)
@@ -67,7 +73,9 @@ struct ReqDesc {
   const float* gboxf;
   // reciprocal space: all h with |A^{-T} h| <= r_recip + max_BZ |k|
   int n_rec;
-  const G4* rec;  // (G_0, G_1, G_2, |G|^2)
+  const G4* rec;      // (G_0, G_1, G_2, |G|^2)
+  const float4* recf; // the same in binary32, for the cutoff screen
+  float R2f, c_lam_f;
   PhiInfo phi[EZ_MAX_NU];
   // quadrature
   const double* u_nodes;
@@ -82,6 +90,7 @@ struct ReqDesc {
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;
   int line0;  // first line (far lines then near lines)
+  unsigned long long* work;  // [2]: in-range reciprocal terms, sum of polynomial lengths
 };
 
 // Work item of a far-field or near-field launch.

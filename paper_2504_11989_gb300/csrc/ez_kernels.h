@@ -11,6 +11,7 @@ struct RecipJob {
   double R2;
   int cap;
   G4* out;
+  float4* outf;
 };
 
 struct GboxJob {
@@ -25,6 +26,7 @@ struct GboxJob {
 
 struct PhiJob {
   double a;
+  double c_lam;
   double t_geo_end;
   int n_int;
   double* out;
@@ -48,6 +50,7 @@ struct EpsteinArgs {
   const double* gbox;
   int n_rec_cap;
   const ReqDesc* rq;  // for n_rec and the reciprocal list
+  float c_lam_f, R2f;
   PhiInfo phi;
   const double* y;
   double* re;

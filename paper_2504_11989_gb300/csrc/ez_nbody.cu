@@ -39,6 +39,20 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[EZ_MAX_PROD], int
   }
 }
 
+// adds the block's work counts to the request's counters (one atomic per warp)
+__device__ __forceinline__ void count_work(const ReqDesc* R, unsigned terms, unsigned coefs) {
+  unsigned long long t = terms, c = coefs;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_down_sync(0xffffffffu, t, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0 && R->work) {
+    atomicAdd(R->work, t);
+    atomicAdd(R->work + 1, c);
+  }
+}
+
 __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd) {
   const int words = (int)(sizeof(PhiInfo) / sizeof(double));
   const double* src = reinterpret_cast<const double*>(R->phi);
@@ -46,31 +60,52 @@ __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd
   for (int i = threadIdx.x; i < nd * words; i += blockDim.x) dst[i] = src[i];
 }
 
-// reciprocal sum at k (x = 0): acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over |G + k| <= R
+// reciprocal sum at k (x = 0): acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over |G + k| <= R.
+// The cutoff test, the branch and the table interval are taken in binary32 (a term
+// within ~1e-7 relative of the cutoff radius may fall either way: it is below the
+// truncation tolerance by the choice of the radius); every value is binary64.
 template <int D>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
-                                          double* acc) {
+                                          const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
   const int nrec = R->n_rec;
-  const double R2 = R->R2_recip, c = R->c_lam;
+  const float R2f = R->R2f, cf = R->c_lam_f;
   const G4* rec = R->rec;
+  const float4* recf = R->recf;
   for (int h = 0; h < nrec; ++h) {
-    const G4 G = ldg_g4(rec + h);
-    double qq;
+    const float4 Gf = __ldg(recf + h);
+    float qqf;
     if (D == 1) {
-      double q0 = G.x + k[0];
-      qq = q0 * q0;
+      const float a = Gf.x + kf[0];
+      qqf = a * a;
     } else if (D == 2) {
-      double q0 = G.x + k[0], q1 = G.y + k[1];
-      qq = fma(q0, q0, q1 * q1);
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1];
+      qqf = fmaf(a, a, b * b);
     } else {
-      double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
-      qq = fma(q0, q0, fma(q1, q1, q2 * q2));
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1], c = Gf.z + kf[2];
+      qqf = fmaf(a, a, fmaf(b, b, c * c));
     }
-    if (qq <= R2) {
-      const double t = c * qq;
+    if (qqf <= R2f) {
+      const G4 G = ldg_g4(rec + h);
+      double qq;
+      if (D == 1) {
+        const double q0 = G.x + k[0];
+        qq = q0 * q0;
+      } else if (D == 2) {
+        const double q0 = G.x + k[0], q1 = G.y + k[1];
+        qq = fma(q0, q0, q1 * q1);
+      } else {
+        const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
+        qq = fma(q0, q0, fma(q1, q1, q2 * q2));
+      }
+      const float tf = cf * qqf;
+      ++terms;
 #pragma unroll
       for (int j = 0; j < EZ_MAX_NU; ++j)
-        if (j < nd) acc[j] += phi_eval(sphi[j], t);
+        if (j < nd) {
+          int n;
+          acc[j] += phi_eval_qq(sphi[j], qq, tf, n);
+          coefs += n;
+        }
     }
   }
 }
@@ -197,6 +232,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
     kcc[i] = R->AiT[i * 3 + ax_c];
   }
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  unsigned terms = 0, coefs = 0;
   const int nn = nv * nv2;
   for (int n = threadIdx.x; n < nn; n += blockDim.x) {
     const int v2l = n / nv, v1 = n - v2l * nv;
@@ -221,12 +257,14 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
         Z[jn] = fma(2.0, sr, b[0].x);
       }
     }
-    recip_sum<3>(R, sphi, nd, k, acc);
+    const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+    recip_sum<3>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
     products(R, nd, np, Z, wv, wsum);
   }
+  count_work(R, terms, coefs);
   block_reduce_store<256>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
@@ -272,6 +310,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
   const double kca0 = R->AiT[0 * 2 + ax_a], kca1 = R->AiT[1 * 2 + ax_a];
   const double kcc0 = R->AiT[0 * 2 + ax_c], kcc1 = R->AiT[1 * 2 + ax_c];
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  unsigned terms = 0, coefs = 0;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const double kta = u * (p1 * R->v_nodes[v]);
     const double wv = R->v_w[v];
@@ -295,12 +334,14 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
-    recip_sum<2>(R, sphi, nd, k, acc);
+    const float kf[2] = {(float)k[0], (float)k[1]};
+    recip_sum<2>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
     products(R, nd, np, Z, wv, wsum);
   }
+  count_work(R, terms, coefs);
   block_reduce_store<128>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
@@ -332,7 +373,9 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], e.x, sr[jn]);
   }
-  recip_sum<1>(R, sphi, nd, k, acc);
+  const float kf[1] = {(float)k[0]};
+  unsigned terms = 0, coefs = 0;
+  recip_sum<1>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
   for (int jn = 0; jn < EZ_MAX_NU; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
@@ -340,6 +383,10 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   products(R, nd, np, Z, w, f);
   double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;
   for (int p = 0; p < np; ++p) o[p] = f[p];
+  if (R->work) {  // some lanes left early: plain atomics, no warp shuffle
+    atomicAdd(R->work, (unsigned long long)terms);
+    atomicAdd(R->work + 1, (unsigned long long)coefs);
+  }
 }
 
 

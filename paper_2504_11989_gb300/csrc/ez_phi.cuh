@@ -122,14 +122,27 @@ __device__ __forceinline__ int phi_interval(float tf, float t_geo_end_f) {
   return i;
 }
 
-__device__ __forceinline__ double phi_table(const PhiInfo& P, double t) {
-  int i = phi_interval((float)t, (float)P.t_geo_end);
-  i = min(i, P.n_int - 1);
-  const double* r = P.tab + (size_t)i * kRec;
-  double x = (t - __ldg(r)) * __ldg(r + 1);
-  double p = __ldg(r + 2 + kNC - 1);
-#pragma unroll
-  for (int k = kNC - 2; k >= 0; --k) p = fma(p, x, __ldg(r + 2 + k));
+// Horner over the kept coefficients in blocks of four (a real loop: the length
+// varies by interval and must not be if-converted into always-issued predicated
+// DFMAs).  Returns the value and the number of coefficients used.
+__device__ __forceinline__ double phi_poly(const double* r, double x, int& n_used) {
+  const int n = __ldg(reinterpret_cast<const int*>(r));
+  n_used = n;
+  const double2* c2 = reinterpret_cast<const double2*>(r + 4);
+  int blk = (n >> 2) - 1;
+  double2 hi = __ldg(c2 + 2 * blk + 1), lo = __ldg(c2 + 2 * blk);
+  double p = fma(hi.y, x, hi.x);
+  p = fma(p, x, lo.y);
+  p = fma(p, x, lo.x);
+#pragma unroll 1
+  for (--blk; blk >= 0; --blk) {
+    hi = __ldg(c2 + 2 * blk + 1);
+    lo = __ldg(c2 + 2 * blk);
+    p = fma(p, x, hi.y);
+    p = fma(p, x, hi.x);
+    p = fma(p, x, lo.y);
+    p = fma(p, x, lo.x);
+  }
   return p;
 }
 
@@ -156,10 +169,27 @@ static __device__ __noinline__ double phi_large(const PhiInfo& P, double t) {
   return exp(-t) * inv * s;
 }
 
+// Phi_a(c |q|^2) from qq = |q|^2 (binary64) and tf ~ c |q|^2 (binary32, used only to
+// pick the branch and the interval).  n_used: coefficients evaluated (work count).
+__device__ __forceinline__ double phi_eval_qq(const PhiInfo& P, double qq, float tf, int& n_used) {
+  if (tf < (float)kT0) {
+    n_used = kNSer;
+    return phi_small(P, P.c_lam * qq);
+  }
+  if (tf > P.t_hi_f) {
+    n_used = kNC;
+    return phi_large(P, P.c_lam * qq);
+  }
+  const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
+  const double* r = P.tab + (size_t)i * kRec;
+  const double2 so = __ldg(reinterpret_cast<const double2*>(r) + 0);  // (n|pad, s) -- s in .y
+  const double o = __ldg(r + 2);
+  return phi_poly(r, fma(qq, so.y, o), n_used);
+}
+
 __device__ __forceinline__ double phi_eval(const PhiInfo& P, double t) {
-  if (t < kT0) return phi_small(P, t);
-  if (t > P.t_hi) return phi_large(P, t);
-  return phi_table(P, t);
+  int n;
+  return phi_eval_qq(P, t / P.c_lam, (float)t, n);
 }
 
 __device__ __forceinline__ G4 ldg_g4(const G4* p) {

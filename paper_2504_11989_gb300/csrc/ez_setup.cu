@@ -48,7 +48,10 @@ __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
     for (int w = 0; w < wid; ++w) off += warp_sums[w];
     if (keep) {
       int pos = base + off + before;
-      if (pos < J.cap) J.out[pos] = G4{G[0], G[1], G[2], G2};
+      if (pos < J.cap) {
+        J.out[pos] = G4{G[0], G[1], G[2], G2};
+        J.outf[pos] = make_float4((float)G[0], (float)G[1], (float)G[2], (float)G2);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -120,6 +123,7 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   }
   const double tm = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
   __shared__ double f[kNC], cj[kNC];
+  __shared__ int nkeep;
   const int k = threadIdx.x;
   const double xk = cospi((k + 0.5) / kNC);
   f[k] = phi_accurate(J.a, tm + h * xk);
@@ -128,17 +132,40 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   for (int q = 0; q < kNC; ++q) s += f[q] * cospi((double)k * (q + 0.5) / kNC);
   cj[k] = (k == 0 ? 1.0 : 2.0) * s / kNC;
   __syncthreads();
-  double b = 0.0;
-  for (int j = k; j < kNC; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
-  double* r = J.out + (size_t)iv * kRec;
-  r[2 + k] = b;
-  if (J.outf) J.outf[(size_t)iv * kRec + 2 + k] = (float)b;
   if (k == 0) {
-    r[0] = tm;
-    r[1] = 1.0 / h;
+    // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance
+    double fm = 0.0;
+    for (int q = 0; q < kNC; ++q) fm = fmax(fm, fabs(f[q]));
+    const double tol = fmax(fm / 36028797018963968.0, 1e-19);  // 2^-55 relative, 1e-19 absolute
+    int n = kNC;
+    for (int cand = 4; cand < kNC; cand += 4) {
+      double tail = 0.0;
+      for (int q = cand; q < kNC; ++q) tail += fabs(cj[q]);
+      if (tail <= tol) {
+        n = cand;
+        break;
+      }
+    }
+    nkeep = n;
+  }
+  __syncthreads();
+  const int n = nkeep;
+  double b = 0.0;
+  if (k < n)
+    for (int j = k; j < n; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
+  double* r = J.out + (size_t)iv * kRec;
+  r[4 + k] = b;
+  if (J.outf) J.outf[(size_t)iv * kRec + 4 + k] = (float)b;
+  if (k == 0) {
+    reinterpret_cast<int*>(r)[0] = n;
+    reinterpret_cast<int*>(r)[1] = 0;
+    r[1] = J.c_lam / h;
+    r[2] = -tm / h;
+    r[3] = 0.0;
     if (J.outf) {
-      J.outf[(size_t)iv * kRec] = (float)tm;
-      J.outf[(size_t)iv * kRec + 1] = (float)(1.0 / h);
+      reinterpret_cast<int*>(J.outf + (size_t)iv * kRec)[0] = n;
+      J.outf[(size_t)iv * kRec + 1] = (float)(J.c_lam / h);
+      J.outf[(size_t)iv * kRec + 2] = (float)(-tm / h);
     }
   }
 }

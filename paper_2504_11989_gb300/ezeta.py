@@ -86,6 +86,8 @@ def lib():
             L.ez_batch_destroy.argtypes = [vp]
             L.ez_batch_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]
+            L.ez_batch_far_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_longlong)]
             L.ez_batch_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
             L.ez_diag_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
             L.ez_layout.argtypes = [ctypes.c_int, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
@@ -278,6 +280,12 @@ class Batch:
         f, t = ctypes.c_float(), ctypes.c_float()
         _check(lib().ez_batch_timing(self.handle, 1 if enable else 0, ctypes.byref(f), ctypes.byref(t)))
         return f.value, t.value
+
+    def far_flops(self):
+        """(algorithmic FP64 flops of the far kernels of the last run, reciprocal terms, coefficients)."""
+        f, t, c = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().ez_batch_far_flops(self.handle, ctypes.byref(f), ctypes.byref(t), ctypes.byref(c)))
+        return f.value, t.value, c.value
 
     def sizes(self):
         """(device bytes, host staging bytes) of the batch."""

@@ -198,3 +198,31 @@ def test_sum_errors(ez):
     with pytest.raises(ez.EzError) as e:
         ez.ez_lattice_sum_nbody(L, [3.0], ez.quadrature(W.config2(16), n_u=0))
     assert e.value.code == ez.EZ_EINVAL
+
+
+def test_mixed_batch_equals_single_requests(ez, oracle_mod):
+    """A batch mixing d = 1, 2, 3, far-only and eps-split sums gives every sum exactly
+    its single-request value (requests are independent inside a launch)."""
+    probs = [
+        W.nbody_problem("hexagonal", 3.0, 4, W.config2(24)),
+        W.atm_problem("Z", W.Quad(n_u=8, n_v=1, u_rule=2, lam=1.0, r_real=8, r_recip=8)),
+        W.atm_problem("fcc", W.Quad(n_u=2, n_v=6, u_rule=2, lam=1.0, r_real=4.5, r_recip=4.5)),
+        W.nbody_problem("Z", 6.0, 2, W.config1(200)),
+        W.nbody_problem("square", 4.0, 2, W.Quad(n_u=5, n_v=12, u_rule=2, lam=1.1, r_real=6, r_recip=5)),
+        W.nbody_problem("bcc", 6.0, 3, W.Quad(n_u=4, n_v=17, lam=1.0, r_real=4.5, r_recip=4.5)),
+    ]
+    lats = [ez.Lattice(p.A) for p in probs]
+    specs = [ez.sum_spec(p.nu, p.expo) for p in probs]
+    quads = [ez.quadrature(p.quad) for p in probs]
+    many, lines, offs = ez.ez_lattice_sums(lats, specs, quads, lines=True)
+    b = ez.Batch(lats, specs, quads)
+    again = b.run()
+    assert np.array_equal(again, many)
+    for i, p in enumerate(probs):
+        one, one_lines, one_offs = ez.ez_lattice_sums([lats[i]], [specs[i]], [quads[i]], lines=True)
+        assert np.array_equal(one[0], many[i]), (i, one[0], many[i])
+        assert np.array_equal(one_lines, lines[offs[i]: offs[i + 1]])
+    # and against the oracle
+    for i, p in enumerate(probs):
+        ref = oracle_mod.nbody(p, threads=16)
+        assert _close(many[i, : len(ref)], ref), (p.name, many[i], ref)
