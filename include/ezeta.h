@@ -103,6 +103,25 @@ int ez_lattice_destroy(ez_lattice lat);
 int ez_epstein_zeta(ez_lattice lat, double nu, const double* x, const double* y, size_t m,
                     double* re, double* im, int prec, void* stream);
 
+/* Same values as ez_epstein_zeta, computed without allocating anything.  The paper
+ * has no counterpart: this serves callers that cannot allocate device memory when
+ * they need a value -- code running inside an allocator or a memory-pool callback,
+ * real-time threads that must stay out of the driver's allocator (cudaMalloc can
+ * synchronise the device and take locks), processes whose device memory is fully
+ * reserved by another framework.  All scratch (descriptors, reciprocal-lattice
+ * list, real-space box, Phi table, pole flag) lives in one static device array of
+ * 256 KiB that every GPU loading this library holds until the process exits.
+ *   y, re, im : DEVICE buffers only (EZ_EINVAL otherwise); x : host, d doubles.
+ * A lattice/exponent whose tables exceed 256 KiB is rejected with EZ_EINVAL and a
+ * message giving the size (use ez_epstein_zeta for it).  The first call on each
+ * device resolves the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call reuses the same array and leaves its
+ * contents behind (the pole flag is cleared at the start of each call); calls that
+ * overlap on the GPU -- other streams or other host threads -- race on it.  The call
+ * synchronises `stream` to read the pole flag. */
+int ez_epstein_zeta_static(ez_lattice lat, double nu, const double* x, const double* y, size_t m,
+                           double* re, double* im, void* stream);
+
 /* --- n-body zeta function (Def. "Many-body zeta function") ------------------- */
 /* zeta^(n)_Lambda(nu_1..nu_n) through the Epstein representation and the Duffy
  * transformation (Cor. "Duffy transformation"), with the eps-split meromorphic

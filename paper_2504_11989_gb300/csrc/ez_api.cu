@@ -1354,3 +1354,211 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   if (status) return fail(EZ_EDOMAIN, "some y lie in the reciprocal lattice with nu <= d (pole)");
   return EZ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Epstein zeta with a static scratch area (no allocation at all).
+//
+// Some callers cannot allocate device memory at the moment they need a value:
+// code running inside an allocator or a memory-pool callback, real-time threads
+// that must not enter the driver's allocator (cudaMalloc can synchronise the
+// device and take locks), and processes whose device memory is fully reserved
+// by another framework.  This entry point computes what ez_epstein_zeta computes
+// but keeps every piece of scratch (descriptors, reciprocal-lattice list,
+// real-space box, Phi table, status flag) in the file-scope array below, which
+// every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticScratchBytes = 256 * 1024;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[64] = {nullptr};  // device address of g_static_scratch, per device ordinal
+
+// Resolves the device address of the static scratch on the current device (first call
+// per device only).  In host code the symbol is a host-side stand-in, never a device address.
+int static_scratch_address(void** out) {
+  int dev = 0;
+  EZ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(EZ_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(EZ_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return EZ_OK;
+}
+}  // namespace
+
+extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, const double* y, size_t m,
+                                      double* re, double* im, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!L || !x || (m && (!y || !re))) return fail(EZ_EINVAL, "NULL argument");
+  if (m == 0) return EZ_OK;
+  if (m > (size_t)1 << 31) return fail(EZ_EINVAL, "m too large");
+  if (!is_device_ptr(y) || !is_device_ptr(re) || (im && !is_device_ptr(im)))
+    return fail(EZ_EINVAL, "ez_epstein_zeta_static takes device buffers for y, re and im "
+                           "(host buffers would need staging memory)");
+  if (!std::isfinite(nu) || !is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
+  if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
+  int rc = init_constants();
+  if (rc) return rc;
+  const int d = L->d;
+  ez_sum_spec s;
+  std::memset(&s, 0, sizeof s);
+  s.n_distinct = 1;
+  s.nu[0] = nu;
+  s.n_prod = 1;
+  s.expo[0][0] = 1;
+  ez_quadrature q;
+  ez_quadrature_default(&q);
+  q.n_u = 1;
+  q.n_v = 1;
+  q.u_rule = 1;
+  Plan p;
+  rc = make_plan(L, s, q, p);
+  if (rc) return rc;
+  double xt[3] = {0, 0, 0};
+  int mx[3] = {0, 0, 0};
+  bool x_in = true;
+  for (int i = 0; i < d; ++i) {
+    double v = 0.0;
+    for (int j = 0; j < d; ++j) v += L->Ai[i * d + j] * x[j];
+    xt[i] = v;
+    mx[i] = (int)std::lrint(v);
+    if (std::fabs(v - mx[i]) > 1e-12) x_in = false;
+  }
+  p.cells = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i < d) {
+      double rn = 0.0;
+      for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+      p.M[i] = (int)std::ceil(p.r_real * std::sqrt(rn) + 0.5 + 1e-9);
+      if (p.M[i] > 24) return fail(EZ_EINVAL, "real-space box too large");
+    }
+    p.box[i] = 2 * p.M[i] + 1;
+    p.cells *= p.box[i];
+  }
+  Layout dl;
+  const size_t o_req = dl.take(sizeof(ReqDesc));
+  const size_t o_rj = dl.take(sizeof(RecipJob));
+  const size_t o_gj = dl.take(sizeof(GboxJob));
+  const size_t o_pj = dl.take(sizeof(PhiJob));
+  const size_t o_rec = dl.take(sizeof(G4) * p.rcap);
+  const size_t o_recf = dl.take(sizeof(float4) * p.rcap);
+  const size_t o_gbox = dl.take(sizeof(double) * p.cells);
+  const size_t o_tab = dl.take(sizeof(double) * kRec * p.phi[0].n_int);
+  const size_t o_st = dl.take(sizeof(int));
+  if (dl.off > kStaticScratchBytes)
+    return fail(EZ_EINVAL, "this lattice and exponent need %zu bytes of scratch; the static area of "
+                           "ez_epstein_zeta_static holds %zu bytes (use ez_epstein_zeta)",
+                dl.off, kStaticScratchBytes);
+  void* base = nullptr;
+  rc = static_scratch_address(&base);
+  if (rc) return rc;
+  char* D = (char*)base;
+  // descriptors on the host stack, copied into the static area (pageable copies are
+  // staged by the driver before cudaMemcpyAsync returns)
+  ReqDesc R;
+  std::memset(&R, 0, sizeof R);
+  R.d = d;
+  R.n_distinct = 1;
+  R.nu[0] = nu;
+  std::memcpy(R.A, L->A, sizeof R.A);
+  std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+  R.lam = p.lam;
+  for (int i = 0; i < 3; ++i) {
+    R.M[i] = p.M[i];
+    R.box[i] = p.box[i];
+  }
+  R.rec = (const G4*)(D + o_rec);
+  R.gbox = (const double*)(D + o_gbox);
+  RecipJob RJ;
+  std::memset(&RJ, 0, sizeof RJ);
+  RJ.req = 0;
+  for (int i = 0; i < 3; ++i) {
+    RJ.lo[i] = p.rlo[i];
+    RJ.ext[i] = p.rext[i];
+  }
+  RJ.R2 = p.R2enum;
+  RJ.cap = (int)p.rcap;
+  RJ.out = (G4*)(D + o_rec);
+  RJ.outf = (float4*)(D + o_recf);
+  GboxJob GJ;
+  std::memset(&GJ, 0, sizeof GJ);
+  GJ.req = 0;
+  for (int i = 0; i < d; ++i) {
+    GJ.x[i] = x[i];
+    GJ.mx[i] = mx[i];
+  }
+  GJ.x_in_lattice = x_in ? 1 : 0;
+  GJ.R2 = p.r_real * p.r_real;
+  GJ.out = (double*)(D + o_gbox);
+  PhiJob PJ;
+  std::memset(&PJ, 0, sizeof PJ);
+  PJ.a = p.phi[0].a;
+  PJ.c_lam = kPi * p.lam * p.lam;
+  PJ.t_geo_end = p.phi[0].t_geo_end;
+  PJ.n_int = p.phi[0].n_int;
+  PJ.out = (double*)(D + o_tab);
+  EZ_CUDA(cudaMemcpyAsync(D + o_req, &R, sizeof R, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemcpyAsync(D + o_rj, &RJ, sizeof RJ, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemcpyAsync(D + o_gj, &GJ, sizeof GJ, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemcpyAsync(D + o_pj, &PJ, sizeof PJ, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemsetAsync(D + o_st, 0, sizeof(int), stream));  // the pole flag must start at zero
+  enum_recip_kernel<<<1, 512, 0, stream>>>((ReqDesc*)(D + o_req), (const RecipJob*)(D + o_rj));
+  EZ_LAUNCHED();
+  gbox_kernel<<<dim3((unsigned)((p.cells + 255) / 256), 1), 256, 0, stream>>>((const ReqDesc*)(D + o_req),
+                                                                              (const GboxJob*)(D + o_gj), 1);
+  EZ_LAUNCHED();
+  phitab_kernel<<<dim3(p.phi[0].n_int, 1), kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
+  EZ_LAUNCHED();
+  EpsteinArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.d = d;
+  A.m = (int)m;
+  A.nu = nu;
+  A.pref = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
+  A.vol_fac = std::pow(p.lam, d) / L->V;
+  A.c_lam = kPi * p.lam * p.lam;
+  A.lam = p.lam;
+  A.R2_recip = p.r_recip * p.r_recip;
+  A.two_over_nu = 2.0 / nu;
+  std::memcpy(A.A, L->A, sizeof A.A);
+  std::memcpy(A.AiT, L->AiT, sizeof A.AiT);
+  std::memcpy(A.At, L->At, sizeof A.At);
+  for (int i = 0; i < d; ++i) {
+    A.x[i] = x[i];
+    A.xt[i] = xt[i];
+    A.mx[i] = mx[i];
+  }
+  A.x_in_lattice = x_in ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    A.M[i] = p.M[i];
+    A.box[i] = p.box[i];
+  }
+  A.gbox = (const double*)(D + o_gbox);
+  A.rq = (const ReqDesc*)(D + o_req);
+  A.phi = p.phi[0];
+  A.phi.c_lam = A.c_lam;
+  A.phi.tab = (const double*)(D + o_tab);
+  A.c_lam_f = (float)A.c_lam;
+  A.R2f = (float)A.R2_recip;
+  A.y = y;
+  A.re = re;
+  A.im = im;
+  A.status = (int*)(D + o_st);
+  epstein_kernel<<<(unsigned)((m + 127) / 128), 128, 0, stream>>>(A);
+  EZ_LAUNCHED();
+  int status = 0;
+  EZ_CUDA(cudaMemcpyAsync(&status, D + o_st, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EZ_CUDA(cudaStreamSynchronize(stream));
+  if (status) return fail(EZ_EDOMAIN, "some y lie in the reciprocal lattice with nu <= d (pole)");
+  return EZ_OK;
+}

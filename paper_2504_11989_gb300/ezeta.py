@@ -72,6 +72,7 @@ def lib():
             L.ez_lattice_destroy.argtypes = [vp]
             L.ez_quadrature_default.argtypes = [ctypes.POINTER(ez_quadrature)]
             L.ez_epstein_zeta.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, ctypes.c_int, vp]
+            L.ez_epstein_zeta_static.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, vp]
             L.ez_lattice_sum_nbody.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ez_quadrature), vp, vp]
             L.ez_atm_energy.argtypes = [vp, ctypes.POINTER(ez_quadrature), dp, dp, vp]
             L.ez_lattice_sums.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
@@ -192,6 +193,19 @@ def ez_epstein_zeta(lat: Lattice, nu: float, x, y, re=None, im=None, prec: int =
     ip, _ = _ptr(im)
     _check(lib().ez_epstein_zeta(lat.handle, float(nu), xv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), yp,
                                  int(m), rp, ip, int(prec), _stream_ptr(stream)))
+    return re, im
+
+
+def ez_epstein_zeta_static(lat: Lattice, nu: float, x, y, re, im=None, stream=None):
+    """Z_{Lambda,nu}(x, y_i) without any allocation: y, re, im are CUDA tensors owned by
+    the caller; the library's scratch is a 256 KiB static device array (see ezeta.h)."""
+    xv = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
+    m = y.shape[0] if y.dim() > 1 else y.numel() // lat.d
+    yp, _ = _ptr(y)
+    rp, _ = _ptr(re)
+    ip, _ = _ptr(im)
+    _check(lib().ez_epstein_zeta_static(lat.handle, float(nu), xv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        yp, int(m), rp, ip, _stream_ptr(stream)))
     return re, im
 
 
