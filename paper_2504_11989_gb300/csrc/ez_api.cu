@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ez_kernels.h"
+#include "ez_phi.cuh"
 
 using namespace ez;
 
@@ -177,6 +178,24 @@ static void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>&
   }
 }
 
+// rules are reused across calls (planning a batch of sums must not recompute them)
+static void gauss_legendre01_cached(int n, std::vector<double>& x, std::vector<double>& w) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::vector<double>, std::vector<double>>> cache;  // index n
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cache.size() > n && !cache[n].first.empty()) {
+      x = cache[n].first;
+      w = cache[n].second;
+      return;
+    }
+  }
+  gauss_legendre01(n, x, w);
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)cache.size() <= n) cache.resize(n + 1);
+  cache[n] = {x, w};
+}
+
 // ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------
@@ -331,7 +350,6 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.ell > 8) return fail(EZ_EINVAL, "ell = %d > 8", p.ell);
   p.prec = q.prec;
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
-  if (p.prec == EZ_MIXED) return fail(EZ_EUNSUPPORTED, "mixed precision not built yet");
   p.lam = q.lambda > 0.0 ? q.lambda : std::pow(L->V, 1.0 / d);
   p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(kTcut / kPi);
   p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(kTcut / kPi) / p.lam;
@@ -381,7 +399,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
 
   // quadrature rules
   std::vector<double> x, w;
-  gauss_legendre01(q.n_u, x, w);
+  gauss_legendre01_cached(q.n_u, x, w);
   if (p.u_rule == 1) {
     p.un.resize(q.n_u);
     p.uw.resize(q.n_u);
@@ -402,7 +420,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   }
   p.n_ui = (int)p.un.size();
   if (d > 1) {
-    gauss_legendre01(p.n_v, p.vn, p.vw);
+    gauss_legendre01_cached(p.n_v, p.vn, p.vw);
   } else {
     p.vn.assign(1, 0.0);
     p.vw.assign(1, 1.0);
@@ -413,6 +431,61 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   for (int j = 0; j < spec.n_distinct; ++j) {
     fill_phi_host(p.phi[j], 0.5 * (d - spec.nu[j]), c_lam * p.r_recip * p.r_recip);
     fill_rser(p.rser[j], 0.5 * (d - spec.nu[j]), p.lam, 15);
+  }
+
+  // mixed form: t_mix = first t beyond which every |Phi_a(t)| t <= 1e-7, t_mid = first t
+  // beyond which every |Phi_a(t)| <= 1e-6 (all exponents of the sum)
+  if (p.prec == EZ_MIXED) {
+    double tmix = kT0, tmid = kT0;
+    for (int j = 0; j < spec.n_distinct; ++j) {
+      const double a = p.phi[j].a;
+      double bad_mix = kT0, bad_mid = kT0;
+      for (double t = kT0; t <= p.phi[j].t_hi; t += 0.25) {
+        const double f = std::fabs(phi_accurate(a, t));
+        if (f * t > 1e-7) bad_mix = t;
+        if (f > 1e-6) bad_mid = t;
+      }
+      tmix = std::max(tmix, bad_mix + 0.25);
+      tmid = std::max(tmid, bad_mid + 0.25);
+    }
+    tmid = std::min(tmid, tmix);
+    tmix = (double)(float)tmix;
+    for (int j = 0; j < spec.n_distinct; ++j) {
+      p.phi[j].t_mix_f = (float)tmix;
+      p.phi[j].t_mid_f = (float)tmid;
+      // tail fit: g(s) = t e^t Phi_a(t), s = tmix/t in (0, 1], Chebyshev interpolation at
+      // 24 points in x = 2s - 1, truncated to degree 7 and rewritten in powers of s
+      const int N = 24;
+      double gv[N], cc[N];
+      for (int k = 0; k < N; ++k) {
+        const double xk = std::cos(kPi * (k + 0.5) / N);
+        const double sk = 0.5 * (xk + 1.0);
+        gv[k] = phi_scaled_large(p.phi[j].a, tmix / sk);
+      }
+      for (int q = 0; q < N; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += gv[k] * std::cos(kPi * q * (k + 0.5) / N);
+        cc[q] = (q == 0 ? 1.0 : 2.0) * acc / N;
+      }
+      // sum_{q<8} cc[q] T_q(2s - 1) -> powers of s
+      double Tm[8][8] = {{0}};  // Tm[q][i]: coefficient of s^i in T_q(2s - 1)
+      Tm[0][0] = 1.0;
+      Tm[1][0] = -1.0;
+      Tm[1][1] = 2.0;
+      for (int q = 2; q < 8; ++q)
+        for (int i = 0; i < 8; ++i) {
+          double v = -Tm[q - 2][i] - 2.0 * Tm[q - 1][i];
+          if (i > 0) v += 4.0 * Tm[q - 1][i - 1];
+          Tm[q][i] = v;
+        }
+      for (int i = 0; i < 8; ++i) {
+        double v = 0.0;
+        for (int q = i; q < 8; ++q) v += cc[q] * Tm[q][i];
+        p.phi[j].tail_p[i] = (float)v;
+      }
+    }
+  } else {
+    for (int j = 0; j < spec.n_distinct; ++j) p.phi[j].t_mix_f = p.phi[j].t_mid_f = 3.0e38f;
   }
 
   // near part
@@ -568,7 +641,8 @@ struct ez_batch_s {
   char* d = nullptr;
   char* h = nullptr;
   size_t dbytes = 0, hbytes = 0;
-  size_t o_work = 0;
+  size_t o_work = 0, o_phj = 0;
+  int n_phase = 0, max_phase_pairs = 0;
   size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
   int n_phi = 0, n_tay = 0;
@@ -658,10 +732,39 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_rl0 = hl.take(sizeof(long long) * n_req);
   B.o_rnl = dl.take(sizeof(int) * n_req);
   const size_t h_rnl = hl.take(sizeof(int) * n_req);
+  // phase tables: one per distinct (d, u rule, n_u, eps, n_v) among the d <= 2 sums
+  std::vector<int> phase_of(n_req, -1), phase_rep, phase_mp1;
+  for (int r = 0; r < n_req; ++r) {
+    const Plan& p = plans[r];
+    if (p.d > 2) continue;
+    int Mx = std::max(p.M[0], p.d > 1 ? p.M[1] : 0);
+    int g = -1;
+    for (int q = 0; q < (int)phase_rep.size(); ++q) {
+      const Plan& o = plans[phase_rep[q]];
+      if (o.d == p.d && o.u_rule == p.u_rule && o.n_ui == p.n_ui && o.n_v == p.n_v && o.eps == p.eps &&
+          o.un == p.un) {
+        g = q;
+        break;
+      }
+    }
+    if (g < 0) {
+      g = (int)phase_rep.size();
+      phase_rep.push_back(r);
+      phase_mp1.push_back(Mx + 1);
+    }
+    phase_mp1[g] = std::max(phase_mp1[g], Mx + 1);
+    phase_of[r] = g;
+  }
+  B.n_phase = (int)phase_rep.size();
+  B.max_phase_pairs = 0;
+  for (int g = 0; g < B.n_phase; ++g)
+    B.max_phase_pairs = std::max(B.max_phase_pairs, plans[phase_rep[g]].n_ui * plans[phase_rep[g]].n_v);
+  B.o_phj = dl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
+  const size_t h_phj = hl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
   std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
-  std::vector<std::vector<size_t>> o_tab(n_req);
+  std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
     o_un[r] = dl.take(sizeof(double) * p.n_ui);
@@ -688,9 +791,15 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_recf[r] = dl.take(sizeof(float4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
+    for (int j = 0; j < p.spec.n_distinct; ++j) o_tabf[r].push_back(dl.take(sizeof(float) * kRec * p.phi[j].n_int));
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
+  }
+  std::vector<size_t> o_phase(B.n_phase);
+  for (int g = 0; g < B.n_phase; ++g) {
+    const Plan& p = plans[phase_rep[g]];
+    o_phase[g] = dl.take(sizeof(double2) * (size_t)p.n_ui * p.n_v * phase_mp1[g]);
   }
   B.o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
   B.o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
@@ -744,18 +853,20 @@ int batch_layout(ez_batch_s& B, bool fill) {
     for (int j = 0; j < p.spec.n_distinct; ++j) {
       double nu = p.spec.nu[j];
       R.nu[j] = nu;
+      R.two_over_nu[j] = 2.0 / nu;
       R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
       R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
       R.phi[j] = p.phi[j];
       R.phi[j].c_lam = R.c_lam;
       R.phi[j].tab = (const double*)dptr(o_tab[r][j]);
+      R.phi[j].tabf = (const float*)dptr(o_tabf[r][j]);
       PhiJob& J = pjobs[ipj++];
       J.a = p.phi[j].a;
       J.c_lam = R.c_lam;
       J.t_geo_end = p.phi[j].t_geo_end;
       J.n_int = p.phi[j].n_int;
       J.out = (double*)dptr(o_tab[r][j]);
-      J.outf = nullptr;
+      J.outf = (float*)dptr(o_tabf[r][j]);
     }
     for (int i = 0; i < 3; ++i) {
       R.M[i] = p.M[i];
@@ -772,6 +883,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.u_w = (const double*)dptr(o_uw[r]);
     R.v_nodes = (const double*)dptr(o_vn[r]);
     R.v_w = (const double*)dptr(o_vw[r]);
+    if (phase_of[r] >= 0) {
+      R.phase = (const double2*)dptr(o_phase[phase_of[r]]);
+      R.phase_mp1 = phase_mp1[phase_of[r]];
+    }
     std::memcpy(Hs + h_un[r], p.un.data(), sizeof(double) * p.n_ui);
     std::memcpy(Hs + h_uw[r], p.uw.data(), sizeof(double) * p.n_ui);
     std::memcpy(Hs + h_vn[r], p.vn.data(), sizeof(double) * p.vn.size());
@@ -809,6 +924,19 @@ int batch_layout(ez_batch_s& B, bool fill) {
         std::memcpy(T.rser, p.rser[j], sizeof T.rser);
         T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
       }
+  }
+  {
+    PhaseJob* phj = (PhaseJob*)(Hs + h_phj);
+    for (int g = 0; g < B.n_phase; ++g) {
+      const int r = phase_rep[g];
+      const Plan& p = plans[r];
+      phj[g].n_ui = p.n_ui;
+      phj[g].n_v = p.d == 1 ? 1 : p.n_v;
+      phj[g].mp1 = phase_mp1[g];
+      phj[g].u = (const double*)dptr(o_un[r]);
+      phj[g].v = p.d == 1 ? nullptr : (const double*)dptr(o_vn[r]);
+      phj[g].out = (double2*)dptr(o_phase[g]);
+    }
   }
   // items (far: grouped by d; near after)
   size_t ii = 0;
@@ -888,6 +1016,11 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
     phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
     taylor_kernel<<<(tot_alpha + 63) / 64, 64, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
+    EZ_LAUNCHED();
+  }
+  if (B.n_phase) {
+    phase_kernel<<<dim3((unsigned)((B.max_phase_pairs + 127) / 128), B.n_phase), 128, 0, stream>>>(
+        (const PhaseJob*)dptr(B.o_phj));
     EZ_LAUNCHED();
   }
   Item* ditems = (Item*)dptr(B.o_items);

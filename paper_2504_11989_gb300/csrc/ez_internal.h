@@ -28,7 +28,7 @@ constexpr int kRec = kNC + 4;
 constexpr int kNGeo = 5;
 constexpr double kT0 = 0.5;
 constexpr double kGeoR = 1.4;
-constexpr int kNSer = 22;
+constexpr int kNSer = 16;  // t < 1/2: 0.5^16/16! ~ 7e-19
 constexpr int kMaxInt = 320;  // intervals per table (t_hi <= ~316)
 
 // reciprocal-space record: (G_0, G_1, G_2, |G|^2) with G = A^{-T} h
@@ -45,9 +45,12 @@ struct PhiInfo {
   double t_geo_end;   // kT0 * kGeoR^kNGeo
   double t_hi;        // end of the tabulated range
   float t_geo_end_f, t_hi_f;
+  float t_mix_f;      // mixed form: terms with t >= t_mix_f are evaluated in binary32
+  float t_mid_f;      // mixed form: t_mid_f <= t < t_mix_f: binary64 argument, binary32 polynomial
+  float tail_p[8];    // mixed form, t >= t_mix_f: Phi_a(t) = e^{-t} t^{-1} sum_k tail_p[k] (t_mix_f/t)^k
   int n_int;          // number of intervals
   const double* tab;  // n_int * kRec doubles (device)
-  const float* tabf;  // float copy for the mixed form (device)
+  const float* tabf;  // binary32 table (own polynomial lengths) for the mixed form (device)
   double ser[kNSer];  // entire part for t < kT0
 };
 
@@ -64,7 +67,7 @@ struct ReqDesc {
   int expo[EZ_MAX_PROD][EZ_MAX_NU];
   double A[9], AiT[9];
   double V, lam, c_lam, vol_fac, R2_recip, eps;
-  double nu[EZ_MAX_NU], pref[EZ_MAX_NU];
+  double nu[EZ_MAX_NU], pref[EZ_MAX_NU], two_over_nu[EZ_MAX_NU];
   double sig[EZ_MAX_NU];  // singular coefficient sigma_nu of s_hat
   int islog[EZ_MAX_NU];
   // real space: full box prod_i (2 M_i + 1), g = 0 outside the ball and at m = 0
@@ -82,6 +85,10 @@ struct ReqDesc {
   const double* u_w;
   const double* v_nodes;
   const double* v_w;
+  // d <= 2: powers e^{2 pi i m u v}, m = 0..phase_mp1-1, per (u node, v node); shared by every
+  // sum of a batch with the same quadrature (the phases do not depend on the lattice)
+  const double2* phase;
+  int phase_mp1;
   // near part
   int n_alpha;            // multi-indices with |alpha| even <= 2 ell
   const int* alpha;       // [n_alpha][3]

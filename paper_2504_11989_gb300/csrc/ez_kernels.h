@@ -40,6 +40,13 @@ struct TaylorJob {
   double* out;    // [n_alpha]
 };
 
+struct PhaseJob {
+  int n_ui, n_v, mp1;
+  const double* u;
+  const double* v;  // NULL for d = 1 (v = 1)
+  double2* out;     // [n_ui][n_v][mp1]
+};
+
 struct EpsteinArgs {
   int d, m;
   double nu, pref, vol_fac, c_lam, lam, R2_recip, two_over_nu;
@@ -73,6 +80,7 @@ __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const lon
 __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines,
                              int n_req, const double* lines, double* out);
 __global__ void epstein_kernel(EpsteinArgs args);
+__global__ void phase_kernel(const PhaseJob* jobs);
 
 size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v);
 cudaError_t upload_cheb2mono(const double* host_matrix);  // kNC x kNC

@@ -63,14 +63,23 @@ __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd
 // reciprocal sum at k (x = 0): acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over |G + k| <= R.
 // The cutoff test, the branch and the table interval are taken in binary32 (a term
 // within ~1e-7 relative of the cutoff radius may fall either way: it is below the
-// truncation tolerance by the choice of the radius); every value is binary64.
-template <int D>
+// truncation tolerance by the choice of the radius).  FP64 form: every value is
+// binary64.  Mixed form (MIXED): terms with t >= t_mix (|Phi| t <= 1e-7 beyond it) are
+// evaluated in binary32; terms with t_mid <= t < t_mix (|Phi| <= 1e-6) get their argument
+// in binary64 and their polynomial in binary32; both are summed in binary32 with Kahan
+// compensation.  The rest (and the h = 0 term near k = 0) stays binary64.
+template <int D, bool MIXED>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
   const int nrec = R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
+  const float tmix = MIXED ? sphi[0].t_mix_f : 0.0f;
+  const float tmid = MIXED ? sphi[0].t_mid_f : 0.0f;
   const G4* rec = R->rec;
   const float4* recf = R->recf;
+  float sf[EZ_MAX_NU], cpf[EZ_MAX_NU];
+#pragma unroll
+  for (int j = 0; j < EZ_MAX_NU; ++j) sf[j] = cpf[j] = 0.0f;
   for (int h = 0; h < nrec; ++h) {
     const float4 Gf = __ldg(recf + h);
     float qqf;
@@ -85,6 +94,18 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
       qqf = fmaf(a, a, fmaf(b, b, c * c));
     }
     if (qqf <= R2f) {
+      const float tf = cf * qqf;
+      if (MIXED && tf >= tmix) {
+#pragma unroll
+        for (int j = 0; j < EZ_MAX_NU; ++j)
+          if (j < nd) {  // Kahan: sf + cpf carries the tail sum
+            const float y = phi_tail_f(sphi[j], tf) - cpf[j];
+            const float t = sf[j] + y;
+            cpf[j] = (t - sf[j]) - y;
+            sf[j] = t;
+          }
+        continue;
+      }
       const G4 G = ldg_g4(rec + h);
       double qq;
       if (D == 1) {
@@ -97,7 +118,17 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
         qq = fma(q0, q0, fma(q1, q1, q2 * q2));
       }
-      const float tf = cf * qqf;
+      if (MIXED && tf >= tmid) {
+#pragma unroll
+        for (int j = 0; j < EZ_MAX_NU; ++j)
+          if (j < nd) {
+            const float y = phi_eval_mid(sphi[j], qq, tf) - cpf[j];
+            const float t = sf[j] + y;
+            cpf[j] = (t - sf[j]) - y;
+            sf[j] = t;
+          }
+        continue;
+      }
       ++terms;
 #pragma unroll
       for (int j = 0; j < EZ_MAX_NU; ++j)
@@ -108,6 +139,20 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         }
     }
   }
+  if (MIXED) {
+#pragma unroll
+    for (int j = 0; j < EZ_MAX_NU; ++j)
+      if (j < nd) acc[j] += (double)sf[j] - (double)cpf[j];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void recip_any(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
+                                          const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
+  if (R->prec == EZ_MIXED)
+    recip_sum<D, true>(R, sphi, nd, k, kf, acc, terms, coefs);
+  else
+    recip_sum<D, false>(R, sphi, nd, k, kf, acc, terms, coefs);
 }
 
 __device__ __forceinline__ void products(const ReqDesc* R, int nd, int np, const double* Z, double w,
@@ -258,10 +303,10 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       }
     }
     const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-    recip_sum<3>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_any<3>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
-      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
     products(R, nd, np, Z, wv, wsum);
   }
   count_work(R, terms, coefs);
@@ -315,30 +360,30 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
     const double kta = u * (p1 * R->v_nodes[v]);
     const double wv = R->v_w[v];
     double k[2] = {fma(kca0, kta, kcc0 * u), fma(kca1, kta, kcc1 * u)};
-    double sn, cs;
-    sincospi(2.0 * kta, &sn, &cs);
-    const double2 e1 = make_double2(cs, sn);
+    // e^{2 pi i ma kta} = (e^{2 pi i ma u v})^* for p1 = -1: conjugation is exact in the table
+    const double2* ph = R->phase + ((size_t)it.iu * nv + v) * R->phase_mp1;
+    const double sgn = p1;
     double sr[EZ_MAX_NU], Z[EZ_MAX_NU], acc[EZ_MAX_NU];
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
-    double2 e = make_double2(1.0, 0.0);
     for (int ma = 1; ma <= Ma; ++ma) {
-      e = cmul(e, e1);
+      const double2 e = ph[ma];
+      const double ey = sgn * e.y;
 #pragma unroll
       for (int jn = 0; jn < EZ_MAX_NU; ++jn)
         if (jn < nd) {
           const double2 hh = H[jn * (Ma + 1) + ma];
-          sr[jn] = fma(e.x, hh.x, fma(-e.y, hh.y, sr[jn]));
+          sr[jn] = fma(e.x, hh.x, fma(-ey, hh.y, sr[jn]));
         }
     }
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_sum<2>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_any<2>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
-      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
     products(R, nd, np, Z, wv, wsum);
   }
   count_work(R, terms, coefs);
@@ -360,25 +405,22 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   const double w = 2.0 * R->u_w[iu];
   const int M = R->M[0];
   double k[1] = {R->AiT[0] * u};
-  double sn, cs;
-  sincospi(2.0 * u, &sn, &cs);
-  const double2 e1 = make_double2(cs, sn);
-  double2 e = make_double2(1.0, 0.0);
+  const double2* ph = R->phase + (size_t)iu * R->phase_mp1;
   double sr[EZ_MAX_NU], acc[EZ_MAX_NU], Z[EZ_MAX_NU];
 #pragma unroll
   for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
   for (int m = 1; m <= M; ++m) {
-    e = cmul(e, e1);
+    const double ex = ph[m].x;
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
-      if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], e.x, sr[jn]);
+      if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
-  const float kf[1] = {(float)k[0]};
   unsigned terms = 0, coefs = 0;
-  recip_sum<1>(R, sphi, nd, k, kf, acc, terms, coefs);
+  const float kf[1] = {(float)k[0]};
+  recip_any<1>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
   for (int jn = 0; jn < EZ_MAX_NU; ++jn)
-    if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - 2.0 / R->nu[jn]);
+    if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
   double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   products(R, nd, np, Z, w, f);
   double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;

@@ -54,6 +54,26 @@ __host__ __device__ inline double phi_cf(double a, double t) {
   return exp(-t) * h;
 }
 
+// t e^{t} Phi_a(t) for large t (t > a + 1): t times the Legendre continued fraction, so
+// that nothing underflows (used to fit the binary32 tail of the mixed form).
+__host__ __device__ inline double phi_scaled_large(double a, double t) {
+  const double tiny = 1e-300;
+  double b = t + 1.0 - a, c = 1.0 / tiny, dd = 1.0 / b, h = dd;
+  for (int i = 1; i < 20000; ++i) {
+    double an = -(double)i * ((double)i - a);
+    b += 2.0;
+    dd = fma(an, dd, b);
+    if (fabs(dd) < tiny) dd = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    dd = 1.0 / dd;
+    double del = dd * c;
+    h *= del;
+    if (fabs(del - 1.0) < 2e-17) break;
+  }
+  return t * h;
+}
+
 __host__ __device__ inline double phi_accurate(double a, double t) {
   int two_a = (int)lrint(2.0 * a);
   if (!(t > 0.0)) return a < 0.0 ? -1.0 / a : (double)INFINITY;
@@ -185,6 +205,66 @@ __device__ __forceinline__ double phi_eval_qq(const PhiInfo& P, double qq, float
   const double2 so = __ldg(reinterpret_cast<const double2*>(r) + 0);  // (n|pad, s) -- s in .y
   const double o = __ldg(r + 2);
   return phi_poly(r, fma(qq, so.y, o), n_used);
+}
+
+// binary32 evaluation for the mixed form (tail terms, t >= t_mix_f)
+__device__ __forceinline__ float phi_eval_f(const PhiInfo& P, float qqf, float tf) {
+  if (tf > P.t_hi_f) return __expf(-tf) / tf;  // only beyond the tabulated range (cutoff edge)
+  const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
+  const float* r = P.tabf + (size_t)i * kRec;
+  const float4 head = __ldg(reinterpret_cast<const float4*>(r));  // (n|bits, s, o, pad)
+  const int n = __float_as_int(head.x);
+  const float x = fmaf(qqf, head.y, head.z);
+  const float4* c4 = reinterpret_cast<const float4*>(r + 4);
+  int blk = (n >> 2) - 1;
+  float4 c = __ldg(c4 + blk);
+  float p = fmaf(c.w, x, c.z);
+  p = fmaf(p, x, c.y);
+  p = fmaf(p, x, c.x);
+#pragma unroll 1
+  for (--blk; blk >= 0; --blk) {
+    c = __ldg(c4 + blk);
+    p = fmaf(p, x, c.w);
+    p = fmaf(p, x, c.z);
+    p = fmaf(p, x, c.y);
+    p = fmaf(p, x, c.x);
+  }
+  return p;
+}
+
+// mixed form, tail (t >= t_mix): e^{-t} t^{-1} P(t_mix / t), no tables and no branches
+__device__ __forceinline__ float phi_tail_f(const PhiInfo& P, float tf) {
+  const float r = __frcp_rn(tf);
+  const float sv = P.t_mix_f * r;
+  float p = P.tail_p[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) p = fmaf(p, sv, P.tail_p[k]);
+  return __expf(-tf) * r * p;
+}
+
+// mixed form, middle range: argument x from |q|^2 in binary64, polynomial of the binary32
+// table evaluated at the rounded x (no amplification of the argument error by t)
+__device__ __forceinline__ float phi_eval_mid(const PhiInfo& P, double qq, float tf) {
+  const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
+  const double* r = P.tab + (size_t)i * kRec;
+  const float xf = (float)fma(qq, __ldg(r + 1), __ldg(r + 2));
+  const float* rf = P.tabf + (size_t)i * kRec;
+  const int n = __ldg(reinterpret_cast<const int*>(rf));
+  const float4* c4 = reinterpret_cast<const float4*>(rf + 4);
+  int blk = (n >> 2) - 1;
+  float4 c = __ldg(c4 + blk);
+  float p = fmaf(c.w, xf, c.z);
+  p = fmaf(p, xf, c.y);
+  p = fmaf(p, xf, c.x);
+#pragma unroll 1
+  for (--blk; blk >= 0; --blk) {
+    c = __ldg(c4 + blk);
+    p = fmaf(p, xf, c.w);
+    p = fmaf(p, xf, c.z);
+    p = fmaf(p, xf, c.y);
+    p = fmaf(p, xf, c.x);
+  }
+  return p;
 }
 
 __device__ __forceinline__ double phi_eval(const PhiInfo& P, double t) {

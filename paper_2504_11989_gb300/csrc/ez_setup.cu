@@ -132,30 +132,34 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   for (int q = 0; q < kNC; ++q) s += f[q] * cospi((double)k * (q + 0.5) / kNC);
   cj[k] = (k == 0 ? 1.0 : 2.0) * s / kNC;
   __syncthreads();
+  __shared__ int nkeep_f;
   if (k == 0) {
-    // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance
+    // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance:
+    // binary64 table max(2^-55 max|Phi|, 1e-19), binary32 table 2^-26 max|Phi|
     double fm = 0.0;
     for (int q = 0; q < kNC; ++q) fm = fmax(fm, fabs(f[q]));
-    const double tol = fmax(fm / 36028797018963968.0, 1e-19);  // 2^-55 relative, 1e-19 absolute
-    int n = kNC;
-    for (int cand = 4; cand < kNC; cand += 4) {
+    const double tol = fmax(fm / 36028797018963968.0, 1e-19);
+    const double tolf = fm / 67108864.0;
+    int n = kNC, nf = kNC;
+    for (int cand = kNC - 4; cand >= 4; cand -= 4) {
       double tail = 0.0;
       for (int q = cand; q < kNC; ++q) tail += fabs(cj[q]);
-      if (tail <= tol) {
-        n = cand;
-        break;
-      }
+      if (tail <= tol) n = cand;
+      if (tail <= tolf) nf = cand;
     }
     nkeep = n;
+    nkeep_f = nf;
   }
   __syncthreads();
-  const int n = nkeep;
-  double b = 0.0;
+  const int n = nkeep, nf = nkeep_f;
+  double b = 0.0, bf = 0.0;
   if (k < n)
     for (int j = k; j < n; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
+  if (k < nf)
+    for (int j = k; j < nf; ++j) bf += cj[j] * c_cheb2mono[j * kNC + k];
   double* r = J.out + (size_t)iv * kRec;
   r[4 + k] = b;
-  if (J.outf) J.outf[(size_t)iv * kRec + 4 + k] = (float)b;
+  if (J.outf) J.outf[(size_t)iv * kRec + 4 + k] = (float)bf;
   if (k == 0) {
     reinterpret_cast<int*>(r)[0] = n;
     reinterpret_cast<int*>(r)[1] = 0;
@@ -163,9 +167,11 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
     r[2] = -tm / h;
     r[3] = 0.0;
     if (J.outf) {
-      reinterpret_cast<int*>(J.outf + (size_t)iv * kRec)[0] = n;
-      J.outf[(size_t)iv * kRec + 1] = (float)(J.c_lam / h);
-      J.outf[(size_t)iv * kRec + 2] = (float)(-tm / h);
+      float* rf = J.outf + (size_t)iv * kRec;
+      reinterpret_cast<int*>(rf)[0] = nf;
+      rf[1] = (float)(J.c_lam / h);
+      rf[2] = (float)(-tm / h);
+      rf[3] = 0.0f;
     }
   }
 }
@@ -301,6 +307,25 @@ __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_
   const double t = R->c_lam * R->rec[hi].w;
   const int stride = 2 * R->ell + 1;
   for (int n = 0; n < stride; ++n) J.phiG[(size_t)hi * stride + n] = t > 0.0 ? phi_accurate(a + n, t) : 0.0;
+}
+
+// Phase powers e^{2 pi i m u v} (m < mp1) for every (u node, v node) of a quadrature;
+// one thread per node pair, sincospi once and complex rotations after.
+__global__ void phase_kernel(const PhaseJob* jobs) {
+  const PhaseJob J = jobs[blockIdx.y];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)J.n_ui * J.n_v) return;
+  const int iu = (int)(i / J.n_v), iv = (int)(i % J.n_v);
+  const double arg = J.v ? J.u[iu] * J.v[iv] : J.u[iu];
+  double sn, cs;
+  sincospi(2.0 * arg, &sn, &cs);
+  double2* o = J.out + (size_t)i * J.mp1;
+  double2 e = make_double2(1.0, 0.0);
+  o[0] = e;
+  for (int m = 1; m < J.mp1; ++m) {
+    e = make_double2(fma(e.x, cs, -e.y * sn), fma(e.x, sn, e.y * cs));
+    o[m] = e;
+  }
 }
 
 }  // namespace ez

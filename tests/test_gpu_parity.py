@@ -226,3 +226,51 @@ def test_mixed_batch_equals_single_requests(ez, oracle_mod):
     for i, p in enumerate(probs):
         ref = oracle_mod.nbody(p, threads=16)
         assert _close(many[i, : len(ref)], ref), (p.name, many[i], ref)
+
+
+# ------------------------------------------------------------------ mixed form
+MIXED_TOL = 1e-10  # stated bound of the mixed form (binary32 tails, binary64 heads)
+
+
+def _compare_mixed(ez, oracle_mod, prob, threads=16):
+    L = ez.Lattice(prob.A)
+    spec = ez.sum_spec(prob.nu, prob.expo)
+    npr = len(prob.expo)
+    qm = ez.quadrature(prob.quad, prec=ez.EZ_MIXED)
+    got, lines, offs = ez.ez_lattice_sums([L], [spec], [qm], lines=True)
+    ref, far, near = oracle_mod.nbody(prob, threads=threads, lines=True)
+    ref_lines = far.reshape(-1, npr)
+    if prob.quad.u_rule == 2:
+        ref_lines = np.concatenate([ref_lines, near])
+    lines = lines[offs[0]: offs[1], :npr]
+    floor = np.max(np.abs(ref_lines), axis=0)
+    assert np.all(np.abs(lines - ref_lines) <= MIXED_TOL * np.maximum(np.abs(ref_lines), floor)), prob.name
+    assert _close(got[0, :npr], ref, tol=MIXED_TOL), (prob.name, got[0, :npr], ref)
+    return got[0, :npr], ref
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=[p.name + f"-{i}" for i, p in enumerate(SMALL)])
+def test_mixed_parity_small(ez, oracle_mod, prob):
+    _compare_mixed(ez, oracle_mod, prob)
+
+
+@pytest.mark.parametrize("lat", ["square", "hexagonal"])
+def test_mixed_config2_full_size_uses_binary32_tails(ez, oracle_mod, lat):
+    prob = W.nbody_problem(lat, 3.0, 3, W.config2(256))
+    got, ref = _compare_mixed(ez, oracle_mod, prob)
+    L = ez.Lattice(prob.A)
+    fp64 = ez.ez_lattice_sum_nbody(L, [3.0] * 3, ez.quadrature(prob.quad))
+    assert fp64 != got[0]  # the tail really ran in binary32
+    assert abs(fp64 - got[0]) <= MIXED_TOL * abs(fp64)
+
+
+def test_mixed_batch_matches_single(ez):
+    probs = [W.nbody_problem("hexagonal", 3.0, 3, W.config2(32)), W.atm_problem("square", W.Quad(
+        n_u=4, n_v=8, u_rule=2, lam=1.0, r_real=6, r_recip=6))]
+    lats = [ez.Lattice(p.A) for p in probs]
+    specs = [ez.sum_spec(p.nu, p.expo) for p in probs]
+    quads = [ez.quadrature(p.quad, prec=ez.EZ_MIXED) for p in probs]
+    many = ez.ez_lattice_sums(lats, specs, quads)
+    for i in range(len(probs)):
+        one = ez.ez_lattice_sums([lats[i]], [specs[i]], [quads[i]])
+        assert np.array_equal(one[0], many[i])
