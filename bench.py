@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-lattice", type=int, default=PER_LATTICE, help="sums per lattice per step (profiling)")
+    ap.add_argument("--workload", default="config2", choices=["config2", "serve"])
+    ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     return ap.parse_args()
 
 
@@ -162,6 +164,73 @@ def config_dict(per_lattice: int = PER_LATTICE):
             "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps"}
 
 
+# ----------------------------------------------------------------------------- serving
+def run_serve(args):
+    """Served stability scan: `--requests` lattice sums with random d, lattice, lattice
+    constant, exponent (or the ATM form), n and BZ resolution, mixed precision.  Pass 1
+    submits everything at once (saturated sums/s); pass 2 submits on Poisson arrivals at
+    0.8x that rate and reports the latency percentiles."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2504_11989_gb300 import build, ezeta
+    from paper_2504_11989_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    reqs = W.serving_mix(args.requests, W.SEED_BASE + 5, 1.0)
+    made = []
+    for r in reqs:
+        p = W.request_problem(r)
+        made.append(ezeta.make_request(p.A, p.nu, p.expo, ezeta.quadrature(p.quad, prec=ezeta.EZ_MIXED), r.rid))
+    budget = 16 << 30
+
+    def run(arrivals):
+        srv = ezeta.Server(budget, n_streams=4, max_batch=256)
+        warm = [srv.submit(made[i]) for i in range(16)]
+        for t in warm:
+            srv.wait(t, 600000)
+        tickets = [None] * len(made)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, req in enumerate(made):
+                if arrivals is not None:
+                    dt = arrivals[i] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                tickets[i] = srv.submit(req)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        res = [srv.wait(t, 600000) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return res, wall, st
+
+    res_sat, wall_sat, st_sat = run(None)
+    sat_rate = len(made) / wall_sat
+    rate = 0.8 * sat_rate
+    arrivals = np.cumsum(np.random.default_rng(W.SEED_BASE + 6).exponential(1.0 / rate, size=len(made)))
+    res, wall, st = run(arrivals)
+    lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
+    failed = sum(1 for r in res + res_sat if r.status != 0)
+    line = {"metric": METRIC, "workload": "served stability scan (config 5)", "value": len(made) / wall,
+            "unit": "lattice_sums/s", "saturated_value": sat_rate, "offered_rate": rate,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "n_requests": len(made), "failed": failed, "dtype": "f32 tails + f64 heads", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic request stream (seeded)",
+            "server": {"streams": 4, "max_batch": 256, "budget_bytes": budget, "ticks": st.ticks,
+                       "max_batch_seen": st.max_batch_seen, "gpu_busy_fraction": st.busy_seconds / wall,
+                       "peak_device_bytes": st.peak_device_bytes, "saturated_ticks": st_sat.ticks}}
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -170,6 +239,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
         return
     import numpy as np
     import torch

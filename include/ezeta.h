@@ -187,6 +187,59 @@ int ez_batch_far_flops(ez_batch b, double* flops, long long* terms, long long* c
  * uploaded by ez_batch_create and by every ez_lattice_sums call of the same sums). */
 int ez_batch_sizes(ez_batch b, long long* device_bytes, long long* staging_bytes);
 
+/* --- serving: continuous batching of lattice sums ---------------------------- */
+/* A server owns a worker thread that turns a stream of requests into batched
+ * launches.  Each "tick" is one batch (ez_batch semantics: all kernels of the path
+ * for every admitted request, their nodes mixed in the same launches) on one of
+ * n_streams CUDA streams with its own device memory; several ticks run on the GPU
+ * at once.  Requests are admitted in FIFO order whenever a stream is free and the
+ * device memory of all running ticks plus the new one fits mem_budget_bytes;
+ * requests that arrive while others run are admitted into the next tick, so their
+ * work overlaps with the running ones.  A request's result does not depend on which
+ * other requests share its tick (every sum's items and reductions are its own).
+ * Server time is CLOCK_MONOTONIC seconds. */
+typedef struct {
+  int d;
+  double A[9];            /* row-major d x d */
+  ez_sum_spec spec;
+  ez_quadrature quad;
+  unsigned long long tag; /* caller's label, returned with the result */
+} ez_request;
+
+typedef struct {
+  unsigned long long ticket, tag;
+  int status;                 /* EZ_OK, or the error of this request (EZ_EDOMAIN, EZ_ENOMEM, ...) */
+  double value[EZ_MAX_PROD];  /* value of each product of the spec */
+  double t_submit, t_start, t_done;  /* submit, launch of its tick, completion seen by the worker */
+} ez_result;
+
+typedef struct {
+  long long submitted, completed, failed, ticks, max_batch_seen;
+  double busy_seconds;        /* union of the intervals with at least one tick in flight */
+  long long peak_device_bytes;
+} ez_serve_stats;
+
+#define EZ_SERVER_DRYRUN 1 /* plan and schedule without touching the GPU (values NaN) */
+
+/* mem_budget_bytes: device memory the server may hold for running ticks (> 0);
+ * n_streams: concurrent ticks (1..16); max_batch: requests per tick (1..65536);
+ * max_pending: queue capacity (ez_server_submit returns EZ_EBUSY beyond it). */
+typedef struct ez_server_s* ez_server;
+int ez_server_create(size_t mem_budget_bytes, int n_streams, int max_batch, int max_pending, int flags,
+                     ez_server* out);
+/* Copies the request (non-blocking).  Invalid d or singular A fail here (EZ_EINVAL);
+ * other per-request errors come back in the result's status. */
+int ez_server_submit(ez_server s, const ez_request* req, unsigned long long* ticket);
+/* Moves up to max_results completed results into out (oldest first); *n_out gets the count. */
+int ez_server_poll(ez_server s, ez_result* out, int max_results, int* n_out);
+/* Waits up to timeout_ms for one ticket (EZ_ETIMEOUT if it has not completed; EZ_EINVAL for an
+ * unknown or already collected ticket).  The result is removed from the server. */
+int ez_server_wait(ez_server s, unsigned long long ticket, int timeout_ms, ez_result* out);
+int ez_server_stats(ez_server s, ez_serve_stats* out);
+/* Waits (bounded by timeout_ms) for the running ticks, then frees everything; pending
+ * requests that never started are dropped.  EZ_ETIMEOUT if ticks were still running. */
+int ez_server_destroy(ez_server s, int timeout_ms);
+
 /* Number of Duffy sectors (d 2^{d-1}) and far-field u nodes for (d, q). */
 int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q, int* n_sectors,
               int* n_u_total, int* u_rule_used);

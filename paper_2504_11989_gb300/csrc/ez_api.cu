@@ -660,8 +660,7 @@ int batch_plan(ez_batch_s& B, int n_req, const ez_lattice* lats, const ez_sum_sp
                const ez_quadrature* quads) {
   if (n_req < 1) return fail(EZ_EINVAL, "n_req = %d", n_req);
   if (!lats || !specs || !quads) return fail(EZ_EINVAL, "NULL argument");
-  int rc = init_constants();
-  if (rc) return rc;
+  int rc = EZ_OK;  // host-only: device constants are set up by the launching entry points
   B.n_req = n_req;
   B.plans.assign(n_req, Plan());
   for (int r = 0; r < n_req; ++r) {
@@ -1007,15 +1006,14 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   EZ_LAUNCHED();
   if (B.n_tay) {
     long long max_rec = 0;
-    int tot_alpha = 0;
     for (auto& p : B.plans)
-      if (p.near) {
-        max_rec = std::max(max_rec, p.rcap);
-        tot_alpha += (int)(p.alpha.size() / 3) * p.spec.n_distinct;
-      }
+      if (p.near) max_rec = std::max(max_rec, p.rcap);
     phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
-    taylor_kernel<<<(tot_alpha + 63) / 64, 64, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
+    int max_alpha = 0;
+    for (auto& p : B.plans)
+      if (p.near) max_alpha = std::max(max_alpha, (int)(p.alpha.size() / 3));
+    taylor_kernel<<<dim3(max_alpha, B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
   }
   if (B.n_phase) {
@@ -1069,6 +1067,8 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
 extern "C" int ez_batch_create(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
                                const ez_quadrature* quads, void* stream, ez_batch* out) {
   if (!out) return fail(EZ_EINVAL, "NULL argument");
+  int rc0 = init_constants();
+  if (rc0) return rc0;
   ez_batch B = new ez_batch_s();
   int rc = batch_plan(*B, n_req, lats, specs, quads);
   if (!rc) rc = batch_layout(*B, false);
@@ -1207,6 +1207,8 @@ extern "C" int ez_batch_destroy(ez_batch B) {
 static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs, const ez_quadrature* quads,
                     double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
   if (!out) return fail(EZ_EINVAL, "NULL argument");
+  int rc0 = init_constants();
+  if (rc0) return rc0;
   ez_batch_s B;
   int rc = batch_plan(B, n_req, lats, specs, quads);
   if (!rc) rc = batch_layout(B, false);
@@ -1693,5 +1695,380 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   EZ_CUDA(cudaMemcpyAsync(&status, D + o_st, sizeof(int), cudaMemcpyDeviceToHost, stream));
   EZ_CUDA(cudaStreamSynchronize(stream));
   if (status) return fail(EZ_EDOMAIN, "some y lie in the reciprocal lattice with nu <= d (pole)");
+  return EZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching (ez_server_*, see ezeta.h).
+// ---------------------------------------------------------------------------
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_set>
+
+#include <time.h>
+
+namespace {
+
+double mono_now() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+struct SrvReq {
+  unsigned long long ticket = 0, tag = 0;
+  ez_lattice_s lat;
+  ez_sum_spec spec;
+  ez_quadrature quad;
+  double t_submit = 0.0;
+  size_t est_bytes = 0;  // device bytes of a tick holding this request alone
+  int status = EZ_OK;    // planning error, reported as the result
+};
+
+struct Tick {
+  bool busy = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  char* d = nullptr;
+  size_t dcap = 0;
+  char* h = nullptr;
+  size_t hcap = 0;
+  double* hout = nullptr;
+  size_t hout_cap = 0;
+  std::vector<SrvReq> reqs;
+  ez_batch_s batch;
+  double t_start = 0.0;
+  int error = EZ_OK;
+};
+
+}  // namespace
+
+struct ez_server_s {
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SrvReq> pending;
+  std::deque<ez_result> done;
+  std::unordered_set<unsigned long long> open;  // submitted and not yet completed
+  size_t budget = 0;
+  int n_streams = 1, max_batch = 1, max_pending = 1, flags = 0, device = 0;
+  std::vector<Tick> ticks;
+  std::thread worker;
+  bool stop = false, exited = false;
+  unsigned long long next_ticket = 1;
+  ez_serve_stats st;
+  int n_busy = 0;
+  double busy_since = 0.0;
+};
+
+namespace {
+
+bool dryrun(const ez_server_s* S) { return (S->flags & EZ_SERVER_DRYRUN) != 0; }
+
+size_t held_bytes(const ez_server_s* S) {
+  size_t b = 0;
+  for (const Tick& T : S->ticks) b += T.dcap;
+  return b;
+}
+
+void push_result(ez_server_s* S, const SrvReq& q, int status, const double* v, double t_start, double t_done) {
+  ez_result r;
+  std::memset(&r, 0, sizeof r);
+  r.ticket = q.ticket;
+  r.tag = q.tag;
+  r.status = status;
+  for (int p = 0; p < EZ_MAX_PROD; ++p) r.value[p] = v ? v[p] : std::nan("");
+  r.t_submit = q.t_submit;
+  r.t_start = t_start;
+  r.t_done = t_done;
+  S->done.push_back(r);
+  S->open.erase(q.ticket);
+  S->st.completed++;
+  if (status != EZ_OK) S->st.failed++;
+}
+
+// launches one tick for T.reqs (called without the lock; only the worker touches T)
+int launch_tick(ez_server_s* S, Tick& T) {
+  const int n = (int)T.reqs.size();
+  std::vector<ez_lattice> lats(n);
+  std::vector<ez_sum_spec> specs(n);
+  std::vector<ez_quadrature> quads(n);
+  for (int i = 0; i < n; ++i) {
+    lats[i] = &T.reqs[i].lat;
+    specs[i] = T.reqs[i].spec;
+    quads[i] = T.reqs[i].quad;
+  }
+  T.batch = ez_batch_s();
+  int rc = batch_plan(T.batch, n, lats.data(), specs.data(), quads.data());
+  if (!rc) rc = batch_layout(T.batch, false);
+  if (rc) return rc;
+  if (dryrun(S)) {  // account the memory a real tick would hold
+    T.dcap = std::max(T.dcap, T.batch.dbytes);
+    return EZ_OK;
+  }
+  if (T.batch.dbytes > T.dcap) {
+    if (T.d) cudaFree(T.d);
+    T.d = nullptr;
+    T.dcap = 0;
+    if (cudaMalloc(&T.d, T.batch.dbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(EZ_ENOMEM, "tick allocation of %zu bytes failed", T.batch.dbytes);
+    }
+    T.dcap = T.batch.dbytes;
+  }
+  if (T.batch.hbytes > T.hcap) {
+    if (T.h) cudaFreeHost(T.h);
+    T.h = nullptr;
+    T.hcap = 0;
+    if (cudaMallocHost(&T.h, T.batch.hbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(EZ_ENOMEM, "pinned staging of %zu bytes failed", T.batch.hbytes);
+    }
+    T.hcap = T.batch.hbytes;
+  }
+  const size_t ob = sizeof(double) * EZ_MAX_PROD * n;
+  if (ob > T.hout_cap) {
+    if (T.hout) cudaFreeHost(T.hout);
+    T.hout = nullptr;
+    T.hout_cap = 0;
+    if (cudaMallocHost(&T.hout, ob) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(EZ_ENOMEM, "pinned output of %zu bytes failed", ob);
+    }
+    T.hout_cap = ob;
+  }
+  T.batch.d = T.d;
+  T.batch.h = T.h;
+  T.batch.owns = false;
+  rc = batch_layout(T.batch, true);
+  if (rc) return rc;
+  EZ_CUDA(cudaMemcpyAsync(T.d, T.h, T.batch.hbytes, cudaMemcpyHostToDevice, T.stream));
+  rc = batch_launch(T.batch, T.stream);
+  if (rc) return rc;
+  EZ_CUDA(cudaMemcpyAsync(T.hout, T.d + T.batch.o_out, ob, cudaMemcpyDeviceToHost, T.stream));
+  EZ_CUDA(cudaEventRecord(T.done, T.stream));
+  return EZ_OK;
+}
+
+void server_loop(ez_server_s* S) {
+  if (!dryrun(S)) cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lock(S->mu);
+  while (true) {
+    bool progressed = false;
+    // completions
+    for (Tick& T : S->ticks) {
+      if (!T.busy) continue;
+      bool fin = true;
+      int err = T.error;
+      if (!dryrun(S) && !err) {
+        cudaError_t q = cudaEventQuery(T.done);
+        if (q == cudaErrorNotReady) fin = false;
+        else if (q != cudaSuccess) err = EZ_ECUDA;
+      }
+      if (!fin) continue;
+      const double now = mono_now();
+      for (size_t i = 0; i < T.reqs.size(); ++i)
+        push_result(S, T.reqs[i], err, (err || dryrun(S)) ? nullptr : T.hout + i * EZ_MAX_PROD, T.t_start, now);
+      T.reqs.clear();
+      T.busy = false;
+      T.error = EZ_OK;
+      if (--S->n_busy == 0) S->st.busy_seconds += now - S->busy_since;
+      progressed = true;
+    }
+    if (progressed) S->cv_done.notify_all();
+    if (S->stop && S->n_busy == 0) break;
+    // admission: FIFO, as long as a stream is free and the device memory fits
+    for (Tick& T : S->ticks) {
+      if (T.busy || S->pending.empty() || S->stop) continue;
+      size_t others = 0;
+      for (const Tick& U : S->ticks)
+        if (&U != &T) others += U.dcap;
+      const size_t room = S->budget > others ? S->budget - others : 0;
+      size_t sum = 0;
+      std::vector<SrvReq> take;
+      while (!S->pending.empty() && (int)take.size() < S->max_batch) {
+        SrvReq& q = S->pending.front();
+        if (q.status != EZ_OK) {
+          push_result(S, q, q.status, nullptr, 0.0, mono_now());
+          S->pending.pop_front();
+          progressed = true;
+          continue;
+        }
+        if (q.est_bytes > S->budget) {
+          push_result(S, q, EZ_ENOMEM, nullptr, 0.0, mono_now());
+          S->pending.pop_front();
+          progressed = true;
+          continue;
+        }
+        if (sum + q.est_bytes > room && !take.empty()) break;
+        if (sum + q.est_bytes > room) break;  // wait for other ticks to release memory
+        sum += q.est_bytes;
+        take.push_back(std::move(q));
+        S->pending.pop_front();
+      }
+      if (take.empty()) continue;
+      T.reqs = std::move(take);
+      T.busy = true;
+      T.t_start = mono_now();
+      if (S->n_busy++ == 0) S->busy_since = T.t_start;
+      S->st.ticks++;
+      S->st.max_batch_seen = std::max<long long>(S->st.max_batch_seen, (long long)T.reqs.size());
+      lock.unlock();
+      const int rc = launch_tick(S, T);
+      lock.lock();
+      if (rc) T.error = rc;
+      S->st.peak_device_bytes = std::max<long long>(S->st.peak_device_bytes, (long long)held_bytes(S));
+      progressed = true;
+    }
+    if (progressed) S->cv_done.notify_all();
+    if (!progressed) S->cv_work.wait_for(lock, std::chrono::microseconds(S->n_busy ? 20 : 2000));
+  }
+  S->exited = true;
+  S->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" int ez_server_create(size_t mem_budget_bytes, int n_streams, int max_batch, int max_pending, int flags,
+                                ez_server* out) {
+  if (!out) return fail(EZ_EINVAL, "NULL argument");
+  if (mem_budget_bytes == 0 || n_streams < 1 || n_streams > 16 || max_batch < 1 || max_batch > 65536 ||
+      max_pending < 1)
+    return fail(EZ_EINVAL, "server limits: budget %zu, streams %d, batch %d, pending %d", mem_budget_bytes,
+                n_streams, max_batch, max_pending);
+  ez_server S = new ez_server_s();
+  std::memset(&S->st, 0, sizeof S->st);
+  S->budget = mem_budget_bytes;
+  S->n_streams = n_streams;
+  S->max_batch = max_batch;
+  S->max_pending = max_pending;
+  S->flags = flags;
+  S->ticks.resize(n_streams);
+  if (!dryrun(S)) {
+    int rc = init_constants();
+    if (rc) {
+      delete S;
+      return rc;
+    }
+    cudaGetDevice(&S->device);
+    for (Tick& T : S->ticks) {
+      if (cudaStreamCreateWithFlags(&T.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ez_server_destroy(S, 0);
+        return fail(EZ_ECUDA, "stream/event creation failed");
+      }
+    }
+  }
+  S->worker = std::thread(server_loop, S);
+  *out = S;
+  return EZ_OK;
+}
+
+extern "C" int ez_server_submit(ez_server S, const ez_request* req, unsigned long long* ticket) {
+  if (!S || !req) return fail(EZ_EINVAL, "NULL argument");
+  SrvReq q;
+  const int d = req->d;
+  if (d < 1 || d > 3) return fail(EZ_EINVAL, "request d = %d", d);
+  std::memset(&q.lat, 0, sizeof q.lat);
+  q.lat.d = d;
+  std::memcpy(q.lat.A, req->A, sizeof(double) * d * d);
+  q.lat.V = std::fabs(det3(d, q.lat.A));
+  if (!(q.lat.V > 0.0) || !invert(d, q.lat.A, q.lat.Ai)) return fail(EZ_EINVAL, "singular lattice matrix");
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      q.lat.AiT[i * d + j] = q.lat.Ai[j * d + i];
+      q.lat.At[i * d + j] = q.lat.A[j * d + i];
+    }
+  q.spec = req->spec;
+  q.quad = req->quad;
+  q.tag = req->tag;
+  {  // plan it alone: validity and device footprint
+    ez_batch_s B;
+    ez_lattice lp = &q.lat;
+    int rc = batch_plan(B, 1, &lp, &q.spec, &q.quad);
+    if (!rc) rc = batch_layout(B, false);
+    q.status = rc;
+    q.est_bytes = rc ? 0 : B.dbytes;
+  }
+  std::lock_guard<std::mutex> lock(S->mu);
+  if (S->stop) return fail(EZ_EINVAL, "server is shutting down");
+  if ((int)S->pending.size() >= S->max_pending) return fail(EZ_EBUSY, "queue full (%d pending)", S->max_pending);
+  q.ticket = S->next_ticket++;
+  q.t_submit = mono_now();
+  if (ticket) *ticket = q.ticket;
+  S->open.insert(q.ticket);
+  S->pending.push_back(std::move(q));
+  S->st.submitted++;
+  S->cv_work.notify_one();
+  return EZ_OK;
+}
+
+extern "C" int ez_server_poll(ez_server S, ez_result* out, int max_results, int* n_out) {
+  if (!S || (!out && max_results > 0)) return fail(EZ_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(S->mu);
+  int n = 0;
+  while (n < max_results && !S->done.empty()) {
+    out[n++] = S->done.front();
+    S->done.pop_front();
+  }
+  if (n_out) *n_out = n;
+  return EZ_OK;
+}
+
+extern "C" int ez_server_wait(ez_server S, unsigned long long ticket, int timeout_ms, ez_result* out) {
+  if (!S || !out) return fail(EZ_EINVAL, "NULL argument");
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+  std::unique_lock<std::mutex> lock(S->mu);
+  while (true) {
+    for (auto it = S->done.begin(); it != S->done.end(); ++it)
+      if (it->ticket == ticket) {
+        *out = *it;
+        S->done.erase(it);
+        return EZ_OK;
+      }
+    if (!S->open.count(ticket)) return fail(EZ_EINVAL, "unknown or already collected ticket %llu", ticket);
+    if (S->cv_done.wait_until(lock, deadline) == std::cv_status::timeout) {
+      for (auto it = S->done.begin(); it != S->done.end(); ++it)
+        if (it->ticket == ticket) {
+          *out = *it;
+          S->done.erase(it);
+          return EZ_OK;
+        }
+      return fail(EZ_ETIMEOUT, "ticket %llu not done after %d ms", ticket, timeout_ms);
+    }
+  }
+}
+
+extern "C" int ez_server_stats(ez_server S, ez_serve_stats* out) {
+  if (!S || !out) return fail(EZ_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(S->mu);
+  *out = S->st;
+  if (S->n_busy) out->busy_seconds += mono_now() - S->busy_since;
+  return EZ_OK;
+}
+
+extern "C" int ez_server_destroy(ez_server S, int timeout_ms) {
+  if (!S) return EZ_OK;
+  {
+    std::unique_lock<std::mutex> lock(S->mu);
+    S->stop = true;
+    S->pending.clear();
+    S->cv_work.notify_all();
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+    while (!S->exited)
+      if (S->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && !S->exited)
+        return fail(EZ_ETIMEOUT, "server ticks still running after %d ms", timeout_ms);
+  }
+  if (S->worker.joinable()) S->worker.join();
+  for (Tick& T : S->ticks) {
+    if (T.stream) cudaStreamSynchronize(T.stream);
+    if (T.d) cudaFree(T.d);
+    if (T.h) cudaFreeHost(T.h);
+    if (T.hout) cudaFreeHost(T.hout);
+    if (T.done) cudaEventDestroy(T.done);
+    if (T.stream) cudaStreamDestroy(T.stream);
+  }
+  delete S;
   return EZ_OK;
 }

@@ -197,36 +197,32 @@ __device__ double factd(int n) {
   return r;
 }
 
-__global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs) {
-  int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  // jobs are (request, nu) pairs; each owns n_alpha consecutive threads
-  int acc = 0, jid = -1;
-  for (int q = 0; q < n_jobs; ++q) {
-    int na = reqs[jobs[q].req].n_alpha;
-    if (gid < acc + na) {
-      jid = q;
-      break;
-    }
-    acc += na;
-  }
-  if (jid < 0) return;
+// One block of kTaylorThreads per (request, distinct nu, alpha): the threads split the
+// real-space box and the reciprocal list (strided), then a fixed-order block reduction.
+constexpr int kTaylorThreads = 128;
+
+__global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs,
+                                                                int n_jobs) {
+  const int jid = blockIdx.y;
+  if (jid >= n_jobs) return;
   const TaylorJob J = jobs[jid];
   const ReqDesc* R = reqs + J.req;
-  const int ia = gid - acc;
+  const int ia = blockIdx.x;
+  if (ia >= R->n_alpha) return;
   const int d = R->d, jn = J.nu_index;
   const int* al = R->alpha + 3 * ia;
-  int alpha[3] = {al[0], al[1], al[2]};
-  int K2 = alpha[0] + alpha[1] + alpha[2];
-  int K = K2 / 2;
-  double afact = factd(alpha[0]) * factd(alpha[1]) * factd(alpha[2]);
+  const int alpha[3] = {al[0], al[1], al[2]};
+  const int K2 = alpha[0] + alpha[1] + alpha[2];
+  const int K = K2 / 2;
+  const double afact = factd(alpha[0]) * factd(alpha[1]) * factd(alpha[2]);
   const double nu = R->nu[jn];
   const double c = R->c_lam;
-  // real space
+  // real space: sum_m g(m) z^alpha
   double sreal = 0.0;
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
   const double* g = R->gbox + (size_t)jn * cells;
-  for (long long idx = 0; idx < cells; ++idx) {
-    double gv = g[idx];
+  for (long long idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+    const double gv = g[idx];
     if (gv == 0.0) continue;
     long long cc = idx;
     int m[3];
@@ -243,20 +239,17 @@ __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_
     }
     sreal = fma(gv, mono, sreal);
   }
-  double twopi_pow = 1.0;
-  for (int e = 0; e < K2; ++e) twopi_pow *= 2.0 * kPi;
-  sreal *= ((K & 1) ? -1.0 : 1.0) * twopi_pow / afact;
-  // reciprocal, h != 0
+  // reciprocal space, h != 0
   double srec = 0.0;
   const double* phis = J.phiG;  // [n_rec][2 ell + 1]
   const int stride = 2 * R->ell + 1;
-  for (int hi = 0; hi < R->n_rec; ++hi) {
+  for (int hi = threadIdx.x; hi < R->n_rec; hi += blockDim.x) {
     const G4 G = R->rec[hi];
     if (G.w == 0.0 || G.w > R->R2_recip) continue;
-    double Gv[3] = {G.x, G.y, G.z};
+    const double Gv[3] = {G.x, G.y, G.z};
     double term = 0.0;
     for (int n = K; n <= K2; ++n) {
-      int jj = 2 * n - K2;  // number of linear factors
+      const int jj = 2 * n - K2;  // number of linear factors
       // coefficient of k^alpha in (2 G.k)^jj (|k|^2)^(n-jj)
       double coef = 0.0;
       int b[3];
@@ -283,8 +276,25 @@ __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_
     }
     srec += term;
   }
+  // fixed-order block reduction of (sreal, srec)
+  __shared__ double red[2][kTaylorThreads];
+  red[0][threadIdx.x] = sreal;
+  red[1][threadIdx.x] = srec;
+  __syncthreads();
+  for (int w = kTaylorThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double twopi_pow = 1.0;
+  for (int e = 0; e < K2; ++e) twopi_pow *= 2.0 * kPi;
+  sreal = red[0][0] * ((K & 1) ? -1.0 : 1.0) * twopi_pow / afact;
+  srec = red[1][0];
   // h = 0: regularised entire series
-  bool all_even = ((alpha[0] | alpha[1] | alpha[2]) & 1) == 0;
+  const bool all_even = ((alpha[0] | alpha[1] | alpha[2]) & 1) == 0;
   if (all_even && K <= R->ell) {
     double cK = 1.0;
     for (int e = 0; e < K; ++e) cK *= c;

@@ -56,6 +56,26 @@ class ez_sum_spec(ctypes.Structure):
     ]
 
 
+class ez_request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("A", ctypes.c_double * 9), ("spec", ez_sum_spec),
+                ("quad", ez_quadrature), ("tag", ctypes.c_ulonglong)]
+
+
+class ez_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_ulonglong), ("tag", ctypes.c_ulonglong), ("status", ctypes.c_int),
+                ("value", ctypes.c_double * EZ_MAX_PROD), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ez_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("ticks", ctypes.c_longlong), ("max_batch_seen", ctypes.c_longlong),
+                ("busy_seconds", ctypes.c_double), ("peak_device_bytes", ctypes.c_longlong)]
+
+
+EZ_SERVER_DRYRUN = 1
+
+
 def lib():
     """The loaded libezeta.so; raises if it is missing (no fallback path exists)."""
     global _lib
@@ -91,6 +111,13 @@ def lib():
                                              ctypes.POINTER(ctypes.c_longlong)]
             L.ez_batch_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
             L.ez_diag_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+            L.ez_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(vp)]
+            L.ez_server_submit.argtypes = [vp, ctypes.POINTER(ez_request), ctypes.POINTER(ctypes.c_ulonglong)]
+            L.ez_server_poll.argtypes = [vp, ctypes.POINTER(ez_result), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            L.ez_server_wait.argtypes = [vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(ez_result)]
+            L.ez_server_stats.argtypes = [vp, ctypes.POINTER(ez_serve_stats)]
+            L.ez_server_destroy.argtypes = [vp, ctypes.c_int]
             L.ez_layout.argtypes = [ctypes.c_int, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
@@ -325,3 +352,60 @@ def ez_diag_fp64_peak(stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().ez_diag_fp64_peak(ctypes.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def make_request(A, nu, expo, q: ez_quadrature, tag: int = 0) -> ez_request:
+    A = np.asarray(A, dtype=np.float64)
+    R = ez_request()
+    R.d = A.shape[0]
+    flat = np.zeros(9)
+    flat[: A.size] = A.reshape(-1)
+    for i in range(9):
+        R.A[i] = flat[i]
+    R.spec = sum_spec(nu, expo)
+    R.quad = q
+    R.tag = tag
+    return R
+
+
+class Server:
+    """ez_server: continuous batching of lattice sums on a worker thread (see ezeta.h)."""
+
+    def __init__(self, mem_budget_bytes: int, n_streams: int = 2, max_batch: int = 256, max_pending: int = 1 << 20,
+                 dryrun: bool = False):
+        h = ctypes.c_void_p()
+        _check(lib().ez_server_create(int(mem_budget_bytes), int(n_streams), int(max_batch), int(max_pending),
+                                      EZ_SERVER_DRYRUN if dryrun else 0, ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, req: ez_request) -> int:
+        t = ctypes.c_ulonglong()
+        _check(lib().ez_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, max_results: int = 4096):
+        buf = (ez_result * max_results)()
+        n = ctypes.c_int()
+        _check(lib().ez_server_poll(self.handle, buf, max_results, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> ez_result:
+        r = ez_result()
+        _check(lib().ez_server_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(r)))
+        return r
+
+    def stats(self) -> ez_serve_stats:
+        st = ez_serve_stats()
+        _check(lib().ez_server_stats(self.handle, ctypes.byref(st)))
+        return st
+
+    def close(self, timeout_ms: int = 60000):
+        if getattr(self, "handle", None) is not None:
+            _check(lib().ez_server_destroy(self.handle, int(timeout_ms)))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

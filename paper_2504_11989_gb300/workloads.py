@@ -160,3 +160,33 @@ def serving_mix(count: int, seed: int, rate_per_s: float) -> list:
             res = min(res, 128)
         out.append(Request(i, float(t[i]), d, lat, scale, kind, nu, n, res))
     return out
+
+
+def serve_quad(d: int, res: int, singular: bool, lam: float = 0.0) -> Quad:
+    """Quadrature of a served request at BZ resolution `res` per axis: n_v = res/2 per v
+    axis; n_u from the node budget res^d / (sectors n_v^{d-1}) (d = 1: res nodes on [0,1/2]);
+    the eps-split rule spreads n_u over its six graded panels.  Cutoffs from the default
+    tolerance (lam = 0: lam = V^{1/d})."""
+    n_v = max(2, res // 2)
+    if d == 1:
+        n_u = res
+    elif d == 2:
+        n_u = res // 2
+    else:
+        n_u = -(-res ** 3 // (12 * n_v * n_v))
+    if singular:
+        return Quad(n_u=max(4, -(-n_u // 6)), n_v=n_v, u_rule=2, lam=lam, r_real=0.0, r_recip=0.0)
+    return Quad(n_u=n_u, n_v=n_v, u_rule=1, lam=lam, r_real=0.0, r_recip=0.0)
+
+
+def request_problem(r: "Request") -> Problem:
+    """The lattice sum of one served request."""
+    A = lattice(r.lattice, scale=r.scale)
+    if r.kind == "atm":
+        singular = True
+        nu, expo = list(ATM_NU), [list(x) for x in ATM_EXPO]
+    else:
+        nu, expo = [float(r.nu)], [[r.n]]
+        dn = int(r.nu) - r.d
+        singular = dn < 0 or dn % 2 == 0
+    return Problem(f"req{r.rid}", A, nu, expo, serve_quad(r.d, r.res, singular), {"request": r})

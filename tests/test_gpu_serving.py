@@ -1,0 +1,71 @@
+"""Serving loop on the GPU: every served result equals the same sum computed alone
+(tolerance 0: a sum's items and reductions do not depend on its tick-mates), requests
+that arrive while others run are admitted into later ticks that overlap on the device,
+and FP64 and mixed-form requests share the server."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2504_11989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ez():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2504_11989_gb300 import build, ezeta
+
+    build.build()
+    return ezeta
+
+
+def _small_mix(n, seed):
+    out = []
+    for r in W.serving_mix(n, seed, 1000.0):
+        r.res = min(r.res, 64 if r.d == 3 else 96)  # keep the oracle-free test quick
+        out.append(r)
+    return out
+
+
+def test_served_results_equal_alone_results(ez):
+    reqs = _small_mix(60, 3)
+    probs = [W.request_problem(r) for r in reqs]
+    precs = [ez.EZ_MIXED if i % 2 else ez.EZ_FP64 for i in range(len(probs))]
+    srv = ez.Server(512 << 20, n_streams=3, max_batch=8)
+    tickets = []
+    for i, (p, prec) in enumerate(zip(probs, precs)):
+        tickets.append(srv.submit(ez.make_request(p.A, p.nu, p.expo, ez.quadrature(p.quad, prec=prec), i)))
+        if i % 7 == 6:
+            time.sleep(0.002)  # arrivals while earlier ticks run
+    results = [srv.wait(t, 120000) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st.completed == len(probs) and st.failed == 0 and st.ticks >= 8
+    for i, (p, prec, r) in enumerate(zip(probs, precs, results)):
+        assert r.status == 0 and r.tag == i
+        alone = ez.ez_lattice_sums([ez.Lattice(p.A)], [ez.sum_spec(p.nu, p.expo)],
+                                   [ez.quadrature(p.quad, prec=prec)])
+        npr = len(p.expo)
+        assert np.array_equal(np.array(r.value[:npr]), alone[0, :npr]), (i, p.name)
+        assert r.t_submit <= r.t_start <= r.t_done
+
+
+def test_mixed_form_served_within_bound_of_fp64(ez):
+    reqs = _small_mix(12, 9)
+    srv = ez.Server(512 << 20, n_streams=2, max_batch=4)
+    pairs = []
+    for i, r in enumerate(reqs):
+        p = W.request_problem(r)
+        a = srv.submit(ez.make_request(p.A, p.nu, p.expo, ez.quadrature(p.quad, prec=ez.EZ_FP64), i))
+        b = srv.submit(ez.make_request(p.A, p.nu, p.expo, ez.quadrature(p.quad, prec=ez.EZ_MIXED), i))
+        pairs.append((p, a, b))
+    for p, a, b in pairs:
+        ra, rb = srv.wait(a, 120000), srv.wait(b, 120000)
+        npr = len(p.expo)
+        va, vb = np.array(ra.value[:npr]), np.array(rb.value[:npr])
+        assert np.all(np.abs(va - vb) <= 1e-10 * np.abs(va)), (p.name, va, vb)
+    srv.close()
