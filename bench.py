@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-lattice", type=int, default=PER_LATTICE, help="sums per lattice per step (profiling)")
-    ap.add_argument("--workload", default="config2", choices=["config2", "serve"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "serve", "config1", "config3", "config4"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     return ap.parse_args()
 
@@ -231,6 +231,103 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- other configs
+def _time_batch(ezeta, torch, lats, specs, quads, steps, warmup, stream, flush):
+    batch = ezeta.Batch(lats, specs, quads, stream=stream)
+    out = torch.zeros(len(lats) * ezeta.EZ_MAX_PROD, dtype=torch.float64, device="cuda")
+    for _ in range(max(3, warmup)):
+        batch.run(out, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    batch.timing(True)
+    far = []
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            batch.run(out, stream)
+            ev[k][1].record(stream)
+            far.append(batch.timing(True)[0])
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    vals = out.view(len(lats), ezeta.EZ_MAX_PROD).cpu().numpy().copy()
+    flops = batch.far_flops()[0]
+    lines, offs = batch.lines()
+    return vals, sum(ms) / steps, sum(far) / steps, flops, lines, offs
+
+
+def run_config(args):
+    """Configs 1, 3, 4 of the workload list, FP64 and mixed form, one JSON line each."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2504_11989_gb300 import build, ezeta
+    from paper_2504_11989_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    oracle.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    auto = dict(lam=0.0, r_real=0.0, r_recip=0.0)
+    if args.workload == "config1":
+        probs = []
+        for s in W.lattice_constants(1024, W.SEED_BASE + 11):
+            probs.append(W.nbody_problem("Z", 4.0, 3, W.Quad(n_u=4096, n_v=1, u_rule=1, lam=s, r_real=8 * s,
+                                                            r_recip=8 / s), scale=s))
+        label = "zeta^(3)_Z(4,4,4), 4096 GL nodes on [0,1/2], 8 shells, 1024 lattice constants per step"
+    elif args.workload == "config3":
+        probs = [W.atm_problem(n, W.Quad(n_u=8, n_v=64, u_rule=2, **auto)) for n in ("sc", "fcc", "bcc")]
+        label = "ATM energy on sc, fcc, bcc (unit density), 12 sectors x 48 u x 64^2 v nodes + eps-split near part"
+    else:
+        probs = [W.nbody_problem("fcc", 6.0, n, W.Quad(n_u=32, n_v=48, u_rule=1, **auto)) for n in (3, 4, 5, 6, 8)]
+        label = "zeta^(n)(6,..,6) on fcc, n = 3,4,5,6,8, 12 sectors x 32 u x 48^2 v nodes"
+    lats = [ezeta.Lattice(p.A) for p in probs]
+    specs = [ezeta.sum_spec(p.nu, p.expo) for p in probs]
+    res = {}
+    for prec, tag in ((ezeta.EZ_FP64, "f64"), (ezeta.EZ_MIXED, "mixed")):
+        quads = [ezeta.quadrature(p.quad, prec=prec) for p in probs]
+        res[tag] = _time_batch(ezeta, torch, lats, specs, quads, args.steps, args.warmup, stream, flush)
+    per_factor = None
+    if args.workload == "config4":
+        quads = [ezeta.quadrature(p.quad, dedupe=0) for p in probs]
+        specs_pf = [ezeta.sum_spec([6.0] * p.expo[0][0], [[1] * p.expo[0][0]]) for p in probs]
+        per_factor = []
+        for i in range(len(probs)):
+            _, ms1, _, _, _, _ = _time_batch(ezeta, torch, [lats[i]], [specs_pf[i]], [quads[i]], 3, 3, stream, flush)
+            per_factor.append({"n": probs[i].expo[0][0], "ms": ms1})
+    # sampled oracle lines (full-size sums): first product, a few far lines of each sum
+    rng = np.random.default_rng(4)
+    worst = {"f64": 0.0, "mixed": 0.0}
+    t0 = time.perf_counter()
+    for i, p in enumerate(W.explicit_splitting(p) for p in probs[:3]):
+        ns, nu_t = oracle.n_sectors(p), oracle.n_u_total(p)
+        for _ in range(2 if args.workload != "config1" else 8):
+            sct, iu = int(rng.integers(ns)), int(rng.integers(nu_t))
+            ref = oracle.nbody_line(p, sct, iu)
+            for tag in worst:
+                _, _, _, _, lines, offs = res[tag]
+                row = lines[offs[i] + sct * nu_t + iu, : len(ref)]
+                scale = np.max(np.abs(lines[offs[i]: offs[i + 1], : len(ref)]), axis=0)
+                worst[tag] = max(worst[tag], float(np.max(np.abs(row - ref) / np.maximum(np.abs(ref), scale))))
+    cpu_s = time.perf_counter() - t0
+    for tag in ("f64", "mixed"):
+        vals, ms, far_ms, flops, _, _ = res[tag]
+        line = {"metric": METRIC, "workload": args.workload, "config": label, "dtype": tag, "sums_per_step": len(probs),
+                "value": len(probs) / (ms / 1e3), "unit": "lattice_sums/s", "ms_per_step": ms,
+                "far_ms_per_step": far_ms, "far_tflops_algorithmic": flops / (far_ms * 1e-3) / 1e12,
+                "max_line_rel_err_vs_oracle": worst[tag], "oracle_lines_seconds": cpu_s,
+                "values": [list(map(float, v[: len(p.expo)])) for v, p in zip(vals, probs)][:6]}
+        if args.workload == "config3":
+            line["atm_energy"] = [float(v[0] / 24 - 3 * v[1] / 16 + 3 * v[2] / 8) for v in vals]
+        if tag == "mixed":
+            line["speedup_vs_f64"] = res["f64"][1] / ms
+        if per_factor is not None and tag == "f64":
+            line["per_factor_ms_vs_n"] = per_factor
+        print(json.dumps(line))
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -243,6 +340,10 @@ def main():
     if args.workload == "serve":
         if rank == 0:
             run_serve(args)
+        return
+    if args.workload in ("config1", "config3", "config4"):
+        if rank == 0:
+            run_config(args)
         return
     import numpy as np
     import torch

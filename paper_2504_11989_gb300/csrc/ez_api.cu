@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "ez_kernels.h"
@@ -350,7 +351,10 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.ell > 8) return fail(EZ_EINVAL, "ell = %d > 8", p.ell);
   p.prec = q.prec;
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
-  p.lam = q.lambda > 0.0 ? q.lambda : std::pow(L->V, 1.0 / d);
+  // default splitting parameter: the separable real-space contraction costs O(M) per node
+  // while the reciprocal sum costs O(terms); lam = 2 V^{1/d} (d <= 2), 2.5 V^{1/3} (d = 3)
+  // moves most of the work to real space (the result does not depend on lam)
+  p.lam = q.lambda > 0.0 ? q.lambda : (d == 3 ? 2.5 : 2.0) * std::pow(L->V, 1.0 / d);
   p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(kTcut / kPi);
   p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(kTcut / kPi) / p.lam;
   p.nsect = d * (1 << (d - 1));
@@ -620,8 +624,7 @@ int init_constants() {
   for (int j = 2; j < kNC; ++j)
     for (int i = 0; i < kNC; ++i) c[j][i] = (i > 0 ? 2.0 * c[j - 1][i - 1] : 0.0) - c[j - 2][i];
   EZ_CUDA(upload_cheb2mono(&c[0][0]));
-  EZ_CUDA(cudaFuncSetAttribute(far_kernel_d3, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  EZ_CUDA(cudaFuncSetAttribute(far_kernel_d2, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  EZ_CUDA(far_set_smem_limits());
   g_init = true;
   return EZ_OK;
 }
@@ -645,8 +648,17 @@ struct ez_batch_s {
   int n_phase = 0, max_phase_pairs = 0;
   size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
-  int n_phi = 0, n_tay = 0;
-  size_t far_begin[4] = {0, 0, 0, 0}, far_end[4] = {0, 0, 0, 0}, near_begin = 0, near_end = 0;
+  int n_phi = 0, n_tay = 0, n_pcopy = 0;
+  size_t o_pcj = 0;
+  std::vector<std::pair<int, int>> phi_master;  // per distinct a: (request, nu index) computing the table
+  std::vector<std::array<int, 3>> phi_copy;     // (request, nu index, group) copying it
+  struct FarGroup {
+    int d, ndm;
+    bool mixed;
+    size_t begin, end, smem;
+  };
+  std::vector<FarGroup> far;  // far-field launches: items grouped by (d, precision, exponent class)
+  size_t near_begin = 0, near_end = 0;
   long long n_lines = 0;
   std::vector<long long> line0;
   bool ran = false;
@@ -713,12 +725,42 @@ int batch_layout(ez_batch_s& B, bool fill) {
   int& n_phi = B.n_phi;
   int& n_tay = B.n_tay;
   n_phi = n_tay = 0;
-  for (int r = 0; r < n_req; ++r) {
-    n_phi += plans[r].spec.n_distinct;
+  for (int r = 0; r < n_req; ++r)
     if (plans[r].near) n_tay += plans[r].spec.n_distinct;
+  // Phi tables depend on a alone (up to the argument scale of each record): one table per
+  // distinct a, computed for the member with the most intervals, copied to the others
+  {
+    std::vector<std::vector<std::pair<int, int>>> groups;
+    for (int r = 0; r < n_req; ++r)
+      for (int j = 0; j < plans[r].spec.n_distinct; ++j) {
+        const PhiInfo& P = plans[r].phi[j];
+        int g = 0;
+        for (; g < (int)groups.size(); ++g) {
+          const PhiInfo& Q = plans[groups[g][0].first].phi[groups[g][0].second];
+          if (Q.a == P.a && Q.t_geo_end == P.t_geo_end) break;
+        }
+        if (g == (int)groups.size()) groups.emplace_back();
+        groups[g].push_back({r, j});
+      }
+    B.phi_master.clear();
+    B.phi_copy.clear();
+    for (int g = 0; g < (int)groups.size(); ++g) {
+      size_t m = 0;
+      for (size_t i = 1; i < groups[g].size(); ++i)
+        if (plans[groups[g][i].first].phi[groups[g][i].second].n_int >
+            plans[groups[g][m].first].phi[groups[g][m].second].n_int)
+          m = i;
+      B.phi_master.push_back(groups[g][m]);
+      for (size_t i = 0; i < groups[g].size(); ++i)
+        if (i != m) B.phi_copy.push_back({groups[g][i].first, groups[g][i].second, g});
+    }
+    n_phi = (int)B.phi_master.size();
+    B.n_pcopy = (int)B.phi_copy.size();
   }
   B.o_pj = dl.take(sizeof(PhiJob) * n_phi);
   const size_t h_pj = hl.take(sizeof(PhiJob) * n_phi);
+  B.o_pcj = dl.take(sizeof(PhiCopyJob) * std::max(B.n_pcopy, 1));
+  const size_t h_pcj = hl.take(sizeof(PhiCopyJob) * std::max(B.n_pcopy, 1));
   B.o_tj = dl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
   const size_t h_tj = hl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
   B.o_lreq = dl.take(sizeof(int) * n_lines);
@@ -762,8 +804,9 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_phj = hl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
   std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
-  std::vector<size_t> o_rec(n_req), o_recf(n_req), o_gbox(n_req), o_tay(n_req), o_phig(n_req);
-  std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req);
+  std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
+      o_phig(n_req);
+  std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
     o_un[r] = dl.take(sizeof(double) * p.n_ui);
@@ -788,9 +831,12 @@ int batch_layout(ez_batch_s& B, bool fill) {
     Plan& p = plans[r];
     o_rec[r] = dl.take(sizeof(G4) * p.rcap);
     o_recf[r] = dl.take(sizeof(float4) * p.rcap);
+    o_reclo[r] = dl.take(sizeof(float4) * p.rcap);
+    o_rectmp[r] = dl.take(sizeof(G4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tabf[r].push_back(dl.take(sizeof(float) * kRec * p.phi[j].n_int));
+    for (int j = 0; j < p.spec.n_distinct; ++j) o_tabff[r].push_back(dl.take(sizeof(float) * kRecFF * p.phi[j].n_int));
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
@@ -825,7 +871,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   int* lnseg = (int*)(Hs + h_lnseg);
   long long* rl0 = (long long*)(Hs + h_rl0);
   int* rnl = (int*)(Hs + h_rnl);
-  int ipj = 0, itj = 0;
+  int itj = 0;
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
     const ez_lattice_s* L = p.L;
@@ -859,13 +905,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.phi[j].c_lam = R.c_lam;
       R.phi[j].tab = (const double*)dptr(o_tab[r][j]);
       R.phi[j].tabf = (const float*)dptr(o_tabf[r][j]);
-      PhiJob& J = pjobs[ipj++];
-      J.a = p.phi[j].a;
-      J.c_lam = R.c_lam;
-      J.t_geo_end = p.phi[j].t_geo_end;
-      J.n_int = p.phi[j].n_int;
-      J.out = (double*)dptr(o_tab[r][j]);
-      J.outf = (float*)dptr(o_tabf[r][j]);
+      R.phi[j].tabff = (const float*)dptr(o_tabff[r][j]);
     }
     for (int i = 0; i < 3; ++i) {
       R.M[i] = p.M[i];
@@ -874,6 +914,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.gbox = (const double*)dptr(o_gbox[r]);
     R.rec = (const G4*)dptr(o_rec[r]);
     R.recf = (const float4*)dptr(o_recf[r]);
+    R.reclo = (const float4*)dptr(o_reclo[r]);
     R.R2f = (float)(p.r_recip * p.r_recip);
     R.work = (unsigned long long*)dptr(B.o_work) + 2 * r;
     R.c_lam_f = (float)R.c_lam;
@@ -908,6 +949,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
     RJ.cap = (int)p.rcap;
     RJ.out = (G4*)dptr(o_rec[r]);
     RJ.outf = (float4*)dptr(o_recf[r]);
+    RJ.outlo = (float4*)dptr(o_reclo[r]);
+    RJ.tmp = (G4*)dptr(o_rectmp[r]);
     GboxJob& GJ = gjobs[r];
     std::memset(&GJ, 0, sizeof GJ);
     GJ.req = r;
@@ -924,6 +967,33 @@ int batch_layout(ez_batch_s& B, bool fill) {
         T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
       }
   }
+  for (int g = 0; g < n_phi; ++g) {
+    const int r = B.phi_master[g].first, j = B.phi_master[g].second;
+    PhiJob& J = pjobs[g];
+    J.a = plans[r].phi[j].a;
+    J.c_lam = reqs[r].c_lam;
+    J.t_geo_end = plans[r].phi[j].t_geo_end;
+    J.n_int = plans[r].phi[j].n_int;
+    J.out = (double*)dptr(o_tab[r][j]);
+    J.outf = (float*)dptr(o_tabf[r][j]);
+    J.outff = (float*)dptr(o_tabff[r][j]);
+  }
+  {
+    PhiCopyJob* cj = (PhiCopyJob*)(Hs + h_pcj);
+    for (int c = 0; c < B.n_pcopy; ++c) {
+      const int r = B.phi_copy[c][0], j = B.phi_copy[c][1];
+      const int rm = B.phi_master[B.phi_copy[c][2]].first, jm = B.phi_master[B.phi_copy[c][2]].second;
+      cj[c].src = (const double*)dptr(o_tab[rm][jm]);
+      cj[c].srcf = (const float*)dptr(o_tabf[rm][jm]);
+      cj[c].srcff = (const float*)dptr(o_tabff[rm][jm]);
+      cj[c].out = (double*)dptr(o_tab[r][j]);
+      cj[c].outf = (float*)dptr(o_tabf[r][j]);
+      cj[c].outff = (float*)dptr(o_tabff[r][j]);
+      cj[c].c_lam = reqs[r].c_lam;
+      cj[c].t_geo_end = plans[r].phi[j].t_geo_end;
+      cj[c].n_int = plans[r].phi[j].n_int;
+    }
+  }
   {
     PhaseJob* phj = (PhaseJob*)(Hs + h_phj);
     for (int g = 0; g < B.n_phase; ++g) {
@@ -937,24 +1007,29 @@ int batch_layout(ez_batch_s& B, bool fill) {
       phj[g].out = (double2*)dptr(o_phase[g]);
     }
   }
-  // items (far: grouped by d; near after)
+  // items (far: grouped by d, precision and exponent class, one launch per group; near after)
   size_t ii = 0;
-  for (int d = 1; d <= 3; ++d) {
-    B.far_begin[d] = ii;
-    for (int r : order) {
-      Plan& p = plans[r];
-      if (p.d != d) continue;
-      if (d == 1) {
-        for (int c = 0; c < p.n_far_items; ++c) items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
-      } else {
-        long long s0 = seg_far0[r];
-        for (int s = 0; s < p.nsect; ++s)
-          for (int iu = 0; iu < p.n_ui; ++iu)
-            for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, s0++};
+  B.far.clear();
+  for (int d = 1; d <= 3; ++d)
+    for (int mixed = 0; mixed < 2; ++mixed)
+      for (int ndm : {1, 4, 8}) {
+        ez_batch_s::FarGroup g{d, ndm, mixed != 0, ii, ii, 0};
+        for (int r : order) {
+          Plan& p = plans[r];
+          if (p.d != d || (p.prec == EZ_MIXED) != (mixed != 0) || far_nd_class(p.spec.n_distinct) != ndm) continue;
+          g.smem = std::max(g.smem, p.smem);
+          if (d == 1) {
+            for (int c = 0; c < p.n_far_items; ++c) items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
+          } else {
+            long long s0 = seg_far0[r];
+            for (int s = 0; s < p.nsect; ++s)
+              for (int iu = 0; iu < p.n_ui; ++iu)
+                for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, s0++};
+          }
+        }
+        g.end = ii;
+        if (g.end > g.begin) B.far.push_back(g);
       }
-    }
-    B.far_end[d] = ii;
-  }
   B.near_begin = ii;
   for (int r : order) {
     Plan& p = plans[r];
@@ -995,15 +1070,27 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   ReqDesc* dreqs = (ReqDesc*)dptr(B.o_req);
   enum_recip_kernel<<<B.n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(B.o_rj));
   EZ_LAUNCHED();
+  {
+    long long max_rcap = 0;
+    for (auto& p : B.plans) max_rcap = std::max(max_rcap, p.rcap);
+    sort_recip_kernel<<<dim3((unsigned)((max_rcap + 255) / 256), B.n_req), 256, 0, stream>>>(
+        dreqs, (const RecipJob*)dptr(B.o_rj));
+    EZ_LAUNCHED();
+  }
   long long max_cells = 0;
   for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
   gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
   EZ_LAUNCHED();
-  int max_int = 0;
-  for (auto& p : B.plans)
-    for (int j = 0; j < p.spec.n_distinct; ++j) max_int = std::max(max_int, p.phi[j].n_int);
+  int max_int = 0, max_int_copy = 0;
+  for (auto& m : B.phi_master) max_int = std::max(max_int, B.plans[m.first].phi[m.second].n_int);
+  for (auto& c : B.phi_copy) max_int_copy = std::max(max_int_copy, B.plans[c[0]].phi[c[1]].n_int);
   phitab_kernel<<<dim3(max_int, B.n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
   EZ_LAUNCHED();
+  if (B.n_pcopy) {
+    phicopy_kernel<<<dim3((max_int_copy * kRec + 127) / 128, B.n_pcopy), 128, 0, stream>>>(
+        (const PhiCopyJob*)dptr(B.o_pcj));
+    EZ_LAUNCHED();
+  }
   if (B.n_tay) {
     long long max_rec = 0;
     for (auto& p : B.plans)
@@ -1024,23 +1111,9 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   Item* ditems = (Item*)dptr(B.o_items);
   double* dseg = (double*)dptr(B.o_seg);
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[1], stream));
-  if (B.far_end[1] > B.far_begin[1]) {
-    far_kernel_d1<<<(unsigned)(B.far_end[1] - B.far_begin[1]), 128, 0, stream>>>(dreqs, ditems + B.far_begin[1], dseg);
-    EZ_LAUNCHED();
-  }
-  if (B.far_end[2] > B.far_begin[2]) {
-    size_t sm = 0;
-    for (auto& p : B.plans)
-      if (p.d == 2) sm = std::max(sm, p.smem);
-    far_kernel_d2<<<(unsigned)(B.far_end[2] - B.far_begin[2]), 128, sm, stream>>>(dreqs, ditems + B.far_begin[2], dseg);
-    EZ_LAUNCHED();
-  }
-  if (B.far_end[3] > B.far_begin[3]) {
-    size_t sm = 0;
-    for (auto& p : B.plans)
-      if (p.d == 3) sm = std::max(sm, p.smem);
-    if (sm > 200 * 1024) return fail(EZ_EINVAL, "far kernel needs %zu bytes of shared memory", sm);
-    far_kernel_d3<<<(unsigned)(B.far_end[3] - B.far_begin[3]), 256, sm, stream>>>(dreqs, ditems + B.far_begin[3], dseg);
+  for (const auto& g : B.far) {
+    if (g.d == 3 && g.smem > 200 * 1024) return fail(EZ_EINVAL, "far kernel needs %zu bytes of shared memory", g.smem);
+    EZ_CUDA(launch_far(g.d, g.mixed, g.ndm, (unsigned)(g.end - g.begin), g.smem, stream, dreqs, ditems + g.begin, dseg));
     EZ_LAUNCHED();
   }
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[2], stream));
@@ -1054,7 +1127,7 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
                                                                      (const int*)dptr(B.o_lnseg), (int)B.n_lines, dseg, dlines);
   EZ_LAUNCHED();
   double* dout = (double*)dptr(B.o_out);
-  total_kernel<<<(B.n_req * EZ_MAX_PROD + 127) / 128, 128, 0, stream>>>(dreqs, (const long long*)dptr(B.o_rl0),
+  total_kernel<<<B.n_req, 128, 0, stream>>>(dreqs, (const long long*)dptr(B.o_rl0),
                                                                      (const int*)dptr(B.o_rnl), B.n_req, dlines, dout);
   EZ_LAUNCHED();
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[3], stream));
@@ -1349,6 +1422,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   q.n_u = 1;
   q.n_v = 1;
   q.u_rule = 1;
+  q.lambda = std::pow(L->V, 1.0 / d);  // per-thread real-space box: keep it small
   Plan p;
   rc = make_plan(L, s, q, p);
   if (rc) return rc;
@@ -1417,6 +1491,8 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   RJ.cap = (int)p.rcap;
   RJ.out = (G4*)(D + o_rec);
   RJ.outf = (float4*)(D + o_recf);
+  RJ.outlo = nullptr;
+  RJ.tmp = nullptr;
   GboxJob& GJ = *(GboxJob*)(Hs + h_gj);
   std::memset(&GJ, 0, sizeof GJ);
   GJ.req = 0;
@@ -1434,6 +1510,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   PJ.n_int = p.phi[0].n_int;
   PJ.out = (double*)(D + o_tab);
   PJ.outf = nullptr;
+  PJ.outff = nullptr;
   EZ_CUDA(cudaMemcpyAsync(D, Hs, hl.off, cudaMemcpyHostToDevice, stream));
   EZ_CUDA(cudaMemsetAsync(D + o_st, 0, sizeof(int), stream));
   if (!y_dev) EZ_CUDA(cudaMemcpyAsync(D + o_y, y, sizeof(double) * m * d, cudaMemcpyHostToDevice, stream));
@@ -1556,6 +1633,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   q.n_u = 1;
   q.n_v = 1;
   q.u_rule = 1;
+  q.lambda = std::pow(L->V, 1.0 / d);  // per-thread real-space box: keep it small
   Plan p;
   rc = make_plan(L, s, q, p);
   if (rc) return rc;

@@ -30,6 +30,12 @@ constexpr double kT0 = 0.5;
 constexpr double kGeoR = 1.4;
 constexpr int kNSer = 16;  // t < 1/2: 0.5^16/16! ~ 7e-19
 constexpr int kMaxInt = 320;  // intervals per table (t_hi <= ~316)
+// Float-float table of the mixed form (kRecFF floats per interval, 16-byte aligned):
+// int n (shortest length in {4, 8, 12, 16} with Chebyshev tail below 2^-47 max|Phi|), pad,
+// s = c/h and m = t_mid/c as float-float pairs, two pads, then b_0 .. b_{kNC-1} as
+// (hi, lo) pairs.  x = s (|q|^2 - m): |q|^2 and m lie within a factor 2 of each other on
+// the interval, so the leading difference is exact (Sterbenz).
+constexpr int kRecFF = 8 + 2 * kNC;
 
 // reciprocal-space record: (G_0, G_1, G_2, |G|^2) with G = A^{-T} h
 struct alignas(32) G4 {
@@ -51,6 +57,7 @@ struct PhiInfo {
   int n_int;          // number of intervals
   const double* tab;  // n_int * kRec doubles (device)
   const float* tabf;  // binary32 table (own polynomial lengths) for the mixed form (device)
+  const float* tabff; // float-float table (n_int * kRecFF floats) for the mixed form (device)
   double ser[kNSer];  // entire part for t < kT0
 };
 
@@ -78,6 +85,7 @@ struct ReqDesc {
   int n_rec;
   const G4* rec;      // (G_0, G_1, G_2, |G|^2)
   const float4* recf; // the same in binary32, for the cutoff screen
+  const float4* reclo; // G - (double)recf (binary32): recf + reclo is G as float-float
   float R2f, c_lam_f;
   PhiInfo phi[EZ_MAX_NU];
   // quadrature

@@ -12,6 +12,8 @@ struct RecipJob {
   int cap;
   G4* out;
   float4* outf;
+  float4* outlo;  // low parts of the float-float G (may be null)
+  G4* tmp;        // non-null: enumerate into tmp; sort_recip_kernel then writes out/outf/outlo
 };
 
 struct GboxJob {
@@ -31,6 +33,21 @@ struct PhiJob {
   int n_int;
   double* out;
   float* outf;
+  float* outff;  // float-float table (may be null)
+};
+
+// Copy of one Phi table computed for another request with the same a (the records do not
+// depend on the lattice except for the argument scale s = c_lam / h, which is rewritten).
+struct PhiCopyJob {
+  const double* src;
+  const float* srcf;
+  const float* srcff;
+  double* out;
+  float* outf;
+  float* outff;
+  double c_lam;
+  double t_geo_end;
+  int n_int;
 };
 
 struct TaylorJob {
@@ -66,14 +83,18 @@ struct EpsteinArgs {
 };
 
 __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs);
+__global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs);
 __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs);
 __global__ void phitab_kernel(const PhiJob* jobs);
+__global__ void phicopy_kernel(const PhiCopyJob* jobs);
 __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 
-__global__ void far_kernel_d1(const ReqDesc* reqs, const Item* items, double* seg);
-__global__ void far_kernel_d2(const ReqDesc* reqs, const Item* items, double* seg);
-__global__ void far_kernel_d3(const ReqDesc* reqs, const Item* items, double* seg);
+// far-field kernels (d = 1, 2, 3): binary64 or mixed form, at most ndm distinct exponents
+inline int far_nd_class(int nd) { return nd <= 1 ? 1 : (nd <= 4 ? 4 : 8); }
+cudaError_t launch_far(int d, bool mixed, int ndm, unsigned grid, size_t smem, cudaStream_t st,
+                       const ReqDesc* reqs, const Item* items, double* seg);
+cudaError_t far_set_smem_limits();
 __global__ void near_kernel(const ReqDesc* reqs, const Item* items, double* seg);
 __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
                              const int* line_nseg, int n_lines, const double* seg, double* lines);

@@ -10,6 +10,7 @@
 // The reciprocal sum runs per node over the compacted list of A^{-T} h.
 #include <cstdio>
 
+#include "ez_ff.cuh"
 #include "ez_kernels.h"
 #include "ez_phi.cuh"
 
@@ -60,26 +61,17 @@ __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd
   for (int i = threadIdx.x; i < nd * words; i += blockDim.x) dst[i] = src[i];
 }
 
-// reciprocal sum at k (x = 0): acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over |G + k| <= R.
-// The cutoff test, the branch and the table interval are taken in binary32 (a term
-// within ~1e-7 relative of the cutoff radius may fall either way: it is below the
-// truncation tolerance by the choice of the radius).  FP64 form: every value is
-// binary64.  Mixed form (MIXED): terms with t >= t_mix (|Phi| t <= 1e-7 beyond it) are
-// evaluated in binary32; terms with t_mid <= t < t_mix (|Phi| <= 1e-6) get their argument
-// in binary64 and their polynomial in binary32; both are summed in binary32 with Kahan
-// compensation.  The rest (and the h = 0 term near k = 0) stays binary64.
-template <int D, bool MIXED>
+// reciprocal sum at k (x = 0), FP64 form: acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over
+// |G + k| <= R, every value binary64.  The cutoff test, the branch and the table interval
+// are taken in binary32 (a term within ~1e-7 relative of the cutoff radius may fall either
+// way: it is below the truncation tolerance by the choice of the radius).
+template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
   const int nrec = R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
-  const float tmix = MIXED ? sphi[0].t_mix_f : 0.0f;
-  const float tmid = MIXED ? sphi[0].t_mid_f : 0.0f;
   const G4* rec = R->rec;
   const float4* recf = R->recf;
-  float sf[EZ_MAX_NU], cpf[EZ_MAX_NU];
-#pragma unroll
-  for (int j = 0; j < EZ_MAX_NU; ++j) sf[j] = cpf[j] = 0.0f;
   for (int h = 0; h < nrec; ++h) {
     const float4 Gf = __ldg(recf + h);
     float qqf;
@@ -95,17 +87,6 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
     }
     if (qqf <= R2f) {
       const float tf = cf * qqf;
-      if (MIXED && tf >= tmix) {
-#pragma unroll
-        for (int j = 0; j < EZ_MAX_NU; ++j)
-          if (j < nd) {  // Kahan: sf + cpf carries the tail sum
-            const float y = phi_tail_f(sphi[j], tf) - cpf[j];
-            const float t = sf[j] + y;
-            cpf[j] = (t - sf[j]) - y;
-            sf[j] = t;
-          }
-        continue;
-      }
       const G4 G = ldg_g4(rec + h);
       double qq;
       if (D == 1) {
@@ -118,20 +99,9 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
         qq = fma(q0, q0, fma(q1, q1, q2 * q2));
       }
-      if (MIXED && tf >= tmid) {
-#pragma unroll
-        for (int j = 0; j < EZ_MAX_NU; ++j)
-          if (j < nd) {
-            const float y = phi_eval_mid(sphi[j], qq, tf) - cpf[j];
-            const float t = sf[j] + y;
-            cpf[j] = (t - sf[j]) - y;
-            sf[j] = t;
-          }
-        continue;
-      }
       ++terms;
 #pragma unroll
-      for (int j = 0; j < EZ_MAX_NU; ++j)
+      for (int j = 0; j < NDM; ++j)
         if (j < nd) {
           int n;
           acc[j] += phi_eval_qq(sphi[j], qq, tf, n);
@@ -139,22 +109,159 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         }
     }
   }
-  if (MIXED) {
-#pragma unroll
-    for (int j = 0; j < EZ_MAX_NU; ++j)
-      if (j < nd) acc[j] += (double)sf[j] - (double)cpf[j];
-  }
 }
 
-template <int D>
+// Mixed form of the same sum.  Terms by t = pi lam^2 |G + k|^2 (binary32 screen):
+//  * t >= t_mix (|Phi| t <= 1e-7 beyond it): binary32, e^{-t} t^{-1} P(t_mix/t);
+//  * t_mid <= t < t_mix (|Phi| <= 1e-6): float-float argument, binary32 polynomial;
+//  * kT0 <= t < t_mid (the heads): float-float |G + k|^2, argument and Horner scheme on
+//    the float-float table (~46 bits, no binary64 instruction);
+//  * t < kT0 (the h = 0 term near k = 0) or beyond the table: binary64 as in the FP64 form.
+// The list is sorted by |G|: once |G| > sqrt(t_mix / c) + |k|, every remaining term is a
+// binary32 tail, evaluated by a loop without branches (the cutoff is a select).  Tails
+// are summed in binary32, the middle range with Kahan compensation, heads in float-float.
+template <int D, int NDM>
+__device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
+                                                const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
+  const int nrec = R->n_rec;
+  const float R2f = R->R2f, cf = R->c_lam_f;
+  const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
+  const float t_hi = sphi[0].t_hi_f, t_geo = sphi[0].t_geo_end_f;
+  const int last = sphi[0].n_int - 1;
+  const float* tabff0 = sphi[0].tabff;
+  const float4* recf = R->recf;
+  const float4* reclo = R->reclo;
+  float klo[3] = {0.0f, 0.0f, 0.0f}, kn2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    klo[i] = (float)(k[i] - (double)kf[i]);
+    kn2 = fmaf(kf[i], kf[i], kn2);
+  }
+  // |G| beyond which t > t_mix for this k (relative margin for the binary32 rounding)
+  const float gb = (sqrtf(tmix / cf) + sqrtf(kn2)) * 1.0001f;
+  const float gb2 = gb * gb;
+  float sf[NDM], cpf[NDM], st[NDM];
+  ff hs[NDM];
+#pragma unroll
+  for (int j = 0; j < NDM; ++j) {
+    sf[j] = cpf[j] = st[j] = 0.0f;
+    hs[j] = ff{0.0f, 0.0f};
+  }
+  int h = 0;
+  for (; h < nrec; ++h) {
+    const float4 Gf = __ldg(recf + h);
+    if (Gf.w > gb2) break;
+    float qqf;
+    if (D == 1) {
+      const float a = Gf.x + kf[0];
+      qqf = a * a;
+    } else if (D == 2) {
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1];
+      qqf = fmaf(a, a, b * b);
+    } else {
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1], c = Gf.z + kf[2];
+      qqf = fmaf(a, a, fmaf(b, b, c * c));
+    }
+    if (qqf > R2f) continue;
+    const float tf = cf * qqf;
+    if (tf >= tmix) {
+      const float r = __frcp_rn(tf), e = __expf(-tf) * r, sv = tmix * r;
+#pragma unroll
+      for (int j = 0; j < NDM; ++j)
+        if (j < nd) st[j] = fmaf(e, phi_tail_poly(sphi[j], sv), st[j]);
+      continue;
+    }
+    if (tf < (float)kT0 || tf > t_hi) {  // rare: binary64 series / asymptotic branches
+      const G4 G = ldg_g4(R->rec + h);
+      double qq;
+      if (D == 1) {
+        const double q0 = G.x + k[0];
+        qq = q0 * q0;
+      } else if (D == 2) {
+        const double q0 = G.x + k[0], q1 = G.y + k[1];
+        qq = fma(q0, q0, q1 * q1);
+      } else {
+        const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
+        qq = fma(q0, q0, fma(q1, q1, q2 * q2));
+      }
+      ++terms;
+#pragma unroll
+      for (int j = 0; j < NDM; ++j)
+        if (j < nd) {
+          int n;
+          acc[j] += phi_eval_qq(sphi[j], qq, tf, n);
+          coefs += n;
+        }
+      continue;
+    }
+    // float-float |G + k|^2 and x = s (|q|^2 - m) (s, m shared by every exponent)
+    const float4 Gl = __ldg(reclo + h);
+    ff qq = ff_sqr(ff_add4(Gf.x, Gl.x, kf[0], klo[0]));
+    if (D >= 2) qq = ff_add(qq, ff_sqr(ff_add4(Gf.y, Gl.y, kf[1], klo[1])));
+    if (D >= 3) qq = ff_add(qq, ff_sqr(ff_add4(Gf.z, Gl.z, kf[2], klo[2])));
+    const int iv = min(phi_interval(tf, t_geo), last);
+    const float4 hd = __ldg(reinterpret_cast<const float4*>(tabff0 + (size_t)iv * kRecFF));      // n, 0, s
+    const float4 hm = __ldg(reinterpret_cast<const float4*>(tabff0 + (size_t)iv * kRecFF) + 1);  // m, 0, 0
+    const ff dq = ff_two_sum(__fsub_rn(qq.hi, hm.x), __fsub_rn(qq.lo, hm.y));  // leading difference exact
+    const ff x = ff_mul(dq, ff{hd.z, hd.w});
+    if (tf >= tmid) {
+#pragma unroll
+      for (int j = 0; j < NDM; ++j)
+        if (j < nd) {  // Kahan: sf + cpf carries the middle range
+          const float y = phi_poly_f(sphi[j].tabf + (size_t)iv * kRec, x.hi) - cpf[j];
+          const float t = sf[j] + y;
+          cpf[j] = (t - sf[j]) - y;
+          sf[j] = t;
+        }
+      continue;
+    }
+    ++terms;
+#pragma unroll
+    for (int j = 0; j < NDM; ++j)
+      if (j < nd) {
+        int n;
+        hs[j] = ff_add(hs[j], phi_poly_ff(sphi[j].tabff + (size_t)iv * kRecFF, x, n));
+        coefs += n;
+      }
+  }
+  // the rest: binary32 tails only
+#pragma unroll 2
+  for (; h < nrec; ++h) {
+    const float4 Gf = __ldg(recf + h);
+    float qqf;
+    if (D == 1) {
+      const float a = Gf.x + kf[0];
+      qqf = a * a;
+    } else if (D == 2) {
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1];
+      qqf = fmaf(a, a, b * b);
+    } else {
+      const float a = Gf.x + kf[0], b = Gf.y + kf[1], c = Gf.z + kf[2];
+      qqf = fmaf(a, a, fmaf(b, b, c * c));
+    }
+    const float tf = cf * qqf;
+    const float r = __frcp_rn(tf), sv = tmix * r;
+    const float e = qqf <= R2f ? __expf(-tf) * r : 0.0f;
+#pragma unroll
+    for (int j = 0; j < NDM; ++j)
+      if (j < nd) st[j] = fmaf(e, phi_tail_poly(sphi[j], sv), st[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < NDM; ++j)
+    if (j < nd)
+      acc[j] += ((double)hs[j].hi + (double)hs[j].lo) + (((double)sf[j] - (double)cpf[j]) + (double)st[j]);
+}
+
+template <int D, bool MIXED, int NDM>
 __device__ __forceinline__ void recip_any(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
-  if (R->prec == EZ_MIXED)
-    recip_sum<D, true>(R, sphi, nd, k, kf, acc, terms, coefs);
+  if constexpr (MIXED)
+    recip_sum_mixed<D, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
   else
-    recip_sum<D, false>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_sum<D, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 }
 
+template <int NDM>
 __device__ __forceinline__ void products(const ReqDesc* R, int nd, int np, const double* Z, double w,
                                          double (&acc)[EZ_MAX_PROD]) {
 #pragma unroll
@@ -182,10 +289,11 @@ size_t far_smem_bytes(int d, int nd, const int* M, int n_v) {
 }
 
 // ------------------------------------------------------------------------- d = 3
+template <bool MIXED, int NDM>
 __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__ reqs,
                                                        const Item* __restrict__ items, double* __restrict__ seg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  __shared__ PhiInfo sphi[NDM];
   const Item it = items[blockIdx.x];
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
@@ -287,9 +395,9 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
     double k[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) k[i] = fma(kca[i], kta, fma(kcb[i], ktb, kcc[i] * u));
-    double Z[EZ_MAX_NU], acc[EZ_MAX_NU];
+    double Z[NDM], acc[NDM];
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn) {
+    for (int jn = 0; jn < NDM; ++jn) {
       acc[jn] = 0.0;
       if (jn < nd) {
         const double2* b = B + jn * (Ma + 1) * kVChunk + v2l;
@@ -303,21 +411,22 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       }
     }
     const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-    recip_any<3>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_any<3, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+    for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
-    products(R, nd, np, Z, wv, wsum);
+    products<NDM>(R, nd, np, Z, wv, wsum);
   }
   count_work(R, terms, coefs);
   block_reduce_store<256>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
 // ------------------------------------------------------------------------- d = 2
+template <bool MIXED, int NDM>
 __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__ reqs,
                                                        const Item* __restrict__ items, double* __restrict__ seg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  __shared__ PhiInfo sphi[NDM];
   const Item it = items[blockIdx.x];
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
@@ -363,37 +472,38 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
     // e^{2 pi i ma kta} = (e^{2 pi i ma u v})^* for p1 = -1: conjugation is exact in the table
     const double2* ph = R->phase + ((size_t)it.iu * nv + v) * R->phase_mp1;
     const double sgn = p1;
-    double sr[EZ_MAX_NU], Z[EZ_MAX_NU], acc[EZ_MAX_NU];
+    double sr[NDM], Z[NDM], acc[NDM];
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
+    for (int jn = 0; jn < NDM; ++jn) sr[jn] = acc[jn] = 0.0;
     for (int ma = 1; ma <= Ma; ++ma) {
       const double2 e = ph[ma];
       const double ey = sgn * e.y;
 #pragma unroll
-      for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      for (int jn = 0; jn < NDM; ++jn)
         if (jn < nd) {
           const double2 hh = H[jn * (Ma + 1) + ma];
           sr[jn] = fma(e.x, hh.x, fma(-ey, hh.y, sr[jn]));
         }
     }
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+    for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_any<2>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_any<2, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+    for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
-    products(R, nd, np, Z, wv, wsum);
+    products<NDM>(R, nd, np, Z, wv, wsum);
   }
   count_work(R, terms, coefs);
   block_reduce_store<128>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
 // ------------------------------------------------------------------------- d = 1
+template <bool MIXED, int NDM>
 __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__ reqs,
                                                        const Item* __restrict__ items, double* __restrict__ seg) {
-  __shared__ PhiInfo sphi[EZ_MAX_NU];
+  __shared__ PhiInfo sphi[NDM];
   const Item it = items[blockIdx.x];
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod;
@@ -406,23 +516,23 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   const int M = R->M[0];
   double k[1] = {R->AiT[0] * u};
   const double2* ph = R->phase + (size_t)iu * R->phase_mp1;
-  double sr[EZ_MAX_NU], acc[EZ_MAX_NU], Z[EZ_MAX_NU];
+  double sr[NDM], acc[NDM], Z[NDM];
 #pragma unroll
-  for (int jn = 0; jn < EZ_MAX_NU; ++jn) sr[jn] = acc[jn] = 0.0;
+  for (int jn = 0; jn < NDM; ++jn) sr[jn] = acc[jn] = 0.0;
   for (int m = 1; m <= M; ++m) {
     const double ex = ph[m].x;
 #pragma unroll
-    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+    for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
   unsigned terms = 0, coefs = 0;
   const float kf[1] = {(float)k[0]};
-  recip_any<1>(R, sphi, nd, k, kf, acc, terms, coefs);
+  recip_any<1, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
-  for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+  for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
   double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
-  products(R, nd, np, Z, w, f);
+  products<NDM>(R, nd, np, Z, w, f);
   double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;
   for (int p = 0; p < np; ++p) o[p] = f[p];
   if (R->work) {  // some lanes left early: plain atomics, no warp shuffle
@@ -577,21 +687,84 @@ __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const lon
   }
 }
 
-// compensated (Neumaier) sum of a request's lines in order
+// Compensated (Neumaier) sum of a request's lines.  One block of 128 threads per request:
+// thread (slot j, product p) sums lines j, j + 32, j + 64, ... in order; the 32 partial
+// sums of each product are then added in slot order.  The order is fixed, so the result
+// does not depend on the batch the request runs in.
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+  const double t = s + x;
+  c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
 __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines, int n_req,
                              const double* lines, double* out) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = g / EZ_MAX_PROD, p = g % EZ_MAX_PROD;
+  static_assert(EZ_MAX_PROD == 4, "128 threads = 32 slots x 4 products");
+  const int r = blockIdx.x;
   if (r >= n_req) return;
+  const int p = threadIdx.x & 3, j = threadIdx.x >> 2;
+  const int nl = req_nlines[r];
+  const double* base = lines + (size_t)req_line0[r] * EZ_MAX_PROD;
   double s = 0.0, c = 0.0;
-  if (p < reqs[r].n_prod)
-    for (int q = 0; q < req_nlines[r]; ++q) {
-      const double x = lines[(size_t)(req_line0[r] + q) * EZ_MAX_PROD + p];
-      const double t = s + x;
-      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
-      s = t;
+  for (int q = j; q < nl; q += 32) neumaier_add(s, c, base[(size_t)q * EZ_MAX_PROD + p]);
+  __shared__ double ps[128], pc[128];
+  ps[threadIdx.x] = s;
+  pc[threadIdx.x] = c;
+  __syncthreads();
+  if (j == 0) {
+    double S = 0.0, C = 0.0;
+    for (int q = 0; q < 32; ++q) {
+      neumaier_add(S, C, ps[q * 4 + p]);
+      C += pc[q * 4 + p];
     }
-  out[(size_t)r * EZ_MAX_PROD + p] = s + c;
+    out[(size_t)r * EZ_MAX_PROD + p] = p < reqs[r].n_prod ? S + C : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------- launch
+// Far-field variants: binary64 or mixed form, at most NDM in {1, 4, 8} distinct exponents
+// (the per-node arrays are sized by NDM, which keeps the register count of the common
+// single-exponent sums low).
+template <bool MIXED, int NDM>
+static cudaError_t launch_far_t(int d, unsigned grid, size_t smem, cudaStream_t st, const ReqDesc* reqs,
+                                const Item* items, double* seg) {
+  if (d == 1)
+    far_kernel_d1<MIXED, NDM><<<grid, 128, 0, st>>>(reqs, items, seg);
+  else if (d == 2)
+    far_kernel_d2<MIXED, NDM><<<grid, 128, smem, st>>>(reqs, items, seg);
+  else
+    far_kernel_d3<MIXED, NDM><<<grid, 256, smem, st>>>(reqs, items, seg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far(int d, bool mixed, int ndm, unsigned grid, size_t smem, cudaStream_t st,
+                       const ReqDesc* reqs, const Item* items, double* seg) {
+  if (mixed) {
+    if (ndm == 1) return launch_far_t<true, 1>(d, grid, smem, st, reqs, items, seg);
+    if (ndm == 4) return launch_far_t<true, 4>(d, grid, smem, st, reqs, items, seg);
+    return launch_far_t<true, 8>(d, grid, smem, st, reqs, items, seg);
+  }
+  if (ndm == 1) return launch_far_t<false, 1>(d, grid, smem, st, reqs, items, seg);
+  if (ndm == 4) return launch_far_t<false, 4>(d, grid, smem, st, reqs, items, seg);
+  return launch_far_t<false, 8>(d, grid, smem, st, reqs, items, seg);
+}
+
+template <bool MIXED, int NDM>
+static cudaError_t far_smem_limits_t() {
+  cudaError_t e = cudaFuncSetAttribute(far_kernel_d3<MIXED, NDM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(far_kernel_d2<MIXED, NDM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+}
+
+cudaError_t far_set_smem_limits() {
+  cudaError_t e;
+  if ((e = far_smem_limits_t<false, 1>()) != cudaSuccess) return e;
+  if ((e = far_smem_limits_t<false, 4>()) != cudaSuccess) return e;
+  if ((e = far_smem_limits_t<false, 8>()) != cudaSuccess) return e;
+  if ((e = far_smem_limits_t<true, 1>()) != cudaSuccess) return e;
+  if ((e = far_smem_limits_t<true, 4>()) != cudaSuccess) return e;
+  return far_smem_limits_t<true, 8>();
 }
 
 }  // namespace ez

@@ -16,6 +16,7 @@
 
 #include <cmath>
 
+#include "ez_ff.cuh"
 #include "ez_internal.h"
 
 namespace ez {
@@ -207,50 +208,18 @@ __device__ __forceinline__ double phi_eval_qq(const PhiInfo& P, double qq, float
   return phi_poly(r, fma(qq, so.y, o), n_used);
 }
 
-// binary32 evaluation for the mixed form (tail terms, t >= t_mix_f)
-__device__ __forceinline__ float phi_eval_f(const PhiInfo& P, float qqf, float tf) {
-  if (tf > P.t_hi_f) return __expf(-tf) / tf;  // only beyond the tabulated range (cutoff edge)
-  const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
-  const float* r = P.tabf + (size_t)i * kRec;
-  const float4 head = __ldg(reinterpret_cast<const float4*>(r));  // (n|bits, s, o, pad)
-  const int n = __float_as_int(head.x);
-  const float x = fmaf(qqf, head.y, head.z);
-  const float4* c4 = reinterpret_cast<const float4*>(r + 4);
-  int blk = (n >> 2) - 1;
-  float4 c = __ldg(c4 + blk);
-  float p = fmaf(c.w, x, c.z);
-  p = fmaf(p, x, c.y);
-  p = fmaf(p, x, c.x);
-#pragma unroll 1
-  for (--blk; blk >= 0; --blk) {
-    c = __ldg(c4 + blk);
-    p = fmaf(p, x, c.w);
-    p = fmaf(p, x, c.z);
-    p = fmaf(p, x, c.y);
-    p = fmaf(p, x, c.x);
-  }
-  return p;
-}
-
 // mixed form, tail (t >= t_mix): e^{-t} t^{-1} P(t_mix / t), no tables and no branches
-__device__ __forceinline__ float phi_tail_f(const PhiInfo& P, float tf) {
-  const float r = __frcp_rn(tf);
-  const float sv = P.t_mix_f * r;
+__device__ __forceinline__ float phi_tail_poly(const PhiInfo& P, float sv) {
   float p = P.tail_p[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) p = fmaf(p, sv, P.tail_p[k]);
-  return __expf(-tf) * r * p;
+  return p;
 }
 
-// mixed form, middle range: argument x from |q|^2 in binary64, polynomial of the binary32
-// table evaluated at the rounded x (no amplification of the argument error by t)
-__device__ __forceinline__ float phi_eval_mid(const PhiInfo& P, double qq, float tf) {
-  const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
-  const double* r = P.tab + (size_t)i * kRec;
-  const float xf = (float)fma(qq, __ldg(r + 1), __ldg(r + 2));
-  const float* rf = P.tabf + (size_t)i * kRec;
-  const int n = __ldg(reinterpret_cast<const int*>(rf));
-  const float4* c4 = reinterpret_cast<const float4*>(rf + 4);
+// mixed form, middle range: binary32 Horner scheme on the binary32 record r at x
+__device__ __forceinline__ float phi_poly_f(const float* r, float xf) {
+  const int n = __ldg(reinterpret_cast<const int*>(r));
+  const float4* c4 = reinterpret_cast<const float4*>(r + 4);
   int blk = (n >> 2) - 1;
   float4 c = __ldg(c4 + blk);
   float p = fmaf(c.w, xf, c.z);
@@ -263,6 +232,24 @@ __device__ __forceinline__ float phi_eval_mid(const PhiInfo& P, double qq, float
     p = fmaf(p, xf, c.z);
     p = fmaf(p, xf, c.y);
     p = fmaf(p, xf, c.x);
+  }
+  return p;
+}
+
+// mixed form, heads: Horner scheme in float-float on the float-float record r (coefficient
+// pairs (hi, lo), two per 16-byte load); n_used: coefficients evaluated
+__device__ __forceinline__ ff phi_poly_ff(const float* r, ff x, int& n_used) {
+  const int n = __ldg(reinterpret_cast<const int*>(r));
+  n_used = n;
+  const float4* c4 = reinterpret_cast<const float4*>(r + 8);
+  int blk = (n >> 1) - 1;
+  float4 c = __ldg(c4 + blk);  // (b_{2 blk}, b_{2 blk + 1})
+  ff p = ff_add(ff_mul(ff{c.z, c.w}, x), ff{c.x, c.y});
+#pragma unroll 1
+  for (--blk; blk >= 0; --blk) {
+    c = __ldg(c4 + blk);
+    p = ff_add(ff_mul(p, x), ff{c.z, c.w});
+    p = ff_add(ff_mul(p, x), ff{c.x, c.y});
   }
   return p;
 }

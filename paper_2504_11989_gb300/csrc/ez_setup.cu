@@ -1,5 +1,6 @@
 // Setup kernels: lattice-point tables, incomplete-gamma tables and Taylor
 // tensors of Z^reg at the origin.  All of them run once per lattice sum.
+#include "ez_ff.cuh"
 #include "ez_kernels.h"
 #include "ez_phi.cuh"
 
@@ -48,9 +49,14 @@ __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
     for (int w = 0; w < wid; ++w) off += warp_sums[w];
     if (keep) {
       int pos = base + off + before;
-      if (pos < J.cap) {
+      if (pos < J.cap && J.tmp) {
+        J.tmp[pos] = G4{G[0], G[1], G[2], G2};
+      } else if (pos < J.cap) {
         J.out[pos] = G4{G[0], G[1], G[2], G2};
         J.outf[pos] = make_float4((float)G[0], (float)G[1], (float)G[2], (float)G2);
+        if (J.outlo)
+          J.outlo[pos] = make_float4((float)(G[0] - (double)(float)G[0]), (float)(G[1] - (double)(float)G[1]),
+                                     (float)(G[2] - (double)(float)G[2]), 0.0f);
       }
     }
     __syncthreads();
@@ -62,6 +68,41 @@ __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
     __syncthreads();
   }
   if (threadIdx.x == 0) R->n_rec = min(base, J.cap);
+}
+
+// ---------------------------------------------------------------------------
+// Reciprocal points of a request in ascending order of |G|^2 (ties: enumeration order),
+// by rank: one thread per point counts the points before it (the keys are staged in
+// shared memory in chunks).  Writes the binary64 list and its float and float-float
+// copies.  Grid: (points / blockDim, requests).
+// ---------------------------------------------------------------------------
+__global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs) {
+  const RecipJob J = jobs[blockIdx.y];
+  if (!J.tmp) return;
+  const int n = reqs[J.req].n_rec;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if ((long long)blockIdx.x * blockDim.x >= n) return;  // whole block past the end (uniform)
+  constexpr int kChunk = 1024;
+  __shared__ double key[kChunk];
+  const G4 G = i < n ? J.tmp[i] : G4{0.0, 0.0, 0.0, 0.0};
+  int rank = 0;
+  for (int base = 0; base < n; base += kChunk) {
+    const int m = min(kChunk, n - base);
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += blockDim.x) key[q] = J.tmp[base + q].w;
+    __syncthreads();
+    if (i < n)
+      for (int q = 0; q < m; ++q) {
+        const double w = key[q];
+        rank += (w < G.w || (w == G.w && base + q < i)) ? 1 : 0;
+      }
+  }
+  if (i >= n) return;
+  J.out[rank] = G;
+  const float hx = (float)G.x, hy = (float)G.y, hz = (float)G.z;
+  J.outf[rank] = make_float4(hx, hy, hz, (float)G.w);
+  if (J.outlo)
+    J.outlo[rank] = make_float4((float)(G.x - (double)hx), (float)(G.y - (double)hy), (float)(G.z - (double)hz), 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -109,19 +150,26 @@ __constant__ double c_cheb2mono[kNC * kNC];  // [j][i]: coefficient of x^i in T_
 
 cudaError_t upload_cheb2mono(const double* m) { return cudaMemcpyToSymbol(c_cheb2mono, m, sizeof(double) * kNC * kNC); }
 
-__global__ void phitab_kernel(const PhiJob* jobs) {
-  const PhiJob J = jobs[blockIdx.y];
-  const int iv = blockIdx.x;
-  if (iv >= J.n_int) return;
+// midpoint and half-width of interpolation interval iv (geometric, then unit width)
+__device__ __forceinline__ void phi_interval_bounds(int iv, double t_geo_end, double& tm, double& h) {
   double lo, hi;
   if (iv < kNGeo) {
     lo = kT0 * pow(kGeoR, (double)iv);
     hi = lo * kGeoR;
   } else {
-    lo = J.t_geo_end + (iv - kNGeo);
+    lo = t_geo_end + (iv - kNGeo);
     hi = lo + 1.0;
   }
-  const double tm = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+  tm = 0.5 * (lo + hi);
+  h = 0.5 * (hi - lo);
+}
+
+__global__ void phitab_kernel(const PhiJob* jobs) {
+  const PhiJob J = jobs[blockIdx.y];
+  const int iv = blockIdx.x;
+  if (iv >= J.n_int) return;
+  double tm, h;
+  phi_interval_bounds(iv, J.t_geo_end, tm, h);
   __shared__ double f[kNC], cj[kNC];
   __shared__ int nkeep;
   const int k = threadIdx.x;
@@ -132,7 +180,7 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   for (int q = 0; q < kNC; ++q) s += f[q] * cospi((double)k * (q + 0.5) / kNC);
   cj[k] = (k == 0 ? 1.0 : 2.0) * s / kNC;
   __syncthreads();
-  __shared__ int nkeep_f;
+  __shared__ int nkeep_f, nkeep_ff;
   if (k == 0) {
     // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance:
     // binary64 table max(2^-55 max|Phi|, 1e-19), binary32 table 2^-26 max|Phi|
@@ -140,23 +188,39 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
     for (int q = 0; q < kNC; ++q) fm = fmax(fm, fabs(f[q]));
     const double tol = fmax(fm / 36028797018963968.0, 1e-19);
     const double tolf = fm / 67108864.0;
-    int n = kNC, nf = kNC;
+    const double tolff = fm / 140737488355328.0;  // 2^-47: float-float table
+    int n = kNC, nf = kNC, nff = kNC;
     for (int cand = kNC - 4; cand >= 4; cand -= 4) {
       double tail = 0.0;
       for (int q = cand; q < kNC; ++q) tail += fabs(cj[q]);
       if (tail <= tol) n = cand;
       if (tail <= tolf) nf = cand;
+      if (tail <= tolff) nff = cand;
     }
     nkeep = n;
     nkeep_f = nf;
+    nkeep_ff = nff;
   }
   __syncthreads();
-  const int n = nkeep, nf = nkeep_f;
-  double b = 0.0, bf = 0.0;
+  const int n = nkeep, nf = nkeep_f, nff = nkeep_ff;
+  double b = 0.0, bf = 0.0, bff = 0.0;
   if (k < n)
     for (int j = k; j < n; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
   if (k < nf)
     for (int j = k; j < nf; ++j) bf += cj[j] * c_cheb2mono[j * kNC + k];
+  if (k < nff)
+    for (int j = k; j < nff; ++j) bff += cj[j] * c_cheb2mono[j * kNC + k];
+  if (J.outff) {
+    float* rff = J.outff + (size_t)iv * kRecFF;
+    ff_split(bff, rff[8 + 2 * k], rff[9 + 2 * k]);
+    if (k == 0) {
+      reinterpret_cast<int*>(rff)[0] = nff;
+      rff[1] = 0.0f;
+      ff_split(J.c_lam / h, rff[2], rff[3]);
+      ff_split(tm / J.c_lam, rff[4], rff[5]);
+      rff[6] = rff[7] = 0.0f;
+    }
+  }
   double* r = J.out + (size_t)iv * kRec;
   r[4 + k] = b;
   if (J.outf) J.outf[(size_t)iv * kRec + 4 + k] = (float)bf;
@@ -173,6 +237,39 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
       rf[2] = (float)(-tm / h);
       rf[3] = 0.0f;
     }
+  }
+}
+
+// One thread per record element of a copy job (blockIdx.y): the coefficient records of a
+// table computed for the same a, with the argument scale of the destination request.
+__global__ void phicopy_kernel(const PhiCopyJob* jobs) {
+  const PhiCopyJob J = jobs[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iv = e / kRec, k = e - iv * kRec;
+  if (iv >= J.n_int) return;
+  const size_t o = (size_t)iv * kRec;
+  double tm, h;
+  phi_interval_bounds(iv, J.t_geo_end, tm, h);
+  const size_t off = (size_t)iv * kRecFF;
+  if (k >= 4) {
+    J.out[o + k] = J.src[o + k];
+    J.outf[o + k] = J.srcf[o + k];
+    J.outff[off + 2 * k] = J.srcff[off + 2 * k];
+    J.outff[off + 2 * k + 1] = J.srcff[off + 2 * k + 1];
+  } else if (k == 0) {
+    reinterpret_cast<int*>(J.outff + off)[0] = reinterpret_cast<const int*>(J.srcff + off)[0];
+    J.outff[off + 1] = 0.0f;
+    ff_split(J.c_lam / h, J.outff[off + 2], J.outff[off + 3]);
+    ff_split(tm / J.c_lam, J.outff[off + 4], J.outff[off + 5]);
+    J.outff[off + 6] = J.outff[off + 7] = 0.0f;
+    J.out[o] = J.src[o];  // int n, int 0
+    J.out[o + 1] = J.c_lam / h;
+    J.out[o + 2] = J.src[o + 2];
+    J.out[o + 3] = 0.0;
+    reinterpret_cast<int*>(J.outf + o)[0] = reinterpret_cast<const int*>(J.srcf + o)[0];
+    J.outf[o + 1] = (float)(J.c_lam / h);
+    J.outf[o + 2] = J.srcf[o + 2];
+    J.outf[o + 3] = 0.0f;
   }
 }
 

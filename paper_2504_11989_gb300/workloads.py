@@ -123,6 +123,18 @@ def config4(n_v: int = 48, n_u: int = 32) -> Quad:
     return Quad(n_u=n_u, n_v=n_v, u_rule=1, lam=1.0, r_real=4.5, r_recip=4.5)
 
 
+def explicit_splitting(prob: Problem, shells: float = 6.0) -> Problem:
+    """Copy of `prob` whose automatic splitting parameter and cutoffs (lam = 0, r = 0)
+    are replaced by explicit ones: lam = V^{1/d}, r_real = shells lam, r_recip = shells / lam.
+    The lattice sum does not depend on lam; the oracle needs explicit values."""
+    q = prob.quad
+    if q.lam > 0.0 and q.r_real > 0.0 and q.r_recip > 0.0:
+        return prob
+    lam = q.lam if q.lam > 0.0 else abs(float(np.linalg.det(prob.A))) ** (1.0 / prob.d)
+    q2 = Quad(q.n_u, q.n_v, q.u_rule, q.eps, q.ell, lam, shells * lam, shells / lam)
+    return Problem(prob.name, prob.A, prob.nu, prob.expo, q2, dict(prob.meta))
+
+
 def lattice_constants(count: int, seed: int, lo: float = 0.9, hi: float = 1.3) -> np.ndarray:
     return np.random.default_rng(seed).uniform(lo, hi, size=count)
 

@@ -80,12 +80,9 @@ def test_layout_rejects_hadamard_pole_and_bad_exponents(ez):
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
-    import importlib
-
     from paper_2504_11989_gb300 import ezeta
 
     monkeypatch.setattr(ezeta, "_lib", None)
     monkeypatch.setattr(ezeta, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         ezeta.lib()
-    importlib.reload(ezeta)

@@ -156,6 +156,29 @@ def test_config3_atm_full_size_sampled_lines(ez, oracle_mod):
     assert _close(got, lines.sum(axis=0), tol=1e-14, floor=np.max(np.abs(got)))
 
 
+AUTO = dict(lam=0.0, r_real=0.0, r_recip=0.0)
+
+
+@pytest.mark.parametrize("prob", [
+    W.nbody_problem("Z", 4.0, 3, W.Quad(n_u=64, n_v=1, **AUTO), scale=1.2),
+    W.nbody_problem("hexagonal", 3.0, 3, W.Quad(n_u=16, n_v=16, **AUTO), scale=0.9),
+    W.atm_problem("square", W.Quad(n_u=6, n_v=10, u_rule=2, **AUTO), scale=1.1),
+    W.nbody_problem("fcc", 6.0, 4, W.Quad(n_u=4, n_v=11, **AUTO), scale=1.3),
+    W.atm_problem("bcc", W.Quad(n_u=3, n_v=6, u_rule=2, **AUTO)),
+], ids=lambda p: p.name)
+def test_default_splitting_parameter_matches_oracle(ez, oracle_mod, prob):
+    """lam = 0 lets the library pick lam and the cutoffs; every quadrature line must agree
+    with the oracle run at its own explicit lam = V^{1/d} (the sum does not depend on lam)."""
+    got, lines = _run(ez, prob)
+    ref, far, near = oracle_mod.nbody(W.explicit_splitting(prob), threads=16, lines=True)
+    ref_lines = far.reshape(-1, far.shape[2])
+    if prob.quad.u_rule == 2:
+        ref_lines = np.concatenate([ref_lines, near])
+    floor = np.max(np.abs(ref_lines), axis=0)
+    assert np.all(np.abs(lines - ref_lines) <= TOL * np.maximum(np.abs(ref_lines), floor)), prob.name
+    assert _close(got, ref), (prob.name, got, ref)
+
+
 def test_nbody_api_matches_batch_and_is_deterministic(ez, oracle_mod):
     prob = W.nbody_problem("hexagonal", 3.0, 4, W.config2(40))
     L = ez.Lattice(prob.A)
