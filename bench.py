@@ -167,9 +167,10 @@ def config_dict(per_lattice: int = PER_LATTICE):
 # ----------------------------------------------------------------------------- serving
 def run_serve(args):
     """Served stability scan: `--requests` lattice sums with random d, lattice, lattice
-    constant, exponent (or the ATM form), n and BZ resolution, mixed precision.  Pass 1
-    submits everything at once (saturated sums/s); pass 2 submits on Poisson arrivals at
-    0.8x that rate and reports the latency percentiles."""
+    constant, exponent (or the ATM form), n and BZ resolution, mixed precision.  The same
+    requests run saturated in the plain FP64 form first (reference rate and values), then
+    saturated in the mixed form (sums/s, error against FP64), then on Poisson arrivals at
+    0.8x the mixed saturated rate (latency percentiles)."""
     import threading
 
     import numpy as np
@@ -181,13 +182,14 @@ def run_serve(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     build.build()
     reqs = W.serving_mix(args.requests, W.SEED_BASE + 5, 1.0)
-    made = []
+    made, made64 = [], []
     for r in reqs:
         p = W.request_problem(r)
         made.append(ezeta.make_request(p.A, p.nu, p.expo, ezeta.quadrature(p.quad, prec=ezeta.EZ_MIXED), r.rid))
+        made64.append(ezeta.make_request(p.A, p.nu, p.expo, ezeta.quadrature(p.quad, prec=ezeta.EZ_FP64), r.rid))
     budget = 16 << 30
 
-    def run(arrivals):
+    def run(arrivals, made=made):
         srv = ezeta.Server(budget, n_streams=4, max_batch=256)
         warm = [srv.submit(made[i]) for i in range(16)]
         for t in warm:
@@ -212,8 +214,14 @@ def run_serve(args):
         srv.close()
         return res, wall, st
 
+    res64, wall64, _ = run(None, made64)  # the plain FP64 form, saturated, same requests
     res_sat, wall_sat, st_sat = run(None)
     sat_rate = len(made) / wall_sat
+    rel = []
+    for a, b in zip(res_sat, res64):
+        va, vb = np.asarray(a.value, dtype=float), np.asarray(b.value, dtype=float)
+        ok = np.isfinite(vb) & (vb != 0)
+        rel.append(float(np.max(np.abs(va[ok] - vb[ok]) / np.abs(vb[ok]))) if ok.any() else 0.0)
     rate = 0.8 * sat_rate
     arrivals = np.cumsum(np.random.default_rng(W.SEED_BASE + 6).exponential(1.0 / rate, size=len(made)))
     res, wall, st = run(arrivals)
@@ -223,7 +231,9 @@ def run_serve(args):
             "unit": "lattice_sums/s", "saturated_value": sat_rate, "offered_rate": rate,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "n_requests": len(made), "failed": failed, "dtype": "f32 tails + f64 heads", "n_gpus": 1,
+            "fp64_saturated_value": len(made64) / wall64, "speedup_vs_fp64_saturated": wall64 / wall_sat,
+            "max_rel_err_vs_fp64": max(rel), "median_rel_err_vs_fp64": float(np.median(rel)),
+            "n_requests": len(made), "failed": failed, "dtype": "f32 tails + float-float heads", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic request stream (seeded)",
             "server": {"streams": 4, "max_batch": 256, "budget_bytes": budget, "ticks": st.ticks,
                        "max_batch_seen": st.max_batch_seen, "gpu_busy_fraction": st.busy_seconds / wall,
@@ -463,7 +473,7 @@ def main():
                      "recip_terms_per_launch": n_terms, "mean_poly_len": n_coefs / max(1, n_terms)},
         "clocks": clocks,
         "mixed_precision": {"value": mixed_value, "unit": "lattice_sums/s", "speedup_vs_fp64": mixed_value / value,
-                            "dtype": "f32 tails + f64 heads", "ms_per_step": mixed_ms / args.steps,
+                            "dtype": "f32 tails + float-float heads", "ms_per_step": mixed_ms / args.steps,
                             "max_rel_err_vs_fp64": float(np.max(np.abs(res_m - res) / np.abs(res)))},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -13,6 +13,7 @@
 #include <array>
 #include <vector>
 
+#include "ez_ff.cuh"
 #include "ez_kernels.h"
 #include "ez_phi.cuh"
 
@@ -220,6 +221,7 @@ struct Plan {
   bool near;
   std::vector<int> alpha, alpha_off;
   int nch;            // far segments per line (d = 3: v2 chunks)
+  int vchunk;         // d = 3: v2 rows per far-field block
   int n_far_seg, n_far_items, near_per_sector, n_near_seg, n_lines_far, n_lines;
   size_t smem;
 };
@@ -351,10 +353,24 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.ell > 8) return fail(EZ_EINVAL, "ell = %d > 8", p.ell);
   p.prec = q.prec;
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
-  // default splitting parameter: the separable real-space contraction costs O(M) per node
-  // while the reciprocal sum costs O(terms); lam = 2 V^{1/d} (d <= 2), 2.5 V^{1/3} (d = 3)
-  // moves most of the work to real space (the result does not depend on lam)
-  p.lam = q.lambda > 0.0 ? q.lambda : (d == 3 ? 2.5 : 2.0) * std::pow(L->V, 1.0 / d);
+  // default splitting parameter (the result does not depend on lam): the separable
+  // real-space contraction costs O(M) per node, the reciprocal sum O(terms).  Measured
+  // optima on GB300: lam = 2 V^{1/d} for d <= 2; in 3-D 4 V^{1/3} for the FP64 form and
+  // 3 V^{1/3} for the mixed form, whose reciprocal tails are cheap binary32 work; capped so
+  // that the real-space box half-width stays <= 16
+  if (q.lambda > 0.0) {
+    p.lam = q.lambda;
+  } else {
+    const double f = d < 3 ? 2.0 : (p.prec == EZ_MIXED ? 3.0 : 4.0);
+    double amax = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double rn = 0.0;
+      for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+      amax = std::max(amax, std::sqrt(rn));
+    }
+    const double lam_cap = 16.0 / (std::sqrt(kTcut / kPi) * amax) * (1.0 - 1e-9);
+    p.lam = std::min(f * std::pow(L->V, 1.0 / d), q.r_real > 0.0 ? 1e300 : lam_cap);
+  }
   p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(kTcut / kPi);
   p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(kTcut / kPi) / p.lam;
   p.nsect = d * (1 << (d - 1));
@@ -516,8 +532,23 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     }
   }
 
-  // segments
-  p.nch = d == 3 ? (p.n_v + kVChunk - 1) / kVChunk : 1;
+  // segments.  d = 3: a far-field block takes vchunk = ceil(n_v / q) rows v2 of a line.
+  // The phase and H stages cost the same per block, so q is the smallest split whose
+  // shared memory fits two blocks per SM (~110 KB) and that still gives the sum at least
+  // four blocks per SM of the GPU (608); failing that, the most blocks with vchunk >= 8.
+  p.vchunk = 1;
+  if (d == 3) {
+    const long long lines = (long long)p.nsect * p.n_ui;
+    p.vchunk = std::min(p.n_v, kVChunkMin);
+    for (int q = 1; q <= p.n_v; ++q) {
+      const int c = (p.n_v + q - 1) / q;
+      if (c < kVChunkMin && q > 1) break;
+      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 110 * 1024) continue;
+      p.vchunk = c;
+      if (lines * ((p.n_v + c - 1) / c) >= 608) break;
+    }
+  }
+  p.nch = d == 3 ? (p.n_v + p.vchunk - 1) / p.vchunk : 1;
   if (d == 1) {
     p.n_far_seg = p.n_ui;
     p.n_far_items = (p.n_ui + 127) / 128;
@@ -530,7 +561,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   p.n_near_seg = p.nsect * p.near_per_sector;
   p.n_lines_far = p.nsect * p.n_ui;
   p.n_lines = p.n_lines_far + (p.near ? p.nsect : 0);
-  p.smem = far_smem_bytes(d, spec.n_distinct, p.M, p.n_v);
+  p.smem = far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, p.vchunk);
   return EZ_OK;
 }
 
@@ -804,8 +835,9 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_phj = hl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
   std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
+  std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req);
+      o_phig(n_req), o_gboxff(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -817,6 +849,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
     h_vn[r] = hl.take(sizeof(double) * p.vn.size());
     o_vw[r] = dl.take(sizeof(double) * p.vw.size());
     h_vw[r] = hl.take(sizeof(double) * p.vw.size());
+    o_vff[r] = dl.take(sizeof(float2) * p.vn.size());
+    h_vff[r] = hl.take(sizeof(float2) * p.vn.size());
+    o_vwff[r] = dl.take(sizeof(float2) * p.vw.size());
+    h_vwff[r] = hl.take(sizeof(float2) * p.vw.size());
     o_al[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
     h_al[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
     o_alo[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
@@ -834,6 +870,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_reclo[r] = dl.take(sizeof(float4) * p.rcap);
     o_rectmp[r] = dl.take(sizeof(G4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
+    o_gboxff[r] = p.prec == EZ_MIXED ? dl.take(sizeof(float2) * p.cells * p.spec.n_distinct) : 0;
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tabf[r].push_back(dl.take(sizeof(float) * kRec * p.phi[j].n_int));
     for (int j = 0; j < p.spec.n_distinct; ++j) o_tabff[r].push_back(dl.take(sizeof(float) * kRecFF * p.phi[j].n_int));
@@ -841,10 +878,15 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
   }
-  std::vector<size_t> o_phase(B.n_phase);
+  std::vector<size_t> o_phase(B.n_phase), o_phaseff(B.n_phase, 0);
+  std::vector<char> phase_mixed(B.n_phase, 0);
+  for (int r = 0; r < n_req; ++r)
+    if (phase_of[r] >= 0 && plans[r].prec == EZ_MIXED) phase_mixed[phase_of[r]] = 1;
   for (int g = 0; g < B.n_phase; ++g) {
     const Plan& p = plans[phase_rep[g]];
-    o_phase[g] = dl.take(sizeof(double2) * (size_t)p.n_ui * p.n_v * phase_mp1[g]);
+    const size_t n = (size_t)p.n_ui * p.n_v * phase_mp1[g];
+    o_phase[g] = dl.take(sizeof(double2) * n);
+    if (phase_mixed[g]) o_phaseff[g] = dl.take(sizeof(float4) * n);
   }
   B.o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
   B.o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
@@ -911,6 +953,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.M[i] = p.M[i];
       R.box[i] = p.box[i];
     }
+    R.vchunk = p.vchunk;
     R.gbox = (const double*)dptr(o_gbox[r]);
     R.rec = (const G4*)dptr(o_rec[r]);
     R.recf = (const float4*)dptr(o_recf[r]);
@@ -923,8 +966,22 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.u_w = (const double*)dptr(o_uw[r]);
     R.v_nodes = (const double*)dptr(o_vn[r]);
     R.v_w = (const double*)dptr(o_vw[r]);
+    R.v_ff = (const float2*)dptr(o_vff[r]);
+    R.vw_ff = (const float2*)dptr(o_vwff[r]);
+    {
+      float2* vf = (float2*)(Hs + h_vff[r]);
+      float2* wf = (float2*)(Hs + h_vwff[r]);
+      for (size_t i = 0; i < p.vn.size(); ++i) ff_split(p.vn[i], vf[i].x, vf[i].y);
+      for (size_t i = 0; i < p.vw.size(); ++i) ff_split(p.vw[i], wf[i].x, wf[i].y);
+      for (int j = 0; j < p.spec.n_distinct; ++j) {
+        ff_split(R.pref[j], R.pref_ff[j].x, R.pref_ff[j].y);
+        ff_split(R.two_over_nu[j], R.tov_ff[j].x, R.tov_ff[j].y);
+      }
+      ff_split(R.vol_fac, R.vol_ff.x, R.vol_ff.y);
+    }
     if (phase_of[r] >= 0) {
       R.phase = (const double2*)dptr(o_phase[phase_of[r]]);
+      R.phaseff = o_phaseff[phase_of[r]] ? (const float4*)dptr(o_phaseff[phase_of[r]]) : nullptr;
       R.phase_mp1 = phase_mp1[phase_of[r]];
     }
     std::memcpy(Hs + h_un[r], p.un.data(), sizeof(double) * p.n_ui);
@@ -957,6 +1014,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
     GJ.x_in_lattice = 1;
     GJ.R2 = p.r_real * p.r_real;
     GJ.out = (double*)dptr(o_gbox[r]);
+    GJ.outff = o_gboxff[r] ? (float2*)dptr(o_gboxff[r]) : nullptr;
+    R.gboxff = o_gboxff[r] ? (const float2*)dptr(o_gboxff[r]) : nullptr;
     if (p.near)
       for (int j = 0; j < p.spec.n_distinct; ++j) {
         TaylorJob& T = tjobs[itj++];
@@ -1005,6 +1064,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       phj[g].u = (const double*)dptr(o_un[r]);
       phj[g].v = p.d == 1 ? nullptr : (const double*)dptr(o_vn[r]);
       phj[g].out = (double2*)dptr(o_phase[g]);
+      phj[g].outff = o_phaseff[g] ? (float4*)dptr(o_phaseff[g]) : nullptr;
     }
   }
   // items (far: grouped by d, precision and exponent class, one launch per group; near after)
@@ -1245,7 +1305,7 @@ extern "C" int ez_batch_far_flops(ez_batch B, double* flops, long long* terms, l
       const double Mm = (p.M[0] + p.M[1] + p.M[2]) / 3.0;
       per_node += Mm * 4.0 * nd + 2.0 * nd;
       blocks = (double)p.nsect * p.n_ui * p.nch;
-      const double nv2 = std::min(kVChunk, p.n_v);
+      const double nv2 = std::min(p.vchunk, p.n_v);
       per_block = (Mm + 1) * p.n_v * 6.0 + (Mm + 1) * nv2 * 6.0 + nd * (Mm + 1) * (2 * Mm + 1) * Mm * 4.0 +
                   nd * (Mm + 1) * nv2 * Mm * 8.0;
     }

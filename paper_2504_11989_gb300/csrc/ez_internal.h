@@ -67,7 +67,7 @@ struct PhiInfo {
 constexpr int kMaxD = 3;
 constexpr int kMaxFactor = 64;
 constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
-constexpr int kVChunk = 16;      // v2 rows per block for d = 3
+constexpr int kVChunkMin = 8;   // d = 3: fewest v2 rows per far-field block
 
 struct ReqDesc {
   int d, nsect, n_ui, n_v, u_rule, n_distinct, n_prod, ell, prec;
@@ -79,8 +79,9 @@ struct ReqDesc {
   int islog[EZ_MAX_NU];
   // real space: full box prod_i (2 M_i + 1), g = 0 outside the ball and at m = 0
   int M[3], box[3];
+  int vchunk;          // d = 3: v2 rows per far-field block
   const double* gbox;  // [n_distinct][box0][box1][box2]
-  const float* gboxf;
+  const float2* gboxff; // the same as float-float (hi, lo), for the mixed form
   // reciprocal space: all h with |A^{-T} h| <= r_recip + max_BZ |k|
   int n_rec;
   const G4* rec;      // (G_0, G_1, G_2, |G|^2)
@@ -93,9 +94,14 @@ struct ReqDesc {
   const double* u_w;
   const double* v_nodes;
   const double* v_w;
+  const float2* v_ff;   // v nodes and weights as float-float, for the mixed form
+  const float2* vw_ff;
+  // float-float copies of the per-exponent constants, for the mixed form
+  float2 pref_ff[EZ_MAX_NU], tov_ff[EZ_MAX_NU], vol_ff;
   // d <= 2: powers e^{2 pi i m u v}, m = 0..phase_mp1-1, per (u node, v node); shared by every
   // sum of a batch with the same quadrature (the phases do not depend on the lattice)
   const double2* phase;
+  const float4* phaseff;  // the same as float-float complex (re hi, re lo, im hi, im lo)
   int phase_mp1;
   // near part
   int n_alpha;            // multi-indices with |alpha| even <= 2 ell

@@ -23,7 +23,7 @@ struct GboxJob {
   int x_in_lattice;
   double R2;
   double* out;
-  float* outf;
+  float2* outff;  // float-float copy (may be null)
 };
 
 struct PhiJob {
@@ -62,6 +62,7 @@ struct PhaseJob {
   const double* u;
   const double* v;  // NULL for d = 1 (v = 1)
   double2* out;     // [n_ui][n_v][mp1]
+  float4* outff;    // float-float copy (may be null)
 };
 
 struct EpsteinArgs {
@@ -103,7 +104,7 @@ __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, co
 __global__ void epstein_kernel(EpsteinArgs args);
 __global__ void phase_kernel(const PhaseJob* jobs);
 
-size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v);
+size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v, int vchunk);
 cudaError_t upload_cheb2mono(const double* host_matrix);  // kNC x kNC
 
 }  // namespace ez

@@ -2,7 +2,7 @@
 // (Thm "Epstein representation", Cor. "Duffy transformation", Sec. 3).
 //
 // Far field: a block owns one Duffy line (sector s, u node) -- for d = 3 one
-// chunk of kVChunk v2 rows of it.  On a line k~ = u sigma^j(p1 v1, p2 v2, 1), so
+// chunk of vchunk v2 rows of it.  On a line k~ = u sigma^j(p1 v1, p2 v2, 1), so
 // the real-space sum of every node factorises over the axes:
 //   sum_m g(m) e^{2 pi i m.k~} = sum_{ma} Ea(ma, v1) B(ma, v2),
 //   B(ma, v2) = sum_{mb} Eb(mb, v2) H(ma, mb),  H(ma, mb) = sum_{mc} g(m) e^{2 pi i mc u},
@@ -121,8 +121,8 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
 // binary32 tail, evaluated by a loop without branches (the cutoff is a select).  Tails
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
 template <int D, int NDM>
-__device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
-                                                const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
+__device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
+                                                ff* A, unsigned& terms, unsigned& coefs) {
   const int nrec = R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
@@ -131,15 +131,20 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   const float* tabff0 = sphi[0].tabff;
   const float4* recf = R->recf;
   const float4* reclo = R->reclo;
-  float klo[3] = {0.0f, 0.0f, 0.0f}, kn2 = 0.0f;
+  float kf[3] = {0.0f, 0.0f, 0.0f}, klo[3] = {0.0f, 0.0f, 0.0f}, kn2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    klo[i] = (float)(k[i] - (double)kf[i]);
+    kf[i] = kff[i].hi;
+    klo[i] = kff[i].lo;
     kn2 = fmaf(kf[i], kf[i], kn2);
   }
-  // |G| beyond which t > t_mix for this k (relative margin for the binary32 rounding)
-  const float gb = (sqrtf(tmix / cf) + sqrtf(kn2)) * 1.0001f;
+  // |G| beyond which t > t_mix for this k, and beyond which |G + k| > R (relative margins
+  // for the binary32 rounding)
+  const float kn = sqrtf(kn2);
+  const float gb = (sqrtf(tmix / cf) + kn) * 1.0001f;
   const float gb2 = gb * gb;
+  const float gc = (sqrtf(R2f) + kn) * 1.0001f;
+  const float gc2 = gc * gc;
   float sf[NDM], cpf[NDM], st[NDM];
   ff hs[NDM];
 #pragma unroll
@@ -173,23 +178,24 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     }
     if (tf < (float)kT0 || tf > t_hi) {  // rare: binary64 series / asymptotic branches
       const G4 G = ldg_g4(R->rec + h);
-      double qq;
-      if (D == 1) {
-        const double q0 = G.x + k[0];
-        qq = q0 * q0;
-      } else if (D == 2) {
-        const double q0 = G.x + k[0], q1 = G.y + k[1];
-        qq = fma(q0, q0, q1 * q1);
-      } else {
-        const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
-        qq = fma(q0, q0, fma(q1, q1, q2 * q2));
+      const double q0 = G.x + ((double)kf[0] + (double)klo[0]);
+      double qq = q0 * q0;
+      if (D >= 2) {
+        const double q1 = G.y + ((double)kf[1] + (double)klo[1]);
+        qq = fma(q1, q1, qq);
+      }
+      if (D >= 3) {
+        const double q2 = G.z + ((double)kf[2] + (double)klo[2]);
+        qq = fma(q2, q2, qq);
       }
       ++terms;
 #pragma unroll
       for (int j = 0; j < NDM; ++j)
         if (j < nd) {
           int n;
-          acc[j] += phi_eval_qq(sphi[j], qq, tf, n);
+          float hi, lo;
+          ff_split(phi_eval_qq(sphi[j], qq, tf, n), hi, lo);
+          hs[j] = ff_add(hs[j], ff{hi, lo});
           coefs += n;
         }
       continue;
@@ -224,10 +230,11 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
         coefs += n;
       }
   }
-  // the rest: binary32 tails only
+  // the rest: binary32 tails only, up to the cutoff
 #pragma unroll 2
   for (; h < nrec; ++h) {
     const float4 Gf = __ldg(recf + h);
+    if (Gf.w > gc2) break;
     float qqf;
     if (D == 1) {
       const float a = Gf.x + kf[0];
@@ -248,17 +255,41 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   }
 #pragma unroll
   for (int j = 0; j < NDM; ++j)
-    if (j < nd)
-      acc[j] += ((double)hs[j].hi + (double)hs[j].lo) + (((double)sf[j] - (double)cpf[j]) + (double)st[j]);
+    if (j < nd) A[j] = ff_add_f(ff_add_f(ff_add_f(hs[j], sf[j]), -cpf[j]), st[j]);
 }
 
-template <int D, bool MIXED, int NDM>
-__device__ __forceinline__ void recip_any(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
-                                          const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
-  if constexpr (MIXED)
-    recip_sum_mixed<D, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
-  else
-    recip_sum<D, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+// Mixed form, node assembly in float-float: Z_j = P_j (Zr_j + (lam^d/V) A_j - 2/nu_j)
+// (Zr: real-space part incl. the m = 0 column, A: reciprocal sum), then every product
+// prod_j Z_j^{e_pj} times the node weight w added to wsum.
+template <int NDM>
+__device__ __forceinline__ void assemble_mixed(const ReqDesc* R, int nd, int np, const ff* Zr, const ff* A, ff w,
+                                               ff (&wsum)[EZ_MAX_PROD]) {
+  ff Z[NDM];
+  const ff vol{R->vol_ff.x, R->vol_ff.y};
+#pragma unroll
+  for (int j = 0; j < NDM; ++j)
+    if (j < nd) {
+      ff t = ff_add(Zr[j], ff_mul(vol, A[j]));
+      t = ff_add(t, ff{-R->tov_ff[j].x, -R->tov_ff[j].y});
+      Z[j] = ff_mul(ff{R->pref_ff[j].x, R->pref_ff[j].y}, t);
+    }
+#pragma unroll
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    if (p >= np) break;
+    ff f{1.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < NDM; ++j)
+      if (j < nd)
+        for (int q = 0; q < R->expo[p][j]; ++q) f = ff_mul(f, Z[j]);
+    wsum[p] = ff_add(wsum[p], ff_mul(w, f));
+  }
+}
+
+// float-float of a binary64 value held in a register (per block or per node setup)
+__device__ __forceinline__ ff ffd(double x) {
+  ff r;
+  ff_split(x, r.hi, r.lo);
+  return r;
 }
 
 template <int NDM>
@@ -276,19 +307,47 @@ __device__ __forceinline__ void products(const ReqDesc* R, int nd, int np, const
   }
 }
 
-size_t far_smem_bytes(int d, int nd, const int* M, int n_v) {
+size_t far_smem_bytes(int d, int nd, const int* M, int n_v, int vchunk) {
   int Mx = 0;
   for (int i = 0; i < d; ++i) Mx = M[i] > Mx ? M[i] : Mx;
   size_t n = 0;
   if (d == 3)
-    n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * kVChunk + (Mx + 1) + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
-        (size_t)nd * (Mx + 1) * kVChunk;
+    n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * vchunk + (Mx + 1) + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
+        (size_t)nd * (Mx + 1) * vchunk;
   else if (d == 2)
     n = (size_t)(Mx + 1) + (size_t)nd * (Mx + 1);
   return n * sizeof(double2);
 }
 
+// Compensated dot product step (the Dot2 scheme of Ogita, Rump and Oishi, 2005, on
+// float-float operands): s + c += (a_hi + a_lo)(b_hi + b_lo).  The leading product and
+// the running sum are split exactly (two_prod, two_sum); the cross terms and the errors
+// go to c.  ~12 binary32 instructions, result as if accumulated with ~48 bits.
+__device__ __forceinline__ void dot2_acc(float& s, float& c, float a_hi, float a_lo, float b_hi, float b_lo) {
+  const float p = __fmul_rn(a_hi, b_hi);
+  float e = __fmaf_rn(a_hi, b_hi, -p);
+  e = __fmaf_rn(a_hi, b_lo, __fmaf_rn(a_lo, b_hi, e));
+  const ff t = ff_two_sum(s, p);
+  s = t.hi;
+  c = __fadd_rn(c, __fadd_rn(t.lo, e));
+}
+
+__device__ __forceinline__ float4 ff_complex(double2 z) {
+  float4 r;
+  ff_split(z.x, r.x, r.y);
+  ff_split(z.y, r.z, r.w);
+  return r;
+}
+
 // ------------------------------------------------------------------------- d = 3
+// Block: one Duffy line (sector, u) and vchunk rows v2 of it, all n_v values of v1.
+// Shared memory (16-byte entries): Ea[(Ma+1) n_v], Eb[(Mb+1) vchunk], Ec[Mc+1],
+// H[nd (Ma+1) (2Mb+1)], B[nd (Ma+1) vchunk].  H is stored folded over mb:
+// H(ma, 0), and for mb > 0  Hs = H(ma, mb) + H(ma, -mb) at +mb, Hd = H(ma, mb) - H(ma, -mb) at -mb,
+// so that with Eb(-mb) = conj Eb(mb):  B = H(ma,0) + sum_mb (Hs.re E.re - Hd.im E.im) + i (Hs.im E.re + Hd.re E.im).
+// FP64 form: every entry binary64.  Mixed form: phases, H and B are float-float complex
+// numbers (float4: re hi, re lo, im hi, im lo), B and the per-node contraction are
+// compensated dot products in binary32 (H itself is accumulated in binary64 once per block).
 template <bool MIXED, int NDM>
 __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__ reqs,
                                                        const Item* __restrict__ items, double* __restrict__ seg) {
@@ -296,7 +355,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
   __shared__ PhiInfo sphi[NDM];
   const Item it = items[blockIdx.x];
   const ReqDesc* R = reqs + it.req;
-  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
+  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v, vch = R->vchunk;
   load_phi(sphi, R, nd);
 
   const int j = it.sector >> 2, pb = it.sector & 3;
@@ -305,7 +364,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
   const double u = R->u_nodes[it.iu];
   const double wblk = 2.0 * R->u_w[it.iu] * u * u;
   const int Ma = R->M[ax_a], Mb = R->M[ax_b], Mc = R->M[ax_c];
-  const int v2_0 = it.chunk * kVChunk, nv2 = min(kVChunk, nv - v2_0);
+  const int v2_0 = it.chunk * vch, nv2 = min(vch, nv - v2_0);
   const int st[3] = {R->box[1] * R->box[2], R->box[2], 1};
   const int sta = st[ax_a], stb = st[ax_b], stc = st[ax_c];
   const int gbase = R->M[0] * st[0] + R->M[1] * st[1] + R->M[2] * st[2];
@@ -313,19 +372,25 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
 
   double2* Ea = reinterpret_cast<double2*>(smem_raw);
   double2* Eb = Ea + (Ma + 1) * nv;
-  double2* Ec = Eb + (Mb + 1) * kVChunk;
+  double2* Ec = Eb + (Mb + 1) * vch;
   double2* H = Ec + (Mc + 1);
   double2* B = H + nd * (Ma + 1) * (2 * Mb + 1);
+  float4* Ea4 = reinterpret_cast<float4*>(Ea);
+  float4* Eb4 = reinterpret_cast<float4*>(Eb);
+  float4* H4 = reinterpret_cast<float4*>(H);
+  float4* B4 = reinterpret_cast<float4*>(B);
 
   for (int v1 = threadIdx.x; v1 < nv; v1 += blockDim.x) {
     double sn, cs;
     sincospi(2.0 * (u * (p1 * R->v_nodes[v1])), &sn, &cs);
     const double2 e1 = make_double2(cs, sn);
     double2 e = make_double2(1.0, 0.0);
-    Ea[v1] = e;
-    for (int ma = 1; ma <= Ma; ++ma) {
-      e = cmul(e, e1);
-      Ea[ma * nv + v1] = e;
+    for (int ma = 0; ma <= Ma; ++ma) {
+      if (ma) e = cmul(e, e1);
+      if constexpr (MIXED)
+        Ea4[ma * nv + v1] = ff_complex(e);
+      else
+        Ea[ma * nv + v1] = e;
     }
   }
   for (int v2l = threadIdx.x; v2l < nv2; v2l += blockDim.x) {
@@ -333,47 +398,123 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
     sincospi(2.0 * (u * (p2 * R->v_nodes[v2_0 + v2l])), &sn, &cs);
     const double2 e1 = make_double2(cs, sn);
     double2 e = make_double2(1.0, 0.0);
-    Eb[v2l] = e;
-    for (int mb = 1; mb <= Mb; ++mb) {
-      e = cmul(e, e1);
-      Eb[mb * kVChunk + v2l] = e;
+    for (int mb = 0; mb <= Mb; ++mb) {
+      if (mb) e = cmul(e, e1);
+      if constexpr (MIXED)
+        Eb4[mb * vch + v2l] = ff_complex(e);
+      else
+        Eb[mb * vch + v2l] = e;
     }
   }
   if (threadIdx.x <= Mc) {
     double sn, cs;
     sincospi(2.0 * ((double)threadIdx.x * u), &sn, &cs);
-    Ec[threadIdx.x] = make_double2(cs, sn);
+    if constexpr (MIXED)
+      reinterpret_cast<float4*>(Ec)[threadIdx.x] = ff_complex(make_double2(cs, sn));
+    else
+      Ec[threadIdx.x] = make_double2(cs, sn);
   }
   __syncthreads();
 
-  const int nH = (Ma + 1) * (2 * Mb + 1);
-  for (int e = threadIdx.x; e < nd * nH; e += blockDim.x) {
-    const int jn = e / nH, r = e - jn * nH;
-    const int ma = r / (2 * Mb + 1), mb = r - ma * (2 * Mb + 1) - Mb;
-    const double* g = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
-    double hr = g[0], hi = 0.0;
-    for (int mc = 1; mc <= Mc; ++mc) {
-      const double gp = g[mc * stc], gm = g[-mc * stc];
-      hr = fma(gp + gm, Ec[mc].x, hr);
-      hi = fma(gp - gm, Ec[mc].y, hi);
+  // H(ma, +-mb) = sum_mc g(m) e^{2 pi i mc u}, one thread per (jn, ma, mb >= 0), folded
+  const int nH = (Ma + 1) * (2 * Mb + 1), nHp = (Ma + 1) * (Mb + 1);
+  if constexpr (MIXED) {
+    const float4* Ec4 = reinterpret_cast<const float4*>(Eb4 + (Mb + 1) * vch);
+    for (int e = threadIdx.x; e < nd * nHp; e += blockDim.x) {
+      const int jn = e / nHp, r = e - jn * nHp;
+      const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
+      const float2* gp_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta + mb * stb;
+      const float2* gm_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta - mb * stb;
+      // H(ma, +mb) and H(ma, -mb): real parts pair g(+mc) + g(-mc) with cos, imaginary
+      // parts g(+mc) - g(-mc) with sin
+      float s0 = gp_[0].x, c0 = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
+      for (int mc = 1; mc <= Mc; ++mc) {
+        const float4 E = Ec4[mc];
+        const float2 a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
+        dot2_acc(s0, c0, a.x, a.y, E.x, E.y);
+        dot2_acc(s0, c0, b.x, b.y, E.x, E.y);
+        dot2_acc(s1, c1, a.x, a.y, E.z, E.w);
+        dot2_acc(s1, c1, -b.x, -b.y, E.z, E.w);
+        dot2_acc(s2, c2, c.x, c.y, E.x, E.y);
+        dot2_acc(s2, c2, dd.x, dd.y, E.x, E.y);
+        dot2_acc(s3, c3, c.x, c.y, E.z, E.w);
+        dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
+      }
+      const ff pr = ff_two_sum(s0, c0), pi = ff_two_sum(s1, c1), mr = ff_two_sum(s2, c2), mi = ff_two_sum(s3, c3);
+      const int base = jn * nH + ma * (2 * Mb + 1) + Mb;
+      if (mb == 0) {
+        H4[base] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+      } else {
+        const ff sr = ff_add(pr, mr), si = ff_add(pi, mi);
+        const ff dr = ff_add(pr, ff{-mr.hi, -mr.lo}), di = ff_add(pi, ff{-mi.hi, -mi.lo});
+        H4[base + mb] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+        H4[base - mb] = make_float4(dr.hi, dr.lo, di.hi, di.lo);
+      }
     }
-    H[e] = make_double2(hr, hi);
+  } else
+  for (int e = threadIdx.x; e < nd * nHp; e += blockDim.x) {
+    const int jn = e / nHp, r = e - jn * nHp;
+    const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
+    const double* gp_ = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
+    const double* gm_ = R->gbox + (size_t)jn * cells + gbase + ma * sta - mb * stb;
+    double pr = gp_[0], pi = 0.0, mr = gm_[0], mi = 0.0;
+    for (int mc = 1; mc <= Mc; ++mc) {
+      const double2 E = Ec[mc];
+      const double a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
+      pr = fma(a + b, E.x, pr);
+      pi = fma(a - b, E.y, pi);
+      mr = fma(c + dd, E.x, mr);
+      mi = fma(c - dd, E.y, mi);
+    }
+    double2 hs, hd;
+    if (mb == 0) {
+      hs = make_double2(pr, pi);
+      hd = hs;
+    } else {
+      hs = make_double2(pr + mr, pi + mi);
+      hd = make_double2(pr - mr, pi - mi);
+    }
+    const int base = jn * nH + ma * (2 * Mb + 1) + Mb;
+    if constexpr (MIXED) {
+      H4[base + mb] = ff_complex(hs);
+      if (mb) H4[base - mb] = ff_complex(hd);
+    } else {
+      H[base + mb] = hs;
+      if (mb) H[base - mb] = hd;
+    }
   }
   __syncthreads();
 
+  // B(ma, v2) = H(ma, 0) + sum_{mb >= 1} (Hs E, Hd E) as above
   const int nB = (Ma + 1) * nv2;
   for (int e = threadIdx.x; e < nd * nB; e += blockDim.x) {
     const int jn = e / nB, r = e - jn * nB;
     const int ma = r / nv2, v2l = r - ma * nv2;
-    const double2* h = H + (jn * (Ma + 1) + ma) * (2 * Mb + 1) + Mb;
-    double br = h[0].x, bi = h[0].y;
-    for (int mb = 1; mb <= Mb; ++mb) {
-      const double2 E = Eb[mb * kVChunk + v2l];
-      const double2 hp = h[mb], hm = h[-mb];
-      br = fma(hp.x + hm.x, E.x, fma(hm.y - hp.y, E.y, br));
-      bi = fma(hp.y + hm.y, E.x, fma(hp.x - hm.x, E.y, bi));
+    const int hb = (jn * (Ma + 1) + ma) * (2 * Mb + 1) + Mb;
+    if constexpr (MIXED) {
+      const float4* h = H4 + hb;
+      float sr = h[0].x, cr = h[0].y, si = h[0].z, ci = h[0].w;
+      for (int mb = 1; mb <= Mb; ++mb) {
+        const float4 E = Eb4[mb * vch + v2l];
+        const float4 hs = h[mb], hd = h[-mb];
+        dot2_acc(sr, cr, hs.x, hs.y, E.x, E.y);
+        dot2_acc(sr, cr, -hd.z, -hd.w, E.z, E.w);
+        dot2_acc(si, ci, hs.z, hs.w, E.x, E.y);
+        dot2_acc(si, ci, hd.x, hd.y, E.z, E.w);
+      }
+      const ff re = ff_two_sum(sr, cr), im = ff_two_sum(si, ci);
+      B4[(jn * (Ma + 1) + ma) * vch + v2l] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    } else {
+      const double2* h = H + hb;
+      double br = h[0].x, bi = h[0].y;
+      for (int mb = 1; mb <= Mb; ++mb) {
+        const double2 E = Eb[mb * vch + v2l];
+        const double2 hs = h[mb], hd = h[-mb];
+        br = fma(hs.x, E.x, fma(-hd.y, E.y, br));
+        bi = fma(hs.y, E.x, fma(hd.x, E.y, bi));
+      }
+      B[(jn * (Ma + 1) + ma) * vch + v2l] = make_double2(br, bi);
     }
-    B[(jn * (Ma + 1) + ma) * kVChunk + v2l] = make_double2(br, bi);
   }
   __syncthreads();
 
@@ -387,35 +528,75 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   unsigned terms = 0, coefs = 0;
   const int nn = nv * nv2;
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-    const int v2l = n / nv, v1 = n - v2l * nv;
-    const double kta = u * (p1 * R->v_nodes[v1]);
-    const double ktb = u * (p2 * R->v_nodes[v2_0 + v2l]);
-    const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
-    double k[3];
+  if constexpr (MIXED) {
+    // k = alpha v1 + beta v2 + gamma in float-float (alpha = u p1 A^{-T} e_a, ...)
+    ff al[3], be[3], ga[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) k[i] = fma(kca[i], kta, fma(kcb[i], ktb, kcc[i] * u));
-    double Z[NDM], acc[NDM];
-#pragma unroll
-    for (int jn = 0; jn < NDM; ++jn) {
-      acc[jn] = 0.0;
-      if (jn < nd) {
-        const double2* b = B + jn * (Ma + 1) * kVChunk + v2l;
-        double sr = 0.0;
-        for (int ma = 1; ma <= Ma; ++ma) {
-          const double2 E = Ea[ma * nv + v1];
-          const double2 bb = b[ma * kVChunk];
-          sr = fma(E.x, bb.x, fma(-E.y, bb.y, sr));
-        }
-        Z[jn] = fma(2.0, sr, b[0].x);
-      }
+    for (int i = 0; i < 3; ++i) {
+      al[i] = ffd(kca[i] * (u * p1));
+      be[i] = ffd(kcb[i] * (u * p2));
+      ga[i] = ffd(kcc[i] * u);
     }
-    const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-    recip_any<3, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+    ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+      const int v2l = n / nv, v1 = n - v2l * nv;
+      const float2 a1 = __ldg(R->v_ff + v1), a2 = __ldg(R->v_ff + v2_0 + v2l);
+      const float2 w1 = __ldg(R->vw_ff + v1), w2 = __ldg(R->vw_ff + v2_0 + v2l);
+      const ff x1{a1.x, a1.y}, x2{a2.x, a2.y};
+      ff k[3];
 #pragma unroll
-    for (int jn = 0; jn < NDM; ++jn)
-      if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
-    products<NDM>(R, nd, np, Z, wv, wsum);
+      for (int i = 0; i < 3; ++i) k[i] = ff_add(ff_add(ff_mul(al[i], x1), ff_mul(be[i], x2)), ga[i]);
+      ff Zr[NDM], A[NDM];
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn)
+        if (jn < nd) {
+          const float4* b = B4 + jn * (Ma + 1) * vch + v2l;
+          float s = 0.0f, c = 0.0f;
+          for (int ma = 1; ma <= Ma; ++ma) {
+            const float4 E = Ea4[ma * nv + v1];
+            const float4 bb = b[ma * vch];
+            dot2_acc(s, c, E.x, E.y, bb.x, bb.y);
+            dot2_acc(s, c, -E.z, -E.w, bb.z, bb.w);
+          }
+          const ff S = ff_two_sum(s, c);
+          Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b[0].x, b[0].y});
+        }
+      recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs);
+      assemble_mixed<NDM>(R, nd, np, Zr, A, ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y}), ws);
+    }
+#pragma unroll
+    for (int p = 0; p < EZ_MAX_PROD; ++p) wsum[p] = (double)ws[p].hi + (double)ws[p].lo;
+  } else {
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+      const int v2l = n / nv, v1 = n - v2l * nv;
+      const double kta = u * (p1 * R->v_nodes[v1]);
+      const double ktb = u * (p2 * R->v_nodes[v2_0 + v2l]);
+      const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
+      double k[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) k[i] = fma(kca[i], kta, fma(kcb[i], ktb, kcc[i] * u));
+      double Z[NDM], acc[NDM];
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn) {
+        acc[jn] = 0.0;
+        if (jn < nd) {
+          const double2* b = B + jn * (Ma + 1) * vch + v2l;
+          double sr = 0.0;
+          for (int ma = 1; ma <= Ma; ++ma) {
+            const double2 E = Ea[ma * nv + v1];
+            const double2 bb = b[ma * vch];
+            sr = fma(E.x, bb.x, fma(-E.y, bb.y, sr));
+          }
+          Z[jn] = fma(2.0, sr, b[0].x);
+        }
+      }
+      const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+      recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn)
+        if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
+      products<NDM>(R, nd, np, Z, wv, wsum);
+    }
   }
   count_work(R, terms, coefs);
   block_reduce_store<256>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
@@ -458,13 +639,56 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
       hr = fma(gp + gm, Ec[mc].x, hr);
       hi = fma(gp - gm, Ec[mc].y, hi);
     }
-    H[e] = make_double2(hr, hi);
+    if constexpr (MIXED)
+      reinterpret_cast<float4*>(H)[e] = ff_complex(make_double2(hr, hi));
+    else
+      H[e] = make_double2(hr, hi);
   }
   __syncthreads();
   const double kca0 = R->AiT[0 * 2 + ax_a], kca1 = R->AiT[1 * 2 + ax_a];
   const double kcc0 = R->AiT[0 * 2 + ax_c], kcc1 = R->AiT[1 * 2 + ax_c];
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   unsigned terms = 0, coefs = 0;
+  if constexpr (MIXED) {
+    // k = alpha v + gamma in float-float; real space by compensated dot products on the
+    // float-float phase table (conjugated for p1 = -1) and H
+    const float4* H4 = reinterpret_cast<const float4*>(H);
+    const ff al[2] = {ffd(kca0 * (u * p1)), ffd(kca1 * (u * p1))};
+    const ff ga[2] = {ffd(kcc0 * u), ffd(kcc1 * u)};
+    const float sg = (float)p1;
+    ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const float2 a = __ldg(R->v_ff + v), wv = __ldg(R->vw_ff + v);
+      const ff x{a.x, a.y};
+      const ff k[2] = {ff_add(ff_mul(al[0], x), ga[0]), ff_add(ff_mul(al[1], x), ga[1])};
+      const float4* ph = R->phaseff + ((size_t)it.iu * nv + v) * R->phase_mp1;
+      float s[NDM], c[NDM];
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn) s[jn] = c[jn] = 0.0f;
+      for (int ma = 1; ma <= Ma; ++ma) {
+        const float4 e = __ldg(ph + ma);
+#pragma unroll
+        for (int jn = 0; jn < NDM; ++jn)
+          if (jn < nd) {
+            const float4 hh = H4[jn * (Ma + 1) + ma];
+            dot2_acc(s[jn], c[jn], e.x, e.y, hh.x, hh.y);
+            dot2_acc(s[jn], c[jn], -sg * e.z, -sg * e.w, hh.z, hh.w);
+          }
+      }
+      ff Zr[NDM], A[NDM];
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn)
+        if (jn < nd) {
+          const ff S = ff_two_sum(s[jn], c[jn]);
+          const float4 h0 = H4[jn * (Ma + 1)];
+          Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{h0.x, h0.y});
+        }
+      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs);
+      assemble_mixed<NDM>(R, nd, np, Zr, A, ff{wv.x, wv.y}, ws);
+    }
+#pragma unroll
+    for (int p = 0; p < EZ_MAX_PROD; ++p) wsum[p] = (double)ws[p].hi + (double)ws[p].lo;
+  } else
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const double kta = u * (p1 * R->v_nodes[v]);
     const double wv = R->v_w[v];
@@ -489,7 +713,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_any<2, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -514,6 +738,36 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   const double u = R->u_nodes[iu];
   const double w = 2.0 * R->u_w[iu];
   const int M = R->M[0];
+  unsigned terms = 0, coefs = 0;
+  double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+  if constexpr (MIXED) {
+    const ff k[1] = {ffd(R->AiT[0] * u)};
+    const float4* ph = R->phaseff + (size_t)iu * R->phase_mp1;
+    float s[NDM], c[NDM];
+#pragma unroll
+    for (int jn = 0; jn < NDM; ++jn) s[jn] = c[jn] = 0.0f;
+    for (int m = 1; m <= M; ++m) {
+      const float4 e = __ldg(ph + m);
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn)
+        if (jn < nd) {
+          const float2 g = __ldg(R->gboxff + (size_t)jn * R->box[0] + M + m);
+          dot2_acc(s[jn], c[jn], g.x, g.y, e.x, e.y);
+        }
+    }
+    ff Zr[NDM], A[NDM];
+#pragma unroll
+    for (int jn = 0; jn < NDM; ++jn)
+      if (jn < nd) {
+        const ff S = ff_two_sum(s[jn], c[jn]);
+        Zr[jn] = ff{2.0f * S.hi, 2.0f * S.lo};
+      }
+    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs);
+    ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    assemble_mixed<NDM>(R, nd, np, Zr, A, ffd(w), ws);
+#pragma unroll
+    for (int p = 0; p < EZ_MAX_PROD; ++p) f[p] = (double)ws[p].hi + (double)ws[p].lo;
+  } else {
   double k[1] = {R->AiT[0] * u};
   const double2* ph = R->phase + (size_t)iu * R->phase_mp1;
   double sr[NDM], acc[NDM], Z[NDM];
@@ -525,14 +779,13 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
-  unsigned terms = 0, coefs = 0;
   const float kf[1] = {(float)k[0]};
-  recip_any<1, MIXED, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
 #pragma unroll
   for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
-  double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   products<NDM>(R, nd, np, Z, w, f);
+  }
   double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;
   for (int p = 0; p < np; ++p) o[p] = f[p];
   if (R->work) {  // some lanes left early: plain atomics, no warp shuffle

@@ -138,7 +138,11 @@ __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs
   bool excluded = J.x_in_lattice ? center : false;
   if (!excluded && r2 <= J.R2 && r2 > 0.0) g = phi_accurate(0.5 * R->nu[jn], kPi * r2 / (R->lam * R->lam));
   J.out[idx] = g;
-  if (J.outf) J.outf[idx] = (float)g;
+  if (J.outff) {
+    float hi, lo;
+    ff_split(g, hi, lo);
+    J.outff[idx] = make_float2(hi, lo);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -427,11 +431,17 @@ __global__ void phase_kernel(const PhaseJob* jobs) {
   double sn, cs;
   sincospi(2.0 * arg, &sn, &cs);
   double2* o = J.out + (size_t)i * J.mp1;
+  float4* off = J.outff ? J.outff + (size_t)i * J.mp1 : nullptr;
   double2 e = make_double2(1.0, 0.0);
-  o[0] = e;
-  for (int m = 1; m < J.mp1; ++m) {
-    e = make_double2(fma(e.x, cs, -e.y * sn), fma(e.x, sn, e.y * cs));
+  for (int m = 0; m < J.mp1; ++m) {
+    if (m) e = make_double2(fma(e.x, cs, -e.y * sn), fma(e.x, sn, e.y * cs));
     o[m] = e;
+    if (off) {
+      float4 f;
+      ff_split(e.x, f.x, f.y);
+      ff_split(e.y, f.z, f.w);
+      off[m] = f;
+    }
   }
 }
 
