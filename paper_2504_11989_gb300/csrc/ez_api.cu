@@ -203,7 +203,8 @@ static void gauss_legendre01_cached(int n, std::vector<double>& x, std::vector<d
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr double kTcut = 45.0;  // default cutoffs: exp(-45) ~ 3e-20
+constexpr double kTcut = 45.0;       // default cutoffs, FP64 form: exp(-45) ~ 3e-20
+constexpr double kTcutMixed = 36.0;  // mixed form (stated bound 1e-10): exp(-36) ~ 2e-16
 
 struct Plan {
   const ez_lattice_s* L;
@@ -222,6 +223,7 @@ struct Plan {
   std::vector<int> alpha, alpha_off;
   int nch;            // far segments per line (d = 3: v2 chunks)
   int vchunk;         // d = 3: v2 rows per far-field block
+  int m_hp[3];        // mixed form: |m_i| >= m_hp[i] summed in plain binary32
   int n_far_seg, n_far_items, near_per_sector, n_near_seg, n_lines_far, n_lines;
   size_t smem;
 };
@@ -264,6 +266,8 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
       P.ser[n] = -sg / (fact * (a + n));
     }
   }
+  for (int n = 0; n < kNSer; ++n) ff_split(P.ser[n], P.ser_ff[n].x, P.ser_ff[n].y);
+  ff_split(P.gam, P.gam_ff.x, P.gam_ff.y);
 }
 
 // regularised h = 0 series (lambda piece of the log case included)
@@ -358,6 +362,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   // optima on GB300: lam = 2 V^{1/d} for d <= 2; in 3-D 4 V^{1/3} for the FP64 form and
   // 3 V^{1/3} for the mixed form, whose reciprocal tails are cheap binary32 work; capped so
   // that the real-space box half-width stays <= 16
+  const double tcut = p.prec == EZ_MIXED ? kTcutMixed : kTcut;
   if (q.lambda > 0.0) {
     p.lam = q.lambda;
   } else {
@@ -368,11 +373,11 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
       for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
       amax = std::max(amax, std::sqrt(rn));
     }
-    const double lam_cap = 16.0 / (std::sqrt(kTcut / kPi) * amax) * (1.0 - 1e-9);
+    const double lam_cap = 16.0 / (std::sqrt(tcut / kPi) * amax) * (1.0 - 1e-9);
     p.lam = std::min(f * std::pow(L->V, 1.0 / d), q.r_real > 0.0 ? 1e300 : lam_cap);
   }
-  p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(kTcut / kPi);
-  p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(kTcut / kPi) / p.lam;
+  p.r_real = q.r_real > 0.0 ? q.r_real : p.lam * std::sqrt(tcut / kPi);
+  p.r_recip = q.r_recip > 0.0 ? q.r_recip : std::sqrt(tcut / kPi) / p.lam;
   p.nsect = d * (1 << (d - 1));
   p.near = p.u_rule == 2;
 
@@ -389,6 +394,44 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     }
     p.box[i] = 2 * p.M[i] + 1;
     p.cells *= p.box[i];
+  }
+  // mixed form: along lattice axis i, real-space terms with |m_i| >= m_hp[i] are below
+  // 1e-8 of the nearest-neighbour term (|z| >= |m_i| / |row_i(A^{-1})|, Phi decreasing),
+  // so the contraction stages sum them in plain binary32
+  {
+    double dmin2 = 1e300;
+    for (int a = -2; a <= 2; ++a)
+      for (int b = (d > 1 ? -2 : 0); b <= (d > 1 ? 2 : 0); ++b)
+        for (int c = (d > 2 ? -2 : 0); c <= (d > 2 ? 2 : 0); ++c) {
+          if (!a && !b && !c) continue;
+          const int m[3] = {a, b, c};
+          double r2 = 0.0;
+          for (int i = 0; i < d; ++i) {
+            double z = 0.0;
+            for (int j = 0; j < d; ++j) z += L->A[i * d + j] * m[j];
+            r2 += z * z;
+          }
+          dmin2 = std::min(dmin2, r2);
+        }
+    for (int i = 0; i < 3; ++i) {
+      p.m_hp[i] = p.M[i] + 1;
+      if (i >= d) continue;
+      double rn = 0.0;
+      for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+      for (int m = 1; m <= p.M[i]; ++m) {
+        bool small = true;
+        for (int j = 0; j < spec.n_distinct && small; ++j) {
+          const double a = 0.5 * spec.nu[j];
+          const double ref = std::fabs(phi_accurate(a, kPi * dmin2 / (p.lam * p.lam)));
+          const double tail = std::fabs(phi_accurate(a, kPi * (m * m / rn) / (p.lam * p.lam)));
+          small = tail <= 1e-8 * ref;
+        }
+        if (small) {
+          p.m_hp[i] = m;
+          break;
+        }
+      }
+    }
   }
   // reciprocal enumeration: |A^{-T} h| <= r_recip + max_BZ |k|
   double kmax = 0.0;
@@ -954,6 +997,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.box[i] = p.box[i];
     }
     R.vchunk = p.vchunk;
+    for (int i = 0; i < 3; ++i) R.m_hp[i] = p.m_hp[i];
     R.gbox = (const double*)dptr(o_gbox[r]);
     R.rec = (const G4*)dptr(o_rec[r]);
     R.recf = (const float4*)dptr(o_recf[r]);
@@ -961,6 +1005,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.R2f = (float)(p.r_recip * p.r_recip);
     R.work = (unsigned long long*)dptr(B.o_work) + 2 * r;
     R.c_lam_f = (float)R.c_lam;
+    ff_split(R.c_lam, R.c_lam_ff.x, R.c_lam_ff.y);
     R.n_rec = 0;
     R.u_nodes = (const double*)dptr(o_un[r]);
     R.u_w = (const double*)dptr(o_uw[r]);

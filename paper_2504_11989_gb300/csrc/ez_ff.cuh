@@ -72,6 +72,23 @@ __device__ __forceinline__ ff ff_add4(float a_hi, float a_lo, float b_hi, float 
   return ff_fast_two_sum(s.hi, s.lo);
 }
 
+// 1 / a: binary32 reciprocal refined by one Newton step with the residual 1 - a y
+// computed exactly by fma
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  const float y = __frcp_rn(a.hi);
+  float e = __fmaf_rn(-a.hi, y, 1.0f);
+  e = __fmaf_rn(-a.lo, y, e);
+  return ff_fast_two_sum(y, __fmul_rn(y, e));
+}
+
+// sqrt(a), a > 0: binary32 root refined by one Newton step, a - y^2 from two_prod
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  const float y = sqrtf(a.hi);
+  const ff p = ff_two_prod(y, y);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+  return ff_fast_two_sum(y, __fdividef(r, __fmul_rn(2.0f, y)));
+}
+
 // split of a binary64 value (setup and per-node code; not for inner loops)
 __host__ __device__ __forceinline__ void ff_split(double x, float& hi, float& lo) {
   hi = (float)x;

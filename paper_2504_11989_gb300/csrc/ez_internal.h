@@ -59,6 +59,8 @@ struct PhiInfo {
   const float* tabf;  // binary32 table (own polynomial lengths) for the mixed form (device)
   const float* tabff; // float-float table (n_int * kRecFF floats) for the mixed form (device)
   double ser[kNSer];  // entire part for t < kT0
+  float2 ser_ff[kNSer];  // the same as float-float, and Gamma(a) (or (-1)^m/m!), for the mixed form
+  float2 gam_ff;
 };
 
 // ---------------------------------------------------------------------------
@@ -80,6 +82,7 @@ struct ReqDesc {
   // real space: full box prod_i (2 M_i + 1), g = 0 outside the ball and at m = 0
   int M[3], box[3];
   int vchunk;          // d = 3: v2 rows per far-field block
+  int m_hp[3];         // mixed form: real-space terms with |m_i| >= m_hp[i] are summed in binary32
   const double* gbox;  // [n_distinct][box0][box1][box2]
   const float2* gboxff; // the same as float-float (hi, lo), for the mixed form
   // reciprocal space: all h with |A^{-T} h| <= r_recip + max_BZ |k|
@@ -88,6 +91,7 @@ struct ReqDesc {
   const float4* recf; // the same in binary32, for the cutoff screen
   const float4* reclo; // G - (double)recf (binary32): recf + reclo is G as float-float
   float R2f, c_lam_f;
+  float2 c_lam_ff;    // c_lam as float-float
   PhiInfo phi[EZ_MAX_NU];
   // quadrature
   const double* u_nodes;

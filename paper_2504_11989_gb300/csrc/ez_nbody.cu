@@ -111,6 +111,54 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
   }
 }
 
+// Mixed form, t < kT0 (the h = 0 term near k = 0): Phi_a(t) = sum_n ser_n t^n + singular
+// part, the series in float-float; the singular part gam t^{-a} from float-float 1/t and
+// sqrt(t), or -gam t^m log t with log t taken once in binary64 for every exponent.
+template <int NDM>
+__device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, ff t, ff* hs, unsigned& coefs) {
+  bool need_log = false, need_inv = false, need_sqrt = false;
+#pragma unroll
+  for (int j = 0; j < NDM; ++j)
+    if (j < nd) {
+      const int e = -sphi[j].two_a;
+      need_log |= sphi[j].log_m >= 0;
+      need_inv |= sphi[j].log_m < 0 && e < 0;
+      need_sqrt |= sphi[j].log_m < 0 && (e & 1);
+    }
+  ff lt{0.0f, 0.0f}, inv{0.0f, 0.0f}, sq{0.0f, 0.0f};
+  if (need_log) {
+    float hi, lo;
+    ff_split(log((double)t.hi + (double)t.lo), hi, lo);
+    lt = ff{hi, lo};
+  }
+  if (need_inv) inv = ff_rcp(t);
+  if (need_sqrt) sq = ff_sqrt(t);
+#pragma unroll
+  for (int j = 0; j < NDM; ++j)
+    if (j < nd) {
+      const PhiInfo& P = sphi[j];
+      ff p{P.ser_ff[kNSer - 1].x, P.ser_ff[kNSer - 1].y};
+#pragma unroll 1
+      for (int n = kNSer - 2; n >= 0; --n) p = ff_add(ff_mul(p, t), ff{P.ser_ff[n].x, P.ser_ff[n].y});
+      const ff gam{P.gam_ff.x, P.gam_ff.y};
+      if (P.log_m >= 0) {
+        ff tm{1.0f, 0.0f};
+        for (int q = 0; q < P.log_m; ++q) tm = ff_mul(tm, t);
+        const ff sgl = ff_mul(ff_mul(gam, tm), lt);
+        p = ff_add(p, ff{-sgl.hi, -sgl.lo});
+      } else {
+        const int e = -P.two_a;  // power of sqrt(t)
+        ff r = (e & 1) ? sq : ff{1.0f, 0.0f};
+        const int kk = e >> 1;  // floor(e / 2)
+        const ff base = kk < 0 ? inv : t;
+        for (int q = 0; q < (kk < 0 ? -kk : kk); ++q) r = ff_mul(r, base);
+        p = ff_add(p, ff_mul(gam, r));
+      }
+      hs[j] = ff_add(hs[j], p);
+      coefs += kNSer;
+    }
+}
+
 // Mixed form of the same sum.  Terms by t = pi lam^2 |G + k|^2 (binary32 screen):
 //  * t >= t_mix (|Phi| t <= 1e-7 beyond it): binary32, e^{-t} t^{-1} P(t_mix/t);
 //  * t_mid <= t < t_mix (|Phi| <= 1e-6): float-float argument, binary32 polynomial;
@@ -176,7 +224,19 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
         if (j < nd) st[j] = fmaf(e, phi_tail_poly(sphi[j], sv), st[j]);
       continue;
     }
-    if (tf < (float)kT0 || tf > t_hi) {  // rare: binary64 series / asymptotic branches
+    if (tf < (float)kT0) {  // near the origin: float-float series and singular part
+      const float4 Gl = __ldg(reclo + h);
+      ff qq = ff_sqr(ff_add4(Gf.x, Gl.x, kf[0], klo[0]));
+      if (D >= 2) qq = ff_add(qq, ff_sqr(ff_add4(Gf.y, Gl.y, kf[1], klo[1])));
+      if (D >= 3) qq = ff_add(qq, ff_sqr(ff_add4(Gf.z, Gl.z, kf[2], klo[2])));
+      const ff t = ff_mul(ff{R->c_lam_ff.x, R->c_lam_ff.y}, qq);
+      if (t.hi > 0.0f) {
+        ++terms;
+        phi_small_mixed<NDM>(sphi, nd, t, hs, coefs);
+        continue;
+      }
+    }
+    if (tf < (float)kT0 || tf > t_hi) {  // rare: t = 0, or beyond the table: binary64
       const G4 G = ldg_g4(R->rec + h);
       const double q0 = G.x + ((double)kf[0] + (double)klo[0]);
       double qq = q0 * q0;
@@ -428,7 +488,8 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       // H(ma, +mb) and H(ma, -mb): real parts pair g(+mc) + g(-mc) with cos, imaginary
       // parts g(+mc) - g(-mc) with sin
       float s0 = gp_[0].x, c0 = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
-      for (int mc = 1; mc <= Mc; ++mc) {
+      const int mc_hp = min(Mc + 1, R->m_hp[ax_c]);
+      for (int mc = 1; mc < mc_hp; ++mc) {
         const float4 E = Ec4[mc];
         const float2 a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
         dot2_acc(s0, c0, a.x, a.y, E.x, E.y);
@@ -440,6 +501,19 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
         dot2_acc(s3, c3, c.x, c.y, E.z, E.w);
         dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
       }
+      float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;  // |mc| >= m_hp: below 1e-8, binary32
+      for (int mc = mc_hp; mc <= Mc; ++mc) {
+        const float4 E = Ec4[mc];
+        const float a = gp_[mc * stc].x, b = gp_[-mc * stc].x, c = gm_[mc * stc].x, dd = gm_[-mc * stc].x;
+        q0 = fmaf(a + b, E.x, q0);
+        q1 = fmaf(a - b, E.z, q1);
+        q2 = fmaf(c + dd, E.x, q2);
+        q3 = fmaf(c - dd, E.z, q3);
+      }
+      c0 += q0;
+      c1 += q1;
+      c2 += q2;
+      c3 += q3;
       const ff pr = ff_two_sum(s0, c0), pi = ff_two_sum(s1, c1), mr = ff_two_sum(s2, c2), mi = ff_two_sum(s3, c3);
       const int base = jn * nH + ma * (2 * Mb + 1) + Mb;
       if (mb == 0) {
@@ -494,7 +568,8 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
     if constexpr (MIXED) {
       const float4* h = H4 + hb;
       float sr = h[0].x, cr = h[0].y, si = h[0].z, ci = h[0].w;
-      for (int mb = 1; mb <= Mb; ++mb) {
+      const int mb_hp = min(Mb + 1, R->m_hp[ax_b]);
+      for (int mb = 1; mb < mb_hp; ++mb) {
         const float4 E = Eb4[mb * vch + v2l];
         const float4 hs = h[mb], hd = h[-mb];
         dot2_acc(sr, cr, hs.x, hs.y, E.x, E.y);
@@ -502,6 +577,15 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
         dot2_acc(si, ci, hs.z, hs.w, E.x, E.y);
         dot2_acc(si, ci, hd.x, hd.y, E.z, E.w);
       }
+      float pr = 0.0f, pi = 0.0f;  // |mb| >= m_hp: binary32
+      for (int mb = mb_hp; mb <= Mb; ++mb) {
+        const float4 E = Eb4[mb * vch + v2l];
+        const float4 hs = h[mb], hd = h[-mb];
+        pr = fmaf(hs.x, E.x, fmaf(-hd.z, E.z, pr));
+        pi = fmaf(hs.z, E.x, fmaf(hd.x, E.z, pi));
+      }
+      cr += pr;
+      ci += pi;
       const ff re = ff_two_sum(sr, cr), im = ff_two_sum(si, ci);
       B4[(jn * (Ma + 1) + ma) * vch + v2l] = make_float4(re.hi, re.lo, im.hi, im.lo);
     } else {
@@ -538,6 +622,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       ga[i] = ffd(kcc[i] * u);
     }
     ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
     for (int n = threadIdx.x; n < nn; n += blockDim.x) {
       const int v2l = n / nv, v1 = n - v2l * nv;
       const float2 a1 = __ldg(R->v_ff + v1), a2 = __ldg(R->v_ff + v2_0 + v2l);
@@ -551,14 +636,19 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       for (int jn = 0; jn < NDM; ++jn)
         if (jn < nd) {
           const float4* b = B4 + jn * (Ma + 1) * vch + v2l;
-          float s = 0.0f, c = 0.0f;
-          for (int ma = 1; ma <= Ma; ++ma) {
+          float s = 0.0f, c = 0.0f, q = 0.0f;
+          for (int ma = 1; ma < ma_hp; ++ma) {
             const float4 E = Ea4[ma * nv + v1];
             const float4 bb = b[ma * vch];
             dot2_acc(s, c, E.x, E.y, bb.x, bb.y);
             dot2_acc(s, c, -E.z, -E.w, bb.z, bb.w);
           }
-          const ff S = ff_two_sum(s, c);
+          for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
+            const float4 E = Ea4[ma * nv + v1];
+            const float4 bb = b[ma * vch];
+            q = fmaf(E.x, bb.x, fmaf(-E.z, bb.z, q));
+          }
+          const ff S = ff_two_sum(s, c + q);
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b[0].x, b[0].y});
         }
       recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs);
@@ -656,6 +746,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
     const ff al[2] = {ffd(kca0 * (u * p1)), ffd(kca1 * (u * p1))};
     const ff ga[2] = {ffd(kcc0 * u), ffd(kcc1 * u)};
     const float sg = (float)p1;
+    const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
     ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
       const float2 a = __ldg(R->v_ff + v), wv = __ldg(R->vw_ff + v);
@@ -665,7 +756,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
       float s[NDM], c[NDM];
 #pragma unroll
       for (int jn = 0; jn < NDM; ++jn) s[jn] = c[jn] = 0.0f;
-      for (int ma = 1; ma <= Ma; ++ma) {
+      for (int ma = 1; ma < ma_hp; ++ma) {
         const float4 e = __ldg(ph + ma);
 #pragma unroll
         for (int jn = 0; jn < NDM; ++jn)
@@ -673,6 +764,15 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
             const float4 hh = H4[jn * (Ma + 1) + ma];
             dot2_acc(s[jn], c[jn], e.x, e.y, hh.x, hh.y);
             dot2_acc(s[jn], c[jn], -sg * e.z, -sg * e.w, hh.z, hh.w);
+          }
+      }
+      for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
+        const float4 e = __ldg(ph + ma);
+#pragma unroll
+        for (int jn = 0; jn < NDM; ++jn)
+          if (jn < nd) {
+            const float4 hh = H4[jn * (Ma + 1) + ma];
+            c[jn] = fmaf(e.x, hh.x, fmaf(-sg * e.z, hh.z, c[jn]));
           }
       }
       ff Zr[NDM], A[NDM];
