@@ -31,10 +31,11 @@ GRID = 256
 R_CUT = 6.0
 NU = 3.0
 N_BODY = 3
-# DRAM bytes (read + write) of far_kernel_d2 per sum of this workload, from the ncu capture
-# summarised in profiles/far_kernel_d2_config2.md (4 sums: 250.6 KB); traffic scales with the
-# number of sums (per-sum tables).  Set to None whenever that kernel changes until re-captured.
-FAR_DRAM_BYTES_PER_SUM = 250.624e3 / 4
+# DRAM bytes (read + write) of one far_kernel_d2 launch of the default 128-sum step, from the
+# full-size ncu capture summarised in profiles/far_kernel_d2_config2.md.  Set to None whenever
+# that kernel changes until re-captured (other batch sizes report null: the shared phase
+# table makes the traffic not proportional to the number of sums).
+FAR_DRAM_BYTES_PER_LAUNCH = 7972608
 
 
 def parse():
@@ -60,6 +61,22 @@ def workload(rank: int, per_lattice: int = PER_LATTICE):
         for s in W.lattice_constants(per_lattice, W.SEED_BASE + 1 + 100 * rank + li):
             items.append((name, float(s)))
     return items
+
+
+def job_rate(local_ms: float, sums_per_rank: int, steps: int, dist=None, device: str = "cpu"):
+    """Whole-job lattice sums/s: every rank ran sums_per_rank * steps sums (weak scaling, no
+    data exchange between ranks); the job took as long as its slowest rank.  Returns the
+    rate and that time (ms)."""
+    import torch
+
+    ms = float(local_ms)
+    world = 1
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        world = dist.get_world_size()
+    return world * sums_per_rank * steps / (ms / 1e3), ms
 
 
 def quad_for(scale: float):
@@ -399,15 +416,11 @@ def main():
     torch.cuda.synchronize()
     launches = ezeta.ez_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
-    clocks = sampler.stop()
     n_sums = len(items)
-    value = world * n_sums * args.steps / (total_ms / 1e3)
+    value, total_ms = job_rate(sum(step_ms), n_sums, args.steps, dist, "cuda")
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
     res = out.view(n_sums, ezeta.EZ_MAX_PROD)[:, 0].cpu().numpy()
 
     # mixed form (binary32 tails, binary64 heads), same workload and timing rules
@@ -425,13 +438,8 @@ def main():
             batch_m.run(out_m, stream)
             evm[k][1].record(stream)
     torch.cuda.synchronize()
-    mixed_ms = sum(a.elapsed_time(b) for a, b in evm)
-    if dist:
-        t = torch.tensor([mixed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mixed_ms = float(t.item())
+    mixed_value, mixed_ms = job_rate(sum(a.elapsed_time(b) for a, b in evm), n_sums, args.steps, dist, "cuda")
     res_m = out_m.view(n_sums, ezeta.EZ_MAX_PROD)[:, 0].cpu().numpy()
-    mixed_value = world * n_sums * args.steps / (mixed_ms / 1e3)
 
     # end to end through the C ABI with host buffers (planning, upload, kernels, download)
     host_out = np.zeros((n_sums, ezeta.EZ_MAX_PROD))
@@ -441,7 +449,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ezeta.ez_lattice_sums(lats, [spec] * n_sums, quads, out=host_out)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value, _ = job_rate(1e3 * (time.perf_counter() - t0), n_sums, e2e_steps, dist, "cuda")
     assert np.array_equal(host_out[:, 0], res), "batch and one-shot paths disagree"
     _, staging = batch.sizes()
 
@@ -461,12 +469,12 @@ def main():
         "zeta_evals_per_s": {"per_factor": value * nodes_total / n_sums * N_BODY, "distinct_nu": value * nodes_total / n_sums},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "unit": f"per step of {n_sums} sums"},
-        "e2e": {"value": world * n_sums / e2e_s, "unit": "lattice_sums/s", "h2d_bytes_per_step": int(staging),
+        "e2e": {"value": e2e_value, "unit": "lattice_sums/s", "h2d_bytes_per_step": int(staging),
                 "d2h_bytes_per_step": int(n_sums * ezeta.EZ_MAX_PROD * 8)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "far_kernel_d2", "achieved": achieved, "peak": peak_nominal,
                      "unit": "TFLOP/s", "frac": achieved / peak_nominal,
-                     "traffic": None if FAR_DRAM_BYTES_PER_SUM is None else FAR_DRAM_BYTES_PER_SUM * n_sums,
+                     "traffic": FAR_DRAM_BYTES_PER_LAUNCH if args.per_lattice == PER_LATTICE else None,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
                                     f"DFMA probe measured {probe:.3f} TFLOP/s in this run",
                      "far_ms_per_launch": far_mean_ms, "flops_per_launch": flops,

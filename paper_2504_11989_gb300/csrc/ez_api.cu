@@ -354,7 +354,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   p.eps = q.eps > 0.0 ? q.eps : 1e-2;
   if (!(p.eps < 0.5)) return fail(EZ_EINVAL, "eps = %g", p.eps);
   p.ell = q.ell > 0 ? q.ell : 4;
-  if (p.ell > 8) return fail(EZ_EINVAL, "ell = %d > 8", p.ell);
+  if (p.ell > kMaxEll) return fail(EZ_EINVAL, "ell = %d > %d", p.ell, kMaxEll);
   p.prec = q.prec;
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
   // default splitting parameter (the result does not depend on lam): the separable

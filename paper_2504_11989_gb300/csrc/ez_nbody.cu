@@ -631,25 +631,39 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
       ff k[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) k[i] = ff_add(ff_add(ff_mul(al[i], x1), ff_mul(be[i], x2)), ga[i]);
+      // sum_{ma >= 1} Re(Ea B) per exponent: two independent compensated chains (real and
+      // imaginary products) per exponent, interleaved over the exponents
       ff Zr[NDM], A[NDM];
+      float s0[NDM], c0[NDM], s1[NDM], c1[NDM];
+#pragma unroll
+      for (int jn = 0; jn < NDM; ++jn) s0[jn] = c0[jn] = s1[jn] = c1[jn] = 0.0f;
+      const float4* bcol = B4 + v2l;
+      for (int ma = 1; ma < ma_hp; ++ma) {
+        const float4 E = Ea4[ma * nv + v1];
+#pragma unroll
+        for (int jn = 0; jn < NDM; ++jn)
+          if (jn < nd) {
+            const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
+            dot2_acc(s0[jn], c0[jn], E.x, E.y, bb.x, bb.y);
+            dot2_acc(s1[jn], c1[jn], -E.z, -E.w, bb.z, bb.w);
+          }
+      }
+      for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
+        const float4 E = Ea4[ma * nv + v1];
+#pragma unroll
+        for (int jn = 0; jn < NDM; ++jn)
+          if (jn < nd) {
+            const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
+            c0[jn] = fmaf(E.x, bb.x, fmaf(-E.z, bb.z, c0[jn]));
+          }
+      }
 #pragma unroll
       for (int jn = 0; jn < NDM; ++jn)
         if (jn < nd) {
-          const float4* b = B4 + jn * (Ma + 1) * vch + v2l;
-          float s = 0.0f, c = 0.0f, q = 0.0f;
-          for (int ma = 1; ma < ma_hp; ++ma) {
-            const float4 E = Ea4[ma * nv + v1];
-            const float4 bb = b[ma * vch];
-            dot2_acc(s, c, E.x, E.y, bb.x, bb.y);
-            dot2_acc(s, c, -E.z, -E.w, bb.z, bb.w);
-          }
-          for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
-            const float4 E = Ea4[ma * nv + v1];
-            const float4 bb = b[ma * vch];
-            q = fmaf(E.x, bb.x, fmaf(-E.z, bb.z, q));
-          }
-          const ff S = ff_two_sum(s, c + q);
-          Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b[0].x, b[0].y});
+          const ff t = ff_two_sum(s0[jn], s1[jn]);
+          const ff S = ff_fast_two_sum(t.hi, t.lo + (c0[jn] + c1[jn]));
+          const float4 b0 = bcol[jn * (Ma + 1) * vch];
+          Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b0.x, b0.y});
         }
       recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs);
       assemble_mixed<NDM>(R, nd, np, Zr, A, ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y}), ws);
@@ -753,9 +767,9 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
       const ff x{a.x, a.y};
       const ff k[2] = {ff_add(ff_mul(al[0], x), ga[0]), ff_add(ff_mul(al[1], x), ga[1])};
       const float4* ph = R->phaseff + ((size_t)it.iu * nv + v) * R->phase_mp1;
-      float s[NDM], c[NDM];
+      float s[NDM], c[NDM], s1[NDM], c1[NDM];  // real and imaginary product chains
 #pragma unroll
-      for (int jn = 0; jn < NDM; ++jn) s[jn] = c[jn] = 0.0f;
+      for (int jn = 0; jn < NDM; ++jn) s[jn] = c[jn] = s1[jn] = c1[jn] = 0.0f;
       for (int ma = 1; ma < ma_hp; ++ma) {
         const float4 e = __ldg(ph + ma);
 #pragma unroll
@@ -763,7 +777,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
           if (jn < nd) {
             const float4 hh = H4[jn * (Ma + 1) + ma];
             dot2_acc(s[jn], c[jn], e.x, e.y, hh.x, hh.y);
-            dot2_acc(s[jn], c[jn], -sg * e.z, -sg * e.w, hh.z, hh.w);
+            dot2_acc(s1[jn], c1[jn], -sg * e.z, -sg * e.w, hh.z, hh.w);
           }
       }
       for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
@@ -779,7 +793,8 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
 #pragma unroll
       for (int jn = 0; jn < NDM; ++jn)
         if (jn < nd) {
-          const ff S = ff_two_sum(s[jn], c[jn]);
+          const ff t = ff_two_sum(s[jn], s1[jn]);
+          const ff S = ff_fast_two_sum(t.hi, t.lo + (c[jn] + c1[jn]));
           const float4 h0 = H4[jn * (Ma + 1)];
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{h0.x, h0.y});
         }
@@ -911,7 +926,7 @@ __device__ double ipow(double x, int e) {
   return e < 0 ? 1.0 / r : r;
 }
 
-__device__ double near_product(const ReqDesc* R, int p, const double (*C)[9], double wn, double w2, double L) {
+__device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEll + 1], double wn, double w2, double L) {
   const int nd = R->n_distinct, d = R->d, ell = R->ell;
   int e[EZ_MAX_NU], t[EZ_MAX_NU];
   for (int j = 0; j < nd; ++j) {
@@ -1006,18 +1021,21 @@ __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ r
       w2 = fma(s, s, w2);
     }
     for (int i = d; i < 3; ++i) w[i] = 0.0;
-    double C[EZ_MAX_NU][9];
+    // C_k(w) = sum_{|alpha| = 2k} D[alpha] w^alpha: one monomial per alpha (powers of w
+    // tabulated once), shared by every exponent
+    double pw[3][2 * kMaxEll + 1];
+    for (int i = 0; i < 3; ++i) {
+      pw[i][0] = 1.0;
+      for (int q = 1; q <= 2 * ell; ++q) pw[i][q] = pw[i][q - 1] * w[i];
+    }
+    double C[EZ_MAX_NU][kMaxEll + 1];
     for (int jn = 0; jn < nd; ++jn)
-      for (int kk = 0; kk <= ell; ++kk) {
-        double s = 0.0;
-        for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
-          const int* al = R->alpha + 3 * ia;
-          double mono = 1.0;
-          for (int i = 0; i < 3; ++i)
-            for (int q = 0; q < al[i]; ++q) mono *= w[i];
-          s = fma(R->taylor[(size_t)jn * R->n_alpha + ia], mono, s);
-        }
-        C[jn][kk] = s;
+      for (int kk = 0; kk <= ell; ++kk) C[jn][kk] = 0.0;
+    for (int kk = 0; kk <= ell; ++kk)
+      for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
+        const int* al = R->alpha + 3 * ia;
+        const double mono = pw[0][al[0]] * pw[1][al[1]] * pw[2][al[2]];
+        for (int jn = 0; jn < nd; ++jn) C[jn][kk] = fma(R->taylor[(size_t)jn * R->n_alpha + ia], mono, C[jn][kk]);
       }
     const double L = log(kPi * R->eps * R->eps * w2);
     const double wn = sqrt(w2);

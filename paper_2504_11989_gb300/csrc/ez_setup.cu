@@ -298,33 +298,37 @@ __device__ double factd(int n) {
   return r;
 }
 
-// One block of kTaylorThreads per (request, distinct nu, alpha): the threads split the
-// real-space box and the reciprocal list (strided), then a fixed-order block reduction.
+// One block of kTaylorThreads per (request, alpha), every distinct nu of the request at
+// once (grid y runs over the request's Taylor jobs; the blocks of all but its first job
+// return at once).  Real space: z^alpha is even (|alpha| even) and g(-m) = g(m), so the
+// threads sweep the half box after the centre cell and the sum is doubled; each cell's
+// monomial serves every exponent.  Reciprocal space: the k^alpha coefficients of each
+// lattice point serve every exponent.  Fixed-order block reduction.
 constexpr int kTaylorThreads = 128;
 
 __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs,
                                                                 int n_jobs) {
   const int jid = blockIdx.y;
   if (jid >= n_jobs) return;
-  const TaylorJob J = jobs[jid];
-  const ReqDesc* R = reqs + J.req;
+  const TaylorJob J0 = jobs[jid];
+  if (J0.nu_index != 0) return;
+  const ReqDesc* R = reqs + J0.req;
   const int ia = blockIdx.x;
   if (ia >= R->n_alpha) return;
-  const int d = R->d, jn = J.nu_index;
+  const int d = R->d, nd = R->n_distinct;
   const int* al = R->alpha + 3 * ia;
   const int alpha[3] = {al[0], al[1], al[2]};
   const int K2 = alpha[0] + alpha[1] + alpha[2];
   const int K = K2 / 2;
   const double afact = factd(alpha[0]) * factd(alpha[1]) * factd(alpha[2]);
-  const double nu = R->nu[jn];
   const double c = R->c_lam;
-  // real space: sum_m g(m) z^alpha
-  double sreal = 0.0;
+  double sreal[EZ_MAX_NU], srec[EZ_MAX_NU];
+#pragma unroll
+  for (int jn = 0; jn < EZ_MAX_NU; ++jn) sreal[jn] = srec[jn] = 0.0;
+  // real space: 2 sum_{m > 0} g(m) z^alpha over the half box
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
-  const double* g = R->gbox + (size_t)jn * cells;
-  for (long long idx = threadIdx.x; idx < cells; idx += blockDim.x) {
-    const double gv = g[idx];
-    if (gv == 0.0) continue;
+  for (long long idx = cells / 2 + 1 + threadIdx.x; idx < cells; idx += blockDim.x) {
+    if (R->gbox[idx] == 0.0) continue;  // outside the ball (the same for every exponent)
     long long cc = idx;
     int m[3];
     m[2] = (int)(cc % R->box[2]) - R->M[2];
@@ -338,17 +342,16 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
       for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
       for (int e = 0; e < alpha[i]; ++e) mono *= zi;
     }
-    sreal = fma(gv, mono, sreal);
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+      if (jn < nd) sreal[jn] = fma(R->gbox[(size_t)jn * cells + idx], mono, sreal[jn]);
   }
   // reciprocal space, h != 0
-  double srec = 0.0;
-  const double* phis = J.phiG;  // [n_rec][2 ell + 1]
   const int stride = 2 * R->ell + 1;
   for (int hi = threadIdx.x; hi < R->n_rec; hi += blockDim.x) {
     const G4 G = R->rec[hi];
     if (G.w == 0.0 || G.w > R->R2_recip) continue;
     const double Gv[3] = {G.x, G.y, G.z};
-    double term = 0.0;
     for (int n = K; n <= K2; ++n) {
       const int jj = 2 * n - K2;  // number of linear factors
       // coefficient of k^alpha in (2 G.k)^jj (|k|^2)^(n-jj)
@@ -373,40 +376,44 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
       if (coef == 0.0) continue;
       double cn = 1.0;
       for (int e = 0; e < n; ++e) cn *= c;
-      term += ((n & 1) ? -1.0 : 1.0) * phis[(size_t)hi * stride + n] * cn / factd(n) * binom(n, jj) * coef;
+      const double f = ((n & 1) ? -1.0 : 1.0) * cn / factd(n) * binom(n, jj) * coef;
+#pragma unroll
+      for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+        if (jn < nd) srec[jn] = fma(jobs[jid + jn].phiG[(size_t)hi * stride + n], f, srec[jn]);
     }
-    srec += term;
   }
-  // fixed-order block reduction of (sreal, srec)
-  __shared__ double red[2][kTaylorThreads];
-  red[0][threadIdx.x] = sreal;
-  red[1][threadIdx.x] = srec;
+  // fixed-order block reduction of (sreal, srec) per exponent
+  __shared__ double red[2 * EZ_MAX_NU][kTaylorThreads];
+#pragma unroll
+  for (int jn = 0; jn < EZ_MAX_NU; ++jn) {
+    red[2 * jn][threadIdx.x] = sreal[jn];
+    red[2 * jn + 1][threadIdx.x] = srec[jn];
+  }
   __syncthreads();
   for (int w = kTaylorThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + w];
-      red[1][threadIdx.x] += red[1][threadIdx.x + w];
-    }
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 2 * nd; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x >= nd) return;
+  const int jn = threadIdx.x;
+  const TaylorJob J = jobs[jid + jn];
   double twopi_pow = 1.0;
   for (int e = 0; e < K2; ++e) twopi_pow *= 2.0 * kPi;
-  sreal = red[0][0] * ((K & 1) ? -1.0 : 1.0) * twopi_pow / afact;
-  srec = red[1][0];
+  const double sr = 2.0 * red[2 * jn][0] * ((K & 1) ? -1.0 : 1.0) * twopi_pow / afact;
+  double sk = red[2 * jn + 1][0];
   // h = 0: regularised entire series
   const bool all_even = ((alpha[0] | alpha[1] | alpha[2]) & 1) == 0;
   if (all_even && K <= R->ell) {
     double cK = 1.0;
     for (int e = 0; e < K; ++e) cK *= c;
-    srec += J.rser[K] * cK * factd(K) / (factd(alpha[0] / 2) * factd(alpha[1] / 2) * factd(alpha[2] / 2));
+    sk += J.rser[K] * cK * factd(K) / (factd(alpha[0] / 2) * factd(alpha[1] / 2) * factd(alpha[2] / 2));
   }
-  double v = sreal + R->vol_fac * srec;
-  if (K2 == 0) v -= 2.0 / nu;
+  double v = sr + R->vol_fac * sk;
+  if (K2 == 0) v -= 2.0 / R->nu[jn];
   J.out[ia] = R->pref[jn] * v;
 }
 
-// Phi_{a+n}(c |G_h|^2), n = 0..2 ell, for every reciprocal point (setup of the tensors).
 __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs) {
   int jid = blockIdx.y;
   if (jid >= n_jobs) return;

@@ -156,6 +156,45 @@ def test_config3_atm_full_size_sampled_lines(ez, oracle_mod):
     assert _close(got, lines.sum(axis=0), tol=1e-14, floor=np.max(np.abs(got)))
 
 
+def _sampled_lines(ez, oracle_mod, prob, seed, n_pick, tol, prec=None):
+    """Full-size sum on the GPU; a few of its quadrature lines from the oracle (run at the
+    explicit splitting parameter when the GPU sum uses the default one)."""
+    L = ez.Lattice(prob.A)
+    q = ez.quadrature(prob.quad) if prec is None else ez.quadrature(prob.quad, prec=prec)
+    out, lines, offs = ez.ez_lattice_sums([L], [ez.sum_spec(prob.nu, prob.expo)], [q], lines=True)
+    npr = len(prob.expo)
+    got, lines = out[0, :npr], lines[offs[0]: offs[1], :npr]
+    ref_prob = W.explicit_splitting(prob)
+    ns, nu_t = oracle_mod.n_sectors(ref_prob), oracle_mod.n_u_total(ref_prob)
+    rng = np.random.default_rng(seed)
+    picks = [(int(rng.integers(ns)), int(rng.integers(nu_t))) for _ in range(n_pick)]
+    if prob.quad.u_rule == 2:
+        picks.append((int(rng.integers(ns)), -1))
+    with ThreadPoolExecutor(8) as ex:
+        refs = list(ex.map(lambda si: oracle_mod.nbody_line(ref_prob, si[0], si[1]), picks))
+    floor = np.max(np.abs(lines), axis=0)
+    for (s, iu), ref in zip(picks, refs):
+        row = lines[s * nu_t + iu] if iu >= 0 else lines[ns * nu_t + s]
+        assert np.all(np.abs(row - ref) <= tol * np.maximum(np.abs(ref), floor[: len(ref)])), (s, iu, row, ref)
+    # the lines add up to the value (fixed-order compensated reduction; the numpy sum of
+    # lines of both signs is only accurate relative to the sum of their magnitudes)
+    assert np.all(np.abs(got - lines.sum(axis=0)) <= 1e-14 * np.sum(np.abs(lines), axis=0))
+    return got
+
+
+@pytest.mark.parametrize("n", [3, 8])
+def test_config4_full_size_sampled_lines(ez, oracle_mod, n):
+    """fcc, nu = 6, 12 sectors x 32 u x 48^2 v nodes, default splitting parameter."""
+    prob = W.nbody_problem("fcc", 6.0, n, W.Quad(n_u=32, n_v=48, lam=0.0, r_real=0.0, r_recip=0.0))
+    _sampled_lines(ez, oracle_mod, prob, 40 + n, 5, TOL)
+
+
+@pytest.mark.parametrize("lat", ["sc", "bcc"])
+def test_config3_atm_default_lambda_sampled_lines(ez, oracle_mod, lat):
+    prob = W.atm_problem(lat, W.Quad(n_u=8, n_v=64, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0))
+    _sampled_lines(ez, oracle_mod, prob, 7, 4, TOL)
+
+
 AUTO = dict(lam=0.0, r_real=0.0, r_recip=0.0)
 
 
@@ -285,6 +324,15 @@ def test_mixed_config2_full_size_uses_binary32_tails(ez, oracle_mod, lat):
     fp64 = ez.ez_lattice_sum_nbody(L, [3.0] * 3, ez.quadrature(prob.quad))
     assert fp64 != got[0]  # the tail really ran in binary32
     assert abs(fp64 - got[0]) <= MIXED_TOL * abs(fp64)
+
+
+@pytest.mark.parametrize("prob", [
+    W.atm_problem("fcc", W.Quad(n_u=8, n_v=64, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0)),
+    W.nbody_problem("fcc", 6.0, 5, W.Quad(n_u=32, n_v=48, lam=0.0, r_real=0.0, r_recip=0.0)),
+    W.nbody_problem("bcc", 12.0, 2, W.Quad(n_u=8, n_v=32, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0), scale=1.2),
+], ids=["atm-fcc-config3", "fcc-nu6-n5-config4", "bcc-nu12-served"])
+def test_mixed_full_size_sampled_lines(ez, oracle_mod, prob):
+    _sampled_lines(ez, oracle_mod, prob, 11, 4, MIXED_TOL, prec=ez.EZ_MIXED)
 
 
 def test_mixed_batch_matches_single(ez):
