@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-lattice", type=int, default=PER_LATTICE, help="sums per lattice per step (profiling)")
-    ap.add_argument("--workload", default="config2", choices=["config2", "serve", "config1", "config3", "config4"])
+    ap.add_argument("--workload", default="config2",
+                    choices=["config2", "serve", "config1", "config3", "config4", "epstein"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     return ap.parse_args()
 
@@ -355,6 +356,60 @@ def run_config(args):
         print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- Epstein zeta
+def run_epstein(args):
+    """ez_epstein_zeta alone: 2^20 points y uniform in the Brillouin zone per call (device
+    buffers), x = 0 and x uniform in the unit cell, d = 1, 2, 3; evaluations/s, and the
+    largest error of 256 sampled points against the oracle relative to max(1, |Z|)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2504_11989_gb300 import build, ezeta
+    from paper_2504_11989_gb300 import workloads as W
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    oracle.build()
+    m = 1 << 20
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(W.SEED_BASE + 21)
+    cases = [("Z", 4.0), ("hexagonal", 3.0), ("fcc", 6.0), ("sc", 4.0)]
+    for lat_name, nu in cases:
+        A = W.lattice(lat_name)
+        d = A.shape[0]
+        L = ezeta.Lattice(A)
+        Ait = np.linalg.inv(A).T
+        for xkind in ("x=0", "x in cell"):
+            kt = rng.uniform(-0.5, 0.5, size=(m, d))
+            y = kt @ Ait.T  # y = A^{-T} k~
+            x = np.zeros(d) if xkind == "x=0" else A @ rng.uniform(0.0, 1.0, size=d)
+            yd = torch.tensor(y, dtype=torch.float64, device="cuda")
+            re = torch.empty(m, dtype=torch.float64, device="cuda")
+            im = torch.empty(m, dtype=torch.float64, device="cuda")
+            with torch.cuda.stream(stream):
+                for _ in range(max(3, args.warmup)):
+                    ezeta.ez_epstein_zeta(L, nu, x, yd, re, im, stream=stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for k in range(args.steps):
+                    ev[k][0].record(stream)
+                    ezeta.ez_epstein_zeta(L, nu, x, yd, re, im, stream=stream)
+                    ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            idx = rng.choice(m, size=256, replace=False)
+            got = re.cpu().numpy()[idx] + 1j * im.cpu().numpy()[idx]
+            lam = abs(np.linalg.det(A)) ** (1.0 / d)
+            ref = np.array([oracle.epstein_zeta(A, nu, x, y[i], lam, 9.0 * lam, 9.0 / lam) for i in idx])
+            # relative to max(1, |Z|), as the parity tests (Z crosses zero inside the zone)
+            err = float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)))
+            print(json.dumps({"metric": METRIC, "workload": "epstein", "lattice": lat_name, "d": d, "nu": nu,
+                              "x": xkind, "points_per_call": m, "value": m / (ms * 1e-3) / 1e6, "unit": "M evals/s",
+                              "ms_per_call": ms, "dtype": "f64", "max_err_vs_oracle_256_rel_to_max_1_absZ": err}))
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -371,6 +426,10 @@ def main():
     if args.workload in ("config1", "config3", "config4"):
         if rank == 0:
             run_config(args)
+        return
+    if args.workload == "epstein":
+        if rank == 0:
+            run_epstein(args)
         return
     import numpy as np
     import torch

@@ -699,6 +699,7 @@ int init_constants() {
     for (int i = 0; i < kNC; ++i) c[j][i] = (i > 0 ? 2.0 * c[j - 1][i - 1] : 0.0) - c[j - 2][i];
   EZ_CUDA(upload_cheb2mono(&c[0][0]));
   EZ_CUDA(far_set_smem_limits());
+  EZ_CUDA(upload_inv_int());
   g_init = true;
   return EZ_OK;
 }

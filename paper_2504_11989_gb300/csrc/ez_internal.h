@@ -70,6 +70,7 @@ constexpr int kMaxD = 3;
 constexpr int kMaxFactor = 64;
 constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
 constexpr int kMaxEll = 8;       // largest Taylor order parameter ell of the near part
+constexpr int kInvIntHalf = 256; // near part: table of 1/n for |n| <= kInvIntHalf
 constexpr int kVChunkMin = 8;   // d = 3: fewest v2 rows per far-field block
 
 struct ReqDesc {

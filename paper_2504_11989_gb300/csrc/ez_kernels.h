@@ -96,6 +96,7 @@ inline int far_nd_class(int nd) { return nd <= 1 ? 1 : (nd <= 4 ? 4 : 8); }
 cudaError_t launch_far(int d, bool mixed, int ndm, unsigned grid, size_t smem, cudaStream_t st,
                        const ReqDesc* reqs, const Item* items, double* seg);
 cudaError_t far_set_smem_limits();
+cudaError_t upload_inv_int();
 __global__ void near_kernel(const ReqDesc* reqs, const Item* items, double* seg);
 __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
                              const int* line_nseg, int n_lines, const double* seg, double* lines);

@@ -915,6 +915,15 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
 // every product expanded over how many of each factor's singular parts s_hat/V enter,
 // integrated on (0, eps) in closed form (Hadamard finite part):
 //   I_m(mu) = eps^mu J_m,  J_0 = 1/mu,  J_m = L^m/mu - (2m/mu) J_{m-1},  L = log(pi eps^2 |w|^2).
+// 1/n for |n| <= kInvIntHalf (n = 0 unused), filled once by upload_inv_int
+__constant__ double c_inv_int[2 * kInvIntHalf + 1];
+
+cudaError_t upload_inv_int() {
+  double t[2 * kInvIntHalf + 1];
+  for (int n = -kInvIntHalf; n <= kInvIntHalf; ++n) t[n + kInvIntHalf] = n ? 1.0 / n : 0.0;
+  return cudaMemcpyToSymbol(c_inv_int, t, sizeof t);
+}
+
 __device__ double ipow(double x, int e) {
   double r = 1.0, b = x;
   int k = e < 0 ? -e : e;
@@ -966,11 +975,14 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
     double epm = ipow(R->eps, mu);
     double sumk = 0.0;
     for (int k = 0; k <= deg; ++k) {
-      const double muk = (double)(mu + 2 * k);
-      double J = 1.0 / muk, Lp = 1.0;
+      // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
+      // reciprocals of small integers (no division in the loop)
+      const int mk = mu + 2 * k;
+      const double inv = (mk >= -kInvIntHalf && mk <= kInvIntHalf) ? c_inv_int[mk + kInvIntHalf] : 1.0 / (double)mk;
+      double J = inv, Lp = 1.0;
       for (int i = 1; i <= mlog; ++i) {
         Lp *= L;
-        J = Lp / muk - (2.0 * i / muk) * J;
+        J = fma(-2.0 * i, J, Lp) * inv;
       }
       sumk = fma(G[k], epm * J, sumk);
       epm *= eps2;
