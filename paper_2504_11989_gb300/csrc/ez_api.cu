@@ -268,6 +268,7 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   }
   for (int n = 0; n < kNSer; ++n) ff_split(P.ser[n], P.ser_ff[n].x, P.ser_ff[n].y);
   ff_split(P.gam, P.gam_ff.x, P.gam_ff.y);
+  P.a_f = (float)a;
 }
 
 // regularised h = 0 series (lambda piece of the log case included)
@@ -1007,6 +1008,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.work = (unsigned long long*)dptr(B.o_work) + 2 * r;
     R.c_lam_f = (float)R.c_lam;
     ff_split(R.c_lam, R.c_lam_ff.x, R.c_lam_ff.y);
+    R.order_chain = p.spec.n_distinct >= 3;
+    for (int j = 1; j < p.spec.n_distinct; ++j) R.order_chain &= p.spec.nu[j] == p.spec.nu[0] + 2.0 * j;
     R.n_rec = 0;
     R.u_nodes = (const double*)dptr(o_un[r]);
     R.u_w = (const double*)dptr(o_uw[r]);

@@ -61,6 +61,8 @@ struct PhiInfo {
   double ser[kNSer];  // entire part for t < kT0
   float2 ser_ff[kNSer];  // the same as float-float, and Gamma(a) (or (-1)^m/m!), for the mixed form
   float2 gam_ff;
+  float a_f;             // a in binary32 (exact: a is a small half-integer)
+  float pad_f;
 };
 
 // ---------------------------------------------------------------------------
@@ -94,6 +96,8 @@ struct ReqDesc {
   const float4* reclo; // G - (double)recf (binary32): recf + reclo is G as float-float
   float R2f, c_lam_f;
   float2 c_lam_ff;    // c_lam as float-float
+  int order_chain;     // mixed form: nu_j = nu_0 + 2j (>= 3 exponents), so the reciprocal orders
+                       // a_j = a_0 - j are linked by t Phi_{a+1} = a Phi_a + e^{-t}
   PhiInfo phi[EZ_MAX_NU];
   // quadrature
   const double* u_nodes;

@@ -111,12 +111,34 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
   }
 }
 
+// Mixed form, binary32 tail term for every exponent: Phi_a(t) = e^{-t} t^{-1} P_a(t_mix/t).
+// With an order chain (orders a_j = a_0 - j) only the lowest order uses its fit; the others
+// follow upward from t Phi_{a+1} = a Phi_a + e^{-t} (stable for t > t_mix > |a|).
+template <int NDM>
+__device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain, float E, float r, float sv,
+                                        float* st) {
+  float prev = 0.0f;
+#pragma unroll
+  for (int j = NDM - 1; j >= 0; --j)
+    if (j < nd) {
+      const float v = (!chain || j == nd - 1) ? E * r * phi_tail_poly(sphi[j], sv)
+                                              : fmaf(sphi[j + 1].a_f, prev, E) * r;
+      prev = v;
+      st[j] += v;
+    }
+}
+
 // Mixed form, t < kT0 (the h = 0 term near k = 0): Phi_a(t) = sum_n ser_n t^n + singular
 // part, the series in float-float; the singular part gam t^{-a} from float-float 1/t and
 // sqrt(t), or -gam t^m log t with log t taken once in binary64 for every exponent.
 template <int NDM>
-__device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, ff t, ff* hs, unsigned& coefs) {
-  bool need_log = false, need_inv = false, need_sqrt = false;
+__device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, bool chain, ff t, ff* hs,
+                                                unsigned& coefs) {
+  // with an order chain whose lowest order is negative, e^{-t} = t Phi_{a+1} - a Phi_a from
+  // the two lowest orders is a sum of positive terms, and every step up from a >= 0,
+  // Phi_{a+1} = (a Phi_a + e^{-t}) / t, is too: those orders skip the series
+  chain = chain && sphi[nd - 1].a_f < 0.0f;
+  bool need_log = false, need_inv = chain, need_sqrt = false;
 #pragma unroll
   for (int j = 0; j < NDM; ++j)
     if (j < nd) {
@@ -133,10 +155,16 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, ff 
   }
   if (need_inv) inv = ff_rcp(t);
   if (need_sqrt) sq = ff_sqrt(t);
+  ff prev{0.0f, 0.0f}, E{0.0f, 0.0f};
 #pragma unroll
-  for (int j = 0; j < NDM; ++j)
+  for (int j = NDM - 1; j >= 0; --j)
     if (j < nd) {
       const PhiInfo& P = sphi[j];
+      if (chain && j < nd - 2 && sphi[j + 1].a_f >= 0.0f) {
+        prev = ff_mul(ff_add(ff_mul(ff{sphi[j + 1].a_f, 0.0f}, prev), E), inv);
+        hs[j] = ff_add(hs[j], prev);
+        continue;
+      }
       ff p{P.ser_ff[kNSer - 1].x, P.ser_ff[kNSer - 1].y};
 #pragma unroll 1
       for (int n = kNSer - 2; n >= 0; --n) p = ff_add(ff_mul(p, t), ff{P.ser_ff[n].x, P.ser_ff[n].y});
@@ -154,6 +182,11 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, ff 
         for (int q = 0; q < (kk < 0 ? -kk : kk); ++q) r = ff_mul(r, base);
         p = ff_add(p, ff_mul(gam, r));
       }
+      if (chain && j == nd - 2) {  // e^{-t} from the two lowest orders
+        const ff ap = ff_mul(ff{sphi[nd - 1].a_f, 0.0f}, prev);
+        E = ff_add(ff_mul(t, p), ff{-ap.hi, -ap.lo});
+      }
+      prev = p;
       hs[j] = ff_add(hs[j], p);
       coefs += kNSer;
     }
@@ -166,7 +199,7 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, ff 
 //    the float-float table (~46 bits, no binary64 instruction);
 //  * t < kT0 (the h = 0 term near k = 0) or beyond the table: binary64 as in the FP64 form.
 // The list is sorted by |G|: once |G| > sqrt(t_mix / c) + |k|, every remaining term is a
-// binary32 tail, evaluated by a loop without branches (the cutoff is a select).  Tails
+// binary32 tail, evaluated by a short loop that skips the points beyond the cutoff.  Tails
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
@@ -179,6 +212,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   const float* tabff0 = sphi[0].tabff;
   const float4* recf = R->recf;
   const float4* reclo = R->reclo;
+  const bool chain = NDM >= 3 && R->order_chain;
   float kf[3] = {0.0f, 0.0f, 0.0f}, klo[3] = {0.0f, 0.0f, 0.0f}, kn2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -218,10 +252,8 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     if (qqf > R2f) continue;
     const float tf = cf * qqf;
     if (tf >= tmix) {
-      const float r = __frcp_rn(tf), e = __expf(-tf) * r, sv = tmix * r;
-#pragma unroll
-      for (int j = 0; j < NDM; ++j)
-        if (j < nd) st[j] = fmaf(e, phi_tail_poly(sphi[j], sv), st[j]);
+      const float r = __frcp_rn(tf), E = __expf(-tf), sv = tmix * r;
+      tails_f<NDM>(sphi, nd, chain, E, r, sv, st);
       continue;
     }
     if (tf < (float)kT0) {  // near the origin: float-float series and singular part
@@ -232,7 +264,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       const ff t = ff_mul(ff{R->c_lam_ff.x, R->c_lam_ff.y}, qq);
       if (t.hi > 0.0f) {
         ++terms;
-        phi_small_mixed<NDM>(sphi, nd, t, hs, coefs);
+        phi_small_mixed<NDM>(sphi, nd, chain, t, hs, coefs);
         continue;
       }
     }
@@ -271,10 +303,22 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     const ff dq = ff_two_sum(__fsub_rn(qq.hi, hm.x), __fsub_rn(qq.lo, hm.y));  // leading difference exact
     const ff x = ff_mul(dq, ff{hd.z, hd.w});
     if (tf >= tmid) {
+      // descending j = ascending order; with a chain only the two lowest orders use the
+      // table, the others follow from t Phi_{a+1} = a Phi_a + e^{-t}
+      float prev = 0.0f, Ef = 0.0f;
+      const float rt = chain ? __frcp_rn(tf) : 0.0f;
 #pragma unroll
-      for (int j = 0; j < NDM; ++j)
-        if (j < nd) {  // Kahan: sf + cpf carries the middle range
-          const float y = phi_poly_f(sphi[j].tabf + (size_t)iv * kRec, x.hi) - cpf[j];
+      for (int j = NDM - 1; j >= 0; --j)
+        if (j < nd) {
+          float v;
+          if (!chain || j >= nd - 2) {
+            v = phi_poly_f(sphi[j].tabf + (size_t)iv * kRec, x.hi);
+            if (chain && j == nd - 2) Ef = fmaf(tf, v, -sphi[nd - 1].a_f * prev);
+          } else {
+            v = fmaf(sphi[j + 1].a_f, prev, Ef) * rt;
+          }
+          prev = v;
+          const float y = v - cpf[j];  // Kahan: sf + cpf carries the middle range
           const float t = sf[j] + y;
           cpf[j] = (t - sf[j]) - y;
           sf[j] = t;
@@ -282,13 +326,32 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       continue;
     }
     ++terms;
-#pragma unroll
-    for (int j = 0; j < NDM; ++j)
-      if (j < nd) {
-        int n;
-        hs[j] = ff_add(hs[j], phi_poly_ff(sphi[j].tabff + (size_t)iv * kRecFF, x, n));
-        coefs += n;
+    {
+      ff prev{0.0f, 0.0f}, E{0.0f, 0.0f}, rt{0.0f, 0.0f};
+      if (chain) {
+        const ff tff = ff_mul(ff{R->c_lam_ff.x, R->c_lam_ff.y}, qq);
+        rt = ff_rcp(tff);
+        E = tff;  // holds t until the two table orders are known
       }
+#pragma unroll
+      for (int j = NDM - 1; j >= 0; --j)
+        if (j < nd) {
+          ff v;
+          if (!chain || j >= nd - 2) {
+            int n;
+            v = phi_poly_ff(sphi[j].tabff + (size_t)iv * kRecFF, x, n);
+            coefs += n;
+            if (chain && j == nd - 2) {  // e^{-t} = t Phi_{a+1} - a Phi_a with a the lowest order
+              const ff ap = ff_mul(ff{sphi[nd - 1].a_f, 0.0f}, prev);
+              E = ff_add(ff_mul(E, v), ff{-ap.hi, -ap.lo});
+            }
+          } else {
+            v = ff_mul(ff_add(ff_mul(ff{sphi[j + 1].a_f, 0.0f}, prev), E), rt);
+          }
+          prev = v;
+          hs[j] = ff_add(hs[j], v);
+        }
+    }
   }
   // the rest: binary32 tails only, up to the cutoff
 #pragma unroll 2
@@ -306,12 +369,10 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       const float a = Gf.x + kf[0], b = Gf.y + kf[1], c = Gf.z + kf[2];
       qqf = fmaf(a, a, fmaf(b, b, c * c));
     }
+    if (qqf > R2f) continue;  // outside the cutoff (neighbouring nodes mostly agree: little divergence)
     const float tf = cf * qqf;
     const float r = __frcp_rn(tf), sv = tmix * r;
-    const float e = qqf <= R2f ? __expf(-tf) * r : 0.0f;
-#pragma unroll
-    for (int j = 0; j < NDM; ++j)
-      if (j < nd) st[j] = fmaf(e, phi_tail_poly(sphi[j], sv), st[j]);
+    tails_f<NDM>(sphi, nd, chain, __expf(-tf), r, sv, st);
   }
 #pragma unroll
   for (int j = 0; j < NDM; ++j)
