@@ -360,14 +360,14 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
   // default splitting parameter (the result does not depend on lam): the separable
   // real-space contraction costs O(M) per node, the reciprocal sum O(terms).  Measured
-  // optima on GB300: lam = 2 V^{1/d} for d <= 2; in 3-D 4 V^{1/3} for the FP64 form and
-  // 3 V^{1/3} for the mixed form, whose reciprocal tails are cheap binary32 work; capped so
-  // that the real-space box half-width stays <= 16
+  // optima on GB300: lam = 2 V for d = 1, 3 V^{1/2} for d = 2, in 3-D 4 V^{1/3} for the FP64
+  // form and 3.5 V^{1/3} for the mixed form, whose reciprocal tails are cheap binary32 work;
+  // capped so that the real-space box half-width stays <= 16
   const double tcut = p.prec == EZ_MIXED ? kTcutMixed : kTcut;
   if (q.lambda > 0.0) {
     p.lam = q.lambda;
   } else {
-    const double f = d < 3 ? 2.0 : (p.prec == EZ_MIXED ? 3.0 : 4.0);
+    const double f = d == 1 ? 2.0 : d == 2 ? 3.0 : (p.prec == EZ_MIXED ? 3.5 : 4.0);
     double amax = 0.0;
     for (int i = 0; i < d; ++i) {
       double rn = 0.0;
@@ -578,7 +578,8 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
 
   // segments.  d = 3: a far-field block takes vchunk = ceil(n_v / q) rows v2 of a line.
   // The phase and H stages cost the same per block, so q is the smallest split whose
-  // shared memory fits two blocks per SM (~110 KB) and that still gives the sum at least
+  // shared memory fits two blocks per SM (96 KB dynamic + the static reciprocal-list
+  // cache and tables) and that still gives the sum at least
   // four blocks per SM of the GPU (608); failing that, the most blocks with vchunk >= 8.
   p.vchunk = 1;
   if (d == 3) {
@@ -587,7 +588,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     for (int q = 1; q <= p.n_v; ++q) {
       const int c = (p.n_v + q - 1) / q;
       if (c < kVChunkMin && q > 1) break;
-      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 110 * 1024) continue;
+      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 96 * 1024) continue;
       p.vchunk = c;
       if (lines * ((p.n_v + c - 1) / c) >= 608) break;
     }

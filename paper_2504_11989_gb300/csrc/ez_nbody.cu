@@ -9,6 +9,7 @@
 // H and B are built once per block in shared memory; g(-m) = g(m) folds ma < 0.
 // The reciprocal sum runs per node over the compacted list of A^{-T} h.
 #include <cstdio>
+#include <type_traits>
 
 #include "ez_ff.cuh"
 #include "ez_kernels.h"
@@ -61,13 +62,33 @@ __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd
   for (int i = threadIdx.x; i < nd * words; i += blockDim.x) dst[i] = src[i];
 }
 
+// Mixed form: the first kRecCache points of the |G|-sorted reciprocal list, staged in
+// shared memory once per block: every node of the block walks the list in the same order,
+// so each load is a broadcast from shared memory.
+constexpr int kRecCache = 256;
+struct RecCacheF64 {};  // the FP64 form reads the list through the read-only cache (measured faster)
+struct RecCacheMix {
+  float4 f[kRecCache];   // binary32 hi parts and |G|^2
+  float4 lo[kRecCache];  // low parts of the float-float G
+};
+
+__device__ __forceinline__ void load_rec_cache(RecCacheF64&, const ReqDesc*) {}
+__device__ __forceinline__ void load_rec_cache(RecCacheMix& c, const ReqDesc* R) {
+  const int n = min(R->n_rec, kRecCache);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    c.f[i] = __ldg(R->recf + i);
+    c.lo[i] = __ldg(R->reclo + i);
+  }
+}
+
 // reciprocal sum at k (x = 0), FP64 form: acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over
 // |G + k| <= R, every value binary64.  The cutoff test, the branch and the table interval
 // are taken in binary32 (a term within ~1e-7 relative of the cutoff radius may fall either
 // way: it is below the truncation tolerance by the choice of the radius).
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
-                                          const float* kf, double* acc, unsigned& terms, unsigned& coefs) {
+                                          const float* kf, double* acc, unsigned& terms, unsigned& coefs,
+                                          const RecCacheF64&) {
   const int nrec = R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const G4* rec = R->rec;
@@ -203,7 +224,7 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, boo
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
-                                                ff* A, unsigned& terms, unsigned& coefs) {
+                                                ff* A, unsigned& terms, unsigned& coefs, const RecCacheMix& rc) {
   const int nrec = R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
@@ -236,7 +257,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   }
   int h = 0;
   for (; h < nrec; ++h) {
-    const float4 Gf = __ldg(recf + h);
+    const float4 Gf = h < kRecCache ? rc.f[h] : __ldg(recf + h);
     if (Gf.w > gb2) break;
     float qqf;
     if (D == 1) {
@@ -257,7 +278,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       continue;
     }
     if (tf < (float)kT0) {  // near the origin: float-float series and singular part
-      const float4 Gl = __ldg(reclo + h);
+      const float4 Gl = h < kRecCache ? rc.lo[h] : __ldg(reclo + h);
       ff qq = ff_sqr(ff_add4(Gf.x, Gl.x, kf[0], klo[0]));
       if (D >= 2) qq = ff_add(qq, ff_sqr(ff_add4(Gf.y, Gl.y, kf[1], klo[1])));
       if (D >= 3) qq = ff_add(qq, ff_sqr(ff_add4(Gf.z, Gl.z, kf[2], klo[2])));
@@ -293,7 +314,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       continue;
     }
     // float-float |G + k|^2 and x = s (|q|^2 - m) (s, m shared by every exponent)
-    const float4 Gl = __ldg(reclo + h);
+    const float4 Gl = h < kRecCache ? rc.lo[h] : __ldg(reclo + h);
     ff qq = ff_sqr(ff_add4(Gf.x, Gl.x, kf[0], klo[0]));
     if (D >= 2) qq = ff_add(qq, ff_sqr(ff_add4(Gf.y, Gl.y, kf[1], klo[1])));
     if (D >= 3) qq = ff_add(qq, ff_sqr(ff_add4(Gf.z, Gl.z, kf[2], klo[2])));
@@ -356,7 +377,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   // the rest: binary32 tails only, up to the cutoff
 #pragma unroll 2
   for (; h < nrec; ++h) {
-    const float4 Gf = __ldg(recf + h);
+    const float4 Gf = h < kRecCache ? rc.f[h] : __ldg(recf + h);
     if (Gf.w > gc2) break;
     float qqf;
     if (D == 1) {
@@ -478,6 +499,8 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v, vch = R->vchunk;
   load_phi(sphi, R, nd);
+  __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
+  load_rec_cache(rcache, R);
 
   const int j = it.sector >> 2, pb = it.sector & 3;
   const double p1 = (pb & 1) ? -1.0 : 1.0, p2 = (pb & 2) ? -1.0 : 1.0;
@@ -726,7 +749,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
           const float4 b0 = bcol[jn * (Ma + 1) * vch];
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b0.x, b0.y});
         }
-      recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs);
+      recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
       assemble_mixed<NDM>(R, nd, np, Zr, A, ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y}), ws);
     }
 #pragma unroll
@@ -756,7 +779,7 @@ __global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__
         }
       }
       const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-      recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+      recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
 #pragma unroll
       for (int jn = 0; jn < NDM; ++jn)
         if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -777,6 +800,8 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v;
   load_phi(sphi, R, nd);
+  __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
+  load_rec_cache(rcache, R);
   const int j = it.sector >> 1;
   const double p1 = (it.sector & 1) ? -1.0 : 1.0;
   const int ax_a = j, ax_c = 1 - j;
@@ -859,7 +884,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
           const float4 h0 = H4[jn * (Ma + 1)];
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{h0.x, h0.y});
         }
-      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs);
+      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
       assemble_mixed<NDM>(R, nd, np, Zr, A, ff{wv.x, wv.y}, ws);
     }
 #pragma unroll
@@ -889,7 +914,7 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
 #pragma unroll
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -908,6 +933,8 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   const ReqDesc* R = reqs + it.req;
   const int nd = R->n_distinct, np = R->n_prod;
   load_phi(sphi, R, nd);
+  __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
+  load_rec_cache(rcache, R);
   __syncthreads();
   const int iu = it.iu + threadIdx.x;
   if (iu >= R->n_ui) return;
@@ -938,7 +965,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
         const ff S = ff_two_sum(s[jn], c[jn]);
         Zr[jn] = ff{2.0f * S.hi, 2.0f * S.lo};
       }
-    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs);
+    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
     ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     assemble_mixed<NDM>(R, nd, np, Zr, A, ffd(w), ws);
 #pragma unroll
@@ -956,7 +983,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
   const float kf[1] = {(float)k[0]};
-  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs);
+  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
 #pragma unroll
   for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
