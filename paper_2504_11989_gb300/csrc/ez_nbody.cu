@@ -1023,7 +1023,9 @@ __device__ double ipow(double x, int e) {
   return e < 0 ? 1.0 / r : r;
 }
 
-__device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEll + 1], double wn, double w2, double L) {
+// sig_w[j] = sigma_j |w|^{nu_j - d} / V (per ray, shared by every product and subset)
+__device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEll + 1], const double* sig_w,
+                               double L) {
   const int nd = R->n_distinct, d = R->d, ell = R->ell;
   int e[EZ_MAX_NU], t[EZ_MAX_NU];
   for (int j = 0; j < nd; ++j) {
@@ -1032,18 +1034,18 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
   }
   double total = 0.0;
   double G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
-  const double eps2 = R->eps * R->eps;
+  const double eps2 = R->eps * R->eps, inv_eps = 1.0 / R->eps;
   while (true) {
-    double mult = 1.0, coef = 1.0;
+    double coef = 1.0;
+    long long mult = 1;  // product of binomials (exact integers)
     int mu = d, mlog = 0;
     for (int j = 0; j < nd; ++j) {
       if (t[j]) {
-        double bj = 1.0;
+        long long bj = 1;
         for (int i = 1; i <= t[j]; ++i) bj = bj * (e[j] - t[j] + i) / i;
         mult *= bj;
-        const int dn = (int)lrint(R->nu[j]) - d;
-        coef *= ipow(R->sig[j] * ipow(wn, dn) / R->V, t[j]);
-        mu += t[j] * dn;
+        for (int i = 0; i < t[j]; ++i) coef *= sig_w[j];
+        mu += t[j] * ((int)lrint(R->nu[j]) - d);
         mlog += t[j] * R->islog[j];
       }
     }
@@ -1060,7 +1062,7 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
         deg = nd2;
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
-    double epm = ipow(R->eps, mu);
+    double epm = mu >= 0 ? ipow(R->eps, mu) : ipow(inv_eps, -mu);
     double sumk = 0.0;
     for (int k = 0; k <= deg; ++k) {
       // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
@@ -1075,7 +1077,7 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
       sumk = fma(G[k], epm * J, sumk);
       epm *= eps2;
     }
-    total = fma(mult * coef, sumk, total);
+    total = fma((double)mult * coef, sumk, total);
     int j = 0;
     for (; j < nd; ++j) {
       if (t[j] < e[j]) {
@@ -1138,8 +1140,13 @@ __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ r
         for (int jn = 0; jn < nd; ++jn) C[jn][kk] = fma(R->taylor[(size_t)jn * R->n_alpha + ia], mono, C[jn][kk]);
       }
     const double L = log(kPi * R->eps * R->eps * w2);
-    const double wn = sqrt(w2);
-    for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * near_product(R, p, C, wn, w2, L);
+    const double wn = sqrt(w2), inv_wn = 1.0 / wn, inv_V = 1.0 / R->V;
+    double sig_w[EZ_MAX_NU];
+    for (int jn = 0; jn < nd; ++jn) {
+      const int dn = (int)lrint(R->nu[jn]) - d;
+      sig_w[jn] = R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V;
+    }
+    for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * near_product(R, p, C, sig_w, L);
   }
   block_reduce_store<128>(val, np, 1.0, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
