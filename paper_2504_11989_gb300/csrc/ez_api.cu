@@ -745,6 +745,9 @@ struct ez_batch_s {
 
 namespace {
 
+// chunks of kTaylorCells cells in the half real-space box after the centre cell
+long long taylor_chunks(const Plan& p) { return (p.cells / 2 + kTaylorCells - 1) / kTaylorCells; }
+
 int batch_plan(ez_batch_s& B, int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
                const ez_quadrature* quads) {
   if (n_req < 1) return fail(EZ_EINVAL, "n_req = %d", n_req);
@@ -883,7 +886,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req), o_gboxff(n_req);
+      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -923,6 +926,9 @@ int batch_layout(ez_batch_s& B, bool fill) {
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
+    o_tpart[r] = p.near ? dl.take(sizeof(double) * std::max<long long>(taylor_chunks(p), 1) * std::max<size_t>(na, 1) *
+                                  p.spec.n_distinct)
+                        : 0;
   }
   std::vector<size_t> o_phase(B.n_phase), o_phaseff(B.n_phase, 0);
   std::vector<char> phase_mixed(B.n_phase, 0);
@@ -1074,6 +1080,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
         T.phiG = (double*)dptr(o_phig[r]) + (size_t)j * p.rcap * (2 * p.ell + 1);
         std::memcpy(T.rser, p.rser[j], sizeof T.rser);
         T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
+        T.part = (double*)dptr(o_tpart[r]);
+        T.n_chunk = (int)taylor_chunks(p);
       }
   }
   for (int g = 0; g < n_phi; ++g) {
@@ -1208,8 +1216,17 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
     phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
     int max_alpha = 0;
+    long long max_chunk = 0;
     for (auto& p : B.plans)
-      if (p.near) max_alpha = std::max(max_alpha, (int)(p.alpha.size() / 3));
+      if (p.near) {
+        max_alpha = std::max(max_alpha, (int)(p.alpha.size() / 3));
+        max_chunk = std::max(max_chunk, taylor_chunks(p));
+      }
+    if (max_chunk > 0) {
+      taylor_real_kernel<<<dim3((unsigned)max_chunk, B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj),
+                                                                                  B.n_tay);
+      EZ_LAUNCHED();
+    }
     taylor_kernel<<<dim3(max_alpha, B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
     EZ_LAUNCHED();
   }

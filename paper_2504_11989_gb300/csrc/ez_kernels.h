@@ -55,7 +55,10 @@ struct TaylorJob {
   double* phiG;   // [n_rec_cap][2 ell + 1]
   double rser[16];  // entire series of the regularised h = 0 term (lambda piece included)
   double* out;    // [n_alpha]
+  double* part;   // first job of a request: real-space partial moments [n_chunk][n_alpha][n_distinct]
+  int n_chunk;    // chunks of kTaylorCells cells of the half box
 };
+constexpr int kTaylorCells = 64;
 
 struct PhaseJob {
   int n_ui, n_v, mp1;
@@ -89,6 +92,7 @@ __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs
 __global__ void phitab_kernel(const PhiJob* jobs);
 __global__ void phicopy_kernel(const PhiCopyJob* jobs);
 __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
+__global__ void taylor_real_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 
 // far-field kernels (d = 1, 2, 3): binary64 or mixed form, at most ndm distinct exponents

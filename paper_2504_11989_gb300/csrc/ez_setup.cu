@@ -298,14 +298,81 @@ __device__ double factd(int n) {
   return r;
 }
 
-// One block of kTaylorThreads per (request, alpha), every distinct nu of the request at
-// once (grid y runs over the request's Taylor jobs; the blocks of all but its first job
-// return at once).  Real space: z^alpha is even (|alpha| even) and g(-m) = g(m), so the
-// threads sweep the half box after the centre cell and the sum is doubled; each cell's
-// monomial serves every exponent.  Reciprocal space: the k^alpha coefficients of each
-// lattice point serve every exponent.  Fixed-order block reduction.
 constexpr int kTaylorThreads = 128;
 
+// Real-space moments of the Taylor tensors, per chunk of kTaylorCells cells of the half
+// box after the centre cell (g(-m) = g(m) and the monomials are even): the block tabulates
+// the powers z_i^e of its cells and their g values in shared memory, then thread alpha
+// sums g(m) z^alpha over the chunk in cell order for every exponent.  One block per
+// (chunk, request); the partial moments are added over the chunks in chunk order by
+// taylor_kernel.
+__global__ void __launch_bounds__(kTaylorThreads) taylor_real_kernel(const ReqDesc* reqs, const TaylorJob* jobs,
+                                                                     int n_jobs) {
+  const int jid = blockIdx.y;
+  if (jid >= n_jobs) return;
+  const TaylorJob J = jobs[jid];
+  if (J.nu_index != 0 || (int)blockIdx.x >= J.n_chunk) return;
+  const ReqDesc* R = reqs + J.req;
+  const int d = R->d, nd = R->n_distinct, ne = 2 * R->ell + 1;
+  __shared__ double pw[3][2 * kMaxEll + 1][kTaylorCells];
+  __shared__ double gv[EZ_MAX_NU][kTaylorCells];
+  const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
+  const long long c0 = cells / 2 + 1 + (long long)blockIdx.x * kTaylorCells;
+  const int nc = (int)min((long long)kTaylorCells, cells - c0);
+  const int c = threadIdx.x;
+  if (c < kTaylorCells) {
+    double z[3] = {0.0, 0.0, 0.0};
+    bool live = false;
+    if (c < nc) {
+      const long long idx = c0 + c;
+      live = R->gbox[idx] != 0.0;  // outside the ball (the same for every exponent)
+      long long cc = idx;
+      int m[3];
+      m[2] = (int)(cc % R->box[2]) - R->M[2];
+      cc /= R->box[2];
+      m[1] = (int)(cc % R->box[1]) - R->M[1];
+      cc /= R->box[1];
+      m[0] = (int)cc - R->M[0];
+      for (int i = 0; i < d; ++i) {
+        double zi = 0.0;
+        for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
+        z[i] = zi;
+      }
+      for (int jn = 0; jn < nd; ++jn) gv[jn][c] = live ? R->gbox[(size_t)jn * cells + idx] : 0.0;
+    } else {
+      for (int jn = 0; jn < nd; ++jn) gv[jn][c] = 0.0;
+    }
+    for (int i = 0; i < 3; ++i) {
+      double p = 1.0;
+      for (int e = 0; e < ne; ++e) {
+        pw[i][e][c] = p;
+        p *= z[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int ia = threadIdx.x; ia < R->n_alpha; ia += blockDim.x) {
+    const int* al = R->alpha + 3 * ia;
+    const int a0 = al[0], a1 = al[1], a2 = al[2];
+    double acc[EZ_MAX_NU];
+#pragma unroll
+    for (int jn = 0; jn < EZ_MAX_NU; ++jn) acc[jn] = 0.0;
+    for (int q = 0; q < nc; ++q) {
+      const double mono = pw[0][a0][q] * pw[1][a1][q] * pw[2][a2][q];
+#pragma unroll
+      for (int jn = 0; jn < EZ_MAX_NU; ++jn)
+        if (jn < nd) acc[jn] = fma(gv[jn][q], mono, acc[jn]);
+    }
+    double* o = J.part + ((size_t)blockIdx.x * R->n_alpha + ia) * nd;
+    for (int jn = 0; jn < nd; ++jn) o[jn] = acc[jn];
+  }
+}
+
+// One block of kTaylorThreads per (request, alpha), every distinct nu of the request at
+// once (grid y runs over the request's Taylor jobs; the blocks of all but its first job
+// return at once).  Real space: the half-box moments of taylor_real_kernel, doubled.
+// Reciprocal space: the k^alpha coefficients of each lattice point serve every exponent.
+// Fixed-order block reduction.
 __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs,
                                                                 int n_jobs) {
   const int jid = blockIdx.y;
@@ -325,26 +392,12 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
   double sreal[EZ_MAX_NU], srec[EZ_MAX_NU];
 #pragma unroll
   for (int jn = 0; jn < EZ_MAX_NU; ++jn) sreal[jn] = srec[jn] = 0.0;
-  // real space: 2 sum_{m > 0} g(m) z^alpha over the half box
-  const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
-  for (long long idx = cells / 2 + 1 + threadIdx.x; idx < cells; idx += blockDim.x) {
-    if (R->gbox[idx] == 0.0) continue;  // outside the ball (the same for every exponent)
-    long long cc = idx;
-    int m[3];
-    m[2] = (int)(cc % R->box[2]) - R->M[2];
-    cc /= R->box[2];
-    m[1] = (int)(cc % R->box[1]) - R->M[1];
-    cc /= R->box[1];
-    m[0] = (int)cc - R->M[0];
-    double mono = 1.0;
-    for (int i = 0; i < d; ++i) {
-      double zi = 0.0;
-      for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
-      for (int e = 0; e < alpha[i]; ++e) mono *= zi;
-    }
+  // real space: 2 sum_{m > 0} g(m) z^alpha, the chunk moments of taylor_real_kernel
+  for (int ch = threadIdx.x; ch < J0.n_chunk; ch += blockDim.x) {
+    const double* pp = J0.part + ((size_t)ch * R->n_alpha + ia) * nd;
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn)
-      if (jn < nd) sreal[jn] = fma(R->gbox[(size_t)jn * cells + idx], mono, sreal[jn]);
+      if (jn < nd) sreal[jn] += pp[jn];
   }
   // reciprocal space, h != 0
   const int stride = 2 * R->ell + 1;
