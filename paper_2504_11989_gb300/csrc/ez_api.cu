@@ -217,7 +217,9 @@ struct Plan {
   long long rcap;
   double R2enum;
   std::vector<double> un, uw, vn, vw;
-  PhiInfo phi[EZ_MAX_NU];
+  PhiInfo phi[EZ_MAX_NU];       // reciprocal orders (d - nu)/2, argument pi lam^2 |q|^2
+  PhiInfo phi_real[EZ_MAX_NU];  // real-space orders nu/2 for the box g, argument t itself
+  bool real_tab;                // the box is large enough for tables to pay (else continued fractions)
   double rser[EZ_MAX_NU][16];
   bool near;
   std::vector<int> alpha, alpha_off;
@@ -434,6 +436,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
       }
     }
   }
+  p.real_tab = p.cells * spec.n_distinct >= 4096;
   // reciprocal enumeration: |A^{-T} h| <= r_recip + max_BZ |k|
   double kmax = 0.0;
   for (int c = 0; c < (1 << d); ++c) {
@@ -494,6 +497,8 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   const double c_lam = kPi * p.lam * p.lam;
   for (int j = 0; j < spec.n_distinct; ++j) {
     fill_phi_host(p.phi[j], 0.5 * (d - spec.nu[j]), c_lam * p.r_recip * p.r_recip);
+    fill_phi_host(p.phi_real[j], 0.5 * spec.nu[j], kPi * p.r_real * p.r_real / (p.lam * p.lam));
+    p.phi_real[j].c_lam = 1.0;
     fill_rser(p.rser[j], 0.5 * (d - spec.nu[j]), p.lam, 15);
   }
 
@@ -745,6 +750,11 @@ struct ez_batch_s {
 
 namespace {
 
+// Phi table slot of a plan: reciprocal order j (slot j) or real-space order j (EZ_MAX_NU + j)
+const PhiInfo& phi_slot(const Plan& p, int slot) {
+  return slot < EZ_MAX_NU ? p.phi[slot] : p.phi_real[slot - EZ_MAX_NU];
+}
+
 // chunks of kTaylorCells cells in the half real-space box after the centre cell
 long long taylor_chunks(const Plan& p) { return (p.cells / 2 + kTaylorCells - 1) / kTaylorCells; }
 
@@ -809,26 +819,29 @@ int batch_layout(ez_batch_s& B, bool fill) {
     if (plans[r].near) n_tay += plans[r].spec.n_distinct;
   // Phi tables depend on a alone (up to the argument scale of each record): one table per
   // distinct a, computed for the member with the most intervals, copied to the others
+  // (slot j < EZ_MAX_NU: reciprocal order j; slot EZ_MAX_NU + j: real-space order j)
   {
     std::vector<std::vector<std::pair<int, int>>> groups;
     for (int r = 0; r < n_req; ++r)
-      for (int j = 0; j < plans[r].spec.n_distinct; ++j) {
-        const PhiInfo& P = plans[r].phi[j];
-        int g = 0;
-        for (; g < (int)groups.size(); ++g) {
-          const PhiInfo& Q = plans[groups[g][0].first].phi[groups[g][0].second];
-          if (Q.a == P.a && Q.t_geo_end == P.t_geo_end) break;
+      for (int k = 0; k < (plans[r].real_tab ? 2 : 1); ++k)
+        for (int j = 0; j < plans[r].spec.n_distinct; ++j) {
+          const int slot = k * EZ_MAX_NU + j;
+          const PhiInfo& P = phi_slot(plans[r], slot);
+          int g = 0;
+          for (; g < (int)groups.size(); ++g) {
+            const PhiInfo& Q = phi_slot(plans[groups[g][0].first], groups[g][0].second);
+            if (Q.a == P.a && Q.t_geo_end == P.t_geo_end) break;
+          }
+          if (g == (int)groups.size()) groups.emplace_back();
+          groups[g].push_back({r, slot});
         }
-        if (g == (int)groups.size()) groups.emplace_back();
-        groups[g].push_back({r, j});
-      }
     B.phi_master.clear();
     B.phi_copy.clear();
     for (int g = 0; g < (int)groups.size(); ++g) {
       size_t m = 0;
       for (size_t i = 1; i < groups[g].size(); ++i)
-        if (plans[groups[g][i].first].phi[groups[g][i].second].n_int >
-            plans[groups[g][m].first].phi[groups[g][m].second].n_int)
+        if (phi_slot(plans[groups[g][i].first], groups[g][i].second).n_int >
+            phi_slot(plans[groups[g][m].first], groups[g][m].second).n_int)
           m = i;
       B.phi_master.push_back(groups[g][m]);
       for (size_t i = 0; i < groups[g].size(); ++i)
@@ -920,9 +933,16 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_rectmp[r] = dl.take(sizeof(G4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     o_gboxff[r] = p.prec == EZ_MIXED ? dl.take(sizeof(float2) * p.cells * p.spec.n_distinct) : 0;
-    for (int j = 0; j < p.spec.n_distinct; ++j) o_tab[r].push_back(dl.take(sizeof(double) * kRec * p.phi[j].n_int));
-    for (int j = 0; j < p.spec.n_distinct; ++j) o_tabf[r].push_back(dl.take(sizeof(float) * kRec * p.phi[j].n_int));
-    for (int j = 0; j < p.spec.n_distinct; ++j) o_tabff[r].push_back(dl.take(sizeof(float) * kRecFF * p.phi[j].n_int));
+    o_tab[r].assign(2 * EZ_MAX_NU, 0);
+    o_tabf[r].assign(2 * EZ_MAX_NU, 0);
+    o_tabff[r].assign(2 * EZ_MAX_NU, 0);
+    for (int k = 0; k < (p.real_tab ? 2 : 1); ++k)
+      for (int j = 0; j < p.spec.n_distinct; ++j) {
+        const int slot = k * EZ_MAX_NU + j, ni = phi_slot(p, slot).n_int;
+        o_tab[r][slot] = dl.take(sizeof(double) * kRec * ni);
+        o_tabf[r][slot] = dl.take(sizeof(float) * kRec * ni);
+        o_tabff[r][slot] = dl.take(sizeof(float) * kRecFF * ni);
+      }
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
@@ -1070,6 +1090,13 @@ int batch_layout(ez_batch_s& B, bool fill) {
     GJ.x_in_lattice = 1;
     GJ.R2 = p.r_real * p.r_real;
     GJ.out = (double*)dptr(o_gbox[r]);
+    GJ.use_tab = p.real_tab ? 1 : 0;
+    for (int j = 0; p.real_tab && j < p.spec.n_distinct; ++j) {
+      GJ.phi[j] = p.phi_real[j];
+      GJ.phi[j].tab = (const double*)dptr(o_tab[r][EZ_MAX_NU + j]);
+      GJ.phi[j].tabf = nullptr;
+      GJ.phi[j].tabff = nullptr;
+    }
     GJ.outff = o_gboxff[r] ? (float2*)dptr(o_gboxff[r]) : nullptr;
     R.gboxff = o_gboxff[r] ? (const float2*)dptr(o_gboxff[r]) : nullptr;
     if (p.near)
@@ -1087,10 +1114,11 @@ int batch_layout(ez_batch_s& B, bool fill) {
   for (int g = 0; g < n_phi; ++g) {
     const int r = B.phi_master[g].first, j = B.phi_master[g].second;
     PhiJob& J = pjobs[g];
-    J.a = plans[r].phi[j].a;
-    J.c_lam = reqs[r].c_lam;
-    J.t_geo_end = plans[r].phi[j].t_geo_end;
-    J.n_int = plans[r].phi[j].n_int;
+    const PhiInfo& P = phi_slot(plans[r], j);
+    J.a = P.a;
+    J.c_lam = j < EZ_MAX_NU ? reqs[r].c_lam : 1.0;
+    J.t_geo_end = P.t_geo_end;
+    J.n_int = P.n_int;
     J.out = (double*)dptr(o_tab[r][j]);
     J.outf = (float*)dptr(o_tabf[r][j]);
     J.outff = (float*)dptr(o_tabff[r][j]);
@@ -1106,9 +1134,9 @@ int batch_layout(ez_batch_s& B, bool fill) {
       cj[c].out = (double*)dptr(o_tab[r][j]);
       cj[c].outf = (float*)dptr(o_tabf[r][j]);
       cj[c].outff = (float*)dptr(o_tabff[r][j]);
-      cj[c].c_lam = reqs[r].c_lam;
-      cj[c].t_geo_end = plans[r].phi[j].t_geo_end;
-      cj[c].n_int = plans[r].phi[j].n_int;
+      cj[c].c_lam = j < EZ_MAX_NU ? reqs[r].c_lam : 1.0;
+      cj[c].t_geo_end = phi_slot(plans[r], j).t_geo_end;
+      cj[c].n_int = phi_slot(plans[r], j).n_int;
     }
   }
   {
@@ -1195,13 +1223,9 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
         dreqs, (const RecipJob*)dptr(B.o_rj));
     EZ_LAUNCHED();
   }
-  long long max_cells = 0;
-  for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
-  gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
-  EZ_LAUNCHED();
   int max_int = 0, max_int_copy = 0;
-  for (auto& m : B.phi_master) max_int = std::max(max_int, B.plans[m.first].phi[m.second].n_int);
-  for (auto& c : B.phi_copy) max_int_copy = std::max(max_int_copy, B.plans[c[0]].phi[c[1]].n_int);
+  for (auto& m : B.phi_master) max_int = std::max(max_int, phi_slot(B.plans[m.first], m.second).n_int);
+  for (auto& c : B.phi_copy) max_int_copy = std::max(max_int_copy, phi_slot(B.plans[c[0]], c[1]).n_int);
   phitab_kernel<<<dim3(max_int, B.n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
   EZ_LAUNCHED();
   if (B.n_pcopy) {
@@ -1209,6 +1233,11 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
         (const PhiCopyJob*)dptr(B.o_pcj));
     EZ_LAUNCHED();
   }
+  // the real-space box reads the real-order Phi tables: after phitab/phicopy
+  long long max_cells = 0;
+  for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
+  gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
+  EZ_LAUNCHED();
   if (B.n_tay) {
     long long max_rec = 0;
     for (auto& p : B.plans)

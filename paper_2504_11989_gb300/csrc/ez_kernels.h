@@ -24,6 +24,8 @@ struct GboxJob {
   double R2;
   double* out;
   float2* outff;  // float-float copy (may be null)
+  int use_tab;    // 1: g from the tables of the real-space orders in phi (c_lam = 1, argument t)
+  PhiInfo phi[EZ_MAX_NU];
 };
 
 struct PhiJob {

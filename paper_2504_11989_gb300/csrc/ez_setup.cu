@@ -112,7 +112,7 @@ __global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs) {
 __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs) {
   int jid = blockIdx.y;
   if (jid >= n_jobs) return;
-  const GboxJob J = jobs[jid];
+  const GboxJob& J = jobs[jid];
   const ReqDesc* R = reqs + J.req;
   const int d = R->d;
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
@@ -136,7 +136,10 @@ __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs
   }
   double g = 0.0;
   bool excluded = J.x_in_lattice ? center : false;
-  if (!excluded && r2 <= J.R2 && r2 > 0.0) g = phi_accurate(0.5 * R->nu[jn], kPi * r2 / (R->lam * R->lam));
+  if (!excluded && r2 <= J.R2 && r2 > 0.0) {
+    const double t = kPi * r2 / (R->lam * R->lam);
+    g = J.use_tab ? phi_eval(J.phi[jn], t) : phi_accurate(0.5 * R->nu[jn], t);
+  }
   J.out[idx] = g;
   if (J.outff) {
     float hi, lo;
