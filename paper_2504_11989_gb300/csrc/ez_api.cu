@@ -899,7 +899,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req);
+      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_tayff(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -945,6 +945,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       }
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
+    o_tayff[r] = dl.take(sizeof(float2) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
     o_tpart[r] = p.near ? dl.take(sizeof(double) * std::max<long long>(taylor_chunks(p), 1) * std::max<size_t>(na, 1) *
                                   p.spec.n_distinct)
@@ -1068,6 +1069,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.alpha = (const int*)dptr(o_al[r]);
     R.alpha_off = (const int*)dptr(o_alo[r]);
     R.taylor = (const double*)dptr(o_tay[r]);
+    R.taylor_ff = (const float2*)dptr(o_tayff[r]);
     if (!p.alpha.empty()) {
       std::memcpy(Hs + h_al[r], p.alpha.data(), sizeof(int) * p.alpha.size());
       std::memcpy(Hs + h_alo[r], p.alpha_off.data(), sizeof(int) * p.alpha_off.size());
@@ -1107,6 +1109,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
         T.phiG = (double*)dptr(o_phig[r]) + (size_t)j * p.rcap * (2 * p.ell + 1);
         std::memcpy(T.rser, p.rser[j], sizeof T.rser);
         T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
+        T.outff = (float2*)dptr(o_tayff[r]) + (size_t)j * R.n_alpha;
         T.part = (double*)dptr(o_tpart[r]);
         T.n_chunk = (int)taylor_chunks(p);
       }

@@ -118,6 +118,7 @@ struct ReqDesc {
   const int* alpha;       // [n_alpha][3]
   const int* alpha_off;   // start of |alpha| = 2k blocks, k = 0..ell+1
   const double* taylor;   // [n_distinct][n_alpha] : d^alpha Z^reg(0) / alpha!
+  const float2* taylor_ff; // the same as float-float (mixed form)
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;
   int line0;  // first line (far lines then near lines)

@@ -1005,11 +1005,17 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
 //   I_m(mu) = eps^mu J_m,  J_0 = 1/mu,  J_m = L^m/mu - (2m/mu) J_{m-1},  L = log(pi eps^2 |w|^2).
 // 1/n for |n| <= kInvIntHalf (n = 0 unused), filled once by upload_inv_int
 __constant__ double c_inv_int[2 * kInvIntHalf + 1];
+__constant__ float2 c_inv_int_ff[2 * kInvIntHalf + 1];  // the same as float-float
 
 cudaError_t upload_inv_int() {
   double t[2 * kInvIntHalf + 1];
-  for (int n = -kInvIntHalf; n <= kInvIntHalf; ++n) t[n + kInvIntHalf] = n ? 1.0 / n : 0.0;
-  return cudaMemcpyToSymbol(c_inv_int, t, sizeof t);
+  float2 tf[2 * kInvIntHalf + 1];
+  for (int n = -kInvIntHalf; n <= kInvIntHalf; ++n) {
+    t[n + kInvIntHalf] = n ? 1.0 / n : 0.0;
+    ff_split(t[n + kInvIntHalf], tf[n + kInvIntHalf].x, tf[n + kInvIntHalf].y);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_inv_int, t, sizeof t);
+  return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_inv_int_ff, tf, sizeof tf);
 }
 
 __device__ double ipow(double x, int e) {
@@ -1023,20 +1029,78 @@ __device__ double ipow(double x, int e) {
   return e < 0 ? 1.0 / r : r;
 }
 
+// Number types of the near part: binary64 (FP64 form) and float-float (mixed form, where
+// the FP64 pipe would otherwise dominate: the products and Hadamard sums are ~3000
+// operations per ray).
+struct FFN {
+  float hi, lo;
+};
+__device__ __forceinline__ FFN operator+(FFN a, FFN b) {
+  const ff r = ff_add(ff{a.hi, a.lo}, ff{b.hi, b.lo});
+  return FFN{r.hi, r.lo};
+}
+__device__ __forceinline__ FFN operator*(FFN a, FFN b) {
+  const ff r = ff_mul(ff{a.hi, a.lo}, ff{b.hi, b.lo});
+  return FFN{r.hi, r.lo};
+}
+__device__ __forceinline__ double nfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ FFN nfma(FFN a, FFN b, FFN c) { return a * b + c; }
+template <typename N>
+__device__ __forceinline__ N nfrom(double x);
+template <>
+__device__ __forceinline__ double nfrom<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ FFN nfrom<FFN>(double x) {
+  FFN r;
+  ff_split(x, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ double nto(double x) { return x; }
+__device__ __forceinline__ double nto(FFN x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double ninv(double, int mk) {
+  return (mk >= -kInvIntHalf && mk <= kInvIntHalf) ? c_inv_int[mk + kInvIntHalf] : 1.0 / (double)mk;
+}
+__device__ __forceinline__ FFN ninv(FFN, int mk) {
+  if (mk >= -kInvIntHalf && mk <= kInvIntHalf) {
+    const float2 v = c_inv_int_ff[mk + kInvIntHalf];
+    return FFN{v.x, v.y};
+  }
+  return nfrom<FFN>(1.0 / (double)mk);
+}
+template <typename N>
+__device__ __forceinline__ N npow(N x, int e) {  // e >= 0
+  N r = nfrom<N>(1.0);
+  while (e) {
+    if (e & 1) r = r * x;
+    x = x * x;
+    e >>= 1;
+  }
+  return r;
+}
+__device__ __forceinline__ double ntaylor(const ReqDesc* R, int jn, int ia, double) {
+  return R->taylor[(size_t)jn * R->n_alpha + ia];
+}
+__device__ __forceinline__ FFN ntaylor(const ReqDesc* R, int jn, int ia, FFN) {
+  const float2 v = R->taylor_ff[(size_t)jn * R->n_alpha + ia];
+  return FFN{v.x, v.y};
+}
+
 // sig_w[j] = sigma_j |w|^{nu_j - d} / V (per ray, shared by every product and subset)
-__device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEll + 1], const double* sig_w,
-                               double L) {
+template <typename N>
+__device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], const N* sig_w, N L) {
   const int nd = R->n_distinct, d = R->d, ell = R->ell;
   int e[EZ_MAX_NU], t[EZ_MAX_NU];
   for (int j = 0; j < nd; ++j) {
     e[j] = R->expo[p][j];
     t[j] = 0;
   }
-  double total = 0.0;
-  double G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
-  const double eps2 = R->eps * R->eps, inv_eps = 1.0 / R->eps;
+  N total = nfrom<N>(0.0);
+  N G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
+  const N eps = nfrom<N>(R->eps), inv_eps = nfrom<N>(1.0 / R->eps), eps2 = eps * eps;
   while (true) {
-    double coef = 1.0;
+    N coef = nfrom<N>(1.0);
     long long mult = 1;  // product of binomials (exact integers)
     int mu = d, mlog = 0;
     for (int j = 0; j < nd; ++j) {
@@ -1044,40 +1108,40 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
         long long bj = 1;
         for (int i = 1; i <= t[j]; ++i) bj = bj * (e[j] - t[j] + i) / i;
         mult *= bj;
-        for (int i = 0; i < t[j]; ++i) coef *= sig_w[j];
+        for (int i = 0; i < t[j]; ++i) coef = coef * sig_w[j];
         mu += t[j] * ((int)lrint(R->nu[j]) - d);
         mlog += t[j] * R->islog[j];
       }
     }
     int deg = 0;
-    G[0] = 1.0;
+    G[0] = nfrom<N>(1.0);
     for (int j = 0; j < nd; ++j)
       for (int r = 0; r < e[j] - t[j]; ++r) {
         const int nd2 = min(deg + ell, kNearMaxDeg);
         for (int i = 0; i <= nd2; ++i) {
-          double s = 0.0;
-          for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = fma(G[q], C[j][i - q], s);
+          N s = nfrom<N>(0.0);
+          for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = nfma(G[q], C[j][i - q], s);
           T[i] = s;
         }
         deg = nd2;
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
-    double epm = mu >= 0 ? ipow(R->eps, mu) : ipow(inv_eps, -mu);
-    double sumk = 0.0;
+    N epm = mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu);
+    N sumk = nfrom<N>(0.0);
     for (int k = 0; k <= deg; ++k) {
       // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
       // reciprocals of small integers (no division in the loop)
       const int mk = mu + 2 * k;
-      const double inv = (mk >= -kInvIntHalf && mk <= kInvIntHalf) ? c_inv_int[mk + kInvIntHalf] : 1.0 / (double)mk;
-      double J = inv, Lp = 1.0;
+      const N inv = ninv(epm, mk);
+      N J = inv, Lp = nfrom<N>(1.0);
       for (int i = 1; i <= mlog; ++i) {
-        Lp *= L;
-        J = fma(-2.0 * i, J, Lp) * inv;
+        Lp = Lp * L;
+        J = (Lp + J * nfrom<N>(-2.0 * i)) * inv;
       }
-      sumk = fma(G[k], epm * J, sumk);
-      epm *= eps2;
+      sumk = nfma(G[k], epm * J, sumk);
+      epm = epm * eps2;
     }
-    total = fma((double)mult * coef, sumk, total);
+    total = nfma(nfrom<N>((double)mult) * coef, sumk, total);
     int j = 0;
     for (; j < nd; ++j) {
       if (t[j] < e[j]) {
@@ -1091,11 +1155,42 @@ __device__ double near_product(const ReqDesc* R, int p, const double (*C)[kMaxEl
   return total;
 }
 
+// one ray: C_k(w) of every exponent, then every product's near integral
+template <typename N>
+__device__ void near_ray(const ReqDesc* R, const double* w, double w2, double wv, double (&val)[EZ_MAX_PROD]) {
+  const int d = R->d, ell = R->ell, nd = R->n_distinct, np = R->n_prod;
+  // C_k(w) = sum_{|alpha| = 2k} D[alpha] w^alpha: one monomial per alpha (powers of w
+  // tabulated once), shared by every exponent
+  N pw[3][2 * kMaxEll + 1];
+  for (int i = 0; i < 3; ++i) {
+    const N wi = nfrom<N>(w[i]);
+    pw[i][0] = nfrom<N>(1.0);
+    for (int q = 1; q <= 2 * ell; ++q) pw[i][q] = pw[i][q - 1] * wi;
+  }
+  N C[EZ_MAX_NU][kMaxEll + 1];
+  for (int jn = 0; jn < nd; ++jn)
+    for (int kk = 0; kk <= ell; ++kk) C[jn][kk] = nfrom<N>(0.0);
+  for (int kk = 0; kk <= ell; ++kk)
+    for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
+      const int* al = R->alpha + 3 * ia;
+      const N mono = pw[0][al[0]] * pw[1][al[1]] * pw[2][al[2]];
+      for (int jn = 0; jn < nd; ++jn) C[jn][kk] = nfma(ntaylor(R, jn, ia, mono), mono, C[jn][kk]);
+    }
+  const N L = nfrom<N>(log(kPi * R->eps * R->eps * w2));
+  const double wn = sqrt(w2), inv_wn = 1.0 / wn, inv_V = 1.0 / R->V;
+  N sig_w[EZ_MAX_NU];
+  for (int jn = 0; jn < nd; ++jn) {
+    const int dn = (int)lrint(R->nu[jn]) - d;
+    sig_w[jn] = nfrom<N>(R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V);
+  }
+  for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * nto(near_product<N>(R, p, C, sig_w, L));
+}
+
 __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
                                                    double* __restrict__ seg) {
   const Item it = items[blockIdx.x];
   const ReqDesc* R = reqs + it.req;
-  const int d = R->d, nv = R->n_v, ell = R->ell, nd = R->n_distinct, np = R->n_prod;
+  const int d = R->d, nv = R->n_v, np = R->n_prod;
   const int nrays = d == 1 ? 1 : (d == 2 ? nv : nv * nv);
   const int r = it.chunk * blockDim.x + threadIdx.x;
   double val[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
@@ -1123,35 +1218,14 @@ __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ r
       w2 = fma(s, s, w2);
     }
     for (int i = d; i < 3; ++i) w[i] = 0.0;
-    // C_k(w) = sum_{|alpha| = 2k} D[alpha] w^alpha: one monomial per alpha (powers of w
-    // tabulated once), shared by every exponent
-    double pw[3][2 * kMaxEll + 1];
-    for (int i = 0; i < 3; ++i) {
-      pw[i][0] = 1.0;
-      for (int q = 1; q <= 2 * ell; ++q) pw[i][q] = pw[i][q - 1] * w[i];
-    }
-    double C[EZ_MAX_NU][kMaxEll + 1];
-    for (int jn = 0; jn < nd; ++jn)
-      for (int kk = 0; kk <= ell; ++kk) C[jn][kk] = 0.0;
-    for (int kk = 0; kk <= ell; ++kk)
-      for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
-        const int* al = R->alpha + 3 * ia;
-        const double mono = pw[0][al[0]] * pw[1][al[1]] * pw[2][al[2]];
-        for (int jn = 0; jn < nd; ++jn) C[jn][kk] = fma(R->taylor[(size_t)jn * R->n_alpha + ia], mono, C[jn][kk]);
-      }
-    const double L = log(kPi * R->eps * R->eps * w2);
-    const double wn = sqrt(w2), inv_wn = 1.0 / wn, inv_V = 1.0 / R->V;
-    double sig_w[EZ_MAX_NU];
-    for (int jn = 0; jn < nd; ++jn) {
-      const int dn = (int)lrint(R->nu[jn]) - d;
-      sig_w[jn] = R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V;
-    }
-    for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * near_product(R, p, C, sig_w, L);
+    if (R->prec == EZ_MIXED)
+      near_ray<FFN>(R, w, w2, wv, val);
+    else
+      near_ray<double>(R, w, w2, wv, val);
   }
   block_reduce_store<128>(val, np, 1.0, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
-// ------------------------------------------------------------------------- reductions
 __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
                              const int* line_nseg, int n_lines, const double* seg, double* lines) {
   const int L = blockIdx.x * blockDim.x + threadIdx.x;
