@@ -491,7 +491,7 @@ __device__ __forceinline__ float4 ff_complex(double2 z) {
 // numbers (float4: re hi, re lo, im hi, im lo), B and the per-node contraction are
 // compensated dot products in binary32 (H itself is accumulated in binary64 once per block).
 template <bool MIXED, int NDM>
-__global__ void __launch_bounds__(256) far_kernel_d3(const ReqDesc* __restrict__ reqs,
+__global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d3(const ReqDesc* __restrict__ reqs,
                                                        const Item* __restrict__ items, double* __restrict__ seg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PhiInfo sphi[NDM];
