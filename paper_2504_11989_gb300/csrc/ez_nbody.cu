@@ -791,9 +791,10 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
 }
 
 // ------------------------------------------------------------------------- d = 2
+
 template <bool MIXED, int NDM>
-__global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__ reqs,
-                                                       const Item* __restrict__ items, double* __restrict__ seg) {
+__device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
+                                            double* __restrict__ seg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PhiInfo sphi[NDM];
   const Item it = items[blockIdx.x];
@@ -922,6 +923,18 @@ __global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__
   }
   count_work(R, terms, coefs);
   block_reduce_store<128>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
+}
+
+template <bool MIXED, int NDM>
+__global__ void __launch_bounds__(128) far_kernel_d2(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
+                                                     double* __restrict__ seg) {
+  far_d2_body<MIXED, NDM>(reqs, items, seg);
+}
+// the single-exponent mixed variant trades a few spills for 32 resident warps per SM
+__global__ void __launch_bounds__(128, 8) far_kernel_d2_mixed1(const ReqDesc* __restrict__ reqs,
+                                                               const Item* __restrict__ items,
+                                                               double* __restrict__ seg) {
+  far_d2_body<true, 1>(reqs, items, seg);
 }
 
 // ------------------------------------------------------------------------- d = 1
@@ -1282,6 +1295,8 @@ static cudaError_t launch_far_t(int d, unsigned grid, size_t smem, cudaStream_t 
                                 const Item* items, double* seg) {
   if (d == 1)
     far_kernel_d1<MIXED, NDM><<<grid, 128, 0, st>>>(reqs, items, seg);
+  else if (d == 2 && MIXED && NDM == 1)
+    far_kernel_d2_mixed1<<<grid, 128, smem, st>>>(reqs, items, seg);
   else if (d == 2)
     far_kernel_d2<MIXED, NDM><<<grid, 128, smem, st>>>(reqs, items, seg);
   else
@@ -1310,7 +1325,8 @@ static cudaError_t far_smem_limits_t() {
 }
 
 cudaError_t far_set_smem_limits() {
-  cudaError_t e;
+  cudaError_t e = cudaFuncSetAttribute(far_kernel_d2_mixed1, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (e != cudaSuccess) return e;
   if ((e = far_smem_limits_t<false, 1>()) != cudaSuccess) return e;
   if ((e = far_smem_limits_t<false, 4>()) != cudaSuccess) return e;
   if ((e = far_smem_limits_t<false, 8>()) != cudaSuccess) return e;
