@@ -67,15 +67,22 @@ typedef struct {
                      3 V^{1/2} (d = 2), 4 V^{1/3} (d = 3, EZ_FP64) or 3.5 V^{1/3} (d = 3, EZ_MIXED),
                      lowered if needed so that the real-space box half-width stays <= 16.  The sum
                      does not depend on it (Crandall's formula, Sec. 2); ez_epstein_zeta uses V^{1/d} */
-  double r_real;  /* real-space cutoff |z| <= r_real (default sqrt(45/pi) lambda) */
-  double r_recip; /* reciprocal cutoff |g + k| <= r_recip (default sqrt(45/pi) / lambda) */
+  double r_real;  /* real-space cutoff |z| <= r_real (default sqrt(T/pi) lambda, T = 45 for
+                     EZ_FP64, 36 for EZ_MIXED) */
+  double r_recip; /* reciprocal cutoff |g + k| <= r_recip (default sqrt(T/pi) / lambda) */
   int prec;       /* ez_precision */
   int dedupe;     /* 1: one Epstein zeta evaluation per distinct nu and node (default);
                      0: one evaluation per factor (n <= EZ_MAX_NU) */
+  int part;       /* n_parts > 1: only part `part` (0 <= part < n_parts) of the sum: a contiguous
+                     range of its Duffy lines (sector, u node), the near part in part 0.  The
+                     values of the n_parts parts add up to the whole sum (to rounding), so one
+                     sum can be split over several GPUs or streams; 0 and 0 (or n_parts <= 1):
+                     the whole sum */
+  int n_parts;
 } ez_quadrature;
 
 /* Fills *q with the defaults (n_u = 32, n_v = 32, u_rule 0, eps 1e-2, ell 4, lambda 0,
- * cutoffs 0, EZ_FP64, dedupe 1). */
+ * cutoffs 0, EZ_FP64, dedupe 1, the whole sum). */
 void ez_quadrature_default(ez_quadrature* q);
 
 /* One lattice sum: product p = prod_j Z_{nu_j}(k)^{expo[p][j]} integrated over the

@@ -227,6 +227,9 @@ struct Plan {
   int vchunk;         // d = 3: v2 rows per far-field block
   int m_hp[3];        // mixed form: |m_i| >= m_hp[i] summed in plain binary32
   int n_far_seg, n_far_items, near_per_sector, n_near_seg, n_lines_far, n_lines;
+  int part, n_parts;          // the part of the sum this plan computes
+  long long line_lo, line_hi; // its far lines [line_lo, line_hi) of sector * n_ui + iu
+  bool near_active;           // the near part is computed (part 0 of an eps-split sum)
   size_t smem;
 };
 
@@ -599,12 +602,23 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     }
   }
   p.nch = d == 3 ? (p.n_v + p.vchunk - 1) / p.vchunk : 1;
+  // part of the sum: far lines [line_lo, line_hi) (d = 1: items are chunks of 128 u nodes;
+  // nodes of a chunk outside the range are computed but their lines are empty)
+  p.n_parts = q.n_parts > 1 ? q.n_parts : 1;
+  p.part = p.n_parts > 1 ? q.part : 0;
+  if (p.part < 0 || p.part >= p.n_parts) return fail(EZ_EINVAL, "part %d of %d", q.part, q.n_parts);
+  {
+    const long long nl = (long long)p.nsect * p.n_ui;
+    p.line_lo = nl * p.part / p.n_parts;
+    p.line_hi = nl * (p.part + 1) / p.n_parts;
+  }
+  p.near_active = p.near && p.part == 0;
   if (d == 1) {
     p.n_far_seg = p.n_ui;
-    p.n_far_items = (p.n_ui + 127) / 128;
+    p.n_far_items = p.line_hi > p.line_lo ? (int)((p.line_hi - 1) / 128 - p.line_lo / 128 + 1) : 0;
   } else {
     p.n_far_seg = p.nsect * p.n_ui * p.nch;
-    p.n_far_items = p.n_far_seg;
+    p.n_far_items = (int)((p.line_hi - p.line_lo) * p.nch);
   }
   int nrays = d == 1 ? 1 : (d == 2 ? p.n_v : p.n_v * p.n_v);
   p.near_per_sector = p.near ? (nrays + 127) / 128 : 0;
@@ -797,7 +811,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   for (int r : order) {
     seg_near0[r] = n_seg;
     n_seg += plans[r].n_near_seg;
-    n_items_near += plans[r].n_near_seg;
+    if (plans[r].near_active) n_items_near += plans[r].n_near_seg;
   }
   for (int r = 0; r < n_req; ++r) {
     line0[r] = n_lines;
@@ -816,7 +830,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   int& n_tay = B.n_tay;
   n_phi = n_tay = 0;
   for (int r = 0; r < n_req; ++r)
-    if (plans[r].near) n_tay += plans[r].spec.n_distinct;
+    if (plans[r].near_active) n_tay += plans[r].spec.n_distinct;
   // Phi tables depend on a alone (up to the argument scale of each record): one table per
   // distinct a, computed for the member with the most intervals, copied to the others
   // (slot j < EZ_MAX_NU: reciprocal order j; slot EZ_MAX_NU + j: real-space order j)
@@ -1101,7 +1115,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     }
     GJ.outff = o_gboxff[r] ? (float2*)dptr(o_gboxff[r]) : nullptr;
     R.gboxff = o_gboxff[r] ? (const float2*)dptr(o_gboxff[r]) : nullptr;
-    if (p.near)
+    if (p.near_active)
       for (int j = 0; j < p.spec.n_distinct; ++j) {
         TaylorJob& T = tjobs[itj++];
         T.req = r;
@@ -1168,12 +1182,13 @@ int batch_layout(ez_batch_s& B, bool fill) {
           if (p.d != d || (p.prec == EZ_MIXED) != (mixed != 0) || far_nd_class(p.spec.n_distinct) != ndm) continue;
           g.smem = std::max(g.smem, p.smem);
           if (d == 1) {
-            for (int c = 0; c < p.n_far_items; ++c) items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
+            for (int c = (int)(p.line_lo / 128); c * 128LL < p.line_hi; ++c)
+              items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
           } else {
-            long long s0 = seg_far0[r];
-            for (int s = 0; s < p.nsect; ++s)
-              for (int iu = 0; iu < p.n_ui; ++iu)
-                for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, s0++};
+            for (long long L = p.line_lo; L < p.line_hi; ++L) {
+              const int s = (int)(L / p.n_ui), iu = (int)(L % p.n_ui);
+              for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, seg_far0[r] + L * p.nch + c};
+            }
           }
         }
         g.end = ii;
@@ -1182,6 +1197,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   B.near_begin = ii;
   for (int r : order) {
     Plan& p = plans[r];
+    if (!p.near_active) continue;
     long long s0 = seg_near0[r];
     for (int s = 0; s < p.nsect; ++s)
       for (int c = 0; c < p.near_per_sector; ++c) items[ii++] = Item{r, s, 0, c, s0++};
@@ -1196,16 +1212,17 @@ int batch_layout(ez_batch_s& B, bool fill) {
     for (int s = 0; s < p.nsect; ++s)
       for (int iu = 0; iu < p.n_ui; ++iu) {
         long long L = L0 + (long long)s * p.n_ui + iu;
+        const long long Lr = (long long)s * p.n_ui + iu;
         lreq[L] = r;
-        lseg0[L] = seg_far0[r] + ((long long)s * p.n_ui + iu) * p.nch;
-        lnseg[L] = p.nch;
+        lseg0[L] = seg_far0[r] + Lr * p.nch;
+        lnseg[L] = (Lr >= p.line_lo && Lr < p.line_hi) ? p.nch : 0;  // lines of other parts are empty
       }
     if (p.near)
       for (int s = 0; s < p.nsect; ++s) {
         long long L = L0 + p.n_lines_far + s;
         lreq[L] = r;
         lseg0[L] = seg_near0[r] + (long long)s * p.near_per_sector;
-        lnseg[L] = p.near_per_sector;
+        lnseg[L] = p.near_active ? p.near_per_sector : 0;
       }
   }
   return EZ_OK;

@@ -44,6 +44,8 @@ class ez_quadrature(ctypes.Structure):
         ("r_recip", ctypes.c_double),
         ("prec", ctypes.c_int),
         ("dedupe", ctypes.c_int),
+        ("part", ctypes.c_int),
+        ("n_parts", ctypes.c_int),
     ]
 
 

@@ -79,6 +79,17 @@ def test_layout_rejects_hadamard_pole_and_bad_exponents(ez):
     assert e.value.code == ez.EZ_EINVAL
 
 
+def test_layout_rejects_bad_part(ez):
+    q = ez.quadrature(W.Quad(n_u=8, n_v=8), part=3, n_parts=2)
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_layout(2, ez.sum_spec([3.0], [[2]]), q)
+    assert e.value.code == ez.EZ_EINVAL
+    # a valid part plans like the whole sum (same tables and line count)
+    whole = ez.ez_layout(2, ez.sum_spec([3.0], [[2]]), ez.quadrature(W.Quad(n_u=8, n_v=8)))
+    part = ez.ez_layout(2, ez.sum_spec([3.0], [[2]]), ez.quadrature(W.Quad(n_u=8, n_v=8), part=1, n_parts=2))
+    assert part[1:] == whole[1:]
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     from paper_2504_11989_gb300 import ezeta
 

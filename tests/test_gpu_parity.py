@@ -218,6 +218,35 @@ def test_default_splitting_parameter_matches_oracle(ez, oracle_mod, prob):
     assert _close(got, ref), (prob.name, got, ref)
 
 
+@pytest.mark.parametrize("prob,prec", [
+    (W.nbody_problem("Z", 4.0, 3, W.config1(300)), 0),
+    (W.nbody_problem("hexagonal", 3.0, 3, W.config2(34)), 0),
+    (W.atm_problem("square", W.Quad(n_u=6, n_v=10, u_rule=2, lam=1.0, r_real=6, r_recip=6)), 0),
+    (W.nbody_problem("fcc", 6.0, 3, W.Quad(n_u=5, n_v=19, **AUTO)), 0),
+    (W.atm_problem("sc", W.Quad(n_u=3, n_v=12, u_rule=2, **AUTO)), 1),
+], ids=["d1", "d2", "d2-atm-near", "d3", "d3-atm-mixed"])
+def test_parts_add_up_to_the_whole(ez, prob, prec):
+    """n_parts = 3 splits a sum over contiguous ranges of Duffy lines (near part in part
+    0): each part's lines equal the whole sum's lines bitwise on its range and are zero
+    elsewhere, and the three values add up to the whole value."""
+    L = ez.Lattice(prob.A)
+    spec = ez.sum_spec(prob.nu, prob.expo)
+    npr = len(prob.expo)
+    whole, wl, offs = ez.ez_lattice_sums([L], [spec], [ez.quadrature(prob.quad, prec=prec)], lines=True)
+    wl = wl[offs[0]: offs[1], :npr]
+    parts = [ez.quadrature(prob.quad, prec=prec, part=k, n_parts=3) for k in range(3)]
+    vals, pl, poffs = ez.ez_lattice_sums([L] * 3, [spec] * 3, parts, lines=True)
+    covered = np.zeros(len(wl), dtype=int)
+    for k in range(3):
+        lk = pl[poffs[k]: poffs[k + 1], :npr]
+        nz = np.any(lk != 0.0, axis=1)
+        assert np.array_equal(lk[nz], wl[nz])
+        covered += nz
+    assert np.all(covered[np.any(wl != 0.0, axis=1)] == 1)  # every line in exactly one part
+    tot = vals[:, :npr].sum(axis=0)
+    assert np.all(np.abs(tot - whole[0, :npr]) <= 1e-14 * np.sum(np.abs(wl), axis=0))
+
+
 def test_nbody_api_matches_batch_and_is_deterministic(ez, oracle_mod):
     prob = W.nbody_problem("hexagonal", 3.0, 4, W.config2(40))
     L = ez.Lattice(prob.A)
