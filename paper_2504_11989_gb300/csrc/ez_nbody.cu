@@ -93,6 +93,15 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
   const float R2f = R->R2f, cf = R->c_lam_f;
   const G4* rec = R->rec;
   const float4* recf = R->recf;
+  // |G + k|^2 = |G|^2 + |k|^2 + 2 G.k: with 2k and |k|^2 per node, d FMAs and one add per
+  // term (for k in the reduced cell |G + k| is not much smaller than |G|: no cancellation
+  // beyond a few ulp)
+  double k2v[3] = {0.0, 0.0, 0.0}, kk2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    k2v[i] = 2.0 * k[i];
+    kk2 = fma(k[i], k[i], kk2);
+  }
   for (int h = 0; h < nrec; ++h) {
     const float4 Gf = __ldg(recf + h);
     float qqf;
@@ -109,17 +118,9 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
     if (qqf <= R2f) {
       const float tf = cf * qqf;
       const G4 G = ldg_g4(rec + h);
-      double qq;
-      if (D == 1) {
-        const double q0 = G.x + k[0];
-        qq = q0 * q0;
-      } else if (D == 2) {
-        const double q0 = G.x + k[0], q1 = G.y + k[1];
-        qq = fma(q0, q0, q1 * q1);
-      } else {
-        const double q0 = G.x + k[0], q1 = G.y + k[1], q2 = G.z + k[2];
-        qq = fma(q0, q0, fma(q1, q1, q2 * q2));
-      }
+      double qq = fma(k2v[0], G.x, G.w + kk2);
+      if (D >= 2) qq = fma(k2v[1], G.y, qq);
+      if (D >= 3) qq = fma(k2v[2], G.z, qq);
       ++terms;
 #pragma unroll
       for (int j = 0; j < NDM; ++j)

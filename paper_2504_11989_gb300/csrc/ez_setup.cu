@@ -190,10 +190,10 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   __shared__ int nkeep_f, nkeep_ff;
   if (k == 0) {
     // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance:
-    // binary64 table max(2^-55 max|Phi|, 1e-19), binary32 table 2^-26 max|Phi|
+    // binary64 table max(2^-53 max|Phi|, 1e-19), binary32 table 2^-26 max|Phi|
     double fm = 0.0;
     for (int q = 0; q < kNC; ++q) fm = fmax(fm, fabs(f[q]));
-    const double tol = fmax(fm / 36028797018963968.0, 1e-19);
+    const double tol = fmax(fm / 9007199254740992.0, 1e-19);  // 2^-53 max|Phi|
     const double tolf = fm / 67108864.0;
     const double tolff = fm / 140737488355328.0;  // 2^-47: float-float table
     int n = kNC, nf = kNC, nff = kNC;
