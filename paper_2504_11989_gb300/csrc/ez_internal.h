@@ -19,7 +19,7 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 //   coefficients kept (4, 8, 12 or 16, an int in the first slot), s = c/h and
 //   o = -t_mid/h so that x = fma(|q|^2, s, o) with t = c |q|^2, one pad slot, then
 //   b_0 .. b_{kNC-1} (monomials in x; b_j = 0 for j >= n).  n is the shortest length whose Chebyshev
-//   tail is below max(2^-53 max|Phi|, 1e-19) on the interval.
+//   tail is below max(2^-53 max|Phi|, 1e-19) on the interval: 1 (a constant), 4, 8, 12 or 16.
 // t < kT0: series of the entire part plus the singular term.
 // t > t_hi: asymptotic expansion e^{-t}/t (1 + (a-1)/t + (a-1)(a-2)/t^2 + ...).
 // ---------------------------------------------------------------------------

@@ -149,6 +149,7 @@ __device__ __forceinline__ int phi_interval(float tf, float t_geo_end_f) {
 __device__ __forceinline__ double phi_poly(const double* r, double x, int& n_used) {
   const int n = __ldg(reinterpret_cast<const int*>(r));
   n_used = n;
+  if (n == 1) return __ldg(r + 4);  // constant on the interval (below the tolerance)
   const double2* c2 = reinterpret_cast<const double2*>(r + 4);
   int blk = (n >> 2) - 1;
   double2 hi = __ldg(c2 + 2 * blk + 1), lo = __ldg(c2 + 2 * blk);

@@ -204,6 +204,11 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
       if (tail <= tolf) nf = cand;
       if (tail <= tolff) nff = cand;
     }
+    // binary64 table: a single coefficient where the whole non-constant part is below the
+    // tolerance (far tails, |Phi| < ~1e-19: one load instead of a Horner scheme)
+    double tail1 = 0.0;
+    for (int q = 1; q < kNC; ++q) tail1 += fabs(cj[q]);
+    if (tail1 <= tol) n = 1;
     nkeep = n;
     nkeep_f = nf;
     nkeep_ff = nff;
