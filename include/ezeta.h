@@ -74,10 +74,11 @@ typedef struct {
   int dedupe;     /* 1: one Epstein zeta evaluation per distinct nu and node (default);
                      0: one evaluation per factor (n <= EZ_MAX_NU) */
   int part;       /* n_parts > 1: only part `part` (0 <= part < n_parts) of the sum: a contiguous
-                     range of its Duffy lines (sector, u node), the near part in part 0.  The
-                     values of the n_parts parts add up to the whole sum (to rounding), so one
-                     sum can be split over several GPUs or streams; 0 and 0 (or n_parts <= 1):
-                     the whole sum */
+                     range of its Duffy lines (sector, u node) for d <= 2, of its line groups
+                     (the four sectors 4 j .. 4 j + 3 of one axis j, u node) for d = 3, the
+                     near part in part 0.  The values of the n_parts parts add up to the whole
+                     sum (to rounding), so one sum can be split over several GPUs or streams;
+                     0 and 0 (or n_parts <= 1): the whole sum */
   int n_parts;
 } ez_quadrature;
 

@@ -227,8 +227,10 @@ struct Plan {
   int vchunk;         // d = 3: v2 rows per far-field block
   int m_hp[3];        // mixed form: |m_i| >= m_hp[i] summed in plain binary32
   int n_far_seg, n_far_items, near_per_sector, n_near_seg, n_lines_far, n_lines;
+  int hslot;                  // d = 3: 16-byte entries of the folded H of one line group
   int part, n_parts;          // the part of the sum this plan computes
-  long long line_lo, line_hi; // its far lines [line_lo, line_hi) of sector * n_ui + iu
+  long long line_lo, line_hi; // its far lines [line_lo, line_hi) of sector * n_ui + iu (d <= 2)
+                              // or line groups of j * n_ui + iu (d = 3: the four sectors 4 j + pb)
   bool near_active;           // the near part is computed (part 0 of an eps-split sum)
   size_t smem;
 };
@@ -584,31 +586,43 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     }
   }
 
-  // segments.  d = 3: a far-field block takes vchunk = ceil(n_v / q) rows v2 of a line.
-  // The phase and H stages cost the same per block, so q is the smallest split whose
-  // shared memory fits two blocks per SM (96 KB dynamic + the static reciprocal-list
-  // cache and tables) and that still gives the sum at least
-  // four blocks per SM of the GPU (608); failing that, the most blocks with vchunk >= 8.
+  // segments.  d = 3: a far-field block takes the four sectors of a line group (axis j,
+  // u node) and vchunk rows v2 of them; its 256 threads run n_v * rows nodes per sign p2.
+  // vchunk is the largest count whose shared memory fits two blocks per SM (100 KB dynamic
+  // + the static reciprocal-list cache and tables, <= 12 KB) that maximises (busy thread slots) x
+  // (busy block slots of the last wave, 304 = two blocks per SM of the GPU) for the sum.
   p.vchunk = 1;
   if (d == 3) {
-    const long long lines = (long long)p.nsect * p.n_ui;
+    const long long groups = (long long)d * p.n_ui;
+    double best = -1.0;
     p.vchunk = std::min(p.n_v, kVChunkMin);
-    for (int q = 1; q <= p.n_v; ++q) {
-      const int c = (p.n_v + q - 1) / q;
-      if (c < kVChunkMin && q > 1) break;
-      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 96 * 1024) continue;
-      p.vchunk = c;
-      if (lines * ((p.n_v + c - 1) / c) >= 608) break;
+    for (int c = p.n_v; c >= 1; --c) {
+      if (c < kVChunkMin && c < p.n_v) break;
+      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 100 * 1024) continue;
+      const int nch = (p.n_v + c - 1) / c;
+      double work = 0.0, slots = 0.0;
+      for (int k = 0; k < nch; ++k) {
+        const long long nn = (long long)p.n_v * std::min(c, p.n_v - k * c);
+        work += (double)nn;
+        slots += 256.0 * (double)((nn + 255) / 256);
+      }
+      const double blocks = (double)groups * nch;
+      const double score = work / slots * blocks / (304.0 * std::ceil(blocks / 304.0));
+      if (score > best + 1e-9) {
+        best = score;
+        p.vchunk = c;
+      }
     }
   }
   p.nch = d == 3 ? (p.n_v + p.vchunk - 1) / p.vchunk : 1;
-  // part of the sum: far lines [line_lo, line_hi) (d = 1: items are chunks of 128 u nodes;
-  // nodes of a chunk outside the range are computed but their lines are empty)
+  // part of the sum: far lines [line_lo, line_hi) of sector * n_ui + iu for d <= 2, line
+  // groups [line_lo, line_hi) of j * n_ui + iu for d = 3 (d = 1: items are chunks of 128 u
+  // nodes; nodes of a chunk outside the range are computed but their lines are empty)
   p.n_parts = q.n_parts > 1 ? q.n_parts : 1;
   p.part = p.n_parts > 1 ? q.part : 0;
   if (p.part < 0 || p.part >= p.n_parts) return fail(EZ_EINVAL, "part %d of %d", q.part, q.n_parts);
   {
-    const long long nl = (long long)p.nsect * p.n_ui;
+    const long long nl = (long long)(d == 3 ? d : p.nsect) * p.n_ui;
     p.line_lo = nl * p.part / p.n_parts;
     p.line_hi = nl * (p.part + 1) / p.n_parts;
   }
@@ -626,6 +640,11 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   p.n_lines_far = p.nsect * p.n_ui;
   p.n_lines = p.n_lines_far + (p.near ? p.nsect : 0);
   p.smem = far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, p.vchunk);
+  {
+    int Mx = 0;
+    for (int i = 0; i < d; ++i) Mx = std::max(Mx, p.M[i]);
+    p.hslot = d == 3 ? spec.n_distinct * (Mx + 1) * (2 * Mx + 1) : 0;
+  }
   return EZ_OK;
 }
 
@@ -745,7 +764,7 @@ struct ez_batch_s {
   size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
   int n_phi = 0, n_tay = 0, n_pcopy = 0;
-  size_t o_pcj = 0;
+  size_t o_pcj = 0, o_hj = 0;
   std::vector<std::pair<int, int>> phi_master;  // per distinct a: (request, nu index) computing the table
   std::vector<std::array<int, 3>> phi_copy;     // (request, nu index, group) copying it
   struct FarGroup {
@@ -826,6 +845,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_rj = hl.take(sizeof(RecipJob) * n_req);
   B.o_gj = dl.take(sizeof(GboxJob) * n_req);
   const size_t h_gj = hl.take(sizeof(GboxJob) * n_req);
+  B.o_hj = dl.take(sizeof(HboxJob) * n_req);
+  const size_t h_hj = hl.take(sizeof(HboxJob) * n_req);
   int& n_phi = B.n_phi;
   int& n_tay = B.n_tay;
   n_phi = n_tay = 0;
@@ -913,7 +934,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_tayff(n_req);
+      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_tayff(n_req), o_hbox(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -947,6 +968,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_rectmp[r] = dl.take(sizeof(G4) * p.rcap);
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     o_gboxff[r] = p.prec == EZ_MIXED ? dl.take(sizeof(float2) * p.cells * p.spec.n_distinct) : 0;
+    o_hbox[r] = p.d == 3 ? dl.take(16 * (size_t)p.hslot * std::max<long long>(p.line_hi - p.line_lo, 1)) : 0;
     o_tab[r].assign(2 * EZ_MAX_NU, 0);
     o_tabf[r].assign(2 * EZ_MAX_NU, 0);
     o_tabff[r].assign(2 * EZ_MAX_NU, 0);
@@ -993,6 +1015,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   Item* items = (Item*)(Hs + h_items);
   RecipJob* rjobs = (RecipJob*)(Hs + h_rj);
   GboxJob* gjobs = (GboxJob*)(Hs + h_gj);
+  HboxJob* hjobs = (HboxJob*)(Hs + h_hj);
   PhiJob* pjobs = (PhiJob*)(Hs + h_pj);
   TaylorJob* tjobs = (TaylorJob*)(Hs + h_tj);
   int* lreq = (int*)(Hs + h_lreq);
@@ -1115,6 +1138,16 @@ int batch_layout(ez_batch_s& B, bool fill) {
     }
     GJ.outff = o_gboxff[r] ? (float2*)dptr(o_gboxff[r]) : nullptr;
     R.gboxff = o_gboxff[r] ? (const float2*)dptr(o_gboxff[r]) : nullptr;
+    HboxJob& HJ = hjobs[r];
+    HJ.req = r;
+    HJ.g_lo = p.d == 3 ? (int)p.line_lo : 0;
+    HJ.g_hi = p.d == 3 ? (int)p.line_hi : 0;
+    HJ.out = p.d == 3 && p.prec != EZ_MIXED ? (double2*)dptr(o_hbox[r]) : nullptr;
+    HJ.outff = p.d == 3 && p.prec == EZ_MIXED ? (float4*)dptr(o_hbox[r]) : nullptr;
+    R.hbox = HJ.out;
+    R.hboxff = HJ.outff;
+    R.hslot = p.hslot;
+    R.hg_lo = HJ.g_lo;
     if (p.near_active)
       for (int j = 0; j < p.spec.n_distinct; ++j) {
         TaylorJob& T = tjobs[itj++];
@@ -1186,8 +1219,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
               items[ii++] = Item{r, 0, c * 128, c, seg_far0[r] + c * 128};
           } else {
             for (long long L = p.line_lo; L < p.line_hi; ++L) {
-              const int s = (int)(L / p.n_ui), iu = (int)(L % p.n_ui);
-              for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, seg_far0[r] + L * p.nch + c};
+              // d = 3: L is a line group (axis j, u node); the item covers sectors 4 j .. 4 j + 3
+              const int s = (int)(L / p.n_ui) * (d == 3 ? 4 : 1), iu = (int)(L % p.n_ui);
+              const long long Ls = (long long)s * p.n_ui + iu;
+              for (int c = 0; c < p.nch; ++c) items[ii++] = Item{r, s, iu, c, seg_far0[r] + Ls * p.nch + c};
             }
           }
         }
@@ -1215,7 +1250,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
         const long long Lr = (long long)s * p.n_ui + iu;
         lreq[L] = r;
         lseg0[L] = seg_far0[r] + Lr * p.nch;
-        lnseg[L] = (Lr >= p.line_lo && Lr < p.line_hi) ? p.nch : 0;  // lines of other parts are empty
+        const long long Lp = p.d == 3 ? (long long)(s / 4) * p.n_ui + iu : Lr;  // line (group) of the part range
+        lnseg[L] = (Lp >= p.line_lo && Lp < p.line_hi) ? p.nch : 0;  // lines of other parts are empty
       }
     if (p.near)
       for (int s = 0; s < p.nsect; ++s) {
@@ -1258,6 +1294,15 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
   gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
   EZ_LAUNCHED();
+  {
+    long long max_groups = 0;
+    for (auto& p : B.plans)
+      if (p.d == 3) max_groups = std::max(max_groups, p.line_hi - p.line_lo);
+    if (max_groups > 0) {
+      hbox_kernel<<<dim3((unsigned)max_groups, B.n_req), 128, 0, stream>>>(dreqs, (const HboxJob*)dptr(B.o_hj));
+      EZ_LAUNCHED();
+    }
+  }
   if (B.n_tay) {
     long long max_rec = 0;
     for (auto& p : B.plans)
@@ -1418,12 +1463,14 @@ extern "C" int ez_batch_far_flops(ez_batch B, double* flops, long long* terms, l
       blocks = (double)p.nsect * p.n_ui;
       per_block = nd * (Ma + 1) * Mc * 4.0;
     } else {
+      // a block covers the four sectors of a line group: the two nodes p1 = +-1 of a
+      // (v1, v2, p2) share one pass over ma (two FMAs), B_{+-} one pass over mb (four);
+      // H is built by hbox_kernel, outside the far kernel
       const double Mm = (p.M[0] + p.M[1] + p.M[2]) / 3.0;
-      per_node += Mm * 4.0 * nd + 2.0 * nd;
-      blocks = (double)p.nsect * p.n_ui * p.nch;
+      per_node += Mm * 2.0 * nd + 3.0 * nd;
+      blocks = (double)d * p.n_ui * p.nch;
       const double nv2 = std::min(p.vchunk, p.n_v);
-      per_block = (Mm + 1) * p.n_v * 6.0 + (Mm + 1) * nv2 * 6.0 + nd * (Mm + 1) * (2 * Mm + 1) * Mm * 4.0 +
-                  nd * (Mm + 1) * nv2 * Mm * 8.0;
+      per_block = (Mm + 1) * p.n_v * 6.0 + (Mm + 1) * nv2 * 6.0 + nd * (Mm + 1) * nv2 * (Mm * 8.0 + 4.0);
     }
     total += per_term + nodes * per_node + blocks * per_block;
   }

@@ -74,6 +74,7 @@ constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
 constexpr int kMaxEll = 8;       // largest Taylor order parameter ell of the near part
 constexpr int kInvIntHalf = 256; // near part: table of 1/n for |n| <= kInvIntHalf
 constexpr int kVChunkMin = 8;   // d = 3: fewest v2 rows per far-field block
+constexpr int kMaxBoxM = 16;    // largest real-space box half-width M_i
 
 struct ReqDesc {
   int d, nsect, n_ui, n_v, u_rule, n_distinct, n_prod, ell, prec;
@@ -89,6 +90,11 @@ struct ReqDesc {
   int m_hp[3];         // mixed form: real-space terms with |m_i| >= m_hp[i] are summed in binary32
   const double* gbox;  // [n_distinct][box0][box1][box2]
   const float2* gboxff; // the same as float-float (hi, lo), for the mixed form
+  // d = 3: folded H(ma, mb) per line group G = j n_ui + iu in [hg_lo, hg_lo + groups), hslot
+  // 16-byte entries per group: double2 (FP64 form, hbox) or float-float complex (hboxff)
+  const double2* hbox;
+  const float4* hboxff;
+  int hslot, hg_lo;
   // reciprocal space: all h with |A^{-T} h| <= r_recip + max_BZ |k|
   int n_rec;
   const G4* rec;      // (G_0, G_1, G_2, |G|^2)

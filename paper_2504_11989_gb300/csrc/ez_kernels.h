@@ -28,6 +28,13 @@ struct GboxJob {
   PhiInfo phi[EZ_MAX_NU];
 };
 
+// d = 3 far field: H of the line groups [g_lo, g_hi) of one request (slot G - g_lo)
+struct HboxJob {
+  int req, g_lo, g_hi;
+  double2* out;   // FP64 form
+  float4* outff;  // mixed form (float-float complex); exactly one of out / outff is set
+};
+
 struct PhiJob {
   double a;
   double c_lam;
@@ -92,6 +99,7 @@ struct EpsteinArgs {
 __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs);
 __global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs);
 __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs);
+__global__ void hbox_kernel(const ReqDesc* reqs, const HboxJob* jobs);
 __global__ void phitab_kernel(const PhiJob* jobs);
 __global__ void phicopy_kernel(const PhiCopyJob* jobs);
 __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);

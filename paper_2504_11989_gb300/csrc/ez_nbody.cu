@@ -1,12 +1,14 @@
 // Far-field, near-field and reduction kernels of the n-body lattice sums
 // (Thm "Epstein representation", Cor. "Duffy transformation", Sec. 3).
 //
-// Far field: a block owns one Duffy line (sector s, u node) -- for d = 3 one
-// chunk of vchunk v2 rows of it.  On a line k~ = u sigma^j(p1 v1, p2 v2, 1), so
-// the real-space sum of every node factorises over the axes:
+// Far field: a block owns one Duffy line (sector s, u node) for d <= 2; for d = 3 the
+// four sectors of one axis j and u node (a line group), vchunk v2 rows of them.  On a
+// line k~ = u sigma^j(p1 v1, p2 v2, 1), so the real-space sum of every node factorises
+// over the axes:
 //   sum_m g(m) e^{2 pi i m.k~} = sum_{ma} Ea(ma, v1) B(ma, v2),
 //   B(ma, v2) = sum_{mb} Eb(mb, v2) H(ma, mb),  H(ma, mb) = sum_{mc} g(m) e^{2 pi i mc u},
-// H and B are built once per block in shared memory; g(-m) = g(m) folds ma < 0.
+// H once per line group (d = 3) or per block, B once per block in shared memory;
+// g(-m) = g(m) folds ma < 0.
 // The reciprocal sum runs per node over the compacted list of A^{-T} h.
 #include <cstdio>
 #include <type_traits>
@@ -454,9 +456,9 @@ size_t far_smem_bytes(int d, int nd, const int* M, int n_v, int vchunk) {
   int Mx = 0;
   for (int i = 0; i < d; ++i) Mx = M[i] > Mx ? M[i] : Mx;
   size_t n = 0;
-  if (d == 3)
-    n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * vchunk + (Mx + 1) + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
-        (size_t)nd * (Mx + 1) * vchunk;
+  if (d == 3)  // Ea, Eb, H, B_{+-}, and 8 bytes per (exponent, thread) for the p1 = -1 node
+    n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * vchunk + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
+        2 * (size_t)nd * (Mx + 1) * vchunk + (size_t)nd * 128;
   else if (d == 2)
     n = (size_t)(Mx + 1) + (size_t)nd * (Mx + 1);
   return n * sizeof(double2);
@@ -483,139 +485,40 @@ __device__ __forceinline__ float4 ff_complex(double2 z) {
 }
 
 // ------------------------------------------------------------------------- d = 3
-// Block: one Duffy line (sector, u) and vchunk rows v2 of it, all n_v values of v1.
-// Shared memory (16-byte entries): Ea[(Ma+1) n_v], Eb[(Mb+1) vchunk], Ec[Mc+1],
-// H[nd (Ma+1) (2Mb+1)], B[nd (Ma+1) vchunk].  H is stored folded over mb:
-// H(ma, 0), and for mb > 0  Hs = H(ma, mb) + H(ma, -mb) at +mb, Hd = H(ma, mb) - H(ma, -mb) at -mb,
-// so that with Eb(-mb) = conj Eb(mb):  B = H(ma,0) + sum_mb (Hs.re E.re - Hd.im E.im) + i (Hs.im E.re + Hd.re E.im).
-// FP64 form: every entry binary64.  Mixed form: phases, H and B are float-float complex
-// numbers (float4: re hi, re lo, im hi, im lo), B and the per-node contraction are
-// compensated dot products in binary32 (H itself is accumulated in binary64 once per block).
-template <bool MIXED, int NDM>
-__global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d3(const ReqDesc* __restrict__ reqs,
-                                                       const Item* __restrict__ items, double* __restrict__ seg) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ PhiInfo sphi[NDM];
-  const Item it = items[blockIdx.x];
-  const ReqDesc* R = reqs + it.req;
-  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v, vch = R->vchunk;
-  load_phi(sphi, R, nd);
-  __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
-  load_rec_cache(rcache, R);
-
-  const int j = it.sector >> 2, pb = it.sector & 3;
-  const double p1 = (pb & 1) ? -1.0 : 1.0, p2 = (pb & 2) ? -1.0 : 1.0;
+// A line group is the axis j of the Duffy sector and the u node: its four sectors (sign
+// patterns p1, p2 of k~ = u sigma^j(p1 v1, p2 v2, 1)) share H(ma, mb) = sum_mc g(m)
+// e^{2 pi i mc u}, which depends on neither the signs nor v.  It is built once per
+// (request, line group) by hbox_kernel in binary64 and stored folded over mb:
+//   H(ma, 0) at mb = 0,  Hs = H(ma, mb) + H(ma, -mb) at +mb,  Hd = H(ma, mb) - H(ma, -mb) at -mb,
+// as double2 (FP64 form) or float-float complex (mixed form: re hi, re lo, im hi, im lo).
+__global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __restrict__ jobs) {
+  const HboxJob& J = jobs[blockIdx.y];
+  const int G = J.g_lo + (int)blockIdx.x;
+  if (G >= J.g_hi) return;
+  const ReqDesc* R = reqs + J.req;
+  const int nd = R->n_distinct, j = G / R->n_ui, iu = G - j * R->n_ui;
   const int ax_a = j, ax_b = (j + 1) % 3, ax_c = (j + 2) % 3;
-  const double u = R->u_nodes[it.iu];
-  const double wblk = 2.0 * R->u_w[it.iu] * u * u;
   const int Ma = R->M[ax_a], Mb = R->M[ax_b], Mc = R->M[ax_c];
-  const int v2_0 = it.chunk * vch, nv2 = min(vch, nv - v2_0);
+  const double u = R->u_nodes[iu];
   const int st[3] = {R->box[1] * R->box[2], R->box[2], 1};
   const int sta = st[ax_a], stb = st[ax_b], stc = st[ax_c];
   const int gbase = R->M[0] * st[0] + R->M[1] * st[1] + R->M[2] * st[2];
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
-
-  double2* Ea = reinterpret_cast<double2*>(smem_raw);
-  double2* Eb = Ea + (Ma + 1) * nv;
-  double2* Ec = Eb + (Mb + 1) * vch;
-  double2* H = Ec + (Mc + 1);
-  double2* B = H + nd * (Ma + 1) * (2 * Mb + 1);
-  float4* Ea4 = reinterpret_cast<float4*>(Ea);
-  float4* Eb4 = reinterpret_cast<float4*>(Eb);
-  float4* H4 = reinterpret_cast<float4*>(H);
-  float4* B4 = reinterpret_cast<float4*>(B);
-
-  for (int v1 = threadIdx.x; v1 < nv; v1 += blockDim.x) {
+  __shared__ double2 Ec[kMaxBoxM + 1];
+  for (int mc = threadIdx.x; mc <= Mc; mc += blockDim.x) {
     double sn, cs;
-    sincospi(2.0 * (u * (p1 * R->v_nodes[v1])), &sn, &cs);
-    const double2 e1 = make_double2(cs, sn);
-    double2 e = make_double2(1.0, 0.0);
-    for (int ma = 0; ma <= Ma; ++ma) {
-      if (ma) e = cmul(e, e1);
-      if constexpr (MIXED)
-        Ea4[ma * nv + v1] = ff_complex(e);
-      else
-        Ea[ma * nv + v1] = e;
-    }
-  }
-  for (int v2l = threadIdx.x; v2l < nv2; v2l += blockDim.x) {
-    double sn, cs;
-    sincospi(2.0 * (u * (p2 * R->v_nodes[v2_0 + v2l])), &sn, &cs);
-    const double2 e1 = make_double2(cs, sn);
-    double2 e = make_double2(1.0, 0.0);
-    for (int mb = 0; mb <= Mb; ++mb) {
-      if (mb) e = cmul(e, e1);
-      if constexpr (MIXED)
-        Eb4[mb * vch + v2l] = ff_complex(e);
-      else
-        Eb[mb * vch + v2l] = e;
-    }
-  }
-  if (threadIdx.x <= Mc) {
-    double sn, cs;
-    sincospi(2.0 * ((double)threadIdx.x * u), &sn, &cs);
-    if constexpr (MIXED)
-      reinterpret_cast<float4*>(Ec)[threadIdx.x] = ff_complex(make_double2(cs, sn));
-    else
-      Ec[threadIdx.x] = make_double2(cs, sn);
+    sincospi(2.0 * ((double)mc * u), &sn, &cs);
+    Ec[mc] = make_double2(cs, sn);
   }
   __syncthreads();
-
-  // H(ma, +-mb) = sum_mc g(m) e^{2 pi i mc u}, one thread per (jn, ma, mb >= 0), folded
+  const size_t slot = (size_t)(G - J.g_lo) * R->hslot;
   const int nH = (Ma + 1) * (2 * Mb + 1), nHp = (Ma + 1) * (Mb + 1);
-  if constexpr (MIXED) {
-    const float4* Ec4 = reinterpret_cast<const float4*>(Eb4 + (Mb + 1) * vch);
-    for (int e = threadIdx.x; e < nd * nHp; e += blockDim.x) {
-      const int jn = e / nHp, r = e - jn * nHp;
-      const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
-      const float2* gp_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta + mb * stb;
-      const float2* gm_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta - mb * stb;
-      // H(ma, +mb) and H(ma, -mb): real parts pair g(+mc) + g(-mc) with cos, imaginary
-      // parts g(+mc) - g(-mc) with sin
-      float s0 = gp_[0].x, c0 = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
-      const int mc_hp = min(Mc + 1, R->m_hp[ax_c]);
-      for (int mc = 1; mc < mc_hp; ++mc) {
-        const float4 E = Ec4[mc];
-        const float2 a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
-        dot2_acc(s0, c0, a.x, a.y, E.x, E.y);
-        dot2_acc(s0, c0, b.x, b.y, E.x, E.y);
-        dot2_acc(s1, c1, a.x, a.y, E.z, E.w);
-        dot2_acc(s1, c1, -b.x, -b.y, E.z, E.w);
-        dot2_acc(s2, c2, c.x, c.y, E.x, E.y);
-        dot2_acc(s2, c2, dd.x, dd.y, E.x, E.y);
-        dot2_acc(s3, c3, c.x, c.y, E.z, E.w);
-        dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
-      }
-      float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;  // |mc| >= m_hp: below 1e-8, binary32
-      for (int mc = mc_hp; mc <= Mc; ++mc) {
-        const float4 E = Ec4[mc];
-        const float a = gp_[mc * stc].x, b = gp_[-mc * stc].x, c = gm_[mc * stc].x, dd = gm_[-mc * stc].x;
-        q0 = fmaf(a + b, E.x, q0);
-        q1 = fmaf(a - b, E.z, q1);
-        q2 = fmaf(c + dd, E.x, q2);
-        q3 = fmaf(c - dd, E.z, q3);
-      }
-      c0 += q0;
-      c1 += q1;
-      c2 += q2;
-      c3 += q3;
-      const ff pr = ff_two_sum(s0, c0), pi = ff_two_sum(s1, c1), mr = ff_two_sum(s2, c2), mi = ff_two_sum(s3, c3);
-      const int base = jn * nH + ma * (2 * Mb + 1) + Mb;
-      if (mb == 0) {
-        H4[base] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
-      } else {
-        const ff sr = ff_add(pr, mr), si = ff_add(pi, mi);
-        const ff dr = ff_add(pr, ff{-mr.hi, -mr.lo}), di = ff_add(pi, ff{-mi.hi, -mi.lo});
-        H4[base + mb] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
-        H4[base - mb] = make_float4(dr.hi, dr.lo, di.hi, di.lo);
-      }
-    }
-  } else
   for (int e = threadIdx.x; e < nd * nHp; e += blockDim.x) {
     const int jn = e / nHp, r = e - jn * nHp;
     const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
     const double* gp_ = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
     const double* gm_ = R->gbox + (size_t)jn * cells + gbase + ma * sta - mb * stb;
+    // H(ma, +-mb): real parts pair g(+mc) + g(-mc) with cos, imaginary parts the difference with sin
     double pr = gp_[0], pi = 0.0, mr = gm_[0], mi = 0.0;
     for (int mc = 1; mc <= Mc; ++mc) {
       const double2 E = Ec[mc];
@@ -633,60 +536,177 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
       hs = make_double2(pr + mr, pi + mi);
       hd = make_double2(pr - mr, pi - mi);
     }
-    const int base = jn * nH + ma * (2 * Mb + 1) + Mb;
-    if constexpr (MIXED) {
-      H4[base + mb] = ff_complex(hs);
-      if (mb) H4[base - mb] = ff_complex(hd);
+    const size_t base = slot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
+    if (J.outff) {
+      J.outff[base + mb] = ff_complex(hs);
+      if (mb) J.outff[base - mb] = ff_complex(hd);
     } else {
-      H[base + mb] = hs;
-      if (mb) H[base - mb] = hd;
+      J.out[base + mb] = hs;
+      if (mb) J.out[base - mb] = hd;
+    }
+  }
+}
+
+// Far field, d = 3.  Block: the four sectors of one line group and vchunk rows v2, all n_v
+// values of v1.  With the p = +1 phases Ea(ma, v1) = e^{2 pi i ma u v1}, Eb(mb, v2) =
+// e^{2 pi i mb u v2} (p = -1 conjugates them):
+//   B_p2(ma, v2) = X + p2 Y,  X = H(ma, 0) + sum_{mb >= 1} Hs Re Eb,  Y = i sum_{mb >= 1} Hd Im Eb,
+//   Zr_{p1 p2}(v1, v2) = B_p2(0, v2) + 2 (S0 - p1 S1),  S0 = sum_{ma >= 1} Re Ea Re B_p2,
+//   S1 = sum_{ma >= 1} Im Ea Im B_p2,
+// so one pass over mb gives both B of a v2 row and one pass over ma both nodes (p1 = +-1) of
+// a (v1, v2, p2).  Shared memory (16-byte entries): Ea[(Ma+1) n_v], Eb[(Mb+1) vchunk],
+// H[nd (Ma+1) (2Mb+1)] (copied from the line group's slot), B[2][nd (Ma+1) vchunk], then
+// one 8-byte slot per (exponent, thread) holding the real-space part of the p1 = -1 node
+// while the p1 = +1 node runs (registers are the limit of this kernel).
+// FP64 form: every entry binary64.  Mixed form: float-float complex entries; B and the
+// per-node sums are compensated dot products in binary32, |m| >= m_hp in plain binary32.
+template <int NT>
+__device__ __forceinline__ void block_reduce_store2(double (&v)[EZ_MAX_PROD], double (&w)[EZ_MAX_PROD], int np,
+                                                    double scale, double* out_v, double* out_w) {
+  __shared__ double red[NT / 32][2 * EZ_MAX_PROD];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    double x = v[p], y = w[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+      red[wid][p] = x;
+      red[wid][EZ_MAX_PROD + p] = y;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * EZ_MAX_PROD) {
+    double s = 0.0;
+    for (int q = 0; q < NT / 32; ++q) s += red[q][threadIdx.x];
+    const int p = threadIdx.x % EZ_MAX_PROD;
+    if (p < np) (threadIdx.x < EZ_MAX_PROD ? out_v : out_w)[p] = scale * s;
+  }
+  __syncthreads();  // red is reused by the next call
+}
+
+template <bool MIXED, int NDM>
+__global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d3(const ReqDesc* __restrict__ reqs,
+                                                       const Item* __restrict__ items, double* __restrict__ seg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PhiInfo sphi[NDM];
+  const Item it = items[blockIdx.x];
+  const ReqDesc* R = reqs + it.req;
+  const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v, vch = R->vchunk;
+  load_phi(sphi, R, nd);
+  __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
+  load_rec_cache(rcache, R);
+
+  const int j = it.sector >> 2;
+  const int ax_a = j, ax_b = (j + 1) % 3;
+  const double u = R->u_nodes[it.iu];
+  const double wblk = 2.0 * R->u_w[it.iu] * u * u;
+  const int Ma = R->M[ax_a], Mb = R->M[ax_b];
+  const int v2_0 = it.chunk * vch, nv2 = min(vch, nv - v2_0);
+  // segments of the four sectors 4 j + pb (pb = 1: p1 = -1, pb = 2: p2 = -1) of this chunk
+  const long long sstride = (long long)R->n_ui * ((nv + vch - 1) / vch);
+
+  double2* Ea = reinterpret_cast<double2*>(smem_raw);
+  double2* Eb = Ea + (Ma + 1) * nv;
+  double2* H = Eb + (Mb + 1) * vch;
+  const int nH = (Ma + 1) * (2 * Mb + 1);
+  double2* B = H + nd * nH;
+  const int nBs = nd * (Ma + 1) * vch;  // entries of one B_p2
+  float4* Ea4 = reinterpret_cast<float4*>(Ea);
+  float4* Eb4 = reinterpret_cast<float4*>(Eb);
+  float4* H4 = reinterpret_cast<float4*>(H);
+  float4* B4 = reinterpret_cast<float4*>(B);
+  double* zsm = reinterpret_cast<double*>(B + 2 * nBs);  // [nd][256]
+  float2* zsm2 = reinterpret_cast<float2*>(zsm);
+
+  {  // H of the line group: nd nH 16-byte entries, contiguous in its slot
+    const float4* src = reinterpret_cast<const float4*>(MIXED ? (const void*)R->hboxff : (const void*)R->hbox) +
+                        (size_t)(j * R->n_ui + it.iu - R->hg_lo) * R->hslot;
+    for (int e = threadIdx.x; e < nd * nH; e += blockDim.x) H4[e] = __ldg(src + e);
+  }
+  for (int v1 = threadIdx.x; v1 < nv; v1 += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (u * R->v_nodes[v1]), &sn, &cs);
+    const double2 e1 = make_double2(cs, sn);
+    double2 e = make_double2(1.0, 0.0);
+    for (int ma = 0; ma <= Ma; ++ma) {
+      if (ma) e = cmul(e, e1);
+      if constexpr (MIXED)
+        Ea4[ma * nv + v1] = ff_complex(e);
+      else
+        Ea[ma * nv + v1] = e;
+    }
+  }
+  for (int v2l = threadIdx.x; v2l < nv2; v2l += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (u * R->v_nodes[v2_0 + v2l]), &sn, &cs);
+    const double2 e1 = make_double2(cs, sn);
+    double2 e = make_double2(1.0, 0.0);
+    for (int mb = 0; mb <= Mb; ++mb) {
+      if (mb) e = cmul(e, e1);
+      if constexpr (MIXED)
+        Eb4[mb * vch + v2l] = ff_complex(e);
+      else
+        Eb[mb * vch + v2l] = e;
     }
   }
   __syncthreads();
 
-  // B(ma, v2) = H(ma, 0) + sum_{mb >= 1} (Hs E, Hd E) as above
+  // B_{+-}(ma, v2) = X +- Y: one thread per (jn, ma, v2)
   const int nB = (Ma + 1) * nv2;
   for (int e = threadIdx.x; e < nd * nB; e += blockDim.x) {
     const int jn = e / nB, r = e - jn * nB;
     const int ma = r / nv2, v2l = r - ma * nv2;
     const int hb = (jn * (Ma + 1) + ma) * (2 * Mb + 1) + Mb;
+    const int bo = (jn * (Ma + 1) + ma) * vch + v2l;
     if constexpr (MIXED) {
       const float4* h = H4 + hb;
-      float sr = h[0].x, cr = h[0].y, si = h[0].z, ci = h[0].w;
+      float xr = h[0].x, cxr = h[0].y, xi = h[0].z, cxi = h[0].w;
+      float yr = 0.0f, cyr = 0.0f, yi = 0.0f, cyi = 0.0f;
       const int mb_hp = min(Mb + 1, R->m_hp[ax_b]);
       for (int mb = 1; mb < mb_hp; ++mb) {
         const float4 E = Eb4[mb * vch + v2l];
         const float4 hs = h[mb], hd = h[-mb];
-        dot2_acc(sr, cr, hs.x, hs.y, E.x, E.y);
-        dot2_acc(sr, cr, -hd.z, -hd.w, E.z, E.w);
-        dot2_acc(si, ci, hs.z, hs.w, E.x, E.y);
-        dot2_acc(si, ci, hd.x, hd.y, E.z, E.w);
+        dot2_acc(xr, cxr, hs.x, hs.y, E.x, E.y);
+        dot2_acc(yr, cyr, -hd.z, -hd.w, E.z, E.w);
+        dot2_acc(xi, cxi, hs.z, hs.w, E.x, E.y);
+        dot2_acc(yi, cyi, hd.x, hd.y, E.z, E.w);
       }
-      float pr = 0.0f, pi = 0.0f;  // |mb| >= m_hp: binary32
-      for (int mb = mb_hp; mb <= Mb; ++mb) {
+      for (int mb = mb_hp; mb <= Mb; ++mb) {  // below 1e-8: binary32
         const float4 E = Eb4[mb * vch + v2l];
         const float4 hs = h[mb], hd = h[-mb];
-        pr = fmaf(hs.x, E.x, fmaf(-hd.z, E.z, pr));
-        pi = fmaf(hs.z, E.x, fmaf(hd.x, E.z, pi));
+        cxr = fmaf(hs.x, E.x, cxr);
+        cyr = fmaf(-hd.z, E.z, cyr);
+        cxi = fmaf(hs.z, E.x, cxi);
+        cyi = fmaf(hd.x, E.z, cyi);
       }
-      cr += pr;
-      ci += pi;
-      const ff re = ff_two_sum(sr, cr), im = ff_two_sum(si, ci);
-      B4[(jn * (Ma + 1) + ma) * vch + v2l] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      const ff pr = ff_two_sum(xr, yr), pi = ff_two_sum(xi, yi);
+      const ff mr = ff_two_sum(xr, -yr), mi = ff_two_sum(xi, -yi);
+      const ff bpr = ff_fast_two_sum(pr.hi, pr.lo + (cxr + cyr)), bpi = ff_fast_two_sum(pi.hi, pi.lo + (cxi + cyi));
+      const ff bmr = ff_fast_two_sum(mr.hi, mr.lo + (cxr - cyr)), bmi = ff_fast_two_sum(mi.hi, mi.lo + (cxi - cyi));
+      B4[bo] = make_float4(bpr.hi, bpr.lo, bpi.hi, bpi.lo);
+      B4[nBs + bo] = make_float4(bmr.hi, bmr.lo, bmi.hi, bmi.lo);
     } else {
       const double2* h = H + hb;
-      double br = h[0].x, bi = h[0].y;
+      double xr = h[0].x, xi = h[0].y, yr = 0.0, yi = 0.0;
       for (int mb = 1; mb <= Mb; ++mb) {
         const double2 E = Eb[mb * vch + v2l];
         const double2 hs = h[mb], hd = h[-mb];
-        br = fma(hs.x, E.x, fma(-hd.y, E.y, br));
-        bi = fma(hs.y, E.x, fma(hd.x, E.y, bi));
+        xr = fma(hs.x, E.x, xr);
+        yr = fma(-hd.y, E.y, yr);
+        xi = fma(hs.y, E.x, xi);
+        yi = fma(hd.x, E.y, yi);
       }
-      B[(jn * (Ma + 1) + ma) * vch + v2l] = make_double2(br, bi);
+      B[bo] = make_double2(xr + yr, xi + yi);
+      B[nBs + bo] = make_double2(xr - yr, xi - yi);
     }
   }
   __syncthreads();
 
+  const int ax_c = (j + 2) % 3;
   double kca[3], kcb[3], kcc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -694,101 +714,157 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
     kcb[i] = R->AiT[i * 3 + ax_b];
     kcc[i] = R->AiT[i * 3 + ax_c];
   }
-  double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   unsigned terms = 0, coefs = 0;
   const int nn = nv * nv2;
-  if constexpr (MIXED) {
-    // k = alpha v1 + beta v2 + gamma in float-float (alpha = u p1 A^{-T} e_a, ...)
-    ff al[3], be[3], ga[3];
+  for (int s2 = 0; s2 < 2; ++s2) {  // p2 = +1, -1
+    double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0}, wneg[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
+    if constexpr (MIXED) {
+      // k = alpha (p1 v1) + beta v2 + gamma in float-float (alpha = u A^{-T} e_a, beta = p2 u A^{-T} e_b, ...)
+      ff al[3], be[3], ga[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      al[i] = ffd(kca[i] * (u * p1));
-      be[i] = ffd(kcb[i] * (u * p2));
-      ga[i] = ffd(kcc[i] * u);
-    }
-    ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-    const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
-    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-      const int v2l = n / nv, v1 = n - v2l * nv;
-      const float2 a1 = __ldg(R->v_ff + v1), a2 = __ldg(R->v_ff + v2_0 + v2l);
-      const float2 w1 = __ldg(R->vw_ff + v1), w2 = __ldg(R->vw_ff + v2_0 + v2l);
-      const ff x1{a1.x, a1.y}, x2{a2.x, a2.y};
-      ff k[3];
+      for (int i = 0; i < 3; ++i) {
+        al[i] = ffd(kca[i] * u);
+        be[i] = ffd(kcb[i] * (s2 ? -u : u));
+        ga[i] = ffd(kcc[i] * u);
+      }
+      ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      ff wn[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
+      const float4* Bs = B4 + s2 * nBs;
+      for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+        const int v2l = n / nv, v1 = n - v2l * nv;
+        const float2 a1 = __ldg(R->v_ff + v1), a2 = __ldg(R->v_ff + v2_0 + v2l);
+        const float2 w1 = __ldg(R->vw_ff + v1), w2 = __ldg(R->vw_ff + v2_0 + v2l);
+        // S0 and S1 per exponent: two independent compensated chains, interleaved over the exponents
+        ff Zp[NDM], A[NDM];
+        float s0[NDM], c0[NDM], s1[NDM], c1[NDM];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) k[i] = ff_add(ff_add(ff_mul(al[i], x1), ff_mul(be[i], x2)), ga[i]);
-      // sum_{ma >= 1} Re(Ea B) per exponent: two independent compensated chains (real and
-      // imaginary products) per exponent, interleaved over the exponents
-      ff Zr[NDM], A[NDM];
-      float s0[NDM], c0[NDM], s1[NDM], c1[NDM];
+        for (int jn = 0; jn < NDM; ++jn) s0[jn] = c0[jn] = s1[jn] = c1[jn] = 0.0f;
+        const float4* bcol = Bs + v2l;
+        for (int ma = 1; ma < ma_hp; ++ma) {
+          const float4 E = Ea4[ma * nv + v1];
 #pragma unroll
-      for (int jn = 0; jn < NDM; ++jn) s0[jn] = c0[jn] = s1[jn] = c1[jn] = 0.0f;
-      const float4* bcol = B4 + v2l;
-      for (int ma = 1; ma < ma_hp; ++ma) {
-        const float4 E = Ea4[ma * nv + v1];
+          for (int jn = 0; jn < NDM; ++jn)
+            if (jn < nd) {
+              const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
+              dot2_acc(s0[jn], c0[jn], E.x, E.y, bb.x, bb.y);
+              dot2_acc(s1[jn], c1[jn], E.z, E.w, bb.z, bb.w);
+            }
+        }
+        for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
+          const float4 E = Ea4[ma * nv + v1];
+#pragma unroll
+          for (int jn = 0; jn < NDM; ++jn)
+            if (jn < nd) {
+              const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
+              c0[jn] = fmaf(E.x, bb.x, c0[jn]);
+              c1[jn] = fmaf(E.z, bb.z, c1[jn]);
+            }
+        }
 #pragma unroll
         for (int jn = 0; jn < NDM; ++jn)
           if (jn < nd) {
-            const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
-            dot2_acc(s0[jn], c0[jn], E.x, E.y, bb.x, bb.y);
-            dot2_acc(s1[jn], c1[jn], -E.z, -E.w, bb.z, bb.w);
+            const float4 b0 = bcol[jn * (Ma + 1) * vch];
+            const ff tp = ff_two_sum(s0[jn], -s1[jn]), tm = ff_two_sum(s0[jn], s1[jn]);
+            const ff Sp = ff_fast_two_sum(tp.hi, tp.lo + (c0[jn] - c1[jn]));
+            const ff Sm = ff_fast_two_sum(tm.hi, tm.lo + (c0[jn] + c1[jn]));
+            Zp[jn] = ff_add(ff{2.0f * Sp.hi, 2.0f * Sp.lo}, ff{b0.x, b0.y});
+            const ff zm = ff_add(ff{2.0f * Sm.hi, 2.0f * Sm.lo}, ff{b0.x, b0.y});
+            zsm2[jn * 256 + threadIdx.x] = make_float2(zm.hi, zm.lo);
           }
-      }
-      for (int ma = ma_hp; ma <= Ma; ++ma) {  // below 1e-8: binary32
-        const float4 E = Ea4[ma * nv + v1];
+        const ff w = ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y});
+        ff x1{a1.x, a1.y};
+        const ff x2{a2.x, a2.y};
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {  // p1 = +1, then p1 = -1 (x1 and Zp change, ws/wn swap)
+          ff k[3];
 #pragma unroll
-        for (int jn = 0; jn < NDM; ++jn)
+          for (int i = 0; i < 3; ++i) k[i] = ff_add(ff_add(ff_mul(al[i], x1), ff_mul(be[i], x2)), ga[i]);
+          recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
+          assemble_mixed<NDM>(R, nd, np, Zp, A, w, ws);
+          x1 = ff{-x1.hi, -x1.lo};
+#pragma unroll
+          for (int jn = 0; jn < NDM; ++jn)
+            if (jn < nd) {
+              const float2 z = zsm2[jn * 256 + threadIdx.x];
+              Zp[jn] = ff{z.x, z.y};
+            }
+#pragma unroll
+          for (int p = 0; p < EZ_MAX_PROD; ++p) {
+            const ff t = ws[p];
+            ws[p] = wn[p];
+            wn[p] = t;
+          }
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < EZ_MAX_PROD; ++p) {
+        wsum[p] = (double)ws[p].hi + (double)ws[p].lo;
+        wneg[p] = (double)wn[p].hi + (double)wn[p].lo;
+      }
+    } else {
+      const double2* Bs = B + s2 * nBs;
+      for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+        const int v2l = n / nv, v1 = n - v2l * nv;
+        const double kta = u * R->v_nodes[v1];
+        const double ktb = u * (s2 ? -R->v_nodes[v2_0 + v2l] : R->v_nodes[v2_0 + v2l]);
+        const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
+        // k = kb + ka (p1 = +1), then kb - ka
+        double ka[3], kb[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          ka[i] = kca[i] * kta;
+          kb[i] = fma(kcb[i], ktb, kcc[i] * u);
+        }
+        double Zp[NDM];
+#pragma unroll
+        for (int jn = 0; jn < NDM; ++jn) {
+          Zp[jn] = 0.0;
           if (jn < nd) {
-            const float4 bb = bcol[(jn * (Ma + 1) + ma) * vch];
-            c0[jn] = fmaf(E.x, bb.x, fmaf(-E.z, bb.z, c0[jn]));
+            const double2* b = Bs + jn * (Ma + 1) * vch + v2l;
+            double s0 = 0.0, s1 = 0.0;
+            for (int ma = 1; ma <= Ma; ++ma) {
+              const double2 E = Ea[ma * nv + v1];
+              const double2 bb = b[ma * vch];
+              s0 = fma(E.x, bb.x, s0);
+              s1 = fma(E.y, bb.y, s1);
+            }
+            Zp[jn] = fma(2.0, s0 - s1, b[0].x);
+            zsm[jn * 256 + threadIdx.x] = fma(2.0, s0 + s1, b[0].x);
           }
-      }
-#pragma unroll
-      for (int jn = 0; jn < NDM; ++jn)
-        if (jn < nd) {
-          const ff t = ff_two_sum(s0[jn], s1[jn]);
-          const ff S = ff_fast_two_sum(t.hi, t.lo + (c0[jn] + c1[jn]));
-          const float4 b0 = bcol[jn * (Ma + 1) * vch];
-          Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{b0.x, b0.y});
         }
-      recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
-      assemble_mixed<NDM>(R, nd, np, Zr, A, ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y}), ws);
-    }
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {  // p1 = +1, then p1 = -1 (ka and Zp change, wsum/wneg swap)
+          double k[3], acc[NDM], Z[NDM];
 #pragma unroll
-    for (int p = 0; p < EZ_MAX_PROD; ++p) wsum[p] = (double)ws[p].hi + (double)ws[p].lo;
-  } else {
-    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-      const int v2l = n / nv, v1 = n - v2l * nv;
-      const double kta = u * (p1 * R->v_nodes[v1]);
-      const double ktb = u * (p2 * R->v_nodes[v2_0 + v2l]);
-      const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
-      double k[3];
+          for (int i = 0; i < 3; ++i) k[i] = kb[i] + ka[i];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) k[i] = fma(kca[i], kta, fma(kcb[i], ktb, kcc[i] * u));
-      double Z[NDM], acc[NDM];
+          for (int jn = 0; jn < NDM; ++jn) acc[jn] = 0.0;
+          const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
 #pragma unroll
-      for (int jn = 0; jn < NDM; ++jn) {
-        acc[jn] = 0.0;
-        if (jn < nd) {
-          const double2* b = B + jn * (Ma + 1) * vch + v2l;
-          double sr = 0.0;
-          for (int ma = 1; ma <= Ma; ++ma) {
-            const double2 E = Ea[ma * nv + v1];
-            const double2 bb = b[ma * vch];
-            sr = fma(E.x, bb.x, fma(-E.y, bb.y, sr));
+          for (int jn = 0; jn < NDM; ++jn)
+            if (jn < nd) Z[jn] = R->pref[jn] * (Zp[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
+          products<NDM>(R, nd, np, Z, wv, wsum);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) ka[i] = -ka[i];
+#pragma unroll
+          for (int jn = 0; jn < NDM; ++jn)
+            if (jn < nd) Zp[jn] = zsm[jn * 256 + threadIdx.x];
+#pragma unroll
+          for (int p = 0; p < EZ_MAX_PROD; ++p) {
+            const double t = wsum[p];
+            wsum[p] = wneg[p];
+            wneg[p] = t;
           }
-          Z[jn] = fma(2.0, sr, b[0].x);
         }
       }
-      const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-      recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
-#pragma unroll
-      for (int jn = 0; jn < NDM; ++jn)
-        if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
-      products<NDM>(R, nd, np, Z, wv, wsum);
     }
+    double* o = seg + (size_t)it.chunk_seg() * EZ_MAX_PROD;
+    block_reduce_store2<256>(wsum, wneg, np, wblk, o + (size_t)(2 * s2) * sstride * EZ_MAX_PROD,
+                             o + (size_t)(2 * s2 + 1) * sstride * EZ_MAX_PROD);
   }
   count_work(R, terms, coefs);
-  block_reduce_store<256>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
 // ------------------------------------------------------------------------- d = 2
