@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <array>
@@ -276,6 +277,126 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   for (int n = 0; n < kNSer; ++n) ff_split(P.ser[n], P.ser_ff[n].x, P.ser_ff[n].y);
   ff_split(P.gam, P.gam_ff.x, P.gam_ff.y);
   P.a_f = (float)a;
+  // series lengths: sum_{n >= N} |ser_n| t^n (the terms n >= kNSer add < 1e-18 at t = kT0,
+  // bounded by the next one) is increasing in t; breakpoint = largest t <= kT0 (bisection,
+  // rounded down to binary32) where it is <= tol.  They depend on a alone: computed once
+  // per 2a and kept (planning runs for every served request).
+  struct SerBrk {
+    float brk[6], brk_ff[6];
+    int n1[7];
+  };
+  static std::mutex brk_mu;
+  static std::map<int, SerBrk> brk_cache;
+  {
+    std::lock_guard<std::mutex> lk(brk_mu);
+    auto it = brk_cache.find(P.two_a);
+    if (it != brk_cache.end()) {
+      std::memcpy(P.ser_brk, it->second.brk, sizeof P.ser_brk);
+      std::memcpy(P.ser_brk_ff, it->second.brk_ff, sizeof P.ser_brk_ff);
+      std::memcpy(P.ser_n1, it->second.n1, sizeof P.ser_n1);
+      return;
+    }
+  }
+  auto tail = [&](int n0, int n1, double t) {
+    double s = 0.0, tn = std::pow(t, n0);
+    for (int n = n0; n < n1; ++n, tn *= t) s += std::fabs(P.ser[n]) * tn;
+    return s;
+  };
+  auto brk = [&](int N, double tol) {
+    double lo = 0.0, hi = kT0;
+    if (tail(N, kNSer, hi) + std::fabs(P.ser[kNSer - 1]) * std::pow(hi, kNSer) <= tol) return (float)hi;
+    for (int it = 0; it < 48; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (tail(N, kNSer, mid) + std::fabs(P.ser[kNSer - 1]) * std::pow(mid, kNSer) <= tol)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return std::nextafter((float)lo, 0.0f);
+  };
+  for (int i = 0; i < 6; ++i) {
+    P.ser_brk[i] = brk(4 + 2 * i, std::ldexp(1.0, -55));
+    P.ser_brk_ff[i] = brk(4 + 2 * i, std::ldexp(1.0, -50));
+  }
+  for (int i = 0; i < 7; ++i) {
+    const int N = i < 6 ? 4 + 2 * i : kNSer;
+    const double tmax = i < 6 ? (double)P.ser_brk_ff[i] : kT0;
+    int n1 = N;
+    while (n1 > 1 && tail(n1 - 1, N, tmax) <= std::ldexp(1.0, -30)) --n1;
+    P.ser_n1[i] = n1;
+  }
+  SerBrk e;
+  std::memcpy(e.brk, P.ser_brk, sizeof e.brk);
+  std::memcpy(e.brk_ff, P.ser_brk_ff, sizeof e.brk_ff);
+  std::memcpy(e.n1, P.ser_n1, sizeof e.n1);
+  std::lock_guard<std::mutex> lk(brk_mu);
+  brk_cache[P.two_a] = e;
+}
+
+// Mixed form, per order a (cached: planning runs for every served request).
+// Last grid points t = kT0 + 0.25 i (t <= 64) with |Phi_a(t)| t > 1e-7 and with |Phi_a(t)| > 1e-6.
+struct MixScan {
+  double bad_mix, bad_mid;
+};
+const MixScan& mix_scan(int two_a) {
+  static std::mutex mu;
+  static std::map<int, MixScan> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(two_a);
+  if (it != cache.end()) return it->second;
+  const double a = 0.5 * two_a;
+  MixScan m{kT0, kT0};
+  for (int i = 0; kT0 + 0.25 * i <= 64.0; ++i) {
+    const double t = kT0 + 0.25 * i;
+    const double f = std::fabs(phi_accurate(a, t));
+    if (f * t > 1e-7) m.bad_mix = t;
+    if (f > 1e-6) m.bad_mid = t;
+  }
+  return cache[two_a] = m;
+}
+
+// Tail fit of order a beyond t_mix: g(s) = t e^t Phi_a(t), s = t_mix/t in (0, 1], Chebyshev
+// interpolation at 24 points in x = 2s - 1, truncated to degree 7 and rewritten in powers of s.
+struct TailFit {
+  float c[8];
+};
+const TailFit& tail_fit(int two_a, float tmix_f) {
+  static std::mutex mu;
+  static std::map<std::pair<int, float>, TailFit> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({two_a, tmix_f});
+  if (it != cache.end()) return it->second;
+  const double a = 0.5 * two_a, tmix = tmix_f;
+  const int N = 24;
+  double gv[N], cc[N];
+  for (int k = 0; k < N; ++k) {
+    const double xk = std::cos(kPi * (k + 0.5) / N);
+    const double sk = 0.5 * (xk + 1.0);
+    gv[k] = phi_scaled_large(a, tmix / sk);
+  }
+  for (int q = 0; q < N; ++q) {
+    double acc = 0.0;
+    for (int k = 0; k < N; ++k) acc += gv[k] * std::cos(kPi * q * (k + 0.5) / N);
+    cc[q] = (q == 0 ? 1.0 : 2.0) * acc / N;
+  }
+  // sum_{q<8} cc[q] T_q(2s - 1) -> powers of s
+  double Tm[8][8] = {{0}};  // Tm[q][i]: coefficient of s^i in T_q(2s - 1)
+  Tm[0][0] = 1.0;
+  Tm[1][0] = -1.0;
+  Tm[1][1] = 2.0;
+  for (int q = 2; q < 8; ++q)
+    for (int i = 0; i < 8; ++i) {
+      double v = -Tm[q - 2][i] - 2.0 * Tm[q - 1][i];
+      if (i > 0) v += 4.0 * Tm[q - 1][i - 1];
+      Tm[q][i] = v;
+    }
+  TailFit f;
+  for (int i = 0; i < 8; ++i) {
+    double v = 0.0;
+    for (int q = i; q < 8; ++q) v += cc[q] * Tm[q][i];
+    f.c[i] = (float)v;
+  }
+  return cache[{two_a, tmix_f}] = f;
 }
 
 // regularised h = 0 series (lambda piece of the log case included)
@@ -421,24 +542,29 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
           }
           dmin2 = std::min(dmin2, r2);
         }
+    double ref[EZ_MAX_NU];
+    for (int j = 0; j < spec.n_distinct; ++j) ref[j] = std::fabs(phi_accurate(0.5 * spec.nu[j], kPi * dmin2 / (p.lam * p.lam)));
     for (int i = 0; i < 3; ++i) {
       p.m_hp[i] = p.M[i] + 1;
       if (i >= d) continue;
       double rn = 0.0;
       for (int j = 0; j < d; ++j) rn += L->Ai[i * d + j] * L->Ai[i * d + j];
-      for (int m = 1; m <= p.M[i]; ++m) {
-        bool small = true;
-        for (int j = 0; j < spec.n_distinct && small; ++j) {
-          const double a = 0.5 * spec.nu[j];
-          const double ref = std::fabs(phi_accurate(a, kPi * dmin2 / (p.lam * p.lam)));
-          const double tail = std::fabs(phi_accurate(a, kPi * (m * m / rn) / (p.lam * p.lam)));
-          small = tail <= 1e-8 * ref;
-        }
-        if (small) {
-          p.m_hp[i] = m;
-          break;
-        }
+      // smallest m <= M with every |Phi(pi m^2 / (rn lam^2))| <= 1e-8 ref (monotone in m: Phi decreases)
+      auto small = [&](int m) {
+        for (int j = 0; j < spec.n_distinct; ++j)
+          if (std::fabs(phi_accurate(0.5 * spec.nu[j], kPi * (m * m / rn) / (p.lam * p.lam))) > 1e-8 * ref[j])
+            return false;
+        return true;
+      };
+      int lo = 0, hi = p.M[i] + 1;  // small(hi) taken as true, small(lo) false
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (small(mid))
+          hi = mid;
+        else
+          lo = mid;
       }
+      p.m_hp[i] = hi;
     }
   }
   p.real_tab = p.cells * spec.n_distinct >= 4096;
@@ -512,51 +638,20 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.prec == EZ_MIXED) {
     double tmix = kT0, tmid = kT0;
     for (int j = 0; j < spec.n_distinct; ++j) {
-      const double a = p.phi[j].a;
-      double bad_mix = kT0, bad_mid = kT0;
-      for (double t = kT0; t <= p.phi[j].t_hi; t += 0.25) {
-        const double f = std::fabs(phi_accurate(a, t));
-        if (f * t > 1e-7) bad_mix = t;
-        if (f > 1e-6) bad_mid = t;
-      }
-      tmix = std::max(tmix, bad_mix + 0.25);
-      tmid = std::max(tmid, bad_mid + 0.25);
+      // the last grid points t = kT0 + 0.25 i with |Phi_a(t)| t > 1e-7 and |Phi_a(t)| > 1e-6:
+      // Phi_a decreases, so within [kT0, t_hi] they are the uncapped ones capped at t_hi
+      const MixScan& ms = mix_scan(p.phi[j].two_a);
+      const double t_last = kT0 + 0.25 * std::floor((p.phi[j].t_hi - kT0) / 0.25 + 1e-9);
+      tmix = std::max(tmix, std::min(ms.bad_mix, t_last) + 0.25);
+      tmid = std::max(tmid, std::min(ms.bad_mid, t_last) + 0.25);
     }
     tmid = std::min(tmid, tmix);
     tmix = (double)(float)tmix;
     for (int j = 0; j < spec.n_distinct; ++j) {
       p.phi[j].t_mix_f = (float)tmix;
       p.phi[j].t_mid_f = (float)tmid;
-      // tail fit: g(s) = t e^t Phi_a(t), s = tmix/t in (0, 1], Chebyshev interpolation at
-      // 24 points in x = 2s - 1, truncated to degree 7 and rewritten in powers of s
-      const int N = 24;
-      double gv[N], cc[N];
-      for (int k = 0; k < N; ++k) {
-        const double xk = std::cos(kPi * (k + 0.5) / N);
-        const double sk = 0.5 * (xk + 1.0);
-        gv[k] = phi_scaled_large(p.phi[j].a, tmix / sk);
-      }
-      for (int q = 0; q < N; ++q) {
-        double acc = 0.0;
-        for (int k = 0; k < N; ++k) acc += gv[k] * std::cos(kPi * q * (k + 0.5) / N);
-        cc[q] = (q == 0 ? 1.0 : 2.0) * acc / N;
-      }
-      // sum_{q<8} cc[q] T_q(2s - 1) -> powers of s
-      double Tm[8][8] = {{0}};  // Tm[q][i]: coefficient of s^i in T_q(2s - 1)
-      Tm[0][0] = 1.0;
-      Tm[1][0] = -1.0;
-      Tm[1][1] = 2.0;
-      for (int q = 2; q < 8; ++q)
-        for (int i = 0; i < 8; ++i) {
-          double v = -Tm[q - 2][i] - 2.0 * Tm[q - 1][i];
-          if (i > 0) v += 4.0 * Tm[q - 1][i - 1];
-          Tm[q][i] = v;
-        }
-      for (int i = 0; i < 8; ++i) {
-        double v = 0.0;
-        for (int q = i; q < 8; ++q) v += cc[q] * Tm[q][i];
-        p.phi[j].tail_p[i] = (float)v;
-      }
+      const TailFit& tf = tail_fit(p.phi[j].two_a, (float)tmix);
+      for (int i = 0; i < 8; ++i) p.phi[j].tail_p[i] = tf.c[i];
     }
   } else {
     for (int j = 0; j < spec.n_distinct; ++j) p.phi[j].t_mix_f = p.phi[j].t_mid_f = 3.0e38f;

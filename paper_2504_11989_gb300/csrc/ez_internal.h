@@ -20,6 +20,9 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 //   o = -t_mid/h so that x = fma(|q|^2, s, o) with t = c |q|^2, one pad slot, then
 //   b_0 .. b_{kNC-1} (monomials in x; b_j = 0 for j >= n).  n is the shortest length whose Chebyshev
 //   tail is below max(2^-53 max|Phi|, 1e-19) on the interval: 1 (a constant), 4, 8, 12 or 16.
+//   The float-float copy (kRecFF floats: n, J, s hi/lo, m hi/lo, 0, 0, then (hi, lo) pairs)
+//   also holds J (even, 2 <= J <= n): the coefficients j >= J sum to <= 2^-30 min|Phi| on the
+//   interval and are evaluated in binary32.
 // t < kT0: series of the entire part plus the singular term.
 // t > t_hi: asymptotic expansion e^{-t}/t (1 + (a-1)/t + (a-1)(a-2)/t^2 + ...).
 // ---------------------------------------------------------------------------
@@ -63,6 +66,14 @@ struct PhiInfo {
   float2 gam_ff;
   float a_f;             // a in binary32 (exact: a is a small half-integer)
   float pad_f;
+  // t < kT0: below ser_brk[i] the series needs only N = 4 + 2 i terms (i < 6; N = kNSer
+  // above ser_brk[5]): the dropped terms sum to <= 2^-55 (binary64 form) or <= 2^-50
+  // (ser_brk_ff, float-float form) in absolute value.  Float-float form on interval i:
+  // the terms n >= ser_n1[i] sum to <= 2^-30 and are evaluated in binary32.
+  float ser_brk[6];
+  float ser_brk_ff[6];
+  int ser_n1[7];
+  int pad_i;
 };
 
 // ---------------------------------------------------------------------------

@@ -135,6 +135,13 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
   }
 }
 
+// 1/x to ~1 ulp for normal x > 0 (one MUFU operation; binary32 tail and middle-range terms)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Mixed form, binary32 tail term for every exponent: Phi_a(t) = e^{-t} t^{-1} P_a(t_mix/t).
 // With an order chain (orders a_j = a_0 - j) only the lowest order uses its fit; the others
 // follow upward from t Phi_{a+1} = a Phi_a + e^{-t} (stable for t > t_mix > |a|).
@@ -189,9 +196,17 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, boo
         hs[j] = ff_add(hs[j], prev);
         continue;
       }
-      ff p{P.ser_ff[kNSer - 1].x, P.ser_ff[kNSer - 1].y};
+      // N = 4 + 2 iv terms (the rest below 2^-50); n >= N1 in binary32
+      int iv = 0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) iv += t.hi >= P.ser_brk_ff[q] ? 1 : 0;
+      const int N = 4 + 2 * iv, N1 = P.ser_n1[iv];
+      float pf = 0.0f;
 #pragma unroll 1
-      for (int n = kNSer - 2; n >= 0; --n) p = ff_add(ff_mul(p, t), ff{P.ser_ff[n].x, P.ser_ff[n].y});
+      for (int n = N - 1; n >= N1; --n) pf = fmaf(pf, t.hi, P.ser_ff[n].x);
+      ff p{pf, 0.0f};
+#pragma unroll 1
+      for (int n = N1 - 1; n >= 0; --n) p = ff_add(ff_mul(p, t), ff{P.ser_ff[n].x, P.ser_ff[n].y});
       const ff gam{P.gam_ff.x, P.gam_ff.y};
       if (P.log_m >= 0) {
         ff tm{1.0f, 0.0f};
@@ -212,7 +227,7 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, boo
       }
       prev = p;
       hs[j] = ff_add(hs[j], p);
-      coefs += kNSer;
+      coefs += N;
     }
 }
 
@@ -276,7 +291,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     if (qqf > R2f) continue;
     const float tf = cf * qqf;
     if (tf >= tmix) {
-      const float r = __frcp_rn(tf), E = __expf(-tf), sv = tmix * r;
+      const float r = rcp_approx(tf), E = __expf(-tf), sv = tmix * r;
       tails_f<NDM>(sphi, nd, chain, E, r, sv, st);
       continue;
     }
@@ -330,7 +345,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       // descending j = ascending order; with a chain only the two lowest orders use the
       // table, the others follow from t Phi_{a+1} = a Phi_a + e^{-t}
       float prev = 0.0f, Ef = 0.0f;
-      const float rt = chain ? __frcp_rn(tf) : 0.0f;
+      const float rt = chain ? rcp_approx(tf) : 0.0f;
 #pragma unroll
       for (int j = NDM - 1; j >= 0; --j)
         if (j < nd) {
@@ -395,7 +410,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     }
     if (qqf > R2f) continue;  // outside the cutoff (neighbouring nodes mostly agree: little divergence)
     const float tf = cf * qqf;
-    const float r = __frcp_rn(tf), sv = tmix * r;
+    const float r = rcp_approx(tf), sv = tmix * r;
     tails_f<NDM>(sphi, nd, chain, __expf(-tf), r, sv, st);
   }
 #pragma unroll
@@ -456,9 +471,9 @@ size_t far_smem_bytes(int d, int nd, const int* M, int n_v, int vchunk) {
   int Mx = 0;
   for (int i = 0; i < d; ++i) Mx = M[i] > Mx ? M[i] : Mx;
   size_t n = 0;
-  if (d == 3)  // Ea, Eb, H, B_{+-}, and 8 bytes per (exponent, thread) for the p1 = -1 node
+  if (d == 3)  // Ea, Eb, H, B_{+-}, 8 bytes per (exponent, thread) for the p1 = -1 node, k parts
     n = (size_t)(Mx + 1) * n_v + (size_t)(Mx + 1) * vchunk + (size_t)nd * (Mx + 1) * (2 * Mx + 1) +
-        2 * (size_t)nd * (Mx + 1) * vchunk + (size_t)nd * 128;
+        2 * (size_t)nd * (Mx + 1) * vchunk + (size_t)nd * 128 + ((size_t)(n_v + 2 * vchunk) * 24 + 15) / 16;
   else if (d == 2)
     n = (size_t)(Mx + 1) + (size_t)nd * (Mx + 1);
   return n * sizeof(double2);
@@ -557,7 +572,9 @@ __global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __r
 // a (v1, v2, p2).  Shared memory (16-byte entries): Ea[(Ma+1) n_v], Eb[(Mb+1) vchunk],
 // H[nd (Ma+1) (2Mb+1)] (copied from the line group's slot), B[2][nd (Ma+1) vchunk], then
 // one 8-byte slot per (exponent, thread) holding the real-space part of the p1 = -1 node
-// while the p1 = +1 node runs (registers are the limit of this kernel).
+// while the p1 = +1 node runs (registers are the limit of this kernel), and (mixed form)
+// the float-float parts of k = p1 kA(v1) + kB_p2(v2): kA = u v1 A^{-T} e_a,
+// kB = p2 u v2 A^{-T} e_b + u A^{-T} e_c.
 // FP64 form: every entry binary64.  Mixed form: float-float complex entries; B and the
 // per-node sums are compensated dot products in binary32, |m| >= m_hp in plain binary32.
 template <int NT>
@@ -621,6 +638,8 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   float4* B4 = reinterpret_cast<float4*>(B);
   double* zsm = reinterpret_cast<double*>(B + 2 * nBs);  // [nd][256]
   float2* zsm2 = reinterpret_cast<float2*>(zsm);
+  float2* kA = reinterpret_cast<float2*>(zsm + nd * 256);  // [n_v][3]
+  float2* kB = kA + 3 * nv;                                 // [2][vchunk][3]
 
   {  // H of the line group: nd nH 16-byte entries, contiguous in its slot
     const float4* src = reinterpret_cast<const float4*>(MIXED ? (const void*)R->hboxff : (const void*)R->hbox) +
@@ -651,6 +670,28 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         Eb4[mb * vch + v2l] = ff_complex(e);
       else
         Eb[mb * vch + v2l] = e;
+    }
+  }
+  if constexpr (MIXED) {
+    const int ax_c = (j + 2) % 3;
+    for (int e = threadIdx.x; e < nv + 2 * nv2; e += blockDim.x) {
+      if (e < nv) {
+        const float2 a1 = __ldg(R->v_ff + e);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const ff t = ff_mul(ffd(R->AiT[i * 3 + ax_a] * u), ff{a1.x, a1.y});
+          kA[e * 3 + i] = make_float2(t.hi, t.lo);
+        }
+      } else {
+        const int q = e - nv, s2 = q / nv2, v2l = q - s2 * nv2;
+        const float2 a2 = __ldg(R->v_ff + v2_0 + v2l);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const ff t = ff_add(ff_mul(ffd(R->AiT[i * 3 + ax_b] * (s2 ? -u : u)), ff{a2.x, a2.y}),
+                              ffd(R->AiT[i * 3 + ax_c] * u));
+          kB[(s2 * vch + v2l) * 3 + i] = make_float2(t.hi, t.lo);
+        }
+      }
     }
   }
   __syncthreads();
@@ -719,21 +760,12 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   for (int s2 = 0; s2 < 2; ++s2) {  // p2 = +1, -1
     double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0}, wneg[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
     if constexpr (MIXED) {
-      // k = alpha (p1 v1) + beta v2 + gamma in float-float (alpha = u A^{-T} e_a, beta = p2 u A^{-T} e_b, ...)
-      ff al[3], be[3], ga[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        al[i] = ffd(kca[i] * u);
-        be[i] = ffd(kcb[i] * (s2 ? -u : u));
-        ga[i] = ffd(kcc[i] * u);
-      }
       ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       ff wn[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
       const float4* Bs = B4 + s2 * nBs;
       for (int n = threadIdx.x; n < nn; n += blockDim.x) {
         const int v2l = n / nv, v1 = n - v2l * nv;
-        const float2 a1 = __ldg(R->v_ff + v1), a2 = __ldg(R->v_ff + v2_0 + v2l);
         const float2 w1 = __ldg(R->vw_ff + v1), w2 = __ldg(R->vw_ff + v2_0 + v2l);
         // S0 and S1 per exponent: two independent compensated chains, interleaved over the exponents
         ff Zp[NDM], A[NDM];
@@ -773,16 +805,22 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
             zsm2[jn * 256 + threadIdx.x] = make_float2(zm.hi, zm.lo);
           }
         const ff w = ff_mul(ff{w1.x, w1.y}, ff{w2.x, w2.y});
-        ff x1{a1.x, a1.y};
-        const ff x2{a2.x, a2.y};
+        ff ka[3], kb[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float2 a = kA[v1 * 3 + i], b = kB[(s2 * vch + v2l) * 3 + i];
+          ka[i] = ff{a.x, a.y};
+          kb[i] = ff{b.x, b.y};
+        }
 #pragma unroll 1
-        for (int q = 0; q < 2; ++q) {  // p1 = +1, then p1 = -1 (x1 and Zp change, ws/wn swap)
+        for (int q = 0; q < 2; ++q) {  // p1 = +1, then p1 = -1 (ka and Zp change, ws/wn swap)
           ff k[3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) k[i] = ff_add(ff_add(ff_mul(al[i], x1), ff_mul(be[i], x2)), ga[i]);
+          for (int i = 0; i < 3; ++i) k[i] = ff_add(kb[i], ka[i]);
           recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
           assemble_mixed<NDM>(R, nd, np, Zp, A, w, ws);
-          x1 = ff{-x1.hi, -x1.lo};
+#pragma unroll
+          for (int i = 0; i < 3; ++i) ka[i] = ff{-ka[i].hi, -ka[i].lo};
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) {

@@ -169,9 +169,13 @@ __device__ __forceinline__ double phi_poly(const double* r, double x, int& n_use
 }
 
 static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
-  double s = P.ser[kNSer - 1];
-#pragma unroll 4
-  for (int k = kNSer - 2; k >= 0; --k) s = fma(s, t, P.ser[k]);
+  const float tf = (float)t;
+  int N = 4;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) N += tf >= P.ser_brk[i] ? 2 : 0;
+  double s = P.ser[N - 1];
+#pragma unroll 1
+  for (int k = N - 2; k >= 0; --k) s = fma(s, t, P.ser[k]);
   if (t == 0.0) return P.log_m >= 0 ? (P.log_m == 0 ? CUDART_INF : s) : (P.a < 0.0 ? s : CUDART_INF);
   if (P.log_m >= 0) {
     double tm = 1.0;
@@ -239,13 +243,23 @@ __device__ __forceinline__ float phi_poly_f(const float* r, float xf) {
 
 // mixed form, heads: Horner scheme in float-float on the float-float record r (coefficient
 // pairs (hi, lo), two per 16-byte load); n_used: coefficients evaluated
+// The coefficients j >= J (J even, from the record) are small enough for binary32 with x.hi;
+// the scheme continues in float-float below J.
 __device__ __forceinline__ ff phi_poly_ff(const float* r, ff x, int& n_used) {
-  const int n = __ldg(reinterpret_cast<const int*>(r));
-  n_used = n;
+  const int2 nj = __ldg(reinterpret_cast<const int2*>(r));  // (n, J)
+  n_used = nj.x;
   const float4* c4 = reinterpret_cast<const float4*>(r + 8);
-  int blk = (n >> 1) - 1;
-  float4 c = __ldg(c4 + blk);  // (b_{2 blk}, b_{2 blk + 1})
-  ff p = ff_add(ff_mul(ff{c.z, c.w}, x), ff{c.x, c.y});
+  int blk = (nj.x >> 1) - 1;
+  const int blk_ff = (nj.y >> 1) - 1;
+  float pf = 0.0f;
+#pragma unroll 1
+  for (; blk > blk_ff; --blk) {
+    const float4 c = __ldg(c4 + blk);  // (b_{2 blk}, b_{2 blk + 1})
+    pf = fmaf(fmaf(pf, x.hi, c.z), x.hi, c.x);
+  }
+  float4 c = __ldg(c4 + blk);
+  ff p = ff_add(ff_mul(ff{pf, 0.0f}, x), ff{c.z, c.w});
+  p = ff_add(ff_mul(p, x), ff{c.x, c.y});
 #pragma unroll 1
   for (--blk; blk >= 0; --blk) {
     c = __ldg(c4 + blk);

@@ -225,9 +225,28 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
   if (J.outff) {
     float* rff = J.outff + (size_t)iv * kRecFF;
     ff_split(bff, rff[8 + 2 * k], rff[9 + 2 * k]);
+    // J: the coefficients j >= J (x in [-1, 1]) sum to <= 2^-30 min|Phi| on the interval
+    __shared__ double babs[kNC];
+    __shared__ int jsplit;
+    babs[k] = fabs(bff);
+    __syncthreads();
+    if (k == 0) {
+      double fmn = fabs(f[0]);
+      for (int q = 1; q < kNC; ++q) fmn = fmin(fmn, fabs(f[q]));
+      const double thr = ldexp(fmn, -30);
+      int Jc = nff, Jb = nff;
+      double tl = 0.0;
+      for (Jc = nff - 2; Jc >= 2; Jc -= 2) {
+        tl += babs[Jc] + babs[Jc + 1];
+        if (tl > thr) break;
+        Jb = Jc;
+      }
+      jsplit = Jb;
+    }
+    __syncthreads();
     if (k == 0) {
       reinterpret_cast<int*>(rff)[0] = nff;
-      rff[1] = 0.0f;
+      reinterpret_cast<int*>(rff)[1] = jsplit;
       ff_split(J.c_lam / h, rff[2], rff[3]);
       ff_split(tm / J.c_lam, rff[4], rff[5]);
       rff[6] = rff[7] = 0.0f;
@@ -270,7 +289,7 @@ __global__ void phicopy_kernel(const PhiCopyJob* jobs) {
     J.outff[off + 2 * k + 1] = J.srcff[off + 2 * k + 1];
   } else if (k == 0) {
     reinterpret_cast<int*>(J.outff + off)[0] = reinterpret_cast<const int*>(J.srcff + off)[0];
-    J.outff[off + 1] = 0.0f;
+    reinterpret_cast<int*>(J.outff + off)[1] = reinterpret_cast<const int*>(J.srcff + off)[1];
     ff_split(J.c_lam / h, J.outff[off + 2], J.outff[off + 3]);
     ff_split(tm / J.c_lam, J.outff[off + 4], J.outff[off + 5]);
     J.outff[off + 6] = J.outff[off + 7] = 0.0f;
