@@ -683,8 +683,8 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
 
   // segments.  d = 3: a far-field block takes the four sectors of a line group (axis j,
   // u node) and vchunk rows v2 of them; its 256 threads run n_v * rows nodes per sign p2.
-  // vchunk is the largest count whose shared memory fits two blocks per SM (100 KB dynamic
-  // + the static reciprocal-list cache and tables, <= 12 KB) that maximises (busy thread slots) x
+  // vchunk is the largest count whose shared memory fits two blocks per SM (98 KB dynamic
+  // + the static reciprocal-list cache and tables, <= 14 KB) that maximises (busy thread slots) x
   // (busy block slots of the last wave, 304 = two blocks per SM of the GPU) for the sum.
   p.vchunk = 1;
   if (d == 3) {
@@ -693,7 +693,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     p.vchunk = std::min(p.n_v, kVChunkMin);
     for (int c = p.n_v; c >= 1; --c) {
       if (c < kVChunkMin && c < p.n_v) break;
-      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 100 * 1024) continue;
+      if (far_smem_bytes(d, spec.n_distinct, p.M, p.n_v, c) > 98 * 1024) continue;
       const int nch = (p.n_v + c - 1) / c;
       double work = 0.0, slots = 0.0;
       for (int k = 0; k < nch; ++k) {

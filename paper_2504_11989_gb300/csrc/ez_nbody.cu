@@ -67,20 +67,114 @@ __device__ __forceinline__ void load_phi(PhiInfo* sphi, const ReqDesc* R, int nd
 // Mixed form: the first kRecCache points of the |G|-sorted reciprocal list, staged in
 // shared memory once per block: every node of the block walks the list in the same order,
 // so each load is a broadcast from shared memory.
+// FP64 form, d = 3, >= 4 exponents: the points of the list that can lie within the cutoff for
+// some node of the block (a candidate list, in list order, built per block and sign p2 by
+// rec_candidates; measured faster there, slower for one exponent and in the mixed form, whose
+// walk already stops at the |G| bound of the node).  n = -1 (FP64) or n = n_rec (mixed) walks
+// the whole list.
 constexpr int kRecCache = 256;
-struct RecCacheF64 {};  // the FP64 form reads the list through the read-only cache (measured faster)
+struct RecCacheF64 {  // the FP64 form reads the points through the read-only cache (measured faster)
+  int idx[kRecCache];
+  int n;
+};
 struct RecCacheMix {
   float4 f[kRecCache];   // binary32 hi parts and |G|^2
   float4 lo[kRecCache];  // low parts of the float-float G
+  int idx[kRecCache];    // list index of entry i
+  int n;                 // entries to walk (entries >= kRecCache are list entries, read from global)
 };
 
-__device__ __forceinline__ void load_rec_cache(RecCacheF64&, const ReqDesc*) {}
+__device__ __forceinline__ void load_rec_cache(RecCacheF64& c, const ReqDesc*) {
+  if (threadIdx.x == 0) c.n = -1;
+}
 __device__ __forceinline__ void load_rec_cache(RecCacheMix& c, const ReqDesc* R) {
   const int n = min(R->n_rec, kRecCache);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     c.f[i] = __ldg(R->recf + i);
     c.lo[i] = __ldg(R->reclo + i);
+    c.idx[i] = i;
   }
+  if (threadIdx.x == 0) c.n = R->n_rec;
+}
+
+// min over alpha in [-1, 1], beta in [b0, b1] of |w + alpha da + beta db|^2: the stationary
+// point if it is inside, else the minimum over the four edges (each a clamped 1-D problem)
+__device__ __forceinline__ double para_dist2(const double* w, const double* da, const double* db, double b0,
+                                             double b1) {
+  const double aa = da[0] * da[0] + da[1] * da[1] + da[2] * da[2];
+  const double ab = da[0] * db[0] + da[1] * db[1] + da[2] * db[2];
+  const double bb = db[0] * db[0] + db[1] * db[1] + db[2] * db[2];
+  const double wa = w[0] * da[0] + w[1] * da[1] + w[2] * da[2];
+  const double wb = w[0] * db[0] + w[1] * db[1] + w[2] * db[2];
+  const double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  auto q = [&](double al, double be) { return ww + 2.0 * (al * wa + be * wb) + al * al * aa + 2.0 * al * be * ab + be * be * bb; };
+  double best = 1e300;
+  const double det = aa * bb - ab * ab;
+  if (det > 0.0) {
+    const double al = (-wa * bb + wb * ab) / det, be = (-wb * aa + wa * ab) / det;
+    if (al >= -1.0 && al <= 1.0 && be >= b0 && be <= b1) best = q(al, be);
+  }
+  for (int e = 0; e < 2; ++e) {
+    const double al = e ? 1.0 : -1.0;  // edges alpha = -+1
+    const double be = bb > 0.0 ? fmin(fmax(-(wb + al * ab) / bb, b0), b1) : b0;
+    best = fmin(best, q(al, be));
+    const double bf = e ? b1 : b0;  // edges beta = b0, b1
+    const double a2 = aa > 0.0 ? fmin(fmax(-(wa + bf * ab) / aa, -1.0), 1.0) : 0.0;
+    best = fmin(best, q(a2, bf));
+  }
+  return fmax(best, 0.0);
+}
+
+// Candidate list of the block: list points G with |G + k| <= r_recip (1 + 1e-5) for some
+// k = c0 + alpha da + beta db, alpha in [-1, 1], beta in [b0, b1] (every node of the block at
+// one sign p2; the margin is far above the binary32 rounding of the per-node cutoff test, so
+// the nodes skip exactly the points they would have skipped in the whole list).  Kept in list
+// order; more than kRecCache candidates fall back to the whole list.  Call with every thread.
+template <class RC>
+__device__ __noinline__ void rec_candidates(RC& rc, const ReqDesc* R, const double* c0, const double* da, const double* db,
+                               double b0, double b1) {
+  __shared__ int s_cnt[8], s_total;
+  constexpr bool kMix = std::is_same<RC, RecCacheMix>::value;
+  const int nrec = R->n_rec, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double r2m = R->R2_recip * (1.0 + 2e-5);
+  if (threadIdx.x == 0) s_total = 0;
+  __syncthreads();
+  for (int base = 0; base < nrec; base += 256) {
+    const int h = base + (int)threadIdx.x;
+    bool in = false;
+    if (h < nrec) {
+      const G4 G = ldg_g4(R->rec + h);
+      const double w[3] = {G.x + c0[0], G.y + c0[1], G.z + c0[2]};
+      in = para_dist2(w, da, db, b0, b1) <= r2m;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) s_cnt[wid] = __popc(m);
+    __syncthreads();
+    int off = s_total;
+    for (int q = 0; q < wid; ++q) off += s_cnt[q];
+    off += __popc(m & ((1u << lane) - 1u));
+    if (in && off < kRecCache) {
+      rc.idx[off] = h;
+      if constexpr (kMix) {
+        rc.f[off] = __ldg(R->recf + h);
+        rc.lo[off] = __ldg(R->reclo + h);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 8; ++q) s_total += s_cnt[q];
+    __syncthreads();
+  }
+  if (s_total > kRecCache) {
+    if constexpr (kMix) {
+      load_rec_cache(rc, R);
+    } else if (threadIdx.x == 0) {
+      rc.n = -1;
+    }
+  } else if (threadIdx.x == 0) {
+    rc.n = s_total;
+  }
+  __syncthreads();
 }
 
 // reciprocal sum at k (x = 0), FP64 form: acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over
@@ -90,8 +184,9 @@ __device__ __forceinline__ void load_rec_cache(RecCacheMix& c, const ReqDesc* R)
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs,
-                                          const RecCacheF64&) {
-  const int nrec = R->n_rec;
+                                          const RecCacheF64& rc) {
+  const bool list = rc.n >= 0;
+  const int nrec = list ? rc.n : R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const G4* rec = R->rec;
   const float4* recf = R->recf;
@@ -104,7 +199,8 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
     k2v[i] = 2.0 * k[i];
     kk2 = fma(k[i], k[i], kk2);
   }
-  for (int h = 0; h < nrec; ++h) {
+  for (int hh = 0; hh < nrec; ++hh) {
+    const int h = list ? rc.idx[hh] : hh;
     const float4 Gf = __ldg(recf + h);
     float qqf;
     if (D == 1) {
@@ -243,7 +339,7 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, boo
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
                                                 ff* A, unsigned& terms, unsigned& coefs, const RecCacheMix& rc) {
-  const int nrec = R->n_rec;
+  const int nrec = rc.n;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
   const float t_hi = sphi[0].t_hi_f, t_geo = sphi[0].t_geo_end_f;
@@ -308,7 +404,7 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       }
     }
     if (tf < (float)kT0 || tf > t_hi) {  // rare: t = 0, or beyond the table: binary64
-      const G4 G = ldg_g4(R->rec + h);
+      const G4 G = ldg_g4(R->rec + (h < kRecCache ? rc.idx[h] : h));
       const double q0 = G.x + ((double)kf[0] + (double)klo[0]);
       double qq = q0 * q0;
       if (D >= 2) {
@@ -615,7 +711,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   const int nd = R->n_distinct, np = R->n_prod, nv = R->n_v, vch = R->vchunk;
   load_phi(sphi, R, nd);
   __shared__ typename std::conditional<MIXED, RecCacheMix, RecCacheF64>::type rcache;
-  load_rec_cache(rcache, R);
+  if constexpr (MIXED || NDM < 4) load_rec_cache(rcache, R);  // the whole list (else candidates per pass)
 
   const int j = it.sector >> 2;
   const int ax_a = j, ax_b = (j + 1) % 3;
@@ -758,6 +854,21 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   unsigned terms = 0, coefs = 0;
   const int nn = nv * nv2;
   for (int s2 = 0; s2 < 2; ++s2) {  // p2 = +1, -1
+    if constexpr (!MIXED && NDM >= 4) {  // candidates: k = u A^{-T} (alpha e_a + p2 beta e_b + e_c), alpha = p1 v1, beta = v2
+      double c0[3], da[3], db[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        c0[i] = kcc[i] * u;
+        da[i] = kca[i] * u;
+        db[i] = kcb[i] * (s2 ? -u : u);
+      }
+      double b0 = R->v_nodes[v2_0], b1 = b0;
+      for (int q = 1; q < nv2; ++q) {
+        b0 = fmin(b0, R->v_nodes[v2_0 + q]);
+        b1 = fmax(b1, R->v_nodes[v2_0 + q]);
+      }
+      rec_candidates(rcache, R, c0, da, db, b0, b1);
+    }
     double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0}, wneg[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
     if constexpr (MIXED) {
       ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
