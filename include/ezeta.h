@@ -64,7 +64,7 @@ typedef struct {
   double eps;     /* split point of the near part (default 1e-2, Sec. 4.1) */
   int ell;        /* Taylor order 2*ell of Z^reg in the near part (default 4, Sec. 4.1) */
   double lambda;  /* splitting parameter of the incomplete-gamma form; 0 = default: 2 V (d = 1),
-                     3 V^{1/2} (d = 2), 4 V^{1/3} (d = 3, EZ_FP64) or 3.5 V^{1/3} (d = 3, EZ_MIXED),
+                     3 V^{1/2} (d = 2), 4.5 V^{1/3} (d = 3, EZ_FP64) or 4 V^{1/3} (d = 3, EZ_MIXED),
                      lowered if needed so that the real-space box half-width stays <= 16.  The sum
                      does not depend on it (Crandall's formula, Sec. 2); ez_epstein_zeta uses V^{1/d} */
   double r_real;  /* real-space cutoff |z| <= r_real (default sqrt(T/pi) lambda, T = 45 for

@@ -488,14 +488,15 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.prec != EZ_FP64 && p.prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", q.prec);
   // default splitting parameter (the result does not depend on lam): the separable
   // real-space contraction costs O(M) per node, the reciprocal sum O(terms).  Measured
-  // optima on GB300: lam = 2 V for d = 1, 3 V^{1/2} for d = 2, in 3-D 4 V^{1/3} for the FP64
-  // form and 3.5 V^{1/3} for the mixed form, whose reciprocal tails are cheap binary32 work;
-  // capped so that the real-space box half-width stays <= 16
+  // optima on GB300: lam = 2 V for d = 1, 3 V^{1/2} for d = 2; in 3-D the FP64 form is
+  // fastest at the largest lam whose real-space box half-width stays <= 16 (4.5 V^{1/3},
+  // capped), the mixed form at 4 V^{1/3} (its reciprocal tails are cheap binary32 work);
+  // every default is capped so that the box half-width stays <= 16
   const double tcut = p.prec == EZ_MIXED ? kTcutMixed : kTcut;
   if (q.lambda > 0.0) {
     p.lam = q.lambda;
   } else {
-    const double f = d == 1 ? 2.0 : d == 2 ? 3.0 : (p.prec == EZ_MIXED ? 3.5 : 4.0);
+    const double f = d == 1 ? 2.0 : d == 2 ? 3.0 : (p.prec == EZ_MIXED ? 4.0 : 4.5);
     double amax = 0.0;
     for (int i = 0; i < d; ++i) {
       double rn = 0.0;
