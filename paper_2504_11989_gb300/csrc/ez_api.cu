@@ -833,7 +833,15 @@ int init_constants() {
   if (kNC > 1) c[1][1] = 1.0;
   for (int j = 2; j < kNC; ++j)
     for (int i = 0; i < kNC; ++i) c[j][i] = (i > 0 ? 2.0 * c[j - 1][i - 1] : 0.0) - c[j - 2][i];
-  EZ_CUDA(upload_cheb2mono(&c[0][0]));
+  // cosine table of the Chebyshev transform and the Chebyshev points, rounded from
+  // long double
+  double dct[kNC][kNC], xk[kNC];
+  for (int k = 0; k < kNC; ++k) {
+    xk[k] = (double)std::cos(3.14159265358979323846264338327950288L * (k + 0.5L) / kNC);
+    for (int q = 0; q < kNC; ++q)
+      dct[k][q] = (double)std::cos(3.14159265358979323846264338327950288L * k * (q + 0.5L) / kNC);
+  }
+  EZ_CUDA(upload_cheb2mono(&c[0][0], &dct[0][0], xk));
   EZ_CUDA(far_set_smem_limits());
   EZ_CUDA(upload_inv_int());
   g_init = true;
@@ -1378,7 +1386,7 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   int max_int = 0, max_int_copy = 0;
   for (auto& m : B.phi_master) max_int = std::max(max_int, phi_slot(B.plans[m.first], m.second).n_int);
   for (auto& c : B.phi_copy) max_int_copy = std::max(max_int_copy, phi_slot(B.plans[c[0]], c[1]).n_int);
-  phitab_kernel<<<dim3(max_int, B.n_phi), kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
+  phitab_kernel<<<dim3((max_int + kPhiIv - 1) / kPhiIv, B.n_phi), kPhiIv * kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
   EZ_LAUNCHED();
   if (B.n_pcopy) {
     phicopy_kernel<<<dim3((max_int_copy * kRec + 127) / 128, B.n_pcopy), 128, 0, stream>>>(
@@ -1392,10 +1400,17 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   EZ_LAUNCHED();
   {
     long long max_groups = 0;
+    int max_tasks = 0;
     for (auto& p : B.plans)
-      if (p.d == 3) max_groups = std::max(max_groups, p.line_hi - p.line_lo);
+      if (p.d == 3) {
+        max_groups = std::max(max_groups, p.line_hi - p.line_lo);
+        int Mx = 0;
+        for (int i = 0; i < 3; ++i) Mx = std::max(Mx, p.M[i]);
+        max_tasks = std::max(max_tasks, p.spec.n_distinct * (Mx + 1) * (Mx + 1));
+      }
     if (max_groups > 0) {
-      hbox_kernel<<<dim3((unsigned)max_groups, B.n_req), 128, 0, stream>>>(dreqs, (const HboxJob*)dptr(B.o_hj));
+      hbox_kernel<<<dim3((unsigned)max_groups, B.n_req, (unsigned)((max_tasks + 255) / 256)), 256, 0, stream>>>(
+          dreqs, (const HboxJob*)dptr(B.o_hj));
       EZ_LAUNCHED();
     }
   }
@@ -1838,7 +1853,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   gbox_kernel<<<dim3((unsigned)((p.cells + 255) / 256), 1), 256, 0, stream>>>((const ReqDesc*)(D + o_req),
                                                                               (const GboxJob*)(D + o_gj), 1);
   EZ_LAUNCHED();
-  phitab_kernel<<<dim3(p.phi[0].n_int, 1), kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
+  phitab_kernel<<<dim3((p.phi[0].n_int + kPhiIv - 1) / kPhiIv, 1), kPhiIv * kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
   EZ_LAUNCHED();
   EpsteinArgs A;
   std::memset(&A, 0, sizeof A);
@@ -2049,7 +2064,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   gbox_kernel<<<dim3((unsigned)((p.cells + 255) / 256), 1), 256, 0, stream>>>((const ReqDesc*)(D + o_req),
                                                                               (const GboxJob*)(D + o_gj), 1);
   EZ_LAUNCHED();
-  phitab_kernel<<<dim3(p.phi[0].n_int, 1), kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
+  phitab_kernel<<<dim3((p.phi[0].n_int + kPhiIv - 1) / kPhiIv, 1), kPhiIv * kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
   EZ_LAUNCHED();
   EpsteinArgs A;
   std::memset(&A, 0, sizeof A);

@@ -121,6 +121,9 @@ __global__ void epstein_kernel(EpsteinArgs args);
 __global__ void phase_kernel(const PhaseJob* jobs);
 
 size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v, int vchunk);
-cudaError_t upload_cheb2mono(const double* host_matrix);  // kNC x kNC
+// Chebyshev -> monomial matrix (kNC x kNC), cosine table of the transform (kNC x kNC),
+// Chebyshev points (kNC)
+cudaError_t upload_cheb2mono(const double* host_matrix, const double* dct, const double* xk);
+constexpr int kPhiIv = 8;  // phitab_kernel: intervals per block
 
 }  // namespace ez

@@ -599,9 +599,11 @@ __device__ __forceinline__ float4 ff_complex(double2 z) {
 // A line group is the axis j of the Duffy sector and the u node: its four sectors (sign
 // patterns p1, p2 of k~ = u sigma^j(p1 v1, p2 v2, 1)) share H(ma, mb) = sum_mc g(m)
 // e^{2 pi i mc u}, which depends on neither the signs nor v.  It is built once per
-// (request, line group) by hbox_kernel in binary64 and stored folded over mb:
+// (request, line group) by hbox_kernel and stored folded over mb:
 //   H(ma, 0) at mb = 0,  Hs = H(ma, mb) + H(ma, -mb) at +mb,  Hd = H(ma, mb) - H(ma, -mb) at -mb,
-// as double2 (FP64 form) or float-float complex (mixed form: re hi, re lo, im hi, im lo).
+// as double2 summed in binary64 (FP64 form) or as float-float complex (mixed form: re hi,
+// re lo, im hi, im lo) from compensated binary32 dot products.
+// Grid: (line group, job, chunk of 256 tasks (jn, ma, mb >= 0)), one task per thread.
 __global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __restrict__ jobs) {
   const HboxJob& J = jobs[blockIdx.y];
   const int G = J.g_lo + (int)blockIdx.x;
@@ -616,15 +618,62 @@ __global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __r
   const int gbase = R->M[0] * st[0] + R->M[1] * st[1] + R->M[2] * st[2];
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
   __shared__ double2 Ec[kMaxBoxM + 1];
+  __shared__ float4 Ec4[kMaxBoxM + 1];
   for (int mc = threadIdx.x; mc <= Mc; mc += blockDim.x) {
     double sn, cs;
     sincospi(2.0 * ((double)mc * u), &sn, &cs);
     Ec[mc] = make_double2(cs, sn);
+    Ec4[mc] = ff_complex(Ec[mc]);
   }
   __syncthreads();
   const size_t slot = (size_t)(G - J.g_lo) * R->hslot;
   const int nH = (Ma + 1) * (2 * Mb + 1), nHp = (Ma + 1) * (Mb + 1);
-  for (int e = threadIdx.x; e < nd * nHp; e += blockDim.x) {
+  if (J.outff) {
+    // mixed form: compensated dot products in binary32 on the float-float box (the FP64 pipe
+    // is 64 times slower per operation); |mc| >= m_hp (below 1e-8) in plain binary32
+    for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < nd * nHp; e += gridDim.z * blockDim.x) {
+      const int jn = e / nHp, r = e - jn * nHp;
+      const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
+      const float2* gp_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta + mb * stb;
+      const float2* gm_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta - mb * stb;
+      float s0 = gp_[0].x, c0 = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
+      const int mc_hp = min(Mc + 1, R->m_hp[ax_c]);
+      for (int mc = 1; mc < mc_hp; ++mc) {
+        const float4 E = Ec4[mc];
+        const float2 a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
+        dot2_acc(s0, c0, a.x, a.y, E.x, E.y);
+        dot2_acc(s0, c0, b.x, b.y, E.x, E.y);
+        dot2_acc(s1, c1, a.x, a.y, E.z, E.w);
+        dot2_acc(s1, c1, -b.x, -b.y, E.z, E.w);
+        dot2_acc(s2, c2, c.x, c.y, E.x, E.y);
+        dot2_acc(s2, c2, dd.x, dd.y, E.x, E.y);
+        dot2_acc(s3, c3, c.x, c.y, E.z, E.w);
+        dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
+      }
+      float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;
+      for (int mc = mc_hp; mc <= Mc; ++mc) {
+        const float4 E = Ec4[mc];
+        const float a = gp_[mc * stc].x, b = gp_[-mc * stc].x, c = gm_[mc * stc].x, dd = gm_[-mc * stc].x;
+        q0 = fmaf(a + b, E.x, q0);
+        q1 = fmaf(a - b, E.z, q1);
+        q2 = fmaf(c + dd, E.x, q2);
+        q3 = fmaf(c - dd, E.z, q3);
+      }
+      const ff pr = ff_two_sum(s0, c0 + q0), pi = ff_two_sum(s1, c1 + q1);
+      const ff mr = ff_two_sum(s2, c2 + q2), mi = ff_two_sum(s3, c3 + q3);
+      const size_t base = slot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
+      if (mb == 0) {
+        J.outff[base] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+      } else {
+        const ff sr = ff_add(pr, mr), si = ff_add(pi, mi);
+        const ff dr = ff_add(pr, ff{-mr.hi, -mr.lo}), di = ff_add(pi, ff{-mi.hi, -mi.lo});
+        J.outff[base + mb] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+        J.outff[base - mb] = make_float4(dr.hi, dr.lo, di.hi, di.lo);
+      }
+    }
+    return;
+  }
+  for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < nd * nHp; e += gridDim.z * blockDim.x) {
     const int jn = e / nHp, r = e - jn * nHp;
     const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
     const double* gp_ = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
@@ -648,13 +697,8 @@ __global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __r
       hd = make_double2(pr - mr, pi - mi);
     }
     const size_t base = slot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
-    if (J.outff) {
-      J.outff[base + mb] = ff_complex(hs);
-      if (mb) J.outff[base - mb] = ff_complex(hd);
-    } else {
-      J.out[base + mb] = hs;
-      if (mb) J.out[base - mb] = hd;
-    }
+    J.out[base + mb] = hs;
+    if (mb) J.out[base - mb] = hd;
   }
 }
 

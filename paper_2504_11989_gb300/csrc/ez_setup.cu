@@ -149,13 +149,22 @@ __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs
 }
 
 // ---------------------------------------------------------------------------
-// Phi_a tables: one block of kNC threads per (request, distinct nu, interval).
+// Phi_a tables: kNC threads per (distinct a, interval), kPhiIv intervals per block.
 // Chebyshev interpolation at the kNC Chebyshev points of the interval, then
-// conversion to monomials in x in [-1, 1] (matrix in constant memory).
+// conversion to monomials in x in [-1, 1].  The cosine table of the transform, the
+// Chebyshev points and the conversion matrix are uploaded once (constant memory) and
+// staged in shared memory per block.
 // ---------------------------------------------------------------------------
 __constant__ double c_cheb2mono[kNC * kNC];  // [j][i]: coefficient of x^i in T_j(x)
+__constant__ double c_dct[kNC * kNC];        // [k][q]: cos(pi k (q + 1/2) / kNC)
+__constant__ double c_cheb_x[kNC];           // cos(pi (k + 1/2) / kNC)
 
-cudaError_t upload_cheb2mono(const double* m) { return cudaMemcpyToSymbol(c_cheb2mono, m, sizeof(double) * kNC * kNC); }
+cudaError_t upload_cheb2mono(const double* m, const double* dct, const double* xk) {
+  cudaError_t e = cudaMemcpyToSymbol(c_cheb2mono, m, sizeof(double) * kNC * kNC);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dct, dct, sizeof(double) * kNC * kNC);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cheb_x, xk, sizeof(double) * kNC);
+  return e;
+}
 
 // midpoint and half-width of interpolation interval iv (geometric, then unit width)
 __device__ __forceinline__ void phi_interval_bounds(int iv, double t_geo_end, double& tm, double& h) {
@@ -171,23 +180,28 @@ __device__ __forceinline__ void phi_interval_bounds(int iv, double t_geo_end, do
   h = 0.5 * (hi - lo);
 }
 
-__global__ void phitab_kernel(const PhiJob* jobs) {
+__global__ void __launch_bounds__(kPhiIv * kNC) phitab_kernel(const PhiJob* jobs) {
   const PhiJob J = jobs[blockIdx.y];
-  const int iv = blockIdx.x;
-  if (iv >= J.n_int) return;
-  double tm, h;
-  phi_interval_bounds(iv, J.t_geo_end, tm, h);
-  __shared__ double f[kNC], cj[kNC];
-  __shared__ int nkeep;
-  const int k = threadIdx.x;
-  const double xk = cospi((k + 0.5) / kNC);
-  f[k] = phi_accurate(J.a, tm + h * xk);
+  __shared__ double sdct[kNC * kNC], sc2m[kNC * kNC];
+  for (int i = threadIdx.x; i < kNC * kNC; i += blockDim.x) {
+    sdct[i] = c_dct[i];
+    sc2m[i] = c_cheb2mono[i];
+  }
+  const int sub = threadIdx.x / kNC, k = threadIdx.x - sub * kNC;
+  const int iv = blockIdx.x * kPhiIv + sub;
+  const bool live = iv < J.n_int;  // every thread reaches the barriers
+  double tm = 0.0, h = 1.0;
+  if (live) phi_interval_bounds(iv, J.t_geo_end, tm, h);
+  __shared__ double fs[kPhiIv][kNC], cjs[kPhiIv][kNC], babs[kPhiIv][kNC];
+  __shared__ int nkeep[kPhiIv], nkeep_f[kPhiIv], nkeep_ff[kPhiIv], jsplit[kPhiIv];
+  double* f = fs[sub];
+  double* cj = cjs[sub];
+  f[k] = live ? phi_accurate(J.a, tm + h * c_cheb_x[k]) : 0.0;
   __syncthreads();
   double s = 0.0;
-  for (int q = 0; q < kNC; ++q) s += f[q] * cospi((double)k * (q + 0.5) / kNC);
+  for (int q = 0; q < kNC; ++q) s += f[q] * sdct[k * kNC + q];
   cj[k] = (k == 0 ? 1.0 : 2.0) * s / kNC;
   __syncthreads();
-  __shared__ int nkeep_f, nkeep_ff;
   if (k == 0) {
     // shortest length n in {4, 8, 12, 16} whose Chebyshev tail is below the tolerance:
     // binary64 table max(2^-53 max|Phi|, 1e-19), binary32 table 2^-26 max|Phi|
@@ -209,44 +223,41 @@ __global__ void phitab_kernel(const PhiJob* jobs) {
     double tail1 = 0.0;
     for (int q = 1; q < kNC; ++q) tail1 += fabs(cj[q]);
     if (tail1 <= tol) n = 1;
-    nkeep = n;
-    nkeep_f = nf;
-    nkeep_ff = nff;
+    nkeep[sub] = n;
+    nkeep_f[sub] = nf;
+    nkeep_ff[sub] = nff;
   }
   __syncthreads();
-  const int n = nkeep, nf = nkeep_f, nff = nkeep_ff;
+  const int n = nkeep[sub], nf = nkeep_f[sub], nff = nkeep_ff[sub];
   double b = 0.0, bf = 0.0, bff = 0.0;
-  if (k < n)
-    for (int j = k; j < n; ++j) b += cj[j] * c_cheb2mono[j * kNC + k];
-  if (k < nf)
-    for (int j = k; j < nf; ++j) bf += cj[j] * c_cheb2mono[j * kNC + k];
-  if (k < nff)
-    for (int j = k; j < nff; ++j) bff += cj[j] * c_cheb2mono[j * kNC + k];
+  for (int j = k; j < n; ++j) b += cj[j] * sc2m[j * kNC + k];
+  for (int j = k; j < nf; ++j) bf += cj[j] * sc2m[j * kNC + k];
+  for (int j = k; j < nff; ++j) bff += cj[j] * sc2m[j * kNC + k];
+  // J (float-float records): the coefficients j >= J (x in [-1, 1]) sum to <= 2^-30
+  // min|Phi| on the interval
+  babs[sub][k] = fabs(bff);
+  __syncthreads();
+  if (k == 0) {
+    double fmn = fabs(f[0]);
+    for (int q = 1; q < kNC; ++q) fmn = fmin(fmn, fabs(f[q]));
+    const double thr = ldexp(fmn, -30);
+    int Jb = nff;
+    double tl = 0.0;
+    for (int Jc = nff - 2; Jc >= 2; Jc -= 2) {
+      tl += babs[sub][Jc] + babs[sub][Jc + 1];
+      if (tl > thr) break;
+      Jb = Jc;
+    }
+    jsplit[sub] = Jb;
+  }
+  __syncthreads();
+  if (!live) return;
   if (J.outff) {
     float* rff = J.outff + (size_t)iv * kRecFF;
     ff_split(bff, rff[8 + 2 * k], rff[9 + 2 * k]);
-    // J: the coefficients j >= J (x in [-1, 1]) sum to <= 2^-30 min|Phi| on the interval
-    __shared__ double babs[kNC];
-    __shared__ int jsplit;
-    babs[k] = fabs(bff);
-    __syncthreads();
-    if (k == 0) {
-      double fmn = fabs(f[0]);
-      for (int q = 1; q < kNC; ++q) fmn = fmin(fmn, fabs(f[q]));
-      const double thr = ldexp(fmn, -30);
-      int Jc = nff, Jb = nff;
-      double tl = 0.0;
-      for (Jc = nff - 2; Jc >= 2; Jc -= 2) {
-        tl += babs[Jc] + babs[Jc + 1];
-        if (tl > thr) break;
-        Jb = Jc;
-      }
-      jsplit = Jb;
-    }
-    __syncthreads();
     if (k == 0) {
       reinterpret_cast<int*>(rff)[0] = nff;
-      reinterpret_cast<int*>(rff)[1] = jsplit;
+      reinterpret_cast<int*>(rff)[1] = jsplit[sub];
       ff_split(J.c_lam / h, rff[2], rff[3]);
       ff_split(tm / J.c_lam, rff[4], rff[5]);
       rff[6] = rff[7] = 0.0f;
@@ -346,33 +357,43 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_real_kernel(const ReqDe
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
   const long long c0 = cells / 2 + 1 + (long long)blockIdx.x * kTaylorCells;
   const int nc = (int)min((long long)kTaylorCells, cells - c0);
-  const int c = threadIdx.x;
-  if (c < kTaylorCells) {
-    double z[3] = {0.0, 0.0, 0.0};
-    bool live = false;
-    if (c < nc) {
-      const long long idx = c0 + c;
-      live = R->gbox[idx] != 0.0;  // outside the ball (the same for every exponent)
-      long long cc = idx;
-      int m[3];
-      m[2] = (int)(cc % R->box[2]) - R->M[2];
-      cc /= R->box[2];
-      m[1] = (int)(cc % R->box[1]) - R->M[1];
-      cc /= R->box[1];
-      m[0] = (int)cc - R->M[0];
-      for (int i = 0; i < d; ++i) {
-        double zi = 0.0;
-        for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
-        z[i] = zi;
-      }
-      for (int jn = 0; jn < nd; ++jn) gv[jn][c] = live ? R->gbox[(size_t)jn * cells + idx] : 0.0;
-    } else {
-      for (int jn = 0; jn < nd; ++jn) gv[jn][c] = 0.0;
+  // the cells inside the ball (g != 0, the same for every exponent), compacted in cell order:
+  // skipping g = 0 leaves every sum bitwise unchanged
+  const int c = threadIdx.x, lane = c & 31, wid = c >> 5;
+  __shared__ int s_live[kTaylorThreads / 32];
+  double z[3] = {0.0, 0.0, 0.0};
+  bool live = false;
+  long long idx = 0;
+  if (c < nc) {
+    idx = c0 + c;
+    live = R->gbox[idx] != 0.0;
+  }
+  const unsigned lm = __ballot_sync(0xffffffffu, live);
+  if (lane == 0) s_live[wid] = __popc(lm);
+  __syncthreads();
+  int pos = __popc(lm & ((1u << lane) - 1u)), nlive = 0;
+  for (int w = 0; w < kTaylorThreads / 32; ++w) {
+    if (w < wid) pos += s_live[w];
+    nlive += s_live[w];
+  }
+  if (live) {
+    long long cc = idx;
+    int m[3];
+    m[2] = (int)(cc % R->box[2]) - R->M[2];
+    cc /= R->box[2];
+    m[1] = (int)(cc % R->box[1]) - R->M[1];
+    cc /= R->box[1];
+    m[0] = (int)cc - R->M[0];
+    for (int i = 0; i < d; ++i) {
+      double zi = 0.0;
+      for (int k = 0; k < d; ++k) zi = fma(R->A[i * d + k], (double)m[k], zi);
+      z[i] = zi;
     }
+    for (int jn = 0; jn < nd; ++jn) gv[jn][pos] = R->gbox[(size_t)jn * cells + idx];
     for (int i = 0; i < 3; ++i) {
       double p = 1.0;
       for (int e = 0; e < ne; ++e) {
-        pw[i][e][c] = p;
+        pw[i][e][pos] = p;
         p *= z[i];
       }
     }
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_real_kernel(const ReqDe
     double acc[EZ_MAX_NU];
 #pragma unroll
     for (int jn = 0; jn < EZ_MAX_NU; ++jn) acc[jn] = 0.0;
-    for (int q = 0; q < nc; ++q) {
+    for (int q = 0; q < nlive; ++q) {
       const double mono = pw[0][a0][q] * pw[1][a1][q] * pw[2][a2][q];
 #pragma unroll
       for (int jn = 0; jn < EZ_MAX_NU; ++jn)
