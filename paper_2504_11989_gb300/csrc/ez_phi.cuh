@@ -209,6 +209,10 @@ __device__ __forceinline__ double phi_eval_qq(const PhiInfo& P, double qq, float
   const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
   const double* r = P.tab + (size_t)i * kRec;
   const double2 so = __ldg(reinterpret_cast<const double2*>(r) + 0);  // (n|pad, s) -- s in .y
+  if (__double2loint(so.x) == 1) {  // constant record: no argument, no Horner scheme
+    n_used = 0;
+    return __ldg(r + 4);
+  }
   const double o = __ldg(r + 2);
   return phi_poly(r, fma(qq, so.y, o), n_used);
 }
