@@ -1104,7 +1104,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   B.o_seg = dl.take(sizeof(double) * EZ_MAX_PROD * std::max<long long>(n_seg, 1));
   B.o_lines = dl.take(sizeof(double) * EZ_MAX_PROD * n_lines);
   B.o_out = dl.take(sizeof(double) * EZ_MAX_PROD * n_req);
-  B.o_work = dl.take(sizeof(unsigned long long) * 2 * n_req);
+  B.o_work = dl.take(sizeof(unsigned long long) * 3 * n_req);
 
   if (!fill) {
     B.dbytes = dl.off;
@@ -1174,7 +1174,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.recf = (const float4*)dptr(o_recf[r]);
     R.reclo = (const float4*)dptr(o_reclo[r]);
     R.R2f = (float)(p.r_recip * p.r_recip);
-    R.work = (unsigned long long*)dptr(B.o_work) + 2 * r;
+    R.work = (unsigned long long*)dptr(B.o_work) + 3 * r;
     R.c_lam_f = (float)R.c_lam;
     ff_split(R.c_lam, R.c_lam_ff.x, R.c_lam_ff.y);
     R.order_chain = p.spec.n_distinct >= 3;
@@ -1372,7 +1372,7 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   char* D = B.d;
   auto dptr = [&](size_t o) { return (void*)(D + o); };
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[0], stream));
-  EZ_CUDA(cudaMemsetAsync(dptr(B.o_work), 0, sizeof(unsigned long long) * 2 * B.n_req, stream));
+  EZ_CUDA(cudaMemsetAsync(dptr(B.o_work), 0, sizeof(unsigned long long) * 3 * B.n_req, stream));
   ReqDesc* dreqs = (ReqDesc*)dptr(B.o_req);
   enum_recip_kernel<<<B.n_req, 512, 0, stream>>>(dreqs, (const RecipJob*)dptr(B.o_rj));
   EZ_LAUNCHED();
@@ -1549,7 +1549,7 @@ extern "C" int ez_batch_timing(ez_batch B, int enable, float* far_ms, float* tot
 // plus the per-node and per-block real-space and bookkeeping costs of the design.
 extern "C" int ez_batch_far_flops(ez_batch B, double* flops, long long* terms, long long* coefs) {
   if (!B || !B->ran) return fail(EZ_EINVAL, "batch has not run");
-  std::vector<unsigned long long> w(2 * B->n_req);
+  std::vector<unsigned long long> w(3 * B->n_req);
   EZ_CUDA(cudaMemcpy(w.data(), B->d + B->o_work, sizeof(unsigned long long) * w.size(), cudaMemcpyDeviceToHost));
   double total = 0.0;
   long long nt = 0, nc = 0;
@@ -1559,10 +1559,12 @@ extern "C" int ez_batch_far_flops(ez_batch B, double* flops, long long* terms, l
     int nfac = 0;
     for (int pr = 0; pr < p.spec.n_prod; ++pr)
       for (int j = 0; j < nd; ++j) nfac += p.spec.expo[pr][j];
-    const double t = (double)w[2 * r], c = (double)w[2 * r + 1];
-    nt += (long long)w[2 * r];
-    nc += (long long)w[2 * r + 1];
-    double per_term = (3.0 * d - 1.0) * t + 2.0 * c + 1.0 * t * nd;
+    const double t = (double)w[3 * r], c = (double)w[3 * r + 1], qt = (double)w[3 * r + 2];
+    nt += (long long)w[3 * r];
+    nc += (long long)w[3 * r + 1];
+    // |G + k|^2 (3d - 1 flops) where it was formed, 2 flops per coefficient (argument and
+    // Horner steps), one accumulation per term and order
+    double per_term = (3.0 * d - 1.0) * qt + 2.0 * c + 1.0 * t * nd;
     double nodes = (double)p.nsect * p.n_ui * (d == 1 ? 1 : (d == 2 ? p.n_v : (double)p.n_v * p.n_v));
     double per_node = 2.0 * d * d + 4.0 * nd + nfac + 2.0;  // k, assembly, products, weight
     double blocks = 0.0, per_block = 0.0;

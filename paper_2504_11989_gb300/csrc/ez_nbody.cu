@@ -44,16 +44,20 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[EZ_MAX_PROD], int
 }
 
 // adds the block's work counts to the request's counters (one atomic per warp)
-__device__ __forceinline__ void count_work(const ReqDesc* R, unsigned terms, unsigned coefs) {
-  unsigned long long t = terms, c = coefs;
+// work[0]: in-range reciprocal terms, work[1]: polynomial coefficients evaluated,
+// work[2]: terms whose |G + k|^2 was formed (the FP64 form skips it for constant records)
+__device__ __forceinline__ void count_work(const ReqDesc* R, unsigned terms, unsigned coefs, unsigned qterms) {
+  unsigned long long t = terms, c = coefs, q = qterms;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     t += __shfl_down_sync(0xffffffffu, t, o);
     c += __shfl_down_sync(0xffffffffu, c, o);
+    q += __shfl_down_sync(0xffffffffu, q, o);
   }
   if ((threadIdx.x & 31) == 0 && R->work) {
     atomicAdd(R->work, t);
     atomicAdd(R->work + 1, c);
+    atomicAdd(R->work + 2, q);
   }
 }
 
@@ -184,7 +188,7 @@ __device__ __noinline__ void rec_candidates(RC& rc, const ReqDesc* R, const doub
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs,
-                                          const RecCacheF64& rc) {
+                                          unsigned& qterms, const RecCacheF64& rc) {
   const bool list = rc.n >= 0;
   const int nrec = list ? rc.n : R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
@@ -215,16 +219,34 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
     }
     if (qqf <= R2f) {
       const float tf = cf * qqf;
-      const G4 G = ldg_g4(rec + h);
-      double qq = fma(k2v[0], G.x, G.w + kk2);
-      if (D >= 2) qq = fma(k2v[1], G.y, qq);
-      if (D >= 3) qq = fma(k2v[2], G.z, qq);
+      // the binary64 |G + k|^2 only where an order needs it: a constant record (Phi below
+      // the table floor on the interval, picked by the binary32 t) is one load
+      double qq = 0.0;
+      bool have_qq = false;
       ++terms;
 #pragma unroll
       for (int j = 0; j < NDM; ++j)
         if (j < nd) {
+          const PhiInfo& P = sphi[j];
+          if (tf >= (float)kT0 && tf <= P.t_hi_f) {
+            const int i = min(phi_interval(tf, P.t_geo_end_f), P.n_int - 1);
+            const double* r = P.tab + (size_t)i * kRec;
+            const double2 so = __ldg(reinterpret_cast<const double2*>(r));  // (n|pad, s)
+            if (__double2loint(so.x) == 1) {
+              acc[j] += __ldg(r + 4);
+              continue;
+            }
+          }
+          if (!have_qq) {
+            const G4 G = ldg_g4(rec + h);
+            qq = fma(k2v[0], G.x, G.w + kk2);
+            if (D >= 2) qq = fma(k2v[1], G.y, qq);
+            if (D >= 3) qq = fma(k2v[2], G.z, qq);
+            have_qq = true;
+            ++qterms;
+          }
           int n;
-          acc[j] += phi_eval_qq(sphi[j], qq, tf, n);
+          acc[j] += phi_eval_qq(P, qq, tf, n);
           coefs += n;
         }
     }
@@ -895,7 +917,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
     kcb[i] = R->AiT[i * 3 + ax_b];
     kcc[i] = R->AiT[i * 3 + ax_c];
   }
-  unsigned terms = 0, coefs = 0;
+  unsigned terms = 0, coefs = 0, qterms = 0;
   const int nn = nv * nv2;
   for (int s2 = 0; s2 < 2; ++s2) {  // p2 = +1, -1
     if constexpr (!MIXED && NDM >= 4) {  // candidates: k = u A^{-T} (alpha e_a + p2 beta e_b + e_c), alpha = p1 v1, beta = v2
@@ -1034,7 +1056,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn) acc[jn] = 0.0;
           const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
+          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) Z[jn] = R->pref[jn] * (Zp[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1057,7 +1079,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
     block_reduce_store2<256>(wsum, wneg, np, wblk, o + (size_t)(2 * s2) * sstride * EZ_MAX_PROD,
                              o + (size_t)(2 * s2 + 1) * sstride * EZ_MAX_PROD);
   }
-  count_work(R, terms, coefs);
+  count_work(R, terms, coefs, MIXED ? terms : qterms);
 }
 
 // ------------------------------------------------------------------------- d = 2
@@ -1109,7 +1131,7 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
   const double kca0 = R->AiT[0 * 2 + ax_a], kca1 = R->AiT[1 * 2 + ax_a];
   const double kcc0 = R->AiT[0 * 2 + ax_c], kcc1 = R->AiT[1 * 2 + ax_c];
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
-  unsigned terms = 0, coefs = 0;
+  unsigned terms = 0, coefs = 0, qterms = 0;
   if constexpr (MIXED) {
     // k = alpha v + gamma in float-float; real space by compensated dot products on the
     // float-float phase table (conjugated for p1 = -1) and H
@@ -1185,13 +1207,13 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
+    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
 #pragma unroll
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
     products<NDM>(R, nd, np, Z, wv, wsum);
   }
-  count_work(R, terms, coefs);
+  count_work(R, terms, coefs, MIXED ? terms : qterms);
   block_reduce_store<128>(wsum, np, wblk, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
 
@@ -1224,7 +1246,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   const double u = R->u_nodes[iu];
   const double w = 2.0 * R->u_w[iu];
   const int M = R->M[0];
-  unsigned terms = 0, coefs = 0;
+  unsigned terms = 0, coefs = 0, qterms = 0;
   double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   if constexpr (MIXED) {
     const ff k[1] = {ffd(R->AiT[0] * u)};
@@ -1266,7 +1288,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
   const float kf[1] = {(float)k[0]};
-  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, rcache);
+  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
 #pragma unroll
   for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1274,9 +1296,15 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   }
   double* o = seg + (size_t)(it.chunk_seg() + threadIdx.x) * EZ_MAX_PROD;
   for (int p = 0; p < np; ++p) o[p] = f[p];
-  if (R->work) {  // some lanes left early: plain atomics, no warp shuffle
-    atomicAdd(R->work, (unsigned long long)terms);
-    atomicAdd(R->work + 1, (unsigned long long)coefs);
+  if (R->work) {  // lanes beyond n_ui left early: sum over the lanes still active
+    const unsigned am = __activemask();
+    const unsigned t = __reduce_add_sync(am, terms), c = __reduce_add_sync(am, coefs);
+    const unsigned q = __reduce_add_sync(am, MIXED ? terms : qterms);
+    if ((int)(threadIdx.x & 31) == __ffs(am) - 1) {
+      atomicAdd(R->work, (unsigned long long)t);
+      atomicAdd(R->work + 1, (unsigned long long)c);
+      atomicAdd(R->work + 2, (unsigned long long)q);
+    }
   }
 }
 
