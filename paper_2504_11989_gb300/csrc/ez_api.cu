@@ -1145,18 +1145,24 @@ int batch_layout(ez_batch_s& B, bool fill) {
     std::memcpy(R.expo, p.spec.expo, sizeof R.expo);
     std::memcpy(R.A, L->A, sizeof R.A);
     std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+    for (int i = 0; i < 9; ++i) ff_split(R.AiT[i], R.AiT_ff[i].x, R.AiT_ff[i].y);
     R.V = L->V;
     R.lam = p.lam;
     R.c_lam = kPi * p.lam * p.lam;
     R.vol_fac = std::pow(p.lam, p.d) / L->V;
     R.R2_recip = p.r_recip * p.r_recip;
     R.eps = p.eps;
+    R.inv_eps = 1.0 / p.eps;
+    ff_split(R.eps, R.eps_ff.x, R.eps_ff.y);
+    ff_split(R.inv_eps, R.inv_eps_ff.x, R.inv_eps_ff.y);
     for (int j = 0; j < p.spec.n_distinct; ++j) {
       double nu = p.spec.nu[j];
       R.nu[j] = nu;
       R.two_over_nu[j] = 2.0 / nu;
       R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
       R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
+      ff_split(R.sig[j] / L->V, R.sigv_ff[j].x, R.sigv_ff[j].y);
+      R.nu_f[j] = (float)nu;
       R.phi[j] = p.phi[j];
       R.phi[j].c_lam = R.c_lam;
       R.phi[j].tab = (const double*)dptr(o_tab[r][j]);

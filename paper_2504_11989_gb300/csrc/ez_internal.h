@@ -125,6 +125,11 @@ struct ReqDesc {
   const float2* vw_ff;
   // float-float copies of the per-exponent constants, for the mixed form
   float2 pref_ff[EZ_MAX_NU], tov_ff[EZ_MAX_NU], vol_ff;
+  double inv_eps;           // 1 / eps (near part)
+  float2 eps_ff, inv_eps_ff;  // eps and 1 / eps as float-float
+  float2 AiT_ff[9];           // A^{-T} as float-float (mixed-form near part)
+  float2 sigv_ff[EZ_MAX_NU];  // sigma_nu / V as float-float
+  float nu_f[EZ_MAX_NU];      // nu in binary32 (integers)
   // d <= 2: powers e^{2 pi i m u v}, m = 0..phase_mp1-1, per (u node, v node); shared by every
   // sum of a batch with the same quadrature (the phases do not depend on the lattice)
   const double2* phase;

@@ -1368,6 +1368,19 @@ __device__ __forceinline__ FFN nfrom<FFN>(double x) {
   ff_split(x, r.hi, r.lo);
   return r;
 }
+// exact conversion of an integer |v| < 2^48 (binomial products, small multipliers)
+template <typename N>
+__device__ __forceinline__ N nint(long long v);
+template <>
+__device__ __forceinline__ double nint<double>(long long v) {
+  return (double)v;
+}
+template <>
+__device__ __forceinline__ FFN nint<FFN>(long long v) {
+  if (v >= -(1 << 24) && v <= (1 << 24)) return FFN{(float)(int)v, 0.0f};  // exact in binary32
+  const float hi = (float)v;
+  return FFN{hi, (float)(v - (long long)hi)};
+}
 __device__ __forceinline__ double nto(double x) { return x; }
 __device__ __forceinline__ double nto(FFN x) { return (double)x.hi + (double)x.lo; }
 __device__ __forceinline__ double ninv(double, int mk) {
@@ -1382,13 +1395,25 @@ __device__ __forceinline__ FFN ninv(FFN, int mk) {
 }
 template <typename N>
 __device__ __forceinline__ N npow(N x, int e) {  // e >= 0
-  N r = nfrom<N>(1.0);
+  N r = nint<N>(1);
   while (e) {
     if (e & 1) r = r * x;
     x = x * x;
     e >>= 1;
   }
   return r;
+}
+// eps or 1/eps of the near part (set on the host)
+template <typename N>
+__device__ __forceinline__ N neps(const ReqDesc* R, bool inv);
+template <>
+__device__ __forceinline__ double neps<double>(const ReqDesc* R, bool inv) {
+  return inv ? R->inv_eps : R->eps;
+}
+template <>
+__device__ __forceinline__ FFN neps<FFN>(const ReqDesc* R, bool inv) {
+  const float2 v = inv ? R->inv_eps_ff : R->eps_ff;
+  return FFN{v.x, v.y};
 }
 __device__ __forceinline__ double ntaylor(const ReqDesc* R, int jn, int ia, double) {
   return R->taylor[(size_t)jn * R->n_alpha + ia];
@@ -1407,11 +1432,11 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
     e[j] = R->expo[p][j];
     t[j] = 0;
   }
-  N total = nfrom<N>(0.0);
+  N total = nint<N>(0);
   N G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
-  const N eps = nfrom<N>(R->eps), inv_eps = nfrom<N>(1.0 / R->eps), eps2 = eps * eps;
+  const N eps = neps<N>(R, false), inv_eps = neps<N>(R, true), eps2 = eps * eps;
   while (true) {
-    N coef = nfrom<N>(1.0);
+    N coef = nint<N>(1);
     long long mult = 1;  // product of binomials (exact integers)
     int mu = d, mlog = 0;
     for (int j = 0; j < nd; ++j) {
@@ -1420,17 +1445,17 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
         for (int i = 1; i <= t[j]; ++i) bj = bj * (e[j] - t[j] + i) / i;
         mult *= bj;
         for (int i = 0; i < t[j]; ++i) coef = coef * sig_w[j];
-        mu += t[j] * ((int)lrint(R->nu[j]) - d);
+        mu += t[j] * ((int)R->nu_f[j] - d);
         mlog += t[j] * R->islog[j];
       }
     }
     int deg = 0;
-    G[0] = nfrom<N>(1.0);
+    G[0] = nint<N>(1);
     for (int j = 0; j < nd; ++j)
       for (int r = 0; r < e[j] - t[j]; ++r) {
         const int nd2 = min(deg + ell, kNearMaxDeg);
         for (int i = 0; i <= nd2; ++i) {
-          N s = nfrom<N>(0.0);
+          N s = nint<N>(0);
           for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = nfma(G[q], C[j][i - q], s);
           T[i] = s;
         }
@@ -1438,21 +1463,21 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
     N epm = mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu);
-    N sumk = nfrom<N>(0.0);
+    N sumk = nint<N>(0);
     for (int k = 0; k <= deg; ++k) {
       // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
       // reciprocals of small integers (no division in the loop)
       const int mk = mu + 2 * k;
       const N inv = ninv(epm, mk);
-      N J = inv, Lp = nfrom<N>(1.0);
+      N J = inv, Lp = nint<N>(1);
       for (int i = 1; i <= mlog; ++i) {
         Lp = Lp * L;
-        J = (Lp + J * nfrom<N>(-2.0 * i)) * inv;
+        J = (Lp + J * nint<N>(-2 * i)) * inv;
       }
       sumk = nfma(G[k], epm * J, sumk);
       epm = epm * eps2;
     }
-    total = nfma(nfrom<N>((double)mult) * coef, sumk, total);
+    total = nfma(nint<N>(mult) * coef, sumk, total);
     int j = 0;
     for (; j < nd; ++j) {
       if (t[j] < e[j]) {
@@ -1466,35 +1491,78 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
   return total;
 }
 
-// one ray: C_k(w) of every exponent, then every product's near integral
+// one ray: C_k(w) of every exponent, then every product's near integral (scale 2 w_v)
 template <typename N>
-__device__ void near_ray(const ReqDesc* R, const double* w, double w2, double wv, double (&val)[EZ_MAX_PROD]) {
-  const int d = R->d, ell = R->ell, nd = R->n_distinct, np = R->n_prod;
+__device__ void near_core(const ReqDesc* R, const N* wN, N L, const N* sig_w, double scale,
+                          double (&val)[EZ_MAX_PROD]) {
+  const int ell = R->ell, nd = R->n_distinct, np = R->n_prod;
   // C_k(w) = sum_{|alpha| = 2k} D[alpha] w^alpha: one monomial per alpha (powers of w
   // tabulated once), shared by every exponent
   N pw[3][2 * kMaxEll + 1];
   for (int i = 0; i < 3; ++i) {
-    const N wi = nfrom<N>(w[i]);
-    pw[i][0] = nfrom<N>(1.0);
-    for (int q = 1; q <= 2 * ell; ++q) pw[i][q] = pw[i][q - 1] * wi;
+    pw[i][0] = nint<N>(1);
+    for (int q = 1; q <= 2 * ell; ++q) pw[i][q] = pw[i][q - 1] * wN[i];
   }
   N C[EZ_MAX_NU][kMaxEll + 1];
   for (int jn = 0; jn < nd; ++jn)
-    for (int kk = 0; kk <= ell; ++kk) C[jn][kk] = nfrom<N>(0.0);
+    for (int kk = 0; kk <= ell; ++kk) C[jn][kk] = nint<N>(0);
   for (int kk = 0; kk <= ell; ++kk)
     for (int ia = R->alpha_off[kk]; ia < R->alpha_off[kk + 1]; ++ia) {
       const int* al = R->alpha + 3 * ia;
       const N mono = pw[0][al[0]] * pw[1][al[1]] * pw[2][al[2]];
       for (int jn = 0; jn < nd; ++jn) C[jn][kk] = nfma(ntaylor(R, jn, ia, mono), mono, C[jn][kk]);
     }
-  const N L = nfrom<N>(log(kPi * R->eps * R->eps * w2));
+  for (int p = 0; p < np; ++p) val[p] = scale * nto(near_product<N>(R, p, C, sig_w, L));
+}
+
+// FP64 form: per-ray inputs in binary64
+__device__ void near_ray_f64(const ReqDesc* R, const double* dir, double wv, double (&val)[EZ_MAX_PROD]) {
+  const int d = R->d, nd = R->n_distinct;
+  double w[3] = {0.0, 0.0, 0.0}, w2 = 0.0;
+  for (int i = 0; i < d; ++i) {
+    double s = 0.0;
+    for (int q = 0; q < d; ++q) s = fma(R->AiT[i * d + q], dir[q], s);
+    w[i] = s;
+    w2 = fma(s, s, w2);
+  }
+  const double L = log(kPi * R->eps * R->eps * w2);
   const double wn = sqrt(w2), inv_wn = 1.0 / wn, inv_V = 1.0 / R->V;
-  N sig_w[EZ_MAX_NU];
+  double sig_w[EZ_MAX_NU];
   for (int jn = 0; jn < nd; ++jn) {
     const int dn = (int)lrint(R->nu[jn]) - d;
-    sig_w[jn] = nfrom<N>(R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V);
+    sig_w[jn] = R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V;
   }
-  for (int p = 0; p < np; ++p) val[p] = 2.0 * wv * nto(near_product<N>(R, p, C, sig_w, L));
+  near_core<double>(R, w, L, sig_w, 2.0 * wv, val);
+}
+
+// Mixed form: the per-ray inputs in float-float (w = A^{-T} dir, |w|, 1/|w|, the singular
+// weights sigma_nu |w|^{nu - d} / V) and one binary64 log per ray -- binary64 work here would
+// otherwise bound the kernel on the FP64 pipe
+__device__ void near_ray_ff(const ReqDesc* R, const ff* dir, double wv, double (&val)[EZ_MAX_PROD]) {
+  const int d = R->d, nd = R->n_distinct;
+  FFN w[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  ff w2{0.0f, 0.0f};
+  for (int i = 0; i < d; ++i) {
+    ff s{0.0f, 0.0f};
+    for (int q = 0; q < d; ++q) s = ff_add(s, ff_mul(ff{R->AiT_ff[i * d + q].x, R->AiT_ff[i * d + q].y}, dir[q]));
+    w[i] = FFN{s.hi, s.lo};
+    w2 = ff_add(w2, ff_sqr(s));
+  }
+  FFN L;
+  ff_split(log(kPi * R->eps * R->eps * ((double)w2.hi + (double)w2.lo)), L.hi, L.lo);
+  const ff wn = ff_sqrt(w2), inv_wn = ff_rcp(wn);
+  FFN sig_w[EZ_MAX_NU];
+  for (int jn = 0; jn < nd; ++jn) {
+    const int dn = (int)lrintf(R->nu_f[jn]) - d;
+    ff b = dn >= 0 ? wn : inv_wn, r{1.0f, 0.0f};
+    for (int e = dn >= 0 ? dn : -dn; e; e >>= 1) {
+      if (e & 1) r = ff_mul(r, b);
+      b = ff_sqr(b);
+    }
+    const ff sv = ff_mul(ff{R->sigv_ff[jn].x, R->sigv_ff[jn].y}, r);
+    sig_w[jn] = FFN{sv.hi, sv.lo};
+  }
+  near_core<FFN>(R, w, L, sig_w, 2.0 * wv, val);
 }
 
 __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
@@ -1517,22 +1585,22 @@ __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ r
     }
     const int half = 1 << (d - 1);
     const int j = it.sector / half, pb = it.sector % half;
-    double y[3], dir[3], w[3];
-    for (int i = 0; i < d - 1; ++i) y[i] = (((pb >> i) & 1) ? -1.0 : 1.0) * v[i];
-    y[d - 1] = 1.0;
-    for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
-    double w2 = 0.0;
-    for (int i = 0; i < d; ++i) {
-      double s = 0.0;
-      for (int q = 0; q < d; ++q) s = fma(R->AiT[i * d + q], dir[q], s);
-      w[i] = s;
-      w2 = fma(s, s, w2);
+    if (R->prec == EZ_MIXED) {
+      ff y[3], dir[3];
+      for (int i = 0; i < d - 1; ++i) {
+        const float2 vf = R->v_ff[i == 0 ? r % nv : r / nv];
+        y[i] = ((pb >> i) & 1) ? ff{-vf.x, -vf.y} : ff{vf.x, vf.y};
+      }
+      y[d - 1] = ff{1.0f, 0.0f};
+      for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
+      near_ray_ff(R, dir, wv, val);
+    } else {
+      double y[3], dir[3];
+      for (int i = 0; i < d - 1; ++i) y[i] = (((pb >> i) & 1) ? -1.0 : 1.0) * v[i];
+      y[d - 1] = 1.0;
+      for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
+      near_ray_f64(R, dir, wv, val);
     }
-    for (int i = d; i < 3; ++i) w[i] = 0.0;
-    if (R->prec == EZ_MIXED)
-      near_ray<FFN>(R, w, w2, wv, val);
-    else
-      near_ray<double>(R, w, w2, wv, val);
   }
   block_reduce_store<128>(val, np, 1.0, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }
