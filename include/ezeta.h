@@ -255,6 +255,24 @@ int ez_server_destroy(ez_server s, int timeout_ms);
 int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q, int* n_sectors,
               int* n_u_total, int* u_rule_used);
 
+/* Diagnostic (no counterpart in the paper): the plan the library makes for one sum --
+ * splitting parameter, cutoffs, real-space box, block decomposition, this part's range of
+ * far lines, mixed-form thresholds -- computed on the host (no GPU needed).  EZ_EINVAL /
+ * EZ_EDOMAIN as ez_lattice_sums would return for the same arguments. */
+typedef struct {
+  double lambda, r_real, r_recip;
+  int M[3];                 /* real-space box half-widths */
+  int m_hp[3];              /* mixed form: terms with |m_i| >= m_hp[i] summed in plain binary32 */
+  int n_sectors, n_u_total, u_rule;
+  int vchunk, n_chunks;     /* d = 3: v2 rows per far-field block, blocks per line group */
+  long long line_lo, line_hi; /* this part's far lines (d <= 2) or line groups (d = 3) */
+  long long n_far_items;    /* far-field blocks of this part */
+  size_t far_smem_bytes;    /* dynamic shared memory of one far-field block */
+  float t_mix, t_mid;       /* mixed form: binary32 tails beyond t_mix, binary32 polynomial
+                               beyond t_mid (3e38 in the FP64 form) */
+} ez_plan_info;
+int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const ez_quadrature* q, ez_plan_info* out);
+
 /* Diagnostic (no counterpart in the paper): sustained FP64 FMA throughput of the
  * current device in TFLOP/s, from a DFMA loop on every SM timed with CUDA events. */
 int ez_diag_fp64_peak(double* tflops, void* stream);

@@ -1676,6 +1676,33 @@ extern "C" int ez_layout(int d, const ez_sum_spec* spec, const ez_quadrature* q,
   return EZ_OK;
 }
 
+extern "C" int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const ez_quadrature* q, ez_plan_info* out) {
+  if (!lat || !spec || !q || !out) return fail(EZ_EINVAL, "NULL argument");
+  Plan p;
+  int rc = make_plan(lat, *spec, *q, p);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof *out);
+  out->lambda = p.lam;
+  out->r_real = p.r_real;
+  out->r_recip = p.r_recip;
+  for (int i = 0; i < 3; ++i) {
+    out->M[i] = p.M[i];
+    out->m_hp[i] = p.m_hp[i];
+  }
+  out->n_sectors = p.nsect;
+  out->n_u_total = p.n_ui;
+  out->u_rule = p.u_rule;
+  out->vchunk = p.vchunk;
+  out->n_chunks = p.nch;
+  out->line_lo = p.line_lo;
+  out->line_hi = p.line_hi;
+  out->n_far_items = p.n_far_items;
+  out->far_smem_bytes = p.smem;
+  out->t_mix = p.phi[0].t_mix_f;
+  out->t_mid = p.phi[0].t_mid_f;
+  return EZ_OK;
+}
+
 extern "C" int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q, double* value,
                                     void* stream) {
   if (!lat || !nu || !q || !value) return fail(EZ_EINVAL, "NULL argument");

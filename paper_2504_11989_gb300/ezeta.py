@@ -123,6 +123,8 @@ def lib():
             L.ez_layout.argtypes = [ctypes.c_int, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
+            L.ez_plan_describe.argtypes = [ctypes.c_void_p, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
+                                           ctypes.POINTER(ez_plan_info)]
             _lib = L
     return _lib
 
@@ -286,6 +288,22 @@ def ez_lattice_sums(lats, specs, quads, out=None, lines: bool = False, stream=No
     if lines:
         return out, lbuf, np.array(offs[:])
     return out
+
+
+class ez_plan_info(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("r_real", ctypes.c_double), ("r_recip", ctypes.c_double),
+                ("M", ctypes.c_int * 3), ("m_hp", ctypes.c_int * 3), ("n_sectors", ctypes.c_int),
+                ("n_u_total", ctypes.c_int), ("u_rule", ctypes.c_int), ("vchunk", ctypes.c_int),
+                ("n_chunks", ctypes.c_int), ("line_lo", ctypes.c_longlong), ("line_hi", ctypes.c_longlong),
+                ("n_far_items", ctypes.c_longlong), ("far_smem_bytes", ctypes.c_size_t), ("t_mix", ctypes.c_float),
+                ("t_mid", ctypes.c_float)]
+
+
+def ez_plan_describe(lat: "Lattice", spec: ez_sum_spec, q: ez_quadrature) -> ez_plan_info:
+    """The host-side plan of one sum (diagnostic; no GPU needed)."""
+    info = ez_plan_info()
+    _check(lib().ez_plan_describe(lat.handle, ctypes.byref(spec), ctypes.byref(q), ctypes.byref(info)))
+    return info
 
 
 def ez_layout(d: int, spec: ez_sum_spec, q: ez_quadrature):

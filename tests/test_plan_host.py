@@ -1,0 +1,154 @@
+"""Host-side planning checked without a GPU (ez_plan_describe): the partition of a sum into
+parts, the 3-D block decomposition and its shared-memory bound, the default splitting
+parameter, and the mixed form's precision thresholds, the last two against incomplete gamma
+values from mpmath (independent of the library's own Gamma code)."""
+import math
+import shutil
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_11989_gb300 import workloads as W
+
+AUTO = dict(lam=0.0, r_real=0.0, r_recip=0.0)
+
+
+@pytest.fixture(scope="module")
+def ez():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2504_11989_gb300 import build, ezeta
+
+    build.build()
+    return ezeta
+
+
+def _plan(ez, prob, prec=0, **kw):
+    L = ez.Lattice(prob.A)
+    return ez.ez_plan_describe(L, ez.sum_spec(prob.nu, prob.expo), ez.quadrature(prob.quad, prec=prec, **kw))
+
+
+def _phi(a, t):
+    """Phi_a(t) = t^{-a} Gamma(a, t), any real a (mpmath, 30 digits)."""
+    import mpmath
+
+    mpmath.mp.dps = 30
+    return float(mpmath.gammainc(a, t) * mpmath.power(t, -a))
+
+
+PROBS = [
+    W.nbody_problem("Z", 4.0, 3, W.Quad(n_u=300, n_v=1, **AUTO)),
+    W.nbody_problem("hexagonal", 3.0, 3, W.Quad(n_u=20, n_v=17, **AUTO)),
+    W.atm_problem("square", W.Quad(n_u=6, n_v=10, u_rule=2, **AUTO)),
+    W.nbody_problem("fcc", 6.0, 3, W.Quad(n_u=32, n_v=48, **AUTO)),
+    W.atm_problem("sc", W.Quad(n_u=8, n_v=64, u_rule=2, **AUTO)),
+    W.atm_problem("bcc", W.Quad(n_u=3, n_v=7, u_rule=2, **AUTO)),
+    W.nbody_problem("sc", 9.0, 2, W.Quad(n_u=4, n_v=64, u_rule=2, **AUTO)),
+]
+
+
+@pytest.mark.parametrize("prob", PROBS, ids=lambda p: p.name)
+@pytest.mark.parametrize("n_parts", [2, 3, 7])
+def test_parts_tile_the_far_lines(ez, prob, n_parts):
+    """The parts' line ranges are disjoint, contiguous and cover every far line (d <= 2)
+    or line group (d = 3: the four sectors of one axis and u node)."""
+    whole = _plan(ez, prob)
+    d = prob.A.shape[0]
+    units = (3 if d == 3 else whole.n_sectors) * whole.n_u_total
+    assert (whole.line_lo, whole.line_hi) == (0, units)
+    hi = 0
+    for k in range(n_parts):
+        p = _plan(ez, prob, part=k, n_parts=n_parts)
+        assert p.line_lo == hi and p.line_hi >= p.line_lo
+        hi = p.line_hi
+        if d >= 2:
+            assert p.n_far_items == (p.line_hi - p.line_lo) * p.n_chunks
+    assert hi == units
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_3d_blocks_fit_two_per_sm(ez, prec):
+    """d = 3: the v2 rows of a block are covered by the chunks, and a block's dynamic shared
+    memory stays within 98 KB (two blocks per SM) unless the smallest chunk (8 rows) is
+    already larger."""
+    reqs = W.serving_mix(120, W.SEED_BASE + 5, 1.0)
+    seen = 0
+    for r in reqs:
+        if r.d != 3:
+            continue
+        p = W.request_problem(r)
+        info = _plan(ez, p, prec=prec)
+        n_v = p.quad.n_v
+        assert info.n_chunks * info.vchunk >= n_v > (info.n_chunks - 1) * info.vchunk
+        assert info.far_smem_bytes <= 98 * 1024 or info.vchunk == min(n_v, 8)
+        assert max(info.M) <= 16
+        seen += 1
+    assert seen > 10
+
+
+@pytest.mark.parametrize("lat,d", [("Z", 1), ("square", 2), ("hexagonal", 2), ("sc", 3), ("fcc", 3), ("bcc", 3)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_default_splitting_parameter(ez, lat, d, prec):
+    """lam = 0: 2 V (d = 1), 3 V^{1/2} (d = 2), 4.5 V^{1/3} (FP64) or 4 V^{1/3} (mixed) in 3-D,
+    lowered only as far as the real-space box half-width 16 requires; the cutoffs are
+    sqrt(T/pi) lam^{+-1} with T = 45 (FP64) or 36 (mixed)."""
+    A = W.lattice(lat, scale=1.17)
+    V = abs(np.linalg.det(A))
+    prob = W.nbody_problem(lat, 4.0 if d < 3 else 6.0, 3, W.Quad(n_u=8, n_v=8, **AUTO), scale=1.17)
+    info = _plan(ez, prob, prec=prec)
+    f = {1: 2.0, 2: 3.0, 3: 4.0 if prec else 4.5}[d]
+    T = 36.0 if prec else 45.0
+    want = f * V ** (1.0 / d)
+    assert info.lambda_ <= want * (1 + 1e-12)
+    rows = np.linalg.norm(np.linalg.inv(A), axis=1)
+    R = math.sqrt(T / math.pi) * info.lambda_
+    assert info.r_real == pytest.approx(R, rel=1e-12)
+    assert info.r_recip == pytest.approx(math.sqrt(T / math.pi) / info.lambda_, rel=1e-12)
+    M = [math.ceil(R * rn + 1e-9) for rn in rows]
+    assert list(info.M)[:d] == M and max(M) <= 16
+    if info.lambda_ < want * (1 - 1e-12):  # lowered: the box would exceed 16 at the default
+        assert max(math.ceil(math.sqrt(T / math.pi) * want * rn + 1e-9) for rn in rows) > 16
+
+
+@pytest.mark.parametrize("prob", [PROBS[1], PROBS[3], PROBS[4], PROBS[6]], ids=lambda p: p.name)
+def test_mixed_thresholds_against_mpmath(ez, prob):
+    """Mixed form: beyond t_mix every reciprocal order has |Phi_a(t)| t <= 1e-7 and beyond t_mid
+    |Phi_a(t)| <= 1e-6 (on the 0.25 grid the planner scans); one grid step earlier the bound
+    fails for some order (the thresholds are the first grid points that hold)."""
+    info = _plan(ez, prob, prec=1)
+    d = prob.A.shape[0]
+    orders = [0.5 * (d - nu) for nu in prob.nu]
+    tm, td = float(info.t_mix), float(info.t_mid)
+    for t in np.arange(tm, tm + 8.0, 0.25):
+        assert all(abs(_phi(a, t)) * t <= 1e-7 for a in orders), t
+    assert any(abs(_phi(a, tm - 0.25)) * (tm - 0.25) > 1e-7 for a in orders)
+    for t in np.arange(td, tm, 0.25):
+        assert all(abs(_phi(a, t)) <= 1e-6 for a in orders), t
+    if td < tm:
+        assert any(abs(_phi(a, td - 0.25)) > 1e-6 for a in orders)
+
+
+@pytest.mark.parametrize("prob", [PROBS[3], PROBS[4], PROBS[5]], ids=lambda p: p.name)
+def test_mixed_binary32_shells_against_mpmath(ez, prob):
+    """Mixed form: m_hp[i] is the first |m_i| at which every real-space order's term is below
+    1e-8 of its value at the shortest lattice vector (|z| >= |m_i| / |row_i(A^{-1})|)."""
+    info = _plan(ez, prob, prec=1)
+    A = prob.A
+    lam = info.lambda_
+    shifts = [np.array(m) - 2 for m in np.ndindex(5, 5, 5)]
+    dmin2 = min(float(np.sum((A @ m) ** 2)) for m in shifts if np.any(m))
+    Ai = np.linalg.inv(A)
+    orders = [0.5 * nu for nu in prob.nu]
+    ref = [abs(_phi(a, math.pi * dmin2 / lam ** 2)) for a in orders]
+
+    def small(m, rn2):
+        return all(abs(_phi(a, math.pi * (m * m / rn2) / lam ** 2)) <= 1e-8 * r for a, r in zip(orders, ref))
+
+    for i in range(3):
+        rn2 = float(np.sum(Ai[i] ** 2))
+        m = info.m_hp[i]
+        if m <= info.M[i]:
+            assert small(m, rn2)
+        if m > 1:
+            assert not small(m - 1, rn2)
