@@ -138,7 +138,7 @@ __device__ __forceinline__ int phi_interval(float tf, float t_geo_end_f) {
     i = (int)(__log2f(2.0f * tf) * 2.06008f);
     i = max(0, min(i, kNGeo - 1));
   } else {
-    i = kNGeo + (int)(tf - t_geo_end_f);
+    i = kNGeo + (int)((tf - t_geo_end_f) * kUnitInvF);
   }
   return i;
 }

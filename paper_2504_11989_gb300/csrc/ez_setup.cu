@@ -173,8 +173,8 @@ __device__ __forceinline__ void phi_interval_bounds(int iv, double t_geo_end, do
     lo = kT0 * pow(kGeoR, (double)iv);
     hi = lo * kGeoR;
   } else {
-    lo = t_geo_end + (iv - kNGeo);
-    hi = lo + 1.0;
+    lo = t_geo_end + (iv - kNGeo) * kUnitW;
+    hi = lo + kUnitW;
   }
   tm = 0.5 * (lo + hi);
   h = 0.5 * (hi - lo);
