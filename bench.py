@@ -35,7 +35,7 @@ N_BODY = 3
 # full-size ncu capture summarised in profiles/far_kernel_d2_config2.md.  Set to None whenever
 # that kernel changes until re-captured (other batch sizes report null: the shared phase
 # table makes the traffic not proportional to the number of sums).
-FAR_DRAM_BYTES_PER_LAUNCH = None  # re-captured below after the kernel change
+FAR_DRAM_BYTES_PER_LAUNCH = 8673536
 
 
 def parse():

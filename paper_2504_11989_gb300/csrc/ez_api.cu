@@ -250,9 +250,15 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   P.two_a = (int)std::lrint(2.0 * a);
   P.log_m = (is_integer(a) && a <= 0.0) ? (int)std::lrint(-a) : -1;
   P.t_geo_end = kT0 * std::pow(kGeoR, kNGeo);
-  int n_unit = (int)std::ceil(std::max(0.0, t_hi_needed - P.t_geo_end) / kUnitW) + 1;
-  P.n_int = std::min(kNGeo + n_unit, kMaxInt);
-  P.t_hi = P.t_geo_end + (P.n_int - kNGeo) * kUnitW;
+  const double t_half_end = P.t_geo_end + 0.5 * kNHalf;
+  int n_rest;  // intervals after the geometric ones
+  if (t_hi_needed <= t_half_end)
+    n_rest = (int)std::ceil(std::max(0.0, t_hi_needed - P.t_geo_end) / 0.5) + 1;
+  else
+    n_rest = kNHalf + (int)std::ceil(t_hi_needed - t_half_end) + 1;
+  P.n_int = std::min(kNGeo + n_rest, kMaxInt);
+  const int nr = P.n_int - kNGeo;
+  P.t_hi = nr <= kNHalf ? P.t_geo_end + 0.5 * nr : t_half_end + (nr - kNHalf);
   P.t_geo_end_f = (float)P.t_geo_end;
   P.t_hi_f = (float)P.t_hi;
   double fact = 1.0;

@@ -14,8 +14,9 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 // ---------------------------------------------------------------------------
 // Tables of Phi_a(t) = t^{-a} Gamma(a,t) for the reciprocal-space hot loop.
 // t in [kT0, t_hi]: piecewise polynomials in x = (t - t_mid)/h on kNGeo geometric
-//   intervals [kT0 r^i, kT0 r^{i+1}] (r = kGeoR), then intervals of width kUnitW up to
-//   t_hi.  Record of an interval (kRec doubles, 16-byte aligned): the number n of
+//   intervals [kT0 r^i, kT0 r^{i+1}] (r = kGeoR), then kNHalf intervals of width 1/2, then
+//   unit-width intervals up to t_hi (beyond t ~ 45 Phi is below the table floor and the
+//   records hold one coefficient: only their count matters there).  Record of an interval (kRec doubles, 16-byte aligned): the number n of
 //   coefficients kept (4, 8, 12 or 16, an int in the first slot), s = c/h and
 //   o = -t_mid/h so that x = fma(|q|^2, s, o) with t = c |q|^2, one pad slot, then
 //   b_0 .. b_{kNC-1} (monomials in x; b_j = 0 for j >= n).  n is the shortest length whose Chebyshev
@@ -32,9 +33,8 @@ constexpr int kNGeo = 5;
 constexpr double kT0 = 0.5;
 constexpr double kGeoR = 1.4;
 constexpr int kNSer = 16;  // t < 1/2: 0.5^16/16! ~ 7e-19
-constexpr double kUnitW = 0.5;   // width of the intervals beyond the geometric ones
-constexpr float kUnitInvF = 2.0f;  // 1 / kUnitW
-constexpr int kMaxInt = 640;  // intervals per table (t_hi <= ~320)
+constexpr int kNHalf = 100;  // intervals of width 1/2 after the geometric ones
+constexpr int kMaxInt = 420;  // intervals per table (t_hi <= ~366)
 // Float-float table of the mixed form (kRecFF floats per interval, 16-byte aligned):
 // int n (shortest length in {4, 8, 12, 16} with Chebyshev tail below 2^-47 max|Phi|), pad,
 // s = c/h and m = t_mid/c as float-float pairs, two pads, then b_0 .. b_{kNC-1} as

@@ -138,7 +138,8 @@ __device__ __forceinline__ int phi_interval(float tf, float t_geo_end_f) {
     i = (int)(__log2f(2.0f * tf) * 2.06008f);
     i = max(0, min(i, kNGeo - 1));
   } else {
-    i = kNGeo + (int)((tf - t_geo_end_f) * kUnitInvF);
+    const float u = 2.0f * (tf - t_geo_end_f);  // half-width intervals, then unit width
+    i = u < (float)kNHalf ? kNGeo + (int)u : kNGeo + kNHalf + (int)(0.5f * (u - (float)kNHalf));
   }
   return i;
 }

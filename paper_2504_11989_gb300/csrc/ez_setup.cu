@@ -173,8 +173,9 @@ __device__ __forceinline__ void phi_interval_bounds(int iv, double t_geo_end, do
     lo = kT0 * pow(kGeoR, (double)iv);
     hi = lo * kGeoR;
   } else {
-    lo = t_geo_end + (iv - kNGeo) * kUnitW;
-    hi = lo + kUnitW;
+    const int k = iv - kNGeo;  // half-width intervals, then unit width
+    lo = k < kNHalf ? t_geo_end + 0.5 * k : t_geo_end + 0.5 * kNHalf + (k - kNHalf);
+    hi = lo + (k < kNHalf ? 0.5 : 1.0);
   }
   tm = 0.5 * (lo + hi);
   h = 0.5 * (hi - lo);
