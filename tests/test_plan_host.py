@@ -152,3 +152,18 @@ def test_mixed_binary32_shells_against_mpmath(ez, prob):
             assert small(m, rn2)
         if m > 1:
             assert not small(m - 1, rn2)
+
+
+def test_plan_describe_errors_and_fp64_thresholds(ez):
+    """Bad arguments fail as the sums would (part out of range, real-space box wider than
+    16); the FP64 form has no binary32 thresholds, the mixed form's lie inside the table."""
+    prob = W.nbody_problem("fcc", 6.0, 3, W.Quad(n_u=4, n_v=8, **AUTO))
+    with pytest.raises(RuntimeError):
+        _plan(ez, prob, part=3, n_parts=3)
+    with pytest.raises(RuntimeError):
+        _plan(ez, W.nbody_problem("fcc", 6.0, 3, W.Quad(n_u=4, n_v=8, lam=1.0, r_real=40.0, r_recip=4.5)))
+    info = _plan(ez, prob, prec=0)
+    assert info.t_mix > 1e38 and info.t_mid > 1e38
+    mixed = _plan(ez, prob, prec=1)
+    assert 0.5 < mixed.t_mid <= mixed.t_mix < 40.0
+    assert all(1 <= mixed.m_hp[i] <= mixed.M[i] + 1 for i in range(3))
