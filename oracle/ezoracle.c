@@ -110,59 +110,83 @@ static double or_acc_get(const or_acc* a) { return a->s + a->c; }
 /* Upper incomplete gamma: Phi_a(t) = t^{-a} Gamma(a,t) = int_1^inf s^{a-1} e^{-ts} ds */
 /* ------------------------------------------------------------------------- */
 
-/* E_1(t): power series (Abramowitz & Stegun 5.1.11) for t <= 1, continued
- * fraction E_1(t) = e^{-t} / (t+1 - 1/(t+3 - 4/(t+5 - ...))) (A&S 5.1.22,
- * evaluated by the modified Lentz method) for t > 1. */
-double or_expint_e1(double t) {
-  if (!(t > 0.0)) return t == 0.0 ? INFINITY : NAN;
-  if (t <= 1.0) {
-    double sum = 0.0, term = 1.0;
-    for (int k = 1; k < 200; ++k) {
-      term *= -t / k; /* (-t)^k / k! */
-      double add = term / k;
-      sum += add;
-      if (fabs(add) < 1e-18 * fabs(sum)) break;
-    }
-    return -OR_EULER_GAMMA - log(t) - sum;
+/* Phi_a(t) is evaluated from its defining integral by quadrature and by nothing else
+ * (no closed form, continued fraction, series or recurrence in the order a), so that it
+ * is a method of its own, independent of any tabulation of Phi built elsewhere.
+ *
+ * t >= 1: with s = 1 + x, x = e^w,
+ *     Phi_a(t) = e^{-t} int_R (1 + e^w)^{a-1} e^w e^{-t e^w} dw,
+ *   an integrand analytic in the strip |Im w| < pi/2, decaying like e^w as w -> -inf
+ *   and double exponentially as w -> +inf.  The substitution w = c + v - e^{-v} makes
+ *   the left tail double exponential too, and the trapezoidal rule in v converges
+ *   geometrically in 1/h (Takahasi & Mori's double-exponential idea).  c puts the
+ *   integrand's mode near v = 0.  The integrand is unimodal in w: once past its mode
+ *   the terms decrease, and the sum stops when they are below 1e-19 of it. */
+#define OR_DE_KLO (-30) /* v from -3.75 */
+#define OR_DE_KHI 400
+static double or_de_x[OR_DE_KHI - OR_DE_KLO + 1]; /* exp(v - e^{-v}) */
+static double or_de_j[OR_DE_KHI - OR_DE_KLO + 1]; /* dw/dv = 1 + e^{-v} */
+
+/* The nodes depend on v only: tabulated once when the library is loaded. */
+__attribute__((constructor)) static void or_de_init(void) {
+  for (int k = OR_DE_KLO; k <= OR_DE_KHI; ++k) {
+    double v = k * 0.125, ev = exp(-v);
+    or_de_x[k - OR_DE_KLO] = exp(v - ev);
+    or_de_j[k - OR_DE_KLO] = 1.0 + ev;
   }
-  const double tiny = 1e-300;
-  double b = t + 1.0;
-  double c = 1.0 / tiny;
-  double dd = 1.0 / b;
-  double h = dd;
-  for (int i = 1; i < 10000; ++i) {
-    double an = -(double)i * (double)i;
-    b += 2.0;
-    dd = 1.0 / (an * dd + b);
-    c = b + an / c;
-    double del = c * dd;
-    h *= del;
-    if (fabs(del - 1.0) < 1e-17) break;
-  }
-  return h * exp(-t);
 }
 
-/* Phi_a(t) = e^{-t} / (t+1-a - 1(1-a)/(t+3-a - 2(2-a)/(t+5-a - ...))): the even part of
- * Legendre's continued fraction for Gamma(a,t) (DLMF 8.9.2), modified Lentz method. */
-static double or_phi_cf(double a, double t) {
-  const double tiny = 1e-300;
-  double b = t + 1.0 - a;
-  double c = 1.0 / tiny;
-  double dd = 1.0 / b;
-  double h = dd;
-  for (int i = 1; i < 100000; ++i) {
-    double an = -(double)i * ((double)i - a);
-    b += 2.0;
-    dd = an * dd + b;
-    if (fabs(dd) < tiny) dd = tiny;
-    c = b + an / c;
-    if (fabs(c) < tiny) c = tiny;
-    dd = 1.0 / dd;
-    double del = dd * c;
-    h *= del;
-    if (fabs(del - 1.0) < 1e-17) break;
+static double or_phi_t_ge1(double a, double t) {
+  const double h = 0.125;
+  double c = a > 0.0 ? log(fmax(a, 1.0) / t) : -log(t + 1.0 - a);
+  double ec = exp(c);
+  /* (1+x)^{a-1} = (1+x)^n [sqrt(1+x)] with n = floor(a-1): a is a multiple of 1/2 */
+  int n = (int)floor(a - 1.0);
+  int half = (a - 1.0) - n > 0.25;
+  int na = n < 0 ? -n : n;
+  double sum = 0.0;
+  for (int k = OR_DE_KLO; k <= OR_DE_KHI; ++k) {
+    double x = ec * or_de_x[k - OR_DE_KLO];
+    double tx = t * x;
+    if (tx > 745.0) break;
+    double b = 1.0 + x, bp = 1.0;
+    for (int i = 0; i < na; ++i) bp *= b;
+    if (n < 0) bp = 1.0 / bp;
+    if (half) bp *= sqrt(b);
+    double term = bp * x * exp(-tx) * or_de_j[k - OR_DE_KLO];
+    sum += term;
+    /* past the mode of (1+x)^{a-1} x e^{-tx} in log x: d/dlog x = (a-1)x/(1+x) + 1 - tx < 0 */
+    if ((a - 1.0) * x / (1.0 + x) + 1.0 - tx < 0.0 && term < 1e-19 * sum) break;
   }
-  return exp(-t) * h;
+  return exp(-t) * h * sum;
+}
+
+/* t < 1: split the integral at s = 1/t and scale the upper piece, s = r/t:
+ *     Phi_a(t) = int_1^{1/t} s^{a-1} e^{-ts} ds + t^{-a} Phi_a(1).
+ * On the finite piece, with s = e^y (0 <= y <= L = log(1/t)), the integrand
+ * e^{a y - t e^y} has t e^y <= 1, so it is smooth on [0, L]; composite Gauss-Legendre
+ * with 16 nodes on panels of width 1/2 (the last one shorter).  Both pieces are
+ * positive, so nothing cancels. */
+static double or_gl16_x[16], or_gl16_w[16];
+__attribute__((constructor)) static void or_gl16_init(void) { or_gauss_legendre01(16, or_gl16_x, or_gl16_w); }
+
+static double or_phi_t_lt1(double a, double t) {
+  const double* gx = or_gl16_x;
+  const double* gw = or_gl16_w;
+  double L = -log(t);
+  double sum = 0.0;
+  for (double y0 = 0.0; y0 < L; y0 += 0.5) {
+    double wd = fmin(0.5, L - y0);
+    double ps = 0.0;
+    for (int i = 0; i < 16; ++i) {
+      double y = y0 + wd * gx[i];
+      ps += gw[i] * exp(a * y - t * exp(y));
+    }
+    sum += wd * ps;
+    /* a < 0: the rest of [0, L] adds at most e^{a y} (L - y) */
+    if (a < 0.0 && exp(a * (y0 + wd)) * L < 1e-19 * sum) break;
+  }
+  return sum + pow(t, -a) * or_phi_t_ge1(a, 1.0);
 }
 
 double or_phi(double a, double t) {
@@ -171,37 +195,13 @@ double or_phi(double a, double t) {
   if (fabs(tw - (double)twi) > 1e-12) return NAN; /* only a in Z/2 */
   if (t < 0.0 || isnan(t)) return NAN;
   if (t == 0.0) return a < 0.0 ? -1.0 / a : INFINITY;
-  /* negative orders at larger t: the downward recurrence below would lose digits */
-  if (a <= 0.0 && t > 1.0) return or_phi_cf(a, t);
-  double et = exp(-t);
-  if (twi % 2 == 0) {
-    long n = twi / 2;
-    if (n >= 1) {
-      /* Gamma(n,t) = (n-1)! e^{-t} sum_{k<n} t^k/k! */
-      double s = 0.0, term = 1.0;
-      for (long k = 0; k < n; ++k) {
-        s += term;
-        term *= t / (double)(k + 1);
-      }
-      return tgamma((double)n) * et * s * pow(t, -(double)n);
-    }
-    /* Phi_0 = E_1, then Phi_{c-1} = (t Phi_c - e^{-t}) / (c-1) */
-    double phi = or_expint_e1(t);
-    for (long c = 0; c > n; --c) phi = (t * phi - et) / (double)(c - 1);
-    return phi;
-  }
-  /* half-integers from Phi_{1/2}(t) = sqrt(pi/t) erfc(sqrt t) */
-  double phi = sqrt(OR_PI / t) * erfc(sqrt(t));
-  double cur = 0.5;
-  while (cur < a - 0.25) { /* Phi_{c+1} = (c Phi_c + e^{-t}) / t */
-    phi = (cur * phi + et) / t;
-    cur += 1.0;
-  }
-  while (cur > a + 0.25) { /* Phi_{c-1} = (t Phi_c - e^{-t}) / (c-1) */
-    phi = (t * phi - et) / (cur - 1.0);
-    cur -= 1.0;
-  }
-  return phi;
+  return t >= 1.0 ? or_phi_t_ge1(a, t) : or_phi_t_lt1(a, t);
+}
+
+/* E_1(t) = Phi_0(t). */
+double or_expint_e1(double t) {
+  if (!(t > 0.0)) return t == 0.0 ? INFINITY : NAN;
+  return or_phi(0.0, t);
 }
 
 /* is a a non-positive integer (log case of the regularisation)? returns m >= 0 or -1 */
@@ -496,6 +496,8 @@ typedef struct {
   or_points real;   /* 0 < |z| <= r_real */
   double* g;        /* real.n x n_distinct : Phi_{nu/2}(pi |z|^2 / lam^2) */
   or_points rec;    /* |g| <= r_recip + max_BZ |k| */
+  double* phin;     /* rec.n x n_distinct x (2 ell + 1): Phi_{a_j + n}(pi lam^2 |G|^2) for the
+                       near-part Taylor coefficients (ray-independent, so computed once) */
   double* u_nodes;
   double* u_w;
   double* v_nodes;
@@ -549,10 +551,24 @@ static void or_ctx_free(or_ctx* c) {
   or_points_free(&c->real);
   or_points_free(&c->rec);
   free(c->g);
+  free(c->phin);
   free(c->u_nodes);
   free(c->u_w);
   free(c->v_nodes);
   free(c->v_w);
+}
+
+static void or_ctx_phin(or_ctx* c) {
+  const or_problem* P = c->P;
+  int d = c->d, D = 2 * P->ell;
+  c->phin = (double*)malloc(sizeof(double) * (c->rec.n + 1) * P->n_distinct * (D + 1));
+  for (int e = 0; e < c->rec.n; ++e) {
+    double G2 = or_dot(d, c->rec.p + 3 * e, c->rec.p + 3 * e);
+    for (int j = 0; j < P->n_distinct; ++j)
+      for (int n = 0; n <= D; ++n)
+        c->phin[(e * P->n_distinct + j) * (D + 1) + n] =
+            G2 == 0.0 ? 0.0 : or_phi(0.5 * (d - P->nu[j]) + n, OR_PI * P->lam * P->lam * G2);
+  }
 }
 
 static int or_ctx_init(or_ctx* c, const or_problem* P) {
@@ -598,6 +614,7 @@ static int or_ctx_init(or_ctx* c, const or_problem* P) {
     kmax = fmax(kmax, sqrt(or_dot(d, k, k)));
   }
   or_enumerate(d, c->AiT, c->At, zero, P->r_recip + kmax, &c->rec);
+  if (P->u_rule == 2) or_ctx_phin(c);
   int nu_t = or_n_u_total(P);
   c->u_nodes = (double*)malloc(sizeof(double) * nu_t);
   c->u_w = (double*)malloc(sizeof(double) * nu_t);
@@ -782,7 +799,7 @@ static void or_taylor(const or_ctx* c, int j, const double* w, double* C) {
         or_series_mul(dp, delta, dp, D);
         fact *= n;
       }
-      double coef = ((n % 2) ? -1.0 : 1.0) * or_phi(a + n, t0) / fact;
+      double coef = ((n % 2) ? -1.0 : 1.0) * c->phin[(e * P->n_distinct + j) * (D + 1) + n] / fact;
       for (int i = 0; i <= D; ++i) S[i] += coef * dp[i];
     }
     for (int k = 0; k <= ell; ++k) or_acc_add(&rec[k], S[2 * k]);
@@ -804,7 +821,10 @@ static void or_taylor(const or_ctx* c, int j, const double* w, double* C) {
 int or_reg_taylor(const or_problem* P, int j, const double* w, double* C) {
   or_ctx c;
   int rc = or_ctx_init(&c, P);
-  if (!rc) or_taylor(&c, j, w, C);
+  if (!rc) {
+    if (!c.phin) or_ctx_phin(&c);
+    or_taylor(&c, j, w, C);
+  }
   or_ctx_free(&c);
   return rc;
 }

@@ -1,10 +1,12 @@
 """Pins of the oracle's incomplete gamma Phi_a(t) = t^{-a} Gamma(a,t) = E_{1-a}(t).
 
 Phi enters every term of the splitting of Z (real space a = nu/2, reciprocal
-a = (d-nu)/2); the pins are independent of the oracle's closed forms, recurrences
-and continued fractions: scipy's E_n and E_1, numerical quadrature of the defining
-integral int_1^inf s^{a-1} e^{-ts} ds, mpmath's generalized exponential integral,
-and the derivative identity Phi_a' = -Phi_{a+1} used by the Taylor coefficients.
+a = (d-nu)/2, near-part Taylor coefficients a + n).  The oracle evaluates it by
+quadrature of the defining integral int_1^inf s^{a-1} e^{-ts} ds alone; the pins
+are independent of that: scipy's E_n and E_1, adaptive quadrature of the same
+integral by QUADPACK, mpmath's generalized exponential integral at 30 digits, the
+derivative identity Phi_a' = -Phi_{a+1} and the order recurrence
+t Phi_{a+1} = a Phi_a + e^{-t} (integration by parts), which the oracle never uses.
 """
 import math
 
@@ -72,3 +74,27 @@ def test_phi_at_zero(oracle_mod, a):
 
 def test_phi_rejects_non_half_integer(oracle_mod):
     assert math.isnan(oracle_mod.phi(0.3, 1.0))
+
+
+def test_phi_vs_mpmath_dense_grid(oracle_mod):
+    # every order the oracle needs (reciprocal a down to -11/2, Taylor orders a + n up to
+    # a + 2 ell), t from the h = 0 term near k = 0 to beyond every cutoff
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    worst = 0.0
+    for a in [x / 2 for x in range(-13, 29)]:
+        for t in np.logspace(-12, 2.7, 37):
+            ref = mp.expint(1 - a, float(t))
+            got = oracle_mod.phi(a, float(t))
+            worst = max(worst, float(abs(got - ref) / abs(ref)))
+    assert worst < 3e-15, worst
+
+
+@pytest.mark.parametrize("a", [-5.5, -3.0, -1.5, -0.5, 0.0, 0.5, 1.0, 2.5, 6.0])
+def test_phi_order_recurrence(oracle_mod, a):
+    # t Phi_{a+1}(t) = a Phi_a(t) + e^{-t}: integration by parts of the defining integral
+    for t in [1e-3, 0.3, 0.99, 1.0, 2.0, 9.0, 40.0]:
+        lhs = t * oracle_mod.phi(a + 1, t)
+        rhs = a * oracle_mod.phi(a, t) + math.exp(-t)
+        scale = abs(t * oracle_mod.phi(a + 1, t)) + abs(a * oracle_mod.phi(a, t)) + math.exp(-t)
+        assert abs(lhs - rhs) <= 4e-15 * scale, (a, t, lhs, rhs)
