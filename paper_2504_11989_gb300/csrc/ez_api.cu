@@ -829,9 +829,17 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-bool g_init = false;
+// The constants uploaded here (__constant__ tables read by phitab_kernel, the far kernels'
+// shared-memory attributes) live on each device separately: one flag per device ordinal,
+// set under a lock once that device has them.
+std::mutex g_init_mu;
+bool g_init_dev[64] = {false};
 int init_constants() {
-  if (g_init) return EZ_OK;
+  int dev = 0;
+  EZ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(EZ_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_init_mu);
+  if (g_init_dev[dev]) return EZ_OK;
   // Chebyshev -> monomial matrix: T_j(x) = sum_i c[j][i] x^i
   double c[kNC][kNC];
   std::memset(c, 0, sizeof c);
@@ -850,7 +858,7 @@ int init_constants() {
   EZ_CUDA(upload_cheb2mono(&c[0][0], &dct[0][0], xk));
   EZ_CUDA(far_set_smem_limits());
   EZ_CUDA(upload_inv_int());
-  g_init = true;
+  g_init_dev[dev] = true;
   return EZ_OK;
 }
 

@@ -202,6 +202,47 @@ class Lattice:
             self.handle = None
 
 
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _check_zeta_buffers(lat: "Lattice", xv, y, re, im, device_only: bool) -> int:
+    """Checks the caller's buffers of an Epstein zeta call against each other and returns m.
+
+    The C ABI receives bare pointers and cannot see sizes, so an undersized output or a
+    point array of the wrong dimension would make the kernels read or write past the
+    caller's buffers; every such case is rejected here with ValueError."""
+    d = lat.d
+    if xv.size != d:
+        raise ValueError(f"x has {xv.size} components; the lattice has dimension {d}")
+    if isinstance(y, np.ndarray):
+        if y.ndim > 2 or (y.ndim == 2 and y.shape[1] != d) or y.size % d:
+            raise ValueError(f"y must have shape (m, {d}); got {y.shape}")
+    else:
+        if y.dim() > 2 or (y.dim() == 2 and y.shape[1] != d) or y.numel() % d:
+            raise ValueError(f"y must have shape (m, {d}); got {tuple(y.shape)}")
+    m = _numel(y) // d
+    for name, buf in (("re", re), ("im", im)):
+        if buf is not None and _numel(buf) < m:
+            raise ValueError(f"{name} holds {_numel(buf)} values; {m} are needed")
+    bufs = [b for b in (y, re, im) if b is not None]
+    on_gpu = [not isinstance(b, np.ndarray) and b.device.type == "cuda" for b in bufs]
+    if device_only and not all(on_gpu):
+        raise ValueError("y, re and im must be CUDA tensors")
+    if any(on_gpu):
+        import torch
+
+        cur = torch.cuda.current_device()
+        for b, g in zip(bufs, on_gpu):
+            if not g and not isinstance(b, np.ndarray):
+                raise ValueError(f"tensor on {b.device}: use a CUDA tensor or a numpy array")
+            if g and b.device.index != cur:
+                raise ValueError(f"tensor on {b.device}, but the current CUDA device is cuda:{cur}")
+    elif not all(isinstance(b, np.ndarray) for b in bufs):
+        raise ValueError("CPU tensors are not accepted: pass numpy arrays or CUDA tensors")
+    return m
+
+
 def ez_epstein_zeta(lat: Lattice, nu: float, x, y, re=None, im=None, prec: int = EZ_FP64, stream=None):
     """Z_{Lambda,nu}(x, y_i).  y: (m, d) numpy array or CUDA tensor.  Returns (re, im)
     in the same kind of container as y (allocated if not given)."""
@@ -219,6 +260,7 @@ def ez_epstein_zeta(lat: Lattice, nu: float, x, y, re=None, im=None, prec: int =
             re = y.new_zeros(m)
         if im is None:
             im = y.new_zeros(m)
+    m = _check_zeta_buffers(lat, xv, y, re, im, device_only=False)
     yp, _ = _ptr(y)
     rp, _ = _ptr(re)
     ip, _ = _ptr(im)
@@ -231,7 +273,7 @@ def ez_epstein_zeta_static(lat: Lattice, nu: float, x, y, re, im=None, stream=No
     """Z_{Lambda,nu}(x, y_i) without any allocation: y, re, im are CUDA tensors owned by
     the caller; the library's scratch is a 256 KiB static device array (see ezeta.h)."""
     xv = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
-    m = y.shape[0] if y.dim() > 1 else y.numel() // lat.d
+    m = _check_zeta_buffers(lat, xv, y, re, im, device_only=True)
     yp, _ = _ptr(y)
     rp, _ = _ptr(re)
     ip, _ = _ptr(im)

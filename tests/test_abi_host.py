@@ -97,3 +97,30 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ezeta, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         ezeta.lib()
+
+
+def test_epstein_zeta_buffer_checks(ez):
+    # the C ABI gets bare pointers; the binding rejects every size or device mismatch
+    # before a kernel could read or write past the caller's buffers
+    import numpy as np
+    import torch
+
+    lat = ez.Lattice(W.lattice("square"))
+    y = np.zeros((5, 2))
+    with pytest.raises(ValueError, match="x has 3"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0, 0.0], y)
+    with pytest.raises(ValueError, match="shape"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0], np.zeros((5, 3)))
+    with pytest.raises(ValueError, match="shape"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0], np.zeros(7))
+    with pytest.raises(ValueError, match="re holds 4"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0], y, re=np.zeros(4))
+    with pytest.raises(ValueError, match="im holds 2"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0], y, re=np.zeros(5), im=np.zeros(2))
+    with pytest.raises(ValueError, match="CPU tensors"):
+        ez.ez_epstein_zeta(lat, 3.0, [0.0, 0.0], torch.zeros(5, 2, dtype=torch.float64))
+    # the allocation-free entry takes CUDA tensors only
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        ez.ez_epstein_zeta_static(lat, 3.0, [0.0, 0.0], y, np.zeros(5))
+    with pytest.raises(ValueError, match="re holds 1"):
+        ez.ez_epstein_zeta_static(lat, 3.0, [0.0, 0.0], y, np.zeros(1))
