@@ -1,14 +1,22 @@
 #!/usr/bin/env python
-"""Throughput of the Epstein zeta method on GB300: lattice sums/s (and Epstein zeta
-evaluations/s) of the three-body zeta function zeta^(3)(3,3,3) on the square and
-hexagonal lattices (unit density times a seeded lattice constant in [0.9, 1.3]),
-256 x 256 Brillouin-zone grid mapped to 4 Duffy sectors x 128 u x 128 v nodes,
-cutoff radius 6 in real and reciprocal space, FP64.
+"""Throughput of the Epstein zeta method on GB300.
 
-One step = one pass of the whole path (table setup, per-node Epstein zeta, product,
-quadrature reduction) over a batch of 128 sums (64 per lattice).  Prints one JSON line.
+Headline (no flags): the ATM cohesive energy (Prop. in Sec. 2: three three-body zeta
+values, nu = -1, 1, 3, 5, from one pass over the nodes) of the sc, fcc and bcc Bravais
+lattices at unit density, Brillouin-zone grid 128^3 mapped to 12 Duffy sectors x 6 graded
+panels x 8 u nodes x 64^2 v nodes (2.36 M nodes per sum) plus the eps-split near part
+(12 x 64^2 rays), plain FP64 form.  One step = one pass of the whole path (table setup,
+per-node Epstein zeta, products, singular subtraction / near part, quadrature reduction)
+over the three sums.  value = lattice sums (ATM energies) per second.
+
+Nested in the same JSON line: the mixed form of the same workload, the d = 2 three-body
+sums (zeta^(3)(3,3,3) on square and hexagonal, 256^2 grid, 128 sums per step), the d = 3
+chain sums (fcc, nu = 6, n = 3..8, 96^3 grid) with per-factor cost vs n, and the served
+stability scan (10,000 Poisson requests, p50/p99 latency, error against the oracle).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload headline|config1|config2|config3|config4|serve|epstein]
+                  [--split-sum]
 """
 from __future__ import annotations
 
@@ -19,49 +27,47 @@ import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Epstein zeta evals/sec and lattice sums/sec at stated rel. error; p50/p99 latency"
-PER_LATTICE = 64
-LATTICES = ("square", "hexagonal")
-GRID = 256
-R_CUT = 6.0
-NU = 3.0
-N_BODY = 3
-# DRAM bytes (read + write) of one far_kernel_d2 launch of the default 128-sum step, from the
-# full-size ncu capture summarised in profiles/far_kernel_d2_config2.md.  Set to None whenever
-# that kernel changes until re-captured (other batch sizes report null: the shared phase
-# table makes the traffic not proportional to the number of sums).
-FAR_DRAM_BYTES_PER_LAUNCH = 8673536
+UNIT = "lattice_sums/s"
+HEADLINE_LATTICES = ("sc", "fcc", "bcc")
+# Counters of the dominant kernels from the committed ncu summaries (full command in each
+# file).  None when the kernel has changed since the capture.
+PROFILES = {
+    # far_kernel_d3<FP64, 4 exponents>, config 3 (profiles/far_kernel_d3_config3.md)
+    "far_d3_f64_dram_bytes_per_launch": None,
+    # far_kernel_d3<mixed, 4 exponents>: issue-slot and binary32-pipe utilisation
+    "far_d3_mixed_issue_frac": None,
+    "far_d3_mixed_fp32_pipe_frac": None,
+    # far_kernel_d2<FP64, 1 exponent>, config 2, 128 sums (profiles/far_kernel_d2_config2.md)
+    "far_d2_f64_dram_bytes_per_launch": None,
+}
+FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max SM clock
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA lanes x flops x max SM clock
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--per-lattice", type=int, default=PER_LATTICE, help="sums per lattice per step (profiling)")
-    ap.add_argument("--workload", default="config2",
-                    choices=["config2", "serve", "config1", "config3", "config4", "epstein"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "config1", "config2", "config3", "config4", "serve", "epstein"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
+    ap.add_argument("--split-sum", action="store_true",
+                    help="N > 1: split every config-3 sum over the ranks by Duffy line groups")
+    ap.add_argument("--per-lattice", type=int, default=64, help="config 2: sums per lattice per step")
+    ap.add_argument("--no-oracle", action="store_true", help="single configs: skip the oracle lines (profiling)")
     return ap.parse_args()
-
-
-def workload(rank: int, per_lattice: int = PER_LATTICE):
-    """[(lattice name, lattice constant)] of the sums of one step."""
-    from paper_2504_11989_gb300 import workloads as W
-
-    items = []
-    for li, name in enumerate(LATTICES):
-        for s in W.lattice_constants(per_lattice, W.SEED_BASE + 1 + 100 * rank + li):
-            items.append((name, float(s)))
-    return items
 
 
 def job_rate(local_ms: float, sums_per_rank: int, steps: int, dist=None, device: str = "cpu"):
@@ -80,11 +86,21 @@ def job_rate(local_ms: float, sums_per_rank: int, steps: int, dist=None, device:
     return world * sums_per_rank * steps / (ms / 1e3), ms
 
 
-def quad_for(scale: float):
-    from paper_2504_11989_gb300 import workloads as W
+def add_parts_in_rank_order(part_values, dist=None):
+    """Sum of the parts of split sums, added in rank order on every rank (deterministic):
+    part_values is this rank's (n_sums, n_prod) array; returns the whole sums."""
+    import numpy as np
+    import torch
 
-    # lattice constant s scales lambda = V^{1/d} = s and the cutoffs (6 spacings)
-    return W.Quad(n_u=GRID // 2, n_v=GRID // 2, u_rule=1, lam=scale, r_real=R_CUT * scale, r_recip=R_CUT / scale)
+    v = torch.tensor(np.asarray(part_values, dtype=np.float64))
+    if dist is None:
+        return v.numpy()
+    gathered = [torch.zeros_like(v) for _ in range(dist.get_world_size())]
+    dist.all_gather(gathered, v)
+    total = gathered[0].clone()
+    for g in gathered[1:]:
+        total += g
+    return total.numpy()
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -132,83 +148,219 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-# ----------------------------------------------------------------------------- CPU oracle
-def oracle_sums(items, seconds: float, threads: int):
-    """Oracle on the first sums of the workload until `seconds` have elapsed."""
+# ----------------------------------------------------------------------------- workloads
+def headline_problems():
+    """Config 3: ATM on sc, fcc, bcc at unit density, default splitting parameter."""
+    from paper_2504_11989_gb300 import workloads as W
+
+    return [W.atm_problem(n, W.Quad(n_u=8, n_v=64, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0))
+            for n in HEADLINE_LATTICES]
+
+
+def headline_config():
+    return {"workload": "config 3: ATM cohesive energy (three three-body zeta values, nu = -1,1,3,5) on sc, fcc, "
+                        "bcc at unit density; 128^3 BZ grid -> 12 sectors x 6 graded panels x 8 u x 64^2 v = "
+                        "2,359,296 far nodes + 12 x 64^2 near-part rays per sum; eps = 1e-2, ell = 4; default "
+                        "splitting parameter and cutoffs (e^-45)",
+            "global_batch": len(HEADLINE_LATTICES), "nodes_per_sum": 12 * 6 * 8 * 64 * 64,
+            "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps"}
+
+
+def config2_problems(rank: int, per_lattice: int):
+    from paper_2504_11989_gb300 import workloads as W
+
+    probs = []
+    for li, name in enumerate(("square", "hexagonal")):
+        for s in W.lattice_constants(per_lattice, W.SEED_BASE + 1 + 100 * rank + li):
+            s = float(s)
+            q = W.Quad(n_u=128, n_v=128, u_rule=1, lam=s, r_real=6.0 * s, r_recip=6.0 / s)
+            probs.append(W.nbody_problem(name, 3.0, 3, q, scale=s))
+    return probs
+
+
+def config1_problems():
+    from paper_2504_11989_gb300 import workloads as W
+
+    return [W.nbody_problem("Z", 4.0, 3, W.Quad(n_u=4096, n_v=1, u_rule=1, lam=s, r_real=8 * s, r_recip=8 / s),
+                            scale=s) for s in map(float, W.lattice_constants(1024, W.SEED_BASE + 11))]
+
+
+def config4_problems():
+    from paper_2504_11989_gb300 import workloads as W
+
+    return [W.nbody_problem("fcc", 6.0, n, W.Quad(n_u=32, n_v=48, u_rule=1, lam=0.0, r_real=0.0, r_recip=0.0))
+            for n in (3, 4, 5, 6, 8)]
+
+
+# ----------------------------------------------------------------------------- GPU timing
+class Ctx:
+    def __init__(self, local: int):
+        import torch
+
+        from paper_2504_11989_gb300 import build, ezeta
+
+        torch.cuda.set_device(local)
+        build.build()
+        self.torch, self.ez = torch, ezeta
+        self.stream = torch.cuda.Stream()
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+
+def time_batch(C: Ctx, probs, prec: int, steps: int, warmup: int, part=(0, 1), lines=False, extra_quad=None):
+    """Runs ez_batch_run `warmup` times, then `steps` timed runs (CUDA events on the launching
+    stream, L2 flushed between them outside the events).  Returns a dict of results."""
+    torch, ez = C.torch, C.ez
+    lats = [ez.Lattice(p.A) for p in probs]
+    specs = [ez.sum_spec(p.nu, p.expo) for p in probs]
+    kw = dict(prec=prec, part=part[0], n_parts=part[1])
+    if extra_quad:
+        kw.update(extra_quad)
+    quads = [ez.quadrature(p.quad, **kw) for p in probs]
+    batch = ez.Batch(lats, specs, quads, stream=C.stream)
+    out = torch.zeros(len(probs) * ez.EZ_MAX_PROD, dtype=torch.float64, device="cuda")
+    for _ in range(max(3, warmup)):
+        batch.run(out, C.stream)
+    torch.cuda.synchronize()
+    batch.timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    far = []
+    launches0 = ez.ez_launch_count()
+    with torch.cuda.stream(C.stream):
+        for k in range(steps):
+            C.flush.fill_(k & 0xFF)
+            ev[k][0].record(C.stream)
+            batch.run(out, C.stream)
+            ev[k][1].record(C.stream)
+            far.append(batch.timing(True)[0])
+    torch.cuda.synchronize()
+    launches = ez.ez_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    flops, terms, coefs = batch.far_flops()
+    res = {"vals": out.view(len(probs), ez.EZ_MAX_PROD).cpu().numpy().copy(), "step_ms": step_ms,
+           "ms": sum(step_ms) / steps, "far_ms": sum(far) / steps, "flops": flops, "terms": terms, "coefs": coefs,
+           "launches": launches // steps, "lats": lats, "specs": specs, "quads": quads}
+    if lines:
+        res["lines"], res["offs"] = batch.lines()
+    return res
+
+
+def oracle_line_errors(probs, res, n_lines: int, seed: int, threads: int, shells: float = 4.5):
+    """Largest relative error of sampled quadrature lines of the GPU sums against the oracle
+    (each line relative to max(|line|, largest line of its sum)), and the oracle's seconds.
+    The oracle lines run in parallel host threads (ctypes releases the GIL)."""
+    import numpy as np
+
     import oracle
     from paper_2504_11989_gb300 import workloads as W
 
     oracle.build()
-    vals, t0 = [], time.perf_counter()
-    for name, s in items:
-        prob = W.nbody_problem(name, NU, N_BODY, quad_for(s), scale=s)
-        vals.append(float(oracle.nbody(prob, threads=threads)[0]))
-        if time.perf_counter() - t0 >= seconds:
-            break
-    return vals, time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i, p in enumerate(probs):
+        pe = W.explicit_splitting(p, shells=shells)
+        ns, nu_t = oracle.n_sectors(pe), oracle.n_u_total(pe)
+        for _ in range(n_lines):
+            jobs.append((i, pe, int(rng.integers(ns)), int(rng.integers(nu_t)), nu_t))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        refs = list(ex.map(lambda j: oracle.nbody_line(j[1], j[2], j[3]), jobs))
+    dt = time.perf_counter() - t0
+    worst = 0.0
+    for (i, pe, sct, iu, nu_t), ref in zip(jobs, refs):
+        lines, offs = res["lines"], res["offs"]
+        row = lines[offs[i] + sct * nu_t + iu, : len(ref)]
+        scale = np.max(np.abs(lines[offs[i]: offs[i + 1], : len(ref)]), axis=0)
+        worst = max(worst, float(np.max(np.abs(row - ref) / np.maximum(np.abs(ref), scale))))
+    return worst, dt, len(jobs)
 
 
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    threads = os.cpu_count() or 1
-    items = workload(0)
-    per_step = max(1, int(args.cpu_seconds / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_sums(items[:1], 0.0, threads)
-    times, n_done = [], 0
-    for k in range(args.steps):
-        sub = items[(k * per_step) % len(items):][:per_step]
-        vals, dt = oracle_sums(sub, 1e9, threads)
-        times.append(dt)
-        n_done += len(vals)
-    total = sum(times)
-    value = n_done / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lattice_sums/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic lattices (seeded lattice constants)",
-            "config": config_dict(),
-            "cpu_baseline": {"value": value, "unit": "lattice_sums/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} full sum(s) per step of the same workload"},
-            "e2e": {"value": value, "unit": "lattice_sums/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+def oracle_rate_config3(seconds: float, threads: int):
+    """The oracle on the headline workload: sampled full-size far lines of the three sums
+    (the same Duffy lines the GPU computes), run in `threads` host threads for about
+    `seconds`, extrapolated to whole sums (far lines of a sum x measured seconds per line,
+    plus its 12 near-part lines at their measured cost)."""
+    import numpy as np
+
+    import oracle
+    from paper_2504_11989_gb300 import workloads as W
+
+    oracle.build()
+    probs = [W.explicit_splitting(p, shells=4.5) for p in headline_problems()]
+    rng = np.random.default_rng(W.SEED_BASE + 33)
+    ns, nu_t = oracle.n_sectors(probs[0]), oracle.n_u_total(probs[0])
+    # near lines first (one per lattice), then far lines in rounds of `threads`
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda p: oracle.nbody_line(p, int(rng.integers(ns)), -1), probs))
+    near_s = (time.perf_counter() - t0) / len(probs) * min(threads, len(probs))  # seconds of one core per line
+    far_lines, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or far_lines == 0:
+        jobs = [(probs[int(rng.integers(3))], int(rng.integers(ns)), int(rng.integers(nu_t))) for _ in range(threads)]
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda j: oracle.nbody_line(*j), jobs))
+        far_lines += len(jobs)
+    far_s_core = (time.perf_counter() - t1) * threads / far_lines  # seconds of one core per far line
+    sum_core_s = ns * nu_t * far_s_core + ns * near_s
+    value = threads / sum_core_s
+    return value, {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
+                   "sample": f"{far_lines} full-size far lines + 3 near-part lines of the three sums, "
+                             f"{threads} host threads; extrapolated to whole sums ({ns * nu_t} far + {ns} near "
+                             f"lines each)", "seconds": time.perf_counter() - t0}
 
 
-def config_dict(per_lattice: int = PER_LATTICE):
-    return {"workload": "zeta^(3)(3,3,3) on square+hexagonal lattices, 256^2 BZ grid (4x128x128 Duffy nodes), "
-                        f"cutoff radius 6, {per_lattice} lattice constants per lattice per step",
-            "global_batch": len(LATTICES) * per_lattice, "nodes_per_sum": 4 * (GRID // 2) ** 2,
-            "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps"}
+def fp64_roofline(res, kernel: str, dram_bytes, probe: float):
+    achieved = res["flops"] / (res["far_ms"] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_NOMINAL, "traffic": dram_bytes,
+            "peak_source": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal unit counts and clock; "
+                           f"DFMA probe in this run {probe:.3f} TFLOP/s)",
+            "far_ms_per_launch": res["far_ms"], "flops_per_launch": res["flops"],
+            "recip_terms_per_launch": res["terms"], "mean_poly_len": res["coefs"] / max(1, res["terms"])}
+
+
+# ----------------------------------------------------------------------------- e2e
+def e2e_rate(C: Ctx, probs, prec: int, steps: int, dist=None):
+    """The same sums through the one-shot C ABI call with host buffers: planning, upload of
+    the descriptors from pinned staging, every kernel, download of the values."""
+    import numpy as np
+
+    ez = C.ez
+    lats = [ez.Lattice(p.A) for p in probs]
+    specs = [ez.sum_spec(p.nu, p.expo) for p in probs]
+    quads = [ez.quadrature(p.quad, prec=prec) for p in probs]
+    host_out = np.zeros((len(probs), ez.EZ_MAX_PROD))
+    ez.ez_lattice_sums(lats, specs, quads, out=host_out)
+    C.torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ez.ez_lattice_sums(lats, specs, quads, out=host_out)
+    rate, _ = job_rate(1e3 * (time.perf_counter() - t0), len(probs), steps, dist, "cuda")
+    batch = ez.Batch(lats, specs, quads)
+    _, staging = batch.sizes()
+    return rate, host_out, int(staging)
 
 
 # ----------------------------------------------------------------------------- serving
-def run_serve(args):
-    """Served stability scan: `--requests` lattice sums with random d, lattice, lattice
-    constant, exponent (or the ATM form), n and BZ resolution, mixed precision.  The same
-    requests run saturated in the plain FP64 form first (reference rate and values), then
-    saturated in the mixed form (sums/s, error against FP64), then on Poisson arrivals at
-    0.8x the mixed saturated rate (latency percentiles)."""
-    import threading
-
+def serve_block(C: Ctx, n_requests: int, oracle_sample: int = 64, threads: int = 16):
+    """Served stability scan: n_requests lattice sums with random d, lattice, lattice
+    constant, exponent (or the ATM form), n and BZ resolution.  Saturated in the FP64 form,
+    saturated in the mixed form, then the mixed form on Poisson arrivals at 0.8x its
+    saturated rate (per-request latency = completion - submission).  Errors: mixed vs FP64
+    on every request; and, on a sample, every served value equals the same request run
+    alone, whose sampled quadrature lines are checked against the oracle."""
     import numpy as np
-    import torch
 
-    from paper_2504_11989_gb300 import build, ezeta
+    ez = C.ez
     from paper_2504_11989_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
-    reqs = W.serving_mix(args.requests, W.SEED_BASE + 5, 1.0)
-    made, made64 = [], []
-    for r in reqs:
-        p = W.request_problem(r)
-        made.append(ezeta.make_request(p.A, p.nu, p.expo, ezeta.quadrature(p.quad, prec=ezeta.EZ_MIXED), r.rid))
-        made64.append(ezeta.make_request(p.A, p.nu, p.expo, ezeta.quadrature(p.quad, prec=ezeta.EZ_FP64), r.rid))
+    reqs = W.serving_mix(n_requests, W.SEED_BASE + 5, 1.0)
+    probs = [W.request_problem(r) for r in reqs]
+    made = {prec: [ez.make_request(p.A, p.nu, p.expo, ez.quadrature(p.quad, prec=prec), r.rid)
+                   for r, p in zip(reqs, probs)] for prec in (ez.EZ_FP64, ez.EZ_MIXED)}
     budget = 16 << 30
 
-    def run(arrivals, made=made):
-        srv = ezeta.Server(budget, n_streams=4, max_batch=256)
+    def run(arrivals, made):
+        srv = ez.Server(budget, n_streams=4, max_batch=256)
         warm = [srv.submit(made[i]) for i in range(16)]
         for t in warm:
             srv.wait(t, 600000)
@@ -232,132 +384,228 @@ def run_serve(args):
         srv.close()
         return res, wall, st
 
-    res64, wall64, _ = run(None, made64)  # the plain FP64 form, saturated, same requests
-    res_sat, wall_sat, st_sat = run(None)
-    sat_rate = len(made) / wall_sat
+    res64, wall64, _ = run(None, made[ez.EZ_FP64])
+    res_sat, wall_sat, st_sat = run(None, made[ez.EZ_MIXED])
+    sat_rate = n_requests / wall_sat
     rel = []
     for a, b in zip(res_sat, res64):
         va, vb = np.asarray(a.value, dtype=float), np.asarray(b.value, dtype=float)
         ok = np.isfinite(vb) & (vb != 0)
         rel.append(float(np.max(np.abs(va[ok] - vb[ok]) / np.abs(vb[ok]))) if ok.any() else 0.0)
     rate = 0.8 * sat_rate
-    arrivals = np.cumsum(np.random.default_rng(W.SEED_BASE + 6).exponential(1.0 / rate, size=len(made)))
-    res, wall, st = run(arrivals)
+    arrivals = np.cumsum(np.random.default_rng(W.SEED_BASE + 6).exponential(1.0 / rate, size=n_requests))
+    res, wall, st = run(arrivals, made[ez.EZ_MIXED])
     lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
-    failed = sum(1 for r in res + res_sat if r.status != 0)
-    line = {"metric": METRIC, "workload": "served stability scan (config 5)", "value": len(made) / wall,
-            "unit": "lattice_sums/s", "saturated_value": sat_rate, "offered_rate": rate,
+    failed = sum(1 for r in res + res_sat + res64 if r.status != 0)
+    # oracle sample: served == alone (bitwise), alone lines vs oracle lines
+    rng = np.random.default_rng(W.SEED_BASE + 7)
+    pick = sorted(rng.choice(n_requests, size=min(oracle_sample, n_requests), replace=False).tolist())
+    worst = {"f64": 0.0, "mixed": 0.0}
+    same = True
+    t0 = time.perf_counter()
+    for tag, prec, served in (("f64", ez.EZ_FP64, res64), ("mixed", ez.EZ_MIXED, res_sat)):
+        sub = [probs[i] for i in pick]
+        lats = [ez.Lattice(p.A) for p in sub]
+        specs = [ez.sum_spec(p.nu, p.expo) for p in sub]
+        quads = [ez.quadrature(p.quad, prec=prec) for p in sub]
+        out, lines, offs = ez.ez_lattice_sums(lats, specs, quads, lines=True)
+        for k, i in enumerate(pick):
+            npr = len(sub[k].expo)
+            same &= bool(np.array_equal(out[k, :npr], np.asarray(served[i].value[:npr])))
+        e, _, _ = oracle_line_errors(sub, {"lines": lines, "offs": offs}, 1, W.SEED_BASE + 8, threads)
+        worst[tag] = e
+    oracle_s = time.perf_counter() - t0
+    return {"workload": "config 5: served stability scan, " + f"{n_requests} requests (d in 1..3, sc/fcc/bcc/"
+                        "square/hexagonal/Z, lattice constant U[0.9,1.3], nu in {4,6,9,12} or ATM, n in {2,3}, "
+                        "BZ resolution in {64..256} (d=3 <= 128))",
+            "value": n_requests / wall, "unit": UNIT, "offered_rate": rate,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "fp64_saturated_value": len(made64) / wall64, "speedup_vs_fp64_saturated": wall64 / wall_sat,
-            "max_rel_err_vs_fp64": max(rel), "median_rel_err_vs_fp64": float(np.median(rel)),
-            "n_requests": len(made), "failed": failed, "dtype": "f32 tails + float-float heads", "n_gpus": 1,
-            "higher_is_better": True, "data": "synthetic request stream (seeded)",
+                           "max": float(lat.max()), "unit": "per request (completion - submission)"},
+            "mixed_saturated_value": sat_rate, "fp64_saturated_value": n_requests / wall64,
+            "mixed_vs_fp64_saturated": wall64 / wall_sat,
+            "max_rel_err_mixed_vs_fp64": max(rel), "median_rel_err_mixed_vs_fp64": float(np.median(rel)),
+            "oracle_sample": {"requests": len(pick), "served_equals_alone": same,
+                              "max_line_rel_err_f64": worst["f64"], "max_line_rel_err_mixed": worst["mixed"],
+                              "seconds": oracle_s,
+                              "how": "each sampled request run alone (bitwise equal to its served value), one "
+                                     "random quadrature line of it against the oracle"},
+            "failed": failed, "dtype": "mixed (binary32 tails, float-float heads, binary64 near origin)",
             "server": {"streams": 4, "max_batch": 256, "budget_bytes": budget, "ticks": st.ticks,
                        "max_batch_seen": st.max_batch_seen, "gpu_busy_fraction": st.busy_seconds / wall,
                        "peak_device_bytes": st.peak_device_bytes, "saturated_ticks": st_sat.ticks}}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle (the plain FP64 CPU program) on the headline workload's config, metric and
+    unit, timed on the host cores: each step is a bounded sample of sampled full-size lines
+    extrapolated to whole sums."""
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rate_config3(0.0, threads)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, info = oracle_rate_config3(per_step, threads)
+        vals.append(v)
+        secs += info["seconds"]
+    value = len(vals) / sum(1.0 / v for v in vals)  # sums per second over the steps
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value * len(HEADLINE_LATTICES),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (lattice presets of the paper at unit density)", "config": headline_config(),
+            "cpu_baseline": dict(info, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-# ----------------------------------------------------------------------------- other configs
-def _time_batch(ezeta, torch, lats, specs, quads, steps, warmup, stream, flush):
-    batch = ezeta.Batch(lats, specs, quads, stream=stream)
-    out = torch.zeros(len(lats) * ezeta.EZ_MAX_PROD, dtype=torch.float64, device="cuda")
-    for _ in range(max(3, warmup)):
-        batch.run(out, stream)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    batch.timing(True)
-    far = []
-    with torch.cuda.stream(stream):
-        for k in range(steps):
-            flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            batch.run(out, stream)
-            ev[k][1].record(stream)
-            far.append(batch.timing(True)[0])
-    torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    vals = out.view(len(lats), ezeta.EZ_MAX_PROD).cpu().numpy().copy()
-    flops = batch.far_flops()[0]
-    lines, offs = batch.lines()
-    return vals, sum(ms) / steps, sum(far) / steps, flops, lines, offs
-
-
-def run_config(args):
-    """Configs 1, 3, 4 of the workload list, FP64 and mixed form, one JSON line each."""
+# ----------------------------------------------------------------------------- headline
+def run_headline(args, rank, world, local):
     import numpy as np
     import torch
 
-    import oracle
-    from paper_2504_11989_gb300 import build, ezeta
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    C = Ctx(local)
+    ez = C.ez
+    probs = headline_problems()
+    split = args.split_sum and world > 1
+    part = (rank, world) if split else (0, 1)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    r64 = time_batch(C, probs, ez.EZ_FP64, args.steps, args.warmup, part=part, lines=(world == 1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    if split:  # strong scaling: each sum's parts on all ranks; the job's sums = the 3 sums
+        value, total_ms = job_rate(sum(r64["step_ms"]), len(probs), args.steps, dist, "cuda")
+        value /= world
+        vals = add_parts_in_rank_order(r64["vals"], dist)
+    else:
+        value, total_ms = job_rate(sum(r64["step_ms"]), len(probs), args.steps, dist, "cuda")
+        vals = r64["vals"]
+    probe = ez.ez_diag_fp64_peak(C.stream)
+    nodes = headline_config()["nodes_per_sum"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (lattice presets of the paper at unit density)",
+        "config": dict(headline_config(), parallelism="one sum split over ranks by Duffy line groups" if split
+                       else "independent sums per GPU"),
+        "zeta_evals_per_s": {"per_factor": value * nodes * 9, "distinct_nu": value * nodes * 4},
+        "gpu_launches": int(r64["launches"]) * args.steps,
+        "roofline": fp64_roofline(r64, "far_kernel_d3<FP64, 4 exponents>",
+                                  PROFILES["far_d3_f64_dram_bytes_per_launch"], probe),
+        "clocks": clocks,
+        "atm_energy": [float(v[0] / 24 - 3 * v[1] / 16 + 3 * v[2] / 8) for v in vals],
+    }
+    if world == 1:
+        threads = os.cpu_count() or 1
+        # end to end through the C ABI with host buffers
+        e2e, host_vals, staging = e2e_rate(C, probs, ez.EZ_FP64, max(2, min(args.steps, 5)))
+        assert np.array_equal(host_vals[:, :3], r64["vals"][:, :3]), "batch and one-shot paths disagree"
+        line["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": staging,
+                       "d2h_bytes_per_step": len(probs) * ez.EZ_MAX_PROD * 8}
+        # mixed form of the same workload
+        rmx = time_batch(C, probs, ez.EZ_MIXED, args.steps, args.warmup, lines=True)
+        p32 = ez.ez_diag_fp32_peak(C.stream)
+        e_f64, cpu_s1, n1 = oracle_line_errors(probs, r64, 4, 4, threads)
+        e_mix, cpu_s2, _ = oracle_line_errors(probs, rmx, 4, 4, threads)
+        line["rel_err_vs_oracle"] = e_f64
+        line["rel_err_vs_oracle_how"] = f"{n1} sampled full-size quadrature lines, relative to the largest line"
+        line["mixed"] = {
+            "value": len(probs) / (rmx["ms"] * 1e-3), "unit": UNIT, "ms_per_step": rmx["ms"],
+            "speedup_vs_fp64": r64["ms"] / rmx["ms"], "far_ms_per_step": rmx["far_ms"],
+            "max_line_rel_err_vs_oracle": e_mix,
+            "max_rel_err_vs_fp64": float(np.max(np.abs(rmx["vals"][:, :3] - r64["vals"][:, :3]) /
+                                                np.abs(r64["vals"][:, :3]))),
+            "dtype": "binary32 tails + float-float heads; binary64 near-origin term, near part, reductions",
+            "roofline": {"bound": "alu (binary32 issue)", "kernel": "far_kernel_d3<mixed, 4 exponents>",
+                         "issue_frac_ncu": PROFILES["far_d3_mixed_issue_frac"],
+                         "fp32_pipe_frac_ncu": PROFILES["far_d3_mixed_fp32_pipe_frac"],
+                         "fp32_peak_measured_tflops": p32, "fp32_peak_nominal_tflops": FP32_PEAK_NOMINAL,
+                         "far_ms_per_launch": rmx["far_ms"]}}
+        # config 2 (d = 2 three-body sums, 128 per step)
+        c2 = config2_problems(0, args.per_lattice)
+        r2 = time_batch(C, c2, ez.EZ_FP64, max(5, args.steps // 2), args.warmup)
+        r2m = time_batch(C, c2, ez.EZ_MIXED, max(5, args.steps // 2), args.warmup)
+        line["config2"] = {
+            "workload": "config 2: zeta^(3)(3,3,3) on square + hexagonal (unit density x s, s in U[0.9,1.3]), "
+                        "256^2 BZ grid -> 4 x 128 x 128 Duffy nodes, cutoff radius 6, "
+                        f"{len(c2)} sums per step",
+            "value": len(c2) / (r2["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r2["ms"],
+            "mixed_value": len(c2) / (r2m["ms"] * 1e-3), "mixed_speedup_vs_fp64": r2["ms"] / r2m["ms"],
+            "mixed_max_rel_err_vs_fp64": float(np.max(np.abs(r2m["vals"][:, 0] - r2["vals"][:, 0]) /
+                                                      np.abs(r2["vals"][:, 0]))),
+            "roofline": fp64_roofline(r2, "far_kernel_d2<FP64, 1 exponent>",
+                                      PROFILES["far_d2_f64_dram_bytes_per_launch"], probe)}
+        # config 4 (fcc nu = 6 chains, n = 3..8), distinct-nu and per-factor evaluation
+        c4 = config4_problems()
+        r4 = time_batch(C, c4, ez.EZ_FP64, max(5, args.steps // 2), args.warmup)
+        r4m = time_batch(C, c4, ez.EZ_MIXED, max(5, args.steps // 2), args.warmup)
+        per_factor = []
+        for p in c4:
+            n = p.expo[0][0]
+            pf = W_nbody_per_factor(p, n)
+            rp = time_batch(C, [pf], ez.EZ_FP64, 5, 3, extra_quad={"dedupe": 0})
+            per_factor.append({"n": n, "ms": rp["ms"]})
+        line["config4"] = {
+            "workload": "config 4: zeta^(n)(6,..,6) on fcc (unit density), n = 3,4,5,6,8; 96^3 BZ grid -> 12 x 32 "
+                        "u x 48^2 v nodes; default splitting parameter and cutoffs",
+            "value": len(c4) / (r4["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r4["ms"],
+            "mixed_value": len(c4) / (r4m["ms"] * 1e-3), "mixed_speedup_vs_fp64": r4["ms"] / r4m["ms"],
+            "per_factor_ms_vs_n": per_factor}
+        # served stability scan
+        line["served"] = serve_block(C, args.requests, 64, threads)
+        if not args.no_cpu_baseline:
+            _, line["cpu_baseline"] = oracle_rate_config3(args.cpu_seconds, threads)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def W_nbody_per_factor(p, n):
+    """The chain sum p with one Epstein zeta evaluation per factor (n distinct entries)."""
     from paper_2504_11989_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
-    oracle.build()
-    stream = torch.cuda.Stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    auto = dict(lam=0.0, r_real=0.0, r_recip=0.0)
-    if args.workload == "config1":
-        probs = []
-        for s in W.lattice_constants(1024, W.SEED_BASE + 11):
-            probs.append(W.nbody_problem("Z", 4.0, 3, W.Quad(n_u=4096, n_v=1, u_rule=1, lam=s, r_real=8 * s,
-                                                            r_recip=8 / s), scale=s))
-        label = "zeta^(3)_Z(4,4,4), 4096 GL nodes on [0,1/2], 8 shells, 1024 lattice constants per step"
-    elif args.workload == "config3":
-        probs = [W.atm_problem(n, W.Quad(n_u=8, n_v=64, u_rule=2, **auto)) for n in ("sc", "fcc", "bcc")]
-        label = "ATM energy on sc, fcc, bcc (unit density), 12 sectors x 48 u x 64^2 v nodes + eps-split near part"
-    else:
-        probs = [W.nbody_problem("fcc", 6.0, n, W.Quad(n_u=32, n_v=48, u_rule=1, **auto)) for n in (3, 4, 5, 6, 8)]
-        label = "zeta^(n)(6,..,6) on fcc, n = 3,4,5,6,8, 12 sectors x 32 u x 48^2 v nodes"
-    lats = [ezeta.Lattice(p.A) for p in probs]
-    specs = [ezeta.sum_spec(p.nu, p.expo) for p in probs]
-    res = {}
-    for prec, tag in ((ezeta.EZ_FP64, "f64"), (ezeta.EZ_MIXED, "mixed")):
-        quads = [ezeta.quadrature(p.quad, prec=prec) for p in probs]
-        res[tag] = _time_batch(ezeta, torch, lats, specs, quads, args.steps, args.warmup, stream, flush)
-    per_factor = None
-    if args.workload == "config4":
-        quads = [ezeta.quadrature(p.quad, dedupe=0) for p in probs]
-        specs_pf = [ezeta.sum_spec([6.0] * p.expo[0][0], [[1] * p.expo[0][0]]) for p in probs]
-        per_factor = []
-        for i in range(len(probs)):
-            _, ms1, _, _, _, _ = _time_batch(ezeta, torch, [lats[i]], [specs_pf[i]], [quads[i]], 3, 3, stream, flush)
-            per_factor.append({"n": probs[i].expo[0][0], "ms": ms1})
-    # sampled oracle lines (full-size sums): first product, a few far lines of each sum
-    rng = np.random.default_rng(4)
-    worst = {"f64": 0.0, "mixed": 0.0}
-    t0 = time.perf_counter()
-    for i, p in enumerate(W.explicit_splitting(p) for p in probs[:3]):
-        ns, nu_t = oracle.n_sectors(p), oracle.n_u_total(p)
-        for _ in range(2 if args.workload != "config1" else 8):
-            sct, iu = int(rng.integers(ns)), int(rng.integers(nu_t))
-            ref = oracle.nbody_line(p, sct, iu)
-            for tag in worst:
-                _, _, _, _, lines, offs = res[tag]
-                row = lines[offs[i] + sct * nu_t + iu, : len(ref)]
-                scale = np.max(np.abs(lines[offs[i]: offs[i + 1], : len(ref)]), axis=0)
-                worst[tag] = max(worst[tag], float(np.max(np.abs(row - ref) / np.maximum(np.abs(ref), scale))))
-    cpu_s = time.perf_counter() - t0
-    for tag in ("f64", "mixed"):
-        vals, ms, far_ms, flops, _, _ = res[tag]
-        line = {"metric": METRIC, "workload": args.workload, "config": label, "dtype": tag, "sums_per_step": len(probs),
-                "value": len(probs) / (ms / 1e3), "unit": "lattice_sums/s", "ms_per_step": ms,
-                "far_ms_per_step": far_ms, "far_tflops_algorithmic": flops / (far_ms * 1e-3) / 1e12,
-                "max_line_rel_err_vs_oracle": worst[tag], "oracle_lines_seconds": cpu_s,
-                "values": [list(map(float, v[: len(p.expo)])) for v, p in zip(vals, probs)][:6]}
-        if args.workload == "config3":
-            line["atm_energy"] = [float(v[0] / 24 - 3 * v[1] / 16 + 3 * v[2] / 8) for v in vals]
-        if tag == "mixed":
-            line["speedup_vs_f64"] = res["f64"][1] / ms
-        if per_factor is not None and tag == "f64":
-            line["per_factor_ms_vs_n"] = per_factor
-        print(json.dumps(line))
+    return W.Problem(p.name + ":per-factor", p.A, [6.0] * n, [[1] * n], p.quad)
 
 
-# ----------------------------------------------------------------------------- Epstein zeta
-def run_epstein(args):
+# ----------------------------------------------------------------------------- single configs
+def run_single(args, local):
+    """One config alone (FP64 and mixed lines) -- profiling and exploration."""
+    import numpy as np
+
+    C = Ctx(local)
+    ez = C.ez
+    probs = {"config1": config1_problems, "config2": lambda: config2_problems(0, args.per_lattice),
+             "config3": headline_problems, "config4": config4_problems}[args.workload]()
+    threads = os.cpu_count() or 1
+    for tag, prec in (("f64", ez.EZ_FP64), ("mixed", ez.EZ_MIXED)):
+        r = time_batch(C, probs, prec, args.steps, args.warmup, lines=True)
+        err, cpu_s, n = (None, 0.0, 0) if args.no_oracle else oracle_line_errors(
+            probs[:3], r, 2 if args.workload != "config1" else 8, 4, threads)
+        print(json.dumps({"metric": METRIC, "workload": args.workload, "dtype": tag, "sums_per_step": len(probs),
+                          "value": len(probs) / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"],
+                          "far_ms_per_step": r["far_ms"],
+                          "far_tflops_algorithmic": r["flops"] / (r["far_ms"] * 1e-3) / 1e12,
+                          "launches_per_step": r["launches"], "max_line_rel_err_vs_oracle": err,
+                          "oracle_lines": n, "oracle_lines_seconds": cpu_s,
+                          "values": [list(map(float, v[: len(p.expo)])) for v, p in zip(r["vals"], probs)][:6]}))
+
+
+def run_epstein(args, local):
     """ez_epstein_zeta alone: 2^20 points y uniform in the Brillouin zone per call (device
     buffers), x = 0 and x uniform in the unit cell, d = 1, 2, 3; evaluations/s, and the
     largest error of 256 sampled points against the oracle relative to max(1, |Z|)."""
@@ -365,45 +613,40 @@ def run_epstein(args):
     import torch
 
     import oracle
-    from paper_2504_11989_gb300 import build, ezeta
     from paper_2504_11989_gb300 import workloads as W
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
+    C = Ctx(local)
+    ez = C.ez
     oracle.build()
     m = 1 << 20
-    stream = torch.cuda.Stream()
     rng = np.random.default_rng(W.SEED_BASE + 21)
-    cases = [("Z", 4.0), ("hexagonal", 3.0), ("fcc", 6.0), ("sc", 4.0)]
-    for lat_name, nu in cases:
+    for lat_name, nu in [("Z", 4.0), ("hexagonal", 3.0), ("fcc", 6.0), ("sc", 4.0)]:
         A = W.lattice(lat_name)
         d = A.shape[0]
-        L = ezeta.Lattice(A)
+        L = ez.Lattice(A)
         Ait = np.linalg.inv(A).T
         for xkind in ("x=0", "x in cell"):
-            kt = rng.uniform(-0.5, 0.5, size=(m, d))
-            y = kt @ Ait.T  # y = A^{-T} k~
+            y = rng.uniform(-0.5, 0.5, size=(m, d)) @ Ait.T
             x = np.zeros(d) if xkind == "x=0" else A @ rng.uniform(0.0, 1.0, size=d)
             yd = torch.tensor(y, dtype=torch.float64, device="cuda")
             re = torch.empty(m, dtype=torch.float64, device="cuda")
             im = torch.empty(m, dtype=torch.float64, device="cuda")
-            with torch.cuda.stream(stream):
+            with torch.cuda.stream(C.stream):
                 for _ in range(max(3, args.warmup)):
-                    ezeta.ez_epstein_zeta(L, nu, x, yd, re, im, stream=stream)
+                    ez.ez_epstein_zeta(L, nu, x, yd, re, im, stream=C.stream)
             torch.cuda.synchronize()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-            with torch.cuda.stream(stream):
+            with torch.cuda.stream(C.stream):
                 for k in range(args.steps):
-                    ev[k][0].record(stream)
-                    ezeta.ez_epstein_zeta(L, nu, x, yd, re, im, stream=stream)
-                    ev[k][1].record(stream)
+                    ev[k][0].record(C.stream)
+                    ez.ez_epstein_zeta(L, nu, x, yd, re, im, stream=C.stream)
+                    ev[k][1].record(C.stream)
             torch.cuda.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
             idx = rng.choice(m, size=256, replace=False)
             got = re.cpu().numpy()[idx] + 1j * im.cpu().numpy()[idx]
             lam = abs(np.linalg.det(A)) ** (1.0 / d)
             ref = np.array([oracle.epstein_zeta(A, nu, x, y[i], lam, 9.0 * lam, 9.0 / lam) for i in idx])
-            # relative to max(1, |Z|), as the parity tests (Z crosses zero inside the zone)
             err = float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)))
             print(json.dumps({"metric": METRIC, "workload": "epstein", "lattice": lat_name, "d": d, "nu": nu,
                               "x": xkind, "points_per_call": m, "value": m / (ms * 1e-3) / 1e6, "unit": "M evals/s",
@@ -419,142 +662,19 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.workload == "headline":
+        run_headline(args, rank, world, local)
+        return
+    if rank != 0:
+        return
     if args.workload == "serve":
-        if rank == 0:
-            run_serve(args)
-        return
-    if args.workload in ("config1", "config3", "config4"):
-        if rank == 0:
-            run_config(args)
-        return
-    if args.workload == "epstein":
-        if rank == 0:
-            run_epstein(args)
-        return
-    import numpy as np
-    import torch
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2504_11989_gb300 import build, ezeta
-    from paper_2504_11989_gb300 import workloads as W
-
-    build.build()
-    items = workload(rank, args.per_lattice)
-    lats = [ezeta.Lattice(W.lattice(n, scale=s)) for n, s in items]
-    spec = ezeta.sum_spec([NU], [[N_BODY]])
-    quads = [ezeta.quadrature(quad_for(s)) for _, s in items]
-    stream = torch.cuda.Stream()
-    batch = ezeta.Batch(lats, [spec] * len(items), quads, stream=stream)
-    out = torch.zeros(len(items) * ezeta.EZ_MAX_PROD, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(max(3, args.warmup)):
-        batch.run(out, stream)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    batch.timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = ezeta.ez_launch_count()
-    far_ms = []
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            batch.run(out, stream)
-            ev[k][1].record(stream)
-            f, _ = batch.timing(True)
-            far_ms.append(f)
-    torch.cuda.synchronize()
-    launches = ezeta.ez_launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    n_sums = len(items)
-    value, total_ms = job_rate(sum(step_ms), n_sums, args.steps, dist, "cuda")
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    res = out.view(n_sums, ezeta.EZ_MAX_PROD)[:, 0].cpu().numpy()
-
-    # mixed form (binary32 tails, binary64 heads), same workload and timing rules
-    quads_m = [ezeta.quadrature(quad_for(s), prec=ezeta.EZ_MIXED) for _, s in items]
-    batch_m = ezeta.Batch(lats, [spec] * len(items), quads_m, stream=stream)
-    out_m = torch.zeros_like(out)
-    for _ in range(max(3, args.warmup)):
-        batch_m.run(out_m, stream)
-    torch.cuda.synchronize()
-    evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            evm[k][0].record(stream)
-            batch_m.run(out_m, stream)
-            evm[k][1].record(stream)
-    torch.cuda.synchronize()
-    mixed_value, mixed_ms = job_rate(sum(a.elapsed_time(b) for a, b in evm), n_sums, args.steps, dist, "cuda")
-    res_m = out_m.view(n_sums, ezeta.EZ_MAX_PROD)[:, 0].cpu().numpy()
-
-    # end to end through the C ABI with host buffers (planning, upload, kernels, download)
-    host_out = np.zeros((n_sums, ezeta.EZ_MAX_PROD))
-    e2e_steps = max(2, min(args.steps, 5))
-    ezeta.ez_lattice_sums(lats, [spec] * n_sums, quads, out=host_out)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ezeta.ez_lattice_sums(lats, [spec] * n_sums, quads, out=host_out)
-    e2e_value, _ = job_rate(1e3 * (time.perf_counter() - t0), n_sums, e2e_steps, dist, "cuda")
-    assert np.array_equal(host_out[:, 0], res), "batch and one-shot paths disagree"
-    _, staging = batch.sizes()
-
-    # roofline of the far-field kernel (one launch per step): algorithmic FP64 flops counted
-    # by the library for the last run (same work every step)
-    flops, n_terms, n_coefs = batch.far_flops()
-    nodes_total = n_sums * 4 * (GRID // 2) ** 2
-    far_mean_ms = float(np.mean(far_ms))
-    achieved = flops / (far_mean_ms * 1e-3) / 1e12
-    peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
-    probe = ezeta.ez_diag_fp64_peak(stream)
-    line = {
-        "metric": METRIC, "value": value, "unit": "lattice_sums/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic lattices (seeded lattice constants)",
-        "config": config_dict(args.per_lattice),
-        "zeta_evals_per_s": {"per_factor": value * nodes_total / n_sums * N_BODY, "distinct_nu": value * nodes_total / n_sums},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "unit": f"per step of {n_sums} sums"},
-        "e2e": {"value": e2e_value, "unit": "lattice_sums/s", "h2d_bytes_per_step": int(staging),
-                "d2h_bytes_per_step": int(n_sums * ezeta.EZ_MAX_PROD * 8)},
-        "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": "far_kernel_d2", "achieved": achieved, "peak": peak_nominal,
-                     "unit": "TFLOP/s", "frac": achieved / peak_nominal,
-                     "traffic": FAR_DRAM_BYTES_PER_LAUNCH if args.per_lattice == PER_LATTICE else None,
-                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
-                                    f"DFMA probe measured {probe:.3f} TFLOP/s in this run",
-                     "far_ms_per_launch": far_mean_ms, "flops_per_launch": flops,
-                     "recip_terms_per_launch": n_terms, "mean_poly_len": n_coefs / max(1, n_terms)},
-        "clocks": clocks,
-        "mixed_precision": {"value": mixed_value, "unit": "lattice_sums/s", "speedup_vs_fp64": mixed_value / value,
-                            "dtype": "f32 tails + float-float heads", "ms_per_step": mixed_ms / args.steps,
-                            "max_rel_err_vs_fp64": float(np.max(np.abs(res_m - res) / np.abs(res)))},
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        vals, dt = oracle_sums(items, args.cpu_seconds, threads)
-        rel = [abs(res[i] - v) / abs(v) for i, v in enumerate(vals)]
-        line["cpu_baseline"] = {"value": len(vals) / dt, "unit": "lattice_sums/s", "cores": threads, "kind": "oracle",
-                                "sample": f"first {len(vals)} sums of the step's batch, full size"}
-        line["rel_err_vs_oracle"] = float(max(rel))
-        line["mixed_precision"]["max_rel_err_vs_oracle"] = float(max(abs(res_m[i] - v) / abs(v) for i, v in enumerate(vals)))
-    if rank == 0:
-        print(json.dumps(line))
-    if dist:
-        dist.destroy_process_group()
+        C = Ctx(local)
+        print(json.dumps(dict(serve_block(C, args.requests, 64, os.cpu_count() or 1), metric=METRIC, n_gpus=1,
+                              higher_is_better=True)))
+    elif args.workload == "epstein":
+        run_epstein(args, local)
+    else:
+        run_single(args, local)
 
 
 if __name__ == "__main__":

@@ -96,16 +96,19 @@ typedef struct {
 } ez_sum_spec;
 
 /* --- lattices (Def. "Lattices") ------------------------------------------------ */
-/* Creates a lattice from A (host, d*d doubles).  EZ_EINVAL if d not in 1..3 or A
- * is singular.  The handle owns device tables built for it. */
-int ez_lattice_create(int d, const double* A, ez_lattice* out);
+/* Creates the lattice (scale A) Z^d from A (host, d*d doubles, row-major as above) and the
+ * lattice constant scale > 0 (1 for A itself; the presets of the paper are given at unit
+ * density and scaled by it).  EZ_EINVAL if d is not in 1..3, scale is not a positive finite
+ * number or A is singular.  The handle keeps the scaled matrix, its inverse and volume. */
+int ez_lattice_create(int d, const double* A, double scale, ez_lattice* out);
 int ez_lattice_destroy(ez_lattice lat);
 
 /* --- Epstein zeta function (Def. "Epstein zeta function") -------------------- */
 /* Z_{Lambda,nu}(x, y_i) for i < m, by the incomplete-gamma splitting with
  * parameter lambda = V^{1/d}: re[i] + i im[i] = sum'_{z} e^{-2 pi i z.y_i} |z - x|^{-nu},
  * meromorphically continued in nu.  nu must be an integer (EZ_EUNSUPPORTED
- * otherwise); nu in -2N0 is EZ_EDOMAIN.
+ * otherwise); nu in -2N0 is EZ_EDOMAIN.  prec must be EZ_FP64: this entry point has no
+ * mixed-precision form, and EZ_MIXED returns EZ_EUNSUPPORTED (any other value EZ_EINVAL).
  *   x  : host, d doubles.
  *   y  : host or device, m*d doubles (point i at y[i*d .. i*d+d-1]).
  *   re, im : host or device, m doubles each (im may be NULL).
@@ -137,10 +140,20 @@ int ez_epstein_zeta_static(ez_lattice lat, double nu, const double* x, const dou
 /* zeta^(n)_Lambda(nu_1..nu_n) through the Epstein representation and the Duffy
  * transformation (Cor. "Duffy transformation"), with the eps-split meromorphic
  * continuation of Sec. 3 when u_rule is 2.
- *   nu    : host, n integers stored as doubles (1 <= n <= 64).
- *   value : host or device, 1 double. */
+ *   nu      : host, n integers stored as doubles (1 <= n <= 64).
+ *   value   : host or device, 1 double.
+ *   err_est : host or device, 1 double, or NULL.  When given, the same sum is also
+ *             computed on the embedded coarse rule -- ceil(n_u/2) u nodes per panel and
+ *             ceil(n_v/2) v nodes per axis, same panels, near part, splitting parameter
+ *             and cutoffs -- in the same launch, and *err_est = |value - coarse value|.
+ *             Both Gauss-Legendre rules converge geometrically, so this bounds the far-
+ *             field quadrature error of the coarse rule and overstates that of value; it
+ *             does not include the lattice-sum truncation (below e^{-45}, or e^{-36} in the
+ *             mixed form) or the near part's Taylor truncation (order 2 ell).  Costs about
+ *             2^{-d} of the sum again.  NULL: no extra work.
+ * Synchronises `stream`. */
 int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q,
-                         double* value, void* stream);
+                         double* value, double* err_est, void* stream);
 
 /* --- ATM cohesive energy (Prop. in Sec. 2) ------------------------------------ */
 /* E = zeta(3,3,3)/24 - 3 zeta(-1,5,5)/16 + 3 zeta(1,3,5)/8; the three zeta^(3) are
@@ -276,6 +289,8 @@ int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const ez_quadratur
 /* Diagnostic (no counterpart in the paper): sustained FP64 FMA throughput of the
  * current device in TFLOP/s, from a DFMA loop on every SM timed with CUDA events. */
 int ez_diag_fp64_peak(double* tflops, void* stream);
+/* The same for binary32 FMA (the pipe of the mixed form's tails and float-float arithmetic). */
+int ez_diag_fp32_peak(double* tflops, void* stream);
 
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* ez_last_error(void);

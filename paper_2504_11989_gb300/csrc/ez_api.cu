@@ -96,15 +96,16 @@ static bool invert(int d, const double* A, double* X) {
   return true;
 }
 
-extern "C" int ez_lattice_create(int d, const double* A, ez_lattice* out) {
+extern "C" int ez_lattice_create(int d, const double* A, double scale, ez_lattice* out) {
   if (!out || !A) return fail(EZ_EINVAL, "ez_lattice_create: NULL argument");
   if (d < 1 || d > 3) return fail(EZ_EINVAL, "ez_lattice_create: d = %d not in 1..3", d);
+  if (!(scale > 0.0) || !std::isfinite(scale)) return fail(EZ_EINVAL, "ez_lattice_create: scale = %g", scale);
   for (int i = 0; i < d * d; ++i)
     if (!std::isfinite(A[i])) return fail(EZ_EINVAL, "ez_lattice_create: non-finite A");
   ez_lattice L = new ez_lattice_s();
   L->d = d;
   std::memset(L->A, 0, sizeof L->A);
-  std::memcpy(L->A, A, sizeof(double) * d * d);
+  for (int i = 0; i < d * d; ++i) L->A[i] = scale * A[i];
   L->V = std::fabs(det3(d, L->A));
   if (!(L->V > 0.0) || !invert(d, L->A, L->Ai)) {
     delete L;
@@ -280,16 +281,13 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
       P.ser[n] = -sg / (fact * (a + n));
     }
   }
-  for (int n = 0; n < kNSer; ++n) ff_split(P.ser[n], P.ser_ff[n].x, P.ser_ff[n].y);
-  ff_split(P.gam, P.gam_ff.x, P.gam_ff.y);
   P.a_f = (float)a;
   // series lengths: sum_{n >= N} |ser_n| t^n (the terms n >= kNSer add < 1e-18 at t = kT0,
   // bounded by the next one) is increasing in t; breakpoint = largest t <= kT0 (bisection,
   // rounded down to binary32) where it is <= tol.  They depend on a alone: computed once
   // per 2a and kept (planning runs for every served request).
   struct SerBrk {
-    float brk[6], brk_ff[6];
-    int n1[7];
+    float brk[6];
   };
   static std::mutex brk_mu;
   static std::map<int, SerBrk> brk_cache;
@@ -298,8 +296,6 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
     auto it = brk_cache.find(P.two_a);
     if (it != brk_cache.end()) {
       std::memcpy(P.ser_brk, it->second.brk, sizeof P.ser_brk);
-      std::memcpy(P.ser_brk_ff, it->second.brk_ff, sizeof P.ser_brk_ff);
-      std::memcpy(P.ser_n1, it->second.n1, sizeof P.ser_n1);
       return;
     }
   }
@@ -320,21 +316,9 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
     }
     return std::nextafter((float)lo, 0.0f);
   };
-  for (int i = 0; i < 6; ++i) {
-    P.ser_brk[i] = brk(4 + 2 * i, std::ldexp(1.0, -55));
-    P.ser_brk_ff[i] = brk(4 + 2 * i, std::ldexp(1.0, -50));
-  }
-  for (int i = 0; i < 7; ++i) {
-    const int N = i < 6 ? 4 + 2 * i : kNSer;
-    const double tmax = i < 6 ? (double)P.ser_brk_ff[i] : kT0;
-    int n1 = N;
-    while (n1 > 1 && tail(n1 - 1, N, tmax) <= std::ldexp(1.0, -30)) --n1;
-    P.ser_n1[i] = n1;
-  }
+  for (int i = 0; i < 6; ++i) P.ser_brk[i] = brk(4 + 2 * i, std::ldexp(1.0, -55));
   SerBrk e;
   std::memcpy(e.brk, P.ser_brk, sizeof e.brk);
-  std::memcpy(e.brk_ff, P.ser_brk_ff, sizeof e.brk_ff);
-  std::memcpy(e.n1, P.ser_n1, sizeof e.n1);
   std::lock_guard<std::mutex> lk(brk_mu);
   brk_cache[P.two_a] = e;
 }
@@ -1052,7 +1036,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_tayff(n_req), o_hbox(n_req);
+      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_hbox(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -1099,7 +1083,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
       }
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
-    o_tayff[r] = dl.take(sizeof(float2) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
     o_tpart[r] = p.near ? dl.take(sizeof(double) * std::max<long long>(taylor_chunks(p), 1) * std::max<size_t>(na, 1) *
                                   p.spec.n_distinct)
@@ -1159,7 +1142,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
     std::memcpy(R.expo, p.spec.expo, sizeof R.expo);
     std::memcpy(R.A, L->A, sizeof R.A);
     std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
-    for (int i = 0; i < 9; ++i) ff_split(R.AiT[i], R.AiT_ff[i].x, R.AiT_ff[i].y);
     R.V = L->V;
     R.lam = p.lam;
     R.c_lam = kPi * p.lam * p.lam;
@@ -1167,15 +1149,12 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.R2_recip = p.r_recip * p.r_recip;
     R.eps = p.eps;
     R.inv_eps = 1.0 / p.eps;
-    ff_split(R.eps, R.eps_ff.x, R.eps_ff.y);
-    ff_split(R.inv_eps, R.inv_eps_ff.x, R.inv_eps_ff.y);
     for (int j = 0; j < p.spec.n_distinct; ++j) {
       double nu = p.spec.nu[j];
       R.nu[j] = nu;
       R.two_over_nu[j] = 2.0 / nu;
       R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
       R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
-      ff_split(R.sig[j] / L->V, R.sigv_ff[j].x, R.sigv_ff[j].y);
       R.nu_f[j] = (float)nu;
       R.phi[j] = p.phi[j];
       R.phi[j].c_lam = R.c_lam;
@@ -1230,7 +1209,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.alpha = (const int*)dptr(o_al[r]);
     R.alpha_off = (const int*)dptr(o_alo[r]);
     R.taylor = (const double*)dptr(o_tay[r]);
-    R.taylor_ff = (const float2*)dptr(o_tayff[r]);
     if (!p.alpha.empty()) {
       std::memcpy(Hs + h_al[r], p.alpha.data(), sizeof(int) * p.alpha.size());
       std::memcpy(Hs + h_alo[r], p.alpha_off.data(), sizeof(int) * p.alpha_off.size());
@@ -1280,7 +1258,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
         T.phiG = (double*)dptr(o_phig[r]) + (size_t)j * p.rcap * (2 * p.ell + 1);
         std::memcpy(T.rser, p.rser[j], sizeof T.rser);
         T.out = (double*)dptr(o_tay[r]) + (size_t)j * R.n_alpha;
-        T.outff = (float2*)dptr(o_tayff[r]) + (size_t)j * R.n_alpha;
         T.part = (double*)dptr(o_tpart[r]);
         T.n_chunk = (int)taylor_chunks(p);
       }
@@ -1718,7 +1695,7 @@ extern "C" int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const e
 }
 
 extern "C" int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q, double* value,
-                                    void* stream) {
+                                    double* err_est, void* stream) {
   if (!lat || !nu || !q || !value) return fail(EZ_EINVAL, "NULL argument");
   if (n < 1 || n > kMaxFactor) return fail(EZ_EINVAL, "n = %d not in 1..%d", n, kMaxFactor);
   ez_sum_spec s;
@@ -1743,13 +1720,30 @@ extern "C" int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, con
       s.expo[0][j]++;
     }
   }
-  double out[EZ_MAX_PROD];
-  int rc = run_sums(1, &lat, &s, q, out, nullptr, nullptr, (cudaStream_t)stream);
+  // with err_est: the same sum on the embedded coarse rule (half the u nodes per panel and
+  // half the v nodes per axis, same panels, near part and cutoffs) in the same batch
+  ez_lattice ls[2] = {lat, lat};
+  ez_sum_spec ss[2] = {s, s};
+  ez_quadrature qs[2] = {*q, *q};
+  qs[1].n_u = std::max(1, (q->n_u + 1) / 2);
+  qs[1].n_v = std::max(1, (q->n_v + 1) / 2);
+  const int nreq = err_est ? 2 : 1;
+  double out[2 * EZ_MAX_PROD];
+  int rc = run_sums(nreq, ls, ss, qs, out, nullptr, nullptr, (cudaStream_t)stream);
   if (rc) return rc;
+  double e = err_est ? std::fabs(out[0] - out[EZ_MAX_PROD]) : 0.0;
   if (is_device_ptr(value))
     EZ_CUDA(cudaMemcpyAsync(value, out, sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
   else
     *value = out[0];
+  if (err_est) {
+    if (is_device_ptr(err_est))
+      EZ_CUDA(cudaMemcpyAsync(err_est, &e, sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    else
+      *err_est = e;
+  }
+  if (is_device_ptr(value) || (err_est && is_device_ptr(err_est)))
+    EZ_CUDA(cudaStreamSynchronize((cudaStream_t)stream));  // the copies read host stack values
   return EZ_OK;
 }
 

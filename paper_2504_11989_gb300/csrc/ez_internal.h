@@ -64,19 +64,13 @@ struct PhiInfo {
   const float* tabf;  // binary32 table (own polynomial lengths) for the mixed form (device)
   const float* tabff; // float-float table (n_int * kRecFF floats) for the mixed form (device)
   double ser[kNSer];  // entire part for t < kT0
-  float2 ser_ff[kNSer];  // the same as float-float, and Gamma(a) (or (-1)^m/m!), for the mixed form
-  float2 gam_ff;
   float a_f;             // a in binary32 (exact: a is a small half-integer)
   float pad_f;
   // t < kT0: below ser_brk[i] the series needs only N = 4 + 2 i terms (i < 6; N = kNSer
-  // above ser_brk[5]): the dropped terms sum to <= 2^-55 (binary64 form) or <= 2^-50
-  // (ser_brk_ff, float-float form) in absolute value.  Float-float form on interval i:
-  // the terms n >= ser_n1[i] sum to <= 2^-30 and are evaluated in binary32.
+  // above ser_brk[5]): the dropped terms sum to <= 2^-55 in absolute value.
   float ser_brk[6];
-  float ser_brk_ff[6];
-  int ser_n1[7];
-  int pad_i;
 };
+static_assert(sizeof(PhiInfo) % sizeof(double) == 0, "PhiInfo is copied to shared memory in doubles");
 
 // ---------------------------------------------------------------------------
 // One lattice sum as seen by the kernels (device resident).
@@ -128,9 +122,6 @@ struct ReqDesc {
   // float-float copies of the per-exponent constants, for the mixed form
   float2 pref_ff[EZ_MAX_NU], tov_ff[EZ_MAX_NU], vol_ff;
   double inv_eps;           // 1 / eps (near part)
-  float2 eps_ff, inv_eps_ff;  // eps and 1 / eps as float-float
-  float2 AiT_ff[9];           // A^{-T} as float-float (mixed-form near part)
-  float2 sigv_ff[EZ_MAX_NU];  // sigma_nu / V as float-float
   float nu_f[EZ_MAX_NU];      // nu in binary32 (integers)
   // d <= 2: powers e^{2 pi i m u v}, m = 0..phase_mp1-1, per (u node, v node); shared by every
   // sum of a batch with the same quadrature (the phases do not depend on the lattice)
@@ -142,7 +133,6 @@ struct ReqDesc {
   const int* alpha;       // [n_alpha][3]
   const int* alpha_off;   // start of |alpha| = 2k blocks, k = 0..ell+1
   const double* taylor;   // [n_distinct][n_alpha] : d^alpha Z^reg(0) / alpha!
-  const float2* taylor_ff; // the same as float-float (mixed form)
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;
   int line0;  // first line (far lines then near lines)

@@ -64,7 +64,6 @@ struct TaylorJob {
   double* phiG;   // [n_rec_cap][2 ell + 1]
   double rser[16];  // entire series of the regularised h = 0 term (lambda piece included)
   double* out;    // [n_alpha]
-  float2* outff;  // [n_alpha] float-float copy (mixed form; may be null)
   double* part;   // first job of a request: real-space partial moments [n_chunk][n_alpha][n_distinct]
   int n_chunk;    // chunks of kTaylorCells cells of the half box
 };

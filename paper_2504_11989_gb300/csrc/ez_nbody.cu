@@ -277,76 +277,33 @@ __device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain,
     }
 }
 
-// Mixed form, t < kT0 (the h = 0 term near k = 0): Phi_a(t) = sum_n ser_n t^n + singular
-// part, the series in float-float; the singular part gam t^{-a} from float-float 1/t and
-// sqrt(t), or -gam t^m log t with log t taken once in binary64 for every exponent.
+// Mixed form, h = 0 term near k = 0 (t < kT0) of an order chain (orders a_j = a_0 + (nd-1-j),
+// lowest a_0 < 0), in binary64: the orders a < 1 by their series (log t and 1/t shared),
+// e^{-t} = t Phi_{a_0+1} - a_0 Phi_{a_0} from the two lowest (a sum of positive terms), and
+// every order a >= 1 upward by Phi_a = ((a-1) Phi_{a-1} + e^{-t}) / t, also positive terms.
 template <int NDM>
-__device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, bool chain, ff t, ff* hs,
-                                                unsigned& coefs) {
-  // with an order chain whose lowest order is negative, e^{-t} = t Phi_{a+1} - a Phi_a from
-  // the two lowest orders is a sum of positive terms, and every step up from a >= 0,
-  // Phi_{a+1} = (a Phi_a + e^{-t}) / t, is too: those orders skip the series
-  chain = chain && sphi[nd - 1].a_f < 0.0f;
-  bool need_log = false, need_inv = chain, need_sqrt = false;
-#pragma unroll
-  for (int j = 0; j < NDM; ++j)
-    if (j < nd) {
-      const int e = -sphi[j].two_a;
-      need_log |= sphi[j].log_m >= 0;
-      need_inv |= sphi[j].log_m < 0 && e < 0;
-      need_sqrt |= sphi[j].log_m < 0 && (e & 1);
+__device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, ff* hs, unsigned& coefs) {
+  bool need_log = false;
+  for (int j = 0; j < nd; ++j) need_log |= sphi[j].a < 1.0 && sphi[j].log_m >= 0;
+  const double lt = need_log ? log(t) : 0.0;
+  const double it = 1.0 / t;
+  double prev = 0.0, E = 0.0;
+  for (int j = nd - 1; j >= 0; --j) {
+    const PhiInfo& P = sphi[j];
+    double v;
+    if (P.a < 1.0) {
+      int n;
+      v = phi_small_shared(P, t, lt, it, n);
+      coefs += n;
+      if (j == nd - 2) E = fma(t, v, -sphi[nd - 1].a * prev);
+    } else {
+      v = fma(sphi[j + 1].a, prev, E) * it;
     }
-  ff lt{0.0f, 0.0f}, inv{0.0f, 0.0f}, sq{0.0f, 0.0f};
-  if (need_log) {
+    prev = v;
     float hi, lo;
-    ff_split(log((double)t.hi + (double)t.lo), hi, lo);
-    lt = ff{hi, lo};
+    ff_split(v, hi, lo);
+    hs[j] = ff_add(hs[j], ff{hi, lo});
   }
-  if (need_inv) inv = ff_rcp(t);
-  if (need_sqrt) sq = ff_sqrt(t);
-  ff prev{0.0f, 0.0f}, E{0.0f, 0.0f};
-#pragma unroll
-  for (int j = NDM - 1; j >= 0; --j)
-    if (j < nd) {
-      const PhiInfo& P = sphi[j];
-      if (chain && j < nd - 2 && sphi[j + 1].a_f >= 0.0f) {
-        prev = ff_mul(ff_add(ff_mul(ff{sphi[j + 1].a_f, 0.0f}, prev), E), inv);
-        hs[j] = ff_add(hs[j], prev);
-        continue;
-      }
-      // N = 4 + 2 iv terms (the rest below 2^-50); n >= N1 in binary32
-      int iv = 0;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) iv += t.hi >= P.ser_brk_ff[q] ? 1 : 0;
-      const int N = 4 + 2 * iv, N1 = P.ser_n1[iv];
-      float pf = 0.0f;
-#pragma unroll 1
-      for (int n = N - 1; n >= N1; --n) pf = fmaf(pf, t.hi, P.ser_ff[n].x);
-      ff p{pf, 0.0f};
-#pragma unroll 1
-      for (int n = N1 - 1; n >= 0; --n) p = ff_add(ff_mul(p, t), ff{P.ser_ff[n].x, P.ser_ff[n].y});
-      const ff gam{P.gam_ff.x, P.gam_ff.y};
-      if (P.log_m >= 0) {
-        ff tm{1.0f, 0.0f};
-        for (int q = 0; q < P.log_m; ++q) tm = ff_mul(tm, t);
-        const ff sgl = ff_mul(ff_mul(gam, tm), lt);
-        p = ff_add(p, ff{-sgl.hi, -sgl.lo});
-      } else {
-        const int e = -P.two_a;  // power of sqrt(t)
-        ff r = (e & 1) ? sq : ff{1.0f, 0.0f};
-        const int kk = e >> 1;  // floor(e / 2)
-        const ff base = kk < 0 ? inv : t;
-        for (int q = 0; q < (kk < 0 ? -kk : kk); ++q) r = ff_mul(r, base);
-        p = ff_add(p, ff_mul(gam, r));
-      }
-      if (chain && j == nd - 2) {  // e^{-t} from the two lowest orders
-        const ff ap = ff_mul(ff{sphi[nd - 1].a_f, 0.0f}, prev);
-        E = ff_add(ff_mul(t, p), ff{-ap.hi, -ap.lo});
-      }
-      prev = p;
-      hs[j] = ff_add(hs[j], p);
-      coefs += N;
-    }
 }
 
 // Mixed form of the same sum.  Terms by t = pi lam^2 |G + k|^2 (binary32 screen):
@@ -354,7 +311,8 @@ __device__ __forceinline__ void phi_small_mixed(const PhiInfo* sphi, int nd, boo
 //  * t_mid <= t < t_mix (|Phi| <= 1e-6): float-float argument, binary32 polynomial;
 //  * kT0 <= t < t_mid (the heads): float-float |G + k|^2, argument and Horner scheme on
 //    the float-float table (~46 bits, no binary64 instruction);
-//  * t < kT0 (the h = 0 term near k = 0) or beyond the table: binary64 as in the FP64 form.
+//  * t < kT0 (the h = 0 term near k = 0: series and singular part) or beyond the table:
+//    binary64 as in the FP64 form, from |G + k|^2 formed in binary64 of the float-float k.
 // The list is sorted by |G|: once |G| > sqrt(t_mix / c) + |k|, every remaining term is a
 // binary32 tail, evaluated by a short loop that skips the points beyond the cutoff.  Tails
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
@@ -413,19 +371,9 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       tails_f<NDM>(sphi, nd, chain, E, r, sv, st);
       continue;
     }
-    if (tf < (float)kT0) {  // near the origin: float-float series and singular part
-      const float4 Gl = h < kRecCache ? rc.lo[h] : __ldg(reclo + h);
-      ff qq = ff_sqr(ff_add4(Gf.x, Gl.x, kf[0], klo[0]));
-      if (D >= 2) qq = ff_add(qq, ff_sqr(ff_add4(Gf.y, Gl.y, kf[1], klo[1])));
-      if (D >= 3) qq = ff_add(qq, ff_sqr(ff_add4(Gf.z, Gl.z, kf[2], klo[2])));
-      const ff t = ff_mul(ff{R->c_lam_ff.x, R->c_lam_ff.y}, qq);
-      if (t.hi > 0.0f) {
-        ++terms;
-        phi_small_mixed<NDM>(sphi, nd, chain, t, hs, coefs);
-        continue;
-      }
-    }
-    if (tf < (float)kT0 || tf > t_hi) {  // rare: t = 0, or beyond the table: binary64
+    // binary64: the incomplete gamma near the origin (t < kT0, the h = 0 term near k = 0:
+    // entire series plus singular part, as in the FP64 form), t = 0, and beyond the table
+    if (tf < (float)kT0 || tf > t_hi) {
       const G4 G = ldg_g4(R->rec + (h < kRecCache ? rc.idx[h] : h));
       const double q0 = G.x + ((double)kf[0] + (double)klo[0]);
       double qq = q0 * q0;
@@ -438,6 +386,10 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
         qq = fma(q2, q2, qq);
       }
       ++terms;
+      if (chain && tf < (float)kT0 && qq > 0.0 && sphi[nd - 1].a < 0.0) {
+        small_chain_f64<NDM>(sphi, nd, sphi[0].c_lam * qq, hs, coefs);
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < NDM; ++j)
         if (j < nd) {
@@ -1316,17 +1268,11 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
 //   I_m(mu) = eps^mu J_m,  J_0 = 1/mu,  J_m = L^m/mu - (2m/mu) J_{m-1},  L = log(pi eps^2 |w|^2).
 // 1/n for |n| <= kInvIntHalf (n = 0 unused), filled once by upload_inv_int
 __constant__ double c_inv_int[2 * kInvIntHalf + 1];
-__constant__ float2 c_inv_int_ff[2 * kInvIntHalf + 1];  // the same as float-float
 
 cudaError_t upload_inv_int() {
   double t[2 * kInvIntHalf + 1];
-  float2 tf[2 * kInvIntHalf + 1];
-  for (int n = -kInvIntHalf; n <= kInvIntHalf; ++n) {
-    t[n + kInvIntHalf] = n ? 1.0 / n : 0.0;
-    ff_split(t[n + kInvIntHalf], tf[n + kInvIntHalf].x, tf[n + kInvIntHalf].y);
-  }
-  cudaError_t e = cudaMemcpyToSymbol(c_inv_int, t, sizeof t);
-  return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_inv_int_ff, tf, sizeof tf);
+  for (int n = -kInvIntHalf; n <= kInvIntHalf; ++n) t[n + kInvIntHalf] = n ? 1.0 / n : 0.0;
+  return cudaMemcpyToSymbol(c_inv_int, t, sizeof t);
 }
 
 __device__ double ipow(double x, int e) {
@@ -1340,33 +1286,14 @@ __device__ double ipow(double x, int e) {
   return e < 0 ? 1.0 / r : r;
 }
 
-// Number types of the near part: binary64 (FP64 form) and float-float (mixed form, where
-// the FP64 pipe would otherwise dominate: the products and Hadamard sums are ~3000
-// operations per ray).
-struct FFN {
-  float hi, lo;
-};
-__device__ __forceinline__ FFN operator+(FFN a, FFN b) {
-  const ff r = ff_add(ff{a.hi, a.lo}, ff{b.hi, b.lo});
-  return FFN{r.hi, r.lo};
-}
-__device__ __forceinline__ FFN operator*(FFN a, FFN b) {
-  const ff r = ff_mul(ff{a.hi, a.lo}, ff{b.hi, b.lo});
-  return FFN{r.hi, r.lo};
-}
+// Number type of the near part (binary64 in both forms: the near part is the
+// integral of the singular subtraction at k -> 0).
 __device__ __forceinline__ double nfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ FFN nfma(FFN a, FFN b, FFN c) { return a * b + c; }
 template <typename N>
 __device__ __forceinline__ N nfrom(double x);
 template <>
 __device__ __forceinline__ double nfrom<double>(double x) {
   return x;
-}
-template <>
-__device__ __forceinline__ FFN nfrom<FFN>(double x) {
-  FFN r;
-  ff_split(x, r.hi, r.lo);
-  return r;
 }
 // exact conversion of an integer |v| < 2^48 (binomial products, small multipliers)
 template <typename N>
@@ -1375,23 +1302,9 @@ template <>
 __device__ __forceinline__ double nint<double>(long long v) {
   return (double)v;
 }
-template <>
-__device__ __forceinline__ FFN nint<FFN>(long long v) {
-  if (v >= -(1 << 24) && v <= (1 << 24)) return FFN{(float)(int)v, 0.0f};  // exact in binary32
-  const float hi = (float)v;
-  return FFN{hi, (float)(v - (long long)hi)};
-}
 __device__ __forceinline__ double nto(double x) { return x; }
-__device__ __forceinline__ double nto(FFN x) { return (double)x.hi + (double)x.lo; }
 __device__ __forceinline__ double ninv(double, int mk) {
   return (mk >= -kInvIntHalf && mk <= kInvIntHalf) ? c_inv_int[mk + kInvIntHalf] : 1.0 / (double)mk;
-}
-__device__ __forceinline__ FFN ninv(FFN, int mk) {
-  if (mk >= -kInvIntHalf && mk <= kInvIntHalf) {
-    const float2 v = c_inv_int_ff[mk + kInvIntHalf];
-    return FFN{v.x, v.y};
-  }
-  return nfrom<FFN>(1.0 / (double)mk);
 }
 template <typename N>
 __device__ __forceinline__ N npow(N x, int e) {  // e >= 0
@@ -1410,17 +1323,8 @@ template <>
 __device__ __forceinline__ double neps<double>(const ReqDesc* R, bool inv) {
   return inv ? R->inv_eps : R->eps;
 }
-template <>
-__device__ __forceinline__ FFN neps<FFN>(const ReqDesc* R, bool inv) {
-  const float2 v = inv ? R->inv_eps_ff : R->eps_ff;
-  return FFN{v.x, v.y};
-}
 __device__ __forceinline__ double ntaylor(const ReqDesc* R, int jn, int ia, double) {
   return R->taylor[(size_t)jn * R->n_alpha + ia];
-}
-__device__ __forceinline__ FFN ntaylor(const ReqDesc* R, int jn, int ia, FFN) {
-  const float2 v = R->taylor_ff[(size_t)jn * R->n_alpha + ia];
-  return FFN{v.x, v.y};
 }
 
 // sig_w[j] = sigma_j |w|^{nu_j - d} / V (per ray, shared by every product and subset)
@@ -1515,7 +1419,7 @@ __device__ void near_core(const ReqDesc* R, const N* wN, N L, const N* sig_w, do
   for (int p = 0; p < np; ++p) val[p] = scale * nto(near_product<N>(R, p, C, sig_w, L));
 }
 
-// FP64 form: per-ray inputs in binary64
+// per-ray inputs in binary64 (both forms)
 __device__ void near_ray_f64(const ReqDesc* R, const double* dir, double wv, double (&val)[EZ_MAX_PROD]) {
   const int d = R->d, nd = R->n_distinct;
   double w[3] = {0.0, 0.0, 0.0}, w2 = 0.0;
@@ -1533,36 +1437,6 @@ __device__ void near_ray_f64(const ReqDesc* R, const double* dir, double wv, dou
     sig_w[jn] = R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V;
   }
   near_core<double>(R, w, L, sig_w, 2.0 * wv, val);
-}
-
-// Mixed form: the per-ray inputs in float-float (w = A^{-T} dir, |w|, 1/|w|, the singular
-// weights sigma_nu |w|^{nu - d} / V) and one binary64 log per ray -- binary64 work here would
-// otherwise bound the kernel on the FP64 pipe
-__device__ void near_ray_ff(const ReqDesc* R, const ff* dir, double wv, double (&val)[EZ_MAX_PROD]) {
-  const int d = R->d, nd = R->n_distinct;
-  FFN w[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-  ff w2{0.0f, 0.0f};
-  for (int i = 0; i < d; ++i) {
-    ff s{0.0f, 0.0f};
-    for (int q = 0; q < d; ++q) s = ff_add(s, ff_mul(ff{R->AiT_ff[i * d + q].x, R->AiT_ff[i * d + q].y}, dir[q]));
-    w[i] = FFN{s.hi, s.lo};
-    w2 = ff_add(w2, ff_sqr(s));
-  }
-  FFN L;
-  ff_split(log(kPi * R->eps * R->eps * ((double)w2.hi + (double)w2.lo)), L.hi, L.lo);
-  const ff wn = ff_sqrt(w2), inv_wn = ff_rcp(wn);
-  FFN sig_w[EZ_MAX_NU];
-  for (int jn = 0; jn < nd; ++jn) {
-    const int dn = (int)lrintf(R->nu_f[jn]) - d;
-    ff b = dn >= 0 ? wn : inv_wn, r{1.0f, 0.0f};
-    for (int e = dn >= 0 ? dn : -dn; e; e >>= 1) {
-      if (e & 1) r = ff_mul(r, b);
-      b = ff_sqr(b);
-    }
-    const ff sv = ff_mul(ff{R->sigv_ff[jn].x, R->sigv_ff[jn].y}, r);
-    sig_w[jn] = FFN{sv.hi, sv.lo};
-  }
-  near_core<FFN>(R, w, L, sig_w, 2.0 * wv, val);
 }
 
 __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ reqs, const Item* __restrict__ items,
@@ -1585,22 +1459,11 @@ __global__ void __launch_bounds__(128) near_kernel(const ReqDesc* __restrict__ r
     }
     const int half = 1 << (d - 1);
     const int j = it.sector / half, pb = it.sector % half;
-    if (R->prec == EZ_MIXED) {
-      ff y[3], dir[3];
-      for (int i = 0; i < d - 1; ++i) {
-        const float2 vf = R->v_ff[i == 0 ? r % nv : r / nv];
-        y[i] = ((pb >> i) & 1) ? ff{-vf.x, -vf.y} : ff{vf.x, vf.y};
-      }
-      y[d - 1] = ff{1.0f, 0.0f};
-      for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
-      near_ray_ff(R, dir, wv, val);
-    } else {
-      double y[3], dir[3];
-      for (int i = 0; i < d - 1; ++i) y[i] = (((pb >> i) & 1) ? -1.0 : 1.0) * v[i];
-      y[d - 1] = 1.0;
-      for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
-      near_ray_f64(R, dir, wv, val);
-    }
+    double y[3], dir[3];
+    for (int i = 0; i < d - 1; ++i) y[i] = (((pb >> i) & 1) ? -1.0 : 1.0) * v[i];
+    y[d - 1] = 1.0;
+    for (int i = 0; i < d; ++i) dir[i] = y[((i - j) % d + d) % d];
+    near_ray_f64(R, dir, wv, val);
   }
   block_reduce_store<128>(val, np, 1.0, seg + (size_t)it.chunk_seg() * EZ_MAX_PROD);
 }

@@ -186,6 +186,31 @@ static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
   return s + P.gam * pow_half(t, P.two_a);
 }
 
+// t < kT0, binary64, with log t (log-case orders) and 1/t supplied by the caller, who
+// shares them between the orders of one reciprocal term: the entire series cut at 2^-55
+// plus the singular part.  n_used: series terms (work count).
+__device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, int& n_used) {
+  const float tf = (float)t;
+  int N = 4;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) N += tf >= P.ser_brk[i] ? 2 : 0;
+  n_used = N;
+  double s = P.ser[N - 1];
+#pragma unroll 1
+  for (int k = N - 2; k >= 0; --k) s = fma(s, t, P.ser[k]);
+  if (P.log_m >= 0) {
+    double tm = 1.0;
+    for (int k = 0; k < P.log_m; ++k) tm *= t;
+    return s - P.gam * tm * lt;
+  }
+  const int e = -P.two_a;  // t^{-a} = sqrt(t)^e
+  double r = (e & 1) ? sqrt(t) : 1.0;
+  const int k = e >> 1;  // floor(e / 2)
+  const double b = k < 0 ? it : t;
+  for (int q = 0; q < (k < 0 ? -k : k); ++q) r *= b;
+  return s + P.gam * r;
+}
+
 static __device__ __noinline__ double phi_large(const PhiInfo& P, double t) {
   double inv = 1.0 / t;
   double s = 1.0, term = 1.0;

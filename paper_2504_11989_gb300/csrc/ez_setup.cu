@@ -514,11 +514,6 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
   double v = sr + R->vol_fac * sk;
   if (K2 == 0) v -= 2.0 / R->nu[jn];
   J.out[ia] = R->pref[jn] * v;
-  if (J.outff) {
-    float hi, lo;
-    ff_split(J.out[ia], hi, lo);
-    J.outff[ia] = make_float2(hi, lo);
-  }
 }
 
 __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs) {

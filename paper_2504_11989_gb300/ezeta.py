@@ -90,12 +90,12 @@ def lib():
             L.ez_last_error.restype = ctypes.c_char_p
             L.ez_launch_count.restype = ctypes.c_longlong
             L.ez_launch_count.argtypes = [ctypes.c_int]
-            L.ez_lattice_create.argtypes = [ctypes.c_int, dp, ctypes.POINTER(vp)]
+            L.ez_lattice_create.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.POINTER(vp)]
             L.ez_lattice_destroy.argtypes = [vp]
             L.ez_quadrature_default.argtypes = [ctypes.POINTER(ez_quadrature)]
             L.ez_epstein_zeta.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, ctypes.c_int, vp]
             L.ez_epstein_zeta_static.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, vp]
-            L.ez_lattice_sum_nbody.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ez_quadrature), vp, vp]
+            L.ez_lattice_sum_nbody.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ez_quadrature), vp, vp, vp]
             L.ez_atm_energy.argtypes = [vp, ctypes.POINTER(ez_quadrature), dp, dp, vp]
             L.ez_lattice_sums.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
                                           ctypes.POINTER(ez_quadrature), vp, vp,
@@ -113,6 +113,7 @@ def lib():
                                              ctypes.POINTER(ctypes.c_longlong)]
             L.ez_batch_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
             L.ez_diag_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+            L.ez_diag_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
             L.ez_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(vp)]
             L.ez_server_submit.argtypes = [vp, ctypes.POINTER(ez_request), ctypes.POINTER(ctypes.c_ulonglong)]
@@ -187,12 +188,13 @@ def sum_spec(nu, expo) -> ez_sum_spec:
 class Lattice:
     """Owning wrapper of an ez_lattice handle (Def. "Lattices")."""
 
-    def __init__(self, A):
+    def __init__(self, A, scale: float = 1.0):
         A = np.ascontiguousarray(A, dtype=np.float64)
         self.d = A.shape[0]
-        self.A = A
+        self.A = A * float(scale)
         h = ctypes.c_void_p()
-        _check(lib().ez_lattice_create(self.d, A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(h)))
+        _check(lib().ez_lattice_create(self.d, A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(scale),
+                                       ctypes.byref(h)))
         self.handle = h
 
     def __del__(self):
@@ -282,17 +284,23 @@ def ez_epstein_zeta_static(lat: Lattice, nu: float, x, y, re, im=None, stream=No
     return re, im
 
 
-def ez_lattice_sum_nbody(lat: Lattice, nu, q: ez_quadrature, out=None, stream=None) -> float:
+def ez_lattice_sum_nbody(lat: Lattice, nu, q: ez_quadrature, out=None, stream=None, err_est: bool = False):
+    """zeta^(n)(nu_1..nu_n).  Returns the value (float), or `out` when a numpy array or CUDA
+    tensor of one double is given; with err_est=True returns (value, error estimate)."""
     nuv = np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    nup = nuv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    e = ctypes.c_double()
+    ep = ctypes.byref(e) if err_est else None
     if out is None:
         v = ctypes.c_double()
-        _check(lib().ez_lattice_sum_nbody(lat.handle, nuv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                          int(nuv.size), ctypes.byref(q), ctypes.byref(v), _stream_ptr(stream)))
-        return v.value
+        _check(lib().ez_lattice_sum_nbody(lat.handle, nup, int(nuv.size), ctypes.byref(q), ctypes.byref(v), ep,
+                                          _stream_ptr(stream)))
+        return (v.value, e.value) if err_est else v.value
+    if _numel(out) < 1:
+        raise ValueError("out holds no value")
     op, _ = _ptr(out)
-    _check(lib().ez_lattice_sum_nbody(lat.handle, nuv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                      int(nuv.size), ctypes.byref(q), op, _stream_ptr(stream)))
-    return out
+    _check(lib().ez_lattice_sum_nbody(lat.handle, nup, int(nuv.size), ctypes.byref(q), op, ep, _stream_ptr(stream)))
+    return (out, e.value) if err_est else out
 
 
 def ez_atm_energy(lat: Lattice, q: ez_quadrature, stream=None):
@@ -413,6 +421,12 @@ class Batch:
 def ez_diag_fp64_peak(stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().ez_diag_fp64_peak(ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
+def ez_diag_fp32_peak(stream=None) -> float:
+    v = ctypes.c_double()
+    _check(lib().ez_diag_fp32_peak(ctypes.byref(v), _stream_ptr(stream)))
     return v.value
 
 

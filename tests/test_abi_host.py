@@ -43,7 +43,7 @@ def test_lattice_validation(ez):
     assert e.value.code == ez.EZ_EINVAL
     h = ctypes.c_void_p()
     A = (ctypes.c_double * 16)(*([1.0] * 16))
-    assert ez.lib().ez_lattice_create(4, A, ctypes.byref(h)) == ez.EZ_EINVAL
+    assert ez.lib().ez_lattice_create(4, A, 1.0, ctypes.byref(h)) == ez.EZ_EINVAL
     assert b"d = 4" in ez.lib().ez_last_error()
     lat = ez.Lattice(W.lattice("fcc"))
     assert lat.d == 3
@@ -124,3 +124,22 @@ def test_epstein_zeta_buffer_checks(ez):
         ez.ez_epstein_zeta_static(lat, 3.0, [0.0, 0.0], y, np.zeros(5))
     with pytest.raises(ValueError, match="re holds 1"):
         ez.ez_epstein_zeta_static(lat, 3.0, [0.0, 0.0], y, np.zeros(1))
+
+
+def test_lattice_scale_argument(ez):
+    import numpy as np
+
+    A = W.lattice("hexagonal")
+    with pytest.raises(ez.EzError) as e:
+        ez.Lattice(A, scale=0.0)
+    assert e.value.code == ez.EZ_EINVAL
+    with pytest.raises(ez.EzError) as e:
+        ez.Lattice(A, scale=float("nan"))
+    assert e.value.code == ez.EZ_EINVAL
+    # the scaled lattice plans like the lattice built from scale * A (the plan sees A only)
+    spec = ez.sum_spec([3.0], [[3]])
+    q = ez.quadrature(W.Quad(n_u=8, n_v=8))
+    a = ez.ez_plan_describe(ez.Lattice(A, scale=1.2), spec, q)
+    b = ez.ez_plan_describe(ez.Lattice(1.2 * A), spec, q)
+    assert (a.lambda_, a.r_real, a.r_recip, list(a.M)) == (b.lambda_, b.r_real, b.r_recip, list(b.M))
+    assert np.allclose(ez.Lattice(A, scale=1.2).A, 1.2 * A)

@@ -374,3 +374,15 @@ def test_mixed_batch_matches_single(ez):
     for i in range(len(probs)):
         one = ez.ez_lattice_sums([lats[i]], [specs[i]], [quads[i]])
         assert np.array_equal(one[0], many[i])
+
+
+def test_err_est_bounds_the_quadrature_error(ez):
+    # zeta^(2)_{Z^2}(3,3) = Z_6(0) = 4 zeta(3) beta(3), beta(3) = pi^3/32 (Cor. one/two-body)
+    exact = 4 * 1.2020569031595942854 * math.pi ** 3 / 32
+    L = ez.Lattice(W.lattice("square"))
+    for n in (4, 6, 10):
+        q = ez.quadrature(W.Quad(n_u=n, n_v=n, u_rule=1, lam=1.0, r_real=6.0, r_recip=6.0))
+        v, err = ez.ez_lattice_sum_nbody(L, [3.0, 3.0], q, err_est=True)
+        assert v == ez.ez_lattice_sum_nbody(L, [3.0, 3.0], q)  # the estimate does not change the value
+        assert abs(v - exact) <= err, (n, v, exact, err)
+        assert err < 0.1 * abs(exact)

@@ -62,8 +62,16 @@ def test_rejects_tables_beyond_the_static_area(ez):
     with pytest.raises(ez.EzError) as e:
         ez.ez_epstein_zeta_static(L, 5.0, np.zeros(3), y, re)
     assert e.value.code == ez.EZ_EINVAL and "static area" in str(e.value)
-    # host buffers are refused too (they would need staging memory)
-    with pytest.raises(ez.EzError) as e:
-        ez.ez_epstein_zeta_static(ez.Lattice(W.lattice("square")), 3.0, np.zeros(2),
-                                  torch.zeros((2, 2), dtype=torch.float64), torch.zeros(2, dtype=torch.float64))
-    assert e.value.code == ez.EZ_EINVAL
+    # host buffers are refused too (they would need staging memory): by the binding, and by
+    # the C ABI itself when called directly
+    sq = ez.Lattice(W.lattice("square"))
+    with pytest.raises(ValueError):
+        ez.ez_epstein_zeta_static(sq, 3.0, np.zeros(2), torch.zeros((2, 2), dtype=torch.float64),
+                                  torch.zeros(2, dtype=torch.float64))
+    import ctypes
+
+    yh, rh, x0 = np.zeros((2, 2)), np.zeros(2), np.zeros(2)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = ez.lib().ez_epstein_zeta_static(sq.handle, 3.0, x0.ctypes.data_as(dp), ctypes.c_void_p(yh.ctypes.data), 2,
+                                         ctypes.c_void_p(rh.ctypes.data), None, None)
+    assert rc == ez.EZ_EINVAL
