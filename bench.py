@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "config1", "config2", "config3", "config4", "serve", "epstein"])
+                    choices=["headline", "config1", "config2", "config3", "config4", "serve", "epstein", "nbody-n"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     ap.add_argument("--split-sum", action="store_true",
                     help="N > 1: split every config-3 sum over the ranks by Duffy line groups")
@@ -653,6 +653,47 @@ def run_epstein(args, local):
                               "ms_per_call": ms, "dtype": "f64", "max_err_vs_oracle_256_rel_to_max_1_absZ": err}))
 
 
+# ----------------------------------------------------------------------------- large n
+def run_nbody_n(args, local):
+    """n-body zeta functions zeta^(n)(3,..,3) for n = 2..51 on the square and hexagonal
+    lattices at unit density (Sec. 4.4): values normalised by Z_3(0)^n (the bound
+    |zeta^(n)| <= prod_i Z_{nu_i}(0) makes every ratio <= 1), and GPU time per sum against
+    n -- one Epstein zeta evaluation per node and distinct exponent, so the cost grows only
+    through the n-factor product (per-factor evaluation, n <= 8, for comparison)."""
+    import numpy as np
+
+    from paper_2504_11989_gb300 import workloads as W
+
+    C = Ctx(local)
+    ez = C.ez
+    ns = list(range(2, 52))
+    out = {}
+    for lat in ("square", "hexagonal"):
+        A = W.lattice(lat)
+        L = ez.Lattice(A)
+        z0 = ez.ez_epstein_zeta(L, 3.0, np.zeros(2), np.zeros((1, 2)))[0][0]
+        q = W.Quad(n_u=128, n_v=128, u_rule=1, lam=0.0, r_real=0.0, r_recip=0.0)
+        probs = [W.nbody_problem(lat, 3.0, n, q) for n in ns]
+        r = time_batch(C, probs, ez.EZ_FP64, max(3, args.steps // 4), args.warmup)
+        ms_n = []
+        for n in (2, 3, 5, 8, 16, 32, 51):
+            rn = time_batch(C, [W.nbody_problem(lat, 3.0, n, q)], ez.EZ_FP64, 5, 3)
+            ms_n.append({"n": n, "ms": rn["ms"]})
+        pf = []
+        for n in (2, 3, 4, 6, 8):
+            p = W.Problem(f"{lat}:pf{n}", A, [3.0] * n, [[1] * n], q)
+            rp = time_batch(C, [p], ez.EZ_FP64, 5, 3, extra_quad={"dedupe": 0})
+            pf.append({"n": n, "ms": rp["ms"]})
+        ratio = [float(r["vals"][i, 0] / z0 ** n) for i, n in enumerate(ns)]
+        out[lat] = {"Z3_0": float(z0), "n": ns, "zeta_over_Z0_pow_n": ratio,
+                    "bound_holds": bool(all(0.0 < x <= 1.0 for x in ratio)),
+                    "monotone": bool(all(a >= b for a, b in zip(ratio, ratio[1:]))),
+                    "batch_ms_all_n": r["ms"], "ms_per_sum_vs_n": ms_n, "per_factor_ms_vs_n": pf}
+    print(json.dumps({"metric": METRIC, "workload": "nbody-n: zeta^(n)(3,..,3), n = 2..51, square and hexagonal "
+                      "(unit density), 256^2 BZ grid (4 x 128 x 128 nodes), FP64", "results": out,
+                      "unit": "ms per sum", "n_gpus": 1}))
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -673,6 +714,8 @@ def main():
                               higher_is_better=True)))
     elif args.workload == "epstein":
         run_epstein(args, local)
+    elif args.workload == "nbody-n":
+        run_nbody_n(args, local)
     else:
         run_single(args, local)
 
