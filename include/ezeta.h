@@ -222,12 +222,15 @@ int ez_batch_sizes(ez_batch b, long long* device_bytes, long long* staging_bytes
  * work overlaps with the running ones.  A request's result does not depend on which
  * other requests share its tick (every sum's items and reductions are its own).
  * Server time is CLOCK_MONOTONIC seconds. */
+#define EZ_REQ_ERR_EST 1 /* ez_request.flags: also return an error estimate (see ez_result) */
+
 typedef struct {
   int d;
   double A[9];            /* row-major d x d */
   ez_sum_spec spec;
   ez_quadrature quad;
   unsigned long long tag; /* caller's label, returned with the result */
+  int flags;              /* 0 or EZ_REQ_ERR_EST */
 } ez_request;
 
 typedef struct {
@@ -235,6 +238,10 @@ typedef struct {
   int status;                 /* EZ_OK, or the error of this request (EZ_EDOMAIN, EZ_ENOMEM, ...) */
   double value[EZ_MAX_PROD];  /* value of each product of the spec */
   double t_submit, t_start, t_done;  /* submit, launch of its tick, completion seen by the worker */
+  double err_est[EZ_MAX_PROD];  /* with EZ_REQ_ERR_EST: |value - value on the embedded coarse rule|,
+                                   as ez_lattice_sum_nbody's err_est (the coarse sum runs in the same
+                                   tick); NaN otherwise.  The mixed form's rounding adds at most its
+                                   stated bound, 1e-10 relative. */
 } ez_result;
 
 typedef struct {
@@ -245,7 +252,11 @@ typedef struct {
 
 #define EZ_SERVER_DRYRUN 1 /* plan and schedule without touching the GPU (values NaN) */
 
-/* mem_budget_bytes: device memory the server may hold for running ticks (> 0);
+/* Device memory: every tick allocates its tables from a memory pool owned by the server, in
+ * stream order, and returns them in stream order when its results have been copied out, so the
+ * worker never synchronises the device; the pool keeps up to mem_budget_bytes for reuse.
+ * Requests are planned by ez_server_submit on the caller's thread; the worker only launches.
+ * mem_budget_bytes: device memory the server may hold for running ticks (> 0);
  * n_streams: concurrent ticks (1..16); max_batch: requests per tick (1..65536);
  * max_pending: queue capacity (ez_server_submit returns EZ_EBUSY beyond it). */
 typedef struct ez_server_s* ez_server;

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <array>
@@ -2173,9 +2174,11 @@ double mono_now() {
 
 struct SrvReq {
   unsigned long long ticket = 0, tag = 0;
-  ez_lattice_s lat;
+  std::shared_ptr<ez_lattice_s> lat;  // stable address: the plans point at it
   ez_sum_spec spec;
   ez_quadrature quad;
+  int flags = 0;
+  Plan plan, plan_coarse;  // made by ez_server_submit on the submitting thread
   double t_submit = 0.0;
   size_t est_bytes = 0;  // device bytes of a tick holding this request alone
   int status = EZ_OK;    // planning error, reported as the result
@@ -2185,13 +2188,14 @@ struct Tick {
   bool busy = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  char* d = nullptr;
-  size_t dcap = 0;
+  char* d = nullptr;   // device memory of the tick, stream-ordered from the server's pool
+  size_t dbytes = 0;   // its size, counted against the budget until the tick completes
   char* h = nullptr;
   size_t hcap = 0;
   double* hout = nullptr;
   size_t hout_cap = 0;
   std::vector<SrvReq> reqs;
+  std::vector<int> slot, slot_coarse;  // batch index of each request (and of its coarse rule, or -1)
   ez_batch_s batch;
   double t_start = 0.0;
   int error = EZ_OK;
@@ -2214,6 +2218,8 @@ struct ez_server_s {
   ez_serve_stats st;
   int n_busy = 0;
   double busy_since = 0.0;
+  cudaMemPool_t pool = nullptr;      // device memory of the ticks (stream-ordered, no device sync)
+  std::vector<void*> retired_host;   // outgrown pinned staging, freed when the server is destroyed
 };
 
 namespace {
@@ -2222,17 +2228,21 @@ bool dryrun(const ez_server_s* S) { return (S->flags & EZ_SERVER_DRYRUN) != 0; }
 
 size_t held_bytes(const ez_server_s* S) {
   size_t b = 0;
-  for (const Tick& T : S->ticks) b += T.dcap;
+  for (const Tick& T : S->ticks) b += T.dbytes;
   return b;
 }
 
-void push_result(ez_server_s* S, const SrvReq& q, int status, const double* v, double t_start, double t_done) {
+void push_result(ez_server_s* S, const SrvReq& q, int status, const double* v, const double* vc, double t_start,
+                 double t_done) {
   ez_result r;
   std::memset(&r, 0, sizeof r);
   r.ticket = q.ticket;
   r.tag = q.tag;
   r.status = status;
-  for (int p = 0; p < EZ_MAX_PROD; ++p) r.value[p] = v ? v[p] : std::nan("");
+  for (int p = 0; p < EZ_MAX_PROD; ++p) {
+    r.value[p] = v ? v[p] : std::nan("");
+    r.err_est[p] = (v && vc) ? std::fabs(v[p] - vc[p]) : std::nan("");
+  }
   r.t_submit = q.t_submit;
   r.t_start = t_start;
   r.t_done = t_done;
@@ -2242,65 +2252,72 @@ void push_result(ez_server_s* S, const SrvReq& q, int status, const double* v, d
   if (status != EZ_OK) S->st.failed++;
 }
 
-// launches one tick for T.reqs (called without the lock; only the worker touches T)
+// grows a pinned host buffer geometrically; the outgrown one is kept until the server is
+// destroyed (freeing pinned memory would synchronise the device under the running ticks)
+template <typename P>
+int grow_pinned(ez_server_s* S, P*& buf, size_t& cap, size_t need, const char* what) {
+  if (need <= cap) return EZ_OK;
+  const size_t ncap = std::max(need, 2 * cap);
+  void* nb = nullptr;
+  if (cudaMallocHost(&nb, ncap) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EZ_ENOMEM, "pinned %s of %zu bytes failed", what, ncap);
+  }
+  if (buf) S->retired_host.push_back((void*)buf);
+  buf = (P*)nb;
+  cap = ncap;
+  return EZ_OK;
+}
+
+// launches one tick for T.reqs (called without the lock; only the worker touches T).  The
+// plans come from ez_server_submit; a request with EZ_REQ_ERR_EST adds its coarse-rule plan.
+// The tick's device memory comes from the server's pool in stream order and goes back to it
+// in stream order after the results are copied out: nothing here synchronises the device.
 int launch_tick(ez_server_s* S, Tick& T) {
   const int n = (int)T.reqs.size();
-  std::vector<ez_lattice> lats(n);
-  std::vector<ez_sum_spec> specs(n);
-  std::vector<ez_quadrature> quads(n);
-  for (int i = 0; i < n; ++i) {
-    lats[i] = &T.reqs[i].lat;
-    specs[i] = T.reqs[i].spec;
-    quads[i] = T.reqs[i].quad;
-  }
   T.batch = ez_batch_s();
-  int rc = batch_plan(T.batch, n, lats.data(), specs.data(), quads.data());
-  if (!rc) rc = batch_layout(T.batch, false);
-  if (rc) return rc;
-  if (dryrun(S)) {  // account the memory a real tick would hold
-    T.dcap = std::max(T.dcap, T.batch.dbytes);
-    return EZ_OK;
+  T.slot.assign(n, -1);
+  T.slot_coarse.assign(n, -1);
+  std::vector<Plan>& plans = T.batch.plans;
+  for (int i = 0; i < n; ++i) {
+    T.slot[i] = (int)plans.size();
+    plans.push_back(T.reqs[i].plan);
+    if (T.reqs[i].flags & EZ_REQ_ERR_EST) {
+      T.slot_coarse[i] = (int)plans.size();
+      plans.push_back(T.reqs[i].plan_coarse);
+    }
   }
-  if (T.batch.dbytes > T.dcap) {
-    if (T.d) cudaFree(T.d);
+  T.batch.n_req = (int)plans.size();
+  int rc = batch_layout(T.batch, false);
+  if (rc) return rc;
+  T.dbytes = T.batch.dbytes;
+  if (dryrun(S)) return EZ_OK;  // account the memory a real tick would hold
+  if (cudaMallocFromPoolAsync((void**)&T.d, T.batch.dbytes, S->pool, T.stream) != cudaSuccess) {
+    cudaGetLastError();
     T.d = nullptr;
-    T.dcap = 0;
-    if (cudaMalloc(&T.d, T.batch.dbytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(EZ_ENOMEM, "tick allocation of %zu bytes failed", T.batch.dbytes);
-    }
-    T.dcap = T.batch.dbytes;
+    T.dbytes = 0;
+    return fail(EZ_ENOMEM, "tick allocation of %zu bytes failed", T.batch.dbytes);
   }
-  if (T.batch.hbytes > T.hcap) {
-    if (T.h) cudaFreeHost(T.h);
-    T.h = nullptr;
-    T.hcap = 0;
-    if (cudaMallocHost(&T.h, T.batch.hbytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(EZ_ENOMEM, "pinned staging of %zu bytes failed", T.batch.hbytes);
-    }
-    T.hcap = T.batch.hbytes;
+  const size_t ob = sizeof(double) * EZ_MAX_PROD * T.batch.n_req;
+  rc = grow_pinned(S, T.h, T.hcap, T.batch.hbytes, "staging");
+  if (!rc) rc = grow_pinned(S, T.hout, T.hout_cap, ob, "output");
+  if (!rc) {
+    T.batch.d = T.d;
+    T.batch.h = T.h;
+    T.batch.owns = false;
+    rc = batch_layout(T.batch, true);
   }
-  const size_t ob = sizeof(double) * EZ_MAX_PROD * n;
-  if (ob > T.hout_cap) {
-    if (T.hout) cudaFreeHost(T.hout);
-    T.hout = nullptr;
-    T.hout_cap = 0;
-    if (cudaMallocHost(&T.hout, ob) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(EZ_ENOMEM, "pinned output of %zu bytes failed", ob);
-    }
-    T.hout_cap = ob;
+  if (!rc && cudaMemcpyAsync(T.d, T.h, T.batch.hbytes, cudaMemcpyHostToDevice, T.stream) != cudaSuccess)
+    rc = fail(EZ_ECUDA, "staging upload failed");
+  if (!rc) rc = batch_launch(T.batch, T.stream);
+  if (!rc && cudaMemcpyAsync(T.hout, T.d + T.batch.o_out, ob, cudaMemcpyDeviceToHost, T.stream) != cudaSuccess)
+    rc = fail(EZ_ECUDA, "result download failed");
+  cudaFreeAsync(T.d, T.stream);  // back to the pool once the stream has passed this point
+  T.d = nullptr;
+  if (rc) {
+    cudaGetLastError();
+    return rc;
   }
-  T.batch.d = T.d;
-  T.batch.h = T.h;
-  T.batch.owns = false;
-  rc = batch_layout(T.batch, true);
-  if (rc) return rc;
-  EZ_CUDA(cudaMemcpyAsync(T.d, T.h, T.batch.hbytes, cudaMemcpyHostToDevice, T.stream));
-  rc = batch_launch(T.batch, T.stream);
-  if (rc) return rc;
-  EZ_CUDA(cudaMemcpyAsync(T.hout, T.d + T.batch.o_out, ob, cudaMemcpyDeviceToHost, T.stream));
   EZ_CUDA(cudaEventRecord(T.done, T.stream));
   return EZ_OK;
 }
@@ -2322,9 +2339,13 @@ void server_loop(ez_server_s* S) {
       }
       if (!fin) continue;
       const double now = mono_now();
+      const bool vals = !err && !dryrun(S);
       for (size_t i = 0; i < T.reqs.size(); ++i)
-        push_result(S, T.reqs[i], err, (err || dryrun(S)) ? nullptr : T.hout + i * EZ_MAX_PROD, T.t_start, now);
+        push_result(S, T.reqs[i], err, vals ? T.hout + (size_t)T.slot[i] * EZ_MAX_PROD : nullptr,
+                    vals && T.slot_coarse[i] >= 0 ? T.hout + (size_t)T.slot_coarse[i] * EZ_MAX_PROD : nullptr,
+                    T.t_start, now);
       T.reqs.clear();
+      T.dbytes = 0;
       T.busy = false;
       T.error = EZ_OK;
       if (--S->n_busy == 0) S->st.busy_seconds += now - S->busy_since;
@@ -2337,20 +2358,20 @@ void server_loop(ez_server_s* S) {
       if (T.busy || S->pending.empty() || S->stop) continue;
       size_t others = 0;
       for (const Tick& U : S->ticks)
-        if (&U != &T) others += U.dcap;
+        if (&U != &T) others += U.dbytes;
       const size_t room = S->budget > others ? S->budget - others : 0;
       size_t sum = 0;
       std::vector<SrvReq> take;
       while (!S->pending.empty() && (int)take.size() < S->max_batch) {
         SrvReq& q = S->pending.front();
         if (q.status != EZ_OK) {
-          push_result(S, q, q.status, nullptr, 0.0, mono_now());
+          push_result(S, q, q.status, nullptr, nullptr, 0.0, mono_now());
           S->pending.pop_front();
           progressed = true;
           continue;
         }
         if (q.est_bytes > S->budget) {
-          push_result(S, q, EZ_ENOMEM, nullptr, 0.0, mono_now());
+          push_result(S, q, EZ_ENOMEM, nullptr, nullptr, 0.0, mono_now());
           S->pending.pop_front();
           progressed = true;
           continue;
@@ -2406,6 +2427,23 @@ extern "C" int ez_server_create(size_t mem_budget_bytes, int n_streams, int max_
       return rc;
     }
     cudaGetDevice(&S->device);
+    // a pool of its own: ticks allocate and free in stream order (no device synchronisation);
+    // it keeps up to the budget for reuse, and never makes one stream wait for another to
+    // reuse memory (only memory whose release the GPU has already passed is reused)
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    unsigned long long keep = mem_budget_bytes;
+    int no = 0;
+    if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess) {
+      cudaGetLastError();
+      ez_server_destroy(S, 0);
+      return fail(EZ_ECUDA, "device memory pool creation failed");
+    }
     for (Tick& T : S->ticks) {
       if (cudaStreamCreateWithFlags(&T.stream, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -2425,23 +2463,39 @@ extern "C" int ez_server_submit(ez_server S, const ez_request* req, unsigned lon
   SrvReq q;
   const int d = req->d;
   if (d < 1 || d > 3) return fail(EZ_EINVAL, "request d = %d", d);
-  std::memset(&q.lat, 0, sizeof q.lat);
-  q.lat.d = d;
-  std::memcpy(q.lat.A, req->A, sizeof(double) * d * d);
-  q.lat.V = std::fabs(det3(d, q.lat.A));
-  if (!(q.lat.V > 0.0) || !invert(d, q.lat.A, q.lat.Ai)) return fail(EZ_EINVAL, "singular lattice matrix");
+  if (req->flags & ~EZ_REQ_ERR_EST) return fail(EZ_EINVAL, "request flags %d", req->flags);
+  q.lat = std::make_shared<ez_lattice_s>();
+  ez_lattice_s& L = *q.lat;
+  std::memset(&L, 0, sizeof L);
+  L.d = d;
+  std::memcpy(L.A, req->A, sizeof(double) * d * d);
+  L.V = std::fabs(det3(d, L.A));
+  if (!(L.V > 0.0) || !invert(d, L.A, L.Ai)) return fail(EZ_EINVAL, "singular lattice matrix");
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
-      q.lat.AiT[i * d + j] = q.lat.Ai[j * d + i];
-      q.lat.At[i * d + j] = q.lat.A[j * d + i];
+      L.AiT[i * d + j] = L.Ai[j * d + i];
+      L.At[i * d + j] = L.A[j * d + i];
     }
   q.spec = req->spec;
   q.quad = req->quad;
   q.tag = req->tag;
-  {  // plan it alone: validity and device footprint
+  q.flags = req->flags;
+  {  // plan it here, on the submitting thread: validity, device footprint, and the plans the
+     // worker launches (it never plans)
+    int rc = make_plan(q.lat.get(), q.spec, q.quad, q.plan);
     ez_batch_s B;
-    ez_lattice lp = &q.lat;
-    int rc = batch_plan(B, 1, &lp, &q.spec, &q.quad);
+    if (!rc) {
+      B.n_req = 1;
+      B.plans.assign(1, q.plan);
+      if (q.flags & EZ_REQ_ERR_EST) {
+        ez_quadrature qc = q.quad;
+        qc.n_u = std::max(1, (q.quad.n_u + 1) / 2);
+        qc.n_v = std::max(1, (q.quad.n_v + 1) / 2);
+        rc = make_plan(q.lat.get(), q.spec, qc, q.plan_coarse);
+        B.n_req = 2;
+        B.plans.push_back(q.plan_coarse);
+      }
+    }
     if (!rc) rc = batch_layout(B, false);
     q.status = rc;
     q.est_bytes = rc ? 0 : B.dbytes;
@@ -2518,12 +2572,13 @@ extern "C" int ez_server_destroy(ez_server S, int timeout_ms) {
   if (S->worker.joinable()) S->worker.join();
   for (Tick& T : S->ticks) {
     if (T.stream) cudaStreamSynchronize(T.stream);
-    if (T.d) cudaFree(T.d);
     if (T.h) cudaFreeHost(T.h);
     if (T.hout) cudaFreeHost(T.hout);
     if (T.done) cudaEventDestroy(T.done);
     if (T.stream) cudaStreamDestroy(T.stream);
   }
+  for (void* p : S->retired_host) cudaFreeHost(p);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
   return EZ_OK;
 }

@@ -58,15 +58,19 @@ class ez_sum_spec(ctypes.Structure):
     ]
 
 
+EZ_REQ_ERR_EST = 1
+
+
 class ez_request(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("A", ctypes.c_double * 9), ("spec", ez_sum_spec),
-                ("quad", ez_quadrature), ("tag", ctypes.c_ulonglong)]
+                ("quad", ez_quadrature), ("tag", ctypes.c_ulonglong), ("flags", ctypes.c_int)]
 
 
 class ez_result(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_ulonglong), ("tag", ctypes.c_ulonglong), ("status", ctypes.c_int),
                 ("value", ctypes.c_double * EZ_MAX_PROD), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("err_est", ctypes.c_double * EZ_MAX_PROD)]
 
 
 class ez_serve_stats(ctypes.Structure):
@@ -430,7 +434,7 @@ def ez_diag_fp32_peak(stream=None) -> float:
     return v.value
 
 
-def make_request(A, nu, expo, q: ez_quadrature, tag: int = 0) -> ez_request:
+def make_request(A, nu, expo, q: ez_quadrature, tag: int = 0, err_est: bool = False) -> ez_request:
     A = np.asarray(A, dtype=np.float64)
     R = ez_request()
     R.d = A.shape[0]
@@ -441,6 +445,7 @@ def make_request(A, nu, expo, q: ez_quadrature, tag: int = 0) -> ez_request:
     R.spec = sum_spec(nu, expo)
     R.quad = q
     R.tag = tag
+    R.flags = EZ_REQ_ERR_EST if err_est else 0
     return R
 
 

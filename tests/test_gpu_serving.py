@@ -106,3 +106,21 @@ def test_served_results_match_the_oracle(ez, oracle_mod):
         got, ref = np.array(r.value[:npr]), np.asarray(ref[:npr])
         tol = 1e-10 if prec == ez.EZ_MIXED else 1e-13
         assert np.all(np.abs(got - ref) <= tol * np.abs(ref)), (p.name, prec, got, ref)
+
+
+def test_served_error_estimate(ez, oracle_mod):
+    """EZ_REQ_ERR_EST: the served value is unchanged (bitwise) and comes with the embedded
+    coarse-rule estimate, which bounds its error against the oracle's converged value."""
+    p = W.nbody_problem("hexagonal", 3.0, 3, W.Quad(n_u=8, n_v=8, u_rule=1, lam=1.0, r_real=6.0, r_recip=6.0))
+    truth = oracle_mod.nbody(W.nbody_problem("hexagonal", 3.0, 3, W.Quad(n_u=48, n_v=48, u_rule=1, lam=1.0,
+                                                                             r_real=6.0, r_recip=6.0)), threads=16)[0]
+    srv = ez.Server(256 << 20, n_streams=2, max_batch=4)
+    q = ez.quadrature(p.quad)
+    a = srv.submit(ez.make_request(p.A, p.nu, p.expo, q, 1, err_est=True))
+    b = srv.submit(ez.make_request(p.A, p.nu, p.expo, q, 2))
+    ra, rb = srv.wait(a, 60000), srv.wait(b, 60000)
+    srv.close()
+    assert ra.status == 0 and rb.status == 0
+    assert ra.value[0] == rb.value[0]
+    assert np.isnan(rb.err_est[0]) and np.isfinite(ra.err_est[0])
+    assert abs(ra.value[0] - truth) <= ra.err_est[0]

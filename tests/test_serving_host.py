@@ -101,3 +101,26 @@ def test_poll_and_queue_limits(ez):
     assert {r.ticket for r in got} == tickets
     assert Counter(r.status for r in got) == Counter({0: 50})
     srv.close()
+
+
+def test_error_estimate_flag_is_planned_with_its_coarse_rule(ez):
+    # EZ_REQ_ERR_EST adds the embedded coarse-rule sum to the request's tick: the tick holds
+    # more device memory; unknown flags are refused at submission
+    A = W.lattice("square")
+    q = ez.quadrature(W.Quad(n_u=16, n_v=16, u_rule=1, lam=1.0, r_real=6.0, r_recip=6.0))
+    peaks = []
+    for flag in (False, True):
+        srv = ez.Server(1 << 30, n_streams=1, max_batch=1, dryrun=True)
+        t = srv.submit(ez.make_request(A, [3.0], [[3]], q, err_est=flag))
+        r = srv.wait(t, 10000)
+        assert r.status == 0
+        peaks.append(srv.stats().peak_device_bytes)
+        srv.close()
+    assert peaks[1] > peaks[0]
+    bad = ez.make_request(A, [3.0], [[3]], q)
+    bad.flags = 6
+    srv = ez.Server(1 << 30, n_streams=1, max_batch=1, dryrun=True)
+    with pytest.raises(ez.EzError) as e:
+        srv.submit(bad)
+    assert e.value.code == ez.EZ_EINVAL
+    srv.close()
