@@ -248,6 +248,10 @@ typedef struct {
   long long submitted, completed, failed, ticks, max_batch_seen;
   double busy_seconds;        /* union of the intervals with at least one tick in flight */
   long long peak_device_bytes;
+  /* resident tables: the incomplete-gamma table of each order a (Phi_a, tabulated in t, the
+   * same for every lattice) is built once, by the first tick that needs it, and read by every
+   * later tick: tables built and (tick, table) reuses */
+  long long phi_tables_built, phi_tables_reused;
 } ez_serve_stats;
 
 #define EZ_SERVER_DRYRUN 1 /* plan and schedule without touching the GPU (values NaN) */

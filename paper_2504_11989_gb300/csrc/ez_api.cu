@@ -866,10 +866,17 @@ struct ez_batch_s {
   int n_phase = 0, max_phase_pairs = 0;
   size_t o_req = 0, o_items = 0, o_rj = 0, o_gj = 0, o_pj = 0, o_tj = 0, o_lreq = 0, o_lseg0 = 0, o_lnseg = 0,
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
-  int n_phi = 0, n_tay = 0, n_pcopy = 0;
-  size_t o_pcj = 0, o_hj = 0;
+  int n_phi = 0, n_tay = 0;
+  int n_phi_jobs = 0;  // phitab jobs of a run (groups whose table this batch fills)
+  size_t o_hj = 0;
   std::vector<std::pair<int, int>> phi_master;  // per distinct a: (request, nu index) computing the table
-  std::vector<std::array<int, 3>> phi_copy;     // (request, nu index, group) copying it
+  // Phi tables held outside the batch (a server's resident tables), per group: the binary64,
+  // binary32 and float-float tables (null: the batch holds the group's table), whether this
+  // batch fills it (phitab job), and with how many intervals.  Set after a first layout pass.
+  std::vector<std::array<void*, 3>> phi_ext;
+  std::vector<char> phi_fill;
+  std::vector<int> phi_fill_nint;
+  std::vector<cudaEvent_t> phi_ready;  // recorded on the run's stream right after its phitab launch
   struct FarGroup {
     int d, ndm;
     bool mixed;
@@ -952,12 +959,14 @@ int batch_layout(ez_batch_s& B, bool fill) {
   const size_t h_hj = hl.take(sizeof(HboxJob) * n_req);
   int& n_phi = B.n_phi;
   int& n_tay = B.n_tay;
+  std::vector<std::vector<int>> phi_group;  // Phi table group of each (request, slot), -1 unused
   n_phi = n_tay = 0;
   for (int r = 0; r < n_req; ++r)
     if (plans[r].near_active) n_tay += plans[r].spec.n_distinct;
-  // Phi tables depend on a alone (up to the argument scale of each record): one table per
-  // distinct a, computed for the member with the most intervals, copied to the others
-  // (slot j < EZ_MAX_NU: reciprocal order j; slot EZ_MAX_NU + j: real-space order j)
+  // Phi tables are tabulated in t itself (reciprocal vectors are stored scaled), so they
+  // depend on the order a alone: one table per distinct a, computed with the most intervals
+  // any member needs and read by every member (slot j < EZ_MAX_NU: reciprocal order j; slot
+  // EZ_MAX_NU + j: real-space order j)
   {
     std::vector<std::vector<std::pair<int, int>>> groups;
     for (int r = 0; r < n_req; ++r)
@@ -974,7 +983,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
           groups[g].push_back({r, slot});
         }
     B.phi_master.clear();
-    B.phi_copy.clear();
+    phi_group.assign(n_req, std::vector<int>(2 * EZ_MAX_NU, -1));
     for (int g = 0; g < (int)groups.size(); ++g) {
       size_t m = 0;
       for (size_t i = 1; i < groups[g].size(); ++i)
@@ -982,16 +991,15 @@ int batch_layout(ez_batch_s& B, bool fill) {
             phi_slot(plans[groups[g][m].first], groups[g][m].second).n_int)
           m = i;
       B.phi_master.push_back(groups[g][m]);
-      for (size_t i = 0; i < groups[g].size(); ++i)
-        if (i != m) B.phi_copy.push_back({groups[g][i].first, groups[g][i].second, g});
+      for (auto& rs : groups[g]) phi_group[rs.first][rs.second] = g;
     }
     n_phi = (int)B.phi_master.size();
-    B.n_pcopy = (int)B.phi_copy.size();
   }
-  B.o_pj = dl.take(sizeof(PhiJob) * n_phi);
-  const size_t h_pj = hl.take(sizeof(PhiJob) * n_phi);
-  B.o_pcj = dl.take(sizeof(PhiCopyJob) * std::max(B.n_pcopy, 1));
-  const size_t h_pcj = hl.take(sizeof(PhiCopyJob) * std::max(B.n_pcopy, 1));
+  const bool ext = (int)B.phi_ext.size() == n_phi;  // resident tables supplied for these groups
+  B.n_phi_jobs = 0;
+  for (int g = 0; g < n_phi; ++g) B.n_phi_jobs += (!ext || !B.phi_ext[g][0] || B.phi_fill[g]) ? 1 : 0;
+  B.o_pj = dl.take(sizeof(PhiJob) * std::max(B.n_phi_jobs, 1));
+  const size_t h_pj = hl.take(sizeof(PhiJob) * std::max(B.n_phi_jobs, 1));
   B.o_tj = dl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
   const size_t h_tj = hl.take(sizeof(TaylorJob) * std::max(n_tay, 1));
   B.o_lreq = dl.take(sizeof(int) * n_lines);
@@ -1075,13 +1083,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_tab[r].assign(2 * EZ_MAX_NU, 0);
     o_tabf[r].assign(2 * EZ_MAX_NU, 0);
     o_tabff[r].assign(2 * EZ_MAX_NU, 0);
-    for (int k = 0; k < (p.real_tab ? 2 : 1); ++k)
-      for (int j = 0; j < p.spec.n_distinct; ++j) {
-        const int slot = k * EZ_MAX_NU + j, ni = phi_slot(p, slot).n_int;
-        o_tab[r][slot] = dl.take(sizeof(double) * kRec * ni);
-        o_tabf[r][slot] = dl.take(sizeof(float) * kRec * ni);
-        o_tabff[r][slot] = dl.take(sizeof(float) * kRecFF * ni);
-      }
     const size_t na = p.alpha.size() / 3;
     o_tay[r] = dl.take(sizeof(double) * std::max<size_t>(na, 1) * p.spec.n_distinct);
     o_phig[r] = p.near ? dl.take(sizeof(double) * p.rcap * (2 * p.ell + 1) * p.spec.n_distinct) : 0;
@@ -1089,6 +1090,23 @@ int batch_layout(ez_batch_s& B, bool fill) {
                                   p.spec.n_distinct)
                         : 0;
   }
+  // the Phi tables: one per group, read by every (request, slot) of the group
+  std::vector<size_t> o_gtab(n_phi, 0), o_gtabf(n_phi, 0), o_gtabff(n_phi, 0);
+  for (int g = 0; g < n_phi; ++g) {
+    if (ext && B.phi_ext[g][0]) continue;
+    const int ni = phi_slot(plans[B.phi_master[g].first], B.phi_master[g].second).n_int;
+    o_gtab[g] = dl.take(sizeof(double) * kRec * ni);
+    o_gtabf[g] = dl.take(sizeof(float) * kRec * ni);
+    o_gtabff[g] = dl.take(sizeof(float) * kRecFF * ni);
+  }
+  for (int r = 0; r < n_req; ++r)
+    for (int slot = 0; slot < 2 * EZ_MAX_NU; ++slot) {
+      const int g = phi_group[r][slot];
+      if (g < 0) continue;
+      o_tab[r][slot] = o_gtab[g];
+      o_tabf[r][slot] = o_gtabf[g];
+      o_tabff[r][slot] = o_gtabff[g];
+    }
   std::vector<size_t> o_phase(B.n_phase), o_phaseff(B.n_phase, 0);
   std::vector<char> phase_mixed(B.n_phase, 0);
   for (int r = 0; r < n_req; ++r)
@@ -1112,6 +1130,12 @@ int batch_layout(ez_batch_s& B, bool fill) {
   char* D = B.d;
   char* Hs = B.h;
   auto dptr = [&](size_t o) { return (void*)(D + o); };
+  // table k (0 binary64, 1 binary32, 2 float-float) of (request r, slot): resident or the batch's
+  auto tab_ptr = [&](int r, int slot, int k) -> void* {
+    const int g = phi_group[r][slot];
+    if (ext && g >= 0 && B.phi_ext[g][0]) return B.phi_ext[g][k];
+    return dptr(k == 0 ? o_tab[r][slot] : k == 1 ? o_tabf[r][slot] : o_tabff[r][slot]);
+  };
   // ---- fill host staging
   ReqDesc* reqs = (ReqDesc*)(Hs + h_req);
   Item* items = (Item*)(Hs + h_items);
@@ -1145,9 +1169,13 @@ int batch_layout(ez_batch_s& B, bool fill) {
     std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
     R.V = L->V;
     R.lam = p.lam;
-    R.c_lam = kPi * p.lam * p.lam;
+    R.c_phys = kPi * p.lam * p.lam;
+    const double sc = std::sqrt(R.c_phys);  // reciprocal vectors in units of 1/s
+    R.inv_s = 1.0 / sc;
+    for (int i = 0; i < 9; ++i) R.AiTs[i] = sc * L->AiT[i];
+    R.c_lam = 1.0;
     R.vol_fac = std::pow(p.lam, p.d) / L->V;
-    R.R2_recip = p.r_recip * p.r_recip;
+    R.R2_recip = R.c_phys * p.r_recip * p.r_recip;
     R.eps = p.eps;
     R.inv_eps = 1.0 / p.eps;
     for (int j = 0; j < p.spec.n_distinct; ++j) {
@@ -1159,9 +1187,9 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.nu_f[j] = (float)nu;
       R.phi[j] = p.phi[j];
       R.phi[j].c_lam = R.c_lam;
-      R.phi[j].tab = (const double*)dptr(o_tab[r][j]);
-      R.phi[j].tabf = (const float*)dptr(o_tabf[r][j]);
-      R.phi[j].tabff = (const float*)dptr(o_tabff[r][j]);
+      R.phi[j].tab = (const double*)tab_ptr(r, j, 0);
+      R.phi[j].tabf = (const float*)tab_ptr(r, j, 1);
+      R.phi[j].tabff = (const float*)tab_ptr(r, j, 2);
     }
     for (int i = 0; i < 3; ++i) {
       R.M[i] = p.M[i];
@@ -1173,10 +1201,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.rec = (const G4*)dptr(o_rec[r]);
     R.recf = (const float4*)dptr(o_recf[r]);
     R.reclo = (const float4*)dptr(o_reclo[r]);
-    R.R2f = (float)(p.r_recip * p.r_recip);
+    R.R2f = (float)R.R2_recip;
     R.work = (unsigned long long*)dptr(B.o_work) + 3 * r;
-    R.c_lam_f = (float)R.c_lam;
-    ff_split(R.c_lam, R.c_lam_ff.x, R.c_lam_ff.y);
+    R.c_lam_f = 1.0f;
+    R.c_lam_ff = make_float2(1.0f, 0.0f);
     R.order_chain = p.spec.n_distinct >= 3;
     for (int j = 1; j < p.spec.n_distinct; ++j) R.order_chain &= p.spec.nu[j] == p.spec.nu[0] + 2.0 * j;
     R.n_rec = 0;
@@ -1220,7 +1248,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       RJ.lo[i] = p.rlo[i];
       RJ.ext[i] = p.rext[i];
     }
-    RJ.R2 = p.R2enum;
+    RJ.R2 = R.c_phys * p.R2enum;
     RJ.cap = (int)p.rcap;
     RJ.out = (G4*)dptr(o_rec[r]);
     RJ.outf = (float4*)dptr(o_recf[r]);
@@ -1235,7 +1263,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     GJ.use_tab = p.real_tab ? 1 : 0;
     for (int j = 0; p.real_tab && j < p.spec.n_distinct; ++j) {
       GJ.phi[j] = p.phi_real[j];
-      GJ.phi[j].tab = (const double*)dptr(o_tab[r][EZ_MAX_NU + j]);
+      GJ.phi[j].tab = (const double*)tab_ptr(r, EZ_MAX_NU + j, 0);
       GJ.phi[j].tabf = nullptr;
       GJ.phi[j].tabff = nullptr;
     }
@@ -1263,33 +1291,18 @@ int batch_layout(ez_batch_s& B, bool fill) {
         T.n_chunk = (int)taylor_chunks(p);
       }
   }
-  for (int g = 0; g < n_phi; ++g) {
+  for (int g = 0, jb = 0; g < n_phi; ++g) {
+    if (ext && B.phi_ext[g][0] && !B.phi_fill[g]) continue;  // resident and already filled
     const int r = B.phi_master[g].first, j = B.phi_master[g].second;
-    PhiJob& J = pjobs[g];
+    PhiJob& J = pjobs[jb++];
     const PhiInfo& P = phi_slot(plans[r], j);
     J.a = P.a;
-    J.c_lam = j < EZ_MAX_NU ? reqs[r].c_lam : 1.0;
+    J.c_lam = 1.0;  // tables in t (reciprocal vectors scaled, real-space argument t itself)
     J.t_geo_end = P.t_geo_end;
-    J.n_int = P.n_int;
-    J.out = (double*)dptr(o_tab[r][j]);
-    J.outf = (float*)dptr(o_tabf[r][j]);
-    J.outff = (float*)dptr(o_tabff[r][j]);
-  }
-  {
-    PhiCopyJob* cj = (PhiCopyJob*)(Hs + h_pcj);
-    for (int c = 0; c < B.n_pcopy; ++c) {
-      const int r = B.phi_copy[c][0], j = B.phi_copy[c][1];
-      const int rm = B.phi_master[B.phi_copy[c][2]].first, jm = B.phi_master[B.phi_copy[c][2]].second;
-      cj[c].src = (const double*)dptr(o_tab[rm][jm]);
-      cj[c].srcf = (const float*)dptr(o_tabf[rm][jm]);
-      cj[c].srcff = (const float*)dptr(o_tabff[rm][jm]);
-      cj[c].out = (double*)dptr(o_tab[r][j]);
-      cj[c].outf = (float*)dptr(o_tabf[r][j]);
-      cj[c].outff = (float*)dptr(o_tabff[r][j]);
-      cj[c].c_lam = j < EZ_MAX_NU ? reqs[r].c_lam : 1.0;
-      cj[c].t_geo_end = phi_slot(plans[r], j).t_geo_end;
-      cj[c].n_int = phi_slot(plans[r], j).n_int;
-    }
+    J.n_int = (ext && B.phi_ext[g][0]) ? B.phi_fill_nint[g] : P.n_int;
+    J.out = (double*)tab_ptr(r, j, 0);
+    J.outf = (float*)tab_ptr(r, j, 1);
+    J.outff = (float*)tab_ptr(r, j, 2);
   }
   {
     PhaseJob* phj = (PhaseJob*)(Hs + h_phj);
@@ -1381,17 +1394,17 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
         dreqs, (const RecipJob*)dptr(B.o_rj));
     EZ_LAUNCHED();
   }
-  int max_int = 0, max_int_copy = 0;
+  int max_int = 0;
   for (auto& m : B.phi_master) max_int = std::max(max_int, phi_slot(B.plans[m.first], m.second).n_int);
-  for (auto& c : B.phi_copy) max_int_copy = std::max(max_int_copy, phi_slot(B.plans[c[0]], c[1]).n_int);
-  phitab_kernel<<<dim3((max_int + kPhiIv - 1) / kPhiIv, B.n_phi), kPhiIv * kNC, 0, stream>>>((const PhiJob*)dptr(B.o_pj));
-  EZ_LAUNCHED();
-  if (B.n_pcopy) {
-    phicopy_kernel<<<dim3((max_int_copy * kRec + 127) / 128, B.n_pcopy), 128, 0, stream>>>(
-        (const PhiCopyJob*)dptr(B.o_pcj));
+  for (size_t g = 0; g < B.phi_fill_nint.size(); ++g)
+    if (B.phi_fill[g]) max_int = std::max(max_int, B.phi_fill_nint[g]);
+  if (B.n_phi_jobs > 0) {
+    phitab_kernel<<<dim3((max_int + kPhiIv - 1) / kPhiIv, B.n_phi_jobs), kPhiIv * kNC, 0, stream>>>(
+        (const PhiJob*)dptr(B.o_pj));
     EZ_LAUNCHED();
   }
-  // the real-space box reads the real-order Phi tables: after phitab/phicopy
+  for (cudaEvent_t e : B.phi_ready) EZ_CUDA(cudaEventRecord(e, stream));
+  // the real-space box reads the real-order Phi tables: after phitab
   long long max_cells = 0;
   for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
   gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
@@ -1852,6 +1865,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   R.nu[0] = nu;
   std::memcpy(R.A, L->A, sizeof R.A);
   std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+  for (int i = 0; i < 9; ++i) R.AiTs[i] = std::sqrt(kPi) * p.lam * L->AiT[i];  // scaled units
   R.lam = p.lam;
   for (int i = 0; i < 3; ++i) {
     R.M[i] = p.M[i];
@@ -1865,7 +1879,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
     RJ.lo[i] = p.rlo[i];
     RJ.ext[i] = p.rext[i];
   }
-  RJ.R2 = p.R2enum;
+  RJ.R2 = kPi * p.lam * p.lam * p.R2enum;
   RJ.cap = (int)p.rcap;
   RJ.out = (G4*)(D + o_rec);
   RJ.outf = (float4*)(D + o_recf);
@@ -1883,7 +1897,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   GJ.out = (double*)(D + o_gbox);
   PhiJob& PJ = *(PhiJob*)(Hs + h_pj);
   PJ.a = p.phi[0].a;
-  PJ.c_lam = kPi * p.lam * p.lam;
+  PJ.c_lam = 1.0;  // the table in t
   PJ.t_geo_end = p.phi[0].t_geo_end;
   PJ.n_int = p.phi[0].n_int;
   PJ.out = (double*)(D + o_tab);
@@ -1906,15 +1920,17 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   A.nu = nu;
   A.pref = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
   A.vol_fac = std::pow(p.lam, d) / L->V;
-  A.c_lam = kPi * p.lam * p.lam;
+  A.c_lam = 1.0;
   A.lam = p.lam;
-  A.R2_recip = p.r_recip * p.r_recip;
+  A.R2_recip = kPi * p.lam * p.lam * p.r_recip * p.r_recip;
   A.two_over_nu = 2.0 / nu;
   std::memcpy(A.A, L->A, sizeof A.A);
-  std::memcpy(A.AiT, L->AiT, sizeof A.AiT);
+  // reciprocal space in scaled units s = sqrt(pi) lam: y~ = s A^{-T} y_reduced, and x / s in the
+  // phases x.(g + y) = (x / s).(g~ + y~)
+  for (int i = 0; i < 9; ++i) A.AiT[i] = std::sqrt(kPi) * p.lam * L->AiT[i];
   std::memcpy(A.At, L->At, sizeof A.At);
   for (int i = 0; i < d; ++i) {
-    A.x[i] = x[i];
+    A.x[i] = x[i] / (std::sqrt(kPi) * p.lam);
     A.xt[i] = xt[i];
     A.mx[i] = mx[i];
   }
@@ -2063,6 +2079,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   R.nu[0] = nu;
   std::memcpy(R.A, L->A, sizeof R.A);
   std::memcpy(R.AiT, L->AiT, sizeof R.AiT);
+  for (int i = 0; i < 9; ++i) R.AiTs[i] = std::sqrt(kPi) * p.lam * L->AiT[i];  // scaled units
   R.lam = p.lam;
   for (int i = 0; i < 3; ++i) {
     R.M[i] = p.M[i];
@@ -2077,7 +2094,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
     RJ.lo[i] = p.rlo[i];
     RJ.ext[i] = p.rext[i];
   }
-  RJ.R2 = p.R2enum;
+  RJ.R2 = kPi * p.lam * p.lam * p.R2enum;
   RJ.cap = (int)p.rcap;
   RJ.out = (G4*)(D + o_rec);
   RJ.outf = (float4*)(D + o_recf);
@@ -2094,7 +2111,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   PhiJob PJ;
   std::memset(&PJ, 0, sizeof PJ);
   PJ.a = p.phi[0].a;
-  PJ.c_lam = kPi * p.lam * p.lam;
+  PJ.c_lam = 1.0;  // the table in t
   PJ.t_geo_end = p.phi[0].t_geo_end;
   PJ.n_int = p.phi[0].n_int;
   PJ.out = (double*)(D + o_tab);
@@ -2117,15 +2134,17 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   A.nu = nu;
   A.pref = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
   A.vol_fac = std::pow(p.lam, d) / L->V;
-  A.c_lam = kPi * p.lam * p.lam;
+  A.c_lam = 1.0;
   A.lam = p.lam;
-  A.R2_recip = p.r_recip * p.r_recip;
+  A.R2_recip = kPi * p.lam * p.lam * p.r_recip * p.r_recip;
   A.two_over_nu = 2.0 / nu;
   std::memcpy(A.A, L->A, sizeof A.A);
-  std::memcpy(A.AiT, L->AiT, sizeof A.AiT);
+  // reciprocal space in scaled units s = sqrt(pi) lam: y~ = s A^{-T} y_reduced, and x / s in the
+  // phases x.(g + y) = (x / s).(g~ + y~)
+  for (int i = 0; i < 9; ++i) A.AiT[i] = std::sqrt(kPi) * p.lam * L->AiT[i];
   std::memcpy(A.At, L->At, sizeof A.At);
   for (int i = 0; i < d; ++i) {
-    A.x[i] = x[i];
+    A.x[i] = x[i] / (std::sqrt(kPi) * p.lam);
     A.xt[i] = xt[i];
     A.mx[i] = mx[i];
   }
@@ -2220,6 +2239,15 @@ struct ez_server_s {
   double busy_since = 0.0;
   cudaMemPool_t pool = nullptr;      // device memory of the ticks (stream-ordered, no device sync)
   std::vector<void*> retired_host;   // outgrown pinned staging, freed when the server is destroyed
+  // resident Phi tables, one per order a (key 2a), kMaxInt intervals: they depend on a alone
+  // (tables in t), so every later tick reads them instead of building its own
+  struct PhiRes {
+    char* p = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ready = nullptr;  // after the phitab launch that filled it
+  };
+  std::map<int, PhiRes> phi_res;
+  size_t phi_res_bytes = 0;
 };
 
 namespace {
@@ -2227,7 +2255,7 @@ namespace {
 bool dryrun(const ez_server_s* S) { return (S->flags & EZ_SERVER_DRYRUN) != 0; }
 
 size_t held_bytes(const ez_server_s* S) {
-  size_t b = 0;
+  size_t b = S->phi_res_bytes;
   for (const Tick& T : S->ticks) b += T.dbytes;
   return b;
 }
@@ -2292,10 +2320,73 @@ int launch_tick(ez_server_s* S, Tick& T) {
   if (rc) return rc;
   T.dbytes = T.batch.dbytes;
   if (dryrun(S)) return EZ_OK;  // account the memory a real tick would hold
+  // resident Phi tables: read those of earlier ticks (after their fill, which may run on
+  // another stream), build the missing ones into new resident tables in this tick
+  std::vector<cudaEvent_t> waits;
+  std::vector<int> fresh;  // resident tables created by this tick (dropped again if it fails)
+  auto drop_fresh = [&]() {
+    for (int key : fresh) {
+      auto it = S->phi_res.find(key);
+      if (it == S->phi_res.end()) continue;
+      cudaFreeAsync(it->second.p, T.stream);
+      if (it->second.ready) cudaEventDestroy(it->second.ready);
+      S->phi_res_bytes -= it->second.bytes;
+      S->phi_res.erase(it);
+    }
+    fresh.clear();
+  };
+  {
+    ez_batch_s& B = T.batch;
+    const int ng = B.n_phi;
+    B.phi_ext.assign(ng, {nullptr, nullptr, nullptr});
+    B.phi_fill.assign(ng, 0);
+    B.phi_fill_nint.assign(ng, 0);
+    B.phi_ready.clear();
+    const size_t b64 = sizeof(double) * kRec * kMaxInt, b32 = sizeof(float) * kRec * kMaxInt,
+                 bff = sizeof(float) * kRecFF * kMaxInt;
+    for (int g = 0; g < ng; ++g) {
+      const PhiInfo& P = phi_slot(B.plans[B.phi_master[g].first], B.phi_master[g].second);
+      auto it = S->phi_res.find(P.two_a);
+      if (it == S->phi_res.end()) {
+        ez_server_s::PhiRes e;
+        e.bytes = b64 + b32 + bff;
+        if (cudaMallocFromPoolAsync((void**)&e.p, e.bytes, S->pool, T.stream) != cudaSuccess) {
+          cudaGetLastError();
+          drop_fresh();
+          return fail(EZ_ENOMEM, "resident Phi table of %zu bytes failed", e.bytes);
+        }
+        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          cudaFreeAsync(e.p, T.stream);
+          drop_fresh();
+          return fail(EZ_ECUDA, "event creation failed");
+        }
+        it = S->phi_res.emplace(P.two_a, e).first;
+        fresh.push_back(P.two_a);
+        S->phi_res_bytes += e.bytes;
+        B.phi_fill[g] = 1;
+        B.phi_fill_nint[g] = kMaxInt;
+        B.phi_ready.push_back(e.ready);
+        S->st.phi_tables_built++;
+      } else {
+        waits.push_back(it->second.ready);
+        S->st.phi_tables_reused++;
+      }
+      char* base = it->second.p;
+      B.phi_ext[g] = {base, base + b64, base + b64 + b32};
+    }
+    rc = batch_layout(B, false);  // without the resident tables
+    if (rc) {
+      drop_fresh();
+      return rc;
+    }
+    T.dbytes = B.dbytes;
+  }
   if (cudaMallocFromPoolAsync((void**)&T.d, T.batch.dbytes, S->pool, T.stream) != cudaSuccess) {
     cudaGetLastError();
     T.d = nullptr;
     T.dbytes = 0;
+    drop_fresh();
     return fail(EZ_ENOMEM, "tick allocation of %zu bytes failed", T.batch.dbytes);
   }
   const size_t ob = sizeof(double) * EZ_MAX_PROD * T.batch.n_req;
@@ -2309,6 +2400,8 @@ int launch_tick(ez_server_s* S, Tick& T) {
   }
   if (!rc && cudaMemcpyAsync(T.d, T.h, T.batch.hbytes, cudaMemcpyHostToDevice, T.stream) != cudaSuccess)
     rc = fail(EZ_ECUDA, "staging upload failed");
+  for (cudaEvent_t e : waits)
+    if (!rc && cudaStreamWaitEvent(T.stream, e, 0) != cudaSuccess) rc = fail(EZ_ECUDA, "stream wait failed");
   if (!rc) rc = batch_launch(T.batch, T.stream);
   if (!rc && cudaMemcpyAsync(T.hout, T.d + T.batch.o_out, ob, cudaMemcpyDeviceToHost, T.stream) != cudaSuccess)
     rc = fail(EZ_ECUDA, "result download failed");
@@ -2316,6 +2409,7 @@ int launch_tick(ez_server_s* S, Tick& T) {
   T.d = nullptr;
   if (rc) {
     cudaGetLastError();
+    drop_fresh();
     return rc;
   }
   EZ_CUDA(cudaEventRecord(T.done, T.stream));
@@ -2578,6 +2672,11 @@ extern "C" int ez_server_destroy(ez_server S, int timeout_ms) {
     if (T.stream) cudaStreamDestroy(T.stream);
   }
   for (void* p : S->retired_host) cudaFreeHost(p);
+  for (auto& kv : S->phi_res) {
+    if (kv.second.p) cudaFreeAsync(kv.second.p, S->ticks[0].stream);
+    if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+  }
+  if (!S->phi_res.empty() && S->ticks[0].stream) cudaStreamSynchronize(S->ticks[0].stream);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
   return EZ_OK;

@@ -87,7 +87,12 @@ struct ReqDesc {
   int d, nsect, n_ui, n_v, u_rule, n_distinct, n_prod, ell, prec;
   int expo[EZ_MAX_PROD][EZ_MAX_NU];
   double A[9], AiT[9];
-  double V, lam, c_lam, vol_fac, R2_recip, eps;
+  // Reciprocal space is stored in scaled units: every reciprocal vector (the list G, the node
+  // k, the cutoff) is multiplied by s = sqrt(pi) lam, so that |G~ + k~|^2 is the argument t of
+  // Phi itself.  The Phi tables then depend on the order a alone (shared by every sum).
+  double AiTs[9];        // s A^{-T}: k~ = s A^{-T} k_reduced, G~ = s A^{-T} h
+  double c_phys, inv_s;  // pi lam^2 = s^2 and 1/s (Taylor tensors are taken in physical k)
+  double V, lam, c_lam, vol_fac, R2_recip, eps;  // c_lam = 1 (scaled units), R2_recip = (s r_recip)^2
   double nu[EZ_MAX_NU], pref[EZ_MAX_NU], two_over_nu[EZ_MAX_NU];
   double sig[EZ_MAX_NU];  // singular coefficient sigma_nu of s_hat
   int islog[EZ_MAX_NU];

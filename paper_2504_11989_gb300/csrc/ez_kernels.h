@@ -45,19 +45,6 @@ struct PhiJob {
   float* outff;  // float-float table (may be null)
 };
 
-// Copy of one Phi table computed for another request with the same a (the records do not
-// depend on the lattice except for the argument scale s = c_lam / h, which is rewritten).
-struct PhiCopyJob {
-  const double* src;
-  const float* srcf;
-  const float* srcff;
-  double* out;
-  float* outf;
-  float* outff;
-  double c_lam;
-  double t_geo_end;
-  int n_int;
-};
 
 struct TaylorJob {
   int req, nu_index;
@@ -80,8 +67,8 @@ struct PhaseJob {
 struct EpsteinArgs {
   int d, m;
   double nu, pref, vol_fac, c_lam, lam, R2_recip, two_over_nu;
-  double A[9], AiT[9], At[9];
-  double x[3], xt[3];  // x and A^{-1} x
+  double A[9], AiT[9], At[9];  // AiT scaled by s = sqrt(pi) lam (reciprocal vectors in scaled units)
+  double x[3], xt[3];  // x / s (paired with scaled reciprocal vectors in the phases) and A^{-1} x
   int x_in_lattice;
   int M[3], box[3], mx[3];
   const double* gbox;
@@ -100,7 +87,6 @@ __global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs);
 __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs);
 __global__ void hbox_kernel(const ReqDesc* reqs, const HboxJob* jobs);
 __global__ void phitab_kernel(const PhiJob* jobs);
-__global__ void phicopy_kernel(const PhiCopyJob* jobs);
 __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 __global__ void taylor_real_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 __global__ void phiseq_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);

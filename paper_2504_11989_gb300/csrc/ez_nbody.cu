@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         const float2 a1 = __ldg(R->v_ff + e);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const ff t = ff_mul(ffd(R->AiT[i * 3 + ax_a] * u), ff{a1.x, a1.y});
+          const ff t = ff_mul(ffd(R->AiTs[i * 3 + ax_a] * u), ff{a1.x, a1.y});
           kA[e * 3 + i] = make_float2(t.hi, t.lo);
         }
       } else {
@@ -801,8 +801,8 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         const float2 a2 = __ldg(R->v_ff + v2_0 + v2l);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const ff t = ff_add(ff_mul(ffd(R->AiT[i * 3 + ax_b] * (s2 ? -u : u)), ff{a2.x, a2.y}),
-                              ffd(R->AiT[i * 3 + ax_c] * u));
+          const ff t = ff_add(ff_mul(ffd(R->AiTs[i * 3 + ax_b] * (s2 ? -u : u)), ff{a2.x, a2.y}),
+                              ffd(R->AiTs[i * 3 + ax_c] * u));
           kB[(s2 * vch + v2l) * 3 + i] = make_float2(t.hi, t.lo);
         }
       }
@@ -865,9 +865,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   double kca[3], kcb[3], kcc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    kca[i] = R->AiT[i * 3 + ax_a];
-    kcb[i] = R->AiT[i * 3 + ax_b];
-    kcc[i] = R->AiT[i * 3 + ax_c];
+    kca[i] = R->AiTs[i * 3 + ax_a];
+    kcb[i] = R->AiTs[i * 3 + ax_b];
+    kcc[i] = R->AiTs[i * 3 + ax_c];
   }
   unsigned terms = 0, coefs = 0, qterms = 0;
   const int nn = nv * nv2;
@@ -1080,8 +1080,8 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
       H[e] = make_double2(hr, hi);
   }
   __syncthreads();
-  const double kca0 = R->AiT[0 * 2 + ax_a], kca1 = R->AiT[1 * 2 + ax_a];
-  const double kcc0 = R->AiT[0 * 2 + ax_c], kcc1 = R->AiT[1 * 2 + ax_c];
+  const double kca0 = R->AiTs[0 * 2 + ax_a], kca1 = R->AiTs[1 * 2 + ax_a];
+  const double kcc0 = R->AiTs[0 * 2 + ax_c], kcc1 = R->AiTs[1 * 2 + ax_c];
   double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   unsigned terms = 0, coefs = 0, qterms = 0;
   if constexpr (MIXED) {
@@ -1201,7 +1201,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
   unsigned terms = 0, coefs = 0, qterms = 0;
   double f[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
   if constexpr (MIXED) {
-    const ff k[1] = {ffd(R->AiT[0] * u)};
+    const ff k[1] = {ffd(R->AiTs[0] * u)};
     const float4* ph = R->phaseff + (size_t)iu * R->phase_mp1;
     float s[NDM], c[NDM];
 #pragma unroll
@@ -1228,7 +1228,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
 #pragma unroll
     for (int p = 0; p < EZ_MAX_PROD; ++p) f[p] = (double)ws[p].hi + (double)ws[p].lo;
   } else {
-  double k[1] = {R->AiT[0] * u};
+  double k[1] = {R->AiTs[0] * u};
   const double2* ph = R->phase + (size_t)iu * R->phase_mp1;
   double sr[NDM], acc[NDM], Z[NDM];
 #pragma unroll

@@ -8,8 +8,9 @@ namespace ez {
 
 // ---------------------------------------------------------------------------
 // Reciprocal lattice points h with |A^{-T} h| <= R (box lo..hi), compacted in
-// lexicographic order by one block (ordered prefix sums), written as
-// (G_0, G_1, G_2, |G|^2).  The count goes to req->n_rec.
+// lexicographic order by one block (ordered prefix sums), written in scaled units
+// G~ = s A^{-T} h as (G~_0, G~_1, G~_2, |G~|^2) (J.R2 is scaled too).  The count goes to
+// req->n_rec.
 // ---------------------------------------------------------------------------
 __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
   const RecipJob J = jobs[blockIdx.x];
@@ -35,7 +36,7 @@ __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs) {
       h[0] = (int)r + J.lo[0];
       for (int i = 0; i < d; ++i) {
         double s = 0.0;
-        for (int k = 0; k < d; ++k) s = fma(R->AiT[i * d + k], (double)h[k], s);
+        for (int k = 0; k < d; ++k) s = fma(R->AiTs[i * d + k], (double)h[k], s);
         G[i] = s;
         G2 = fma(s, s, G2);
       }
@@ -283,39 +284,6 @@ __global__ void __launch_bounds__(kPhiIv * kNC) phitab_kernel(const PhiJob* jobs
   }
 }
 
-// One thread per record element of a copy job (blockIdx.y): the coefficient records of a
-// table computed for the same a, with the argument scale of the destination request.
-__global__ void phicopy_kernel(const PhiCopyJob* jobs) {
-  const PhiCopyJob J = jobs[blockIdx.y];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iv = e / kRec, k = e - iv * kRec;
-  if (iv >= J.n_int) return;
-  const size_t o = (size_t)iv * kRec;
-  double tm, h;
-  phi_interval_bounds(iv, J.t_geo_end, tm, h);
-  const size_t off = (size_t)iv * kRecFF;
-  if (k >= 4) {
-    J.out[o + k] = J.src[o + k];
-    J.outf[o + k] = J.srcf[o + k];
-    J.outff[off + 2 * k] = J.srcff[off + 2 * k];
-    J.outff[off + 2 * k + 1] = J.srcff[off + 2 * k + 1];
-  } else if (k == 0) {
-    reinterpret_cast<int*>(J.outff + off)[0] = reinterpret_cast<const int*>(J.srcff + off)[0];
-    reinterpret_cast<int*>(J.outff + off)[1] = reinterpret_cast<const int*>(J.srcff + off)[1];
-    ff_split(J.c_lam / h, J.outff[off + 2], J.outff[off + 3]);
-    ff_split(tm / J.c_lam, J.outff[off + 4], J.outff[off + 5]);
-    J.outff[off + 6] = J.outff[off + 7] = 0.0f;
-    J.out[o] = J.src[o];  // int n, int 0
-    J.out[o + 1] = J.c_lam / h;
-    J.out[o + 2] = J.src[o + 2];
-    J.out[o + 3] = 0.0;
-    reinterpret_cast<int*>(J.outf + o)[0] = reinterpret_cast<const int*>(J.srcf + o)[0];
-    J.outf[o + 1] = (float)(J.c_lam / h);
-    J.outf[o + 2] = J.srcf[o + 2];
-    J.outf[o + 3] = 0.0f;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Taylor tensors of Z^reg_nu at k = 0:  D[alpha] = d^alpha Z^reg(0) / alpha!, |alpha|
 // even <= 2 ell.  One thread per (request, distinct nu, alpha); serial sums in a
@@ -437,7 +405,7 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
   const int K2 = alpha[0] + alpha[1] + alpha[2];
   const int K = K2 / 2;
   const double afact = factd(alpha[0]) * factd(alpha[1]) * factd(alpha[2]);
-  const double c = R->c_lam;
+  const double c = R->c_phys;  // the tensors are derivatives in physical k
   double sreal[EZ_MAX_NU], srec[EZ_MAX_NU];
 #pragma unroll
   for (int jn = 0; jn < EZ_MAX_NU; ++jn) sreal[jn] = srec[jn] = 0.0;
@@ -453,7 +421,7 @@ __global__ void __launch_bounds__(kTaylorThreads) taylor_kernel(const ReqDesc* r
   for (int hi = threadIdx.x; hi < R->n_rec; hi += blockDim.x) {
     const G4 G = R->rec[hi];
     if (G.w == 0.0 || G.w > R->R2_recip) continue;
-    const double Gv[3] = {G.x, G.y, G.z};
+    const double Gv[3] = {G.x * R->inv_s, G.y * R->inv_s, G.z * R->inv_s};  // physical G
     for (int n = K; n <= K2; ++n) {
       const int jj = 2 * n - K2;  // number of linear factors
       // coefficient of k^alpha in (2 G.k)^jj (|k|^2)^(n-jj)

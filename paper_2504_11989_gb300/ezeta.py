@@ -76,7 +76,8 @@ class ez_result(ctypes.Structure):
 class ez_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("ticks", ctypes.c_longlong), ("max_batch_seen", ctypes.c_longlong),
-                ("busy_seconds", ctypes.c_double), ("peak_device_bytes", ctypes.c_longlong)]
+                ("busy_seconds", ctypes.c_double), ("peak_device_bytes", ctypes.c_longlong),
+                ("phi_tables_built", ctypes.c_longlong), ("phi_tables_reused", ctypes.c_longlong)]
 
 
 EZ_SERVER_DRYRUN = 1
