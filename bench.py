@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "config1", "config2", "config3", "config4", "serve", "epstein", "nbody-n"])
+                    choices=["headline", "config1", "config2", "config3", "config4", "serve", "epstein", "nbody-n",
+                             "phase"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of requests")
     ap.add_argument("--split-sum", action="store_true",
                     help="N > 1: split every config-3 sum over the ranks by Duffy line groups")
@@ -694,6 +695,38 @@ def run_nbody_n(args, local):
                       "unit": "ms per sum", "n_gpus": 1}))
 
 
+# ----------------------------------------------------------------------------- Sec. 5
+def run_phase(args, local):
+    """fcc/bcc stability with (12,6) and (8,4) Lennard-Jones and ATM interactions (Sec. 5):
+    the lattice sums of both unit-nearest-neighbour lattices on the GPU (two Epstein zeta
+    values and one ATM energy each, 128^3-class grid), then the critical ATM coupling at
+    each pressure from the host-side enthalpy minimisation."""
+    from paper_2504_11989_gb300 import phase as P
+    from paper_2504_11989_gb300 import workloads as W
+
+    C = Ctx(local)
+    ez = C.ez
+    q = ez.quadrature(W.Quad(n_u=8, n_v=64, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0))
+    pressures = [0.0, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0]
+    out = {}
+    for n, m in ((12, 6), (8, 4)):
+        C.torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f, b = (P.coefficients(ez, name, n, m, q) for name in P.UNIT_NN)
+        C.torch.cuda.synchronize()
+        gpu_s = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        lam_c = [P.critical_coupling(f, b, p) for p in pressures]
+        out[f"({n},{m})"] = {"pressure": pressures, "lambda_c": lam_c,
+                             "fcc": {"Z_n": f.z_n, "Z_m": f.z_m, "E_atm": f.e_atm, "V": f.volume},
+                             "bcc": {"Z_n": b.z_n, "Z_m": b.z_m, "E_atm": b.e_atm, "V": b.volume},
+                             "fcc_stable_at_lambda_0": [P.enthalpy_gap(f, b, 0.0, p) > 0.0 for p in pressures],
+                             "gpu_seconds": gpu_s, "host_seconds": time.perf_counter() - t1}
+    print(json.dumps({"metric": METRIC, "workload": "phase: fcc/bcc boundary in (p, lambda), LJ (12,6) and (8,4) + "
+                      "ATM; unit nearest-neighbour lattices, 12 x 48 u x 64^2 v nodes + near part, FP64",
+                      "results": out, "n_gpus": 1}))
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -716,6 +749,8 @@ def main():
         run_epstein(args, local)
     elif args.workload == "nbody-n":
         run_nbody_n(args, local)
+    elif args.workload == "phase":
+        run_phase(args, local)
     else:
         run_single(args, local)
 

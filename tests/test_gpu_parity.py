@@ -152,8 +152,10 @@ def test_config3_atm_full_size_sampled_lines(ez, oracle_mod):
     for (s, iu), ref in zip(picks, refs):
         row = lines[s * nu_t + iu] if iu >= 0 else lines[ns * nu_t + s]
         assert np.all(np.abs(row - ref) <= TOL * np.maximum(np.abs(ref), floor[: len(ref)])), (s, iu, row, ref)
-    # the lines add up to the value (fixed-order reduction)
-    assert _close(got, lines.sum(axis=0), tol=1e-14, floor=np.max(np.abs(got)))
+    # the lines add up to the value (fixed-order compensated reduction): against the exactly
+    # rounded sum of the lines, relative to the sum of their magnitudes (the lines cancel)
+    exact = np.array([math.fsum(lines[:, q]) for q in range(lines.shape[1])])
+    assert np.all(np.abs(got - exact) <= 1e-14 * np.sum(np.abs(lines), axis=0))
 
 
 def _sampled_lines(ez, oracle_mod, prob, seed, n_pick, tol, prec=None):
