@@ -140,19 +140,25 @@ static double or_phi_t_ge1(double a, double t) {
   const double h = 0.125;
   double c = a > 0.0 ? log(fmax(a, 1.0) / t) : -log(t + 1.0 - a);
   double ec = exp(c);
-  /* (1+x)^{a-1} = (1+x)^n [sqrt(1+x)] with n = floor(a-1): a is a multiple of 1/2 */
+  /* (1+x)^{a-1} = (1+x)^n [sqrt(1+x)] with n = floor(a-1) when a is a multiple of 1/2,
+     else pow */
   int n = (int)floor(a - 1.0);
   int half = (a - 1.0) - n > 0.25;
   int na = n < 0 ? -n : n;
+  int general = fabs(2.0 * a - round(2.0 * a)) > 1e-12;
   double sum = 0.0;
   for (int k = OR_DE_KLO; k <= OR_DE_KHI; ++k) {
     double x = ec * or_de_x[k - OR_DE_KLO];
     double tx = t * x;
     if (tx > 745.0) break;
     double b = 1.0 + x, bp = 1.0;
-    for (int i = 0; i < na; ++i) bp *= b;
-    if (n < 0) bp = 1.0 / bp;
-    if (half) bp *= sqrt(b);
+    if (general) {
+      bp = pow(b, a - 1.0);
+    } else {
+      for (int i = 0; i < na; ++i) bp *= b;
+      if (n < 0) bp = 1.0 / bp;
+      if (half) bp *= sqrt(b);
+    }
     double term = bp * x * exp(-tx) * or_de_j[k - OR_DE_KLO];
     sum += term;
     /* past the mode of (1+x)^{a-1} x e^{-tx} in log x: d/dlog x = (a-1)x/(1+x) + 1 - tx < 0 */
@@ -190,10 +196,7 @@ static double or_phi_t_lt1(double a, double t) {
 }
 
 double or_phi(double a, double t) {
-  double tw = 2.0 * a;
-  long twi = lround(tw);
-  if (fabs(tw - (double)twi) > 1e-12) return NAN; /* only a in Z/2 */
-  if (t < 0.0 || isnan(t)) return NAN;
+  if (t < 0.0 || isnan(t) || !isfinite(a)) return NAN;
   if (t == 0.0) return a < 0.0 ? -1.0 / a : INFINITY;
   return t >= 1.0 ? or_phi_t_ge1(a, t) : or_phi_t_lt1(a, t);
 }

@@ -21,7 +21,7 @@ extern "C" {
 #define OR_MAXPROD 4
 #define OR_MAXELL 8
 
-/* Phi_a(t) = t^{-a} Gamma(a,t) for a in Z/2, t >= 0; Phi_a(0) = -1/a (a < 0). */
+/* Phi_a(t) = t^{-a} Gamma(a,t) for real a, t >= 0; Phi_a(0) = -1/a (a < 0). */
 double or_phi(double a, double t);
 /* E_1(t), t > 0. */
 double or_expint_e1(double t);

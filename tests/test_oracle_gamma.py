@@ -72,8 +72,18 @@ def test_phi_at_zero(oracle_mod, a):
     assert oracle_mod.phi(a, t) == pytest.approx(sing - 1.0 / a, abs=1e-11)
 
 
-def test_phi_rejects_non_half_integer(oracle_mod):
-    assert math.isnan(oracle_mod.phi(0.3, 1.0))
+@pytest.mark.parametrize("a", [-5.3, -2.05, -0.7, -0.1, 0.05, 0.3, 1.15, 2.8, 6.45])
+def test_phi_general_order(oracle_mod, a):
+    # orders of non-integer exponents (a = nu/2, (d - nu)/2 for real nu): mpmath at 30 digits,
+    # and scipy's regularised upper incomplete gamma for a > 0
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    for t in [1e-9, 1e-4, 0.05, 0.49, 0.5, 0.99, 1.0, 2.7, 11.0, 40.0, 150.0]:
+        ref = float(mp.expint(1 - a, t))
+        assert oracle_mod.phi(a, t) == pytest.approx(ref, rel=3e-15), (a, t)
+        if a > 0:
+            assert oracle_mod.phi(a, t) == pytest.approx(special.gamma(a) * special.gammaincc(a, t) * t ** (-a),
+                                                         rel=1e-13), (a, t)
 
 
 def test_phi_vs_mpmath_dense_grid(oracle_mod):

@@ -156,3 +156,48 @@ def test_zreg_direct_vs_taylor(oracle_mod, lat, nu):
             # Z - s_hat/V cancels the singular term: allow rounding at its size
             sing = abs(oracle_mod.s_hat(d, nu, u * w)) / abs(np.linalg.det(A))
             assert direct == pytest.approx(series, rel=1e-12, abs=1e-12 + 1e-14 * sing)
+
+
+# ----------------------------------------------------------------- real (non-integer) exponents
+@pytest.mark.parametrize("nu", [1.5, 2.3, 3.7, 4.25, 7.9])
+def test_real_nu_d1_closed_forms(oracle_mod, nu):
+    # Z(0) = 2 zeta(nu); Z(x, 0) = zeta(nu, x) + zeta(nu, 1 - x) (Hurwitz); and at y != 0 the
+    # periodic zeta function 2 Re Li_nu(e^{2 pi i y}) (mpmath, 30 digits)
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    assert oracle_mod.epstein_zeta(Z1, nu, [0], [0], 1.0, 9, 9).real == pytest.approx(2 * special.zeta(nu), rel=3e-15)
+    for x in (0.15, 0.6):
+        ref = special.zeta(nu, x) + special.zeta(nu, 1 - x)
+        assert oracle_mod.epstein_zeta(Z1, nu, [x], [0], 1.0, 9, 9).real == pytest.approx(ref, rel=2e-14)
+    for y in (0.07, 0.31, 0.5):
+        ref = float(2 * mp.re(mp.polylog(nu, mp.exp(2j * mp.pi * y))))
+        z = oracle_mod.epstein_zeta(Z1, nu, [0], [y], 1.2, 9, 9)
+        assert z.real == pytest.approx(ref, rel=1e-13, abs=1e-14), (nu, y)
+
+
+@pytest.mark.parametrize("lat,nu", [("hexagonal", 3.4), ("fcc", 5.5), ("square", -0.6)])
+def test_real_nu_lambda_invariance(oracle_mod, lat, nu):
+    A = W.lattice(lat)
+    d = A.shape[0]
+    y = np.linalg.inv(A).T @ (np.arange(1, d + 1) * 0.137)
+    za = oracle_mod.epstein_zeta(A, nu, np.zeros(d), y, 0.8, 9 * 0.8, 9 / 0.8)
+    zb = oracle_mod.epstein_zeta(A, nu, np.zeros(d), y, 1.3, 9 * 1.3, 9 / 1.3)
+    assert abs(za - zb) <= 2e-14 * max(1.0, abs(za))
+
+
+def test_real_nu_lattice_sums(oracle_mod):
+    # Cor. one/two-body: zeta^(2)(nu1, nu2) = Z_{nu1+nu2}(0) and zeta^(1) = 0 for real exponents
+    # (the u integral takes the eps-split, nu - d not an odd integer); three-body against the
+    # direct sum at large exponents (d = 1)
+    for lat, nus in (("square", (2.7, 3.6)), ("Z", (1.8, 2.45))):
+        A = W.lattice(lat)
+        d = A.shape[0]
+        q = W.Quad(n_u=16, n_v=16 if d == 2 else 1, u_rule=2, lam=1.0, r_real=7.0, r_recip=7.0)
+        two = oracle_mod.nbody(W.Problem("z", A, list(nus), [[1, 1]], q), threads=8)[0]
+        ref = oracle_mod.epstein_zeta(A, sum(nus), np.zeros(d), np.zeros(d), 1.0, 9, 9).real
+        assert two == pytest.approx(ref, rel=1e-13)
+        one = oracle_mod.nbody(W.Problem("z", A, [nus[0]], [[1]], q), threads=8)[0]
+        assert abs(one) < 1e-13
+    nus = (6.3, 7.1, 8.6)
+    prob = W.Problem("z", Z1, list(nus), [[1, 1, 1]], W.Quad(n_u=8, n_v=1, u_rule=2, lam=1.0, r_real=9, r_recip=9))
+    assert oracle_mod.nbody(prob)[0] == pytest.approx(brute.zeta_n_direct(Z1, nus, 600), rel=2e-14)
