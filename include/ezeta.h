@@ -38,7 +38,7 @@ extern "C" {
 #define EZ_EINVAL 1        /* bad argument: d, singular A, n, node counts, NULL pointer */
 #define EZ_EDOMAIN 2       /* pole: Gamma(nu/2) pole (nu in -2N0), y in Lambda* with nu <= d,  \
                               or a Hadamard exponent mu + 2k = 0 */
-#define EZ_EUNSUPPORTED 3  /* exponent not an integer (half-integer orders of Gamma(a,t) only) */
+#define EZ_EUNSUPPORTED 3  /* a feature this entry point does not have (e.g. EZ_MIXED in ez_epstein_zeta) */
 #define EZ_ENOMEM 4        /* device allocation failed */
 #define EZ_ECUDA 5         /* CUDA runtime error */
 #define EZ_ETIMEOUT 6      /* a bounded device or host wait ran out */
@@ -106,8 +106,8 @@ int ez_lattice_destroy(ez_lattice lat);
 /* --- Epstein zeta function (Def. "Epstein zeta function") -------------------- */
 /* Z_{Lambda,nu}(x, y_i) for i < m, by the incomplete-gamma splitting with
  * parameter lambda = V^{1/d}: re[i] + i im[i] = sum'_{z} e^{-2 pi i z.y_i} |z - x|^{-nu},
- * meromorphically continued in nu.  nu must be an integer (EZ_EUNSUPPORTED
- * otherwise); nu in -2N0 is EZ_EDOMAIN.  prec must be EZ_FP64: this entry point has no
+ * meromorphically continued in nu.  nu is any real number (orders a = nu/2 and (d - nu)/2
+ * of Gamma(a, t) need not be half-integers); nu in -2N0 is EZ_EDOMAIN.  prec must be EZ_FP64: this entry point has no
  * mixed-precision form, and EZ_MIXED returns EZ_EUNSUPPORTED (any other value EZ_EINVAL).
  *   x  : host, d doubles.
  *   y  : host or device, m*d doubles (point i at y[i*d .. i*d+d-1]).
@@ -140,7 +140,10 @@ int ez_epstein_zeta_static(ez_lattice lat, double nu, const double* x, const dou
 /* zeta^(n)_Lambda(nu_1..nu_n) through the Epstein representation and the Duffy
  * transformation (Cor. "Duffy transformation"), with the eps-split meromorphic
  * continuation of Sec. 3 when u_rule is 2.
- *   nu      : host, n integers stored as doubles (1 <= n <= 64).
+ *   nu      : host, n real exponents (1 <= n <= 64; not in -2N0).  Unless every nu_i - d is a
+ *             positive odd integer the default u rule is the eps-split (u_rule 2), whose near
+ *             part integrates u^{mu-1} log^m in closed form; a product with some mu + 2k = 0
+ *             (a pole of the closed form; the paper gives no formula for it) is EZ_EDOMAIN.
  *   value   : host or device, 1 double.
  *   err_est : host or device, 1 double, or NULL.  When given, the same sum is also
  *             computed on the embedded coarse rule -- ceil(n_u/2) u nodes per panel and

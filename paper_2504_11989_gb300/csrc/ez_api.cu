@@ -250,6 +250,7 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   std::memset(&P, 0, sizeof P);
   P.a = a;
   P.two_a = (int)std::lrint(2.0 * a);
+  P.half = is_integer(2.0 * a) ? 1 : 0;
   P.log_m = (is_integer(a) && a <= 0.0) ? (int)std::lrint(-a) : -1;
   P.t_geo_end = kT0 * std::pow(kGeoR, kNGeo);
   const double t_half_end = P.t_geo_end + 0.5 * kNHalf;
@@ -286,15 +287,15 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   // series lengths: sum_{n >= N} |ser_n| t^n (the terms n >= kNSer add < 1e-18 at t = kT0,
   // bounded by the next one) is increasing in t; breakpoint = largest t <= kT0 (bisection,
   // rounded down to binary32) where it is <= tol.  They depend on a alone: computed once
-  // per 2a and kept (planning runs for every served request).
+  // per order and kept (planning runs for every served request).
   struct SerBrk {
     float brk[6];
   };
   static std::mutex brk_mu;
-  static std::map<int, SerBrk> brk_cache;
+  static std::map<double, SerBrk> brk_cache;
   {
     std::lock_guard<std::mutex> lk(brk_mu);
-    auto it = brk_cache.find(P.two_a);
+    auto it = brk_cache.find(a);
     if (it != brk_cache.end()) {
       std::memcpy(P.ser_brk, it->second.brk, sizeof P.ser_brk);
       return;
@@ -321,7 +322,7 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   SerBrk e;
   std::memcpy(e.brk, P.ser_brk, sizeof e.brk);
   std::lock_guard<std::mutex> lk(brk_mu);
-  brk_cache[P.two_a] = e;
+  brk_cache[a] = e;
 }
 
 // Mixed form, per order a (cached: planning runs for every served request).
@@ -329,13 +330,12 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
 struct MixScan {
   double bad_mix, bad_mid;
 };
-const MixScan& mix_scan(int two_a) {
+const MixScan& mix_scan(double a) {
   static std::mutex mu;
-  static std::map<int, MixScan> cache;
+  static std::map<double, MixScan> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find(two_a);
+  auto it = cache.find(a);
   if (it != cache.end()) return it->second;
-  const double a = 0.5 * two_a;
   MixScan m{kT0, kT0};
   for (int i = 0; kT0 + 0.25 * i <= 64.0; ++i) {
     const double t = kT0 + 0.25 * i;
@@ -343,7 +343,7 @@ const MixScan& mix_scan(int two_a) {
     if (f * t > 1e-7) m.bad_mix = t;
     if (f > 1e-6) m.bad_mid = t;
   }
-  return cache[two_a] = m;
+  return cache[a] = m;
 }
 
 // Tail fit of order a beyond t_mix: g(s) = t e^t Phi_a(t), s = t_mix/t in (0, 1], Chebyshev
@@ -351,13 +351,13 @@ const MixScan& mix_scan(int two_a) {
 struct TailFit {
   float c[8];
 };
-const TailFit& tail_fit(int two_a, float tmix_f) {
+const TailFit& tail_fit(double a, float tmix_f) {
   static std::mutex mu;
-  static std::map<std::pair<int, float>, TailFit> cache;
+  static std::map<std::pair<double, float>, TailFit> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find({two_a, tmix_f});
+  auto it = cache.find({a, tmix_f});
   if (it != cache.end()) return it->second;
-  const double a = 0.5 * two_a, tmix = tmix_f;
+  const double tmix = tmix_f;
   const int N = 24;
   double gv[N], cc[N];
   for (int k = 0; k < N; ++k) {
@@ -387,7 +387,7 @@ const TailFit& tail_fit(int two_a, float tmix_f) {
     for (int q = i; q < 8; ++q) v += cc[q] * Tm[q][i];
     f.c[i] = (float)v;
   }
-  return cache[{two_a, tmix_f}] = f;
+  return cache[{a, tmix_f}] = f;
 }
 
 // regularised h = 0 series (lambda piece of the log case included)
@@ -413,16 +413,17 @@ bool near_exponents_ok(const Plan& p, int prod, std::string* why) {
     t[j] = 0;
   }
   while (true) {
-    int mu = p.d, deg = 0;
+    double mu = p.d;
+    int deg = 0;
     for (int j = 0; j < s.n_distinct; ++j) {
-      mu += t[j] * ((int)std::lrint(s.nu[j]) - p.d);
+      mu += t[j] * (s.nu[j] - p.d);
       deg += (e[j] - t[j]) * p.ell;
     }
     deg = std::min(deg, kNearMaxDeg);
     for (int k = 0; k <= deg; ++k)
-      if (mu + 2 * k == 0) {
+      if (std::fabs(mu + 2 * k) < 1e-9) {
         char b[160];
-        snprintf(b, sizeof b, "Hadamard exponent mu + 2k = 0 (mu = %d, k = %d) in product %d", mu, k, prod);
+        snprintf(b, sizeof b, "Hadamard exponent mu + 2k = 0 (mu = %g, k = %d) in product %d", mu, k, prod);
         *why = b;
         return false;
       }
@@ -461,10 +462,14 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   for (int j = 0; j < spec.n_distinct; ++j) {
     double nu = spec.nu[j];
     if (!std::isfinite(nu)) return fail(EZ_EINVAL, "non-finite exponent");
-    if (!is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
     if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
-    int dn = (int)std::lrint(nu) - d;
-    if (dn < 0 || (dn % 2) == 0) singular = true;
+    // the integrand is analytic in u only when nu - d is a positive odd integer
+    if (!is_integer(nu)) {
+      singular = true;
+    } else {
+      const int dn = (int)std::lrint(nu) - d;
+      if (dn < 0 || (dn % 2) == 0) singular = true;
+    }
   }
   if (q.n_u < 1 || q.n_u > 1 << 20) return fail(EZ_EINVAL, "n_u = %d", q.n_u);
   if (d > 1 && (q.n_v < 1 || q.n_v > 256)) return fail(EZ_EINVAL, "n_v = %d (1..256)", q.n_v);
@@ -632,7 +637,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     for (int j = 0; j < spec.n_distinct; ++j) {
       // the last grid points t = kT0 + 0.25 i with |Phi_a(t)| t > 1e-7 and |Phi_a(t)| > 1e-6:
       // Phi_a decreases, so within [kT0, t_hi] they are the uncapped ones capped at t_hi
-      const MixScan& ms = mix_scan(p.phi[j].two_a);
+      const MixScan& ms = mix_scan(p.phi[j].a);
       const double t_last = kT0 + 0.25 * std::floor((p.phi[j].t_hi - kT0) / 0.25 + 1e-9);
       tmix = std::max(tmix, std::min(ms.bad_mix, t_last) + 0.25);
       tmid = std::max(tmid, std::min(ms.bad_mid, t_last) + 0.25);
@@ -642,7 +647,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
     for (int j = 0; j < spec.n_distinct; ++j) {
       p.phi[j].t_mix_f = (float)tmix;
       p.phi[j].t_mid_f = (float)tmid;
-      const TailFit& tf = tail_fit(p.phi[j].two_a, (float)tmix);
+      const TailFit& tf = tail_fit(p.phi[j].a, (float)tmix);
       for (int i = 0; i < 8; ++i) p.phi[j].tail_p[i] = tf.c[i];
     }
   } else {
@@ -737,8 +742,8 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
 
 // sigma_nu of s_hat (Sec. 3)
 double sigma_of(int d, double nu, int* islog) {
-  int dn = (int)std::lrint(nu) - d;
-  if (dn >= 0 && dn % 2 == 0) {
+  const int dn = (int)std::lrint(nu) - d;
+  if (is_integer(nu) && dn >= 0 && dn % 2 == 0) {
     int m = dn / 2;
     *islog = 1;
     double mf = std::tgamma(m + 1.0);
@@ -1184,7 +1189,6 @@ int batch_layout(ez_batch_s& B, bool fill) {
       R.two_over_nu[j] = 2.0 / nu;
       R.pref[j] = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(p.lam, nu));
       R.sig[j] = sigma_of(p.d, nu, &R.islog[j]);
-      R.nu_f[j] = (float)nu;
       R.phi[j] = p.phi[j];
       R.phi[j].c_lam = R.c_lam;
       R.phi[j].tab = (const double*)tab_ptr(r, j, 0);
@@ -1205,6 +1209,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
     R.work = (unsigned long long*)dptr(B.o_work) + 3 * r;
     R.c_lam_f = 1.0f;
     R.c_lam_ff = make_float2(1.0f, 0.0f);
+    R.near_int_mu = 1;
+    for (int j = 0; j < p.spec.n_distinct; ++j) R.near_int_mu &= is_integer(p.spec.nu[j]) ? 1 : 0;
     R.order_chain = p.spec.n_distinct >= 3;
     for (int j = 1; j < p.spec.n_distinct; ++j) R.order_chain &= p.spec.nu[j] == p.spec.nu[0] + 2.0 * j;
     R.n_rec = 0;
@@ -1797,7 +1803,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   if (m > (size_t)1 << 31) return fail(EZ_EINVAL, "m too large");
   if (prec != EZ_FP64 && prec != EZ_MIXED) return fail(EZ_EINVAL, "prec = %d", prec);
   if (prec == EZ_MIXED) return fail(EZ_EUNSUPPORTED, "mixed precision not built yet");
-  if (!std::isfinite(nu) || !is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
+  if (!std::isfinite(nu)) return fail(EZ_EINVAL, "exponent %g is not finite", nu);
   if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
   int rc = init_constants();
   if (rc) return rc;
@@ -2011,7 +2017,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   if (!is_device_ptr(y) || !is_device_ptr(re) || (im && !is_device_ptr(im)))
     return fail(EZ_EINVAL, "ez_epstein_zeta_static takes device buffers for y, re and im "
                            "(host buffers would need staging memory)");
-  if (!std::isfinite(nu) || !is_integer(nu)) return fail(EZ_EUNSUPPORTED, "exponent %g is not an integer", nu);
+  if (!std::isfinite(nu)) return fail(EZ_EINVAL, "exponent %g is not finite", nu);
   if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
   int rc = init_constants();
   if (rc) return rc;
@@ -2239,14 +2245,14 @@ struct ez_server_s {
   double busy_since = 0.0;
   cudaMemPool_t pool = nullptr;      // device memory of the ticks (stream-ordered, no device sync)
   std::vector<void*> retired_host;   // outgrown pinned staging, freed when the server is destroyed
-  // resident Phi tables, one per order a (key 2a), kMaxInt intervals: they depend on a alone
+  // resident Phi tables, one per order a, kMaxInt intervals: they depend on a alone
   // (tables in t), so every later tick reads them instead of building its own
   struct PhiRes {
     char* p = nullptr;
     size_t bytes = 0;
     cudaEvent_t ready = nullptr;  // after the phitab launch that filled it
   };
-  std::map<int, PhiRes> phi_res;
+  std::map<double, PhiRes> phi_res;  // key: the order a
   size_t phi_res_bytes = 0;
 };
 
@@ -2323,9 +2329,9 @@ int launch_tick(ez_server_s* S, Tick& T) {
   // resident Phi tables: read those of earlier ticks (after their fill, which may run on
   // another stream), build the missing ones into new resident tables in this tick
   std::vector<cudaEvent_t> waits;
-  std::vector<int> fresh;  // resident tables created by this tick (dropped again if it fails)
+  std::vector<double> fresh;  // resident tables created by this tick (dropped again if it fails)
   auto drop_fresh = [&]() {
-    for (int key : fresh) {
+    for (double key : fresh) {
       auto it = S->phi_res.find(key);
       if (it == S->phi_res.end()) continue;
       cudaFreeAsync(it->second.p, T.stream);
@@ -2346,7 +2352,7 @@ int launch_tick(ez_server_s* S, Tick& T) {
                  bff = sizeof(float) * kRecFF * kMaxInt;
     for (int g = 0; g < ng; ++g) {
       const PhiInfo& P = phi_slot(B.plans[B.phi_master[g].first], B.phi_master[g].second);
-      auto it = S->phi_res.find(P.two_a);
+      auto it = S->phi_res.find(P.a);
       if (it == S->phi_res.end()) {
         ez_server_s::PhiRes e;
         e.bytes = b64 + b32 + bff;
@@ -2361,8 +2367,8 @@ int launch_tick(ez_server_s* S, Tick& T) {
           drop_fresh();
           return fail(EZ_ECUDA, "event creation failed");
         }
-        it = S->phi_res.emplace(P.two_a, e).first;
-        fresh.push_back(P.two_a);
+        it = S->phi_res.emplace(P.a, e).first;
+        fresh.push_back(P.a);
         S->phi_res_bytes += e.bytes;
         B.phi_fill[g] = 1;
         B.phi_fill_nint[g] = kMaxInt;
@@ -2535,6 +2541,7 @@ extern "C" int ez_server_create(size_t mem_budget_bytes, int n_streams, int max_
         cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
         cudaMemPoolSetAttribute(S->pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess) {
       cudaGetLastError();
+      S->exited = true;  // no worker yet
       ez_server_destroy(S, 0);
       return fail(EZ_ECUDA, "device memory pool creation failed");
     }
@@ -2542,6 +2549,7 @@ extern "C" int ez_server_create(size_t mem_budget_bytes, int n_streams, int max_
       if (cudaStreamCreateWithFlags(&T.stream, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        S->exited = true;  // no worker yet
         ez_server_destroy(S, 0);
         return fail(EZ_ECUDA, "stream/event creation failed");
       }
@@ -2664,19 +2672,23 @@ extern "C" int ez_server_destroy(ez_server S, int timeout_ms) {
         return fail(EZ_ETIMEOUT, "server ticks still running after %d ms", timeout_ms);
   }
   if (S->worker.joinable()) S->worker.join();
-  for (Tick& T : S->ticks) {
+  for (Tick& T : S->ticks)
     if (T.stream) cudaStreamSynchronize(T.stream);
+  // the resident tables go back to the pool while the streams still exist
+  cudaStream_t s0 = S->ticks.empty() ? nullptr : S->ticks[0].stream;
+  for (auto& kv : S->phi_res) {
+    if (kv.second.p && s0) cudaFreeAsync(kv.second.p, s0);
+    if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+  }
+  S->phi_res.clear();
+  if (s0) cudaStreamSynchronize(s0);
+  for (Tick& T : S->ticks) {
     if (T.h) cudaFreeHost(T.h);
     if (T.hout) cudaFreeHost(T.hout);
     if (T.done) cudaEventDestroy(T.done);
     if (T.stream) cudaStreamDestroy(T.stream);
   }
   for (void* p : S->retired_host) cudaFreeHost(p);
-  for (auto& kv : S->phi_res) {
-    if (kv.second.p) cudaFreeAsync(kv.second.p, S->ticks[0].stream);
-    if (kv.second.ready) cudaEventDestroy(kv.second.ready);
-  }
-  if (!S->phi_res.empty() && S->ticks[0].stream) cudaStreamSynchronize(S->ticks[0].stream);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
   return EZ_OK;

@@ -51,7 +51,7 @@ struct PhiInfo {
   double a;           // order
   double c_lam;       // t = c_lam |q|^2
   int log_m;          // a = -log_m (log case) or -1
-  int two_a;          // 2a (integer)
+  int two_a;          // 2a rounded (exact when half != 0)
   double gam;         // Gamma(a) (non-log) or (-1)^m/m! (log)
   double t_geo_end;   // kT0 * kGeoR^kNGeo
   double t_hi;        // end of the tabulated range
@@ -64,8 +64,8 @@ struct PhiInfo {
   const float* tabf;  // binary32 table (own polynomial lengths) for the mixed form (device)
   const float* tabff; // float-float table (n_int * kRecFF floats) for the mixed form (device)
   double ser[kNSer];  // entire part for t < kT0
-  float a_f;             // a in binary32 (exact: a is a small half-integer)
-  float pad_f;
+  float a_f;             // a in binary32 (exact for the half-integer orders of integer exponents)
+  int half;              // 2a is an integer: t^{-a} by square roots and integer powers, else exp/log
   // t < kT0: below ser_brk[i] the series needs only N = 4 + 2 i terms (i < 6; N = kNSer
   // above ser_brk[5]): the dropped terms sum to <= 2^-55 in absolute value.
   float ser_brk[6];
@@ -96,6 +96,7 @@ struct ReqDesc {
   double nu[EZ_MAX_NU], pref[EZ_MAX_NU], two_over_nu[EZ_MAX_NU];
   double sig[EZ_MAX_NU];  // singular coefficient sigma_nu of s_hat
   int islog[EZ_MAX_NU];
+  int near_int_mu;        // every nu_j is an integer: the Hadamard exponents mu + 2k are integers
   // real space: full box prod_i (2 M_i + 1), g = 0 outside the ball and at m = 0
   int M[3], box[3];
   int vchunk;          // d = 3: v2 rows per far-field block
@@ -127,7 +128,6 @@ struct ReqDesc {
   // float-float copies of the per-exponent constants, for the mixed form
   float2 pref_ff[EZ_MAX_NU], tov_ff[EZ_MAX_NU], vol_ff;
   double inv_eps;           // 1 / eps (near part)
-  float nu_f[EZ_MAX_NU];      // nu in binary32 (integers)
   // d <= 2: powers e^{2 pi i m u v}, m = 0..phase_mp1-1, per (u node, v node); shared by every
   // sum of a batch with the same quadrature (the phases do not depend on the lattice)
   const double2* phase;

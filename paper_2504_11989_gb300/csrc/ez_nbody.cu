@@ -284,7 +284,7 @@ __device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain,
 template <int NDM>
 __device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, ff* hs, unsigned& coefs) {
   bool need_log = false;
-  for (int j = 0; j < nd; ++j) need_log |= sphi[j].a < 1.0 && sphi[j].log_m >= 0;
+  for (int j = 0; j < nd; ++j) need_log |= sphi[j].a < 1.0 && (sphi[j].log_m >= 0 || !sphi[j].half);
   const double lt = need_log ? log(t) : 0.0;
   const double it = 1.0 / t;
   double prev = 0.0, E = 0.0;
@@ -1339,17 +1339,20 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
   N total = nint<N>(0);
   N G[kNearMaxDeg + 1], T[kNearMaxDeg + 1];
   const N eps = neps<N>(R, false), inv_eps = neps<N>(R, true), eps2 = eps * eps;
+  const bool int_mu = R->near_int_mu != 0;  // every nu_j - d an integer: integer mu, tabulated 1/n
   while (true) {
     N coef = nint<N>(1);
     long long mult = 1;  // product of binomials (exact integers)
     int mu = d, mlog = 0;
+    double mu_r = d;  // real mu (non-integer exponents)
     for (int j = 0; j < nd; ++j) {
       if (t[j]) {
         long long bj = 1;
         for (int i = 1; i <= t[j]; ++i) bj = bj * (e[j] - t[j] + i) / i;
         mult *= bj;
         for (int i = 0; i < t[j]; ++i) coef = coef * sig_w[j];
-        mu += t[j] * ((int)R->nu_f[j] - d);
+        if (int_mu) mu += t[j] * ((int)lrint(R->nu[j]) - d);
+        mu_r += t[j] * (R->nu[j] - d);
         mlog += t[j] * R->islog[j];
       }
     }
@@ -1366,13 +1369,13 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
         deg = nd2;
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
-    N epm = mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu);
+    N epm = int_mu ? (mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu)) : exp(mu_r * log(eps));
     N sumk = nint<N>(0);
     for (int k = 0; k <= deg; ++k) {
       // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
-      // reciprocals of small integers (no division in the loop)
+      // reciprocals of small integers (no division in the loop) when mu is an integer
       const int mk = mu + 2 * k;
-      const N inv = ninv(epm, mk);
+      const N inv = int_mu ? ninv(epm, mk) : 1.0 / (mu_r + 2 * k);
       N J = inv, Lp = nint<N>(1);
       for (int i = 1; i <= mlog; ++i) {
         Lp = Lp * L;
@@ -1433,8 +1436,10 @@ __device__ void near_ray_f64(const ReqDesc* R, const double* dir, double wv, dou
   const double wn = sqrt(w2), inv_wn = 1.0 / wn, inv_V = 1.0 / R->V;
   double sig_w[EZ_MAX_NU];
   for (int jn = 0; jn < nd; ++jn) {
-    const int dn = (int)lrint(R->nu[jn]) - d;
-    sig_w[jn] = R->sig[jn] * (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) * inv_V;
+    const double dr = R->nu[jn] - d;
+    const int dn = (int)lrint(dr);
+    const double pw = fabs(dr - dn) < 1e-12 ? (dn >= 0 ? ipow(wn, dn) : ipow(inv_wn, -dn)) : exp(dr * log(wn));
+    sig_w[jn] = R->sig[jn] * pw * inv_V;
   }
   near_core<double>(R, w, L, sig_w, 2.0 * wv, val);
 }

@@ -75,9 +75,53 @@ __host__ __device__ inline double phi_scaled_large(double a, double t) {
   return t * h;
 }
 
+// Legendre's continued fraction for Phi_a(t) evaluated backward from depth n (no forward
+// accumulation of rounding; converges for t > 0, fast where t is not far below a).
+__host__ __device__ inline double phi_cf_backward(double a, double t, int n) {
+  double h = t + 2.0 * n + 1.0 - a;
+  for (int i = n; i > 0; --i) h = (t + 2.0 * i - 1.0 - a) - (double)i * (i - a) / h;
+  return exp(-t) / h;
+}
+
+// Real a that is not a multiple of 1/2 (non-integer exponents).  a > 1, t < a:
+// Phi_a = Gamma(a) t^{-a} - e^{-t} sum_n t^n / (a (a+1) ... (a+n)), the lower incomplete gamma
+// by its series of positive terms (Gamma(a, t) is a sizeable part of Gamma(a) there); else for
+// t >= 1/2 the continued fraction evaluated backward, at depths 200, 400, ... until two agree;
+// for t < 1/2, Gamma(a) t^{-a} minus the entire series sum_n (-t)^n / (n! (a + n)) (a is then
+// not a pole of Gamma).
+__host__ __device__ inline double phi_general(double a, double t) {
+  if (a > 1.0 && t < a) {
+    double s = 0.0, term = 1.0 / a;
+    for (int n = 0; n < 400; ++n) {
+      if (n > 0) term *= t / (a + n);
+      s += term;
+      if (term < 1e-18 * s) break;
+    }
+    return tgamma(a) * exp(-a * log(t)) - exp(-t) * s;
+  }
+  if (t >= 0.5) {
+    double prev = phi_cf_backward(a, t, 200);
+    for (int n = 400; n <= 6400; n *= 2) {
+      const double cur = phi_cf_backward(a, t, n);
+      if (fabs(cur - prev) <= 1e-17 * fabs(cur)) return cur;
+      prev = cur;
+    }
+    return prev;
+  }
+  double s = 0.0, term = 1.0;  // (-t)^n / n!
+  for (int n = 0; n < 80; ++n) {
+    if (n > 0) term *= -t / n;
+    const double add = term / (a + n);
+    s += add;
+    if (n > 4 && fabs(add) < 1e-18 * fabs(s)) break;
+  }
+  return tgamma(a) * exp(-a * log(t)) - s;
+}
+
 __host__ __device__ inline double phi_accurate(double a, double t) {
   int two_a = (int)lrint(2.0 * a);
   if (!(t > 0.0)) return a < 0.0 ? -1.0 / a : (double)INFINITY;
+  if (fabs(2.0 * a - two_a) > 1e-12) return phi_general(a, t);
   bool integer = (two_a & 1) == 0;
   if (integer && a >= 1.0) {
     int n = two_a / 2;
@@ -183,10 +227,10 @@ static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
     for (int k = 0; k < P.log_m; ++k) tm *= t;
     return s - P.gam * tm * log(t);
   }
-  return s + P.gam * pow_half(t, P.two_a);
+  return s + P.gam * (P.half ? pow_half(t, P.two_a) : exp(-P.a * log(t)));
 }
 
-// t < kT0, binary64, with log t (log-case orders) and 1/t supplied by the caller, who
+// t < kT0, binary64, with log t (log-case and non-half-integer orders) and 1/t supplied by the caller, who
 // shares them between the orders of one reciprocal term: the entire series cut at 2^-55
 // plus the singular part.  n_used: series terms (work count).
 __device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, int& n_used) {
@@ -203,6 +247,7 @@ __device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, d
     for (int k = 0; k < P.log_m; ++k) tm *= t;
     return s - P.gam * tm * lt;
   }
+  if (!P.half) return s + P.gam * exp(-P.a * lt);  // non-half-integer order (lt = log t)
   const int e = -P.two_a;  // t^{-a} = sqrt(t)^e
   double r = (e & 1) ? sqrt(t) : 1.0;
   const int k = e >> 1;  // floor(e / 2)

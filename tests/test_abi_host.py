@@ -68,9 +68,11 @@ def test_layout_rejects_hadamard_pole_and_bad_exponents(ez):
     with pytest.raises(ez.EzError) as e:  # d = 1, nu = (-1, 2): mu_T = 1 - 2 + 1 = 0
         ez.ez_layout(1, ez.sum_spec([-1.0, 2.0], [[1, 1]]), q)
     assert e.value.code == ez.EZ_EDOMAIN
+    # a real exponent is planned with the eps-split rule (nu - d is not an odd integer)
+    assert ez.ez_layout(2, ez.sum_spec([2.5], [[2]]), ez.quadrature(W.Quad(n_u=8, n_v=4, u_rule=0)))[2] == 2
     with pytest.raises(ez.EzError) as e:
-        ez.ez_layout(2, ez.sum_spec([2.5], [[2]]), q)
-    assert e.value.code == ez.EZ_EUNSUPPORTED
+        ez.ez_layout(2, ez.sum_spec([float("nan")], [[2]]), q)
+    assert e.value.code == ez.EZ_EINVAL
     with pytest.raises(ez.EzError) as e:
         ez.ez_layout(2, ez.sum_spec([-4.0], [[2]]), q)
     assert e.value.code == ez.EZ_EDOMAIN

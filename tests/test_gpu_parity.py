@@ -74,7 +74,7 @@ def test_epstein_zeta_edge_cases(ez, oracle_mod):
     # ... but nu > d at y = 0 is Z(0)
     re, _ = ez.ez_epstein_zeta(L, 5.0, [0, 0], np.zeros((1, 2)))
     assert _close(re[0], oracle_mod.epstein_zeta(np.eye(2), 5.0, [0, 0], [0, 0], 1.0, 8, 8).real)
-    for bad_nu, code in ((2.5, ez.EZ_EUNSUPPORTED), (-2.0, ez.EZ_EDOMAIN), (0.0, ez.EZ_EDOMAIN)):
+    for bad_nu, code in ((-2.0, ez.EZ_EDOMAIN), (0.0, ez.EZ_EDOMAIN), (float("nan"), ez.EZ_EINVAL)):
         with pytest.raises(ez.EzError) as e:
             ez.ez_epstein_zeta(L, bad_nu, [0, 0], np.zeros((1, 2)))
         assert e.value.code == code
@@ -283,8 +283,11 @@ def test_sum_errors(ez):
     L = ez.Lattice(W.lattice("square"))
     q = ez.quadrature(W.config2(16))
     with pytest.raises(ez.EzError) as e:
-        ez.ez_lattice_sum_nbody(L, [3.5, 3.0], q)
-    assert e.value.code == ez.EZ_EUNSUPPORTED
+        ez.ez_lattice_sum_nbody(L, [float("inf"), 3.0], q)
+    assert e.value.code == ez.EZ_EINVAL
+    with pytest.raises(ez.EzError) as e:  # d = 2, nu = (1, 1): mu = 2 + 2 (1 - 2) = 0
+        ez.ez_lattice_sum_nbody(L, [1.0, 1.0], ez.quadrature(W.config2(16), u_rule=2))
+    assert e.value.code == ez.EZ_EDOMAIN
     with pytest.raises(ez.EzError) as e:
         ez.ez_lattice_sum_nbody(L, [-2.0, 3.0], q)
     assert e.value.code == ez.EZ_EDOMAIN
@@ -412,3 +415,56 @@ def test_large_n_sums(ez, oracle_mod, lat):
     ratio = vals / z3 ** np.array(ns, dtype=float)
     assert np.all(ratio > 0) and np.all(ratio <= 1.0)
     assert np.all(np.diff(ratio) < 0)
+
+
+# ------------------------------------------------------------------ real (non-integer) exponents
+REAL_NU_ZETA = [("Z", [1.5, 2.3, 4.25, -0.7]), ("hexagonal", [0.6, 2.45, 3.3, 5.15]), ("fcc", [-1.3, 2.2, 3.5, 6.5])]
+
+
+@pytest.mark.parametrize("lat,nus", REAL_NU_ZETA)
+def test_epstein_zeta_real_nu(ez, oracle_mod, lat, nus):
+    """Def. "Epstein zeta function" at real nu: Gamma(a, t) of non-half-integer orders on the
+    device (tables from the backward continued fraction and series) against the oracle."""
+    A = W.lattice(lat)
+    d = A.shape[0]
+    L = ez.Lattice(A)
+    rng = np.random.default_rng(23)
+    ys = rng.uniform(-0.5, 0.5, (30, d)) @ np.linalg.inv(A)
+    lam = abs(np.linalg.det(A)) ** (1.0 / d)
+    for nu in nus:
+        for x in (np.zeros(d), A @ rng.uniform(-0.5, 0.5, d)):
+            re, im = ez.ez_epstein_zeta(L, nu, x, ys)
+            for i in range(0, len(ys), 3):
+                z = oracle_mod.epstein_zeta(A, nu, x, ys[i], lam, 9.0 * lam, 9.0 / lam)
+                assert abs(complex(re[i], im[i]) - z) <= TOL * max(1.0, abs(z)), (lat, nu, i, re[i], z)
+
+
+REAL_NU_SUMS = [
+    W.Problem("Z:real3", W.lattice("Z"), [4.5], [[3]], W.Quad(n_u=12, n_v=1, u_rule=0, lam=1.0, r_real=8, r_recip=8)),
+    W.Problem("Z:mixed-orders", W.lattice("Z"), [2.4, 3.7], [[1, 2]], W.Quad(n_u=10, n_v=1, u_rule=0, lam=1.0,
+                                                                            r_real=8, r_recip=8)),
+    W.Problem("hex:real3", W.lattice("hexagonal"), [3.3], [[3]], W.Quad(n_u=5, n_v=10, u_rule=0, lam=1.0, r_real=6,
+                                                                       r_recip=6)),
+    W.Problem("sq:below-d", W.lattice("square"), [1.6, 3.1], [[2, 1]], W.Quad(n_u=5, n_v=9, u_rule=0, lam=1.0,
+                                                                              r_real=6, r_recip=6)),
+    W.Problem("fcc:real2", W.lattice("fcc"), [6.5], [[2]], W.Quad(n_u=3, n_v=6, u_rule=0, lam=1.0, r_real=4.5,
+                                                                  r_recip=4.5)),
+]
+
+
+@pytest.mark.parametrize("prob", REAL_NU_SUMS, ids=[p.name for p in REAL_NU_SUMS])
+def test_nbody_real_nu_parity(ez, oracle_mod, prob):
+    """n-body sums with real exponents (eps-split rule, real Hadamard exponents mu + 2k): every
+    quadrature line against the oracle, FP64 form."""
+    _compare_with_oracle(ez, oracle_mod, prob)
+
+
+def test_real_nu_two_body_identity_and_mixed_form(ez, oracle_mod):
+    # zeta^(2)(nu1, nu2) = Z_{nu1 + nu2}(0) for real exponents; the mixed form within 1e-10
+    A = W.lattice("hexagonal")
+    L = ez.Lattice(A)
+    q = W.Quad(n_u=14, n_v=24, u_rule=2, lam=0.0, r_real=0.0, r_recip=0.0)
+    ref = oracle_mod.epstein_zeta(A, 6.1, np.zeros(2), np.zeros(2), 1.0, 9.0, 9.0).real
+    for prec, tol in ((ez.EZ_FP64, 1e-13), (ez.EZ_MIXED, 1e-10)):
+        v = ez.ez_lattice_sum_nbody(L, [2.75, 3.35], ez.quadrature(q, prec=prec))
+        assert v == pytest.approx(ref, rel=tol)
