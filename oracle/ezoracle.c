@@ -524,6 +524,7 @@ int or_n_u_total(const or_problem* P) {
 }
 
 int or_u_rule(const or_problem* P, double* u, double* w) {
+  if (P->u_rule != 1 && P->u_rule != 2) return 1; /* the rule must be explicit */
   double* x = (double*)malloc(sizeof(double) * P->n_u);
   double* wx = (double*)malloc(sizeof(double) * P->n_u);
   or_gauss_legendre01(P->n_u, x, wx);
@@ -580,7 +581,7 @@ static int or_ctx_init(or_ctx* c, const or_problem* P) {
   int d = P->d;
   c->d = d;
   if (d < 1 || d > 3 || P->n_distinct < 1 || P->n_distinct > OR_MAXNU || P->n_prod < 1 ||
-      P->n_prod > OR_MAXPROD || P->n_u < 1 || (d > 1 && P->n_v < 1))
+      P->n_prod > OR_MAXPROD || P->n_u < 1 || (d > 1 && P->n_v < 1) || (P->u_rule != 1 && P->u_rule != 2))
     return 1;
   if (or_inverse(d, P->A, c->Ai)) return 1;
   or_transpose(d, c->Ai, c->AiT);

@@ -51,7 +51,8 @@ typedef struct {
   double nu[OR_MAXNU];
   int n_prod;
   int expo[OR_MAXPROD][OR_MAXNU]; /* product p = prod_j Z_{nu_j}^{expo[p][j]} */
-  int u_rule;                     /* 1: GL on [0,1/2] (n_u nodes); 2: eps-split, n_u nodes per panel */
+  int u_rule;                     /* 1: GL on [0,1/2] (n_u nodes); 2: eps-split, n_u nodes per panel
+                                     (no automatic choice: anything else is an error) */
   int n_u, n_v;
   double eps;
   int ell;

@@ -440,14 +440,14 @@ def test_epstein_zeta_real_nu(ez, oracle_mod, lat, nus):
 
 
 REAL_NU_SUMS = [
-    W.Problem("Z:real3", W.lattice("Z"), [4.5], [[3]], W.Quad(n_u=12, n_v=1, u_rule=0, lam=1.0, r_real=8, r_recip=8)),
-    W.Problem("Z:mixed-orders", W.lattice("Z"), [2.4, 3.7], [[1, 2]], W.Quad(n_u=10, n_v=1, u_rule=0, lam=1.0,
+    W.Problem("Z:real3", W.lattice("Z"), [4.5], [[3]], W.Quad(n_u=12, n_v=1, u_rule=2, lam=1.0, r_real=8, r_recip=8)),
+    W.Problem("Z:mixed-orders", W.lattice("Z"), [2.4, 3.7], [[1, 2]], W.Quad(n_u=10, n_v=1, u_rule=2, lam=1.0,
                                                                             r_real=8, r_recip=8)),
-    W.Problem("hex:real3", W.lattice("hexagonal"), [3.3], [[3]], W.Quad(n_u=5, n_v=10, u_rule=0, lam=1.0, r_real=6,
+    W.Problem("hex:real3", W.lattice("hexagonal"), [3.3], [[3]], W.Quad(n_u=5, n_v=10, u_rule=2, lam=1.0, r_real=6,
                                                                        r_recip=6)),
-    W.Problem("sq:below-d", W.lattice("square"), [1.6, 3.1], [[2, 1]], W.Quad(n_u=5, n_v=9, u_rule=0, lam=1.0,
+    W.Problem("sq:below-d", W.lattice("square"), [1.6, 3.1], [[2, 1]], W.Quad(n_u=5, n_v=9, u_rule=2, lam=1.0,
                                                                               r_real=6, r_recip=6)),
-    W.Problem("fcc:real2", W.lattice("fcc"), [6.5], [[2]], W.Quad(n_u=3, n_v=6, u_rule=0, lam=1.0, r_real=4.5,
+    W.Problem("fcc:real2", W.lattice("fcc"), [6.5], [[2]], W.Quad(n_u=3, n_v=6, u_rule=2, lam=1.0, r_real=4.5,
                                                                   r_recip=4.5)),
 ]
 
