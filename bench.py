@@ -40,8 +40,9 @@ HEADLINE_LATTICES = ("sc", "fcc", "bcc")
 # Counters of the dominant kernels from the committed ncu summaries (full command in each
 # file).  None when the kernel has changed since the capture.
 PROFILES = {
-    # far_kernel_d3<FP64, 4 exponents>, config 3 (profiles/far_kernel_d3_config3.md)
-    "far_d3_f64_dram_bytes_per_launch": None,
+    # far_kernel_d3<FP64, 4 exponents>, config 3: mean of six launches of the --metrics capture in
+    # profiles/far_kernel_d3_config3.md (15.77-16.08 MB read, 0-512 B written)
+    "far_d3_f64_dram_bytes_per_launch": 15898936,
     # far_kernel_d3<mixed, 4 exponents>: issue-slot and binary32-pipe utilisation
     "far_d3_mixed_issue_frac": None,
     "far_d3_mixed_fp32_pipe_frac": None,
