@@ -43,9 +43,11 @@ PROFILES = {
     # far_kernel_d3<FP64, 4 exponents>, config 3: mean of six launches of the --metrics capture in
     # profiles/far_kernel_d3_config3.md (15.77-16.08 MB read, 0-512 B written)
     "far_d3_f64_dram_bytes_per_launch": 15898936,
-    # far_kernel_d3<mixed, 4 exponents>: issue-slot and binary32-pipe utilisation
-    "far_d3_mixed_issue_frac": None,
-    "far_d3_mixed_fp32_pipe_frac": None,
+    # far_kernel_d3<mixed, 4 exponents>: issue-slot, binary32-pipe and binary64-pipe utilisation
+    # (--set full capture of the current build, profiles/far_kernel_d3_config3.md)
+    "far_d3_mixed_issue_frac": 0.354,
+    "far_d3_mixed_fp32_pipe_frac": 0.189,
+    "far_d3_mixed_fp64_pipe_frac": 0.545,
     # far_kernel_d2<FP64, 1 exponent>, config 2, 128 sums (profiles/far_kernel_d2_config2.md)
     "far_d2_f64_dram_bytes_per_launch": None,
 }
@@ -535,6 +537,7 @@ def run_headline(args, rank, world, local):
             "roofline": {"bound": "alu (binary32 issue)", "kernel": "far_kernel_d3<mixed, 4 exponents>",
                          "issue_frac_ncu": PROFILES["far_d3_mixed_issue_frac"],
                          "fp32_pipe_frac_ncu": PROFILES["far_d3_mixed_fp32_pipe_frac"],
+                         "fp64_pipe_frac_ncu": PROFILES["far_d3_mixed_fp64_pipe_frac"],
                          "fp32_peak_measured_tflops": p32, "fp32_peak_nominal_tflops": FP32_PEAK_NOMINAL,
                          "far_ms_per_launch": rmx["far_ms"]}}
         # config 2 (d = 2 three-body sums, 128 per step)
