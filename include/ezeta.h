@@ -158,6 +158,25 @@ int ez_epstein_zeta_static(ez_lattice lat, double nu, const double* x, const dou
 int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, const ez_quadrature* q,
                          double* value, double* err_est, void* stream);
 
+/* The far-field u integral by adaptive quadrature (Sec. 3: standard adaptive quadrature with
+ * recursive interval subdivision), global and in rounds of one batched launch each.  Round 0
+ * applies the q->n_u-point Gauss-Legendre rule to every starting panel: the graded panels
+ * [eps, 2 eps], ..., [., 1/2] with the near part on (0, eps) when the u rule is the eps-split
+ * (u_rule 2, or 0 resolving to it), else [0, 1/4] and [1/4, 1/2] (u_rule 1: the paper's plain
+ * adaptive integration of the full u interval, for nu_i >= d).  Each later round evaluates the
+ * two halves of every open panel; a panel closes with the value of its halves when
+ * |Q(panel) - Q(halves)| <= tol x |running total| x (panel length / interval length) for every
+ * product, else both halves stay open.  The v rule (q->n_v per axis), cutoffs, splitting
+ * parameter, precision and near part are those of q (part/n_parts must be 0/1).
+ *   tol        : relative tolerance in (0, 1);  max_rounds : 2..60 (open panels left after the
+ *                last round count with their values and carried estimates)
+ *   value      : host, spec->n_prod doubles;  err_est : host, spec->n_prod doubles or NULL
+ *                (sum over closed panels of |Q(panel) - Q(halves)|: the coarse panels' errors)
+ *   n_u_used   : host or NULL, u nodes evaluated over all rounds.
+ * Synchronises `stream`; every round rebuilds the sum's tables. */
+int ez_lattice_sum_adaptive(ez_lattice lat, const ez_sum_spec* spec, const ez_quadrature* q, double tol,
+                            int max_rounds, double* value, double* err_est, long long* n_u_used, void* stream);
+
 /* --- ATM cohesive energy (Prop. in Sec. 2) ------------------------------------ */
 /* E = zeta(3,3,3)/24 - 3 zeta(-1,5,5)/16 + 3 zeta(1,3,5)/8; the three zeta^(3) are
  * computed in one pass over the nodes (distinct nu = -1, 1, 3, 5).

@@ -440,7 +440,10 @@ bool near_exponents_ok(const Plan& p, int prod, std::string* why) {
   return true;
 }
 
-int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadrature& qin, Plan& p) {
+// u_nodes/u_weights (optional, both or neither): an explicit far-field u rule replacing the one
+// q describes (the adaptive driver); q.u_rule still decides whether the near part is present.
+int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadrature& qin, Plan& p,
+              const std::vector<double>* u_nodes = nullptr, const std::vector<double>* u_weights = nullptr) {
   ez_quadrature q = qin;
   p.L = L;
   p.spec = spec;
@@ -595,7 +598,12 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   // quadrature rules
   std::vector<double> x, w;
   gauss_legendre01_cached(q.n_u, x, w);
-  if (p.u_rule == 1) {
+  if (u_nodes && u_weights) {
+    if (u_nodes->empty() || u_nodes->size() != u_weights->size() || u_nodes->size() > (1u << 20))
+      return fail(EZ_EINVAL, "explicit u rule of %zu nodes", u_nodes->size());
+    p.un = *u_nodes;
+    p.uw = *u_weights;
+  } else if (p.u_rule == 1) {
     p.un.resize(q.n_u);
     p.uw.resize(q.n_u);
     for (int i = 0; i < q.n_u; ++i) {
@@ -1630,14 +1638,23 @@ extern "C" int ez_batch_destroy(ez_batch B) {
 }
 
 // one-shot path: the batch lives in the shared arena for the duration of the call
+static int run_batch(ez_batch_s& B, double* out, double* lines_out, long long* line_offsets, cudaStream_t stream);
+
 static int run_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs, const ez_quadrature* quads,
                     double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
   if (!out) return fail(EZ_EINVAL, "NULL argument");
-  int rc0 = init_constants();
-  if (rc0) return rc0;
   ez_batch_s B;
   int rc = batch_plan(B, n_req, lats, specs, quads);
-  if (!rc) rc = batch_layout(B, false);
+  if (rc) return rc;
+  return run_batch(B, out, lines_out, line_offsets, stream);
+}
+
+// runs the planned batch B (plans set, n_req = plans.size()) in the shared arena
+static int run_batch(ez_batch_s& B, double* out, double* lines_out, long long* line_offsets, cudaStream_t stream) {
+  int rc0 = init_constants();
+  if (rc0) return rc0;
+  const int n_req = B.n_req;
+  int rc = batch_layout(B, false);
   if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_arena.mu);
   rc = arena_reserve(B.dbytes, B.hbytes);
@@ -1764,6 +1781,152 @@ extern "C" int ez_lattice_sum_nbody(ez_lattice lat, const double* nu, int n, con
   }
   if (is_device_ptr(value) || (err_est && is_device_ptr(err_est)))
     EZ_CUDA(cudaStreamSynchronize((cudaStream_t)stream));  // the copies read host stack values
+  return EZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive u integration (Sec. 3: the far-field u integral by standard adaptive quadrature
+// with recursive interval subdivision).  Global and in rounds, so every round is one batched
+// launch: round 0 takes the n-point Gauss-Legendre rule on each starting panel (the graded
+// panels [eps, 2 eps], ..., [., 1/2] with the near part on (0, eps) for u_rule 2; [0, 1/4],
+// [1/4, 1/2] for u_rule 1); every later round evaluates the two halves of each open panel,
+// estimates the panel's error as |Q(panel) - Q(left) - Q(right)| (largest over the products,
+// relative to the running total) and closes the panel with Q(left) + Q(right) when that is
+// below tol times the panel's share of the interval, else keeps both halves open.
+// ---------------------------------------------------------------------------
+namespace {
+struct UPanel {
+  double a, b;
+  double q[EZ_MAX_PROD];  // n-point Gauss-Legendre value of the panel (all sectors and v nodes)
+  double e[EZ_MAX_PROD];  // error estimate carried by an open panel (half of its parent's)
+};
+
+// one batched evaluation of the n-point rule on every panel of `panels` (and of the near part
+// when `near`): each panel's value summed over sectors in a fixed order, compensated
+int eval_panels(ez_lattice lat, const ez_sum_spec& spec, const ez_quadrature& q, int n, std::vector<UPanel>& panels,
+                bool near, double* near_val, long long* nodes, cudaStream_t stream) {
+  std::vector<double> gx, gw, un, uw;
+  gauss_legendre01_cached(n, gx, gw);
+  for (const UPanel& P : panels)
+    for (int i = 0; i < n; ++i) {
+      un.push_back(P.a + (P.b - P.a) * gx[i]);
+      uw.push_back((P.b - P.a) * gw[i]);
+    }
+  ez_batch_s B;
+  B.n_req = 1;
+  B.plans.resize(1);
+  int rc = make_plan(lat, spec, q, B.plans[0], &un, &uw);
+  if (rc) return rc;
+  Plan& p = B.plans[0];
+  if (!near) p.near_active = false;
+  rc = batch_layout(B, false);
+  if (rc) return rc;
+  std::vector<double> lines((size_t)B.n_lines * EZ_MAX_PROD), out(EZ_MAX_PROD);
+  rc = run_batch(B, out.data(), lines.data(), nullptr, stream);
+  if (rc) return rc;
+  const int np = spec.n_prod, nsect = p.nsect, nui = p.n_ui;
+  for (size_t k = 0; k < panels.size(); ++k)
+    for (int pr = 0; pr < np; ++pr) {
+      double sum = 0.0, c = 0.0;
+      for (int sct = 0; sct < nsect; ++sct)
+        for (int i = 0; i < n; ++i) {
+          const double x = lines[((size_t)sct * nui + k * n + i) * EZ_MAX_PROD + pr];
+          const double t = sum + x;
+          c += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+          sum = t;
+        }
+      panels[k].q[pr] = sum + c;
+    }
+  if (near_val)
+    for (int pr = 0; pr < np; ++pr) {
+      double sum = 0.0;
+      if (near && p.near)
+        for (int sct = 0; sct < nsect; ++sct) sum += lines[((size_t)nsect * nui + sct) * EZ_MAX_PROD + pr];
+      near_val[pr] = sum;
+    }
+  if (nodes) *nodes += (long long)nui;
+  return EZ_OK;
+}
+}  // namespace
+
+extern "C" int ez_lattice_sum_adaptive(ez_lattice lat, const ez_sum_spec* spec, const ez_quadrature* q, double tol,
+                                       int max_rounds, double* value, double* err_est, long long* n_u_used,
+                                       void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!lat || !spec || !q || !value) return fail(EZ_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || !(tol < 1.0)) return fail(EZ_EINVAL, "tol = %g not in (0, 1)", tol);
+  if (max_rounds < 2 || max_rounds > 60) return fail(EZ_EINVAL, "max_rounds = %d not in 2..60", max_rounds);
+  if (q->n_parts > 1) return fail(EZ_EINVAL, "the adaptive rule integrates the whole sum (n_parts = %d)", q->n_parts);
+  Plan p0;
+  int rc = make_plan(lat, *spec, *q, p0);
+  if (rc) return rc;
+  const int np = spec->n_prod, n = q->n_u;
+  std::vector<UPanel> open;
+  double lo = 0.0;
+  if (p0.u_rule == 2) {
+    lo = p0.eps;
+    for (double a = p0.eps; a < 0.5;) {
+      const double b = std::min(2.0 * a, 0.5);
+      open.push_back(UPanel{a, b, {0, 0, 0, 0}, {0, 0, 0, 0}});
+      a = b;
+    }
+  } else {
+    open.push_back(UPanel{0.0, 0.25, {0, 0, 0, 0}, {0, 0, 0, 0}});
+    open.push_back(UPanel{0.25, 0.5, {0, 0, 0, 0}, {0, 0, 0, 0}});
+  }
+  const double len = 0.5 - lo;
+  double near_val[EZ_MAX_PROD] = {0, 0, 0, 0}, done[EZ_MAX_PROD] = {0, 0, 0, 0}, err[EZ_MAX_PROD] = {0, 0, 0, 0};
+  long long nodes = 0;
+  rc = eval_panels(lat, *spec, *q, n, open, p0.u_rule == 2, near_val, &nodes, stream);
+  if (rc) return rc;
+  for (int round = 1; round < max_rounds && !open.empty(); ++round) {
+    std::vector<UPanel> halves;
+    for (const UPanel& P : open) {
+      const double m = 0.5 * (P.a + P.b);
+      halves.push_back(UPanel{P.a, m, {0, 0, 0, 0}, {0, 0, 0, 0}});
+      halves.push_back(UPanel{m, P.b, {0, 0, 0, 0}, {0, 0, 0, 0}});
+    }
+    rc = eval_panels(lat, *spec, *q, n, halves, false, nullptr, &nodes, stream);
+    if (rc) return rc;
+    // running total for the relative criterion: near part, closed panels, halves of open ones
+    double total[EZ_MAX_PROD];
+    for (int pr = 0; pr < np; ++pr) {
+      total[pr] = near_val[pr] + done[pr];
+      for (const UPanel& h : halves) total[pr] += h.q[pr];
+    }
+    std::vector<UPanel> next;
+    for (size_t k = 0; k < open.size(); ++k) {
+      const UPanel& P = open[k];
+      UPanel L = halves[2 * k], R = halves[2 * k + 1];
+      double worst = 0.0;
+      for (int pr = 0; pr < np; ++pr) {
+        const double e = std::fabs(P.q[pr] - L.q[pr] - R.q[pr]);
+        worst = std::max(worst, e / std::max(std::fabs(total[pr]), 1e-300));
+        L.e[pr] = R.e[pr] = 0.5 * e;
+      }
+      if (worst <= tol * (P.b - P.a) / len) {
+        for (int pr = 0; pr < np; ++pr) {
+          done[pr] += L.q[pr] + R.q[pr];
+          err[pr] += L.e[pr] + R.e[pr];
+        }
+      } else {
+        next.push_back(L);
+        next.push_back(R);
+      }
+    }
+    open.swap(next);
+  }
+  // panels still open when the rounds ran out: their values and carried estimates count
+  for (const UPanel& P : open)
+    for (int pr = 0; pr < np; ++pr) {
+      done[pr] += P.q[pr];
+      err[pr] += P.e[pr];
+    }
+  for (int pr = 0; pr < np; ++pr) {
+    value[pr] = near_val[pr] + done[pr];
+    if (err_est) err_est[pr] = err[pr];
+  }
+  if (n_u_used) *n_u_used = nodes;
   return EZ_OK;
 }
 

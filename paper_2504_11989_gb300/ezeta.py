@@ -102,6 +102,9 @@ def lib():
             L.ez_epstein_zeta_static.argtypes = [vp, ctypes.c_double, dp, vp, ctypes.c_size_t, vp, vp, vp]
             L.ez_lattice_sum_nbody.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ez_quadrature), vp, vp, vp]
             L.ez_atm_energy.argtypes = [vp, ctypes.POINTER(ez_quadrature), dp, dp, vp]
+            L.ez_lattice_sum_adaptive.argtypes = [vp, ctypes.POINTER(ez_sum_spec), ctypes.POINTER(ez_quadrature),
+                                                  ctypes.c_double, ctypes.c_int, dp, dp,
+                                                  ctypes.POINTER(ctypes.c_longlong), vp]
             L.ez_lattice_sums.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ez_sum_spec),
                                           ctypes.POINTER(ez_quadrature), vp, vp,
                                           ctypes.POINTER(ctypes.c_longlong), vp]
@@ -306,6 +309,18 @@ def ez_lattice_sum_nbody(lat: Lattice, nu, q: ez_quadrature, out=None, stream=No
     op, _ = _ptr(out)
     _check(lib().ez_lattice_sum_nbody(lat.handle, nup, int(nuv.size), ctypes.byref(q), op, ep, _stream_ptr(stream)))
     return (out, e.value) if err_est else out
+
+
+def ez_lattice_sum_adaptive(lat: Lattice, spec: ez_sum_spec, q: ez_quadrature, tol: float, max_rounds: int = 30,
+                            stream=None):
+    """Adaptive u integration (see ezeta.h): (values per product, error estimates, u nodes used)."""
+    n = spec.n_prod
+    v = (ctypes.c_double * n)()
+    e = (ctypes.c_double * n)()
+    used = ctypes.c_longlong()
+    _check(lib().ez_lattice_sum_adaptive(lat.handle, ctypes.byref(spec), ctypes.byref(q), float(tol), int(max_rounds),
+                                         v, e, ctypes.byref(used), _stream_ptr(stream)))
+    return np.array(v[:]), np.array(e[:]), used.value
 
 
 def ez_atm_energy(lat: Lattice, q: ez_quadrature, stream=None):
