@@ -46,7 +46,7 @@ def test_adaptive_matches_converged_fixed_rule(ez, oracle_mod, prob, n_ref):
         assert np.all(np.abs(v - ref[: len(v)]) <= 2 * tol * scale + 1e-14 * scale), (prob.name, tol, v, ref)
         assert np.all(err <= 10 * tol * scale) and np.all(np.isfinite(err))
         used.append(n_u)
-    assert used[1] > used[0]  # the tighter tolerance refines more panels
+    assert used[1] >= used[0]  # a tighter tolerance never refines less (analytic cases close at once)
 
 
 def test_plain_adaptive_route_for_nu_above_d(ez, oracle_mod):
