@@ -141,12 +141,14 @@ def test_config2_full_size(ez, oracle_mod, lat):
 
 
 def test_config3_atm_full_size_sampled_lines(ez, oracle_mod):
+    # full size (12 sectors x 48 u x 64^2 v): 32 sampled far lines (every sector at least
+    # twice) and the near-part line of every sector against the oracle
     prob = W.atm_problem("fcc", W.config3())
     got, lines = _run(ez, prob)
     ns, nu_t = oracle_mod.n_sectors(prob), oracle_mod.n_u_total(prob)
     rng = np.random.default_rng(5)
-    picks = [(int(rng.integers(ns)), int(rng.integers(nu_t))) for _ in range(6)] + [(int(rng.integers(ns)), -1)]
-    with ThreadPoolExecutor(8) as ex:
+    picks = [(s % ns, int(rng.integers(nu_t))) for s in range(32)] + [(s, -1) for s in range(ns)]
+    with ThreadPoolExecutor(16) as ex:
         refs = list(ex.map(lambda si: oracle_mod.nbody_line(prob, si[0], si[1]), picks))
     floor = np.max(np.abs(lines), axis=0)
     for (s, iu), ref in zip(picks, refs):
