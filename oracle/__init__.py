@@ -83,6 +83,8 @@ def lib():
             L.or_hadamard.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
             L.or_epstein_zeta.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, dp, dp]
+            L.or_epstein_zeta_nd.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, dp, dp]
             L.or_epstein_zeta_reg.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, dp]
             L.or_s_hat.restype = ctypes.c_double
@@ -144,6 +146,22 @@ def epstein_zeta(A, nu, x, y, lam=1.0, r_real=8.0, r_recip=8.0) -> complex:
                                float(r_recip), ctypes.byref(re), ctypes.byref(im))
     if rc:
         raise OracleError(f"or_epstein_zeta rc={rc}")
+    return complex(re.value, im.value)
+
+
+def epstein_zeta_nd(A, nu, x, y, lam=1.0, r_real=8.0, r_recip=8.0) -> complex:
+    """Z_{Lambda,nu}(x, y) for any dimension d <= 6 (A row-major d x d)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    d = A.shape[0]
+    xv = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
+    yv = np.ascontiguousarray(np.atleast_1d(np.asarray(y, dtype=np.float64)))
+    if xv.size != d or yv.size != d:
+        raise ValueError("x and y need d components")
+    re, im = ctypes.c_double(), ctypes.c_double()
+    rc = lib().or_epstein_zeta_nd(d, _dp(A.reshape(-1)), float(nu), _dp(xv), _dp(yv), float(lam), float(r_real),
+                                  float(r_recip), ctypes.byref(re), ctypes.byref(im))
+    if rc:
+        raise OracleError(f"or_epstein_zeta_nd rc={rc}")
     return complex(re.value, im.value)
 
 

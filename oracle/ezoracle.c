@@ -383,6 +383,173 @@ int or_epstein_zeta(int d, const double* A, double nu, const double* x, const do
 }
 
 /* ------------------------------------------------------------------------- */
+/* Epstein zeta in any dimension d <= OR_MAXD (Sec. 6: the method for any d)    */
+/* ------------------------------------------------------------------------- */
+/* determinant and inverse by Gauss-Jordan elimination with partial pivoting */
+static int or_inverse_nd(int d, const double* A, double* Ai, double* det) {
+  double M[OR_MAXD * 2 * OR_MAXD];
+  int w = 2 * d;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < w; ++j) M[i * w + j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
+  double dt = 1.0;
+  for (int c = 0; c < d; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < d; ++r)
+      if (fabs(M[r * w + c]) > fabs(M[piv * w + c])) piv = r;
+    if (M[piv * w + c] == 0.0) return 1;
+    if (piv != c) {
+      for (int j = 0; j < w; ++j) {
+        double t = M[c * w + j];
+        M[c * w + j] = M[piv * w + j];
+        M[piv * w + j] = t;
+      }
+      dt = -dt;
+    }
+    double pv = M[c * w + c];
+    dt *= pv;
+    for (int j = 0; j < w; ++j) M[c * w + j] /= pv;
+    for (int r = 0; r < d; ++r) {
+      if (r == c) continue;
+      double f = M[r * w + c];
+      if (f != 0.0)
+        for (int j = 0; j < w; ++j) M[r * w + j] -= f * M[c * w + j];
+    }
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Ai[i * d + j] = M[i * w + d + j];
+  *det = dt;
+  return 0;
+}
+
+/* calls f(ctx, z, id) for every integer id with |M id - c| <= R (box from Minv) */
+static void or_enumerate_nd(int d, const double* M, const double* Minv, const double* c, double R,
+                            void (*f)(void*, const double*, const int*), void* ctx) {
+  double mc[OR_MAXD];
+  int lo[OR_MAXD], hi[OR_MAXD], id[OR_MAXD];
+  for (int i = 0; i < d; ++i) {
+    double s = 0.0, rn = 0.0;
+    for (int j = 0; j < d; ++j) {
+      s += Minv[i * d + j] * c[j];
+      rn += Minv[i * d + j] * Minv[i * d + j];
+    }
+    mc[i] = s;
+    double ext = R * sqrt(rn) + 1e-9;
+    lo[i] = (int)floor(mc[i] - ext);
+    hi[i] = (int)ceil(mc[i] + ext);
+    id[i] = lo[i];
+  }
+  while (1) {
+    double z[OR_MAXD], r2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double v = 0.0;
+      for (int j = 0; j < d; ++j) v += M[i * d + j] * (double)id[j];
+      z[i] = v;
+      r2 += (v - c[i]) * (v - c[i]);
+    }
+    if (r2 <= R * R) f(ctx, z, id);
+    int a = d - 1;
+    while (a >= 0 && id[a] == hi[a]) {
+      id[a] = lo[a];
+      --a;
+    }
+    if (a < 0) break;
+    id[a]++;
+  }
+}
+
+typedef struct {
+  int d, x_in;
+  const double *x, *y;
+  const int* mx;
+  double a, lam, nu;
+  or_acc re, im;
+  int pole;
+} or_nd_sum;
+
+static void or_nd_real_term(void* ctx, const double* z, const int* id) {
+  or_nd_sum* S = (or_nd_sum*)ctx;
+  if (S->x_in) {
+    int same = 1;
+    for (int i = 0; i < S->d; ++i) same &= id[i] == S->mx[i];
+    if (same) return;
+  }
+  double r2 = 0.0, yz = 0.0;
+  for (int i = 0; i < S->d; ++i) {
+    r2 += (z[i] - S->x[i]) * (z[i] - S->x[i]);
+    yz += S->y[i] * z[i];
+  }
+  double phi = or_phi(S->a, OR_PI * r2 / (S->lam * S->lam));
+  or_acc_add(&S->re, phi * cos(2.0 * OR_PI * yz));
+  or_acc_add(&S->im, -phi * sin(2.0 * OR_PI * yz));
+}
+
+static void or_nd_recip_term(void* ctx, const double* g, const int* id) {
+  (void)id;
+  or_nd_sum* S = (or_nd_sum*)ctx;
+  double q2 = 0.0, xq = 0.0;
+  for (int i = 0; i < S->d; ++i) {
+    double q = g[i] + S->y[i];
+    q2 += q * q;
+    xq += S->x[i] * q;
+  }
+  double phi;
+  if (q2 == 0.0) {
+    if (S->a >= 0.0) {
+      S->pole = 1;
+      return;
+    }
+    phi = -1.0 / S->a;
+  } else {
+    phi = or_phi(S->a, OR_PI * S->lam * S->lam * q2);
+  }
+  or_acc_add(&S->re, phi * cos(2.0 * OR_PI * xq));
+  or_acc_add(&S->im, -phi * sin(2.0 * OR_PI * xq));
+}
+
+/* The splitting of Z written for any d (the same formula as or_epstein_zeta, with its own
+ * linear algebra and enumeration); d <= OR_MAXD. */
+int or_epstein_zeta_nd(int d, const double* A, double nu, const double* x, const double* y, double lam,
+                       double r_real, double r_recip, double* re, double* im) {
+  if (d < 1 || d > OR_MAXD) return 1;
+  if (or_gamma_pole(0.5 * nu)) return 2;
+  double Ai[OR_MAXD * OR_MAXD], AiT[OR_MAXD * OR_MAXD], At[OR_MAXD * OR_MAXD], det;
+  if (or_inverse_nd(d, A, Ai, &det)) return 1;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      AiT[i * d + j] = Ai[j * d + i];
+      At[i * d + j] = A[j * d + i];
+    }
+  double V = fabs(det);
+  int mx[OR_MAXD], x_in = 1;
+  for (int i = 0; i < d; ++i) {
+    double v = 0.0;
+    for (int j = 0; j < d; ++j) v += Ai[i * d + j] * x[j];
+    mx[i] = (int)lround(v);
+    if (fabs(v - mx[i]) > 1e-12) x_in = 0;
+  }
+  or_nd_sum R = {d, x_in, x, y, mx, 0.5 * nu, lam, nu, {0, 0}, {0, 0}, 0};
+  or_enumerate_nd(d, A, Ai, x, r_real, or_nd_real_term, &R);
+  double my[OR_MAXD];
+  for (int i = 0; i < d; ++i) my[i] = -y[i];
+  or_nd_sum K = {d, 0, x, y, mx, 0.5 * (d - nu), lam, nu, {0, 0}, {0, 0}, 0};
+  or_enumerate_nd(d, AiT, At, my, r_recip, or_nd_recip_term, &K);
+  if (K.pole) return 2;
+  double c = pow(lam, (double)d) / V;
+  double tre = or_acc_get(&R.re) + c * or_acc_get(&K.re);
+  double tim = or_acc_get(&R.im) + c * or_acc_get(&K.im);
+  if (x_in) {
+    double xy = 0.0;
+    for (int i = 0; i < d; ++i) xy += x[i] * y[i];
+    tre -= (2.0 / nu) * cos(2.0 * OR_PI * xy);
+    tim += (2.0 / nu) * sin(2.0 * OR_PI * xy);
+  }
+  double P = or_prefactor(nu, lam);
+  *re = P * tre;
+  *im = P * tim;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Singular part (Sec. 3)                                                      */
 /* ------------------------------------------------------------------------- */
 /* coefficient sigma_nu with s_hat_nu(k) = sigma_nu |k|^{nu-d} [log(pi k^2)]^{is_log} */

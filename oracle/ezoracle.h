@@ -20,6 +20,7 @@ extern "C" {
 #define OR_MAXNU 8
 #define OR_MAXPROD 4
 #define OR_MAXELL 8
+#define OR_MAXD 6 /* largest dimension of or_epstein_zeta_nd */
 
 /* Phi_a(t) = t^{-a} Gamma(a,t) for real a, t >= 0; Phi_a(0) = -1/a (a < 0). */
 double or_phi(double a, double t);
@@ -35,6 +36,11 @@ double or_hadamard(double mu, int m, double eps, double w2);
  * Returns 0 on success, 2 on a pole (y in Lambda* with nu <= d, or Gamma(nu/2) pole). */
 int or_epstein_zeta(int d, const double* A, double nu, const double* x, const double* y,
                     double lam, double r_real, double r_recip, double* re, double* im);
+
+/* The same for any dimension 1 <= d <= OR_MAXD (A row-major d x d); its own linear algebra
+ * (Gauss-Jordan) and lattice enumeration. */
+int or_epstein_zeta_nd(int d, const double* A, double nu, const double* x, const double* y,
+                       double lam, double r_real, double r_recip, double* re, double* im);
 
 /* Regularised Z^reg_{Lambda,nu}(k) = Z(k) - s_hat_nu(k)/V at x = 0 (Sec. 3). */
 int or_epstein_zeta_reg(int d, const double* A, double nu, const double* k, double lam,

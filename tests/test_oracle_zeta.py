@@ -201,3 +201,59 @@ def test_real_nu_lattice_sums(oracle_mod):
     nus = (6.3, 7.1, 8.6)
     prob = W.Problem("z", Z1, list(nus), [[1, 1, 1]], W.Quad(n_u=8, n_v=1, u_rule=2, lam=1.0, r_real=9, r_recip=9))
     assert oracle_mod.nbody(prob)[0] == pytest.approx(brute.zeta_n_direct(Z1, nus, 600), rel=2e-14)
+
+
+# ----------------------------------------------------------------- dimensions d = 4, 5, 6
+@pytest.mark.parametrize("s", [2.5, 3.0, 4.5])
+def test_nd_z4_jacobi_four_squares(oracle_mod, s):
+    # sum' |m|^{-2s} over Z^4 = sum_n r_4(n) n^{-s} = 8 (1 - 4^{1-s}) zeta(s) zeta(s-1) (Jacobi)
+    ref = 8 * (1 - 4 ** (1 - s)) * special.zeta(s) * special.zeta(s - 1)
+    z = oracle_mod.epstein_zeta_nd(np.eye(4), 2 * s, np.zeros(4), np.zeros(4), 1.0, 7.0, 7.0)
+    assert z.real == pytest.approx(ref, rel=1e-14) and abs(z.imag) < 1e-14
+
+
+@pytest.mark.parametrize("d,nu", [(5, 8.0), (6, 9.0), (4, 7.3)])
+def test_nd_zd_theta_integral(oracle_mod, d, nu):
+    # Z_{Z^d,nu}(0) = pi^{nu/2} / Gamma(nu/2) int_0^inf t^{nu/2-1} (theta_3(e^{-pi t})^d - 1) dt
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 25
+    def th(t):  # theta_3(e^{-pi t}), by the Jacobi transformation t^{-1/2} theta_3(e^{-pi/t}) for t < 1
+        return mp.jtheta(3, 0, mp.exp(-mp.pi * t)) if t >= 1 else mp.jtheta(3, 0, mp.exp(-mp.pi / t)) / mp.sqrt(t)
+
+    f = lambda t: t ** (nu / 2 - 1) * (th(t) ** d - 1)
+    ref = float(mp.pi ** (nu / 2) / mp.gamma(nu / 2) * mp.quad(f, [0, 1, mp.inf]))
+    z = oracle_mod.epstein_zeta_nd(np.eye(d), nu, np.zeros(d), np.zeros(d), 1.0, 7.0, 7.0)
+    assert z.real == pytest.approx(ref, rel=1e-13)
+
+
+D4_SKEW = np.array([[1.0, 0.2, 0.0, -0.1], [0.0, 1.1, 0.3, 0.0], [0.1, 0.0, 0.9, 0.2], [0.0, -0.2, 0.1, 1.05]])
+
+
+@pytest.mark.parametrize("nu", [3.0, 6.5, -1.5])
+def test_nd_lambda_invariance(oracle_mod, nu):
+    d = 4
+    x = D4_SKEW @ np.array([0.13, -0.27, 0.4, 0.05])
+    y = np.linalg.inv(D4_SKEW).T @ np.array([0.21, -0.33, 0.12, 0.44])
+    za = oracle_mod.epstein_zeta_nd(D4_SKEW, nu, x, y, 0.85, 7 * 0.85, 7 / 0.85)
+    zb = oracle_mod.epstein_zeta_nd(D4_SKEW, nu, x, y, 1.25, 7 * 1.25, 7 / 1.25)
+    assert abs(za - zb) <= 3e-14 * max(1.0, abs(za))
+
+
+def test_nd_brute_force_and_lower_dimensions(oracle_mod):
+    # large nu: the defining sum sum_z e^{-2 pi i y.z} |z - x|^{-nu} directly (d = 4)
+    nu, d, L = 18.0, 4, 5
+    x = D4_SKEW @ np.array([0.3, 0.1, -0.2, 0.15])
+    y = np.array([0.1, 0.25, -0.3, 0.05])
+    g = np.array(np.meshgrid(*[np.arange(-L, L + 1)] * d, indexing="ij")).reshape(d, -1).T
+    z = g @ D4_SKEW.T
+    r = np.linalg.norm(z - x, axis=1)
+    ref = np.sum(np.exp(-2j * np.pi * (z @ y)) * r ** -nu)
+    got = oracle_mod.epstein_zeta_nd(D4_SKEW, nu, x, y, 1.0, 7.0, 7.0)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+    # d <= 3: the same values as the three-dimensional oracle
+    for lat in ("Z", "hexagonal", "fcc"):
+        A = W.lattice(lat)
+        dd = A.shape[0]
+        xv, yv = A @ (0.2 * np.ones(dd)), 0.17 * np.ones(dd)
+        assert oracle_mod.epstein_zeta_nd(A, 3.7, xv, yv, 1.0, 8, 8) == pytest.approx(
+            oracle_mod.epstein_zeta(A, 3.7, xv, yv, 1.0, 8, 8), rel=1e-15, abs=1e-15)
