@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libezeta.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["ez_setup.cu", "ez_nbody.cu", "ez_epstein.cu", "ez_api.cu", "ez_diag.cu"]
+SOURCES = ["ez_setup.cu", "ez_nbody.cu", "ez_epstein.cu", "ez_epstein_nd.cu", "ez_api.cu", "ez_diag.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

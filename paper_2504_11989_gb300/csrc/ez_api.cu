@@ -61,20 +61,18 @@ extern "C" long long ez_launch_count(int reset) {
 // ---------------------------------------------------------------------------
 // lattices
 // ---------------------------------------------------------------------------
+// Matrices are stored row by row with row length d (z_i = sum_j A[i d + j] m_j); for
+// d <= 3 only the first d * d entries are used, which is the layout the lattice-sum
+// planner and the d <= 3 kernels read.
 struct ez_lattice_s {
   int d;
-  double A[9], Ai[9], AiT[9], At[9], V;
+  double A[kMaxDnd * kMaxDnd], Ai[kMaxDnd * kMaxDnd], AiT[kMaxDnd * kMaxDnd], At[kMaxDnd * kMaxDnd], V;
 };
 
-static double det3(int d, const double* A) {
-  if (d == 1) return A[0];
-  if (d == 2) return A[0] * A[3] - A[1] * A[2];
-  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
-}
-
-// inverse by Gauss-Jordan elimination with partial pivoting
-static bool invert(int d, const double* A, double* X) {
-  double M[3][6];
+// inverse and |det| by Gauss-Jordan elimination with partial pivoting
+static bool invert(int d, const double* A, double* X, double* absdet) {
+  double M[kMaxDnd][2 * kMaxDnd];
+  double det = 1.0;
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < 2 * d; ++j) M[i][j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
   for (int c = 0; c < d; ++c) {
@@ -84,6 +82,7 @@ static bool invert(int d, const double* A, double* X) {
     if (M[p][c] == 0.0 || !std::isfinite(M[p][c])) return false;
     if (p != c)
       for (int j = 0; j < 2 * d; ++j) std::swap(M[p][j], M[c][j]);
+    det *= M[c][c];
     double inv = 1.0 / M[c][c];
     for (int j = 0; j < 2 * d; ++j) M[c][j] *= inv;
     for (int r = 0; r < d; ++r)
@@ -94,12 +93,13 @@ static bool invert(int d, const double* A, double* X) {
   }
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) X[i * d + j] = M[i][j + d];
-  return true;
+  *absdet = std::fabs(det);
+  return std::isfinite(*absdet) && *absdet > 0.0;
 }
 
 extern "C" int ez_lattice_create(int d, const double* A, double scale, ez_lattice* out) {
   if (!out || !A) return fail(EZ_EINVAL, "ez_lattice_create: NULL argument");
-  if (d < 1 || d > 3) return fail(EZ_EINVAL, "ez_lattice_create: d = %d not in 1..3", d);
+  if (d < 1 || d > kMaxDnd) return fail(EZ_EINVAL, "ez_lattice_create: d = %d not in 1..%d", d, kMaxDnd);
   if (!(scale > 0.0) || !std::isfinite(scale)) return fail(EZ_EINVAL, "ez_lattice_create: scale = %g", scale);
   for (int i = 0; i < d * d; ++i)
     if (!std::isfinite(A[i])) return fail(EZ_EINVAL, "ez_lattice_create: non-finite A");
@@ -107,8 +107,7 @@ extern "C" int ez_lattice_create(int d, const double* A, double scale, ez_lattic
   L->d = d;
   std::memset(L->A, 0, sizeof L->A);
   for (int i = 0; i < d * d; ++i) L->A[i] = scale * A[i];
-  L->V = std::fabs(det3(d, L->A));
-  if (!(L->V > 0.0) || !invert(d, L->A, L->Ai)) {
+  if (!invert(d, L->A, L->Ai, &L->V)) {
     delete L;
     return fail(EZ_EINVAL, "ez_lattice_create: singular lattice matrix");
   }
@@ -449,6 +448,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   p.spec = spec;
   p.d = L->d;
   const int d = p.d;
+  if (d > kMaxD) return fail(EZ_EUNSUPPORTED, "lattice sums in d = %d > %d are not built (ez_epstein_zeta is)", d, kMaxD);
   if (spec.n_distinct < 1 || spec.n_distinct > EZ_MAX_NU) return fail(EZ_EINVAL, "n_distinct = %d", spec.n_distinct);
   if (spec.n_prod < 1 || spec.n_prod > EZ_MAX_PROD) return fail(EZ_EINVAL, "n_prod = %d", spec.n_prod);
   int maxfac = 0;
@@ -1958,6 +1958,190 @@ extern "C" int ez_atm_energy(ez_lattice lat, const ez_quadrature* q, double* ene
 // ---------------------------------------------------------------------------
 // Epstein zeta at many y
 // ---------------------------------------------------------------------------
+// d > 3: the real-space ball enumerated once as rows of lattice points (nd_rows_kernel,
+// nd_scan_kernel, nd_fill_kernel), then one thread per y (epstein_nd_kernel, which enumerates
+// its own reciprocal ball).  Splitting parameter lam = V^{1/d}, cutoffs pi |z - x|^2 / lam^2 <= T
+// and pi lam^2 |g + y|^2 <= T.  The row counts are taken in a first pass (one synchronisation)
+// so that the cell list is allocated at its exact size.
+static int epstein_nd(const ez_lattice_s* L, double nu, const double* x, const double* y, size_t m, double* re,
+                      double* im, cudaStream_t stream) {
+  const int d = L->d;
+  const double lam = std::pow(L->V, 1.0 / d);
+  const double s = std::sqrt(kPi) * lam;
+  const double r_real = lam * std::sqrt(kTcut / kPi);
+  NdBallJob JR;
+  std::memset(&JR, 0, sizeof JR);
+  JR.d = d;
+  // real space: the ball |z - x| <= r_real inside the box round(A^{-1} x) + [-M, M]^d
+  int mx[kMaxDnd], Mr[kMaxDnd];
+  double xt[kMaxDnd];
+  bool x_in = true, x_zero = true;
+  for (int i = 0; i < d; ++i) {
+    double v = 0.0, rn = 0.0;
+    for (int j = 0; j < d; ++j) {
+      v += L->Ai[i * d + j] * x[j];
+      rn += L->Ai[i * d + j] * L->Ai[i * d + j];
+    }
+    xt[i] = v;
+    mx[i] = (int)std::lrint(v);
+    if (std::fabs(v - mx[i]) > 1e-12) x_in = false;
+    if (x[i] != 0.0) x_zero = false;
+    Mr[i] = (int)std::ceil(r_real * std::sqrt(rn) + 0.5 + 1e-9);
+    if (2 * Mr[i] + 1 > kNdMaxExt)
+      return fail(EZ_EINVAL, "real-space box half-width %d too large (lattice too skewed)", Mr[i]);
+  }
+  for (int i = 0; i < d * d; ++i) JR.M[i] = L->A[i];
+  for (int i = 0; i < d; ++i) {
+    JR.c[i] = x[i];
+    JR.lo[i] = mx[i] - Mr[i];
+    JR.ext[i] = 2 * Mr[i] + 1;
+    JR.cid[i] = mx[i];
+  }
+  JR.R2 = r_real * r_real;
+  JR.a = 0.5 * nu;
+  JR.pi_over_lam2 = kPi / (lam * lam);
+  JR.skip_center = x_in ? 1 : 0;
+  JR.n_prefix = 1;
+  for (int l = 0; l + 1 < d; ++l) JR.n_prefix *= JR.ext[l];
+  // reciprocal space: Cholesky factor (upper) of the Gram matrix of B = s A^{-T}
+  double Rk[kMaxDnd * kMaxDnd] = {0};
+  {
+    double G[kMaxDnd * kMaxDnd];
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double g = 0.0;
+        for (int k = 0; k < d; ++k) g += (s * L->AiT[k * d + i]) * (s * L->AiT[k * d + j]);
+        G[i * d + j] = g;
+      }
+    for (int i = 0; i < d; ++i) {
+      double dg = G[i * d + i];
+      for (int k = 0; k < i; ++k) dg -= Rk[k * d + i] * Rk[k * d + i];
+      if (!(dg > 0.0)) return fail(EZ_EINVAL, "dual Gram matrix is not positive definite");
+      Rk[i * d + i] = std::sqrt(dg);
+      for (int j = i + 1; j < d; ++j) {
+        double v = G[i * d + j];
+        for (int k = 0; k < i; ++k) v -= Rk[k * d + i] * Rk[k * d + j];
+        Rk[i * d + j] = v / Rk[i * d + i];
+      }
+    }
+  }
+  PhiInfo phi;
+  fill_phi_host(phi, 0.5 * (d - nu), kTcut);
+  phi.c_lam = 1.0;
+  int phase_len = 0;
+  for (int i = 0; i < d; ++i) phase_len += 2 * Mr[i] + 1;
+  unsigned threads = 128;
+  while (threads > 32 && (size_t)phase_len * 16 * threads > (size_t)220 * 1024) threads /= 2;
+  const size_t smem = (size_t)phase_len * 16 * threads;
+
+  const bool y_dev = is_device_ptr(y), re_dev = is_device_ptr(re), im_dev = im && is_device_ptr(im);
+  Layout dl, hl;
+  const size_t o_jr = dl.take(sizeof(NdBallJob)), h_jr = hl.take(sizeof(NdBallJob));
+  const size_t h_cnt = hl.take(4 * sizeof(int));
+  const size_t o_k0r = dl.take(sizeof(int) * JR.n_prefix), o_nr = dl.take(sizeof(int) * JR.n_prefix);
+  const size_t o_rowr = dl.take(sizeof(int4) * JR.n_prefix);
+  const size_t o_cnt = dl.take(4 * sizeof(int));
+  const size_t phase1 = dl.off;
+  std::lock_guard<std::mutex> lock(g_arena.mu);
+  // uploads the job and enumerates the rows (counts_only: the counts alone)
+  auto run_rows = [&](bool counts_only) -> int {
+    char* D = g_arena.d;
+    char* Hs = g_arena.h;
+    JR.row_k0 = (int*)(D + o_k0r);
+    JR.row_n = (int*)(D + o_nr);
+    JR.rows = (int4*)(D + o_rowr);
+    JR.counts = (int*)(D + o_cnt);
+    if (counts_only) JR.cell_cap = 0;
+    std::memcpy(Hs + h_jr, &JR, sizeof JR);
+    EZ_CUDA(cudaMemcpyAsync(D + o_jr, Hs + h_jr, sizeof JR, cudaMemcpyHostToDevice, stream));
+    const NdBallJob* jd = (const NdBallJob*)(D + o_jr);
+    nd_rows_kernel<<<(unsigned)((JR.n_prefix + 255) / 256), 256, 0, stream>>>(jd);
+    EZ_LAUNCHED();
+    nd_scan_kernel<<<1, 1024, 0, stream>>>(jd);
+    EZ_LAUNCHED();
+    if (!counts_only) {
+      nd_fill_kernel<<<4 * 152, 256, 0, stream>>>(jd);
+      EZ_LAUNCHED();
+    }
+    return EZ_OK;
+  };
+  int rc = arena_reserve(phase1, hl.off);
+  if (rc) return rc;
+  rc = run_rows(true);
+  if (rc) return rc;
+  EZ_CUDA(cudaMemcpyAsync(g_arena.h + h_cnt, g_arena.d + o_cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EZ_CUDA(cudaStreamSynchronize(stream));
+  int cnt[2];
+  std::memcpy(cnt, g_arena.h + h_cnt, sizeof cnt);
+  const long long cells_r = std::max(cnt[1], 1);
+  const size_t o_g = dl.take(sizeof(double) * cells_r);
+  const size_t o_pj = dl.take(sizeof(PhiJob)), h_pj = hl.take(sizeof(PhiJob));
+  const size_t o_tab = dl.take(sizeof(double) * kRec * phi.n_int);
+  const size_t o_st = dl.take(sizeof(int));
+  const size_t o_y = y_dev ? 0 : dl.take(sizeof(double) * m * d);
+  const size_t o_re = re_dev ? 0 : dl.take(sizeof(double) * m);
+  const size_t o_im = (!im || im_dev) ? 0 : dl.take(sizeof(double) * m);
+  rc = arena_reserve(dl.off, hl.off);
+  if (rc) return rc;
+  char* D = g_arena.d;
+  char* Hs = g_arena.h;
+  JR.cell_cap = cells_r;
+  JR.out = (double*)(D + o_g);
+  rc = run_rows(false);
+  if (rc) return rc;
+  PhiJob& PJ = *(PhiJob*)(Hs + h_pj);
+  std::memset(&PJ, 0, sizeof PJ);
+  PJ.a = phi.a;
+  PJ.c_lam = 1.0;
+  PJ.t_geo_end = phi.t_geo_end;
+  PJ.n_int = phi.n_int;
+  PJ.out = (double*)(D + o_tab);
+  EZ_CUDA(cudaMemcpyAsync(D + o_pj, &PJ, sizeof PJ, cudaMemcpyHostToDevice, stream));
+  EZ_CUDA(cudaMemsetAsync(D + o_st, 0, sizeof(int), stream));
+  if (!y_dev) EZ_CUDA(cudaMemcpyAsync(D + o_y, y, sizeof(double) * m * d, cudaMemcpyHostToDevice, stream));
+  phitab_kernel<<<dim3((phi.n_int + kPhiIv - 1) / kPhiIv, 1), kPhiIv * kNC, 0, stream>>>((const PhiJob*)(D + o_pj));
+  EZ_LAUNCHED();
+  NdEpsteinArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.d = d;
+  A.m = (int)m;
+  A.pref = std::pow(kPi, 0.5 * nu) / (std::tgamma(0.5 * nu) * std::pow(lam, nu));
+  A.vol_fac = std::pow(lam, d) / L->V;
+  A.R2_recip = kTcut;
+  A.two_over_nu = 2.0 / nu;
+  for (int i = 0; i < d * d; ++i) {
+    A.At[i] = L->At[i];
+    A.Rk[i] = Rk[i];
+  }
+  for (int i = 0; i < d; ++i) {
+    A.xt[i] = xt[i];
+    A.M[i] = Mr[i];
+    A.mx[i] = mx[i];
+  }
+  A.x_zero = x_zero ? 1 : 0;
+  A.x_in_lattice = x_in ? 1 : 0;
+  A.phase_len = phase_len;
+  A.rows = JR.rows;
+  A.rcounts = JR.counts;
+  A.g = JR.out;
+  A.phi = phi;
+  A.phi.tab = (const double*)(D + o_tab);
+  A.y = y_dev ? y : (const double*)(D + o_y);
+  A.re = re_dev ? re : (double*)(D + o_re);
+  A.im = im ? (im_dev ? im : (double*)(D + o_im)) : nullptr;
+  A.status = (int*)(D + o_st);
+  EZ_CUDA(launch_epstein_nd(A, threads, smem, stream));
+  ++t_launches;
+  if (!re_dev) EZ_CUDA(cudaMemcpyAsync(re, D + o_re, sizeof(double) * m, cudaMemcpyDeviceToHost, stream));
+  if (im && !im_dev) EZ_CUDA(cudaMemcpyAsync(im, D + o_im, sizeof(double) * m, cudaMemcpyDeviceToHost, stream));
+  EZ_CUDA(cudaMemcpyAsync(Hs + h_cnt, D + o_st, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EZ_CUDA(cudaStreamSynchronize(stream));
+  int status;
+  std::memcpy(&status, Hs + h_cnt, sizeof status);
+  if (status) return fail(EZ_EDOMAIN, "some y lie in the reciprocal lattice with nu <= d (pole)");
+  return EZ_OK;
+}
+
 extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const double* y, size_t m, double* re,
                                double* im, int prec, void* stream_) {
   cudaStream_t stream = (cudaStream_t)stream_;
@@ -1970,6 +2154,7 @@ extern "C" int ez_epstein_zeta(ez_lattice L, double nu, const double* x, const d
   if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
   int rc = init_constants();
   if (rc) return rc;
+  if (L->d > kMaxD) return epstein_nd(L, nu, x, y, m, re, im, stream);
   const int d = L->d;
   ez_sum_spec s;
   std::memset(&s, 0, sizeof s);
@@ -2180,6 +2365,7 @@ extern "C" int ez_epstein_zeta_static(ez_lattice L, double nu, const double* x, 
   if (!is_device_ptr(y) || !is_device_ptr(re) || (im && !is_device_ptr(im)))
     return fail(EZ_EINVAL, "ez_epstein_zeta_static takes device buffers for y, re and im "
                            "(host buffers would need staging memory)");
+  if (L->d > kMaxD) return fail(EZ_EUNSUPPORTED, "ez_epstein_zeta_static: d = %d > %d (ez_epstein_zeta takes it)", L->d, kMaxD);
   if (!std::isfinite(nu)) return fail(EZ_EINVAL, "exponent %g is not finite", nu);
   if (nu <= 0.0 && is_integer(0.5 * nu)) return fail(EZ_EDOMAIN, "exponent %g is a pole of Gamma(nu/2)", nu);
   int rc = init_constants();
@@ -2734,8 +2920,7 @@ extern "C" int ez_server_submit(ez_server S, const ez_request* req, unsigned lon
   std::memset(&L, 0, sizeof L);
   L.d = d;
   std::memcpy(L.A, req->A, sizeof(double) * d * d);
-  L.V = std::fabs(det3(d, L.A));
-  if (!(L.V > 0.0) || !invert(d, L.A, L.Ai)) return fail(EZ_EINVAL, "singular lattice matrix");
+  if (!invert(d, L.A, L.Ai, &L.V)) return fail(EZ_EINVAL, "singular lattice matrix");
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
       L.AiT[i * d + j] = L.Ai[j * d + i];

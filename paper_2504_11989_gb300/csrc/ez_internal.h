@@ -75,7 +75,8 @@ static_assert(sizeof(PhiInfo) % sizeof(double) == 0, "PhiInfo is copied to share
 // ---------------------------------------------------------------------------
 // One lattice sum as seen by the kernels (device resident).
 // ---------------------------------------------------------------------------
-constexpr int kMaxD = 3;
+constexpr int kMaxD = 3;    // lattice sums (Duffy nodes, near part, serving)
+constexpr int kMaxDnd = 6;  // the Epstein zeta function alone (any dimension up to this)
 constexpr int kMaxFactor = 64;
 constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
 constexpr int kMaxEll = 8;       // largest Taylor order parameter ell of the near part

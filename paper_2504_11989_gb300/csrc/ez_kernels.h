@@ -105,6 +105,54 @@ __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, co
 __global__ void epstein_kernel(EpsteinArgs args);
 __global__ void phase_kernel(const PhaseJob* jobs);
 
+// ---- the Epstein zeta function in any dimension d <= kMaxDnd ----
+// Lattice points id in the box lo + [0, ext) with |M id - c|^2 <= R2, stored as rows along the
+// last axis: one record per non-empty row, in lexicographic order of the row's prefix
+// (id_0 .. id_{d-2}).  Record (int4): x = offset of the row's first cell, y = k0 | n << 16 (the
+// row holds id_{d-1} = lo_{d-1} + k0 + [0, n)), z = prefix, 6 bits per axis (axis l at bit 6 l,
+// index id_l - lo_l), w = the first prefix axis at which the row differs from the previous one.
+constexpr int kNdMaxExt = 63;  // box extent per axis (6-bit prefix fields)
+struct NdBallJob {
+  int d;
+  double M[kMaxDnd * kMaxDnd];  // z_i = sum_j M[i d + j] id_j
+  double c[kMaxDnd];
+  double R2;
+  int lo[kMaxDnd], ext[kMaxDnd];
+  long long n_prefix;  // prod_{l < d - 1} ext_l (1 for d = 1)
+  int* row_k0;         // [n_prefix] scratch
+  int* row_n;          // [n_prefix] scratch
+  int4* rows;          // [n_prefix]: the non-empty rows
+  int* counts;         // [2]: rows, cells
+  long long cell_cap;  // cells the output holds (0: count only, no output)
+  double a, pi_over_lam2;  // g = Phi_a(pi_over_lam2 |z - c|^2)
+  int skip_center;         // the cell id == cid is left out (x in the lattice)
+  int cid[kMaxDnd];
+  double* out;             // [cell] g
+};
+
+struct NdEpsteinArgs {
+  int d, m;
+  double pref, vol_fac, R2_recip, two_over_nu;
+  double At[kMaxDnd * kMaxDnd];  // A^T: reduced coordinates yt = A^T y
+  double Rk[kMaxDnd * kMaxDnd];  // upper triangular, R^T R = B^T B with B = sqrt(pi) lam A^{-T}
+  double xt[kMaxDnd];            // A^{-1} x
+  int x_zero, x_in_lattice;
+  int M[kMaxDnd], mx[kMaxDnd];   // real-space box mx - M + [0, 2 M]
+  int phase_len;                 // sum_l (2 M_l + 1): per-thread phase entries in shared memory
+  const int4* rows;
+  const int* rcounts;  // [0]: real-space rows
+  const double* g;
+  PhiInfo phi;         // order (d - nu) / 2, argument t = pi lam^2 |g* + y|^2
+  const double* y;
+  double* re;
+  double* im;
+  int* status;
+};
+__global__ void nd_rows_kernel(const NdBallJob* job);
+__global__ void nd_scan_kernel(const NdBallJob* job);
+__global__ void nd_fill_kernel(const NdBallJob* job);
+cudaError_t launch_epstein_nd(const NdEpsteinArgs& args, unsigned threads, size_t smem, cudaStream_t st);
+
 size_t far_smem_bytes(int d, int n_distinct, const int* M, int n_v, int vchunk);
 // Chebyshev -> monomial matrix (kNC x kNC), cosine table of the transform (kNC x kNC),
 // Chebyshev points (kNC)

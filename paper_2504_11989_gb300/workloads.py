@@ -37,8 +37,37 @@ PRESETS = {
     "bcc": np.array([[1.0, 1.0, 0.0], [_S2, 0.0, _S2], [0.0, _S2, _S2]]) / _S3,
 }
 
-DIM_OF = {"Z": 1, "square": 2, "hexagonal": 2, "sc": 3, "fcc": 3, "bcc": 3}
-LATTICES_BY_DIM = {1: ["Z"], 2: ["square", "hexagonal"], 3: ["sc", "fcc", "bcc"]}
+
+
+def _from_gram(G) -> np.ndarray:
+    """A basis with Gram matrix G (A^T A = G): the transposed Cholesky factor."""
+    return np.linalg.cholesky(np.asarray(G, dtype=np.float64)).T
+
+
+def _cartan(n: int, edges) -> np.ndarray:
+    """Cartan matrix of a simply laced Dynkin diagram: 2 on the diagonal, -1 per edge."""
+    G = 2.0 * np.eye(n)
+    for i, j in edges:
+        G[i, j] = G[j, i] = -1.0
+    return G
+
+
+# higher dimensions (the Epstein zeta function alone): cubic lattices, the root lattices D4
+# (densest packing in four dimensions), D5 and E6, given by the Gram matrices of their
+# simple roots
+PRESETS.update({
+    "Z4": np.eye(4),
+    "D4": _from_gram(_cartan(4, [(0, 1), (1, 2), (1, 3)])),
+    "Z5": np.eye(5),
+    "D5": _from_gram(_cartan(5, [(0, 1), (1, 2), (2, 3), (2, 4)])),
+    "Z6": np.eye(6),
+    "E6": _from_gram(_cartan(6, [(0, 2), (2, 3), (3, 4), (4, 5), (1, 3)])),
+})
+
+DIM_OF = {"Z": 1, "square": 2, "hexagonal": 2, "sc": 3, "fcc": 3, "bcc": 3, "Z4": 4, "D4": 4, "Z5": 5, "D5": 5,
+          "Z6": 6, "E6": 6}
+LATTICES_BY_DIM = {1: ["Z"], 2: ["square", "hexagonal"], 3: ["sc", "fcc", "bcc"], 4: ["Z4", "D4"], 5: ["Z5", "D5"],
+                   6: ["Z6", "E6"]}
 
 
 def lattice(name: str, unit_density: bool = True, scale: float = 1.0) -> np.ndarray:

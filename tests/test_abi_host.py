@@ -42,11 +42,37 @@ def test_lattice_validation(ez):
         ez.Lattice([[1.0, 2.0], [0.5, 1.0]])
     assert e.value.code == ez.EZ_EINVAL
     h = ctypes.c_void_p()
-    A = (ctypes.c_double * 16)(*([1.0] * 16))
+    A = (ctypes.c_double * 49)(*([1.0] * 49))
+    assert ez.lib().ez_lattice_create(7, A, 1.0, ctypes.byref(h)) == ez.EZ_EINVAL
+    assert b"d = 7" in ez.lib().ez_last_error()
+    # singular in 4 dimensions (all-ones matrix)
     assert ez.lib().ez_lattice_create(4, A, 1.0, ctypes.byref(h)) == ez.EZ_EINVAL
-    assert b"d = 4" in ez.lib().ez_last_error()
     lat = ez.Lattice(W.lattice("fcc"))
     assert lat.d == 3
+
+
+def test_higher_dimensional_lattices(ez):
+    """d = 4..6 lattices exist for the Epstein zeta function; the lattice sums (Duffy nodes,
+    near part) are built for d <= 3 and refuse them with EZ_EUNSUPPORTED, before any device work."""
+    import numpy as np
+
+    for name in ("Z4", "D4", "Z5", "D5", "Z6", "E6"):
+        A = W.lattice(name)
+        assert abs(abs(np.linalg.det(A)) - 1.0) < 1e-12
+        lat = ez.Lattice(A)
+        assert lat.d == A.shape[0]
+    # the root lattices: Gram matrices with 2 on the diagonal before rescaling
+    for name in ("D4", "D5", "E6"):
+        A = W.lattice(name, unit_density=False)
+        G = A.T @ A
+        assert np.allclose(np.diag(G), 2.0) and set(np.round(G[~np.eye(len(G), dtype=bool)], 12)) <= {0.0, -1.0}
+    # det of the Cartan matrices: D_n 4, E6 3
+    assert abs(np.linalg.det(W.lattice("D4", unit_density=False)) ** 2 - 4.0) < 1e-10
+    assert abs(np.linalg.det(W.lattice("E6", unit_density=False)) ** 2 - 3.0) < 1e-10
+    spec = ez.sum_spec([5.0], [[2]])
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_plan_describe(ez.Lattice(W.lattice("D4")), spec, ez.quadrature(W.Quad(n_u=4, n_v=4)))
+    assert e.value.code == ez.EZ_EUNSUPPORTED
 
 
 @pytest.mark.parametrize(
