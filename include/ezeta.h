@@ -11,7 +11,9 @@
  * General rules for every entry point:
  *  - Lattice matrices are row-major d x d (A[i*d+j] = component i of basis
  *    vector j); the lattice is A Z^d and the reciprocal lattice A^{-T} Z^d
- *    (Def. "Lattices").  1 <= d <= 3.
+ *    (Def. "Lattices").  1 <= d <= 3 for the lattice sums (Duffy nodes, near part,
+ *    serving); the Epstein zeta function alone takes 1 <= d <= 6 (Sec. 6: the method
+ *    holds in any dimension).
  *  - Pointers marked "host or device" may point to host memory or to device
  *    memory of the current CUDA device; the library detects which.  The caller
  *    owns every input and output buffer.  Library handles own their own device
@@ -98,8 +100,11 @@ typedef struct {
 /* --- lattices (Def. "Lattices") ------------------------------------------------ */
 /* Creates the lattice (scale A) Z^d from A (host, d*d doubles, row-major as above) and the
  * lattice constant scale > 0 (1 for A itself; the presets of the paper are given at unit
- * density and scaled by it).  EZ_EINVAL if d is not in 1..3, scale is not a positive finite
- * number or A is singular.  The handle keeps the scaled matrix, its inverse and volume. */
+ * density and scaled by it).  EZ_EINVAL if d is not in 1..6, scale is not a positive finite
+ * number or A is singular.  The handle keeps the scaled matrix, its inverse and volume.
+ * Every lattice-sum entry point (ez_lattice_sums, ez_batch_create, ez_lattice_sum_nbody,
+ * ez_lattice_sum_adaptive, ez_atm_energy, ez_plan_describe) and ez_epstein_zeta_static
+ * return EZ_EUNSUPPORTED for a lattice with d > 3. */
 int ez_lattice_create(int d, const double* A, double scale, ez_lattice* out);
 int ez_lattice_destroy(ez_lattice lat);
 
@@ -113,7 +118,12 @@ int ez_lattice_destroy(ez_lattice lat);
  *   y  : host or device, m*d doubles (point i at y[i*d .. i*d+d-1]).
  *   re, im : host or device, m doubles each (im may be NULL).
  * y_i in Lambda* with nu <= d is a pole: re[i] = im[i] = NaN and the call returns
- * EZ_EDOMAIN after finishing the other points.  m = 0 is a no-op. */
+ * EZ_EDOMAIN after finishing the other points.  m = 0 is a no-op.
+ * d = 4..6: cutoffs pi |z - x|^2 / lambda^2 <= 45 and pi lambda^2 |g + y|^2 <= 45 (the
+ * neglected terms are below e^{-45} ~ 3e-20 of the nearest ones); the real-space ball is
+ * enumerated once per call and the reciprocal ball per point, and the call synchronises
+ * `stream` once more to size its tables.  EZ_EINVAL if the bounding box of a ball needs
+ * more than 63 lattice points along an axis (a very skewed basis; reduce it first). */
 int ez_epstein_zeta(ez_lattice lat, double nu, const double* x, const double* y, size_t m,
                     double* re, double* im, int prec, void* stream);
 

@@ -101,3 +101,20 @@ def test_nd_quasi_periodicity_and_poles(ez):
     # nu > d at y = 0 is finite: the g* = 0 term is the limit -1/a of Phi_a(t) - Gamma(a) t^{-a}
     re, _ = ez.ez_epstein_zeta(L, 7.0, np.zeros(d), np.zeros((1, d)))
     assert np.isfinite(re[0]) and re[0] > 0.0
+
+
+def test_lattice_sums_refuse_d_above_3(ez):
+    # the Duffy nodes, near part and static scratch are built for d <= 3: EZ_EUNSUPPORTED
+    import torch
+
+    L = ez.Lattice(W.lattice("D4"))
+    q = ez.quadrature(W.Quad(n_u=4, n_v=4))
+    for call in (lambda: ez.ez_lattice_sum_nbody(L, [5.0, 5.0], q), lambda: ez.ez_atm_energy(L, q)):
+        with pytest.raises(ez.EzError) as e:
+            call()
+        assert e.value.code == ez.EZ_EUNSUPPORTED
+    y = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    re = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(ez.EzError) as e:
+        ez.ez_epstein_zeta_static(L, 5.0, np.zeros(4), y, re)
+    assert e.value.code == ez.EZ_EUNSUPPORTED
