@@ -225,6 +225,8 @@ struct Plan {
   double rser[EZ_MAX_NU][16];
   bool near;
   std::vector<int> alpha, alpha_off;
+  std::vector<double> hadw;   // near part, integer exponents: Hadamard weight coefficients
+  int hadw_lo = 0, hadw_m1 = 0;
   int nch;            // far segments per line (d = 3: v2 chunks)
   int vchunk;         // d = 3: v2 rows per far-field block
   int m_hp[3];        // mixed form: |m_i| >= m_hp[i] summed in plain binary32
@@ -437,6 +439,82 @@ bool near_exponents_ok(const Plan& p, int prod, std::string* why) {
     if (j == s.n_distinct) break;
   }
   return true;
+}
+
+double sigma_of(int d, double nu, int* islog);
+
+// x_i -> -x_i maps the lattice onto itself for every axis i (A^{-1} R_i A is an integer
+// matrix).  Then Z^reg is even in every component of k and each Taylor coefficient with an
+// odd alpha_i vanishes.
+static bool reflection_symmetric(const ez_lattice_s* L) {
+  const int d = L->d;
+  for (int i = 0; i < d; ++i)
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += L->Ai[r * d + k] * (k == i ? -L->A[k * d + c] : L->A[k * d + c]);
+        if (std::fabs(s - std::nearbyint(s)) > 1e-9) return false;
+      }
+  return true;
+}
+
+// Near part with integer exponents: the Hadamard weight of u^{mu'-1} log^m(pi u^2 |w|^2) on
+// (0, eps) is eps^{mu'} J_m(mu') with J_0 = 1/mu', J_m = (L^m - 2 m J_{m-1}) / mu', i.e. the
+// polynomial sum_i c_{m,i}(mu') L^i in L = log(pi eps^2 |w|^2) with c_{m,m} = 1/mu' and
+// c_{m,i} = -2 m c_{m-1,i} / mu' (i < m).  The coefficients eps^{mu'} c_{m,i}(mu') depend on
+// mu' alone: tabulated here for every mu' = mu + 2k and m the products need, so that a ray
+// only evaluates the polynomial in its own L.
+static void hadamard_table(Plan& p) {
+  p.hadw.clear();
+  const ez_sum_spec& s = p.spec;
+  for (int j = 0; j < s.n_distinct; ++j)
+    if (!is_integer(s.nu[j])) return;
+  int islog[EZ_MAX_NU];
+  for (int j = 0; j < s.n_distinct; ++j) sigma_of(p.d, s.nu[j], &islog[j]);
+  int lo = 1 << 30, hi = -(1 << 30), mmax = 0;
+  for (int pr = 0; pr < s.n_prod; ++pr) {
+    int e[EZ_MAX_NU], t[EZ_MAX_NU];
+    for (int j = 0; j < s.n_distinct; ++j) {
+      e[j] = s.expo[pr][j];
+      t[j] = 0;
+    }
+    while (true) {
+      int mu = p.d, deg = 0, ml = 0;
+      for (int j = 0; j < s.n_distinct; ++j) {
+        mu += t[j] * ((int)std::lrint(s.nu[j]) - p.d);
+        deg += (e[j] - t[j]) * p.ell;
+        ml += t[j] * islog[j];
+      }
+      deg = std::min(deg, kNearMaxDeg);
+      lo = std::min(lo, mu);
+      hi = std::max(hi, mu + 2 * deg);
+      mmax = std::max(mmax, ml);
+      int j = 0;
+      for (; j < s.n_distinct; ++j) {
+        if (t[j] < e[j]) {
+          t[j]++;
+          break;
+        }
+        t[j] = 0;
+      }
+      if (j == s.n_distinct) break;
+    }
+  }
+  const int m1 = mmax + 1, n = hi - lo + 1;
+  p.hadw_lo = lo;
+  p.hadw_m1 = m1;
+  p.hadw.assign((size_t)n * m1 * m1, 0.0);
+  std::vector<double> c((size_t)m1 * m1);
+  for (int mu = lo; mu <= hi; ++mu) {
+    if (mu == 0) continue;  // mu + 2k = 0 is refused (EZ_EDOMAIN)
+    const double inv = 1.0 / mu, em = std::pow(p.eps, (double)mu);
+    std::fill(c.begin(), c.end(), 0.0);
+    for (int m = 0; m < m1; ++m) {
+      c[m * m1 + m] = inv;
+      for (int i = 0; i < m; ++i) c[m * m1 + i] = -2.0 * m * c[(m - 1) * m1 + i] * inv;
+    }
+    for (int q = 0; q < m1 * m1; ++q) p.hadw[(size_t)(mu - lo) * m1 * m1 + q] = em * c[q];
+  }
 }
 
 // u_nodes/u_weights (optional, both or neither): an explicit far-field u rule replacing the one
@@ -666,6 +744,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
   if (p.near) {
     p.alpha.clear();
     p.alpha_off.clear();
+    const bool even_only = reflection_symmetric(L);  // odd alpha_i: zero coefficients
     for (int k = 0; k <= p.ell; ++k) {
       p.alpha_off.push_back((int)(p.alpha.size() / 3));
       int K2 = 2 * k;
@@ -674,6 +753,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
           int a2 = K2 - a0 - a1;
           if (d < 3 && a2 != 0) continue;
           if (d < 2 && a1 != 0) continue;
+          if (even_only && ((a0 | a1 | a2) & 1)) continue;
           p.alpha.push_back(a0);
           p.alpha.push_back(a1);
           p.alpha.push_back(a2);
@@ -684,6 +764,7 @@ int make_plan(const ez_lattice_s* L, const ez_sum_spec& spec, const ez_quadratur
       std::string why;
       if (!near_exponents_ok(p, pr, &why)) return fail(EZ_EDOMAIN, "%s", why.c_str());
     }
+    hadamard_table(p);
   }
 
   // segments.  d = 3: a far-field block takes the four sectors of a line group (axis j,
@@ -1054,8 +1135,8 @@ int batch_layout(ez_batch_s& B, bool fill) {
     B.max_phase_pairs = std::max(B.max_phase_pairs, plans[phase_rep[g]].n_ui * plans[phase_rep[g]].n_v);
   B.o_phj = dl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
   const size_t h_phj = hl.take(sizeof(PhaseJob) * std::max(B.n_phase, 1));
-  std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req);
-  std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req);
+  std::vector<size_t> o_un(n_req), o_uw(n_req), o_vn(n_req), o_vw(n_req), o_al(n_req), o_alo(n_req), o_hw(n_req);
+  std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req), h_hw(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
       o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_hbox(n_req);
@@ -1078,10 +1159,13 @@ int batch_layout(ez_batch_s& B, bool fill) {
     h_al[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha.size(), 1));
     o_alo[r] = dl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
     h_alo[r] = hl.take(sizeof(int) * std::max<size_t>(p.alpha_off.size(), 1));
+    o_hw[r] = dl.take(sizeof(double) * std::max<size_t>(p.hadw.size(), 1));
+    h_hw[r] = hl.take(sizeof(double) * std::max<size_t>(p.hadw.size(), 1));
   }
   // everything above is uploaded as one prefix: device and staging offsets must agree
   if (dl.off != hl.off || B.o_items != h_items || B.o_rnl != h_rnl ||
-      (n_req > 0 && (o_alo[n_req - 1] != h_alo[n_req - 1] || o_un[n_req - 1] != h_un[n_req - 1])))
+      (n_req > 0 && (o_alo[n_req - 1] != h_alo[n_req - 1] || o_un[n_req - 1] != h_un[n_req - 1] ||
+                     o_hw[n_req - 1] != h_hw[n_req - 1])))
     return fail(EZ_EINVAL, "internal: staging layout mismatch");
   // device-only tables and outputs
   for (int r = 0; r < n_req; ++r) {
@@ -1256,6 +1340,10 @@ int batch_layout(ez_batch_s& B, bool fill) {
       std::memcpy(Hs + h_al[r], p.alpha.data(), sizeof(int) * p.alpha.size());
       std::memcpy(Hs + h_alo[r], p.alpha_off.data(), sizeof(int) * p.alpha_off.size());
     }
+    R.hadw = p.hadw.empty() ? nullptr : (const double*)dptr(o_hw[r]);
+    R.hadw_lo = p.hadw_lo;
+    R.hadw_m1 = p.hadw_m1;
+    if (!p.hadw.empty()) std::memcpy(Hs + h_hw[r], p.hadw.data(), sizeof(double) * p.hadw.size());
     RecipJob& RJ = rjobs[r];
     RJ.req = r;
     for (int i = 0; i < 3; ++i) {

@@ -139,6 +139,10 @@ struct ReqDesc {
   const int* alpha;       // [n_alpha][3]
   const int* alpha_off;   // start of |alpha| = 2k blocks, k = 0..ell+1
   const double* taylor;   // [n_distinct][n_alpha] : d^alpha Z^reg(0) / alpha!
+  // integer exponents: eps^{mu'} J_m(mu') = sum_{i <= m} hadw[((mu' - hadw_lo) m1 + m) m1 + i] L^i
+  // (m1 = hadw_m1); null otherwise (real exponents: the recurrence per ray)
+  const double* hadw;
+  int hadw_lo, hadw_m1;
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;
   int line0;  // first line (far lines then near lines)

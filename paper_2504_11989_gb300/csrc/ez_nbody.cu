@@ -1369,8 +1369,18 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
         deg = nd2;
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
-    N epm = int_mu ? (mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu)) : exp(mu_r * log(eps));
     N sumk = nint<N>(0);
+    if (R->hadw) {  // integer mu: tabulated coefficients of the weight's polynomial in L
+      const int m1 = R->hadw_m1;
+      const double* q = R->hadw + ((size_t)(mu - R->hadw_lo) * m1 + mlog) * m1;
+      for (int k = 0; k <= deg; ++k, q += 2 * m1 * m1) {
+        N W = q[mlog];
+        for (int i = mlog - 1; i >= 0; --i) W = nfma(W, L, q[i]);
+        sumk = nfma(G[k], W, sumk);
+      }
+      total = nfma(nint<N>(mult) * coef, sumk, total);
+    } else {
+    N epm = int_mu ? (mu >= 0 ? npow(eps, mu) : npow(inv_eps, -mu)) : exp(mu_r * log(eps));
     for (int k = 0; k <= deg; ++k) {
       // J_0 = 1/mu_k, J_i = (L^i - 2 i J_{i-1}) / mu_k with 1/mu_k from the table of
       // reciprocals of small integers (no division in the loop) when mu is an integer
@@ -1385,6 +1395,7 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
       epm = epm * eps2;
     }
     total = nfma(nint<N>(mult) * coef, sumk, total);
+    }
     int j = 0;
     for (; j < nd; ++j) {
       if (t[j] < e[j]) {
