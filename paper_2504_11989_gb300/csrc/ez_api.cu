@@ -253,6 +253,8 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   P.two_a = (int)std::lrint(2.0 * a);
   P.half = is_integer(2.0 * a) ? 1 : 0;
   P.log_m = (is_integer(a) && a <= 0.0) ? (int)std::lrint(-a) : -1;
+  P.below1 = a < 1.0 ? 1 : 0;
+  P.need_lt = (a < 1.0 && (P.log_m >= 0 || !P.half)) ? 1 : 0;
   P.t_geo_end = kT0 * std::pow(kGeoR, kNGeo);
   const double t_half_end = P.t_geo_end + 0.5 * kNHalf;
   int n_rest;  // intervals after the geometric ones
@@ -290,7 +292,7 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
   // rounded down to binary32) where it is <= tol.  They depend on a alone: computed once
   // per order and kept (planning runs for every served request).
   struct SerBrk {
-    float brk[6];
+    float brk[6], brk_mix[6];
   };
   static std::mutex brk_mu;
   static std::map<double, SerBrk> brk_cache;
@@ -299,6 +301,7 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
     auto it = brk_cache.find(a);
     if (it != brk_cache.end()) {
       std::memcpy(P.ser_brk, it->second.brk, sizeof P.ser_brk);
+      std::memcpy(P.ser_brk_mix, it->second.brk_mix, sizeof P.ser_brk_mix);
       return;
     }
   }
@@ -320,8 +323,10 @@ void fill_phi_host(PhiInfo& P, double a, double t_hi_needed) {
     return std::nextafter((float)lo, 0.0f);
   };
   for (int i = 0; i < 6; ++i) P.ser_brk[i] = brk(4 + 2 * i, std::ldexp(1.0, -55));
+  for (int i = 0; i < 6; ++i) P.ser_brk_mix[i] = brk(4 + 2 * i, std::ldexp(1.0, -46));
   SerBrk e;
   std::memcpy(e.brk, P.ser_brk, sizeof e.brk);
+  std::memcpy(e.brk_mix, P.ser_brk_mix, sizeof e.brk_mix);
   std::lock_guard<std::mutex> lk(brk_mu);
   brk_cache[a] = e;
 }
@@ -515,6 +520,15 @@ static void hadamard_table(Plan& p) {
     }
     for (int q = 0; q < m1 * m1; ++q) p.hadw[(size_t)(mu - lo) * m1 * m1 + q] = em * c[q];
   }
+}
+
+// the d = 3 mixed far kernel reads the direction table when its exponents form an order chain
+// (nu_j = nu_0 + 2 j, at least three): the binary64 near-origin chain needs log t and 1/t
+static bool uses_dirlw(const Plan& p) {
+  if (p.d != 3 || p.prec != EZ_MIXED || p.spec.n_distinct < 3) return false;
+  for (int j = 1; j < p.spec.n_distinct; ++j)
+    if (p.spec.nu[j] != p.spec.nu[0] + 2.0 * j) return false;
+  return true;
 }
 
 // u_nodes/u_weights (optional, both or neither): an explicit far-field u rule replacing the one
@@ -1139,7 +1153,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
   std::vector<size_t> h_un(n_req), h_uw(n_req), h_vn(n_req), h_vw(n_req), h_al(n_req), h_alo(n_req), h_hw(n_req);
   std::vector<size_t> o_vff(n_req), h_vff(n_req), o_vwff(n_req), h_vwff(n_req);
   std::vector<size_t> o_rec(n_req), o_recf(n_req), o_reclo(n_req), o_rectmp(n_req), o_gbox(n_req), o_tay(n_req),
-      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_hbox(n_req);
+      o_phig(n_req), o_gboxff(n_req), o_tpart(n_req), o_hbox(n_req), o_dirlw(n_req);
   std::vector<std::vector<size_t>> o_tab(n_req), o_tabf(n_req), o_tabff(n_req);
   for (int r = 0; r < n_req; ++r) {
     Plan& p = plans[r];
@@ -1177,6 +1191,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
     o_gbox[r] = dl.take(sizeof(double) * p.cells * p.spec.n_distinct);
     o_gboxff[r] = p.prec == EZ_MIXED ? dl.take(sizeof(float2) * p.cells * p.spec.n_distinct) : 0;
     o_hbox[r] = p.d == 3 ? dl.take(16 * (size_t)p.hslot * std::max<long long>(p.line_hi - p.line_lo, 1)) : 0;
+    o_dirlw[r] = uses_dirlw(p) ? dl.take(sizeof(double4) * 12 * (size_t)p.n_v * p.n_v) : 0;
     o_tab[r].assign(2 * EZ_MAX_NU, 0);
     o_tabf[r].assign(2 * EZ_MAX_NU, 0);
     o_tabff[r].assign(2 * EZ_MAX_NU, 0);
@@ -1340,6 +1355,7 @@ int batch_layout(ez_batch_s& B, bool fill) {
       std::memcpy(Hs + h_al[r], p.alpha.data(), sizeof(int) * p.alpha.size());
       std::memcpy(Hs + h_alo[r], p.alpha_off.data(), sizeof(int) * p.alpha_off.size());
     }
+    R.dirlw = o_dirlw[r] ? (const double4*)dptr(o_dirlw[r]) : nullptr;
     R.hadw = p.hadw.empty() ? nullptr : (const double*)dptr(o_hw[r]);
     R.hadw_lo = p.hadw_lo;
     R.hadw_m1 = p.hadw_m1;
@@ -1524,6 +1540,15 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
     if (max_groups > 0) {
       hbox_kernel<<<dim3((unsigned)max_groups, B.n_req, (unsigned)((max_tasks + 255) / 256)), 256, 0, stream>>>(
           dreqs, (const HboxJob*)dptr(B.o_hj));
+      EZ_LAUNCHED();
+    }
+  }
+  {
+    long long max_dirs = 0;
+    for (auto& p : B.plans)
+      if (uses_dirlw(p)) max_dirs = std::max(max_dirs, 12LL * p.n_v * p.n_v);
+    if (max_dirs > 0) {
+      dirlw_kernel<<<dim3((unsigned)((max_dirs + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs);
       EZ_LAUNCHED();
     }
   }

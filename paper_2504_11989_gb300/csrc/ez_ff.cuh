@@ -95,4 +95,19 @@ __host__ __device__ __forceinline__ void ff_split(double x, float& hi, float& lo
   lo = (float)(x - (double)hi);
 }
 
+// the same split with two binary64-pipe operations instead of four: hi = x truncated to 24
+// significant bits, assembled by integer operations from the bits of x (binary32 normal
+// range; else the rounded split), lo = x - hi (exact in binary64) rounded to binary32.
+// |lo| <= ulp(hi): a float-float value of ~47 bits.
+__device__ __forceinline__ void ff_split_trunc(double x, float& hi, float& lo) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e > 896 && e < 1151) {
+    hi = __int_as_float((int)((b >> 32) & 0x80000000LL) | ((e - 896) << 23) | (int)((b >> 29) & 0x7fffff));
+    lo = (float)(x - __longlong_as_double(b & ~0x1fffffffLL));
+  } else {
+    ff_split(x, hi, lo);
+  }
+}
+
 }  // namespace ez

@@ -69,6 +69,9 @@ struct PhiInfo {
   // t < kT0: below ser_brk[i] the series needs only N = 4 + 2 i terms (i < 6; N = kNSer
   // above ser_brk[5]): the dropped terms sum to <= 2^-55 in absolute value.
   float ser_brk[6];
+  float ser_brk_mix[6];  // the same for 2^-46 (the mixed form's binary64 order chain)
+  int below1;   // a < 1: the mixed form's binary64 order chain takes its series
+  int need_lt;  // a < 1 with a log term or a non-half-integer order: log t is needed
 };
 static_assert(sizeof(PhiInfo) % sizeof(double) == 0, "PhiInfo is copied to shared memory in doubles");
 
@@ -143,6 +146,12 @@ struct ReqDesc {
   // (m1 = hadw_m1); null otherwise (real exponents: the recurrence per ray)
   const double* hadw;
   int hadw_lo, hadw_m1;
+  // d = 3 mixed form with an order chain: (log |w|^2, 1/|w|^2) of the scaled node direction
+  // w = sigma^j(p1 v1, p2 v2, 1) mapped by A^{-T} (k = u w), index
+  // (((j 2 + [p1 < 0]) 2 + [p2 < 0]) n_v + v2) n_v + v1, as (log |w|^2, |w|^2, 1/|w|^2, 0):
+  // t, log t and 1/t of the h = 0 term follow from u^2, log u^2 and 1/u^2 of the block
+  // (binary64); null otherwise
+  const double4* dirlw;
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;
   int line0;  // first line (far lines then near lines)

@@ -104,6 +104,7 @@ __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, co
                              int n_req, const double* lines, double* out);
 __global__ void epstein_kernel(EpsteinArgs args);
 __global__ void phase_kernel(const PhaseJob* jobs);
+__global__ void dirlw_kernel(const ReqDesc* reqs);
 
 // ---- the Epstein zeta function in any dimension d <= kMaxDnd ----
 // Lattice points id in the box lo + [0, ext) with |M id - c|^2 <= R2, stored as rows along the

@@ -281,19 +281,17 @@ __device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain,
 // lowest a_0 < 0), in binary64: the orders a < 1 by their series (log t and 1/t shared),
 // e^{-t} = t Phi_{a_0+1} - a_0 Phi_{a_0} from the two lowest (a sum of positive terms), and
 // every order a >= 1 upward by Phi_a = ((a-1) Phi_{a-1} + e^{-t}) / t, also positive terms.
+// lt = log t (when some order needs it) and it = 1/t come from the caller.
 template <int NDM>
-__device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, ff* hs, unsigned& coefs) {
-  bool need_log = false;
-  for (int j = 0; j < nd; ++j) need_log |= sphi[j].a < 1.0 && (sphi[j].log_m >= 0 || !sphi[j].half);
-  const double lt = need_log ? log(t) : 0.0;
-  const double it = 1.0 / t;
+__device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, double lt, double it, ff* hs,
+                                             unsigned& coefs) {
   double prev = 0.0, E = 0.0;
   for (int j = nd - 1; j >= 0; --j) {
     const PhiInfo& P = sphi[j];
     double v;
-    if (P.a < 1.0) {
+    if (P.below1) {
       int n;
-      v = phi_small_shared(P, t, lt, it, n);
+      v = phi_small_shared(P, t, lt, it, n, P.ser_brk_mix);
       coefs += n;
       if (j == nd - 2) E = fma(t, v, -sphi[nd - 1].a * prev);
     } else {
@@ -301,7 +299,7 @@ __device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double
     }
     prev = v;
     float hi, lo;
-    ff_split(v, hi, lo);
+    ff_split_trunc(v, hi, lo);
     hs[j] = ff_add(hs[j], ff{hi, lo});
   }
 }
@@ -316,9 +314,12 @@ __device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double
 // The list is sorted by |G|: once |G| > sqrt(t_mix / c) + |k|, every remaining term is a
 // binary32 tail, evaluated by a short loop that skips the points beyond the cutoff.  Tails
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
+// t0, lt0, it0: t, log t and 1/t of the h = 0 term (G = 0) when the caller has them (t0 = 0
+// otherwise).
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
-                                                ff* A, unsigned& terms, unsigned& coefs, const RecCacheMix& rc) {
+                                                ff* A, unsigned& terms, unsigned& coefs, const RecCacheMix& rc,
+                                                double t0, double lt0, double it0) {
   const int nrec = rc.n;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
@@ -374,6 +375,11 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     // binary64: the incomplete gamma near the origin (t < kT0, the h = 0 term near k = 0:
     // entire series plus singular part, as in the FP64 form), t = 0, and beyond the table
     if (tf < (float)kT0 || tf > t_hi) {
+      if (chain && tf < (float)kT0 && Gf.w == 0.0f && t0 > 0.0 && sphi[nd - 1].a < 0.0) {
+        ++terms;
+        small_chain_f64<NDM>(sphi, nd, t0, lt0, it0, hs, coefs);
+        continue;
+      }
       const G4 G = ldg_g4(R->rec + (h < kRecCache ? rc.idx[h] : h));
       const double q0 = G.x + ((double)kf[0] + (double)klo[0]);
       double qq = q0 * q0;
@@ -387,7 +393,10 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
       }
       ++terms;
       if (chain && tf < (float)kT0 && qq > 0.0 && sphi[nd - 1].a < 0.0) {
-        small_chain_f64<NDM>(sphi, nd, sphi[0].c_lam * qq, hs, coefs);
+        const double t = sphi[0].c_lam * qq;
+        bool need_lt = false;
+        for (int j = 0; j < nd; ++j) need_lt |= sphi[j].need_lt != 0;
+        small_chain_f64<NDM>(sphi, nd, t, need_lt ? log(t) : 0.0, 1.0 / t, hs, coefs);
         continue;
       }
 #pragma unroll
@@ -889,6 +898,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
     }
     double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0}, wneg[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
     if constexpr (MIXED) {
+      // log u^2 and 1/u^2 of the block for the h = 0 term's log t and 1/t (binary64)
+      const double4* dirlw = R->dirlw;
+      const double u2 = u * u, lu2 = dirlw ? 2.0 * log(u) : 0.0, iu2 = dirlw ? 1.0 / u2 : 0.0;
       ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       ff wn[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
@@ -946,7 +958,16 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
           ff k[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i) k[i] = ff_add(kb[i], ka[i]);
-          recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
+          double t0 = 0.0, lt0 = 0.0, it0 = 0.0;
+          if (dirlw) {
+            const double4* dp = dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1;
+            const double2 a = __ldg(reinterpret_cast<const double2*>(dp));
+            const double b = __ldg(reinterpret_cast<const double*>(dp) + 2);
+            t0 = u2 * a.y;
+            lt0 = lu2 + a.x;
+            it0 = iu2 * b;
+          }
+          recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, t0, lt0, it0);
           assemble_mixed<NDM>(R, nd, np, Zp, A, w, ws);
 #pragma unroll
           for (int i = 0; i < 3; ++i) ka[i] = ff{-ka[i].hi, -ka[i].lo};
@@ -1129,7 +1150,7 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
           const float4 h0 = H4[jn * (Ma + 1)];
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{h0.x, h0.y});
         }
-      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
+      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, 0.0, 0.0, 0.0);
       assemble_mixed<NDM>(R, nd, np, Zr, A, ff{wv.x, wv.y}, ws);
     }
 #pragma unroll
@@ -1222,7 +1243,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
         const ff S = ff_two_sum(s[jn], c[jn]);
         Zr[jn] = ff{2.0f * S.hi, 2.0f * S.lo};
       }
-    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs, rcache);
+    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, 0.0, 0.0, 0.0);
     ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     assemble_mixed<NDM>(R, nd, np, Zr, A, ffd(w), ws);
 #pragma unroll

@@ -233,11 +233,12 @@ static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
 // t < kT0, binary64, with log t (log-case and non-half-integer orders) and 1/t supplied by the caller, who
 // shares them between the orders of one reciprocal term: the entire series cut at 2^-55
 // plus the singular part.  n_used: series terms (work count).
-__device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, int& n_used) {
+__device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, int& n_used,
+                                                   const float* brk) {
   const float tf = (float)t;
   int N = 4;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) N += tf >= P.ser_brk[i] ? 2 : 0;
+  for (int i = 0; i < 6; ++i) N += tf >= brk[i] ? 2 : 0;
   n_used = N;
   double s = P.ser[N - 1];
 #pragma unroll 1

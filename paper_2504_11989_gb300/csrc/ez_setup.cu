@@ -522,4 +522,32 @@ __global__ void phase_kernel(const PhaseJob* jobs) {
   }
 }
 
+// d = 3 mixed form with an order chain: (log |w|^2, |w|^2, 1/|w|^2) of every scaled node direction
+// w = p1 v1 A^{-T} e_a + p2 v2 A^{-T} e_b + A^{-T} e_c (axes a = j, b = j + 1, c = j + 2 mod 3,
+// scaled by sqrt(pi) lam), so that the far kernel gets t = u^2 |w|^2, log t = 2 log u +
+// log |w|^2 and 1/t = u^{-2} / |w|^2 of the h = 0 term without a logarithm or a division.
+__global__ void dirlw_kernel(const ReqDesc* reqs) {
+  const ReqDesc* R = reqs + blockIdx.y;
+  if (!R->dirlw) return;
+  const int nv = R->n_v;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 12LL * nv * nv) return;
+  const int v1 = (int)(i % nv);
+  long long r = i / nv;
+  const int v2 = (int)(r % nv);
+  r /= nv;
+  const int s2 = (int)(r % 2);
+  r /= 2;
+  const int s1 = (int)(r % 2), j = (int)(r / 2);
+  const int ax_a = j, ax_b = (j + 1) % 3, ax_c = (j + 2) % 3;
+  const double a = s1 ? -R->v_nodes[v1] : R->v_nodes[v1];
+  const double b = s2 ? -R->v_nodes[v2] : R->v_nodes[v2];
+  double w2 = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double wc = fma(R->AiTs[c * 3 + ax_a], a, fma(R->AiTs[c * 3 + ax_b], b, R->AiTs[c * 3 + ax_c]));
+    w2 = fma(wc, wc, w2);
+  }
+  const_cast<double4*>(R->dirlw)[i] = make_double4(log(w2), w2, 1.0 / w2, 0.0);
+}
+
 }  // namespace ez
