@@ -181,14 +181,44 @@ __device__ __noinline__ void rec_candidates(RC& rc, const ReqDesc* R, const doub
   __syncthreads();
 }
 
+// h = 0 term near k = 0 (t < kT0) of an order chain (orders a_j = a_0 + (nd-1-j), lowest
+// a_0 < 0), in binary64: the orders a < 1 by their series (log t and 1/t given by the
+// caller), e^{-t} = t Phi_{a_0+1} - a_0 Phi_{a_0} from the two lowest (a sum of positive
+// terms), and every order a >= 1 upward by Phi_a = ((a-1) Phi_{a-1} + e^{-t}) / t, also
+// positive terms.  brk: the series breakpoints (2^-55 FP64 form, 2^-46 mixed form).
+template <int NDM>
+__device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double t, double lt, double it,
+                                             const float* const* brk, double (&v)[NDM], unsigned& coefs) {
+  double prev = 0.0, E = 0.0;
+#pragma unroll
+  for (int j = NDM - 1; j >= 0; --j)
+    if (j < nd) {
+      const PhiInfo& P = sphi[j];
+      double x;
+      if (P.below1) {
+        int n;
+        x = phi_small_shared(P, t, lt, it, n, brk[j]);
+        coefs += n;
+        if (j == nd - 2) E = fma(t, x, -sphi[nd - 1].a * prev);
+      } else {
+        x = fma(sphi[j + 1].a, prev, E) * it;
+      }
+      prev = x;
+      v[j] = x;
+    }
+}
+
 // reciprocal sum at k (x = 0), FP64 form: acc[j] += Phi_{a_j}(pi lam^2 |G + k|^2) over
 // |G + k| <= R, every value binary64.  The cutoff test, the branch and the table interval
 // are taken in binary32 (a term within ~1e-7 relative of the cutoff radius may fall either
 // way: it is below the truncation tolerance by the choice of the radius).
+// lt0, it0: log t and 1/t of the h = 0 term (G = 0) when the caller has them (NaN lt0
+// otherwise).  With an order chain the terms with t < kT0 take the chain (chain_values).
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs,
-                                          unsigned& qterms, const RecCacheF64& rc) {
+                                          unsigned& qterms, const RecCacheF64& rc, double lt0, double it0) {
+  const bool chain = NDM >= 3 && R->order_chain && sphi[nd - 1].a < 0.0;
   const bool list = rc.n >= 0;
   const int nrec = list ? rc.n : R->n_rec;
   const float R2f = R->R2f, cf = R->c_lam_f;
@@ -224,6 +254,33 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
       double qq = 0.0;
       bool have_qq = false;
       ++terms;
+      if (chain && tf < (float)kT0) {
+        const G4 G = ldg_g4(rec + h);
+        qq = fma(k2v[0], G.x, G.w + kk2);
+        if (D >= 2) qq = fma(k2v[1], G.y, qq);
+        if (D >= 3) qq = fma(k2v[2], G.z, qq);
+        ++qterms;
+        if (qq > 0.0) {
+          const double t = sphi[0].c_lam * qq;
+          double lt = lt0, it = it0;
+          if (!(G.w == 0.0 && lt0 == lt0)) {
+            bool need_lt = false;
+            for (int j = 0; j < nd; ++j) need_lt |= sphi[j].need_lt != 0;
+            lt = need_lt ? log(t) : 0.0;
+            it = 1.0 / t;
+          }
+          const float* brk[NDM];
+#pragma unroll
+          for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk;
+          double v[NDM];
+          chain_values<NDM>(sphi, nd, t, lt, it, brk, v, coefs);
+#pragma unroll
+          for (int j = 0; j < NDM; ++j)
+            if (j < nd) acc[j] += v[j];
+          continue;
+        }
+        have_qq = true;
+      }
 #pragma unroll
       for (int j = 0; j < NDM; ++j)
         if (j < nd) {
@@ -277,31 +334,22 @@ __device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain,
     }
 }
 
-// Mixed form, h = 0 term near k = 0 (t < kT0) of an order chain (orders a_j = a_0 + (nd-1-j),
-// lowest a_0 < 0), in binary64: the orders a < 1 by their series (log t and 1/t shared),
-// e^{-t} = t Phi_{a_0+1} - a_0 Phi_{a_0} from the two lowest (a sum of positive terms), and
-// every order a >= 1 upward by Phi_a = ((a-1) Phi_{a-1} + e^{-t}) / t, also positive terms.
-// lt = log t (when some order needs it) and it = 1/t come from the caller.
+// the mixed form's use: the values split into float-float and added to hs
 template <int NDM>
 __device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, double lt, double it, ff* hs,
                                              unsigned& coefs) {
-  double prev = 0.0, E = 0.0;
-  for (int j = nd - 1; j >= 0; --j) {
-    const PhiInfo& P = sphi[j];
-    double v;
-    if (P.below1) {
-      int n;
-      v = phi_small_shared(P, t, lt, it, n, P.ser_brk_mix);
-      coefs += n;
-      if (j == nd - 2) E = fma(t, v, -sphi[nd - 1].a * prev);
-    } else {
-      v = fma(sphi[j + 1].a, prev, E) * it;
+  const float* brk[NDM];
+#pragma unroll
+  for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk_mix;
+  double v[NDM];
+  chain_values<NDM>(sphi, nd, t, lt, it, brk, v, coefs);
+#pragma unroll
+  for (int j = 0; j < NDM; ++j)
+    if (j < nd) {
+      float hi, lo;
+      ff_split_trunc(v[j], hi, lo);
+      hs[j] = ff_add(hs[j], ff{hi, lo});
     }
-    prev = v;
-    float hi, lo;
-    ff_split_trunc(v, hi, lo);
-    hs[j] = ff_add(hs[j], ff{hi, lo});
-  }
 }
 
 // Mixed form of the same sum.  Terms by t = pi lam^2 |G + k|^2 (binary32 screen):
@@ -992,6 +1040,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
       }
     } else {
       const double2* Bs = B + s2 * nBs;
+      // log u^2 and 1/u^2 of the block for the h = 0 term's log t and 1/t
+      const double4* dirlw = R->dirlw;
+      const double lu2 = dirlw ? 2.0 * log(u) : 0.0, iu2 = dirlw ? 1.0 / (u * u) : 0.0;
       for (int n = threadIdx.x; n < nn; n += blockDim.x) {
         const int v2l = n / nv, v1 = n - v2l * nv;
         const double kta = u * R->v_nodes[v1];
@@ -1029,7 +1080,13 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn) acc[jn] = 0.0;
           const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
+          double lt0 = __longlong_as_double(0x7ff8000000000000LL), it0 = 0.0;
+          if (dirlw) {
+            const double4* dp = dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1;
+            lt0 = lu2 + __ldg(reinterpret_cast<const double*>(dp));
+            it0 = iu2 * __ldg(reinterpret_cast<const double*>(dp) + 2);
+          }
+          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, lt0, it0);
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) Z[jn] = R->pref[jn] * (Zp[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1180,7 +1237,8 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
+    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache,
+                      __longlong_as_double(0x7ff8000000000000LL), 0.0);
 #pragma unroll
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1261,7 +1319,8 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
   const float kf[1] = {(float)k[0]};
-  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache);
+  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache,
+                    __longlong_as_double(0x7ff8000000000000LL), 0.0);
 #pragma unroll
   for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);

@@ -522,7 +522,7 @@ __global__ void phase_kernel(const PhaseJob* jobs) {
   }
 }
 
-// d = 3 mixed form with an order chain: (log |w|^2, |w|^2, 1/|w|^2) of every scaled node direction
+// d = 3 with an order chain: (log |w|^2, |w|^2, 1/|w|^2) of every scaled node direction
 // w = p1 v1 A^{-T} e_a + p2 v2 A^{-T} e_b + A^{-T} e_c (axes a = j, b = j + 1, c = j + 2 mod 3,
 // scaled by sqrt(pi) lam), so that the far kernel gets t = u^2 |w|^2, log t = 2 log u +
 // log |w|^2 and 1/t = u^{-2} / |w|^2 of the h = 0 term without a logarithm or a division.
