@@ -40,14 +40,15 @@ HEADLINE_LATTICES = ("sc", "fcc", "bcc")
 # Counters of the dominant kernels from the committed ncu summaries (full command in each
 # file).  None when the kernel has changed since the capture.
 PROFILES = {
-    # far_kernel_d3<FP64, 4 exponents>, config 3: mean of six launches of the --metrics capture in
-    # profiles/far_kernel_d3_config3.md (15.77-16.08 MB read, 0-512 B written)
-    "far_d3_f64_dram_bytes_per_launch": 15898936,
+    # far_kernel_d3<FP64, 4 exponents>, config 3: mean of four launches of the --metrics capture
+    # of the current build in profiles/far_kernel_d3_config3.md (20.83-20.91 MB read, <= 55 KB
+    # written)
+    "far_d3_f64_dram_bytes_per_launch": 20864640,
     # far_kernel_d3<mixed, 4 exponents>: issue-slot, binary32-pipe and binary64-pipe utilisation
     # (--set full capture of the current build, profiles/far_kernel_d3_config3.md)
-    "far_d3_mixed_issue_frac": 0.354,
-    "far_d3_mixed_fp32_pipe_frac": 0.189,
-    "far_d3_mixed_fp64_pipe_frac": 0.545,
+    "far_d3_mixed_issue_frac": 0.384,
+    "far_d3_mixed_fp32_pipe_frac": 0.211,
+    "far_d3_mixed_fp64_pipe_frac": 0.418,
     # far_kernel_d2<FP64, 1 exponent>, config 2, 128 sums (profiles/far_kernel_d2_config2.md)
     "far_d2_f64_dram_bytes_per_launch": None,
 }
