@@ -168,7 +168,9 @@ def headline_config():
                         "2,359,296 far nodes + 12 x 64^2 near-part rays per sum; eps = 1e-2, ell = 4; default "
                         "splitting parameter and cutoffs (e^-45)",
             "global_batch": len(HEADLINE_LATTICES), "nodes_per_sum": 12 * 6 * 8 * 64 * 64,
-            "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps"}
+            "parallelism": "independent sums per GPU", "l2": "flushed (256 MiB write) between timed steps",
+            "tables": "lattice tables rebuilt every step; Phi_a(t) tables (orders only) filled by the "
+                      "batch's first warm-up run and kept"}
 
 
 def config2_problems(rank: int, per_lattice: int):

@@ -209,12 +209,14 @@ int ez_lattice_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
 /* A batch keeps the plans of n_req sums and the device memory of all their tables
  * and partial sums resident.  ez_batch_create plans, allocates (cudaMalloc and
  * pinned host staging, owned by the batch) and uploads the descriptors on
- * `stream`.  ez_batch_run launches every kernel of the path (tables are rebuilt on
- * each run) and writes out[r*EZ_MAX_PROD + p] (host or device; with host memory
+ * `stream`.  ez_batch_run launches every kernel of the path and writes
+ * out[r*EZ_MAX_PROD + p] (host or device; with host memory
  * the call synchronises `stream`, with device memory it is asynchronous).
  * ez_batch_lines copies the per-line partial sums of the last run (layout as in
  * ez_lattice_sums); ez_batch_n_lines gives their count.  A batch may be run any
- * number of times, on one stream at a time. */
+ * number of times, on one stream at a time.  Every run rebuilds the lattice tables
+ * (reciprocal lists, real-space boxes, Taylor tensors); the tables of Phi_a(t), which
+ * depend on the orders a alone, are filled by the first run and kept by the batch. */
 typedef struct ez_batch_s* ez_batch;
 int ez_batch_create(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
                     const ez_quadrature* quads, void* stream, ez_batch* out);

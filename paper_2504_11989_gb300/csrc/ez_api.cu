@@ -976,6 +976,7 @@ struct ez_batch_s {
          o_rl0 = 0, o_rnl = 0, o_seg = 0, o_lines = 0, o_out = 0;
   int n_phi = 0, n_tay = 0;
   int n_phi_jobs = 0;  // phitab jobs of a run (groups whose table this batch fills)
+  bool phi_built = false;  // an owning batch's Phi tables are filled (by its first run)
   size_t o_hj = 0;
   std::vector<std::pair<int, int>> phi_master;  // per distinct a: (request, nu index) computing the table
   // Phi tables held outside the batch (a server's resident tables), per group: the binary64,
@@ -1516,10 +1517,13 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   for (auto& m : B.phi_master) max_int = std::max(max_int, phi_slot(B.plans[m.first], m.second).n_int);
   for (size_t g = 0; g < B.phi_fill_nint.size(); ++g)
     if (B.phi_fill[g]) max_int = std::max(max_int, B.phi_fill_nint[g]);
-  if (B.n_phi_jobs > 0) {
+  // the Phi tables depend on the orders alone: a batch that owns its memory fills them on
+  // its first run and keeps them (its runs are ordered on one stream at a time)
+  if (B.n_phi_jobs > 0 && !(B.owns && B.phi_built)) {
     phitab_kernel<<<dim3((max_int + kPhiIv - 1) / kPhiIv, B.n_phi_jobs), kPhiIv * kNC, 0, stream>>>(
         (const PhiJob*)dptr(B.o_pj));
     EZ_LAUNCHED();
+    if (B.owns) B.phi_built = true;
   }
   for (cudaEvent_t e : B.phi_ready) EZ_CUDA(cudaEventRecord(e, stream));
   // the real-space box reads the real-order Phi tables: after phitab
