@@ -1578,9 +1578,10 @@ __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const lon
 }
 
 // Compensated (Neumaier) sum of a request's lines.  One block of 128 threads per request:
-// thread (slot j, product p) sums lines j, j + 32, j + 64, ... in order; the 32 partial
-// sums of each product are then added in slot order.  The order is fixed, so the result
-// does not depend on the batch the request runs in.
+// thread (slot j, product p) sums lines j, j + 32, j + 64, ... in order (eight at a time,
+// each group plainly and the groups with compensation); the 32 partial sums of each product
+// are then added in slot order.  The order is fixed, so the result does not depend on the
+// batch the request runs in.
 __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
   const double t = s + x;
   c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
@@ -1595,8 +1596,19 @@ __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, co
   const int p = threadIdx.x & 3, j = threadIdx.x >> 2;
   const int nl = req_nlines[r];
   const double* base = lines + (size_t)req_line0[r] * EZ_MAX_PROD;
+  // groups of eight of the thread's lines summed plainly, each group added with Neumaier's
+  // compensation (error <= 8 ulp of the group's magnitude, at a third of the binary64
+  // operations of a compensated step per line)
   double s = 0.0, c = 0.0;
-  for (int q = j; q < nl; q += 32) neumaier_add(s, c, base[(size_t)q * EZ_MAX_PROD + p]);
+  int q = j;
+  for (; q + 7 * 32 < nl; q += 8 * 32) {
+    const double* b = base + (size_t)q * EZ_MAX_PROD + p;
+    double g = b[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) g += b[(size_t)k * 32 * EZ_MAX_PROD];
+    neumaier_add(s, c, g);
+  }
+  for (; q < nl; q += 32) neumaier_add(s, c, base[(size_t)q * EZ_MAX_PROD + p]);
   __shared__ double ps[128], pc[128];
   ps[threadIdx.x] = s;
   pc[threadIdx.x] = c;
