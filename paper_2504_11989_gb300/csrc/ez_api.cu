@@ -996,6 +996,7 @@ struct ez_batch_s {
   long long n_lines = 0;
   std::vector<long long> line0;
   bool ran = false;
+  bool lines_fresh = false;  // the lines buffer holds the last run's lines
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, far begin, far end, end
 };
@@ -1595,17 +1596,29 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
     near_kernel<<<(unsigned)(B.near_end - B.near_begin), 128, 0, stream>>>(dreqs, ditems + B.near_begin, dseg);
     EZ_LAUNCHED();
   }
-  double* dlines = (double*)dptr(B.o_lines);
-  lines_kernel<<<(unsigned)((B.n_lines + 127) / 128), 128, 0, stream>>>(dreqs, (const int*)dptr(B.o_lreq),
-                                                                     (const long long*)dptr(B.o_lseg0),
-                                                                     (const int*)dptr(B.o_lnseg), (int)B.n_lines, dseg, dlines);
-  EZ_LAUNCHED();
+  // the totals straight from the segments (lines_kernel's order of additions); the lines
+  // themselves are written only when a caller asks for them (batch_make_lines)
   double* dout = (double*)dptr(B.o_out);
-  total_kernel<<<B.n_req, 128, 0, stream>>>(dreqs, (const long long*)dptr(B.o_rl0),
-                                                                     (const int*)dptr(B.o_rnl), B.n_req, dlines, dout);
+  total_kernel<<<B.n_req, 128, 0, stream>>>(dreqs, (const long long*)dptr(B.o_rl0), (const int*)dptr(B.o_rnl),
+                                            B.n_req, (const long long*)dptr(B.o_lseg0), (const int*)dptr(B.o_lnseg),
+                                            dseg, dout);
   EZ_LAUNCHED();
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[3], stream));
   B.ran = true;
+  B.lines_fresh = false;
+  return EZ_OK;
+}
+
+// the per-line partial sums of the last run, from its segments (kept until the next run)
+int batch_make_lines(ez_batch_s& B, cudaStream_t stream) {
+  if (B.lines_fresh || B.n_lines == 0) return EZ_OK;
+  char* base = B.d;
+  auto dptr = [&](size_t o) { return base + o; };
+  lines_kernel<<<(unsigned)((B.n_lines + 127) / 128), 128, 0, stream>>>(
+      (const ReqDesc*)dptr(B.o_req), (const int*)dptr(B.o_lreq), (const long long*)dptr(B.o_lseg0),
+      (const int*)dptr(B.o_lnseg), (int)B.n_lines, (const double*)dptr(B.o_seg), (double*)dptr(B.o_lines));
+  EZ_LAUNCHED();
+  B.lines_fresh = true;
   return EZ_OK;
 }
 
@@ -1662,6 +1675,8 @@ extern "C" int ez_batch_lines(ez_batch B, double* lines, long long* line_offsets
   if (!B || !B->ran) return fail(EZ_EINVAL, "batch has not run");
   cudaStream_t stream = (cudaStream_t)stream_;
   if (lines) {
+    int rc = batch_make_lines(*B, stream);
+    if (rc) return rc;
     EZ_CUDA(cudaMemcpyAsync(lines, B->d + B->o_lines, sizeof(double) * EZ_MAX_PROD * B->n_lines, cudaMemcpyDefault, stream));
     if (!is_device_ptr(lines)) EZ_CUDA(cudaStreamSynchronize(stream));
   }
@@ -1785,8 +1800,11 @@ static int run_batch(ez_batch_s& B, double* out, double* lines_out, long long* l
   rc = batch_launch(B, stream);
   if (rc) return rc;
   EZ_CUDA(cudaMemcpyAsync(out, B.d + B.o_out, sizeof(double) * EZ_MAX_PROD * n_req, cudaMemcpyDefault, stream));
-  if (lines_out)
+  if (lines_out) {
+    rc = batch_make_lines(B, stream);
+    if (rc) return rc;
     EZ_CUDA(cudaMemcpyAsync(lines_out, B.d + B.o_lines, sizeof(double) * EZ_MAX_PROD * B.n_lines, cudaMemcpyDefault, stream));
+  }
   if (line_offsets)
     for (int r = 0; r <= n_req; ++r) line_offsets[r] = r < n_req ? B.line0[r] : B.n_lines;
   EZ_CUDA(cudaStreamSynchronize(stream));

@@ -101,7 +101,8 @@ __global__ void near_kernel(const ReqDesc* reqs, const Item* items, double* seg)
 __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const long long* line_seg0,
                              const int* line_nseg, int n_lines, const double* seg, double* lines);
 __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines,
-                             int n_req, const double* lines, double* out);
+                             int n_req, const long long* line_seg0, const int* line_nseg, const double* seg,
+                             double* out);
 __global__ void epstein_kernel(EpsteinArgs args);
 __global__ void phase_kernel(const PhaseJob* jobs);
 __global__ void dirlw_kernel(const ReqDesc* reqs);

@@ -1577,7 +1577,9 @@ __global__ void lines_kernel(const ReqDesc* reqs, const int* line_req, const lon
   }
 }
 
-// Compensated (Neumaier) sum of a request's lines.  One block of 128 threads per request:
+// Compensated (Neumaier) sum of a request's lines, each line formed from its segments in
+// the order lines_kernel adds them (the total does not depend on whether the lines are
+// written).  One block of 128 threads per request:
 // thread (slot j, product p) sums lines j, j + 32, j + 64, ... in order (eight at a time,
 // each group plainly and the groups with compensation); the 32 partial sums of each product
 // are then added in slot order.  The order is fixed, so the result does not depend on the
@@ -1589,26 +1591,34 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
 }
 
 __global__ void total_kernel(const ReqDesc* reqs, const long long* req_line0, const int* req_nlines, int n_req,
-                             const double* lines, double* out) {
+                             const long long* line_seg0, const int* line_nseg, const double* seg, double* out) {
   static_assert(EZ_MAX_PROD == 4, "128 threads = 32 slots x 4 products");
   const int r = blockIdx.x;
   if (r >= n_req) return;
   const int p = threadIdx.x & 3, j = threadIdx.x >> 2;
   const int nl = req_nlines[r];
-  const double* base = lines + (size_t)req_line0[r] * EZ_MAX_PROD;
+  const long long l0 = req_line0[r];
+  // line q of the request: its segments added in order from 0, as lines_kernel adds them
+  auto line = [&](int q) {
+    const long long L = l0 + q;
+    const double* sp = seg + (size_t)line_seg0[L] * EZ_MAX_PROD + p;
+    const int ns = line_nseg[L];
+    double v = 0.0;
+    for (int k = 0; k < ns; ++k) v += sp[(size_t)k * EZ_MAX_PROD];
+    return v;
+  };
   // groups of eight of the thread's lines summed plainly, each group added with Neumaier's
   // compensation (error <= 8 ulp of the group's magnitude, at a third of the binary64
   // operations of a compensated step per line)
   double s = 0.0, c = 0.0;
   int q = j;
   for (; q + 7 * 32 < nl; q += 8 * 32) {
-    const double* b = base + (size_t)q * EZ_MAX_PROD + p;
-    double g = b[0];
+    double g = line(q);
 #pragma unroll
-    for (int k = 1; k < 8; ++k) g += b[(size_t)k * 32 * EZ_MAX_PROD];
+    for (int k = 1; k < 8; ++k) g += line(q + k * 32);
     neumaier_add(s, c, g);
   }
-  for (; q < nl; q += 32) neumaier_add(s, c, base[(size_t)q * EZ_MAX_PROD + p]);
+  for (; q < nl; q += 32) neumaier_add(s, c, line(q));
   __shared__ double ps[128], pc[128];
   ps[threadIdx.x] = s;
   pc[threadIdx.x] = c;
