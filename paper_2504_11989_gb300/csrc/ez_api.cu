@@ -522,14 +522,8 @@ static void hadamard_table(Plan& p) {
   }
 }
 
-// the d = 3 far kernels read the direction table when the exponents form an order chain
-// (nu_j = nu_0 + 2 j, at least three): the binary64 near-origin chain needs log t and 1/t
-static bool uses_dirlw(const Plan& p) {
-  if (p.d != 3 || p.spec.n_distinct < 3) return false;
-  for (int j = 1; j < p.spec.n_distinct; ++j)
-    if (p.spec.nu[j] != p.spec.nu[0] + 2.0 * j) return false;
-  return true;
-}
+// the d = 3 far kernels read the direction table for the binary64 near-origin term
+static bool uses_dirlw(const Plan& p) { return p.d == 3; }
 
 // u_nodes/u_weights (optional, both or neither): an explicit far-field u rule replacing the one
 // q describes (the adaptive driver); q.u_rule still decides whether the near part is present.

@@ -146,11 +146,10 @@ struct ReqDesc {
   // (m1 = hadw_m1); null otherwise (real exponents: the recurrence per ray)
   const double* hadw;
   int hadw_lo, hadw_m1;
-  // d = 3 with an order chain: (log |w|^2, 1/|w|^2) of the scaled node direction
+  // d = 3: (log |w|^2, |w|^2, 1/|w|^2, |w|) of the scaled node direction
   // w = sigma^j(p1 v1, p2 v2, 1) mapped by A^{-T} (k = u w), index
-  // (((j 2 + [p1 < 0]) 2 + [p2 < 0]) n_v + v2) n_v + v1, as (log |w|^2, |w|^2, 1/|w|^2, 0):
-  // t, log t and 1/t of the h = 0 term follow from u^2, log u^2 and 1/u^2 of the block
-  // (binary64); null otherwise
+  // (((j 2 + [p1 < 0]) 2 + [p2 < 0]) n_v + v2) n_v + v1: t, log t, 1/t and sqrt t of the
+  // h = 0 term follow from u of the block (binary64)
   const double4* dirlw;
   // output slices
   int far_item0, n_far_items, near_item0, n_near_items;

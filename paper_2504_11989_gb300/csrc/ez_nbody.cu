@@ -181,13 +181,46 @@ __device__ __noinline__ void rec_candidates(RC& rc, const ReqDesc* R, const doub
   __syncthreads();
 }
 
+// The direction-table entry of a d = 3 node (null elsewhere) and its block's u: the h = 0
+// term has t = u^2 |w|^2, log t = 2 log u + log |w|^2, 1/t = u^{-2} / |w|^2, sqrt t = u |w|.
+struct NodeDir {
+  const double4* w;  // (log |w|^2, |w|^2, 1/|w|^2, |w|) or null
+  const double* ub;  // the block's (u, u^2, 2 log u, 1/u^2) in shared memory (with w)
+};
+
+// log t, 1/t and sqrt t of a term with t < kT0 for the orders that take their series (every
+// order, or with an order chain those below 1; the chain's recurrence needs 1/t): from the
+// direction table (the h = 0 term of a d = 3 node), else computed where needed
+__device__ __forceinline__ void small_t_aux(const PhiInfo* sphi, int nd, bool chain, double t, const NodeDir& nd0,
+                                            bool h0, double& lt, double& it, double& st) {
+  if (h0 && nd0.w) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(nd0.w));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(nd0.w) + 1);
+    lt = nd0.ub[2] + a.x;
+    it = nd0.ub[3] * b.x;
+    st = nd0.ub[0] * b.y;
+    return;
+  }
+  bool need_lt = false, need_it = chain, need_st = false;
+  for (int j = 0; j < nd; ++j) {
+    const PhiInfo& P = sphi[j];
+    if (chain && !P.below1) continue;
+    need_lt |= P.log_m >= 0 || !P.half;
+    need_it |= P.half && P.log_m < 0 && P.two_a > 0;
+    need_st |= P.half && P.log_m < 0 && (P.two_a & 1);
+  }
+  lt = need_lt ? log(t) : 0.0;
+  it = need_it ? 1.0 / t : 0.0;
+  st = need_st ? sqrt(t) : 0.0;
+}
+
 // h = 0 term near k = 0 (t < kT0) of an order chain (orders a_j = a_0 + (nd-1-j), lowest
 // a_0 < 0), in binary64: the orders a < 1 by their series (log t and 1/t given by the
 // caller), e^{-t} = t Phi_{a_0+1} - a_0 Phi_{a_0} from the two lowest (a sum of positive
 // terms), and every order a >= 1 upward by Phi_a = ((a-1) Phi_{a-1} + e^{-t}) / t, also
 // positive terms.  brk: the series breakpoints (2^-55 FP64 form, 2^-46 mixed form).
 template <int NDM>
-__device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double t, double lt, double it,
+__device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double t, double lt, double it, double st,
                                              const float* const* brk, double (&v)[NDM], unsigned& coefs) {
   double prev = 0.0, E = 0.0;
 #pragma unroll
@@ -197,7 +230,7 @@ __device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double
       double x;
       if (P.below1) {
         int n;
-        x = phi_small_shared(P, t, lt, it, n, brk[j]);
+        x = phi_small_shared(P, t, lt, it, st, n, brk[j]);
         coefs += n;
         if (j == nd - 2) E = fma(t, x, -sphi[nd - 1].a * prev);
       } else {
@@ -212,12 +245,13 @@ __device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double
 // |G + k| <= R, every value binary64.  The cutoff test, the branch and the table interval
 // are taken in binary32 (a term within ~1e-7 relative of the cutoff radius may fall either
 // way: it is below the truncation tolerance by the choice of the radius).
-// lt0, it0: log t and 1/t of the h = 0 term (G = 0) when the caller has them (NaN lt0
-// otherwise).  With an order chain the terms with t < kT0 take the chain (chain_values).
+// nd0: the node's direction-table entry (d = 3; its h = 0 term's log t, 1/t, sqrt t).
+// With an order chain the terms with t < kT0 take the chain (chain_values), log t and 1/t
+// shared by the orders; other orders evaluate their t < kT0 terms one by one (phi_small).
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs,
-                                          unsigned& qterms, const RecCacheF64& rc, double lt0, double it0) {
+                                          unsigned& qterms, const RecCacheF64& rc, const NodeDir& nd0) {
   const bool chain = NDM >= 3 && R->order_chain && sphi[nd - 1].a < 0.0;
   const bool list = rc.n >= 0;
   const int nrec = list ? rc.n : R->n_rec;
@@ -262,18 +296,13 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         ++qterms;
         if (qq > 0.0) {
           const double t = sphi[0].c_lam * qq;
-          double lt = lt0, it = it0;
-          if (!(G.w == 0.0 && lt0 == lt0)) {
-            bool need_lt = false;
-            for (int j = 0; j < nd; ++j) need_lt |= sphi[j].need_lt != 0;
-            lt = need_lt ? log(t) : 0.0;
-            it = 1.0 / t;
-          }
+          double lt, it, st;
+          small_t_aux(sphi, nd, true, t, nd0, G.w == 0.0, lt, it, st);
           const float* brk[NDM];
 #pragma unroll
           for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk;
           double v[NDM];
-          chain_values<NDM>(sphi, nd, t, lt, it, brk, v, coefs);
+          chain_values<NDM>(sphi, nd, t, lt, it, st, brk, v, coefs);
 #pragma unroll
           for (int j = 0; j < NDM; ++j)
             if (j < nd) acc[j] += v[j];
@@ -334,15 +363,31 @@ __device__ __forceinline__ void tails_f(const PhiInfo* sphi, int nd, bool chain,
     }
 }
 
-// the mixed form's use: the values split into float-float and added to hs
+// the mixed form's binary64 near-origin term: the chain, or every order by its series,
+// with log t, 1/t and sqrt t from the direction-table entry w (the h = 0 term of a d = 3
+// node: t = u^2 |w|^2) or computed; the values split into float-float and added to hs.
+// Out of line: it keeps the transcendental code out of the registers of the caller's loop.
 template <int NDM>
-__device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double t, double lt, double it, ff* hs,
-                                             unsigned& coefs) {
-  const float* brk[NDM];
-#pragma unroll
-  for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk_mix;
+__device__ __noinline__ void small_terms_f64(const PhiInfo* sphi, int nd, bool chain, double t, const double4* w,
+                                             const double* ub, ff* hs, unsigned& coefs) {
+  double lt, it, st;
+  const NodeDir nd0{w, ub};
+  small_t_aux(sphi, nd, chain, t, nd0, w != nullptr, lt, it, st);
   double v[NDM];
-  chain_values<NDM>(sphi, nd, t, lt, it, brk, v, coefs);
+  if (chain) {
+    const float* brk[NDM];
+#pragma unroll
+    for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk_mix;
+    chain_values<NDM>(sphi, nd, t, lt, it, st, brk, v, coefs);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NDM; ++j)
+      if (j < nd) {
+        int n;
+        v[j] = phi_small_shared(sphi[j], t, lt, it, st, n, sphi[j].ser_brk_mix);
+        coefs += n;
+      }
+  }
 #pragma unroll
   for (int j = 0; j < NDM; ++j)
     if (j < nd) {
@@ -362,12 +407,11 @@ __device__ __noinline__ void small_chain_f64(const PhiInfo* sphi, int nd, double
 // The list is sorted by |G|: once |G| > sqrt(t_mix / c) + |k|, every remaining term is a
 // binary32 tail, evaluated by a short loop that skips the points beyond the cutoff.  Tails
 // are summed in binary32, the middle range with Kahan compensation, heads in float-float.
-// t0, lt0, it0: t, log t and 1/t of the h = 0 term (G = 0) when the caller has them (t0 = 0
-// otherwise).
+// nd0: the node's direction-table entry (d = 3): t, log t, 1/t and sqrt t of its h = 0 term.
 template <int D, int NDM>
 __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo* sphi, int nd, const ff* kff,
                                                 ff* A, unsigned& terms, unsigned& coefs, const RecCacheMix& rc,
-                                                double t0, double lt0, double it0) {
+                                                const NodeDir& nd0) {
   const int nrec = rc.n;
   const float R2f = R->R2f, cf = R->c_lam_f;
   const float tmix = sphi[0].t_mix_f, tmid = sphi[0].t_mid_f;
@@ -377,6 +421,11 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
   const float4* recf = R->recf;
   const float4* reclo = R->reclo;
   const bool chain = NDM >= 3 && R->order_chain;
+  // binary64 near-origin terms: the order chain, or (a log-case or real order) every order
+  // by its series with log t shared; else each order on its own (phi_eval_qq)
+  const bool chain64 = chain && sphi[nd - 1].a < 0.0;
+  bool shared = chain64;
+  for (int j = 0; j < nd; ++j) shared |= sphi[j].log_m >= 0 || !sphi[j].half;
   float kf[3] = {0.0f, 0.0f, 0.0f}, klo[3] = {0.0f, 0.0f, 0.0f}, kn2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -423,9 +472,10 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
     // binary64: the incomplete gamma near the origin (t < kT0, the h = 0 term near k = 0:
     // entire series plus singular part, as in the FP64 form), t = 0, and beyond the table
     if (tf < (float)kT0 || tf > t_hi) {
-      if (chain && tf < (float)kT0 && Gf.w == 0.0f && t0 > 0.0 && sphi[nd - 1].a < 0.0) {
+      if (shared && tf < (float)kT0 && Gf.w == 0.0f && nd0.w) {  // the h = 0 term from the direction table
         ++terms;
-        small_chain_f64<NDM>(sphi, nd, t0, lt0, it0, hs, coefs);
+        const double t0 = nd0.ub[1] * __ldg(reinterpret_cast<const double*>(nd0.w) + 1);
+        small_terms_f64<NDM>(sphi, nd, chain64, t0, nd0.w, nd0.ub, hs, coefs);
         continue;
       }
       const G4 G = ldg_g4(R->rec + (h < kRecCache ? rc.idx[h] : h));
@@ -440,11 +490,8 @@ __device__ __forceinline__ void recip_sum_mixed(const ReqDesc* R, const PhiInfo*
         qq = fma(q2, q2, qq);
       }
       ++terms;
-      if (chain && tf < (float)kT0 && qq > 0.0 && sphi[nd - 1].a < 0.0) {
-        const double t = sphi[0].c_lam * qq;
-        bool need_lt = false;
-        for (int j = 0; j < nd; ++j) need_lt |= sphi[j].need_lt != 0;
-        small_chain_f64<NDM>(sphi, nd, t, need_lt ? log(t) : 0.0, 1.0 / t, hs, coefs);
+      if (shared && tf < (float)kT0 && qq > 0.0) {
+        small_terms_f64<NDM>(sphi, nd, chain64, sphi[0].c_lam * qq, nullptr, nullptr, hs, coefs);
         continue;
       }
 #pragma unroll
@@ -817,6 +864,15 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
                         (size_t)(j * R->n_ui + it.iu - R->hg_lo) * R->hslot;
     for (int e = threadIdx.x; e < nd * nH; e += blockDim.x) H4[e] = __ldg(src + e);
   }
+  // (u, u^2, 2 log u, 1/u^2) of the block: the h = 0 term's t, log t, 1/t, sqrt t with the
+  // direction table
+  __shared__ double s_ublk[4];
+  if (threadIdx.x == 0) {
+    s_ublk[0] = u;
+    s_ublk[1] = u * u;
+    s_ublk[2] = R->dirlw ? 2.0 * log(u) : 0.0;
+    s_ublk[3] = 1.0 / (u * u);
+  }
   for (int v1 = threadIdx.x; v1 < nv; v1 += blockDim.x) {
     double sn, cs;
     sincospi(2.0 * (u * R->v_nodes[v1]), &sn, &cs);
@@ -946,9 +1002,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
     }
     double wsum[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0}, wneg[EZ_MAX_PROD] = {0.0, 0.0, 0.0, 0.0};
     if constexpr (MIXED) {
-      // log u^2 and 1/u^2 of the block for the h = 0 term's log t and 1/t (binary64)
       const double4* dirlw = R->dirlw;
-      const double u2 = u * u, lu2 = dirlw ? 2.0 * log(u) : 0.0, iu2 = dirlw ? 1.0 / u2 : 0.0;
       ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       ff wn[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
       const int ma_hp = min(Ma + 1, R->m_hp[ax_a]);
@@ -1006,16 +1060,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
           ff k[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i) k[i] = ff_add(kb[i], ka[i]);
-          double t0 = 0.0, lt0 = 0.0, it0 = 0.0;
-          if (dirlw) {
-            const double4* dp = dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1;
-            const double2 a = __ldg(reinterpret_cast<const double2*>(dp));
-            const double b = __ldg(reinterpret_cast<const double*>(dp) + 2);
-            t0 = u2 * a.y;
-            lt0 = lu2 + a.x;
-            it0 = iu2 * b;
-          }
-          recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, t0, lt0, it0);
+          const NodeDir nd0{dirlw ? dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1 : nullptr,
+                            s_ublk};
+          recip_sum_mixed<3, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, nd0);
           assemble_mixed<NDM>(R, nd, np, Zp, A, w, ws);
 #pragma unroll
           for (int i = 0; i < 3; ++i) ka[i] = ff{-ka[i].hi, -ka[i].lo};
@@ -1040,9 +1087,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
       }
     } else {
       const double2* Bs = B + s2 * nBs;
-      // log u^2 and 1/u^2 of the block for the h = 0 term's log t and 1/t
       const double4* dirlw = R->dirlw;
-      const double lu2 = dirlw ? 2.0 * log(u) : 0.0, iu2 = dirlw ? 1.0 / (u * u) : 0.0;
       for (int n = threadIdx.x; n < nn; n += blockDim.x) {
         const int v2l = n / nv, v1 = n - v2l * nv;
         const double kta = u * R->v_nodes[v1];
@@ -1080,13 +1125,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn) acc[jn] = 0.0;
           const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-          double lt0 = __longlong_as_double(0x7ff8000000000000LL), it0 = 0.0;
-          if (dirlw) {
-            const double4* dp = dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1;
-            lt0 = lu2 + __ldg(reinterpret_cast<const double*>(dp));
-            it0 = iu2 * __ldg(reinterpret_cast<const double*>(dp) + 2);
-          }
-          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, lt0, it0);
+          const NodeDir nd0{dirlw ? dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1 : nullptr,
+                            s_ublk};
+          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, nd0);
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) Z[jn] = R->pref[jn] * (Zp[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1207,7 +1248,7 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
           const float4 h0 = H4[jn * (Ma + 1)];
           Zr[jn] = ff_add(ff{2.0f * S.hi, 2.0f * S.lo}, ff{h0.x, h0.y});
         }
-      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, 0.0, 0.0, 0.0);
+      recip_sum_mixed<2, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, NodeDir{nullptr, nullptr});
       assemble_mixed<NDM>(R, nd, np, Zr, A, ff{wv.x, wv.y}, ws);
     }
 #pragma unroll
@@ -1237,8 +1278,7 @@ __device__ __forceinline__ void far_d2_body(const ReqDesc* __restrict__ reqs, co
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = fma(2.0, sr[jn], H[jn * (Ma + 1)].x);
     const float kf[2] = {(float)k[0], (float)k[1]};
-    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache,
-                      __longlong_as_double(0x7ff8000000000000LL), 0.0);
+    recip_sum<2, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, NodeDir{nullptr, nullptr});
 #pragma unroll
     for (int jn = 0; jn < NDM; ++jn)
       if (jn < nd) Z[jn] = R->pref[jn] * (Z[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
@@ -1301,7 +1341,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
         const ff S = ff_two_sum(s[jn], c[jn]);
         Zr[jn] = ff{2.0f * S.hi, 2.0f * S.lo};
       }
-    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, 0.0, 0.0, 0.0);
+    recip_sum_mixed<1, NDM>(R, sphi, nd, k, A, terms, coefs, rcache, NodeDir{nullptr, nullptr});
     ff ws[EZ_MAX_PROD] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     assemble_mixed<NDM>(R, nd, np, Zr, A, ffd(w), ws);
 #pragma unroll
@@ -1319,8 +1359,7 @@ __global__ void __launch_bounds__(128) far_kernel_d1(const ReqDesc* __restrict__
       if (jn < nd) sr[jn] = fma(R->gbox[(size_t)jn * R->box[0] + M + m], ex, sr[jn]);
   }
   const float kf[1] = {(float)k[0]};
-  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache,
-                    __longlong_as_double(0x7ff8000000000000LL), 0.0);
+  recip_sum<1, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, NodeDir{nullptr, nullptr});
 #pragma unroll
   for (int jn = 0; jn < NDM; ++jn)
     if (jn < nd) Z[jn] = R->pref[jn] * (2.0 * sr[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);

@@ -230,11 +230,11 @@ static __device__ __noinline__ double phi_small(const PhiInfo& P, double t) {
   return s + P.gam * (P.half ? pow_half(t, P.two_a) : exp(-P.a * log(t)));
 }
 
-// t < kT0, binary64, with log t (log-case and non-half-integer orders) and 1/t supplied by the caller, who
-// shares them between the orders of one reciprocal term: the entire series cut at 2^-55
-// plus the singular part.  n_used: series terms (work count).
-__device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, int& n_used,
-                                                   const float* brk) {
+// t < kT0, binary64, with log t (log-case and non-half-integer orders), 1/t and sqrt t
+// supplied by the caller, who shares them between the orders of one reciprocal term: the
+// entire series cut at the breakpoints brk plus the singular part.  n_used: series terms.
+__device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, double lt, double it, double st,
+                                                   int& n_used, const float* brk) {
   const float tf = (float)t;
   int N = 4;
 #pragma unroll
@@ -250,7 +250,7 @@ __device__ __forceinline__ double phi_small_shared(const PhiInfo& P, double t, d
   }
   if (!P.half) return s + P.gam * exp(-P.a * lt);  // non-half-integer order (lt = log t)
   const int e = -P.two_a;  // t^{-a} = sqrt(t)^e
-  double r = (e & 1) ? sqrt(t) : 1.0;
+  double r = (e & 1) ? st : 1.0;
   const int k = e >> 1;  // floor(e / 2)
   const double b = k < 0 ? it : t;
   for (int q = 0; q < (k < 0 ? -k : k); ++q) r *= b;

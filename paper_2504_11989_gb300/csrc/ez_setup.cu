@@ -522,10 +522,11 @@ __global__ void phase_kernel(const PhaseJob* jobs) {
   }
 }
 
-// d = 3 with an order chain: (log |w|^2, |w|^2, 1/|w|^2) of every scaled node direction
+// d = 3: (log |w|^2, |w|^2, 1/|w|^2, |w|) of every scaled node direction
 // w = p1 v1 A^{-T} e_a + p2 v2 A^{-T} e_b + A^{-T} e_c (axes a = j, b = j + 1, c = j + 2 mod 3,
-// scaled by sqrt(pi) lam), so that the far kernel gets t = u^2 |w|^2, log t = 2 log u +
-// log |w|^2 and 1/t = u^{-2} / |w|^2 of the h = 0 term without a logarithm or a division.
+// scaled by sqrt(pi) lam), so that the far kernels get t = u^2 |w|^2, log t = 2 log u +
+// log |w|^2, 1/t = u^{-2} / |w|^2 and sqrt t = u |w| of the h = 0 term without a logarithm,
+// a division or a square root per node.
 __global__ void dirlw_kernel(const ReqDesc* reqs) {
   const ReqDesc* R = reqs + blockIdx.y;
   if (!R->dirlw) return;
@@ -547,7 +548,7 @@ __global__ void dirlw_kernel(const ReqDesc* reqs) {
     const double wc = fma(R->AiTs[c * 3 + ax_a], a, fma(R->AiTs[c * 3 + ax_b], b, R->AiTs[c * 3 + ax_c]));
     w2 = fma(wc, wc, w2);
   }
-  const_cast<double4*>(R->dirlw)[i] = make_double4(log(w2), w2, 1.0 / w2, 0.0);
+  const_cast<double4*>(R->dirlw)[i] = make_double4(log(w2), w2, 1.0 / w2, sqrt(w2));
 }
 
 }  // namespace ez
