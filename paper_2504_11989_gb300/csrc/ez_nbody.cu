@@ -310,6 +310,42 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         }
         have_qq = true;
       }
+      if (chain && tf >= (float)kT0 && tf <= sphi[0].t_hi_f) {
+        // the two lowest orders from their tables, e^{-t} = t Phi_{a0+1} - a0 Phi_{a0} from them
+        // (positive terms, a0 < 0) and every higher order upward by Phi_a = ((a-1) Phi_{a-1} +
+        // e^{-t}) / t, also positive terms: half the table records per term.  Where both
+        // records are constants (Phi below the table floor) every order takes its constant.
+        const int i = min(phi_interval(tf, sphi[0].t_geo_end_f), sphi[0].n_int - 1);
+        const double* r0 = sphi[nd - 1].tab + (size_t)i * kRec;
+        const double* r1 = sphi[nd - 2].tab + (size_t)i * kRec;
+        const double2 so0 = __ldg(reinterpret_cast<const double2*>(r0));
+        const double2 so1 = __ldg(reinterpret_cast<const double2*>(r1));
+        const bool c0 = __double2loint(so0.x) == 1, c1 = __double2loint(so1.x) == 1;
+        if (!(c0 && c1)) {
+          const G4 G = ldg_g4(rec + h);
+          qq = fma(k2v[0], G.x, G.w + kk2);
+          if (D >= 2) qq = fma(k2v[1], G.y, qq);
+          if (D >= 3) qq = fma(k2v[2], G.z, qq);
+          ++qterms;
+          const double t = sphi[0].c_lam * qq;
+          int n0 = 0, n1 = 0;
+          const double v0 = c0 ? __ldg(r0 + 4) : phi_poly(r0, fma(qq, so0.y, __ldg(r0 + 2)), n0);
+          const double v1 = c1 ? __ldg(r1 + 4) : phi_poly(r1, fma(qq, so1.y, __ldg(r1 + 2)), n1);
+          coefs += n0 + n1;
+          acc[nd - 1] += v0;
+          acc[nd - 2] += v1;
+          const double E = fma(t, v1, -sphi[nd - 1].a * v0);
+          const double it = 1.0 / t;
+          double prev = v1;
+#pragma unroll
+          for (int j = NDM - 3; j >= 0; --j)
+            if (j <= nd - 3) {
+              prev = fma(sphi[j + 1].a, prev, E) * it;
+              acc[j] += prev;
+            }
+          continue;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < NDM; ++j)
         if (j < nd) {
