@@ -209,7 +209,9 @@ int ez_lattice_sums(int n_req, const ez_lattice* lats, const ez_sum_spec* specs,
 /* A batch keeps the plans of n_req sums and the device memory of all their tables
  * and partial sums resident.  ez_batch_create plans, allocates (cudaMalloc and
  * pinned host staging, owned by the batch) and uploads the descriptors on
- * `stream`.  ez_batch_run launches every kernel of the path and writes
+ * `stream`; it also creates a second CUDA stream and two events of its own, on which
+ * the near part's setup of each run overlaps the rest of the setup (every run stays
+ * ordered on the caller's stream; without them everything runs on it).  ez_batch_run launches every kernel of the path and writes
  * out[r*EZ_MAX_PROD + p] (host or device; with host memory
  * the call synchronises `stream`, with device memory it is asynchronous).
  * ez_batch_lines copies the per-line partial sums of the last run (layout as in

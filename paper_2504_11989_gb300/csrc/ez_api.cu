@@ -993,6 +993,9 @@ struct ez_batch_s {
   bool lines_fresh = false;  // the lines buffer holds the last run's lines
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, far begin, far end, end
+  // owning batches: a second stream for the setup work that does not feed the far kernels
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace {
@@ -1526,6 +1529,37 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
   for (auto& p : B.plans) max_cells = std::max(max_cells, p.cells * p.spec.n_distinct);
   gbox_kernel<<<dim3((unsigned)((max_cells + 255) / 256), B.n_req), 256, 0, stream>>>(dreqs, (const GboxJob*)dptr(B.o_gj), B.n_req);
   EZ_LAUNCHED();
+  // the near part's Taylor tensors (after the box and the tables) run on the batch's second
+  // stream while the main stream builds H and the direction table; joined before the far
+  // kernels (whose timing window stays free of them)
+  const bool fork = B.aux && B.n_tay;
+  cudaStream_t ts = fork ? B.aux : stream;
+  if (fork) {
+    EZ_CUDA(cudaEventRecord(B.fork_ev, stream));
+    EZ_CUDA(cudaStreamWaitEvent(B.aux, B.fork_ev, 0));
+  }
+  if (B.n_tay) {
+    long long max_rec = 0;
+    for (auto& p : B.plans)
+      if (p.near) max_rec = std::max(max_rec, p.rcap);
+    phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, ts>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
+    EZ_LAUNCHED();
+    int max_alpha = 0;
+    long long max_chunk = 0;
+    for (auto& p : B.plans)
+      if (p.near) {
+        max_alpha = std::max(max_alpha, (int)(p.alpha.size() / 3));
+        max_chunk = std::max(max_chunk, taylor_chunks(p));
+      }
+    if (max_chunk > 0) {
+      taylor_real_kernel<<<dim3((unsigned)max_chunk, B.n_tay), 128, 0, ts>>>(dreqs, (const TaylorJob*)dptr(B.o_tj),
+                                                                                  B.n_tay);
+      EZ_LAUNCHED();
+    }
+    taylor_kernel<<<dim3(max_alpha, B.n_tay), 128, 0, ts>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
+    EZ_LAUNCHED();
+  }
+  if (fork) EZ_CUDA(cudaEventRecord(B.join_ev, B.aux));
   {
     long long max_groups = 0;
     int max_tasks = 0;
@@ -1551,32 +1585,12 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
       EZ_LAUNCHED();
     }
   }
-  if (B.n_tay) {
-    long long max_rec = 0;
-    for (auto& p : B.plans)
-      if (p.near) max_rec = std::max(max_rec, p.rcap);
-    phiseq_kernel<<<dim3((unsigned)((max_rec + 127) / 128), B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
-    EZ_LAUNCHED();
-    int max_alpha = 0;
-    long long max_chunk = 0;
-    for (auto& p : B.plans)
-      if (p.near) {
-        max_alpha = std::max(max_alpha, (int)(p.alpha.size() / 3));
-        max_chunk = std::max(max_chunk, taylor_chunks(p));
-      }
-    if (max_chunk > 0) {
-      taylor_real_kernel<<<dim3((unsigned)max_chunk, B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj),
-                                                                                  B.n_tay);
-      EZ_LAUNCHED();
-    }
-    taylor_kernel<<<dim3(max_alpha, B.n_tay), 128, 0, stream>>>(dreqs, (const TaylorJob*)dptr(B.o_tj), B.n_tay);
-    EZ_LAUNCHED();
-  }
   if (B.n_phase) {
     phase_kernel<<<dim3((unsigned)((B.max_phase_pairs + 127) / 128), B.n_phase), 128, 0, stream>>>(
         (const PhaseJob*)dptr(B.o_phj));
     EZ_LAUNCHED();
   }
+  if (fork) EZ_CUDA(cudaStreamWaitEvent(stream, B.join_ev, 0));
   Item* ditems = (Item*)dptr(B.o_items);
   double* dseg = (double*)dptr(B.o_seg);
   if (B.timing) EZ_CUDA(cudaEventRecord(B.ev[1], stream));
@@ -1637,6 +1651,17 @@ extern "C" int ez_batch_create(int n_req, const ez_lattice* lats, const ez_sum_s
       rc = fail(EZ_ENOMEM, "pinned allocation of %zu bytes failed", B->hbytes);
     }
     B->owns = true;
+    // the second stream (optional: without it every kernel runs on the caller's stream)
+    if (cudaStreamCreateWithFlags(&B->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (B->aux) cudaStreamDestroy(B->aux);
+      if (B->fork_ev) cudaEventDestroy(B->fork_ev);
+      if (B->join_ev) cudaEventDestroy(B->join_ev);
+      B->aux = nullptr;
+      B->fork_ev = B->join_ev = nullptr;
+    }
   }
   if (!rc) rc = batch_layout(*B, true);
   if (!rc) {
@@ -1755,6 +1780,12 @@ extern "C" int ez_batch_destroy(ez_batch B) {
   if (!B) return EZ_OK;
   for (int i = 0; i < 4; ++i)
     if (B->ev[i]) cudaEventDestroy(B->ev[i]);
+  if (B->aux) {
+    cudaStreamSynchronize(B->aux);
+    cudaStreamDestroy(B->aux);
+  }
+  if (B->fork_ev) cudaEventDestroy(B->fork_ev);
+  if (B->join_ev) cudaEventDestroy(B->join_ev);
   if (B->owns) {
     if (B->d) cudaFree(B->d);
     if (B->h) cudaFreeHost(B->h);
