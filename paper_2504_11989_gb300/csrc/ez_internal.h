@@ -82,6 +82,8 @@ constexpr int kMaxD = 3;    // lattice sums (Duffy nodes, near part, serving)
 constexpr int kMaxDnd = 6;  // the Epstein zeta function alone (any dimension up to this)
 constexpr int kMaxFactor = 64;
 constexpr int kNearMaxDeg = 64;  // u^2 degree of products in the near part
+constexpr int kNearPowE = 8;      // near part: powers C^r tabulated per ray up to this r
+constexpr int kNearPowCache = 96; // ... in at most this many coefficients (else products factor by factor)
 constexpr int kMaxEll = 8;       // largest Taylor order parameter ell of the near part
 constexpr int kInvIntHalf = 256; // near part: table of 1/n for |n| <= kInvIntHalf
 constexpr int kVChunkMin = 8;   // d = 3: fewest v2 rows per far-field block

@@ -1484,7 +1484,8 @@ __device__ __forceinline__ double ntaylor(const ReqDesc* R, int jn, int ia, doub
 
 // sig_w[j] = sigma_j |w|^{nu_j - d} / V (per ray, shared by every product and subset)
 template <typename N>
-__device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], const N* sig_w, N L) {
+__device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], const N* sig_w, N L, const N* PW,
+                         const int (*pw_off)[kNearPowE + 1]) {
   const int nd = R->n_distinct, d = R->d, ell = R->ell;
   int e[EZ_MAX_NU], t[EZ_MAX_NU];
   for (int j = 0; j < nd; ++j) {
@@ -1513,17 +1514,44 @@ __device__ N near_product(const ReqDesc* R, int p, const N (*C)[kMaxEll + 1], co
     }
     int deg = 0;
     G[0] = nint<N>(1);
-    for (int j = 0; j < nd; ++j)
-      for (int r = 0; r < e[j] - t[j]; ++r) {
-        const int nd2 = min(deg + ell, kNearMaxDeg);
+    if (PW) {  // products of the tabulated powers C_j^r (one convolution per further factor j)
+      deg = -1;
+      for (int j = 0; j < nd; ++j) {
+        const int r = e[j] - t[j];
+        if (r == 0) continue;
+        const N* src = r == 1 ? C[j] : PW + pw_off[j][r];
+        const int sdeg = min(ell * r, kNearMaxDeg);
+        if (deg < 0) {
+          for (int i = 0; i <= sdeg; ++i) G[i] = src[i];
+          deg = sdeg;
+          continue;
+        }
+        const int nd2 = min(deg + sdeg, kNearMaxDeg);
         for (int i = 0; i <= nd2; ++i) {
           N s = nint<N>(0);
-          for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = nfma(G[q], C[j][i - q], s);
+          for (int q = max(0, i - sdeg); q <= min(i, deg); ++q) s = nfma(G[q], src[i - q], s);
           T[i] = s;
         }
         deg = nd2;
         for (int i = 0; i <= deg; ++i) G[i] = T[i];
       }
+      if (deg < 0) {
+        G[0] = nint<N>(1);
+        deg = 0;
+      }
+    } else {
+      for (int j = 0; j < nd; ++j)
+        for (int r = 0; r < e[j] - t[j]; ++r) {
+          const int nd2 = min(deg + ell, kNearMaxDeg);
+          for (int i = 0; i <= nd2; ++i) {
+            N s = nint<N>(0);
+            for (int q = max(0, i - ell); q <= min(i, deg); ++q) s = nfma(G[q], C[j][i - q], s);
+            T[i] = s;
+          }
+          deg = nd2;
+          for (int i = 0; i <= deg; ++i) G[i] = T[i];
+        }
+    }
     N sumk = nint<N>(0);
     if (R->hadw) {  // integer mu: tabulated coefficients of the weight's polynomial in L
       const int m1 = R->hadw_m1;
@@ -1585,7 +1613,36 @@ __device__ void near_core(const ReqDesc* R, const N* wN, N L, const N* sig_w, do
       const N mono = pw[0][al[0]] * pw[1][al[1]] * pw[2][al[2]];
       for (int jn = 0; jn < nd; ++jn) C[jn][kk] = nfma(ntaylor(R, jn, ia, mono), mono, C[jn][kk]);
     }
-  for (int p = 0; p < np; ++p) val[p] = scale * nto(near_product<N>(R, p, C, sig_w, L));
+  // powers C_j^r, 2 <= r <= max over the products of e_pj, tabulated once per ray when they fit
+  N PW[kNearPowCache];
+  int pw_off[EZ_MAX_NU][kNearPowE + 1];
+  bool use_pw = true;
+  int used = 0;
+  for (int jn = 0; jn < nd && use_pw; ++jn) {
+    int emax = 0;
+    for (int p = 0; p < np; ++p) emax = max(emax, R->expo[p][jn]);
+    if (emax > kNearPowE) {
+      use_pw = false;
+      break;
+    }
+    for (int r = 2; r <= emax; ++r) {
+      const int dg = min(ell * r, kNearMaxDeg), dp = min(ell * (r - 1), kNearMaxDeg);
+      if (used + dg + 1 > kNearPowCache) {
+        use_pw = false;
+        break;
+      }
+      const N* prev = r == 2 ? C[jn] : PW + pw_off[jn][r - 1];
+      N* dst = PW + used;
+      for (int i = 0; i <= dg; ++i) {  // C^r = C^{r-1} C, truncated at kNearMaxDeg
+        N sv = nint<N>(0);
+        for (int q = max(0, i - ell); q <= min(i, dp); ++q) sv = nfma(prev[q], C[jn][i - q], sv);
+        dst[i] = sv;
+      }
+      pw_off[jn][r] = used;
+      used += dg + 1;
+    }
+  }
+  for (int p = 0; p < np; ++p) val[p] = scale * nto(near_product<N>(R, p, C, sig_w, L, use_pw ? PW : nullptr, pw_off));
 }
 
 // per-ray inputs in binary64 (both forms)
