@@ -2188,8 +2188,15 @@ static int epstein_nd(const ez_lattice_s* L, double nu, const double* x, const d
   PhiInfo phi;
   fill_phi_host(phi, 0.5 * (d - nu), kTcut);
   phi.c_lam = 1.0;
+  // per-thread phase tables in shared memory: every offset, or above 1 KB per thread (64
+  // entries: d = 6 boxes) the non-negative ones only, which doubles the resident warps
   int phase_len = 0;
   for (int i = 0; i < d; ++i) phase_len += 2 * Mr[i] + 1;
+  const bool half_phases = phase_len > 64;
+  if (half_phases) {
+    phase_len = 0;
+    for (int i = 0; i < d; ++i) phase_len += Mr[i] + 1;
+  }
   unsigned threads = 128;
   while (threads > 32 && (size_t)phase_len * 16 * threads > (size_t)220 * 1024) threads /= 2;
   const size_t smem = (size_t)phase_len * 16 * threads;
@@ -2281,6 +2288,7 @@ static int epstein_nd(const ez_lattice_s* L, double nu, const double* x, const d
   A.x_zero = x_zero ? 1 : 0;
   A.x_in_lattice = x_in ? 1 : 0;
   A.phase_len = phase_len;
+  A.half_phases = half_phases ? 1 : 0;
   A.rows = JR.rows;
   A.rcounts = JR.counts;
   A.g = JR.out;

@@ -9,7 +9,8 @@
 // lattice axis (nd_rows_kernel: the range of each row from the quadratic |z - x|^2 <= r^2,
 // nd_scan_kernel: offsets in one deterministic order, nd_fill_kernel: the g values).  Per y the
 // sum is contracted axis by axis over the rows: the row sums take the last axis' phases from a
-// per-thread table in shared memory, and a row whose prefix differs from the previous one at
+// per-thread table in shared memory (for large boxes the non-negative offsets only, the others
+// as conjugates), and a row whose prefix differs from the previous one at
 // axis l closes the partial sums of axes d-2 .. l, each multiplied by its axis' phase (a nested
 // Horner scheme over the ball, one complex product per closed level).
 // Reciprocal space (a different ball for every y): enumerated per thread by the Fincke-Pohst
@@ -266,7 +267,7 @@ __device__ __forceinline__ void fp_level(const NdEpsteinArgs& P, const double (&
 
 // one thread per y; phase tables of the d axes in shared memory, entry e of thread tid at
 // [e * blockDim + tid]
-template <int D>
+template <int D, bool HALF>
 __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
   extern __shared__ double2 sph[];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,7 +283,9 @@ __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
     for (int q = 0; q < D; ++q) s = fma(P.At[c * D + q], y[q], s);
     yt[c] = s - rint(s);
   }
-  // phases e^{-2 pi i yt_c (k - M_c)}, k in [0, 2 M_c]
+  // phases e^{-2 pi i yt_c o} of the offsets o = k - M_c: all of [-M_c, M_c], or (HALF, for
+  // large boxes) [0, M_c] only, a negative offset taking the conjugate of -o (half the shared
+  // memory per thread, twice the resident warps)
   int base[D];
   {
     int b = 0;
@@ -290,19 +293,27 @@ __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
     for (int c = 0; c < D; ++c) {
       base[c] = b;
       const int Mc = P.M[c];
+      const int z = HALF ? 0 : Mc;  // slot of offset 0
       double sn, cs;
       sincospi(-2.0 * yt[c], &sn, &cs);
       const double2 e1 = make_double2(cs, sn);
       double2 e = make_double2(1.0, 0.0);
-      sph[(size_t)(b + Mc) * nt + tid] = e;
+      sph[(size_t)(b + z) * nt + tid] = e;
       for (int k = 1; k <= Mc; ++k) {
         e = cmul2(e, e1);
-        sph[(size_t)(b + Mc + k) * nt + tid] = e;
-        sph[(size_t)(b + Mc - k) * nt + tid] = make_double2(e.x, -e.y);
+        sph[(size_t)(b + z + k) * nt + tid] = e;
+        if (!HALF) sph[(size_t)(b + z - k) * nt + tid] = make_double2(e.x, -e.y);
       }
-      b += 2 * Mc + 1;
+      b += HALF ? Mc + 1 : 2 * Mc + 1;
     }
   }
+  // phase of box index k (offset k - M_c) on axis c
+  auto phase = [&](int c, int k) {
+    if (!HALF) return sph[(size_t)(base[c] + k) * nt + tid];
+    const int o = k - P.M[c];
+    const double2 e = sph[(size_t)(base[c] + (o >= 0 ? o : -o)) * nt + tid];
+    return o >= 0 ? e : make_double2(e.x, -e.y);
+  };
   // ---- real space over the rows
   static_assert(D >= 2, "rows need a prefix axis");
   double2 acc[D - 1];
@@ -321,8 +332,7 @@ __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
       if (l >= lev) {
         const double2 v = l == D - 2 ? rs : acc[l];
         if (l < D - 2) acc[l] = make_double2(0.0, 0.0);
-        const double2 e = sph[(size_t)(base[l] + pidx[l]) * nt + tid];
-        const double2 cv = cmul2(v, e);
+        const double2 cv = cmul2(v, phase(l, pidx[l]));
         if (l > 0) {
           acc[l - 1].x += cv.x;
           acc[l - 1].y += cv.y;
@@ -340,13 +350,31 @@ __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
     for (int l = 0; l < D - 1; ++l) pidx[l] = (R.z >> (6 * l)) & 63;
     const int k0 = R.y & 0xffff, n = R.y >> 16;
     const double* g = P.g + R.x;
-    const double2* ph = sph + (size_t)(base[D - 1] + k0) * nt + tid;
     double sr = 0.0, si = 0.0;
-    for (int k = 0; k < n; ++k) {
-      const double gv = __ldg(g + k);
-      const double2 e = ph[(size_t)k * nt];
-      sr = fma(gv, e.x, sr);
-      si = fma(gv, e.y, si);
+    if constexpr (HALF) {
+      const int Ml = P.M[D - 1];
+      const double2* ph = sph + (size_t)base[D - 1] * nt + tid;
+      int k = 0;
+      for (; k < n && k0 + k < Ml; ++k) {  // negative offsets: conjugates
+        const double gv = __ldg(g + k);
+        const double2 e = ph[(size_t)(Ml - k0 - k) * nt];
+        sr = fma(gv, e.x, sr);
+        si = fma(-gv, e.y, si);
+      }
+      for (; k < n; ++k) {
+        const double gv = __ldg(g + k);
+        const double2 e = ph[(size_t)(k0 + k - Ml) * nt];
+        sr = fma(gv, e.x, sr);
+        si = fma(gv, e.y, si);
+      }
+    } else {
+      const double2* ph = sph + (size_t)(base[D - 1] + k0) * nt + tid;
+      for (int k = 0; k < n; ++k) {
+        const double gv = __ldg(g + k);
+        const double2 e = ph[(size_t)k * nt];
+        sr = fma(gv, e.x, sr);
+        si = fma(gv, e.y, si);
+      }
     }
     rs = make_double2(sr, si);
   }
@@ -389,17 +417,21 @@ __global__ void __launch_bounds__(128) epstein_nd_kernel(NdEpsteinArgs P) {
 
 cudaError_t launch_epstein_nd(const NdEpsteinArgs& a, unsigned threads, size_t smem, cudaStream_t st) {
   const unsigned grid = (unsigned)((a.m + threads - 1) / threads);
-  switch (a.d) {
-#define EZ_ND_CASE(DD)                                                                              \
-  case DD: {                                                                                        \
-    cudaError_t e = cudaFuncSetAttribute(epstein_nd_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  switch (a.d * 2 + (a.half_phases ? 1 : 0)) {
+#define EZ_ND_CASE(DD, HH)                                                                          \
+  case DD * 2 + HH: {                                                                               \
+    cudaError_t e = cudaFuncSetAttribute(epstein_nd_kernel<DD, HH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                \
     if (e != cudaSuccess) return e;                                                                 \
-    epstein_nd_kernel<DD><<<grid, threads, smem, st>>>(a);                                          \
+    epstein_nd_kernel<DD, HH><<<grid, threads, smem, st>>>(a);                                      \
     return cudaGetLastError();                                                                      \
   }
-    EZ_ND_CASE(4)
-    EZ_ND_CASE(5)
-    EZ_ND_CASE(6)
+    EZ_ND_CASE(4, 0)
+    EZ_ND_CASE(4, 1)
+    EZ_ND_CASE(5, 0)
+    EZ_ND_CASE(5, 1)
+    EZ_ND_CASE(6, 0)
+    EZ_ND_CASE(6, 1)
 #undef EZ_ND_CASE
     default:
       return cudaErrorInvalidValue;

@@ -140,7 +140,9 @@ struct NdEpsteinArgs {
   double xt[kMaxDnd];            // A^{-1} x
   int x_zero, x_in_lattice;
   int M[kMaxDnd], mx[kMaxDnd];   // real-space box mx - M + [0, 2 M]
-  int phase_len;                 // sum_l (2 M_l + 1): per-thread phase entries in shared memory
+  int phase_len;                 // per-thread phase entries in shared memory: sum_l (2 M_l + 1),
+                                 // or sum_l (M_l + 1) with half_phases
+  int half_phases;               // tables of the non-negative offsets only (large boxes)
   const int4* rows;
   const int* rcounts;  // [0]: real-space rows
   const double* g;
