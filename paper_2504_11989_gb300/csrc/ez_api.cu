@@ -1560,20 +1560,20 @@ int batch_launch(ez_batch_s& B, cudaStream_t stream) {
     EZ_LAUNCHED();
   }
   if (fork) EZ_CUDA(cudaEventRecord(B.join_ev, B.aux));
-  {
-    long long max_groups = 0;
-    int max_tasks = 0;
+  {  // H of every line group: column chunks (jn, ma, mb >= 0) x axes x requests
+    long long max_cols = 0;
+    bool mixed_any = false, f64_any = false;
     for (auto& p : B.plans)
-      if (p.d == 3) {
-        max_groups = std::max(max_groups, p.line_hi - p.line_lo);
+      if (p.d == 3 && p.line_hi > p.line_lo) {
         int Mx = 0;
         for (int i = 0; i < 3; ++i) Mx = std::max(Mx, p.M[i]);
-        max_tasks = std::max(max_tasks, p.spec.n_distinct * (Mx + 1) * (Mx + 1));
+        max_cols = std::max(max_cols, (long long)p.spec.n_distinct * (Mx + 1) * (Mx + 1));
+        (p.prec == EZ_MIXED ? mixed_any : f64_any) = true;
       }
-    if (max_groups > 0) {
-      hbox_kernel<<<dim3((unsigned)max_groups, B.n_req, (unsigned)((max_tasks + 255) / 256)), 256, 0, stream>>>(
-          dreqs, (const HboxJob*)dptr(B.o_hj));
-      EZ_LAUNCHED();
+    if (max_cols > 0) {
+      EZ_CUDA(launch_hbox(mixed_any, f64_any, (unsigned)((max_cols + kHboxColsHost - 1) / kHboxColsHost), B.n_req,
+                          dreqs, (const HboxJob*)dptr(B.o_hj), stream));
+      t_launches += (mixed_any ? 1 : 0) + (f64_any ? 1 : 0);
     }
   }
   {

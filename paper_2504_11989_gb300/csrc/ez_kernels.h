@@ -85,7 +85,9 @@ struct EpsteinArgs {
 __global__ void enum_recip_kernel(ReqDesc* reqs, const RecipJob* jobs);
 __global__ void sort_recip_kernel(const ReqDesc* reqs, const RecipJob* jobs);
 __global__ void gbox_kernel(const ReqDesc* reqs, const GboxJob* jobs, int n_jobs);
-__global__ void hbox_kernel(const ReqDesc* reqs, const HboxJob* jobs);
+constexpr int kHboxColsHost = 32;  // hbox_kernel: columns per block (kHboxCols)
+cudaError_t launch_hbox(bool mixed_any, bool f64_any, unsigned col_chunks, int n_req, const ReqDesc* reqs,
+                        const HboxJob* jobs, cudaStream_t st);
 __global__ void phitab_kernel(const PhiJob* jobs);
 __global__ void taylor_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);
 __global__ void taylor_real_kernel(const ReqDesc* reqs, const TaylorJob* jobs, int n_jobs);

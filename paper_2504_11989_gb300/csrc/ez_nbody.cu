@@ -717,103 +717,142 @@ __device__ __forceinline__ float4 ff_complex(double2 z) {
 //   H(ma, 0) at mb = 0,  Hs = H(ma, mb) + H(ma, -mb) at +mb,  Hd = H(ma, mb) - H(ma, -mb) at -mb,
 // as double2 summed in binary64 (FP64 form) or as float-float complex (mixed form: re hi,
 // re lo, im hi, im lo) from compensated binary32 dot products.
-// Grid: (line group, job, chunk of 256 tasks (jn, ma, mb >= 0)), one task per thread.
-__global__ void hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __restrict__ jobs) {
-  const HboxJob& J = jobs[blockIdx.y];
-  const int G = J.g_lo + (int)blockIdx.x;
-  if (G >= J.g_hi) return;
+// Grid: (chunk of kHboxCols columns (jn, ma, mb >= 0), axis j, job).  A block stages its
+// columns' g values along the c axis (both signs of mb) in shared memory once, then computes
+// H for every u node of the axis from them, kHboxU nodes at a time with their phases
+// e^{2 pi i mc u} tabulated; each (column, u node) entry is the same sum, in the same order,
+// as a direct evaluation.  The box is read once per (request, axis) instead of once per line
+// group.
+constexpr int kHboxCols = kHboxColsHost, kHboxU = 32;
+template <bool MIXED>
+__global__ void __launch_bounds__(256) hbox_kernel(const ReqDesc* __restrict__ reqs, const HboxJob* __restrict__ jobs) {
+  using GT = typename std::conditional<MIXED, float2, double>::type;
+  using ET = typename std::conditional<MIXED, float4, double2>::type;
+  __shared__ GT sg[kHboxCols][2][2 * kMaxBoxM + 1];  // [column][+mb, -mb][mc + Mc]
+  __shared__ ET sE[kHboxU][kMaxBoxM + 1];            // [u node of the tile][mc]
+  const HboxJob& J = jobs[blockIdx.z];
+  if (MIXED ? !J.outff : !J.out) return;
   const ReqDesc* R = reqs + J.req;
-  const int nd = R->n_distinct, j = G / R->n_ui, iu = G - j * R->n_ui;
+  const int j = blockIdx.y, n_ui = R->n_ui, nd = R->n_distinct;
+  const int iu_lo = max(0, J.g_lo - j * n_ui), iu_hi = min(n_ui, J.g_hi - j * n_ui);
+  if (iu_hi <= iu_lo) return;
   const int ax_a = j, ax_b = (j + 1) % 3, ax_c = (j + 2) % 3;
   const int Ma = R->M[ax_a], Mb = R->M[ax_b], Mc = R->M[ax_c];
-  const double u = R->u_nodes[iu];
+  const int nHp = (Ma + 1) * (Mb + 1), ncols = nd * nHp;
+  const int c0 = blockIdx.x * kHboxCols;
+  if (c0 >= ncols) return;
+  const int nc = min(kHboxCols, ncols - c0);
   const int st[3] = {R->box[1] * R->box[2], R->box[2], 1};
   const int sta = st[ax_a], stb = st[ax_b], stc = st[ax_c];
   const int gbase = R->M[0] * st[0] + R->M[1] * st[1] + R->M[2] * st[2];
   const long long cells = (long long)R->box[0] * R->box[1] * R->box[2];
-  __shared__ double2 Ec[kMaxBoxM + 1];
-  __shared__ float4 Ec4[kMaxBoxM + 1];
-  for (int mc = threadIdx.x; mc <= Mc; mc += blockDim.x) {
-    double sn, cs;
-    sincospi(2.0 * ((double)mc * u), &sn, &cs);
-    Ec[mc] = make_double2(cs, sn);
-    Ec4[mc] = ff_complex(Ec[mc]);
+  const int nz = 2 * Mc + 1;
+  for (int e = threadIdx.x; e < nc * 2 * nz; e += blockDim.x) {
+    const int col = e / (2 * nz), r = e - col * 2 * nz, sgn = r / nz, z = r - sgn * nz;
+    const int c = c0 + col, jn = c / nHp, q = c - jn * nHp, ma = q / (Mb + 1), mb = q - ma * (Mb + 1);
+    const long long off = (long long)jn * cells + gbase + ma * sta + (sgn ? -mb : mb) * stb + (z - Mc) * stc;
+    if constexpr (MIXED)
+      sg[col][sgn][z] = R->gboxff[off];
+    else
+      sg[col][sgn][z] = R->gbox[off];
   }
-  __syncthreads();
-  const size_t slot = (size_t)(G - J.g_lo) * R->hslot;
-  const int nH = (Ma + 1) * (2 * Mb + 1), nHp = (Ma + 1) * (Mb + 1);
-  if (J.outff) {
-    // mixed form: compensated dot products in binary32 on the float-float box (the FP64 pipe
-    // is 64 times slower per operation); |mc| >= m_hp (below 1e-8) in plain binary32
-    for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < nd * nHp; e += gridDim.z * blockDim.x) {
-      const int jn = e / nHp, r = e - jn * nHp;
-      const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
-      const float2* gp_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta + mb * stb;
-      const float2* gm_ = R->gboxff + (size_t)jn * cells + gbase + ma * sta - mb * stb;
-      float s0 = gp_[0].x, c0 = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
-      const int mc_hp = min(Mc + 1, R->m_hp[ax_c]);
-      for (int mc = 1; mc < mc_hp; ++mc) {
-        const float4 E = Ec4[mc];
-        const float2 a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
-        dot2_acc(s0, c0, a.x, a.y, E.x, E.y);
-        dot2_acc(s0, c0, b.x, b.y, E.x, E.y);
-        dot2_acc(s1, c1, a.x, a.y, E.z, E.w);
-        dot2_acc(s1, c1, -b.x, -b.y, E.z, E.w);
-        dot2_acc(s2, c2, c.x, c.y, E.x, E.y);
-        dot2_acc(s2, c2, dd.x, dd.y, E.x, E.y);
-        dot2_acc(s3, c3, c.x, c.y, E.z, E.w);
-        dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
-      }
-      float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;
-      for (int mc = mc_hp; mc <= Mc; ++mc) {
-        const float4 E = Ec4[mc];
-        const float a = gp_[mc * stc].x, b = gp_[-mc * stc].x, c = gm_[mc * stc].x, dd = gm_[-mc * stc].x;
-        q0 = fmaf(a + b, E.x, q0);
-        q1 = fmaf(a - b, E.z, q1);
-        q2 = fmaf(c + dd, E.x, q2);
-        q3 = fmaf(c - dd, E.z, q3);
-      }
-      const ff pr = ff_two_sum(s0, c0 + q0), pi = ff_two_sum(s1, c1 + q1);
-      const ff mr = ff_two_sum(s2, c2 + q2), mi = ff_two_sum(s3, c3 + q3);
-      const size_t base = slot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
-      if (mb == 0) {
-        J.outff[base] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+  const int nH = (Ma + 1) * (2 * Mb + 1);
+  for (int t0 = iu_lo; t0 < iu_hi; t0 += kHboxU) {
+    const int nt = min(kHboxU, iu_hi - t0);
+    __syncthreads();  // the columns are staged; the previous tile's phases are used up
+    for (int e = threadIdx.x; e < nt * (Mc + 1); e += blockDim.x) {
+      const int t = e / (Mc + 1), mc = e - t * (Mc + 1);
+      double sn, cs;
+      sincospi(2.0 * ((double)mc * R->u_nodes[t0 + t]), &sn, &cs);
+      if constexpr (MIXED)
+        sE[t][mc] = ff_complex(make_double2(cs, sn));
+      else
+        sE[t][mc] = make_double2(cs, sn);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * nt; e += blockDim.x) {
+      const int t = e / nc, col = e - t * nc;
+      const int c = c0 + col, jn = c / nHp, q = c - jn * nHp, ma = q / (Mb + 1), mb = q - ma * (Mb + 1);
+      const GT* gp_ = &sg[col][0][Mc];
+      const GT* gm_ = &sg[col][1][Mc];
+      const ET* Ec = sE[t];
+      const size_t base =
+          (size_t)(j * n_ui + t0 + t - J.g_lo) * R->hslot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
+      if constexpr (MIXED) {
+        // compensated dot products in binary32 on the float-float box; |mc| >= m_hp (below
+        // 1e-8) in plain binary32
+        float s0 = gp_[0].x, c0f = gp_[0].y, s1 = 0.0f, c1 = 0.0f, s2 = gm_[0].x, c2 = gm_[0].y, s3 = 0.0f, c3 = 0.0f;
+        const int mc_hp = min(Mc + 1, R->m_hp[ax_c]);
+        for (int mc = 1; mc < mc_hp; ++mc) {
+          const float4 E = Ec[mc];
+          const float2 a = gp_[mc], b = gp_[-mc], cc = gm_[mc], dd = gm_[-mc];
+          dot2_acc(s0, c0f, a.x, a.y, E.x, E.y);
+          dot2_acc(s0, c0f, b.x, b.y, E.x, E.y);
+          dot2_acc(s1, c1, a.x, a.y, E.z, E.w);
+          dot2_acc(s1, c1, -b.x, -b.y, E.z, E.w);
+          dot2_acc(s2, c2, cc.x, cc.y, E.x, E.y);
+          dot2_acc(s2, c2, dd.x, dd.y, E.x, E.y);
+          dot2_acc(s3, c3, cc.x, cc.y, E.z, E.w);
+          dot2_acc(s3, c3, -dd.x, -dd.y, E.z, E.w);
+        }
+        float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;
+        for (int mc = mc_hp; mc <= Mc; ++mc) {
+          const float4 E = Ec[mc];
+          const float a = gp_[mc].x, b = gp_[-mc].x, cc = gm_[mc].x, dd = gm_[-mc].x;
+          q0 = fmaf(a + b, E.x, q0);
+          q1 = fmaf(a - b, E.z, q1);
+          q2 = fmaf(cc + dd, E.x, q2);
+          q3 = fmaf(cc - dd, E.z, q3);
+        }
+        const ff pr = ff_two_sum(s0, c0f + q0), pi = ff_two_sum(s1, c1 + q1);
+        const ff mr = ff_two_sum(s2, c2 + q2), mi = ff_two_sum(s3, c3 + q3);
+        if (mb == 0) {
+          J.outff[base] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+        } else {
+          const ff sr = ff_add(pr, mr), si = ff_add(pi, mi);
+          const ff dr = ff_add(pr, ff{-mr.hi, -mr.lo}), di = ff_add(pi, ff{-mi.hi, -mi.lo});
+          J.outff[base + mb] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+          J.outff[base - mb] = make_float4(dr.hi, dr.lo, di.hi, di.lo);
+        }
       } else {
-        const ff sr = ff_add(pr, mr), si = ff_add(pi, mi);
-        const ff dr = ff_add(pr, ff{-mr.hi, -mr.lo}), di = ff_add(pi, ff{-mi.hi, -mi.lo});
-        J.outff[base + mb] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
-        J.outff[base - mb] = make_float4(dr.hi, dr.lo, di.hi, di.lo);
+        // H(ma, +-mb): real parts pair g(+mc) + g(-mc) with cos, imaginary parts the difference with sin
+        double pr = gp_[0], pi = 0.0, mr = gm_[0], mi = 0.0;
+        for (int mc = 1; mc <= Mc; ++mc) {
+          const double2 E = Ec[mc];
+          const double a = gp_[mc], b = gp_[-mc], cc = gm_[mc], dd = gm_[-mc];
+          pr = fma(a + b, E.x, pr);
+          pi = fma(a - b, E.y, pi);
+          mr = fma(cc + dd, E.x, mr);
+          mi = fma(cc - dd, E.y, mi);
+        }
+        double2 hs, hd;
+        if (mb == 0) {
+          hs = make_double2(pr, pi);
+          hd = hs;
+        } else {
+          hs = make_double2(pr + mr, pi + mi);
+          hd = make_double2(pr - mr, pi - mi);
+        }
+        J.out[base + mb] = hs;
+        if (mb) J.out[base - mb] = hd;
       }
     }
-    return;
   }
-  for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < nd * nHp; e += gridDim.z * blockDim.x) {
-    const int jn = e / nHp, r = e - jn * nHp;
-    const int ma = r / (Mb + 1), mb = r - ma * (Mb + 1);
-    const double* gp_ = R->gbox + (size_t)jn * cells + gbase + ma * sta + mb * stb;
-    const double* gm_ = R->gbox + (size_t)jn * cells + gbase + ma * sta - mb * stb;
-    // H(ma, +-mb): real parts pair g(+mc) + g(-mc) with cos, imaginary parts the difference with sin
-    double pr = gp_[0], pi = 0.0, mr = gm_[0], mi = 0.0;
-    for (int mc = 1; mc <= Mc; ++mc) {
-      const double2 E = Ec[mc];
-      const double a = gp_[mc * stc], b = gp_[-mc * stc], c = gm_[mc * stc], dd = gm_[-mc * stc];
-      pr = fma(a + b, E.x, pr);
-      pi = fma(a - b, E.y, pi);
-      mr = fma(c + dd, E.x, mr);
-      mi = fma(c - dd, E.y, mi);
-    }
-    double2 hs, hd;
-    if (mb == 0) {
-      hs = make_double2(pr, pi);
-      hd = hs;
-    } else {
-      hs = make_double2(pr + mr, pi + mi);
-      hd = make_double2(pr - mr, pi - mi);
-    }
-    const size_t base = slot + (size_t)jn * nH + ma * (2 * Mb + 1) + Mb;
-    J.out[base + mb] = hs;
-    if (mb) J.out[base - mb] = hd;
+}
+
+cudaError_t launch_hbox(bool mixed_any, bool f64_any, unsigned col_chunks, int n_req, const ReqDesc* reqs,
+                        const HboxJob* jobs, cudaStream_t st) {
+  const dim3 grid(col_chunks, 3, (unsigned)n_req);
+  if (f64_any) {
+    hbox_kernel<false><<<grid, 256, 0, st>>>(reqs, jobs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  if (mixed_any) {
+    hbox_kernel<true><<<grid, 256, 0, st>>>(reqs, jobs);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 // Far field, d = 3.  Block: the four sectors of one line group and vchunk rows v2, all n_v
