@@ -334,6 +334,9 @@ typedef struct {
   size_t far_smem_bytes;    /* dynamic shared memory of one far-field block */
   float t_mix, t_mid;       /* mixed form: binary32 tails beyond t_mix, binary32 polynomial
                                beyond t_mid (3e38 in the FP64 form) */
+  int n_alpha;              /* u_rule 2: Taylor multi-indices alpha of the near part (even
+                               |alpha| <= 2 ell; only all-even alpha on a lattice that every
+                               axis reflection x_i -> -x_i maps onto itself); 0 otherwise */
 } ez_plan_info;
 int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const ez_quadrature* q, ez_plan_info* out);
 

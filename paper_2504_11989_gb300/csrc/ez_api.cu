@@ -1888,6 +1888,7 @@ extern "C" int ez_plan_describe(ez_lattice lat, const ez_sum_spec* spec, const e
   out->far_smem_bytes = p.smem;
   out->t_mix = p.phi[0].t_mix_f;
   out->t_mid = p.phi[0].t_mid_f;
+  out->n_alpha = p.near ? (int)(p.alpha.size() / 3) : 0;
   return EZ_OK;
 }
 

@@ -366,7 +366,7 @@ class ez_plan_info(ctypes.Structure):
                 ("n_u_total", ctypes.c_int), ("u_rule", ctypes.c_int), ("vchunk", ctypes.c_int),
                 ("n_chunks", ctypes.c_int), ("line_lo", ctypes.c_longlong), ("line_hi", ctypes.c_longlong),
                 ("n_far_items", ctypes.c_longlong), ("far_smem_bytes", ctypes.c_size_t), ("t_mix", ctypes.c_float),
-                ("t_mid", ctypes.c_float)]
+                ("t_mid", ctypes.c_float), ("n_alpha", ctypes.c_int)]
 
 
 def ez_plan_describe(lat: "Lattice", spec: ez_sum_spec, q: ez_quadrature) -> ez_plan_info:

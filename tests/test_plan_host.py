@@ -167,3 +167,67 @@ def test_plan_describe_errors_and_fp64_thresholds(ez):
     mixed = _plan(ez, prob, prec=1)
     assert 0.5 < mixed.t_mid <= mixed.t_mix < 40.0
     assert all(1 <= mixed.m_hp[i] <= mixed.M[i] + 1 for i in range(3))
+
+
+def _axis_reflection_invariant(A, radius=3):
+    """Whether every reflection x_i -> -x_i maps the point set A Z^d onto itself, decided on
+    the points A n with |n_j| <= radius (a point set test, independent of any basis algebra)."""
+    d = A.shape[0]
+    grids = np.meshgrid(*[np.arange(-radius, radius + 1)] * d, indexing="ij")
+    n = np.stack([g.ravel() for g in grids])
+    P = A @ n
+    Ainv = np.linalg.inv(A)
+    for i in range(d):
+        R = P.copy()
+        R[i] *= -1.0
+        c = Ainv @ R
+        if np.max(np.abs(c - np.rint(c))) > 1e-9:
+            return False
+    return True
+
+
+def _near_counts(d, ell):
+    """Multi-indices alpha in N^d with |alpha| = 2k, k <= ell: all of them, and the all-even ones."""
+    full = sum(math.comb(2 * k + d - 1, d - 1) for k in range(ell + 1))
+    even = sum(math.comb(k + d - 1, d - 1) for k in range(ell + 1))
+    return full, even
+
+
+def _rot3(seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    return q * np.sign(np.diag(r))
+
+
+NEAR_LATTICES = [
+    ("Z", W.lattice("Z")),
+    ("square", W.lattice("square")),
+    ("hexagonal", W.lattice("hexagonal")),
+    ("oblique", np.array([[1.0, 0.37], [0.0, 1.1]])),
+    ("sc", W.lattice("sc")),
+    ("fcc", W.lattice("fcc")),
+    ("bcc", W.lattice("bcc")),
+    ("orthorhombic", np.diag([1.0, 1.3, 0.8])),
+    ("triclinic", np.array([[1.0, 0.3, 0.2], [0.0, 1.0, 0.1], [0.0, 0.0, 1.0]])),
+    ("rotated sc", _rot3(5)),
+]
+
+
+@pytest.mark.parametrize("ell", [1, 4])
+@pytest.mark.parametrize("name,A", NEAR_LATTICES, ids=[n for n, _ in NEAR_LATTICES])
+def test_near_multi_indices_follow_axis_reflections(ez, name, A, ell):
+    """The near part's Taylor expansion of the regular part of Z (Sec. 3, meromorphic
+    continuation; order 2 ell, Sec. 4.1) keeps
+    every alpha with even |alpha| <= 2 ell; on a lattice that each axis reflection maps onto
+    itself the regular part is even in every component, its odd-alpha coefficients vanish
+    and only the all-even alpha are kept.  The count must follow the point set's symmetry,
+    not the basis: a rotated simple cubic lattice keeps them all."""
+    d = A.shape[0]
+    spec = ez.sum_spec(list(W.ATM_NU), [list(r) for r in W.ATM_EXPO])
+    q = ez.quadrature(W.Quad(n_u=4, n_v=8, u_rule=2, ell=ell, **AUTO))
+    info = ez.ez_plan_describe(ez.Lattice(A), spec, q)
+    full, even = _near_counts(d, ell)
+    want = even if _axis_reflection_invariant(A) else full
+    assert info.n_alpha == want
+    assert _axis_reflection_invariant(A) == (name not in ("oblique", "triclinic", "rotated sc"))
+    far = ez.ez_plan_describe(ez.Lattice(A), spec, ez.quadrature(W.Quad(n_u=4, n_v=8, u_rule=1, **AUTO)))
+    assert far.n_alpha == 0
