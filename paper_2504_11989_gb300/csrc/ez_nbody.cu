@@ -995,7 +995,29 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         }
       }
     }
+  } else {
+    // binary32 parts of k for the cutoff screen (k = kb + p1 ka per node): the binary32
+    // roundings of the binary64 parts the node loop forms, one conversion per part and block
+    const int ax_c = (j + 2) % 3;
+    float* kAf = reinterpret_cast<float*>(kA);
+    float* kBf = reinterpret_cast<float*>(kB);
+    for (int e = threadIdx.x; e < nv + 2 * nv2; e += blockDim.x) {
+      if (e < nv) {
+        const double kta = u * R->v_nodes[e];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kAf[e * 3 + i] = (float)(R->AiTs[i * 3 + ax_a] * kta);
+      } else {
+        const int q = e - nv, s2 = q / nv2, v2l = q - s2 * nv2;
+        const double ktb = u * (s2 ? -R->v_nodes[v2_0 + v2l] : R->v_nodes[v2_0 + v2l]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          kBf[(s2 * vch + v2l) * 3 + i] = (float)fma(R->AiTs[i * 3 + ax_b], ktb, R->AiTs[i * 3 + ax_c] * u);
+      }
+    }
   }
+  // pref_j vol_fac per exponent: the FP64 node value is one FMA on the scaled B (below)
+  __shared__ double s_pv[NDM];
+  if (threadIdx.x < nd && threadIdx.x < NDM) s_pv[threadIdx.x] = R->pref[threadIdx.x] * R->vol_fac;
   __syncthreads();
 
   // B_{+-}(ma, v2) = X +- Y: one thread per (jn, ma, v2)
@@ -1043,8 +1065,11 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         xi = fma(hs.y, E.x, xi);
         yi = fma(hd.x, E.y, yi);
       }
-      B[bo] = make_double2(xr + yr, xi + yi);
-      B[nBs + bo] = make_double2(xr - yr, xi - yi);
+      // scaled by pref_j, with -pref_j 2/nu_j in the real part of the m_a = 0 entry: the
+      // node's Z_j = pref_j (Zp_j + vol_fac acc_j - 2/nu_j) is then one FMA on its Zp_j
+      const double pf = R->pref[jn], c = ma == 0 ? pf * R->two_over_nu[jn] : 0.0;
+      B[bo] = make_double2(fma(pf, xr + yr, -c), pf * (xi + yi));
+      B[nBs + bo] = make_double2(fma(pf, xr - yr, -c), pf * (xi - yi));
     }
   }
   __syncthreads();
@@ -1199,13 +1224,19 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
           for (int i = 0; i < 3; ++i) k[i] = kb[i] + ka[i];
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn) acc[jn] = 0.0;
-          const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+          float kf[3];
+          {
+            const float* kaf = reinterpret_cast<const float*>(kA) + v1 * 3;
+            const float* kbf = reinterpret_cast<const float*>(kB) + (s2 * vch + v2l) * 3;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) kf[i] = q ? kbf[i] - kaf[i] : kbf[i] + kaf[i];
+          }
           const NodeDir nd0{dirlw ? dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1 : nullptr,
                             s_ublk};
           recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, nd0);
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
-            if (jn < nd) Z[jn] = R->pref[jn] * (Zp[jn] + R->vol_fac * acc[jn] - R->two_over_nu[jn]);
+            if (jn < nd) Z[jn] = fma(s_pv[jn], acc[jn], Zp[jn]);
           products<NDM>(R, nd, np, Z, wv, wsum);
 #pragma unroll
           for (int i = 0; i < 3; ++i) ka[i] = -ka[i];
