@@ -42,11 +42,11 @@ HEADLINE_LATTICES = ("sc", "fcc", "bcc")
 PROFILES = {
     # far_kernel_d3<FP64, 4 exponents>, config 3: DRAM bytes read + written, mean of four
     # launches of the --metrics capture of the current build in
-    # profiles/far_kernel_d3_config3.md (20.48-20.68 MB read, 0.28-0.35 MB written)
-    "far_d3_f64_dram_bytes_per_launch": 20929792,
+    # profiles/far_kernel_d3_config3.md (20.49-20.64 MB read, 0.12-0.26 MB written)
+    "far_d3_f64_dram_bytes_per_launch": 20719808,
     # far_kernel_d3<mixed, 4 exponents>: issue-slot, binary32-pipe and binary64-pipe utilisation
     # (--set full capture of the current build, profiles/far_kernel_d3_config3.md)
-    "far_d3_mixed_issue_frac": 0.390,
+    "far_d3_mixed_issue_frac": 0.391,
     "far_d3_mixed_fp32_pipe_frac": 0.215,
     "far_d3_mixed_fp64_pipe_frac": 0.353,
     # far_kernel_d2<FP64, 1 exponent>, config 2, 128 sums (profiles/far_kernel_d2_config2.md)

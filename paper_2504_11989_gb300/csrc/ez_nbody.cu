@@ -295,7 +295,7 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         if (D >= 3) qq = fma(k2v[2], G.z, qq);
         ++qterms;
         if (qq > 0.0) {
-          const double t = sphi[0].c_lam * qq;
+          const double t = D == 3 ? qq : sphi[0].c_lam * qq;  // c_lam = 1 (scaled units); d = 3 skips it
           double lt, it, st;
           small_t_aux(sphi, nd, true, t, nd0, G.w == 0.0, lt, it, st);
           const float* brk[NDM];
@@ -327,7 +327,7 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
           if (D >= 2) qq = fma(k2v[1], G.y, qq);
           if (D >= 3) qq = fma(k2v[2], G.z, qq);
           ++qterms;
-          const double t = sphi[0].c_lam * qq;
+          const double t = D == 3 ? qq : sphi[0].c_lam * qq;  // c_lam = 1 (scaled units); d = 3 skips it
           int n0 = 0, n1 = 0;
           const double v0 = c0 ? __ldg(r0 + 4) : phi_poly(r0, fma(qq, so0.y, __ldg(r0 + 2)), n0);
           const double v1 = c1 ? __ldg(r1 + 4) : phi_poly(r1, fma(qq, so1.y, __ldg(r1 + 2)), n1);
@@ -662,16 +662,34 @@ __device__ __forceinline__ ff ffd(double x) {
   return r;
 }
 
-template <int NDM>
+// Products of the node's zeta values, weighted and accumulated per product.  FIRST: each
+// product starts from its first factor (the d = 3 kernel: one binary64 multiplication fewer
+// per product); the d = 1, 2 kernels keep the loop from 1, which holds fewer registers there.
+template <int NDM, bool FIRST = false>
 __device__ __forceinline__ void products(const ReqDesc* R, int nd, int np, const double* Z, double w,
                                          double (&acc)[EZ_MAX_PROD]) {
 #pragma unroll
   for (int p = 0; p < EZ_MAX_PROD; ++p) {
     if (p >= np) break;
     double f = 1.0;
-    for (int j = 0; j < nd; ++j) {
-      const int e = R->expo[p][j];
-      for (int q = 0; q < e; ++q) f *= Z[j];
+    if constexpr (FIRST) {
+      bool first = true;
+#pragma unroll
+      for (int j = 0; j < NDM; ++j)
+        if (j < nd) {
+          int e = R->expo[p][j];
+          if (e > 0 && first) {
+            f = Z[j];
+            first = false;
+            --e;
+          }
+          for (int q = 0; q < e; ++q) f *= Z[j];
+        }
+    } else {
+      for (int j = 0; j < nd; ++j) {
+        const int e = R->expo[p][j];
+        for (int q = 0; q < e; ++q) f *= Z[j];
+      }
     }
     acc[p] = fma(w, f, acc[p]);
   }
@@ -1213,8 +1231,9 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
               s0 = fma(E.x, bb.x, s0);
               s1 = fma(E.y, bb.y, s1);
             }
-            Zp[jn] = fma(2.0, s0 - s1, b[0].x);
-            zsm[jn * 256 + threadIdx.x] = fma(2.0, s0 + s1, b[0].x);
+            const double t0 = fma(2.0, s0, b[0].x);
+            Zp[jn] = fma(-2.0, s1, t0);
+            zsm[jn * 256 + threadIdx.x] = fma(2.0, s1, t0);
           }
         }
 #pragma unroll 1
@@ -1237,7 +1256,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) Z[jn] = fma(s_pv[jn], acc[jn], Zp[jn]);
-          products<NDM>(R, nd, np, Z, wv, wsum);
+          products<NDM, true>(R, nd, np, Z, wv, wsum);
 #pragma unroll
           for (int i = 0; i < 3; ++i) ka[i] = -ka[i];
 #pragma unroll
