@@ -42,8 +42,8 @@ HEADLINE_LATTICES = ("sc", "fcc", "bcc")
 PROFILES = {
     # far_kernel_d3<FP64, 4 exponents>, config 3: DRAM bytes read + written, mean of four
     # launches of the --metrics capture of the current build in
-    # profiles/far_kernel_d3_config3.md (20.49-20.64 MB read, 0.12-0.26 MB written)
-    "far_d3_f64_dram_bytes_per_launch": 20719808,
+    # profiles/far_kernel_d3_config3.md (20.50-20.73 MB read, 0.35-0.37 MB written)
+    "far_d3_f64_dram_bytes_per_launch": 20932416,
     # far_kernel_d3<mixed, 4 exponents>: issue-slot, binary32-pipe and binary64-pipe utilisation
     # (--set full capture of the current build, profiles/far_kernel_d3_config3.md)
     "far_d3_mixed_issue_frac": 0.391,

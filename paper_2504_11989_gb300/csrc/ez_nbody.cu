@@ -248,7 +248,9 @@ __device__ __forceinline__ void chain_values(const PhiInfo* sphi, int nd, double
 // nd0: the node's direction-table entry (d = 3; its h = 0 term's log t, 1/t, sqrt t).
 // With an order chain the terms with t < kT0 take the chain (chain_values), log t and 1/t
 // shared by the orders; other orders evaluate their t < kT0 terms one by one (phi_small).
-template <int D, int NDM>
+// K2: k holds 2k (the d = 3 kernel forms it from doubled constants; scaling by powers of two
+// is exact, so every value is the same as from k).
+template <int D, int NDM, bool K2 = false>
 __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi, int nd, const double* k,
                                           const float* kf, double* acc, unsigned& terms, unsigned& coefs,
                                           unsigned& qterms, const RecCacheF64& rc, const NodeDir& nd0) {
@@ -262,10 +264,20 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
   // term (for k in the reduced cell |G + k| is not much smaller than |G|: no cancellation
   // beyond a few ulp)
   double k2v[3] = {0.0, 0.0, 0.0}, kk2 = 0.0;
+  if constexpr (K2) {
+    double q2 = 0.0;  // |2k|^2
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    k2v[i] = 2.0 * k[i];
-    kk2 = fma(k[i], k[i], kk2);
+    for (int i = 0; i < D; ++i) {
+      k2v[i] = k[i];
+      q2 = fma(k[i], k[i], q2);
+    }
+    kk2 = 0.25 * q2;
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      k2v[i] = 2.0 * k[i];
+      kk2 = fma(k[i], k[i], kk2);
+    }
   }
   for (int hh = 0; hh < nrec; ++hh) {
     const int h = list ? rc.idx[hh] : hh;
@@ -294,10 +306,12 @@ __device__ __forceinline__ void recip_sum(const ReqDesc* R, const PhiInfo* sphi,
         if (D >= 2) qq = fma(k2v[1], G.y, qq);
         if (D >= 3) qq = fma(k2v[2], G.z, qq);
         ++qterms;
-        if (qq > 0.0) {
+        // qq > 0 and |G|^2 == 0 as integer tests on the binary64 words (neither value is a
+        // NaN; a positive double has a positive bit pattern): off the FP64 pipe
+        if (__double_as_longlong(qq) > 0) {
           const double t = D == 3 ? qq : sphi[0].c_lam * qq;  // c_lam = 1 (scaled units); d = 3 skips it
           double lt, it, st;
-          small_t_aux(sphi, nd, true, t, nd0, G.w == 0.0, lt, it, st);
+          small_t_aux(sphi, nd, true, t, nd0, __double_as_longlong(G.w) == 0, lt, it, st);
           const float* brk[NDM];
 #pragma unroll
           for (int j = 0; j < NDM; ++j) brk[j] = sphi[j].ser_brk;
@@ -1093,23 +1107,25 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
   __syncthreads();
 
   const int ax_c = (j + 2) % 3;
+  // 2 A^{-T} columns: the FP64 node loop forms 2k directly (exact scaling)
   double kca[3], kcb[3], kcc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    kca[i] = R->AiTs[i * 3 + ax_a];
-    kcb[i] = R->AiTs[i * 3 + ax_b];
-    kcc[i] = R->AiTs[i * 3 + ax_c];
+    kca[i] = 2.0 * R->AiTs[i * 3 + ax_a];
+    kcb[i] = 2.0 * R->AiTs[i * 3 + ax_b];
+    kcc[i] = 2.0 * R->AiTs[i * 3 + ax_c];
   }
   unsigned terms = 0, coefs = 0, qterms = 0;
   const int nn = nv * nv2;
   for (int s2 = 0; s2 < 2; ++s2) {  // p2 = +1, -1
     if constexpr (!MIXED && NDM >= 4) {  // candidates: k = u A^{-T} (alpha e_a + p2 beta e_b + e_c), alpha = p1 v1, beta = v2
       double c0[3], da[3], db[3];
+      const double hu = 0.5 * u;  // the constants are doubled
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        c0[i] = kcc[i] * u;
-        da[i] = kca[i] * u;
-        db[i] = kcb[i] * (s2 ? -u : u);
+        c0[i] = kcc[i] * hu;
+        da[i] = kca[i] * hu;
+        db[i] = kcb[i] * (s2 ? -hu : hu);
       }
       double b0 = R->v_nodes[v2_0], b1 = b0;
       for (int q = 1; q < nv2; ++q) {
@@ -1211,7 +1227,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
         const double kta = u * R->v_nodes[v1];
         const double ktb = u * (s2 ? -R->v_nodes[v2_0 + v2l] : R->v_nodes[v2_0 + v2l]);
         const double wv = R->v_w[v1] * R->v_w[v2_0 + v2l];
-        // k = kb + ka (p1 = +1), then kb - ka
+        // 2k = 2kb + 2ka (p1 = +1), then 2kb - 2ka
         double ka[3], kb[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -1252,7 +1268,7 @@ __global__ void __launch_bounds__(256, (MIXED && NDM == 1) ? 3 : 2) far_kernel_d
           }
           const NodeDir nd0{dirlw ? dirlw + (((size_t)(j * 2 + q) * 2 + s2) * nv + v2_0 + v2l) * nv + v1 : nullptr,
                             s_ublk};
-          recip_sum<3, NDM>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, nd0);
+          recip_sum<3, NDM, true>(R, sphi, nd, k, kf, acc, terms, coefs, qterms, rcache, nd0);
 #pragma unroll
           for (int jn = 0; jn < NDM; ++jn)
             if (jn < nd) Z[jn] = fma(s_pv[jn], acc[jn], Zp[jn]);
